@@ -1,0 +1,195 @@
+"""Oracle: a plain CPU kernel-independent FMM in FP64, in the paper's order.
+
+TEST INFRASTRUCTURE ONLY (the CPU oracle; never imported by the product path).
+
+Sec. 3 of the paper (after Ying, Biros & Zorin 2004):
+* multipole expansion, Eq. (s2m): the upward check potential q^{B,u} on the check
+  surface x^{B,u} is evaluated from the sources in a leaf B, and the upward
+  equivalent density phi^{B,u} on y^{B,u} solves G(x^{B,u}, y^{B,u}) phi = q
+  (pseudo-inverse);
+* M2M, Eq. (m2m): the children's phi^{C,u} give the parent's check potential;
+* M2L, Eq. (m2l), S2L for the adaptive X list, L2L, Eq. (l2l): the downward
+  check potential q^{B,d} on x^{B,d}, then phi^{B,d} on y^{B,d} from the
+  downward pseudo-inverse, Eq. (s2l);
+* targets (outline step 4): the local expansion, the W list's upward densities
+  and the near-field direct sum over U(B).
+
+Surfaces (Fig. fmulloc, Fig. m2mm2ll2l): the m0 x m0 x m0 lattice on the boundary
+of [-1, 1]^3, scaled about the box centre. The radii are read off the figure
+coordinates (box half-width 0.8, surfaces at 0.96 and 2.08): the upward
+equivalent and downward check surfaces at 1.2 r, the upward check and
+downward equivalent surfaces at 2.6 r (r = half-width of the box).
+
+Pseudo-inverse (Sec. 3, after the outline: the original pseudo-inverse of the
+cited KIFMM, m0 = 6 by default): a truncated SVD that keeps singular values
+sigma_k >= eps * sigma_max. The kernel has two length scales (1/a, 1/b), so
+every operator depends on the level.
+
+The self term sigma(h_i) I_i and the factor C are added at the end as in
+``direct.direct_sum``. Expansions exist for boxes of level >= 2 (the V lists
+of level-0 and level-1 boxes are empty).
+"""
+import numpy as np
+
+from . import kernel as _k
+from . import tree as _t
+from .direct import pair_sum_c, self_terms
+
+R_INNER = 1.2   # upward equivalent / downward check surface, in box half-widths
+R_OUTER = 2.6   # upward check / downward equivalent surface
+
+
+def surface_lattice(m0):
+    """Lattice points of {-1 + 2j/(m0-1)}^3 on the boundary of the cube, ordered
+    with x fastest."""
+    g = -1.0 + 2.0 * np.arange(m0) / (m0 - 1)
+    pts = []
+    for k in range(m0):
+        for j in range(m0):
+            for i in range(m0):
+                if i in (0, m0 - 1) or j in (0, m0 - 1) or k in (0, m0 - 1):
+                    pts.append((g[i], g[j], g[k]))
+    return np.array(pts, dtype=np.float64)
+
+
+def kmat(X, Y, a, b):
+    """Matrix of kernel values K(|X_i - Y_j|)."""
+    d = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
+    return _k.kernel(d, a, b)
+
+
+def truncated_pinv(A, eps):
+    U, s, Vt = np.linalg.svd(A)
+    keep = s >= eps * s[0]
+    return (Vt[keep].T / s[keep]) @ U[:, keep].T
+
+
+def _offset_index(d):
+    return (d[0] + 3) + 7 * (d[1] + 3) + 49 * (d[2] + 3)
+
+
+def _octant(o):
+    return np.array([(o & 1), (o >> 1) & 1, (o >> 2) & 1], dtype=np.float64)
+
+
+class Operators:
+    """Per-level matrices, all kernel values between surfaces (Eqs. (s2m)-(l2l))."""
+
+    def __init__(self, side, nlevels, m0, a, b, eps=1e-5):
+        s = surface_lattice(m0)
+        self.surf = s
+        self.S = s.shape[0]
+        self.uc2ue, self.dc2de, self.m2m, self.l2l, self.m2l = {}, {}, {}, {}, {}
+        for lev in range(2, nlevels):
+            r = side / 2.0 ** (lev + 1)
+            # Eq. (s2m): G(x^{B,u}, y^{B,u}); Eq. (s2l): G(x^{B,d}, y^{B,d})
+            self.uc2ue[lev] = truncated_pinv(kmat(R_OUTER * r * s, R_INNER * r * s, a, b), eps)
+            self.dc2de[lev] = truncated_pinv(kmat(R_INNER * r * s, R_OUTER * r * s, a, b), eps)
+            # Eq. (m2l): G(x^{B,d}, y^{A,u}) for c_A - c_B = 2 r delta
+            for dz in range(-3, 4):
+                for dy in range(-3, 4):
+                    for dx in range(-3, 4):
+                        if max(abs(dx), abs(dy), abs(dz)) < 2:
+                            continue
+                        off = 2.0 * r * np.array([dx, dy, dz], dtype=np.float64)
+                        self.m2l[(lev, _offset_index((dx, dy, dz)))] = kmat(
+                            R_INNER * r * s, off + R_INNER * r * s, a, b)
+            if lev + 1 < nlevels:
+                rc = r / 2.0
+                for o in range(8):
+                    cc = rc * (2.0 * _octant(o) - 1.0)   # child centre - parent centre
+                    # Eq. (m2m): G(x^{P,u}, y^{C,u})
+                    self.m2m[(lev, o)] = kmat(R_OUTER * r * s, cc + R_INNER * rc * s, a, b)
+                    # Eq. (l2l): G(x^{C,d}, y^{P,d})
+                    self.l2l[(lev, o)] = kmat(cc + R_INNER * rc * s, R_OUTER * r * s, a, b)
+
+
+def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None):
+    points = np.asarray(points, dtype=np.float64)
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
+    t, perm = _t.build_tree(points, h, leaf_size, origin, side)
+    U, V, W, X = _t.build_lists(t)
+    ops = Operators(t.side, t.nlevels, m0, a, b, eps)
+    return dict(tree=t, perm=perm, U=U, V=V, W=W, X=X, ops=ops, points=points[perm],
+                h=h[perm], a=a, b=b, m0=m0)
+
+
+def evaluate(p, I, C=1.0, mode="cell_exact"):
+    """S in input order for source values I (input order)."""
+    t, ops, a, b = p["tree"], p["ops"], p["a"], p["b"]
+    perm = p["perm"]
+    pts, h = p["points"], p["h"]
+    Is = np.asarray(I, dtype=np.float64)[perm]
+    q = Is * h ** 3
+    s = ops.surf
+    nb = len(t.level)
+    S = ops.S
+    centre = np.array([_t.box_center(t, b_) for b_ in range(nb)])
+    rad = t.side / 2.0 ** (t.level + 1)
+
+    # ---- upward pass (post-order: deepest level first), Eqs. (s2m), (m2m)
+    phi_u = np.zeros((nb, S))
+    for lev in range(t.nlevels - 1, 1, -1):
+        for B in range(t.level_start[lev], t.level_start[lev + 1]):
+            if t.leaf[B]:
+                xc = centre[B] + R_OUTER * rad[B] * s
+                sl = slice(t.pstart[B], t.pend[B])
+                chk = kmat(xc, pts[sl], a, b) @ q[sl]
+            else:
+                chk = np.zeros(S)
+                for o in range(8):
+                    c = t.child[B][o]
+                    if c >= 0:
+                        chk += ops.m2m[(lev, o)] @ phi_u[c]
+            phi_u[B] = ops.uc2ue[lev] @ chk
+
+    # ---- downward pass (pre-order: shallowest level first), Eqs. (m2l), (l2l), (s2l)
+    phi_d = np.zeros((nb, S))
+    for lev in range(2, t.nlevels):
+        lo, hi = t.level_start[lev], t.level_start[lev + 1]
+        chk = np.zeros((hi - lo, S))
+        # V list, taken offset by offset: every pair (B, A) with A - B = delta
+        # shares the matrix G(x^{B,d}, y^{A,u}).
+        groups = {}
+        for B in range(lo, hi):
+            for A in p["V"][B]:
+                d = t.anchor[A] - t.anchor[B]
+                groups.setdefault(_offset_index(d), []).append((B - lo, A))
+        for key, pairs in groups.items():
+            tb = np.array([x[0] for x in pairs])
+            sa = np.array([x[1] for x in pairs])
+            np.add.at(chk, tb, phi_u[sa] @ ops.m2l[(lev, key)].T)
+        for B in range(lo, hi):
+            xc = centre[B] + R_INNER * rad[B] * s
+            for A in p["X"][B]:                      # S2L from the sources of leaf A
+                sl = slice(t.pstart[A], t.pend[A])
+                chk[B - lo] += kmat(xc, pts[sl], a, b) @ q[sl]
+            P = int(t.parent[B])
+            if t.level[P] >= 2:                      # L2L from the parent
+                o = int((t.anchor[B][0] & 1) | ((t.anchor[B][1] & 1) << 1) | ((t.anchor[B][2] & 1) << 2))
+                chk[B - lo] += ops.l2l[(lev - 1, o)] @ phi_d[P]
+        phi_d[lo:hi] = chk @ ops.dc2de[lev].T
+
+    # ---- targets (outline step 4)
+    out = np.zeros(pts.shape[0])
+    for B in range(nb):
+        if not t.leaf[B]:
+            continue
+        sl = slice(t.pstart[B], t.pend[B])
+        x = pts[sl]
+        acc = np.zeros(x.shape[0])
+        if t.level[B] >= 2:                          # local expansion
+            acc += kmat(x, centre[B] + R_OUTER * rad[B] * s, a, b) @ phi_d[B]
+        for A in p["W"][B]:                          # W list: upward densities
+            acc += kmat(x, centre[A] + R_INNER * rad[A] * s, a, b) @ phi_u[A]
+        src = np.concatenate([np.arange(t.pstart[A], t.pend[A]) for A in p["U"][B]])
+        acc += pair_sum_c(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b)
+        out[sl] = acc
+    out += self_terms(h, a, b, mode) * Is
+    res = np.empty_like(out)
+    res[perm] = C * out
+    return res
+
+
+def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5):
+    return evaluate(plan(points, h, leaf_size, m0, a, b, eps), I, C, mode)

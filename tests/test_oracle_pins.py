@@ -1,0 +1,215 @@
+"""The oracle pinned to things other than itself: library special functions, closed
+forms (Frullani's integral, the uniformly emitting ball), an independent quadrature
+of the self-cell integral, brute force on tiny inputs, the uniform-grid FFT
+convolution, symmetries, and the list definitions by exhaustive enumeration."""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, special
+
+from oracle import direct as D
+from oracle import kernel as K
+from oracle import kifmm as KF
+from oracle import tree as T
+from paper_2006_03515_gb300 import workloads as W
+
+PRESSURES = [(5.25, 300.0), (5.32, 304.0), (0.532, 30.4), (0.0532, 3.04)]
+
+
+# ---- kernel and E1 -----------------------------------------------------------------------
+def test_e1_matches_scipy():
+    xs = np.concatenate([np.logspace(-10, 0, 41), np.linspace(1.0, 3.0, 21), np.logspace(0.5, 2.8, 31)])
+    for x in xs:
+        assert K.expint_e1(x) == pytest.approx(special.exp1(x), rel=2e-14)
+
+
+@pytest.mark.parametrize("a,b", PRESSURES)
+def test_kernel_has_unit_mass(a, b):
+    # Frullani: int_0^inf (e^{-aR} - e^{-bR}) / (R ln(b/a)) dR = 1, i.e. int K dV = 1.
+    f = lambda R: float(K.kernel(R, a, b)) * 4 * math.pi * R * R
+    pts = np.logspace(math.log10(1e-6 / b), math.log10(80.0 / a), 40)
+    total = integrate.quad(f, 0.0, pts[0], limit=200)[0]
+    for lo, hi in zip(pts[:-1], pts[1:]):
+        total += integrate.quad(f, lo, hi, limit=200)[0]
+    total += integrate.quad(f, pts[-1], np.inf, limit=200)[0]
+    assert total == pytest.approx(1.0, abs=2e-10)
+
+
+def test_kernel_is_g_over_4pi_r2():
+    # Eq. (integral): K(r) = g(r) / (4 pi r^2), g from Eq. (gfun) with p_O2 = 150 Torr.
+    r = np.logspace(-5, 0.5, 50)
+    a, b = K.absorption_coefficients(150.0)
+    g = K.g_over_po2(r, 150.0) * 150.0
+    np.testing.assert_allclose(K.kernel(r, a, b), g / (4 * math.pi * r * r), rtol=1e-12)
+
+
+@pytest.mark.parametrize("a,b", PRESSURES)
+@pytest.mark.parametrize("rho", [1e-3, 0.01, 0.1, 1.0])
+def test_ball_centre_closed_form(a, b, rho):
+    # centre of a uniformly emitting ball of radius rho: (ln(b/a) + E1(b rho) - E1(a rho)) / ln(b/a),
+    # against a radial quadrature of the kernel itself
+    f = lambda R: float(K.kernel(R, a, b)) * 4 * math.pi * R * R
+    brk = sorted(set([rho * t for t in (1e-6, 1e-4, 1e-2, 0.1, 0.3, 1.0)] + [min(rho, 1.0 / b)]))
+    total, lo = 0.0, 0.0
+    for hi in brk:
+        if hi > lo:
+            total += integrate.quad(f, lo, hi, limit=200, epsabs=0, epsrel=1e-13)[0]
+            lo = hi
+    assert K.radial_mass(rho, a, b) == pytest.approx(total, rel=1e-11)
+
+
+def _sigma_duffy(h, a, b, n=48):
+    """Self-cell integral by an independent route: the cube split into six pyramids with
+    apex at the centre, y = t (u, v, h/2), dy = t^2 (h/2) dt du dv, so that
+    K(t R) t^2 stays bounded as t -> 0; Gauss-Legendre in t, u, v on the kernel."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    t = 0.5 * (x + 1)
+    wt = 0.5 * w
+    u = 0.5 * h * x
+    wu = 0.5 * h * w
+    U, V = np.meshgrid(u, u, indexing="ij")
+    WU = np.outer(wu, wu)
+    Rf = np.sqrt(U * U + V * V + 0.25 * h * h)
+    tot = 0.0
+    for tk, wk in zip(t, wt):
+        tot += wk * np.sum(WU * K.kernel(tk * Rf, a, b) * tk * tk * (0.5 * h))
+    return 6.0 * tot
+
+
+@pytest.mark.parametrize("a,b", PRESSURES)
+@pytest.mark.parametrize("h", [1.0 / 32, 1.0 / 128, 1.0 / 512])
+def test_sigma_cell_exact_independent(a, b, h):
+    ref = _sigma_duffy(h, a, b)
+    assert K.sigma_cell_exact(h, a, b) == pytest.approx(ref, rel=2e-10)
+
+
+def test_sigma_cell_exact_large_cell_is_unit_mass():
+    # a cube much larger than 1/a holds the whole kernel mass (Frullani)
+    assert K.sigma_cell_exact(40.0, 5.25, 300.0) == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("a,b", PRESSURES)
+def test_sigma_paper_gl2_is_2pt_gauss_legendre(a, b):
+    # Sec. 3: second-order Gauss-Legendre in each axis; all 8 nodes lie at distance h/2
+    h = 1.0 / 32
+    x, w = np.polynomial.legendre.leggauss(2)
+    s = 0.0
+    for i in range(2):
+        for j in range(2):
+            for k in range(2):
+                r = 0.5 * h * math.sqrt(x[i] ** 2 + x[j] ** 2 + x[k] ** 2)
+                s += (0.5 * h) ** 3 * w[i] * w[j] * w[k] * float(K.kernel(r, a, b))
+    assert K.sigma_paper_gl2(h, a, b) == pytest.approx(s, rel=1e-13)
+
+
+# ---- direct sum ---------------------------------------------------------------------------
+def _tiny(seed=3, n=40):
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 3)) * 0.2
+    h = rng.choice([0.01, 0.02], size=n)
+    I = rng.random(n) * 1e3
+    return pts, h, I
+
+
+@pytest.mark.parametrize("mode", K.SELF_MODES)
+def test_direct_sum_brute_force(mode):
+    pts, h, I = _tiny()
+    a, b = 5.32, 304.0
+    ref = D.brute_force(pts.tolist(), h.tolist(), I.tolist(), a, b, C=0.7, mode=mode)
+    np.testing.assert_allclose(D.direct_sum(pts, h, I, a, b, 0.7, mode, impl="c"), ref, rtol=1e-12)
+    np.testing.assert_allclose(D.direct_sum(pts, h, I, a, b, 0.7, mode, impl="numpy"), ref, rtol=1e-12)
+
+
+@pytest.mark.parametrize("a,b", [(5.32, 304.0), (0.0532, 3.04)])
+def test_fft_equals_direct(a, b):
+    pts, h = W.uniform_grid(None, n_xyz=(12, 10, 8), Lxyz=(0.12, 0.10, 0.08))
+    I = W.gaussian(pts, (0.06, 0.05, 0.04), 0.02, 1e20)
+    ref = D.direct_sum(pts, np.full(len(pts), h), I, a, b)
+    got = D.fft_uniform(I.reshape(8, 10, 12), h, a, b).ravel()
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-12 * np.abs(ref).max())
+
+
+def test_direct_symmetry_and_linearity():
+    pts, h, I = W.config_uniform(10)
+    a, b = 5.25, 300.0
+    S = D.direct_sum(pts, h, I, a, b).reshape(10, 10, 10)
+    for perm in [(1, 0, 2), (2, 1, 0), (0, 2, 1)]:
+        np.testing.assert_allclose(np.transpose(S, perm), S, rtol=1e-12)
+    np.testing.assert_allclose(S[::-1], S, rtol=1e-12)
+    I2 = np.random.default_rng(1).random(len(pts))
+    S2 = D.direct_sum(pts, h, I2, a, b)
+    S12 = D.direct_sum(pts, h, 2.0 * I + 3.0 * I2, a, b)
+    np.testing.assert_allclose(S12, 2.0 * S.ravel() + 3.0 * S2, rtol=1e-12)
+
+
+# ---- tree and lists -----------------------------------------------------------------------
+def _cloud(seed):
+    pts, h, I = W.random_cloud(500, seed)
+    pts[:250] = 0.31 + 0.07 * pts[:250]
+    return pts, h
+
+
+@pytest.mark.parametrize("seed,leaf", [(1, 8), (2, 5), (3, 20)])
+def test_lists_match_set_definitions(seed, leaf):
+    pts, h = _cloud(seed)
+    t, perm = T.build_tree(pts, h, leaf)
+    assert sorted(perm.tolist()) == list(range(len(pts)))
+    fast = T.build_lists(t)
+    slow = T.build_lists_bruteforce(t)
+    for k in range(4):
+        assert fast[k] == slow[k], "list %s differs" % "UVWX"[k]
+    assert any(len(x) for x in fast[2]) and any(len(x) for x in fast[3])   # adaptive case exercised
+    for _, cnt in T.coverage(t, *fast):
+        assert np.all(cnt == 1)
+
+
+def test_tree_boxes_contain_their_points():
+    pts, h = _cloud(4)
+    t, perm = T.build_tree(pts, h, 6)
+    sp = pts[perm]
+    for b in range(len(t.level)):
+        r = T.half_width(t, t.level[b])
+        c = T.box_center(t, b)
+        p = sp[t.pstart[b]:t.pend[b]]
+        assert np.all(np.abs(p - c) <= r * (1 + 1e-12))
+        assert (t.pend[b] - t.pstart[b] <= 6) or not t.leaf[b]
+    # every level-l box is numbered in Morton order
+    for l in range(t.nlevels):
+        lo, hi = t.level_start[l], t.level_start[l + 1]
+        codes = T.interleave(t.anchor[lo:hi])
+        assert np.all(np.diff(codes.astype(np.float64)) > 0)
+
+
+def test_duplicate_point_rejected():
+    pts, h = _cloud(5)
+    pts[7] = pts[3]
+    with pytest.raises(ValueError):
+        T.build_tree(pts, h, 8)
+
+
+def test_uniform_tree_shape():
+    pts, h, _ = W.config_uniform(16)
+    t, _ = T.build_tree(pts, h, 64)
+    assert t.nlevels == 3 and t.leaf.sum() == 64 and t.side == 1.0
+    assert np.all(t.origin == 0.0)
+
+
+# ---- KIFMM ---------------------------------------------------------------------------------
+def test_kifmm_with_one_leaf_is_the_direct_sum():
+    pts, h = _cloud(6)
+    I = np.random.default_rng(0).random(len(pts))
+    ref = D.direct_sum(pts, h, I, 5.32, 304.0)
+    got = KF.kifmm(pts, h, I, 10 ** 6, 6, 5.32, 304.0)
+    np.testing.assert_allclose(got, ref, rtol=1e-13)
+
+
+@pytest.mark.parametrize("m0,tol", [(4, 5e-3), (6, 6e-3), (8, 3e-3)])
+def test_kifmm_accuracy_32cube(m0, tol):
+    # 32^3 cells on a 1 cm cube, centred Gaussian, p = 760 Torr, p_O2 = 150 Torr, leaf 64
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(150.0)
+    ref = D.fft_uniform(I.reshape(32, 32, 32), h[0], a, b).ravel()
+    got = KF.kifmm(pts, h, I, 64, m0, a, b)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err < tol
