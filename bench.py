@@ -1,0 +1,306 @@
+#!/usr/bin/env python3
+"""Throughput of the photoionization KIFMM on one GB300 (S_ph points per second).
+
+Workload (default): 128^3 cell centres of a 1 cm cube (2,097,152 points), Gaussian
+source 1e22 exp(-|r - c|^2 / (0.1 cm)^2), p = 760 Torr, p_O2 = 0.2 p = 152 Torr,
+surface order m0 = 6, leaf size 64. One step = one evaluation of S for the whole
+field (every phase of the evaluation: weights, S2M, M2M, M2L, S2L/L2L, local and
+W-list evaluation, near-field P2P, self term, reordering) in the mixed-precision
+form; the plan (tree, lists, operators) is built once before timing, as in a time
+loop on a fixed mesh. The mixed result is checked against the FP64 form (gate:
+rel-L2 <= 1e-6) before timing.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank runs an independent replica of the workload on its GPU
+(the single-field path has no data-parallel split without a tree exchange).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 512 << 20
+SM_COUNT = 152
+MUFU_PER_SM_CLK = 16.0
+MUFU_PER_PAIR = 3.0     # rsqrt + two exp2 per pair in the FP32 kernel
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="grid cells per axis")
+    ap.add_argument("--m0", type=int, default=6)
+    ap.add_argument("--leaf", type=int, default=64)
+    ap.add_argument("--p", type=float, default=760.0, help="gas pressure (Torr); p_O2 = 0.2 p")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--cpu-n", type=int, default=48, help="grid of the bounded CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = self.rows
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_sample(n_cpu, m0, leaf, a, b, C):
+    """The oracle (plain CPU KIFMM, FP64) on an n_cpu^3 sample of the same workload
+    (same cube, source, pressure, m0 and leaf size); returns points/s of its
+    evaluation and the thread count it used."""
+    import numpy as np
+    from oracle import direct as D
+    from oracle import kifmm as KF
+    from paper_2006_03515_gb300 import workloads as W
+    pts, h, I = W.config_uniform(n_cpu)
+    p = KF.plan(pts, h, leaf, m0, a, b)
+    t0 = time.perf_counter()
+    KF.evaluate(p, I, C)
+    dt = time.perf_counter() - t0
+    return len(pts) / dt, D.c_threads(), dt
+
+
+def run_reference(args):
+    """The oracle as it stands, timed on this machine's host cores."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import build as ob
+    from oracle import direct as D
+    from oracle import kernel as K
+    from oracle import kifmm as KF
+    from paper_2006_03515_gb300 import workloads as W
+    ob.build()
+    a, b = K.absorption_coefficients(0.2 * args.p)
+    C = K.source_scale(args.p)
+    n = 32
+    pts, h, I = W.config_uniform(n)
+    p = KF.plan(pts, h, args.leaf, args.m0, a, b)
+    for _ in range(args.warmup):
+        KF.evaluate(p, I, C)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        KF.evaluate(p, I, C)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = len(pts) / (ms * 1e-3)
+    sample = ("oracle KIFMM evaluation (FP64, numpy + C/OpenMP) on a %d^3 sample of the workload "
+              "(same 1 cm cube, source, pressure, m0=%d, leaf %d); plan excluded" % (n, args.m0, args.leaf))
+    line = {"impl": "reference", "metric": "S_ph points/s (KIFMM evaluation)", "value": value,
+            "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "uniform %d^3 cell centres (sample of the %d^3 workload)" % (n, args.n),
+                       "n_points": len(pts), "m0": args.m0, "leaf": args.leaf, "p_torr": args.p},
+            "cpu_baseline": {"value": value, "unit": "points/s", "cores": D.c_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2006_03515_gb300 import build as pb
+    from paper_2006_03515_gb300 import kifmm, workloads
+    pb.build()
+    os.environ["KIFMM_TIMING"] = "1"
+
+    p_o2 = 0.2 * args.p
+    a, b = kifmm.absorption(p_o2)
+    C = kifmm.scale_c(args.p)
+    pts, h, I = workloads.config_uniform(args.n)
+    npts = len(pts)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        dpts = torch.as_tensor(pts, device=dev)
+        dI = torch.as_tensor(I, device=dev)
+        S = torch.empty_like(dI)
+        t0 = time.perf_counter()
+        plan = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision=args.precision, stream=stream)
+        torch.cuda.synchronize(dev)
+        plan_s = time.perf_counter() - t0
+        info = plan.info()
+        gate = None
+        fp64 = None
+        if not args.no_fp64 and args.precision == "mixed":
+            p64 = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision="fp64", stream=stream)
+            S64 = p64.eval(dI, C=C)
+            plan.eval(dI, S, C=C)
+            torch.cuda.synchronize(dev)
+            gate = float(torch.linalg.norm(S - S64) / torch.linalg.norm(S64))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            t64 = []
+            for _ in range(2):
+                e0.record(stream)
+                p64.eval(dI, S64, C=C)
+                e1.record(stream)
+                e1.synchronize()
+                t64.append(e0.elapsed_time(e1))
+            fp64 = {"points_per_s": npts / (1e-3 * min(t64)), "ms": min(t64)}
+            p64.close()
+            del S64
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        for _ in range(args.warmup):
+            plan.eval(dI, S, C=C)
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        time.sleep(0.25)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        phase_sum = None
+        torch.cuda.synchronize(dev)
+        for k in range(args.steps):
+            flush.fill_(float(k))           # L2 flush between timed steps (outside the events)
+            starts[k].record(stream)
+            plan.eval(dI, S, C=C)
+            ends[k].record(stream)
+            ends[k].synchronize()
+            ph = plan.phase_times()
+            phase_sum = ph if phase_sum is None else [x + y for x, y in zip(phase_sum, ph)]
+        torch.cuda.synchronize(dev)
+        clk = clocks.stop()
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        ms = sum(step_ms) / len(step_ms)
+        if ws > 1:
+            t = torch.tensor([ms], dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t[0])
+        value = ws * npts / (ms * 1e-3)
+
+        # end to end through the public API with host buffers (pinned), copies inside the timed region
+        hI = torch.empty(npts, dtype=torch.float64, pin_memory=True)
+        hS = torch.empty(npts, dtype=torch.float64, pin_memory=True)
+        hI.copy_(torch.as_tensor(I))
+        hIn, hSn = hI.numpy(), hS.numpy()
+        e2e_ms = []
+        for k in range(max(3, args.steps // 2) + 2):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            plan.eval_host(hIn, hSn, C=C)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                e2e_ms.append(e0.elapsed_time(e1))
+        e2e_val = ws * npts / (1e-3 * sum(e2e_ms) / len(e2e_ms))
+        e2e_ok = bool(np.allclose(hSn, S.cpu().numpy(), rtol=0, atol=0))
+
+    phases = ["scatter", "P2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
+    ph_ms = {k: v / args.steps for k, v in zip(phases, phase_sum)}
+    dom = max(ph_ms, key=ph_ms.get)
+    sm_clk = 2070.0
+    if dom == "P2P":
+        achieved = info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3) / 1e9
+        peak = SM_COUNT * MUFU_PER_SM_CLK / MUFU_PER_PAIR * sm_clk * 1e6 / 1e9
+        roof = {"kernel": "k_p2p (near-field pair sum)", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MUFU: 152 SMs x 16 /clk x 2070 MHz / 3 MUFU per pair (derived)"}
+    else:
+        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+    gpu_launches = info["eval_launches"] * args.steps
+    line = {"metric": "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)", "value": value, "unit": "points/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": "uniform %d^3 cell centres, 1 cm cube, Gaussian 1e22 exp(-r^2/0.1^2), "
+                                   "p=%g Torr, pO2=%g, m0=%d, leaf %d, %s" % (args.n, args.p, p_o2, args.m0,
+                                                                             args.leaf, args.precision),
+                       "n_points": npts, "l2": "512 MB buffer written between timed steps",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "gate_rel_l2_mixed_vs_fp64": gate, "fp64": fp64, "plan_s": plan_s,
+            "phase_ms": ph_ms, "roofline": roof, "clocks": clk, "gpu_launches": gpu_launches,
+            "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": npts * 8,
+                    "d2h_bytes_per_step": npts * 8, "matches_device_result": e2e_ok}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        from oracle import build as ob
+        ob.build()
+        v, cores, dt = cpu_sample(args.cpu_n, args.m0, args.leaf, a, b, C)
+        line["cpu_baseline"] = {"value": v, "unit": "points/s", "cores": cores, "kind": "oracle",
+                                "sample": "oracle KIFMM evaluation (FP64, numpy + C/OpenMP) of a %d^3 sample of "
+                                          "the workload (%.1f s); plan excluded" % (args.cpu_n, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,183 @@
+/*
+ * kifmm.h - C-ABI of the GB300 kernel-independent FMM for the Zheleznyak
+ * integral photoionization model (Lin, Zhuang, Cai, Zeng, Bao, arXiv:2006.03515).
+ *
+ * What it computes (Sec. 3, Eq. (summation) with the discrete kernel G):
+ *
+ *   S_i = C * ( sum_{j != i} K(|x_i - x_j|) I_j h_j^3  +  sigma(h_i) I_i ),
+ *   K(R) = (exp(-aR) - exp(-bR)) / (4 pi R^3 ln(b/a))        (Eqs. (integral), (gfun))
+ *
+ * for cell centres x_i of cubic cells of edge h_i, a = chi_min p_O2,
+ * b = chi_max p_O2, and C = xi (omega/alpha) p_q / (p + p_q) (Eq. (Ifun)).
+ * The far part of the sum is approximated by the kernel-independent FMM of
+ * Sec. 3 (equivalent/check surfaces, S2M, M2M, M2L, L2L, outline steps 1-4)
+ * on an adaptive octree; the near part is summed directly (Eq. (nearfar)).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev are DEVICE pointers (cudaMalloc'd or torch CUDA
+ *    tensors) on the current device; *_host are host pointers. All arrays are
+ *    dense and C-contiguous. Points are N x 3 FP64 in cm, row-major (x, y, z).
+ *  - The caller keeps ownership of every array it passes. A plan copies what
+ *    it needs into device buffers it owns; they are freed by kifmm_destroy.
+ *  - Errors are reported by the return status only; no entry point aborts,
+ *    throws, or traps on the device. kifmm_last_error() gives a message for the
+ *    last failing call of the calling thread.
+ *  - A plan is not re-entrant: one kifmm_eval at a time per plan. All work of a
+ *    plan is issued on the stream given in its options (0 = legacy default).
+ *  - kifmm_eval does not allocate memory; every buffer it uses is created by
+ *    kifmm_plan.
+ */
+#ifndef KIFMM_H
+#define KIFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kifmm_plan_s* kifmm_plan_t;
+
+typedef enum {
+    KIFMM_OK = 0,
+    KIFMM_ERR_ARG = -1,             /* invalid argument (size, NULL, range)         */
+    KIFMM_ERR_OOM = -2,             /* device allocation failed                     */
+    KIFMM_ERR_CUDA = -3,            /* a CUDA call or kernel launch failed          */
+    KIFMM_ERR_TIMEOUT = -4,         /* a bounded device wait ran out                */
+    KIFMM_ERR_DUPLICATE_POINT = -5, /* two points with identical coordinates        */
+    KIFMM_ERR_NONFINITE = -6,       /* NaN/Inf in points or cell sizes              */
+    KIFMM_ERR_NUMERIC = -7          /* an operator could not be built (SVD failed)  */
+} kifmm_status;
+
+typedef enum { KIFMM_FP64 = 0, KIFMM_MIXED = 1 } kifmm_precision;
+typedef enum { KIFMM_SELF_CELL_EXACT = 0, KIFMM_SELF_PAPER_GL2 = 1 } kifmm_self_mode;
+typedef enum { KIFMM_F32 = 0, KIFMM_F64 = 1 } kifmm_dtype;
+
+typedef struct {
+    /* KIFMM_FP64: every step in FP64.
+     * KIFMM_MIXED: near-field P2P, check-surface and target evaluations in FP32
+     * (box-local coordinates, compensated sums), M2L in split 3xTF32 form with
+     * FP32 accumulation, the pseudo-inverse applications and the L2L chain in FP64. */
+    int precision;
+    /* Value of the i == j term of the discrete kernel G (Sec. 3):
+     * KIFMM_SELF_CELL_EXACT: the exact integral of K over the cell (default);
+     * KIFMM_SELF_PAPER_GL2: the paper's 2-point Gauss-Legendre value h^3 K(h/2). */
+    int self_mode;
+    /* Relative cut-off of the truncated-SVD pseudo-inverse (Sec. 3, after the
+     * outline): singular values below pinv_eps * sigma_max are dropped.
+     * Default 1e-5. Must lie in (0, 1). */
+    double pinv_eps;
+    /* Root cube. has_root = 0: origin = min_i(x_i - h_i/2) per axis and
+     * side = the largest extent of max_i(x_i + h_i/2) - origin. has_root = 1:
+     * root = {origin_x, origin_y, origin_z, side}; every cell must lie inside. */
+    int has_root;
+    double root[4];
+    /* cudaStream_t on which the plan runs all of its work (NULL = default stream). */
+    void* stream;
+} kifmm_opts;
+
+/* Fills *opts with the defaults above (FP64, cell-exact self term, eps 1e-5,
+ * automatic root, default stream). */
+void kifmm_default_opts(kifmm_opts* opts);
+
+/*
+ * Builds a plan for N cell-centred points (outline step 1 and the operators of
+ * Eqs. (s2m)-(l2l)): root cube, 63-bit Morton keys (21 bits per axis, one FP64
+ * subtraction and one FP64 multiplication per coordinate), stable radix sort,
+ * levelled octree split while a box holds more than leaf_size points (at most
+ * 20 levels; empty children are not created), U/V/W/X interaction lists,
+ * per-level surfaces with surface_order (m0) points per side, truncated-SVD
+ * pseudo-inverses and the M2M/M2L/L2L matrices, and the self-cell values.
+ *
+ *   points_dev   device, N x 3 FP64, cell centres (cm). Must be finite and distinct.
+ *   n            number of points, 1 <= n < 2^31.
+ *   cell_h_dev   device, N FP64 cell edges (cm), or NULL to use uniform_h for all.
+ *   uniform_h    cell edge when cell_h_dev is NULL (> 0).
+ *   leaf_size    m >= 1: a box with more than m points is split.
+ *   surface_order m0 in [3, 12]: lattice points per side of each surface.
+ *   a, b         chi_min p_O2 and chi_max p_O2 in 1/cm, 0 < a < b.
+ *   opts         options, or NULL for kifmm_default_opts().
+ * On success *out receives the plan. Statuses: KIFMM_ERR_ARG,
+ * KIFMM_ERR_NONFINITE, KIFMM_ERR_DUPLICATE_POINT, KIFMM_ERR_OOM,
+ * KIFMM_ERR_CUDA, KIFMM_ERR_NUMERIC. The call synchronises its stream.
+ */
+int kifmm_plan(kifmm_plan_t* out, const double* points_dev, int64_t n,
+               const double* cell_h_dev, double uniform_h, int leaf_size,
+               int surface_order, double a, double b, const kifmm_opts* opts);
+
+/*
+ * One evaluation of S (outline steps 2-4): S_dev[i] = C * (far field through
+ * the FMM + near field by direct summation + sigma(h_i) I_i), in input order.
+ *   I_dev  device, N values of I (cm^-3 s^-1, caller order), dtype F32 or F64.
+ *   S_dev  device, N outputs (same dtype), fully overwritten (never accumulated).
+ *   C      scale factor (1.0 gives the raw sum).
+ * Asynchronous on the plan's stream; allocates nothing; no host synchronisation.
+ * Statuses: KIFMM_ERR_ARG (NULL, bad dtype), KIFMM_ERR_CUDA (launch failure).
+ */
+int kifmm_eval(kifmm_plan_t plan, const void* I_dev, void* S_dev, int dtype, double C);
+
+/*
+ * The same evaluation from host buffers: copies I_host to the device, runs
+ * kifmm_eval, copies S back to S_host and synchronises the plan's stream.
+ * Host buffers may be pageable or pinned (pinned is faster).
+ */
+int kifmm_eval_host(kifmm_plan_t plan, const void* I_host, void* S_host, int dtype, double C);
+
+/*
+ * Evaluates `count` plans (each with its own I and S, possibly of different
+ * sizes and pressures) back to back on plan[0]'s stream; with capture != 0 the
+ * whole batch is recorded once into a CUDA graph held by plan[0] and replayed
+ * on later calls with the same arguments.
+ */
+int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I_dev, void* const* S_dev,
+                     int count, int dtype, const double* C, int capture);
+
+/* Frees every device buffer of the plan (synchronising its stream). NULL is a no-op. */
+void kifmm_destroy(kifmm_plan_t plan);
+
+/* Message of the last failing call on this thread ("" if none). Owned by the library. */
+const char* kifmm_last_error(void);
+
+/* ---- introspection (tests of the tree and lists; host copies) ---- */
+
+typedef struct {
+    int64_t n_points;
+    int64_t n_boxes;
+    int32_t n_levels;
+    int32_t surface_points;     /* S = m0^3 - (m0-2)^3 */
+    int64_t n_leaves;
+    int64_t list_len[4];        /* total entries of U, V, W, X */
+    double origin[3];
+    double side;
+    double pinv_rank_min;       /* smallest kept rank over the levels' pseudo-inverses */
+    int64_t eval_launches;      /* kernels launched by one kifmm_eval of this plan */
+    int64_t p2p_pairs;          /* near-field pair evaluations of one kifmm_eval */
+} kifmm_info;
+
+int kifmm_get_info(kifmm_plan_t plan, kifmm_info* info);
+
+/* Copies the tree to caller-allocated host arrays (any pointer may be NULL):
+ * perm[n_points] (input index of each sorted point), keys[n_points] (Morton keys
+ * in sorted order), level/parent/pstart/pend/leaf[n_boxes], anchor[3*n_boxes]
+ * (integer coordinates at the box's level), child[8*n_boxes] (-1 for empty). */
+int kifmm_get_tree(kifmm_plan_t plan, int64_t* perm, uint64_t* keys, int32_t* level,
+                   int32_t* parent, int64_t* pstart, int64_t* pend, int32_t* leaf,
+                   int32_t* anchor, int32_t* child);
+
+/* Copies interaction list `which` (0 = U, 1 = V, 2 = W, 3 = X) in CSR form:
+ * offsets[n_boxes + 1], items[list_len[which]] (box ids, ascending per box). */
+int kifmm_get_list(kifmm_plan_t plan, int which, int64_t* offsets, int32_t* items);
+
+/* Copies per-point self-cell values sigma(h_i) in sorted order (n_points FP64). */
+int kifmm_get_sigma(kifmm_plan_t plan, double* sigma);
+
+/* Per-phase device times (ms) of the last kifmm_eval when KIFMM_TIMING=1 in
+ * the environment at plan time: [scatter, P2M, M2M, M2L, S2L+L2L+DC2DE,
+ * L2P+M2P, P2P]. Returns the number of phases written (<= cap). */
+int kifmm_get_phase_times(kifmm_plan_t plan, float* ms, int cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KIFMM_H */

@@ -1,0 +1,369 @@
+// The C-ABI (include/kifmm.h): argument checks, plan lifetime, evaluation entry points.
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace kifmm {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+__global__ void gather_sorted_points(const double* pts, const int32_t* perm, int64_t n, double* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t i = perm[k];
+    out[3 * k] = pts[3 * i];
+    out[3 * k + 1] = pts[3 * i + 1];
+    out[3 * k + 2] = pts[3 * i + 2];
+}
+
+static void free_plan(Plan* p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    else cudaDeviceSynchronize();
+    Tree& t = p->tree;
+    for (DevBuf* b : {&t.keys, &t.perm, &t.level, &t.anchor, &t.mcode, &t.parent, &t.child, &t.pstart,
+                      &t.pend, &t.leaf, &t.centre})
+        dev_free(*b);
+    for (auto& L : p->lists) {
+        dev_free(L.off);
+        dev_free(L.items);
+    }
+    dev_free(p->vtab);
+    for (auto& o : p->ops)
+        for (DevBuf* b : {&o.uc2ue, &o.dc2de, &o.m2m, &o.l2l, &o.m2l, &o.m2l_hi, &o.m2l_lo}) dev_free(*b);
+    for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
+                      &p->q, &p->Isort, &p->chk, &p->phi_u, &p->phi_d, &p->phiu_hi, &p->phiu_lo, &p->chk32,
+                      &p->phid32, &p->phiu32, &p->far, &p->wleaves, &p->host_I, &p->host_S})
+        dev_free(*b);
+    for (auto& L : p->lv) {
+        for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes})
+            dev_free(*b);
+        for (int o = 0; o < 8; ++o) {
+            dev_free(L.m2m_src[o]);
+            dev_free(L.m2m_dst[o]);
+        }
+    }
+    for (auto& e : p->ev)
+        if (e) cudaEventDestroy(e);
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    delete p;
+}
+
+}  // namespace kifmm
+
+using namespace kifmm;
+
+struct kifmm_plan_s {
+    Plan* p;
+};
+
+extern "C" {
+
+void kifmm_default_opts(kifmm_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = KIFMM_FP64;
+    o->self_mode = KIFMM_SELF_CELL_EXACT;
+    o->pinv_eps = 1e-5;
+    o->has_root = 0;
+    o->stream = nullptr;
+}
+
+const char* kifmm_last_error(void) { return g_last_error.c_str(); }
+
+int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double* cell_h, double uniform_h,
+               int leaf_size, int surface_order, double a, double b, const kifmm_opts* opts_in) {
+    set_error("");
+    if (!out) {
+        set_error("kifmm_plan: out is NULL");
+        return KIFMM_ERR_ARG;
+    }
+    *out = nullptr;
+    kifmm_opts o;
+    if (opts_in) o = *opts_in;
+    else kifmm_default_opts(&o);
+    if (!points || n < 1 || n >= (int64_t)1 << 31) {
+        set_error("kifmm_plan: need points != NULL and 1 <= n < 2^31");
+        return KIFMM_ERR_ARG;
+    }
+    if (!cell_h && !(uniform_h > 0.0 && std::isfinite(uniform_h))) {
+        set_error("kifmm_plan: uniform_h must be finite and > 0 when cell_h is NULL");
+        return KIFMM_ERR_ARG;
+    }
+    if (leaf_size < 1 || surface_order < 3 || surface_order > 12) {
+        set_error("kifmm_plan: need leaf_size >= 1 and 3 <= surface_order <= 12");
+        return KIFMM_ERR_ARG;
+    }
+    if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) {
+        set_error("kifmm_plan: need 0 < a < b (finite)");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.precision != KIFMM_FP64 && o.precision != KIFMM_MIXED) {
+        set_error("kifmm_plan: unknown precision");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.self_mode != KIFMM_SELF_CELL_EXACT && o.self_mode != KIFMM_SELF_PAPER_GL2) {
+        set_error("kifmm_plan: unknown self_mode");
+        return KIFMM_ERR_ARG;
+    }
+    if (!(o.pinv_eps > 0.0 && o.pinv_eps < 1.0)) {
+        set_error("kifmm_plan: pinv_eps must lie in (0, 1)");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.has_root && !(o.root[3] > 0.0 && std::isfinite(o.root[3]))) {
+        set_error("kifmm_plan: root side must be finite and > 0");
+        return KIFMM_ERR_ARG;
+    }
+    Plan* p = new (std::nothrow) Plan();
+    if (!p) {
+        set_error("kifmm_plan: host allocation failed");
+        return KIFMM_ERR_OOM;
+    }
+    p->precision = o.precision;
+    p->self_mode = o.self_mode;
+    p->pinv_eps = o.pinv_eps;
+    p->stream = (cudaStream_t)o.stream;
+    p->a = a;
+    p->b = b;
+    p->m0 = surface_order;
+    p->S = surface_order * surface_order * surface_order -
+           (surface_order - 2) * (surface_order - 2) * (surface_order - 2);
+    p->Sp = (p->S + 31) / 32 * 32;
+    p->leaf_size = leaf_size;
+    p->tree.n = n;
+    auto fail = [&](int rc) {
+        std::string msg = g_last_error;
+        free_plan(p);
+        cudaGetLastError();
+        g_last_error = msg;
+        return rc;
+    };
+    int rc = build_tree(*p, points, cell_h, uniform_h, o);
+    if (rc) return fail(rc);
+    rc = dev_alloc(p->pts, n * 3 * sizeof(double));
+    if (rc) return fail(rc);
+    gather_sorted_points<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(points, ptr<int32_t>(p->tree.perm), n,
+                                                                           ptr<double>(p->pts));
+    if (cudaGetLastError() != cudaSuccess) {
+        set_error("kifmm_plan: launch failed");
+        return fail(KIFMM_ERR_CUDA);
+    }
+    rc = build_lists(*p);
+    if (rc) return fail(rc);
+    rc = build_operators(*p);
+    if (rc) return fail(rc);
+    rc = build_self_terms(*p, cell_h, uniform_h);
+    if (rc) return fail(rc);
+    rc = build_eval_data(*p);
+    if (rc) return fail(rc);
+    rc = dev_alloc(p->host_I, n * 8);
+    if (rc) return fail(rc);
+    rc = dev_alloc(p->host_S, n * 8);
+    if (rc) return fail(rc);
+    const char* tm = std::getenv("KIFMM_TIMING");
+    if (tm && tm[0] == '1') {
+        p->timing = true;
+        for (auto& e : p->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    }
+    if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+        set_error(std::string("kifmm_plan: ") + cudaGetErrorString(cudaGetLastError()));
+        return fail(KIFMM_ERR_CUDA);
+    }
+    kifmm_plan_s* h = new (std::nothrow) kifmm_plan_s{p};
+    if (!h) return fail(KIFMM_ERR_OOM);
+    *out = h;
+    return KIFMM_OK;
+}
+
+int kifmm_eval(kifmm_plan_t h, const void* I, void* S, int dtype, double C) {
+    if (!h || !h->p || !I || !S || (dtype != KIFMM_F32 && dtype != KIFMM_F64) || !std::isfinite(C)) {
+        set_error("kifmm_eval: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    Plan& p = *h->p;
+    int rc = run_eval(p, I, S, dtype, C);
+    if (rc) return rc;
+    if (p.timing) {
+        cudaEventSynchronize(p.ev[7]);
+        for (int k = 0; k < 7; ++k) cudaEventElapsedTime(&p.phase_ms[k], p.ev[k], p.ev[k + 1]);
+        p.n_phases = 7;
+    }
+    return KIFMM_OK;
+}
+
+int kifmm_eval_host(kifmm_plan_t h, const void* I_host, void* S_host, int dtype, double C) {
+    if (!h || !h->p || !I_host || !S_host || (dtype != KIFMM_F32 && dtype != KIFMM_F64)) {
+        set_error("kifmm_eval_host: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    Plan& p = *h->p;
+    size_t bytes = (size_t)p.tree.n * (dtype == KIFMM_F64 ? 8 : 4);
+    KF_CUDA(cudaMemcpyAsync(p.host_I.p, I_host, bytes, cudaMemcpyHostToDevice, p.stream));
+    KF_TRY(kifmm_eval(h, p.host_I.p, p.host_S.p, dtype, C));
+    KF_CUDA(cudaMemcpyAsync(S_host, p.host_S.p, bytes, cudaMemcpyDeviceToHost, p.stream));
+    KF_CUDA(cudaStreamSynchronize(p.stream));
+    return KIFMM_OK;
+}
+
+int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I, void* const* S, int count, int dtype,
+                     const double* C, int capture) {
+    if (!plans || !I || !S || count < 1) {
+        set_error("kifmm_eval_batch: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    for (int k = 0; k < count; ++k)
+        if (!plans[k] || !plans[k]->p) {
+            set_error("kifmm_eval_batch: NULL plan");
+            return KIFMM_ERR_ARG;
+        }
+    Plan& p0 = *plans[0]->p;
+    cudaStream_t st = p0.stream;
+    std::vector<const void*> key;
+    key.reserve(3 * count + 2);
+    key.push_back((const void*)(intptr_t)count);
+    key.push_back((const void*)(intptr_t)dtype);
+    for (int k = 0; k < count; ++k) {
+        key.push_back(plans[k]);
+        key.push_back(I[k]);
+        key.push_back(S[k]);
+    }
+    auto launch_all = [&]() -> int {
+        for (int k = 0; k < count; ++k) {
+            Plan& pk = *plans[k]->p;
+            cudaStream_t saved = pk.stream;
+            bool saved_t = pk.timing;
+            pk.stream = st;
+            pk.timing = false;
+            int rc = run_eval(pk, I[k], S[k], dtype, C ? C[k] : 1.0);
+            pk.stream = saved;
+            pk.timing = saved_t;
+            if (rc) return rc;
+        }
+        return KIFMM_OK;
+    };
+    if (!capture) return launch_all();
+    if (p0.graph_exec && p0.graph_key == key) {
+        KF_CUDA(cudaGraphLaunch(p0.graph_exec, st));
+        return KIFMM_OK;
+    }
+    if (!st) {
+        set_error("kifmm_eval_batch: graph capture needs a non-default stream in plan[0]");
+        return KIFMM_ERR_ARG;
+    }
+    if (p0.graph_exec) {
+        cudaGraphExecDestroy(p0.graph_exec);
+        p0.graph_exec = nullptr;
+    }
+    cudaGraph_t g;
+    KF_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = launch_all();
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc) {
+        if (e == cudaSuccess) cudaGraphDestroy(g);
+        return rc;
+    }
+    KF_CUDA(e);
+    cudaError_t ei = cudaGraphInstantiate(&p0.graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    KF_CUDA(ei);
+    p0.graph_key = key;
+    KF_CUDA(cudaGraphLaunch(p0.graph_exec, st));
+    return KIFMM_OK;
+}
+
+void kifmm_destroy(kifmm_plan_t h) {
+    if (!h) return;
+    free_plan(h->p);
+    delete h;
+}
+
+int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
+    if (!h || !h->p || !info) {
+        set_error("kifmm_get_info: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    Plan& p = *h->p;
+    info->n_points = p.tree.n;
+    info->n_boxes = p.tree.nboxes;
+    info->n_levels = p.tree.nlevels;
+    info->surface_points = p.S;
+    info->n_leaves = p.nleaves;
+    for (int k = 0; k < 4; ++k) info->list_len[k] = p.lists[k].len;
+    for (int k = 0; k < 3; ++k) info->origin[k] = p.tree.origin[k];
+    info->side = p.tree.side;
+    int rmin = p.S;
+    for (int l = 2; l < p.tree.nlevels; ++l) rmin = std::min(rmin, p.ops[l].rank);
+    info->pinv_rank_min = rmin;
+    info->eval_launches = p.eval_launches;
+    info->p2p_pairs = p.p2p_pairs;
+    return KIFMM_OK;
+}
+
+static int copy_i32_to_i64(const DevBuf& src, int64_t n, int64_t* dst, cudaStream_t st) {
+    if (!dst) return KIFMM_OK;
+    std::vector<int32_t> tmp(n);
+    KF_CUDA(cudaMemcpyAsync(tmp.data(), src.p, n * 4, cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < n; ++i) dst[i] = tmp[i];
+    return KIFMM_OK;
+}
+
+static int copy_raw(const DevBuf& src, size_t bytes, void* dst, cudaStream_t st) {
+    if (!dst) return KIFMM_OK;
+    KF_CUDA(cudaMemcpyAsync(dst, src.p, bytes, cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    return KIFMM_OK;
+}
+
+int kifmm_get_tree(kifmm_plan_t h, int64_t* perm, uint64_t* keys, int32_t* level, int32_t* parent,
+                   int64_t* pstart, int64_t* pend, int32_t* leaf, int32_t* anchor, int32_t* child) {
+    if (!h || !h->p) {
+        set_error("kifmm_get_tree: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    Plan& p = *h->p;
+    Tree& t = p.tree;
+    cudaStream_t st = p.stream;
+    KF_TRY(copy_i32_to_i64(t.perm, t.n, perm, st));
+    KF_TRY(copy_raw(t.keys, t.n * 8, keys, st));
+    KF_TRY(copy_raw(t.level, t.nboxes * 4, level, st));
+    KF_TRY(copy_raw(t.parent, t.nboxes * 4, parent, st));
+    KF_TRY(copy_i32_to_i64(t.pstart, t.nboxes, pstart, st));
+    KF_TRY(copy_i32_to_i64(t.pend, t.nboxes, pend, st));
+    KF_TRY(copy_raw(t.leaf, t.nboxes * 4, leaf, st));
+    KF_TRY(copy_raw(t.anchor, t.nboxes * 12, anchor, st));
+    KF_TRY(copy_raw(t.child, t.nboxes * 32, child, st));
+    return KIFMM_OK;
+}
+
+int kifmm_get_list(kifmm_plan_t h, int which, int64_t* offsets, int32_t* items) {
+    if (!h || !h->p || which < 0 || which > 3) {
+        set_error("kifmm_get_list: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    Plan& p = *h->p;
+    KF_TRY(copy_i32_to_i64(p.lists[which].off, p.tree.nboxes + 1, offsets, p.stream));
+    KF_TRY(copy_raw(p.lists[which].items, p.lists[which].len * 4, items, p.stream));
+    return KIFMM_OK;
+}
+
+int kifmm_get_sigma(kifmm_plan_t h, double* sigma) {
+    if (!h || !h->p || !sigma) {
+        set_error("kifmm_get_sigma: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    return copy_raw(h->p->sigma, h->p->tree.n * 8, sigma, h->p->stream);
+}
+
+int kifmm_get_phase_times(kifmm_plan_t h, float* ms, int cap) {
+    if (!h || !h->p || !ms) return 0;
+    int n = std::min(cap, h->p->n_phases);
+    for (int k = 0; k < n; ++k) ms[k] = h->p->phase_ms[k];
+    return n;
+}
+
+}  // extern "C"

@@ -1,0 +1,902 @@
+// Evaluation (outline steps 2-4 of Sec. 3): S2M (P2M), M2M, M2L, S2L (X list), L2L,
+// local-expansion and W-list evaluation at the targets, near-field P2P, and the self term.
+#include <algorithm>
+#include <cstdlib>
+
+#include "internal.cuh"
+#include "kernel.cuh"
+
+namespace kifmm {
+
+static inline unsigned nbk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ------------------------------------------------------------------------------------
+// plan-time data for the evaluation
+// ------------------------------------------------------------------------------------
+__global__ void gather_points(const double* pts, const int32_t* perm, int64_t n, double* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int64_t i = perm[k];
+    out[3 * k] = pts[3 * i];
+    out[3 * k + 1] = pts[3 * i + 1];
+    out[3 * k + 2] = pts[3 * i + 2];
+}
+
+__global__ void mark_leaf_points(const int32_t* leaf, const int32_t* pstart, const int32_t* pend,
+                                 int64_t nb, int32_t* leaf_of) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb || !leaf[b]) return;
+    for (int i = pstart[b]; i < pend[b]; ++i) leaf_of[i] = (int32_t)b;
+}
+
+// coordinates relative to the centre of the point's own leaf, rounded once to FP32
+__global__ void local_coords(const double* spts, const int32_t* leaf_of, const double* centre,
+                             int64_t n, float4* loc) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double* c = centre + 3 * (int64_t)leaf_of[k];
+    loc[k] = make_float4((float)(spts[3 * k] - c[0]), (float)(spts[3 * k + 1] - c[1]),
+                         (float)(spts[3 * k + 2] - c[2]), 0.f);
+}
+
+__global__ void select_boxes(const int32_t* level, const int32_t* leaf, int64_t lo, int64_t hi,
+                             int want_leaf, int min_level, int32_t* flag) {
+    int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= hi) return;
+    int f = (level[b] >= min_level) && ((want_leaf < 0) || (leaf[b] == want_leaf));
+    flag[b - lo] = f;
+}
+__global__ void compact_boxes(const int32_t* flag, const int32_t* pos, int64_t lo, int64_t cnt,
+                              int32_t* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt) return;
+    if (flag[k]) out[pos[k]] = (int32_t)(lo + k);
+}
+
+// (child, parent) pairs for octant o of the non-leaf boxes in [lo, hi)
+__global__ void m2m_pairs(const int32_t* child, const int32_t* leaf, int64_t lo, int64_t hi, int o,
+                          int32_t* flag) {
+    int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= hi) return;
+    flag[b - lo] = (!leaf[b] && child[8 * b + o] >= 0) ? 1 : 0;
+}
+__global__ void m2m_fill(const int32_t* child, const int32_t* flag, const int32_t* pos, int64_t lo,
+                         int64_t cnt, int o, int32_t* src, int32_t* dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cnt || !flag[k]) return;
+    int64_t b = lo + k;
+    src[pos[k]] = child[8 * b + o];
+    dst[pos[k]] = (int32_t)b;
+}
+
+constexpr int kSlotStride = 344;   // per M2L tile: [count, slot_0, slot_1, ...]
+
+// active offset slots of a tile of consecutive boxes (union of their V lists)
+__global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int tb, int32_t* slots) {
+    int tile = blockIdx.x;
+    __shared__ int mask[kOffsetSlots];
+    for (int s = threadIdx.x; s < kOffsetSlots; s += blockDim.x) mask[s] = 0;
+    __syncthreads();
+    int64_t b0 = lo + (int64_t)tile * tb;
+    for (int e = threadIdx.x; e < tb * kOffsetSlots; e += blockDim.x) {
+        int64_t b = b0 + e / kOffsetSlots;
+        int s = e % kOffsetSlots;
+        if (b < hi && vtab[b * kOffsetSlots + s] >= 0) mask[s] = 1;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int s = 0; s < kOffsetSlots; ++s)
+            if (mask[s]) slots[(int64_t)tile * kSlotStride + 1 + n++] = s;
+        slots[(int64_t)tile * kSlotStride] = n;
+    }
+}
+
+__global__ void nonempty_boxes(const int32_t* off, int64_t lo, int64_t hi, int min_level,
+                               const int32_t* level, int32_t* flag) {
+    int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= hi) return;
+    flag[b - lo] = (off[b + 1] > off[b] && level[b] >= min_level) ? 1 : 0;
+}
+
+constexpr int kM2LTile64 = 32;   // boxes per tile, FP64 M2L
+constexpr int kM2LTile32 = 64;   // boxes per tile, FP32 M2L
+
+// near-field pair evaluations of one evaluation: sum over leaves B of n_B * (sum_{A in U(B)} n_A) - n
+__global__ void count_p2p_pairs(const int32_t* leaves, int64_t nl, const int32_t* uoff, const int32_t* uitems,
+                                const int32_t* pstart, const int32_t* pend, unsigned long long* out) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nl) return;
+    int B = leaves[k];
+    unsigned long long s = 0;
+    for (int u = uoff[B]; u < uoff[B + 1]; ++u) s += (unsigned long long)(pend[uitems[u]] - pstart[uitems[u]]);
+    unsigned long long nb = (unsigned long long)(pend[B] - pstart[B]);
+    atomicAdd(out, nb * s - nb);
+}
+
+int build_eval_data(Plan& p) {
+    Tree& t = p.tree;
+    cudaStream_t st = p.stream;
+    const int64_t n = t.n, nb = t.nboxes;
+    const int S = p.S;
+    KF_TRY(dev_alloc(p.leaf_of, n * 4));
+    mark_leaf_points<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(t.leaf), ptr<int32_t>(t.pstart),
+                                                    ptr<int32_t>(t.pend), nb, ptr<int32_t>(p.leaf_of));
+    KF_LAUNCH();
+    KF_TRY(dev_alloc(p.loc32, n * sizeof(float4)));
+    local_coords<<<nbk(n, 256), 256, 0, st>>>(ptr<double>(p.pts), ptr<int32_t>(p.leaf_of),
+                                              ptr<double>(t.centre), n, ptr<float4>(p.loc32));
+    KF_LAUNCH();
+
+    DevBuf flag, pos, scan_tmp;
+    KF_TRY(dev_alloc(flag, (nb + 1) * 4));
+    KF_TRY(dev_alloc(pos, (nb + 1) * 4));
+    // all leaves, and leaves of level >= 2 (P2M)
+    {
+        select_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), 0, nb, 1, 0,
+                                                   ptr<int32_t>(flag));
+        KF_LAUNCH();
+        int32_t tot = 0;
+        KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), nb, &tot, st, scan_tmp));
+        KF_TRY(dev_alloc(p.leaves, (size_t)std::max(tot, 1) * 4));
+        compact_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), 0, nb,
+                                                     ptr<int32_t>(p.leaves));
+        KF_LAUNCH();
+        p.nleaves = tot;
+        select_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), 0, nb, 1, 2,
+                                                   ptr<int32_t>(flag));
+        KF_LAUNCH();
+        KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), nb, &tot, st, scan_tmp));
+        KF_TRY(dev_alloc(p.p2m_boxes, (size_t)std::max(tot, 1) * 4));
+        compact_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), 0, nb,
+                                                     ptr<int32_t>(p.p2m_boxes));
+        KF_LAUNCH();
+        p.n_p2m = tot;
+        // leaves with a non-empty W list
+        nonempty_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(p.lists[2].off), 0, nb, 0,
+                                                     ptr<int32_t>(t.level), ptr<int32_t>(flag));
+        KF_LAUNCH();
+        KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), nb, &tot, st, scan_tmp));
+        KF_TRY(dev_alloc(p.wleaves, (size_t)std::max(tot, 1) * 4));
+        compact_boxes<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), 0, nb,
+                                                     ptr<int32_t>(p.wleaves));
+        KF_LAUNCH();
+        p.n_wleaves = tot;
+    }
+    {
+        DevBuf cnt;
+        KF_TRY(dev_alloc(cnt, 8));
+        KF_CUDA(cudaMemsetAsync(cnt.p, 0, 8, st));
+        if (p.nleaves > 0) {
+            count_p2p_pairs<<<nbk(p.nleaves, 256), 256, 0, st>>>(ptr<int32_t>(p.leaves), p.nleaves,
+                                                                 ptr<int32_t>(p.lists[0].off), ptr<int32_t>(p.lists[0].items),
+                                                                 ptr<int32_t>(t.pstart), ptr<int32_t>(t.pend),
+                                                                 ptr<unsigned long long>(cnt));
+            KF_LAUNCH();
+        }
+        unsigned long long h = 0;
+        KF_CUDA(cudaMemcpyAsync(&h, cnt.p, 8, cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        p.p2p_pairs = (int64_t)h;
+        dev_free(cnt);
+    }
+    p.lv.clear();
+    p.lv.resize(t.nlevels);
+    for (int l = 2; l < t.nlevels; ++l) {
+        auto& L = p.lv[l];
+        int64_t lo = t.level_start[l], hi = t.level_start[l + 1], cnt = hi - lo;
+        L.n_all = (int)cnt;
+        // M2M pairs per octant (parents at level l, children at l + 1)
+        for (int o = 0; o < 8; ++o) {
+            m2m_pairs<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.child), ptr<int32_t>(t.leaf), lo, hi, o,
+                                                     ptr<int32_t>(flag));
+            KF_LAUNCH();
+            int32_t tot = 0;
+            KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), cnt, &tot, st, scan_tmp));
+            KF_TRY(dev_alloc(L.m2m_src[o], (size_t)std::max(tot, 1) * 4));
+            KF_TRY(dev_alloc(L.m2m_dst[o], (size_t)std::max(tot, 1) * 4));
+            m2m_fill<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.child), ptr<int32_t>(flag), ptr<int32_t>(pos),
+                                                    lo, cnt, o, ptr<int32_t>(L.m2m_src[o]),
+                                                    ptr<int32_t>(L.m2m_dst[o]));
+            KF_LAUNCH();
+            L.n_m2m[o] = tot;
+        }
+        // M2L tiles and their active offset slots
+        int tb = p.precision == KIFMM_MIXED ? kM2LTile32 : kM2LTile64;
+        L.n_tiles = (int)((cnt + tb - 1) / tb);
+        KF_TRY(dev_alloc(L.m2l_slots, (size_t)std::max(L.n_tiles, 1) * kSlotStride * 4));
+        if (L.n_tiles > 0) {
+            m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, ptr<int32_t>(L.m2l_slots));
+            KF_LAUNCH();
+        }
+        // boxes with a non-empty X list
+        nonempty_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(p.lists[3].off), lo, hi, 2,
+                                                       ptr<int32_t>(t.level), ptr<int32_t>(flag));
+        KF_LAUNCH();
+        int32_t tot = 0;
+        KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), cnt, &tot, st, scan_tmp));
+        KF_TRY(dev_alloc(L.xboxes, (size_t)std::max(tot, 1) * 4));
+        compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), lo, cnt,
+                                                      ptr<int32_t>(L.xboxes));
+        KF_LAUNCH();
+        L.n_x = tot;
+    }
+    // workspace
+    KF_TRY(dev_alloc(p.q, n * 8));
+    KF_TRY(dev_alloc(p.Isort, n * 8));
+    KF_TRY(dev_alloc(p.far, n * 8));
+    KF_TRY(dev_alloc(p.chk, (size_t)nb * S * 8));
+    KF_TRY(dev_alloc(p.phi_u, (size_t)nb * S * 8));
+    KF_TRY(dev_alloc(p.phi_d, (size_t)nb * S * 8));
+    KF_CUDA(cudaMemsetAsync(p.phi_u.p, 0, (size_t)nb * S * 8, st));
+    KF_CUDA(cudaMemsetAsync(p.phi_d.p, 0, (size_t)nb * S * 8, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    dev_free(flag); dev_free(pos); dev_free(scan_tmp);
+    return KIFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// evaluation kernels
+// ------------------------------------------------------------------------------------
+struct EvalView {
+    const double* pts;      // sorted coordinates
+    const float4* loc;      // coordinates relative to own leaf centre (FP32)
+    const double* centre;   // box centres
+    const int32_t* level;
+    const int32_t* pstart;
+    const int32_t* pend;
+    const double* surf;     // unit lattice (3*S)
+    double side;
+    int S;
+    KParams kp;
+};
+
+__device__ __forceinline__ double half_width(const EvalView& E, int lev) {
+    return E.side / (double)(2ll << lev);
+}
+
+template <class T>
+__global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, int64_t n, double* Is,
+                            double* q) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double v = (double)I[perm[k]];
+    Is[k] = v;
+    q[k] = v * w[k];
+}
+
+// Kahan-compensated FP32 accumulator
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// S2M (Eq. (s2m), first step): upward check potential of a leaf from its own sources.
+// One block per leaf; check points x_j = c_B + 2.6 r s_j, sources relative to c_B.
+constexpr int P2M_T = 160;
+template <bool MIXED>
+__global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes, const double* q, double* chk) {
+    const int B = boxes[blockIdx.x];
+    const int S = E.S;
+    const double r = half_width(E, E.level[B]);
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    __shared__ float4 sp32[256];
+    __shared__ double sp64[256][4];
+    const double* c = E.centre + 3 * (int64_t)B;
+    for (int j0 = 0; j0 < S; j0 += P2M_T) {
+        const int j = j0 + threadIdx.x;
+        double xj[3];
+        for (int k = 0; k < 3; ++k) xj[k] = kROuter * r * E.surf[3 * min(j, S - 1) + k];
+        Kahan acc32;
+        double acc64 = 0;
+        for (int s0 = p0; s0 < p1; s0 += 256) {
+            const int ns = min(256, p1 - s0);
+            __syncthreads();
+            for (int e = threadIdx.x; e < ns; e += P2M_T) {
+                if (MIXED) {
+                    float4 v = E.loc[s0 + e];
+                    v.w = (float)q[s0 + e];
+                    sp32[e] = v;
+                } else {
+                    for (int k = 0; k < 3; ++k) sp64[e][k] = E.pts[3 * (int64_t)(s0 + e) + k] - c[k];
+                    sp64[e][3] = q[s0 + e];
+                }
+            }
+            __syncthreads();
+            if (MIXED) {
+                const float x0 = (float)xj[0], x1 = (float)xj[1], x2 = (float)xj[2];
+                for (int e = 0; e < ns; ++e) {
+                    const float4 v = sp32[e];
+                    const float dx = x0 - v.x, dy = x1 - v.y, dz = x2 - v.z;
+                    acc32.add(kern_f32(dx * dx + dy * dy + dz * dz, E.kp) * v.w);
+                }
+            } else {
+                for (int e = 0; e < ns; ++e) {
+                    const double dx = xj[0] - sp64[e][0], dy = xj[1] - sp64[e][1], dz = xj[2] - sp64[e][2];
+                    acc64 += kern_f64(sqrt(dx * dx + dy * dy + dz * dz), E.kp) * sp64[e][3];
+                }
+            }
+        }
+        if (j < S) chk[(int64_t)B * S + j] = MIXED ? acc32.value() : acc64;
+    }
+}
+
+// out[dst(c)] (+)= Op (S x S, row-major) * in[src(c)] for c < count, FP64.
+// src/dst NULL means the contiguous range base + c.
+constexpr int AP_TM = 64, AP_TN = 32, AP_TK = 16;
+__global__ void __launch_bounds__(256) k_apply64(const double* __restrict__ Op, int S, const int32_t* src,
+                                                 const int32_t* dst, int64_t base, int count,
+                                                 const double* __restrict__ in, double* out, int accumulate) {
+    __shared__ double As[AP_TK][AP_TM + 1];
+    __shared__ double Bs[AP_TK][AP_TN + 1];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int row0 = blockIdx.y * AP_TM, col0 = blockIdx.x * AP_TN;
+    double acc[2][4] = {};
+    for (int k0 = 0; k0 < S; k0 += AP_TK) {
+        for (int e = tid; e < AP_TM * AP_TK; e += 256) {
+            int rr = e / AP_TK, kk = e % AP_TK;
+            int row = row0 + rr, k = k0 + kk;
+            As[kk][rr] = (row < S && k < S) ? Op[(int64_t)row * S + k] : 0.0;
+        }
+        for (int e = tid; e < AP_TN * AP_TK; e += 256) {
+            int cc = e / AP_TK, kk = e % AP_TK;
+            int col = col0 + cc, k = k0 + kk;
+            double v = 0.0;
+            if (col < count && k < S) {
+                int64_t b = src ? src[col] : base + col;
+                v = in[b * S + k];
+            }
+            Bs[kk][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < AP_TK; ++kk) {
+            double a0 = As[kk][ty], a1 = As[kk][ty + 32];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                double bv = Bs[kk][tx + 8 * j];
+                acc[0][j] += a0 * bv;
+                acc[1][j] += a1 * bv;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        int row = row0 + ty + 32 * i;
+        if (row >= S) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int col = col0 + tx + 8 * j;
+            if (col >= count) continue;
+            int64_t b = dst ? dst[col] : base + col;
+            double* o = out + b * S + row;
+            *o = accumulate ? *o + acc[i][j] : acc[i][j];
+        }
+    }
+}
+
+// M2L (Eq. (m2l)), FP64: chk[B] = sum over V(B) of M2L[slot] * phi_u[A], per tile of
+// kM2LTile64 consecutive boxes of one level; every output is owned by one block.
+__global__ void __launch_bounds__(256) k_m2l64(const double* __restrict__ M, int S, const int32_t* vtab,
+                                               const int32_t* slots, int64_t lo, int64_t hi,
+                                               const double* __restrict__ phi, double* chk) {
+    __shared__ double As[AP_TK][AP_TM + 1];
+    __shared__ double Bs[AP_TK][AP_TN + 1];
+    __shared__ int src[AP_TN];
+    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
+    const int row0 = blockIdx.y * AP_TM;
+    const int64_t b0 = lo + (int64_t)blockIdx.x * AP_TN;
+    const int32_t* sl = slots + (int64_t)blockIdx.x * kSlotStride;
+    const int ns = sl[0];
+    const int64_t SS = (int64_t)S * S;
+    double acc[2][4] = {};
+    for (int si = 0; si < ns; ++si) {
+        const int slot = sl[1 + si];
+        __syncthreads();
+        if (tid < AP_TN) {
+            int64_t b = b0 + tid;
+            src[tid] = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
+        }
+        const double* Op = M + slot * SS;
+        for (int k0 = 0; k0 < S; k0 += AP_TK) {
+            __syncthreads();
+            for (int e = tid; e < AP_TM * AP_TK; e += 256) {
+                int rr = e / AP_TK, kk = e % AP_TK;
+                int row = row0 + rr, k = k0 + kk;
+                As[kk][rr] = (row < S && k < S) ? Op[(int64_t)row * S + k] : 0.0;
+            }
+            for (int e = tid; e < AP_TN * AP_TK; e += 256) {
+                int cc = e / AP_TK, kk = e % AP_TK;
+                int k = k0 + kk;
+                int a = src[cc];
+                Bs[kk][cc] = (a >= 0 && k < S) ? phi[(int64_t)a * S + k] : 0.0;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < AP_TK; ++kk) {
+                double a0 = As[kk][ty], a1 = As[kk][ty + 32];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    double bv = Bs[kk][tx + 8 * j];
+                    acc[0][j] += a0 * bv;
+                    acc[1][j] += a1 * bv;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        int row = row0 + ty + 32 * i;
+        if (row >= S) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t b = b0 + tx + 8 * j;
+            if (b >= hi) continue;
+            chk[b * S + row] = acc[i][j];
+        }
+    }
+}
+
+// M2L, mixed path, FP32 SIMT: FP32 matrices (row stride Sk, zero padded) times the
+// FP32-rounded upward densities, FP32 accumulation; the result goes to the FP64 check
+// potential. Tile: 64 rows x 64 boxes, k-chunks of 32; 4x4 outputs per thread.
+constexpr int M32_TM = 64, M32_TN = 64, M32_TK = 32;
+__global__ void __launch_bounds__(256) k_m2l32(const float* __restrict__ M, int S, int Sk, const int32_t* vtab,
+                                               const int32_t* slots, int64_t lo, int64_t hi,
+                                               const double* __restrict__ phi, double* chk) {
+    __shared__ __align__(16) float As[M32_TK][M32_TM];
+    __shared__ __align__(16) float Bs[M32_TK][M32_TN];
+    __shared__ int src[M32_TN];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int row0 = blockIdx.y * M32_TM;
+    const int64_t b0 = lo + (int64_t)blockIdx.x * M32_TN;
+    const int32_t* sl = slots + (int64_t)blockIdx.x * kSlotStride;
+    const int ns = sl[0];
+    const int64_t per = (int64_t)Sk * Sk;   // rows and columns padded to Sk
+    float acc[4][4] = {};
+    for (int si = 0; si < ns; ++si) {
+        const int slot = sl[1 + si];
+        __syncthreads();
+        if (tid < M32_TN) {
+            int64_t b = b0 + tid;
+            src[tid] = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
+        }
+        const float* Op = M + slot * per;
+        for (int k0 = 0; k0 < Sk; k0 += M32_TK) {
+            __syncthreads();
+            for (int e = tid; e < M32_TM * M32_TK; e += 256) {
+                int rr = e / M32_TK, kk = e % M32_TK;
+                int row = row0 + rr;
+                As[kk][rr] = (row < S) ? Op[(int64_t)row * Sk + k0 + kk] : 0.f;
+            }
+            for (int e = tid; e < M32_TN * M32_TK; e += 256) {
+                int cc = e / M32_TK, kk = e % M32_TK;
+                int k = k0 + kk;
+                int a = src[cc];
+                Bs[kk][cc] = (a >= 0 && k < S) ? (float)phi[(int64_t)a * S + k] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int kk = 0; kk < M32_TK; ++kk) {
+                float av[4], bv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int row = row0 + ty + 16 * i;
+        if (row >= S) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int64_t b = b0 + tx + 16 * j;
+            if (b >= hi) continue;
+            chk[b * S + row] = (double)acc[i][j];
+        }
+    }
+}
+
+// S2L for the X list: downward check potential of B (x_j = c_B + 1.2 r_B s_j) from the
+// sources of every leaf A in X(B). One block per box.
+template <bool MIXED>
+__global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxes, const int32_t* xoff,
+                                               const int32_t* xitems, const double* q, double* chk) {
+    const int B = boxes[blockIdx.x];
+    const int S = E.S;
+    const double r = half_width(E, E.level[B]);
+    const double* cB = E.centre + 3 * (int64_t)B;
+    __shared__ float4 sp32[256];
+    __shared__ double sp64[256][4];
+    for (int j0 = 0; j0 < S; j0 += P2M_T) {
+        const int j = j0 + threadIdx.x;
+        double xj[3];
+        for (int k = 0; k < 3; ++k) xj[k] = kRInner * r * E.surf[3 * min(j, S - 1) + k];
+        Kahan acc32;
+        double acc64 = 0;
+        for (int xi = xoff[B]; xi < xoff[B + 1]; ++xi) {
+            const int A = xitems[xi];
+            const double* cA = E.centre + 3 * (int64_t)A;
+            const float d0 = (float)(cA[0] - cB[0]), d1 = (float)(cA[1] - cB[1]), d2 = (float)(cA[2] - cB[2]);
+            for (int s0 = E.pstart[A]; s0 < E.pend[A]; s0 += 256) {
+                const int ns = min(256, E.pend[A] - s0);
+                __syncthreads();
+                for (int e = threadIdx.x; e < ns; e += P2M_T) {
+                    if (MIXED) {
+                        float4 v = E.loc[s0 + e];
+                        sp32[e] = make_float4(v.x + d0, v.y + d1, v.z + d2, (float)q[s0 + e]);
+                    } else {
+                        for (int k = 0; k < 3; ++k) sp64[e][k] = E.pts[3 * (int64_t)(s0 + e) + k] - cB[k];
+                        sp64[e][3] = q[s0 + e];
+                    }
+                }
+                __syncthreads();
+                if (MIXED) {
+                    const float x0 = (float)xj[0], x1 = (float)xj[1], x2 = (float)xj[2];
+                    for (int e = 0; e < ns; ++e) {
+                        const float4 v = sp32[e];
+                        const float dx = x0 - v.x, dy = x1 - v.y, dz = x2 - v.z;
+                        acc32.add(kern_f32(dx * dx + dy * dy + dz * dz, E.kp) * v.w);
+                    }
+                } else {
+                    for (int e = 0; e < ns; ++e) {
+                        const double dx = xj[0] - sp64[e][0], dy = xj[1] - sp64[e][1], dz = xj[2] - sp64[e][2];
+                        acc64 += kern_f64(sqrt(dx * dx + dy * dy + dz * dz), E.kp) * sp64[e][3];
+                    }
+                }
+            }
+        }
+        if (j < S) chk[(int64_t)B * S + j] += MIXED ? acc32.value() : acc64;
+    }
+}
+
+// Targets, far part: local expansion of the leaf (y = c_B + 2.6 r_B s_k, density phi_d)
+// and the W list (y = c_A + 1.2 r_A s_k, density phi_u). One block per leaf, one thread
+// per target point. Writes far[i] for every point of the leaf.
+constexpr int L2P_T = 64;
+template <bool MIXED>
+__global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves, const int32_t* woff,
+                                             const int32_t* witems, const double* phi_d,
+                                             const double* phi_u, double* far) {
+    const int B = leaves[blockIdx.x];
+    const int S = E.S;
+    const int lev = E.level[B];
+    const double* cB = E.centre + 3 * (int64_t)B;
+    __shared__ float4 s32[320];
+    __shared__ double s64[320][4];
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    const int nsrc_lists = 1 + (woff[B + 1] - woff[B]);
+    for (int t0 = p0; t0 < p1; t0 += L2P_T) {
+        const int i = t0 + threadIdx.x;
+        const bool act = i < p1;
+        float4 xl = act ? E.loc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        double x64[3] = {0, 0, 0};
+        if (!MIXED && act)
+            for (int k = 0; k < 3; ++k) x64[k] = E.pts[3 * (int64_t)i + k] - cB[k];
+        Kahan acc32;
+        double acc64 = 0;
+        for (int li = 0; li < nsrc_lists; ++li) {
+            int A;
+            double rad;
+            const double* dens;
+            if (li == 0) {
+                if (lev < 2) continue;
+                A = B;
+                rad = kROuter * half_width(E, lev);
+                dens = phi_d;
+            } else {
+                A = witems[woff[B] + li - 1];
+                rad = kRInner * half_width(E, E.level[A]);
+                dens = phi_u;
+            }
+            const double* cA = E.centre + 3 * (int64_t)A;
+            const double d[3] = {cA[0] - cB[0], cA[1] - cB[1], cA[2] - cB[2]};
+            for (int s0 = 0; s0 < S; s0 += 320) {
+                const int ns = min(320, S - s0);
+                __syncthreads();
+                for (int e = threadIdx.x; e < ns; e += L2P_T) {
+                    const double* sv = E.surf + 3 * (s0 + e);
+                    double y0 = d[0] + rad * sv[0], y1 = d[1] + rad * sv[1], y2 = d[2] + rad * sv[2];
+                    double ph = dens[(int64_t)A * S + s0 + e];
+                    if (MIXED) s32[e] = make_float4((float)y0, (float)y1, (float)y2, (float)ph);
+                    else {
+                        s64[e][0] = y0; s64[e][1] = y1; s64[e][2] = y2; s64[e][3] = ph;
+                    }
+                }
+                __syncthreads();
+                if (!act) continue;
+                if (MIXED) {
+                    for (int e = 0; e < ns; ++e) {
+                        const float4 v = s32[e];
+                        const float dx = xl.x - v.x, dy = xl.y - v.y, dz = xl.z - v.z;
+                        acc32.add(kern_f32(dx * dx + dy * dy + dz * dz, E.kp) * v.w);
+                    }
+                } else {
+                    for (int e = 0; e < ns; ++e) {
+                        const double dx = x64[0] - s64[e][0], dy = x64[1] - s64[e][1], dz = x64[2] - s64[e][2];
+                        acc64 += kern_f64(sqrt(dx * dx + dy * dy + dz * dz), E.kp) * s64[e][3];
+                    }
+                }
+            }
+        }
+        if (act) far[i] = MIXED ? acc32.value() : acc64;
+    }
+}
+
+// Near field (Eq. (nearfar), first sum) over U(B), plus the far part, the self term and
+// the scale C; writes the result in the caller's order. One block per leaf:
+// 64 targets x 4 source groups; sources staged in shared memory, B-local coordinates.
+constexpr int P2P_T = 256, P2P_TGT = 64, P2P_GRP = P2P_T / P2P_TGT, P2P_CHUNK = 2048;
+template <bool MIXED, class TO>
+__global__ void __launch_bounds__(P2P_T) k_p2p(EvalView E, const int32_t* leaves, const int32_t* uoff,
+                                             const int32_t* uitems, const double* q, const double* far,
+                                             const double* sigma, const double* Is, const int32_t* perm,
+                                             double C, TO* out) {
+    const int B = leaves[blockIdx.x];
+    const double* cB = E.centre + 3 * (int64_t)B;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s32 = reinterpret_cast<float4*>(smem_raw);
+    double* s64 = reinterpret_cast<double*>(smem_raw);
+    __shared__ double red[P2P_GRP][P2P_TGT];
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    const int tl = threadIdx.x % P2P_TGT, g = threadIdx.x / P2P_TGT;
+    const int u0 = uoff[B], u1 = uoff[B + 1];
+    const int chunk = MIXED ? P2P_CHUNK : P2P_CHUNK / 2;
+    for (int t0 = p0; t0 < p1; t0 += P2P_TGT) {
+        const int i = t0 + tl;
+        const bool act = i < p1;
+        float4 xl = act ? E.loc[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        double x64[3] = {0, 0, 0};
+        if (!MIXED && act)
+            for (int k = 0; k < 3; ++k) x64[k] = E.pts[3 * (int64_t)i + k] - cB[k];
+        Kahan acc32;
+        double acc64 = 0;
+        // walk the U list in chunks of sources
+        int ui = u0, uoffs = 0;
+        while (ui < u1) {
+            __syncthreads();
+            int ns = 0;
+            // stage: every thread walks the same boxes, writing its share
+            int wi = ui, wo = uoffs;
+            while (wi < u1 && ns < chunk) {
+                const int A = uitems[wi];
+                const int a0 = E.pstart[A], a1 = E.pend[A];
+                const int take = min(a1 - a0 - wo, chunk - ns);
+                const double* cA = E.centre + 3 * (int64_t)A;
+                if (MIXED) {
+                    const float d0 = (float)(cA[0] - cB[0]), d1 = (float)(cA[1] - cB[1]), d2 = (float)(cA[2] - cB[2]);
+                    for (int e = threadIdx.x; e < take; e += P2P_T) {
+                        float4 v = E.loc[a0 + wo + e];
+                        s32[ns + e] = make_float4(v.x + d0, v.y + d1, v.z + d2, (float)q[a0 + wo + e]);
+                    }
+                } else {
+                    for (int e = threadIdx.x; e < take; e += P2P_T) {
+                        int64_t j = a0 + wo + e;
+                        s64[4 * (ns + e) + 0] = E.pts[3 * j] - cB[0];
+                        s64[4 * (ns + e) + 1] = E.pts[3 * j + 1] - cB[1];
+                        s64[4 * (ns + e) + 2] = E.pts[3 * j + 2] - cB[2];
+                        s64[4 * (ns + e) + 3] = q[j];
+                    }
+                }
+                ns += take;
+                wo += take;
+                if (wo >= a1 - a0) {
+                    ++wi;
+                    wo = 0;
+                }
+            }
+            __syncthreads();
+            if (act) {
+                if (MIXED) {
+                    for (int e = g; e < ns; e += P2P_GRP) {
+                        const float4 v = s32[e];
+                        const float dx = xl.x - v.x, dy = xl.y - v.y, dz = xl.z - v.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        // j == i gives r2 == 0 exactly (same FP32 arithmetic); points are distinct
+                        if (r2 > 0.f) acc32.add(kern_f32(r2, E.kp) * v.w);
+                    }
+                } else {
+                    for (int e = g; e < ns; e += P2P_GRP) {
+                        const double dx = x64[0] - s64[4 * e], dy = x64[1] - s64[4 * e + 1],
+                                     dz = x64[2] - s64[4 * e + 2];
+                        const double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 > 0.0) acc64 += kern_f64(sqrt(r2), E.kp) * s64[4 * e + 3];
+                    }
+                }
+            }
+            ui = wi;
+            uoffs = wo;
+        }
+        red[g][tl] = MIXED ? acc32.value() : acc64;
+        __syncthreads();
+        if (g == 0 && act) {
+            double s = 0;
+            for (int k = 0; k < P2P_GRP; ++k) s += red[k][tl];
+            double v = C * (s + far[i] + sigma[i] * Is[i]);
+            out[perm[i]] = (TO)v;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// driver
+// ------------------------------------------------------------------------------------
+static EvalView make_view(Plan& p) {
+    EvalView E;
+    E.pts = ptr<double>(p.pts);
+    E.loc = ptr<float4>(p.loc32);
+    E.centre = ptr<double>(p.tree.centre);
+    E.level = ptr<int32_t>(p.tree.level);
+    E.pstart = ptr<int32_t>(p.tree.pstart);
+    E.pend = ptr<int32_t>(p.tree.pend);
+    E.surf = ptr<double>(p.surf);
+    E.side = p.tree.side;
+    E.S = p.S;
+    E.kp = make_kparams(p.a, p.b);
+    return E;
+}
+
+static void mark(Plan& p, int k) {
+    if (p.timing) cudaEventRecord(p.ev[k], p.stream);
+}
+
+int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
+    int64_t nl = 0;   // kernels launched by this evaluation
+#define EV_LAUNCH() \
+    do {             \
+        KF_LAUNCH(); \
+        ++nl;        \
+    } while (0)
+    Tree& t = p.tree;
+    cudaStream_t st = p.stream;
+    const int64_t n = t.n;
+    const int S = p.S;
+    const bool mixed = p.precision == KIFMM_MIXED;
+    EvalView E = make_view(p);
+    mark(p, 0);
+    if (dtype == KIFMM_F64)
+        k_scatter_q<double><<<nbk(n, 256), 256, 0, st>>>((const double*)I, ptr<int32_t>(t.perm), ptr<double>(p.w),
+                                                         n, ptr<double>(p.Isort), ptr<double>(p.q));
+    else
+        k_scatter_q<float><<<nbk(n, 256), 256, 0, st>>>((const float*)I, ptr<int32_t>(t.perm), ptr<double>(p.w),
+                                                        n, ptr<double>(p.Isort), ptr<double>(p.q));
+    EV_LAUNCH();
+    mark(p, 1);
+    const int L = t.nlevels;
+    double* chk = ptr<double>(p.chk);
+    double* phu = ptr<double>(p.phi_u);
+    double* phd = ptr<double>(p.phi_d);
+    if (L > 2) {
+        // ---- upward pass: S2M at the leaves, then M2M and the check-to-equivalent solve
+        int64_t lo2 = t.level_start[2];
+        KF_CUDA(cudaMemsetAsync(chk + lo2 * S, 0, (size_t)(t.nboxes - lo2) * S * 8, st));
+        if (p.n_p2m > 0) {
+            if (mixed) k_p2m<true><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), chk);
+            else k_p2m<false><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), chk);
+            EV_LAUNCH();
+        }
+        mark(p, 2);
+        for (int l = L - 1; l >= 2; --l) {
+            auto& LL = p.lv[l];
+            const LevelOps& op = p.ops[l];
+            if (l + 1 < L) {
+                for (int o = 0; o < 8; ++o) {
+                    if (LL.n_m2m[o] == 0) continue;
+                    dim3 g(nbk(LL.n_m2m[o], AP_TN), nbk(S, AP_TM));
+                    k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.m2m) + (int64_t)o * S * S, S,
+                                                 ptr<int32_t>(LL.m2m_src[o]), ptr<int32_t>(LL.m2m_dst[o]), 0,
+                                                 LL.n_m2m[o], phu, chk, 1);
+                    EV_LAUNCH();
+                }
+            }
+            dim3 g(nbk(LL.n_all, AP_TN), nbk(S, AP_TM));
+            k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.uc2ue), S, nullptr, nullptr, t.level_start[l], LL.n_all,
+                                         chk, phu, 0);
+            EV_LAUNCH();
+        }
+        mark(p, 3);
+        // ---- downward pass
+        for (int l = 2; l < L; ++l) {
+            auto& LL = p.lv[l];
+            const LevelOps& op = p.ops[l];
+            int64_t lo = t.level_start[l], hi = t.level_start[l + 1];
+            if (LL.n_tiles > 0) {
+                if (mixed) {
+                    dim3 g(LL.n_tiles, nbk(S, M32_TM));
+                    k_m2l32<<<g, 256, 0, st>>>(ptr<float>(op.m2l_hi), S, p.Sp, ptr<int32_t>(p.vtab),
+                                               ptr<int32_t>(LL.m2l_slots), lo, hi, phu, chk);
+                } else {
+                    dim3 g(LL.n_tiles, nbk(S, AP_TM));
+                    k_m2l64<<<g, 256, 0, st>>>(ptr<double>(op.m2l), S, ptr<int32_t>(p.vtab),
+                                               ptr<int32_t>(LL.m2l_slots), lo, hi, phu, chk);
+                }
+                EV_LAUNCH();
+            }
+        }
+        mark(p, 4);
+        for (int l = 2; l < L; ++l) {
+            auto& LL = p.lv[l];
+            const LevelOps& op = p.ops[l];
+            if (LL.n_x > 0) {
+                if (mixed) k_s2l_x<true><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
+                                                                  ptr<int32_t>(p.lists[3].items), ptr<double>(p.q), chk);
+                else k_s2l_x<false><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
+                                                              ptr<int32_t>(p.lists[3].items), ptr<double>(p.q), chk);
+                EV_LAUNCH();
+            }
+            if (l >= 3) {   // L2L from the parents at level l - 1
+                auto& LP = p.lv[l - 1];
+                const LevelOps& pop = p.ops[l - 1];
+                for (int o = 0; o < 8; ++o) {
+                    if (LP.n_m2m[o] == 0) continue;
+                    dim3 g(nbk(LP.n_m2m[o], AP_TN), nbk(S, AP_TM));
+                    // src = parent (dst list of M2M), dst = child (src list of M2M)
+                    k_apply64<<<g, 256, 0, st>>>(ptr<double>(pop.l2l) + (int64_t)o * S * S, S,
+                                                 ptr<int32_t>(LP.m2m_dst[o]), ptr<int32_t>(LP.m2m_src[o]), 0,
+                                                 LP.n_m2m[o], phd, chk, 1);
+                    EV_LAUNCH();
+                }
+            }
+            dim3 g(nbk(LL.n_all, AP_TN), nbk(S, AP_TM));
+            k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.dc2de), S, nullptr, nullptr, t.level_start[l], LL.n_all,
+                                         chk, phd, 0);
+            EV_LAUNCH();
+        }
+    } else {
+        mark(p, 2);
+        mark(p, 3);
+        mark(p, 4);
+    }
+    mark(p, 5);
+    // ---- targets
+    if (p.nleaves > 0) {
+        if (mixed) k_l2p<true><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<int32_t>(p.lists[2].off),
+                                                                     ptr<int32_t>(p.lists[2].items), phd, phu, ptr<double>(p.far));
+        else k_l2p<false><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<int32_t>(p.lists[2].off),
+                                                                 ptr<int32_t>(p.lists[2].items), phd, phu, ptr<double>(p.far));
+        EV_LAUNCH();
+    }
+    mark(p, 6);
+    {
+        size_t smem = (size_t)P2P_CHUNK * 16;
+        const int32_t* uo = ptr<int32_t>(p.lists[0].off);
+        const int32_t* ui = ptr<int32_t>(p.lists[0].items);
+        unsigned g = (unsigned)p.nleaves;
+        if (mixed) {
+            if (dtype == KIFMM_F64)
+                k_p2p<true, double><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                                            ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (double*)S_out);
+            else
+                k_p2p<true, float><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                                           ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (float*)S_out);
+        } else {
+            if (dtype == KIFMM_F64)
+                k_p2p<false, double><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                                             ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (double*)S_out);
+            else
+                k_p2p<false, float><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                                            ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (float*)S_out);
+        }
+        EV_LAUNCH();
+    }
+    mark(p, 7);
+    p.eval_launches = nl;
+#undef EV_LAUNCH
+    return KIFMM_OK;
+}
+
+}  // namespace kifmm

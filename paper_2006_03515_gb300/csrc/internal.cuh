@@ -1,0 +1,174 @@
+// Internal declarations shared by the translation units of libkifmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/kifmm.h"
+
+namespace kifmm {
+
+constexpr int kKeyBits = 21;
+constexpr int kMaxLevel = 20;
+constexpr int kOffsetSlots = 343;   // (dx, dy, dz) in [-3, 3]^3
+constexpr double kRInner = 1.2;     // upward equivalent / downward check surface (box half-widths)
+constexpr double kROuter = 2.6;     // upward check / downward equivalent surface
+
+// ---- error plumbing ---------------------------------------------------------------
+void set_error(const std::string& msg);
+struct Status {
+    int code = KIFMM_OK;
+    std::string msg;
+};
+#define KF_CUDA(call)                                                                     \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            kifmm::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));        \
+            return KIFMM_ERR_CUDA;                                                        \
+        }                                                                                 \
+    } while (0)
+#define KF_LAUNCH()                                                                       \
+    do {                                                                                  \
+        cudaError_t e_ = cudaGetLastError();                                              \
+        if (e_ != cudaSuccess) {                                                          \
+            kifmm::set_error(std::string("kernel launch (") + __FILE__ + ":" +            \
+                             std::to_string(__LINE__) + "): " + cudaGetErrorString(e_));  \
+            return KIFMM_ERR_CUDA;                                                        \
+        }                                                                                 \
+    } while (0)
+#define KF_TRY(expr)                                                                      \
+    do {                                                                                  \
+        int s_ = (expr);                                                                  \
+        if (s_ != KIFMM_OK) return s_;                                                    \
+    } while (0)
+
+// ---- device buffer owned by a plan ---------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+int dev_alloc(DevBuf& b, size_t bytes);
+void dev_free(DevBuf& b);
+template <class T> T* ptr(const DevBuf& b) { return reinterpret_cast<T*>(b.p); }
+
+// ---- plan ---------------------------------------------------------------------------
+struct Tree {
+    int64_t n = 0;          // points
+    int64_t nboxes = 0;
+    int nlevels = 0;
+    std::vector<int64_t> level_start;   // host copy, nlevels + 1 entries
+    double origin[3] = {0, 0, 0};
+    double side = 0;
+    // device arrays
+    DevBuf keys;      // u64[n] sorted Morton keys
+    DevBuf perm;      // i32[n] input index of sorted point k
+    DevBuf level;     // i32[nb]
+    DevBuf anchor;    // i32[3*nb]
+    DevBuf mcode;     // u64[nb] Morton code of the anchor at the box's level
+    DevBuf parent;    // i32[nb]
+    DevBuf child;     // i32[8*nb]
+    DevBuf pstart;    // i32[nb]
+    DevBuf pend;      // i32[nb]
+    DevBuf leaf;      // i32[nb]
+    DevBuf centre;    // f64[3*nb]
+};
+
+struct Csr {
+    DevBuf off;    // i32[nb+1]
+    DevBuf items;  // i32[len]
+    int64_t len = 0;
+};
+
+struct LevelOps {
+    int level = 0;
+    double r = 0;        // box half-width
+    int rank = 0;        // kept rank of the pseudo-inverse
+    DevBuf uc2ue;        // f64[S*S]  pinv(K(x^{u}, y^{u})): upward check -> equivalent
+    DevBuf dc2de;        // f64[S*S]  pinv(K(x^{d}, y^{d})): downward check -> equivalent
+    DevBuf m2m;          // f64[8*S*S] K(x^{P,u}, y^{C_o,u}), this level = parent level
+    DevBuf l2l;          // f64[8*S*S] K(x^{C_o,d}, y^{P,d}), this level = parent level
+    DevBuf m2l;          // f64[343*S*S] K(x^{B,d}, y^{A,u}), c_A - c_B = 2 r delta
+    DevBuf m2l_hi;       // f32[343*Sp*Sp] TF32-rounded high part (mixed), K-padded
+    DevBuf m2l_lo;       // f32[343*Sp*Sp] residual low part (mixed)
+};
+
+struct Plan {
+    int precision = KIFMM_FP64;
+    int self_mode = KIFMM_SELF_CELL_EXACT;
+    double pinv_eps = 1e-5;
+    cudaStream_t stream = nullptr;
+    double a = 0, b = 0;
+    int m0 = 6, S = 152, Sp = 152;
+    int leaf_size = 64;
+    Tree tree;
+    Csr lists[4];                 // U, V, W, X
+    DevBuf vtab;                  // i32[nb * 343]: source box of V(B) at offset slot, -1 if none
+    std::vector<LevelOps> ops;    // indexed by level (entries below 2 unused)
+    DevBuf surf;                  // f64[3*S] unit lattice
+    // per-point data in sorted order
+    DevBuf pts;       // f64[3n] sorted coordinates
+    DevBuf loc32;     // f32[4n] coordinates relative to the leaf centre (x, y, z, pad)
+    DevBuf w;         // f64[n] cell volume h^3
+    DevBuf sigma;     // f64[n] self-cell value
+    DevBuf leaf_of;   // i32[n] leaf box of each sorted point
+    // leaves and per-level box lists
+    DevBuf leaves;    // i32[nleaves]
+    int64_t nleaves = 0;
+    DevBuf p2m_boxes;      // i32: leaves of level >= 2
+    int64_t n_p2m = 0;
+    // eval workspace
+    DevBuf q;          // f64[n]  I*h^3 (sorted)
+    DevBuf Isort;      // f64[n]
+    DevBuf chk;        // f64[nb*S] check potentials (up and down share)
+    DevBuf phi_u;      // f64[nb*S]
+    DevBuf phi_d;      // f64[nb*S]
+    DevBuf phiu_hi;    // f32[nb*Sp] (mixed)
+    DevBuf phiu_lo;    // f32[nb*Sp]
+    DevBuf chk32;      // f32[nb*Sp] M2L output (mixed)
+    DevBuf phid32;     // f32[nb*S]  (mixed) downward density in FP32 for L2P
+    DevBuf phiu32;     // f32[nb*S]  (mixed) upward density in FP32 for M2P
+    DevBuf far;        // f64[n] far-field part at the sorted points
+    DevBuf host_I;     // staging for kifmm_eval_host (n * 8 bytes each)
+    DevBuf host_S;
+    // per-level work lists for the batched matrix applications
+    struct LevelLists {
+        DevBuf all;        int n_all = 0;        // boxes of the level
+        DevBuf leafs;      int n_leaf = 0;       // leaves of the level
+        DevBuf nonleaf;    int n_nonleaf = 0;    // non-leaf boxes of the level
+        DevBuf m2m_src[8]; DevBuf m2m_dst[8]; int n_m2m[8] = {0};   // child (src), parent (dst)
+        DevBuf m2l_tiles;  int n_tiles = 0;      // tile -> first box (tiles of kM2LTile boxes)
+        DevBuf m2l_slots;  DevBuf m2l_slot_off;  // per tile: list of active offset slots
+        DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
+    };
+    std::vector<LevelLists> lv;
+    DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
+    int64_t eval_launches = 0;   // kernels of the last evaluation
+    int64_t p2p_pairs = 0;       // near-field pairs of one evaluation
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[9] = {};
+    float phase_ms[8] = {0};
+    int n_phases = 0;
+    // batch graph
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<const void*> graph_key;
+};
+
+// tree.cu
+int build_tree(Plan& p, const double* points_dev, const double* h_dev, double uniform_h,
+               const kifmm_opts& o);
+int build_lists(Plan& p);
+int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cudaStream_t st,
+                     DevBuf& tmp_keys, DevBuf& tmp_vals, DevBuf& hist);
+int device_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_host,
+                    cudaStream_t st, DevBuf& scratch);
+// operators.cu
+int build_operators(Plan& p);
+int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
+// eval.cu
+int build_eval_data(Plan& p);
+int run_eval(Plan& p, const void* I, void* S, int dtype, double C);
+
+}  // namespace kifmm

@@ -1,0 +1,74 @@
+// The photoionization kernel on the device (Eqs. (integral) and (gfun) of the paper):
+//   K(R) = (exp(-aR) - exp(-bR)) / (4 pi R^3 ln(b/a)),  a = chi_min p_O2, b = chi_max p_O2.
+// Both forms write the difference as exp(-aR) * (1 - exp(-(b-a)R)) so that it keeps
+// its relative precision when (b-a)R is small (low pressure).
+#pragma once
+#include <cuda_runtime.h>
+
+namespace kifmm {
+
+struct KParams {
+    double a, b, bma, norm;   // norm = 1 / (4 pi ln(b/a))
+    float a_l2e, bma_l2e, bma_f, norm_f;   // FP32 forms: a*log2(e), (b-a)*log2(e), b-a, norm
+};
+
+inline KParams make_kparams(double a, double b) {
+    KParams k;
+    k.a = a;
+    k.b = b;
+    k.bma = b - a;
+    k.norm = 1.0 / (4.0 * 3.14159265358979323846 * log(b / a));
+    const double l2e = 1.4426950408889634074;
+    k.a_l2e = (float)(a * l2e);
+    k.bma_l2e = (float)((b - a) * l2e);
+    k.bma_f = (float)(b - a);
+    k.norm_f = (float)k.norm;
+    return k;
+}
+
+// FP64: CUDA's exp / expm1.
+__device__ __forceinline__ double kern_f64(double R, const KParams& k) {
+    return -exp(-k.a * R) * expm1(-k.bma * R) * k.norm / (R * R * R);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// 1 - exp(-x) for x >= 0 in FP32. For x < 0.5 the Maclaurin series of 1 - e^{-x},
+// x (1 - x/2 (1 - x/3 (1 - ... (1 - x/10)))), truncated after the x^10 term
+// (relative truncation error below x^10/11! < 3e-11 for x < 0.5); otherwise
+// 1 - 2^{-x log2 e}, where the subtraction loses at most a factor 1/(1 - e^{-0.5}) = 2.5.
+__device__ __forceinline__ float one_minus_exp_neg(float x, float x_l2e) {
+    if (x < 0.5f) {
+        float t = 1.0f - x * (1.0f / 10.0f);
+        t = 1.0f - x * (1.0f / 9.0f) * t;
+        t = 1.0f - x * (1.0f / 8.0f) * t;
+        t = 1.0f - x * (1.0f / 7.0f) * t;
+        t = 1.0f - x * (1.0f / 6.0f) * t;
+        t = 1.0f - x * (1.0f / 5.0f) * t;
+        t = 1.0f - x * (1.0f / 4.0f) * t;
+        t = 1.0f - x * (1.0f / 3.0f) * t;
+        t = 1.0f - x * 0.5f * t;
+        return x * t;
+    }
+    return 1.0f - ex2_approx(-x_l2e);
+}
+
+// FP32 kernel from the squared distance r2 > 0 (box-local coordinates).
+__device__ __forceinline__ float kern_f32(float r2, const KParams& k) {
+    const float rinv = rsqrt_approx(r2);
+    const float R = r2 * rinv;
+    const float ea = ex2_approx(-k.a_l2e * R);
+    const float m1 = one_minus_exp_neg(k.bma_f * R, k.bma_l2e * R);
+    return ea * m1 * k.norm_f * (rinv * rinv * rinv);
+}
+
+}  // namespace kifmm

@@ -1,0 +1,498 @@
+// Plan, part 2: equivalent/check surfaces, the per-level translation matrices
+// (Eqs. (s2m), (m2m), (m2l), (l2l), (s2l) of the paper), their truncated-SVD
+// pseudo-inverses, and the self-cell values of the discrete kernel G (Sec. 3).
+#include <algorithm>
+#include <cmath>
+
+#include "internal.cuh"
+#include "kernel.cuh"
+
+namespace kifmm {
+
+// Lattice {-1 + 2j/(m0-1)}^3 restricted to the cube's boundary, x fastest.
+__global__ void surface_lattice(int m0, double* s) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int n = 0;
+    for (int k = 0; k < m0; ++k)
+        for (int j = 0; j < m0; ++j)
+            for (int i = 0; i < m0; ++i)
+                if (i == 0 || i == m0 - 1 || j == 0 || j == m0 - 1 || k == 0 || k == m0 - 1) {
+                    s[3 * n + 0] = -1.0 + 2.0 * i / (m0 - 1);
+                    s[3 * n + 1] = -1.0 + 2.0 * j / (m0 - 1);
+                    s[3 * n + 2] = -1.0 + 2.0 * k / (m0 - 1);
+                    ++n;
+                }
+}
+
+// out[i*S + j] = K(|(d + rx s_i) - (ry s_j)|): target point i on a surface of radius rx
+// about the origin shifted by d, source point j on a surface of radius ry about the origin.
+// blockIdx.y selects one of `nmat` matrices with shifts d[3*blockIdx.y ...].
+__global__ void surface_kmat(const double* s, int S, double rx, double ry, const double* d,
+                             KParams kp, double* out, int64_t stride) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * S) return;
+    int i = (int)(e / S), j = (int)(e % S);
+    const double* dd = d + 3 * blockIdx.y;
+    double r2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        double x = dd[k] + rx * s[3 * i + k] - ry * s[3 * j + k];
+        r2 += x * x;
+    }
+    out[blockIdx.y * stride + e] = (dd[0] == 0.0 && dd[1] == 0.0 && dd[2] == 0.0 && r2 == 0.0)
+                                       ? 0.0 : kern_f64(sqrt(r2), kp);
+}
+
+// One-sided (Hestenes) Jacobi SVD, one CTA per matrix, column-major A (S x S) and V.
+// Column pairs follow the round-robin (circle) ordering: in round r player n-1 meets r
+// and (r+i) meets (r-i) mod (n-1), so every round rotates n/2 disjoint pairs.
+// On return A holds U*Sigma (columns), V the right singular vectors; conv[0] = sweeps
+// used, or -1 if the off-diagonal criterion was not met within max_sweeps.
+__global__ void jacobi_svd(double* Aall, double* Vall, int S, int max_sweeps, int* conv) {
+    double* A = Aall + (int64_t)blockIdx.x * S * S;
+    double* V = Vall + (int64_t)blockIdx.x * S * S;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int64_t e = threadIdx.x; e < (int64_t)S * S; e += blockDim.x) V[e] = (e / S == e % S) ? 1.0 : 0.0;
+    __shared__ int rotated;
+    __syncthreads();
+    const int n = S;          // S is even for every m0
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        if (threadIdx.x == 0) rotated = 0;
+        __syncthreads();
+        for (int r = 0; r < n - 1; ++r) {
+            for (int pi = warp; pi < n / 2; pi += nw) {
+                int p, q;
+                if (pi == 0) {
+                    p = r;
+                    q = n - 1;
+                } else {
+                    p = (r + pi) % (n - 1);
+                    q = (r - pi + (n - 1)) % (n - 1);
+                }
+                double* ap = A + (int64_t)p * S;
+                double* aq = A + (int64_t)q * S;
+                double al = 0, be = 0, ga = 0;
+                for (int i = lane; i < S; i += 32) {
+                    double x = ap[i], y = aq[i];
+                    al += x * x;
+                    be += y * y;
+                    ga += x * y;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (al == 0.0 || be == 0.0) continue;
+                if (fabs(ga) <= 1e-14 * sqrt(al * be)) continue;
+                double zeta = (be - al) / (2.0 * ga);
+                double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                double c = 1.0 / sqrt(1.0 + t * t);
+                double sn = c * t;
+                for (int i = lane; i < S; i += 32) {
+                    double x = ap[i], y = aq[i];
+                    ap[i] = c * x - sn * y;
+                    aq[i] = sn * x + c * y;
+                }
+                double* vp = V + (int64_t)p * S;
+                double* vq = V + (int64_t)q * S;
+                for (int i = lane; i < S; i += 32) {
+                    double x = vp[i], y = vq[i];
+                    vp[i] = c * x - sn * y;
+                    vq[i] = sn * x + c * y;
+                }
+                if (lane == 0) rotated = 1;
+            }
+            __syncthreads();
+        }
+        __syncthreads();
+        if (!rotated) break;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) conv[blockIdx.x] = (sweep < max_sweeps) ? sweep + 1 : -1;
+}
+
+// sigma_k = |a_k| and the kept rank for the relative cut-off eps.
+__global__ void svd_sigma(const double* Aall, int S, double eps, double* sig_all, int* rank) {
+    const double* A = Aall + (int64_t)blockIdx.x * S * S;
+    double* sig = sig_all + (int64_t)blockIdx.x * S;
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+        double s = 0;
+        for (int i = 0; i < S; ++i) s += A[(int64_t)k * S + i] * A[(int64_t)k * S + i];
+        sig[k] = sqrt(s);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double mx = 0;
+        for (int k = 0; k < S; ++k) mx = fmax(mx, sig[k]);
+        int r = 0;
+        for (int k = 0; k < S; ++k) {
+            if (sig[k] >= eps * mx) ++r;
+            else sig[k] = 0.0;   // dropped
+        }
+        rank[blockIdx.x] = r;
+    }
+}
+
+// Truncated pseudo-inverse, row-major: P[j*S + i] = sum_k V[j][k] U[i][k] / sigma_k,
+// with U[i][k] = A[i][k] / sigma_k (A holds U Sigma). T = transposed output (P^T).
+__global__ void svd_pinv(const double* Aall, const double* Vall, const double* sig_all, int S,
+                         double* P, double* PT) {
+    const double* A = Aall + (int64_t)blockIdx.y * S * S;
+    const double* V = Vall + (int64_t)blockIdx.y * S * S;
+    const double* sig = sig_all + (int64_t)blockIdx.y * S;
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * S) return;
+    int j = (int)(e / S), i = (int)(e % S);
+    double acc = 0;
+    for (int k = 0; k < S; ++k) {
+        double s = sig[k];
+        if (s > 0.0) acc += V[(int64_t)k * S + j] * A[(int64_t)k * S + i] / (s * s);
+    }
+    P[(int64_t)blockIdx.y * S * S + e] = acc;
+    PT[(int64_t)blockIdx.y * S * S + (int64_t)i * S + j] = acc;
+}
+
+__global__ void transpose_to_colmajor(const double* in, double* out, int S, int nmat) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * S * nmat) return;
+    int64_t m = e / ((int64_t)S * S);
+    int64_t r = e % ((int64_t)S * S);
+    int i = (int)(r / S), j = (int)(r % S);
+    out[m * S * S + (int64_t)j * S + i] = in[e];
+}
+
+// M2L matrices for the mixed path in FP32, rows and columns padded to Sp with zeros.
+__global__ void split_m2l(const double* m2l, int S, int Sp, float* hi, float* lo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t per = (int64_t)Sp * Sp;
+    if (e >= per * kOffsetSlots) return;
+    int64_t slot = e / per;
+    int i = (int)((e % per) / Sp), j = (int)(e % Sp);
+    double v = (i < S && j < S) ? m2l[slot * S * S + (int64_t)i * S + j] : 0.0;
+    hi[e] = (float)v;
+    if (lo) lo[e] = (float)(v - (double)(float)v);
+}
+
+static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+int build_operators(Plan& p) {
+    cudaStream_t st = p.stream;
+    const int S = p.S;
+    const int L = p.tree.nlevels;
+    const KParams kp = make_kparams(p.a, p.b);
+    KF_TRY(dev_alloc(p.surf, 3 * S * sizeof(double)));
+    surface_lattice<<<1, 1, 0, st>>>(p.m0, ptr<double>(p.surf));
+    KF_LAUNCH();
+    p.ops.clear();
+    p.ops.resize(std::max(L, 1));
+    if (L <= 2) return KIFMM_OK;   // no box has a far field
+
+    const int nlev = L - 2;        // levels 2 .. L-1
+    const int64_t SS = (int64_t)S * S;
+    DevBuf A, V, sig, rank, conv, shifts, P, PT;
+    KF_TRY(dev_alloc(A, nlev * SS * 8));
+    KF_TRY(dev_alloc(V, nlev * SS * 8));
+    KF_TRY(dev_alloc(sig, nlev * S * 8));
+    KF_TRY(dev_alloc(rank, nlev * 4));
+    KF_TRY(dev_alloc(conv, nlev * 4));
+    KF_TRY(dev_alloc(P, nlev * SS * 8));
+    KF_TRY(dev_alloc(PT, nlev * SS * 8));
+    KF_TRY(dev_alloc(shifts, kOffsetSlots * 3 * 8));
+    double zero3[3] = {0, 0, 0};
+    DevBuf z;
+    KF_TRY(dev_alloc(z, 3 * 8));
+    KF_CUDA(cudaMemcpyAsync(z.p, zero3, 24, cudaMemcpyHostToDevice, st));
+    // upward check-to-equivalent systems K(x^{B,u}, y^{B,u}) for every level
+    for (int l = 2; l < L; ++l) {
+        double r = p.tree.side / (double)(2ll << l);
+        p.ops[l].level = l;
+        p.ops[l].r = r;
+        DevBuf tmp;
+        KF_TRY(dev_alloc(tmp, SS * 8));
+        surface_kmat<<<dim3(nb(SS, 256), 1), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r,
+                                                           kRInner * r, ptr<double>(z), kp,
+                                                           ptr<double>(tmp), SS);
+        KF_LAUNCH();
+        transpose_to_colmajor<<<nb(SS, 256), 256, 0, st>>>(ptr<double>(tmp), ptr<double>(A) + (l - 2) * SS, S, 1);
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));
+        dev_free(tmp);
+    }
+    jacobi_svd<<<nlev, 1024, 0, st>>>(ptr<double>(A), ptr<double>(V), S, 60, ptr<int>(conv));
+    KF_LAUNCH();
+    svd_sigma<<<nlev, 256, 0, st>>>(ptr<double>(A), S, p.pinv_eps, ptr<double>(sig), ptr<int>(rank));
+    KF_LAUNCH();
+    svd_pinv<<<dim3(nb(SS, 256), nlev), 256, 0, st>>>(ptr<double>(A), ptr<double>(V), ptr<double>(sig), S,
+                                                      ptr<double>(P), ptr<double>(PT));
+    KF_LAUNCH();
+    std::vector<int> hrank(nlev), hconv(nlev);
+    KF_CUDA(cudaMemcpyAsync(hrank.data(), rank.p, nlev * 4, cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaMemcpyAsync(hconv.data(), conv.p, nlev * 4, cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    for (int l = 2; l < L; ++l) {
+        if (hconv[l - 2] < 0) {
+            set_error("kifmm_plan: Jacobi SVD did not converge at level " + std::to_string(l));
+            return KIFMM_ERR_NUMERIC;
+        }
+        LevelOps& op = p.ops[l];
+        op.rank = hrank[l - 2];
+        KF_TRY(dev_alloc(op.uc2ue, SS * 8));
+        KF_TRY(dev_alloc(op.dc2de, SS * 8));
+        KF_CUDA(cudaMemcpyAsync(op.uc2ue.p, ptr<double>(P) + (l - 2) * SS, SS * 8, cudaMemcpyDeviceToDevice, st));
+        // K is symmetric, so G(x^{B,d}, y^{B,d}) = G(x^{B,u}, y^{B,u})^T (the downward check
+        // surface is the upward equivalent one and vice versa) and its pseudo-inverse is
+        // the transpose of the upward one.
+        KF_CUDA(cudaMemcpyAsync(op.dc2de.p, ptr<double>(PT) + (l - 2) * SS, SS * 8, cudaMemcpyDeviceToDevice, st));
+    }
+    // M2L: 343 offset slots per level (the 27 near slots stay zero)
+    std::vector<double> sh(kOffsetSlots * 3);
+    for (int l = 2; l < L; ++l) {
+        LevelOps& op = p.ops[l];
+        double r = op.r;
+        for (int dz = -3; dz <= 3; ++dz)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dx = -3; dx <= 3; ++dx) {
+                    int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                    // target (downward check, centre c_B = 0) minus source centre c_A = 2 r delta
+                    sh[3 * sl + 0] = -2.0 * r * dx;
+                    sh[3 * sl + 1] = -2.0 * r * dy;
+                    sh[3 * sl + 2] = -2.0 * r * dz;
+                }
+        KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, st));
+        KF_TRY(dev_alloc(op.m2l, kOffsetSlots * SS * 8));
+        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(
+            ptr<double>(p.surf), S, kRInner * r, kRInner * r, ptr<double>(shifts), kp, ptr<double>(op.m2l), SS);
+        KF_LAUNCH();
+        // zero the 27 near slots (|delta|_inf <= 1)
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                    KF_CUDA(cudaMemsetAsync(ptr<double>(op.m2l) + sl * SS, 0, SS * 8, st));
+                }
+        if (p.precision == KIFMM_MIXED) {
+            int64_t per = (int64_t)p.Sp * p.Sp;
+            KF_TRY(dev_alloc(op.m2l_hi, kOffsetSlots * per * 4));
+            split_m2l<<<nb(kOffsetSlots * per, 256), 256, 0, st>>>(ptr<double>(op.m2l), S, p.Sp,
+                                                                  ptr<float>(op.m2l_hi), nullptr);
+            KF_LAUNCH();
+        }
+        // M2M / L2L from this level (parent) to level l+1 (children)
+        if (l + 1 < L) {
+            double rc = r / 2.0;
+            for (int o = 0; o < 8; ++o) {
+                double cc[3] = {rc * (2.0 * (o & 1) - 1.0), rc * (2.0 * ((o >> 1) & 1) - 1.0),
+                                rc * (2.0 * ((o >> 2) & 1) - 1.0)};
+                // M2M: target = parent upward check (centre 0), source = child equivalent at cc
+                sh[3 * o + 0] = -cc[0];
+                sh[3 * o + 1] = -cc[1];
+                sh[3 * o + 2] = -cc[2];
+                // L2L: target = child downward check at cc, source = parent equivalent at 0
+                sh[24 + 3 * o + 0] = cc[0];
+                sh[24 + 3 * o + 1] = cc[1];
+                sh[24 + 3 * o + 2] = cc[2];
+            }
+            KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), 48 * 8, cudaMemcpyHostToDevice, st));
+            KF_TRY(dev_alloc(op.m2m, 8 * SS * 8));
+            KF_TRY(dev_alloc(op.l2l, 8 * SS * 8));
+            surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * rc,
+                                                              ptr<double>(shifts), kp, ptr<double>(op.m2m), SS);
+            KF_LAUNCH();
+            surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * rc, kROuter * r,
+                                                              ptr<double>(shifts) + 24, kp, ptr<double>(op.l2l), SS);
+            KF_LAUNCH();
+        }
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    KF_CUDA(cudaStreamSynchronize(st));
+    dev_free(A); dev_free(V); dev_free(sig); dev_free(rank); dev_free(conv);
+    dev_free(P); dev_free(PT); dev_free(shifts); dev_free(z);
+    return KIFMM_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// self-cell values sigma(h) (discrete kernel G, i == j)
+// ------------------------------------------------------------------------------------
+// E1(x), x > 0: Abramowitz & Stegun 5.1.11 (power series) for x <= 1, and the
+// continued fraction 5.1.22 in its even-contracted form, evaluated with the
+// modified Lentz method, for x > 1.
+__device__ double e1_dev(double x) {
+    if (x <= 1.0) {
+        double s = 0.0, term = 1.0;
+        for (int n = 1; n < 60; ++n) {
+            term *= -x / n;
+            double add = -term / n;
+            s += add;
+            if (fabs(add) < 1e-18 * fmax(1.0, fabs(s))) break;
+        }
+        return -0.57721566490153286061 - log(x) + s;
+    }
+    const double tiny = 1e-300;
+    double bq = x + 1.0, c = 1.0 / tiny, d = 1.0 / bq, h = d;
+    for (int i = 1; i < 10000; ++i) {
+        double an = -(double)i * i;
+        bq += 2.0;
+        d = 1.0 / (an * d + bq);
+        c = bq + an / c;
+        double del = c * d;
+        h *= del;
+        if (fabs(del - 1.0) < 1e-16) break;
+    }
+    return h * exp(-x);
+}
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on the three-term
+// recurrence of the Legendre polynomials.
+__global__ void gauss_legendre(int n, double* x, double* w) {
+    int i = threadIdx.x;
+    if (i >= n) return;
+    double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
+    double pp = 0;
+    for (int it = 0; it < 100; ++it) {
+        double p1 = 1.0, p2 = 0.0;
+        for (int k = 1; k <= n; ++k) {
+            double p3 = p2;
+            p2 = p1;
+            p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
+        }
+        pp = n * (z * p1 - p2) / (z * z - 1.0);
+        double z1 = z;
+        z = z1 - p1 / pp;
+        if (fabs(z - z1) < 1e-16) break;
+    }
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+}
+
+// One block per distinct cell edge h: sigma = 6 * sum_{ij} w_i w_j (h/2)/R^3 F(R) / (4 pi ln(b/a)),
+// R = sqrt(u_i^2 + u_j^2 + h^2/4), u = (h/2) t, F(R) = ln(b/a) + E1(bR) - E1(aR)  (cell_exact);
+// or the paper's 2-point Gauss-Legendre value h^3 * 3 g(rho) / (pi * 3h^2), rho = h/2.
+__global__ void self_sigma(const double* hs, int nh, double a, double b, int mode, int nq,
+                           const double* gx, const double* gw, double* out) {
+    int k = blockIdx.x;
+    if (k >= nh) return;
+    double h = hs[k];
+    double lba = log(b / a);
+    if (mode == KIFMM_SELF_PAPER_GL2) {
+        if (threadIdx.x == 0) {
+            double s2 = 3.0 * h * h;
+            double rho = sqrt(s2 / 12.0);
+            double g = (exp(-a * rho) - exp(-b * rho)) / (rho * lba);
+            out[k] = h * h * h * 3.0 * g / (3.14159265358979323846 * s2);
+        }
+        return;
+    }
+    __shared__ double red[256];
+    double acc = 0;
+    for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
+        int i = e / nq, j = e % nq;
+        double ui = 0.5 * h * gx[i], uj = 0.5 * h * gx[j];
+        double wi = 0.5 * h * gw[i], wj = 0.5 * h * gw[j];
+        double R = sqrt(ui * ui + uj * uj + 0.25 * h * h);
+        double F = lba + e1_dev(b * R) - e1_dev(a * R);
+        acc += wi * wj * (0.5 * h) / (R * R * R) * F;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = 6.0 * red[0] / (4.0 * 3.14159265358979323846 * lba);
+}
+
+__global__ void h_bits(const double* h, const int32_t* perm, int64_t n, uint64_t* key, int32_t* val) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = __double_as_longlong(h[perm[i]]);
+    val[i] = (int32_t)i;
+}
+__global__ void uniq_flags(const uint64_t* key, int64_t n, int32_t* flag) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+__global__ void uniq_gather(const uint64_t* key, const int32_t* flag, const int32_t* pos, int64_t n,
+                            double* hs) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flag[i]) return;
+    hs[pos[i]] = __longlong_as_double(key[i]);
+}
+// sorted-order point k: sigma[k] = sig_u[unique index of h(perm[k])]; w[k] = h^3
+__global__ void scatter_sigma(const uint64_t* key, const int32_t* val, const int32_t* flag,
+                              const int32_t* pos, int64_t n, const double* sig_u, double* sigma,
+                              double* w) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int u = pos[i] + flag[i] - 1;
+    int k = val[i];
+    sigma[k] = sig_u[u];
+    double h = __longlong_as_double(key[i]);
+    w[k] = h * h * h;
+}
+__global__ void fill_uniform(int64_t n, double s, double h, double* sigma, double* w) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    sigma[i] = s;
+    w[i] = h * h * h;
+}
+
+int build_self_terms(Plan& p, const double* h_dev, double uh) {
+    cudaStream_t st = p.stream;
+    const int64_t n = p.tree.n;
+    const int NQ = 64;
+    DevBuf gx, gw;
+    KF_TRY(dev_alloc(gx, NQ * 8));
+    KF_TRY(dev_alloc(gw, NQ * 8));
+    gauss_legendre<<<1, NQ, 0, st>>>(NQ, ptr<double>(gx), ptr<double>(gw));
+    KF_LAUNCH();
+    KF_TRY(dev_alloc(p.sigma, n * 8));
+    KF_TRY(dev_alloc(p.w, n * 8));
+    if (!h_dev) {
+        DevBuf hb, sb;
+        KF_TRY(dev_alloc(hb, 8));
+        KF_TRY(dev_alloc(sb, 8));
+        KF_CUDA(cudaMemcpyAsync(hb.p, &uh, 8, cudaMemcpyHostToDevice, st));
+        self_sigma<<<1, 256, 0, st>>>(ptr<double>(hb), 1, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
+                                      ptr<double>(gw), ptr<double>(sb));
+        KF_LAUNCH();
+        double s = 0;
+        KF_CUDA(cudaMemcpyAsync(&s, sb.p, 8, cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        fill_uniform<<<nb(n, 256), 256, 0, st>>>(n, s, uh, ptr<double>(p.sigma), ptr<double>(p.w));
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));
+        dev_free(hb); dev_free(sb); dev_free(gx); dev_free(gw);
+        return KIFMM_OK;
+    }
+    DevBuf key, val, tk, tv, hist, flag, pos, scan_tmp, hs, su;
+    KF_TRY(dev_alloc(key, n * 8));
+    KF_TRY(dev_alloc(val, n * 4));
+    KF_TRY(dev_alloc(flag, n * 4));
+    KF_TRY(dev_alloc(pos, n * 4));
+    h_bits<<<nb(n, 256), 256, 0, st>>>(h_dev, ptr<int32_t>(p.tree.perm), n, ptr<uint64_t>(key), ptr<int32_t>(val));
+    KF_LAUNCH();
+    KF_TRY(radix_sort_pairs(ptr<uint64_t>(key), ptr<int32_t>(val), n, 64, st, tk, tv, hist));
+    uniq_flags<<<nb(n, 256), 256, 0, st>>>(ptr<uint64_t>(key), n, ptr<int32_t>(flag));
+    KF_LAUNCH();
+    int32_t nu = 0;
+    KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), n, &nu, st, scan_tmp));
+    KF_TRY(dev_alloc(hs, (size_t)nu * 8));
+    KF_TRY(dev_alloc(su, (size_t)nu * 8));
+    uniq_gather<<<nb(n, 256), 256, 0, st>>>(ptr<uint64_t>(key), ptr<int32_t>(flag), ptr<int32_t>(pos), n,
+                                            ptr<double>(hs));
+    KF_LAUNCH();
+    self_sigma<<<nu, 256, 0, st>>>(ptr<double>(hs), nu, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
+                                   ptr<double>(gw), ptr<double>(su));
+    KF_LAUNCH();
+    scatter_sigma<<<nb(n, 256), 256, 0, st>>>(ptr<uint64_t>(key), ptr<int32_t>(val), ptr<int32_t>(flag),
+                                              ptr<int32_t>(pos), n, ptr<double>(su), ptr<double>(p.sigma),
+                                              ptr<double>(p.w));
+    KF_LAUNCH();
+    KF_CUDA(cudaStreamSynchronize(st));
+    for (DevBuf* d : {&key, &val, &tk, &tv, &hist, &flag, &pos, &scan_tmp, &hs, &su, &gx, &gw}) dev_free(*d);
+    return KIFMM_OK;
+}
+
+}  // namespace kifmm

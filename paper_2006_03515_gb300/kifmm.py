@@ -1,0 +1,234 @@
+"""Python binding of libkifmm (include/kifmm.h): argument marshalling only.
+
+Every step of the computation runs in the CUDA library; this module passes
+device pointers of torch tensors (or host buffers for ``eval_host``) and maps
+status codes to exceptions. It fails loudly when the library is missing: there
+is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "_build", "libkifmm.so")
+
+KIFMM_FP64, KIFMM_MIXED = 0, 1
+KIFMM_SELF_CELL_EXACT, KIFMM_SELF_PAPER_GL2 = 0, 1
+KIFMM_F32, KIFMM_F64 = 0, 1
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
+          -5: "ERR_DUPLICATE_POINT", -6: "ERR_NONFINITE", -7: "ERR_NUMERIC"}
+PRECISION = {"fp64": KIFMM_FP64, "mixed": KIFMM_MIXED}
+SELF_MODE = {"cell_exact": KIFMM_SELF_CELL_EXACT, "paper_gl2": KIFMM_SELF_PAPER_GL2}
+
+# Absorption of O2 (Eq. (gfun)): chi_min, chi_max in 1/(cm Torr).
+CHI_MIN, CHI_MAX = 0.035, 2.0
+
+
+def absorption(p_o2):
+    """(a, b) = (chi_min p_O2, chi_max p_O2)."""
+    return CHI_MIN * p_o2, CHI_MAX * p_o2
+
+
+def scale_c(p, p_q=30.0, xi_omega_alpha=0.06):
+    """C = xi (omega/alpha) p_q / (p + p_q) of Eq. (Ifun)."""
+    return xi_omega_alpha * p_q / (p + p_q)
+
+
+class KifmmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (STATUS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
+                ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int64), ("n_boxes", ctypes.c_int64), ("n_levels", ctypes.c_int32),
+                ("surface_points", ctypes.c_int32), ("n_leaves", ctypes.c_int64),
+                ("list_len", ctypes.c_int64 * 4), ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
+                ("pinv_rank_min", ctypes.c_double), ("eval_launches", ctypes.c_int64),
+                ("p2p_pairs", ctypes.c_int64)]
+
+
+EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
+           "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
+           "kifmm_get_sigma", "kifmm_get_phase_times"]
+
+_lib = None
+
+
+def lib_path():
+    return _LIB_PATH
+
+
+def load():
+    """Loads libkifmm.so (built by ``paper_2006_03515_gb300.build``); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libkifmm.so is not built (%s); run paper_2006_03515_gb300.build.build()" % _LIB_PATH)
+    L = ctypes.CDLL(_LIB_PATH)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    L.kifmm_default_opts.argtypes = [ctypes.POINTER(_Opts)]
+    L.kifmm_default_opts.restype = None
+    L.kifmm_plan.argtypes = [ctypes.POINTER(vp), vp, i64, vp, dbl, i32, i32, dbl, dbl, ctypes.POINTER(_Opts)]
+    L.kifmm_eval.argtypes = [vp, vp, vp, i32, dbl]
+    L.kifmm_eval_host.argtypes = [vp, vp, vp, i32, dbl]
+    L.kifmm_eval_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32,
+                                   ctypes.POINTER(dbl), i32]
+    L.kifmm_destroy.argtypes = [vp]
+    L.kifmm_destroy.restype = None
+    L.kifmm_last_error.restype = ctypes.c_char_p
+    L.kifmm_get_info.argtypes = [vp, ctypes.POINTER(_Info)]
+    L.kifmm_get_tree.argtypes = [vp] + [vp] * 9
+    L.kifmm_get_list.argtypes = [vp, i32, vp, vp]
+    L.kifmm_get_sigma.argtypes = [vp, vp]
+    L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
+    for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_get_info",
+                 "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != 0:
+        raise KifmmError(rc, load().kifmm_last_error().decode())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream))
+
+
+class Plan:
+    """A KIFMM plan over fixed points (outline step 1 and the operators)."""
+
+    def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
+                 self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None):
+        import torch
+        L = load()
+        if not (isinstance(points, torch.Tensor) and points.is_cuda):
+            raise TypeError("points must be a CUDA tensor")
+        self._points = points.detach().to(torch.float64).contiguous()
+        if self._points.dim() != 2 or self._points.shape[1] != 3:
+            raise ValueError("points must be N x 3")
+        self.n = int(self._points.shape[0])
+        hp, uh = None, 0.0
+        if isinstance(h, torch.Tensor):
+            self._h = h.detach().to(device=self._points.device, dtype=torch.float64).contiguous()
+            if self._h.numel() != self.n:
+                raise ValueError("h must have N entries")
+            hp = ctypes.c_void_p(self._h.data_ptr())
+        else:
+            self._h = None
+            uh = float(h)
+        o = _Opts()
+        L.kifmm_default_opts(ctypes.byref(o))
+        o.precision = PRECISION[precision]
+        o.self_mode = SELF_MODE[self_mode]
+        o.pinv_eps = float(pinv_eps)
+        if root is not None:
+            o.has_root = 1
+            for k in range(4):
+                o.root[k] = float(root[k])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        o.stream = _stream_ptr(self.stream)
+        self.precision = precision
+        self._h_ptr = ctypes.c_void_p()
+        _check(L.kifmm_plan(ctypes.byref(self._h_ptr), ctypes.c_void_p(self._points.data_ptr()), self.n, hp, uh,
+                            int(leaf_size), int(surface_order), float(a), float(b), ctypes.byref(o)))
+
+    @property
+    def handle(self):
+        return self._h_ptr
+
+    def eval(self, I, S=None, C=1.0):
+        """S = C * (sum over the FMM + near field + self term); I: CUDA tensor (N,) f32/f64."""
+        import torch
+        if not (isinstance(I, torch.Tensor) and I.is_cuda and I.is_contiguous() and I.numel() == self.n):
+            raise TypeError("I must be a contiguous CUDA tensor with N entries")
+        dt = {torch.float64: KIFMM_F64, torch.float32: KIFMM_F32}[I.dtype]
+        if S is None:
+            S = torch.empty_like(I)
+        _check(load().kifmm_eval(self._h_ptr, ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(S.data_ptr()), dt,
+                                 float(C)))
+        return S
+
+    def eval_host(self, I, S=None, C=1.0):
+        """The same evaluation from host numpy buffers (copies inside the call)."""
+        I = np.ascontiguousarray(I)
+        dt = {np.dtype(np.float64): KIFMM_F64, np.dtype(np.float32): KIFMM_F32}[I.dtype]
+        if S is None:
+            S = np.empty_like(I)
+        _check(load().kifmm_eval_host(self._h_ptr, ctypes.c_void_p(I.ctypes.data), ctypes.c_void_p(S.ctypes.data),
+                                      dt, float(C)))
+        return S
+
+    def info(self):
+        inf = _Info()
+        _check(load().kifmm_get_info(self._h_ptr, ctypes.byref(inf)))
+        return dict(n_points=inf.n_points, n_boxes=inf.n_boxes, n_levels=inf.n_levels,
+                    surface_points=inf.surface_points, n_leaves=inf.n_leaves, list_len=list(inf.list_len),
+                    origin=list(inf.origin), side=inf.side, pinv_rank_min=int(inf.pinv_rank_min),
+                    eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs))
+
+    def tree(self):
+        inf = self.info()
+        n, nb = inf["n_points"], inf["n_boxes"]
+        out = dict(perm=np.empty(n, np.int64), keys=np.empty(n, np.uint64), level=np.empty(nb, np.int32),
+                   parent=np.empty(nb, np.int32), pstart=np.empty(nb, np.int64), pend=np.empty(nb, np.int64),
+                   leaf=np.empty(nb, np.int32), anchor=np.empty((nb, 3), np.int32),
+                   child=np.empty((nb, 8), np.int32))
+        order = ["perm", "keys", "level", "parent", "pstart", "pend", "leaf", "anchor", "child"]
+        _check(load().kifmm_get_tree(self._h_ptr, *[ctypes.c_void_p(out[k].ctypes.data) for k in order]))
+        return out
+
+    def list(self, which):
+        inf = self.info()
+        off = np.empty(inf["n_boxes"] + 1, np.int64)
+        items = np.empty(max(1, inf["list_len"][which]), np.int32)
+        _check(load().kifmm_get_list(self._h_ptr, int(which), ctypes.c_void_p(off.ctypes.data),
+                                     ctypes.c_void_p(items.ctypes.data)))
+        return off, items[:inf["list_len"][which]]
+
+    def sigma(self):
+        s = np.empty(self.n, np.float64)
+        _check(load().kifmm_get_sigma(self._h_ptr, ctypes.c_void_p(s.ctypes.data)))
+        return s
+
+    def phase_times(self):
+        ms = (ctypes.c_float * 8)()
+        k = load().kifmm_get_phase_times(self._h_ptr, ms, 8)
+        return list(ms)[:k]
+
+    def close(self):
+        if self._h_ptr:
+            load().kifmm_destroy(self._h_ptr)
+            self._h_ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def eval_batch(plans, Is, Ss, C=None, capture=False):
+    """Evaluates several plans back to back on plans[0]'s stream (optionally as one CUDA graph)."""
+    import torch
+    n = len(plans)
+    dt = {torch.float64: KIFMM_F64, torch.float32: KIFMM_F32}[Is[0].dtype]
+    ph = (ctypes.c_void_p * n)(*[p.handle.value for p in plans])
+    ip = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Is])
+    sp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Ss])
+    cc = (ctypes.c_double * n)(*([1.0] * n if C is None else [float(c) for c in C]))
+    _check(load().kifmm_eval_batch(ph, ip, sp, n, dt, cc, 1 if capture else 0))
+    return Ss

@@ -1,0 +1,85 @@
+"""The C-ABI library builds for sm_103a, loads, exports every entry point that
+include/*.h declares, and rejects bad arguments on the host (no GPU needed)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from paper_2006_03515_gb300 import build, kifmm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(hdr).read()
+        names += re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(kifmm_\w+)\s*\(", txt, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return kifmm.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(kifmm.EXPORTS) == names
+
+
+def test_default_opts(lib):
+    o = kifmm._Opts()
+    lib.kifmm_default_opts(ctypes.byref(o))
+    assert o.precision == kifmm.KIFMM_FP64
+    assert o.self_mode == kifmm.KIFMM_SELF_CELL_EXACT
+    assert o.pinv_eps == 1e-5 and o.has_root == 0 and not o.stream
+
+
+def _plan(lib, **kw):
+    args = dict(out=ctypes.byref(ctypes.c_void_p()), pts=ctypes.c_void_p(16), n=10, h=None, uh=0.1, leaf=8, m0=6,
+                a=5.0, b=300.0, opts=None)
+    args.update(kw)
+    return lib.kifmm_plan(args["out"], args["pts"], args["n"], args["h"], args["uh"], args["leaf"], args["m0"],
+                          args["a"], args["b"], args["opts"])
+
+
+@pytest.mark.parametrize("kw", [dict(out=None), dict(pts=None), dict(n=0), dict(n=-3), dict(uh=0.0),
+                                dict(uh=float("nan")), dict(leaf=0), dict(m0=2), dict(m0=13), dict(a=0.0),
+                                dict(b=4.0), dict(a=float("inf"))])
+def test_plan_rejects_bad_arguments(lib, kw):
+    assert _plan(lib, **kw) == -1
+    assert lib.kifmm_last_error().decode().startswith("kifmm_plan")
+
+
+def test_plan_rejects_bad_options(lib):
+    for field, value in [("precision", 7), ("self_mode", 3), ("pinv_eps", 0.0), ("pinv_eps", 1.5)]:
+        o = kifmm._Opts()
+        lib.kifmm_default_opts(ctypes.byref(o))
+        setattr(o, field, value)
+        assert _plan(lib, opts=ctypes.byref(o)) == -1
+    o = kifmm._Opts()
+    lib.kifmm_default_opts(ctypes.byref(o))
+    o.has_root = 1
+    o.root[3] = -1.0
+    assert _plan(lib, opts=ctypes.byref(o)) == -1
+
+
+def test_eval_rejects_null(lib):
+    assert lib.kifmm_eval(None, None, None, 1, 1.0) == -1
+    assert lib.kifmm_eval_host(None, None, None, 1, 1.0) == -1
+    assert lib.kifmm_get_info(None, None) == -1
+    lib.kifmm_destroy(None)
+
+
+def test_physics_constants():
+    # Eq. (gfun) and Eq. (Ifun) with the parameters of Sec. 4.1
+    a, b = kifmm.absorption(150.0)
+    assert a == pytest.approx(5.25, rel=1e-15) and b == 300.0
+    assert kifmm.scale_c(760.0) == pytest.approx(0.06 * 30.0 / 790.0)
