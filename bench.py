@@ -233,6 +233,7 @@ def main():
             phase_sum = ph if phase_sum is None else [x + y for x, y in zip(phase_sum, ph)]
         torch.cuda.synchronize(dev)
         clk = clocks.stop()
+        launches_per_step = plan.info()["eval_launches"]
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         ms = sum(step_ms) / len(step_ms)
         if ws > 1:
@@ -273,7 +274,7 @@ def main():
     else:
         roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
                 "traffic": None}
-    gpu_launches = info["eval_launches"] * args.steps
+    gpu_launches = launches_per_step * args.steps
     line = {"metric": "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)", "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -33,10 +33,11 @@ static void free_plan(Plan* p) {
     }
     dev_free(p->vtab);
     for (auto& o : p->ops)
-        for (DevBuf* b : {&o.uc2ue, &o.dc2de, &o.m2m, &o.l2l, &o.m2l, &o.m2l_hi, &o.m2l_lo}) dev_free(*b);
+        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.A, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32})
+            dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
-                      &p->q, &p->Isort, &p->chk, &p->phi_u, &p->phi_d, &p->phiu_hi, &p->phiu_lo, &p->chk32,
-                      &p->phid32, &p->phiu32, &p->far, &p->wleaves, &p->host_I, &p->host_S})
+                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->dd, &p->phid, &p->phiu,
+                      &p->far, &p->wleaves, &p->host_I, &p->host_S})
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes})

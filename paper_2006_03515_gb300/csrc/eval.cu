@@ -99,8 +99,7 @@ __global__ void nonempty_boxes(const int32_t* off, int64_t lo, int64_t hi, int m
     flag[b - lo] = (off[b + 1] > off[b] && level[b] >= min_level) ? 1 : 0;
 }
 
-constexpr int kM2LTile64 = 32;   // boxes per tile, FP64 M2L
-constexpr int kM2LTile32 = 64;   // boxes per tile, FP32 M2L
+constexpr int kM2LTile = 64;     // boxes per M2L tile (both precisions)
 
 // near-field pair evaluations of one evaluation: sum over leaves B of n_B * (sum_{A in U(B)} n_A) - n
 __global__ void count_p2p_pairs(const int32_t* leaves, int64_t nl, const int32_t* uoff, const int32_t* uitems,
@@ -202,12 +201,25 @@ int build_eval_data(Plan& p) {
             L.n_m2m[o] = tot;
         }
         // M2L tiles and their active offset slots
-        int tb = p.precision == KIFMM_MIXED ? kM2LTile32 : kM2LTile64;
+        int tb = kM2LTile;
         L.n_tiles = (int)((cnt + tb - 1) / tb);
         KF_TRY(dev_alloc(L.m2l_slots, (size_t)std::max(L.n_tiles, 1) * kSlotStride * 4));
         if (L.n_tiles > 0) {
             m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, ptr<int32_t>(L.m2l_slots));
             KF_LAUNCH();
+        }
+        // leaves of this level
+        select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 1, 2,
+                                                    ptr<int32_t>(flag) + lo);
+        KF_LAUNCH();
+        {
+            int32_t nlf = 0;
+            KF_TRY(device_scan_i32(ptr<int32_t>(flag) + lo, ptr<int32_t>(pos), cnt, &nlf, st, scan_tmp));
+            KF_TRY(dev_alloc(L.leafs, (size_t)std::max(nlf, 1) * 4));
+            compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag) + lo, ptr<int32_t>(pos), lo, cnt,
+                                                          ptr<int32_t>(L.leafs));
+            KF_LAUNCH();
+            L.n_leaf = nlf;
         }
         // boxes with a non-empty X list
         nonempty_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(p.lists[3].off), lo, hi, 2,
@@ -222,14 +234,22 @@ int build_eval_data(Plan& p) {
         L.n_x = tot;
     }
     // workspace
+    const int R = p.R;
+    const size_t ts = p.precision == KIFMM_MIXED ? 4 : 8;
     KF_TRY(dev_alloc(p.q, n * 8));
     KF_TRY(dev_alloc(p.Isort, n * 8));
     KF_TRY(dev_alloc(p.far, n * 8));
     KF_TRY(dev_alloc(p.chk, (size_t)nb * S * 8));
-    KF_TRY(dev_alloc(p.phi_u, (size_t)nb * S * 8));
-    KF_TRY(dev_alloc(p.phi_d, (size_t)nb * S * 8));
-    KF_CUDA(cudaMemsetAsync(p.phi_u.p, 0, (size_t)nb * S * 8, st));
-    KF_CUDA(cudaMemsetAsync(p.phi_d.p, 0, (size_t)nb * S * 8, st));
+    KF_TRY(dev_alloc(p.cu, (size_t)nb * R * 8));
+    KF_TRY(dev_alloc(p.dd, (size_t)nb * R * ts));
+    KF_TRY(dev_alloc(p.phid, (size_t)nb * S * ts));
+    KF_CUDA(cudaMemsetAsync(p.phid.p, 0, (size_t)nb * S * ts, st));
+    if (p.precision == KIFMM_MIXED) KF_TRY(dev_alloc(p.cu32, (size_t)nb * R * 4));
+    if (p.lists[3].len > 0) KF_TRY(dev_alloc(p.chkx, (size_t)nb * S * ts));
+    if (p.lists[2].len > 0) {
+        KF_TRY(dev_alloc(p.phiu, (size_t)nb * S * ts));
+        KF_CUDA(cudaMemsetAsync(p.phiu.p, 0, (size_t)nb * S * ts, st));
+    }
     KF_CUDA(cudaStreamSynchronize(st));
     dev_free(flag); dev_free(pos); dev_free(scan_tmp);
     return KIFMM_OK;
@@ -327,40 +347,43 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
     }
 }
 
-// out[dst(c)] (+)= Op (S x S, row-major) * in[src(c)] for c < count, FP64.
-// src/dst NULL means the contiguous range base + c.
+// out[dst(c)][row] (+)= sum_k Op[row][k] * in[src(c)][k] for row < Mo, k < Ki, c < count:
+// one translation matrix applied to many boxes (a GEMM whose columns are gathered and
+// scattered by box index). src/dst NULL means the contiguous range base + c.
+// Tile: 64 rows x 32 boxes, k-chunks of 16; each thread 2 rows x 4 boxes.
 constexpr int AP_TM = 64, AP_TN = 32, AP_TK = 16;
-__global__ void __launch_bounds__(256) k_apply64(const double* __restrict__ Op, int S, const int32_t* src,
-                                                 const int32_t* dst, int64_t base, int count,
-                                                 const double* __restrict__ in, double* out, int accumulate) {
-    __shared__ double As[AP_TK][AP_TM + 1];
-    __shared__ double Bs[AP_TK][AP_TN + 1];
+template <class T>
+__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int Mo, int Ki, const int32_t* src,
+                                               const int32_t* dst, int64_t base, int count,
+                                               const T* __restrict__ in, int ldi, T* out, int ldo, int accumulate) {
+    __shared__ T As[AP_TK][AP_TM + 1];
+    __shared__ T Bs[AP_TK][AP_TN + 1];
     const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
     const int row0 = blockIdx.y * AP_TM, col0 = blockIdx.x * AP_TN;
-    double acc[2][4] = {};
-    for (int k0 = 0; k0 < S; k0 += AP_TK) {
+    T acc[2][4] = {};
+    for (int k0 = 0; k0 < Ki; k0 += AP_TK) {
         for (int e = tid; e < AP_TM * AP_TK; e += 256) {
             int rr = e / AP_TK, kk = e % AP_TK;
             int row = row0 + rr, k = k0 + kk;
-            As[kk][rr] = (row < S && k < S) ? Op[(int64_t)row * S + k] : 0.0;
+            As[kk][rr] = (row < Mo && k < Ki) ? Op[(int64_t)row * Ki + k] : T(0);
         }
         for (int e = tid; e < AP_TN * AP_TK; e += 256) {
             int cc = e / AP_TK, kk = e % AP_TK;
             int col = col0 + cc, k = k0 + kk;
-            double v = 0.0;
-            if (col < count && k < S) {
+            T v = T(0);
+            if (col < count && k < Ki) {
                 int64_t b = src ? src[col] : base + col;
-                v = in[b * S + k];
+                v = in[b * ldi + k];
             }
             Bs[kk][cc] = v;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < AP_TK; ++kk) {
-            double a0 = As[kk][ty], a1 = As[kk][ty + 32];
+            T a0 = As[kk][ty], a1 = As[kk][ty + 32];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                double bv = Bs[kk][tx + 8 * j];
+                T bv = Bs[kk][tx + 8 * j];
                 acc[0][j] += a0 * bv;
                 acc[1][j] += a1 * bv;
             }
@@ -370,151 +393,103 @@ __global__ void __launch_bounds__(256) k_apply64(const double* __restrict__ Op, 
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
         int row = row0 + ty + 32 * i;
-        if (row >= S) continue;
+        if (row >= Mo) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int col = col0 + tx + 8 * j;
             if (col >= count) continue;
             int64_t b = dst ? dst[col] : base + col;
-            double* o = out + b * S + row;
+            T* o = out + b * ldo + row;
             *o = accumulate ? *o + acc[i][j] : acc[i][j];
         }
     }
 }
 
-// M2L (Eq. (m2l)), FP64: chk[B] = sum over V(B) of M2L[slot] * phi_u[A], per tile of
-// kM2LTile64 consecutive boxes of one level; every output is owned by one block.
-__global__ void __launch_bounds__(256) k_m2l64(const double* __restrict__ M, int S, const int32_t* vtab,
-                                               const int32_t* slots, int64_t lo, int64_t hi,
-                                               const double* __restrict__ phi, double* chk) {
-    __shared__ double As[AP_TK][AP_TM + 1];
-    __shared__ double Bs[AP_TK][AP_TN + 1];
-    __shared__ int src[AP_TN];
-    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-    const int row0 = blockIdx.y * AP_TM;
-    const int64_t b0 = lo + (int64_t)blockIdx.x * AP_TN;
-    const int32_t* sl = slots + (int64_t)blockIdx.x * kSlotStride;
-    const int ns = sl[0];
-    const int64_t SS = (int64_t)S * S;
-    double acc[2][4] = {};
-    for (int si = 0; si < ns; ++si) {
-        const int slot = sl[1 + si];
-        __syncthreads();
-        if (tid < AP_TN) {
-            int64_t b = b0 + tid;
-            src[tid] = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
-        }
-        const double* Op = M + slot * SS;
-        for (int k0 = 0; k0 < S; k0 += AP_TK) {
-            __syncthreads();
-            for (int e = tid; e < AP_TM * AP_TK; e += 256) {
-                int rr = e / AP_TK, kk = e % AP_TK;
-                int row = row0 + rr, k = k0 + kk;
-                As[kk][rr] = (row < S && k < S) ? Op[(int64_t)row * S + k] : 0.0;
-            }
-            for (int e = tid; e < AP_TN * AP_TK; e += 256) {
-                int cc = e / AP_TK, kk = e % AP_TK;
-                int k = k0 + kk;
-                int a = src[cc];
-                Bs[kk][cc] = (a >= 0 && k < S) ? phi[(int64_t)a * S + k] : 0.0;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int kk = 0; kk < AP_TK; ++kk) {
-                double a0 = As[kk][ty], a1 = As[kk][ty + 32];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    double bv = Bs[kk][tx + 8 * j];
-                    acc[0][j] += a0 * bv;
-                    acc[1][j] += a1 * bv;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        int row = row0 + ty + 32 * i;
-        if (row >= S) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int64_t b = b0 + tx + 8 * j;
-            if (b >= hi) continue;
-            chk[b * S + row] = acc[i][j];
-        }
-    }
-}
-
-// M2L, mixed path, FP32 SIMT: FP32 matrices (row stride Sk, zero padded) times the
-// FP32-rounded upward densities, FP32 accumulation; the result goes to the FP64 check
-// potential. Tile: 64 rows x 64 boxes, k-chunks of 32; 4x4 outputs per thread.
-constexpr int M32_TM = 64, M32_TN = 64, M32_TK = 32;
-__global__ void __launch_bounds__(256) k_m2l32(const float* __restrict__ M, int S, int Sk, const int32_t* vtab,
-                                               const int32_t* slots, int64_t lo, int64_t hi,
-                                               const double* __restrict__ phi, double* chk) {
-    __shared__ __align__(16) float As[M32_TK][M32_TM];
-    __shared__ __align__(16) float Bs[M32_TK][M32_TN];
-    __shared__ int src[M32_TN];
+// M2L (Eq. (m2l)) in coefficients: d[B] = sum over V(B) of T[slot] c[A], for a tile of
+// M2L_TN consecutive boxes of one level, looping over the tile's active offset slots;
+// every output belongs to one block. T is [343][R][R] (zero padded), c and d are [nb][R].
+// Tile: 64 rows x 64 boxes, k-chunks of 32 (R is a multiple of 32), each thread 4 x 4
+// outputs; the next chunk is fetched into registers while the current one is used.
+constexpr int M2L_TM = 64, M2L_TN = kM2LTile, M2L_TK = 32;
+template <class T>
+__global__ void __launch_bounds__(256) k_m2l(const T* __restrict__ Tm, int R, const int32_t* vtab,
+                                             const int32_t* slots, int64_t lo, int64_t hi,
+                                             const T* __restrict__ c, T* d) {
+    __shared__ T As[M2L_TK][M2L_TM + 1];
+    __shared__ T Bs[M2L_TK][M2L_TN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int row0 = blockIdx.y * M32_TM;
-    const int64_t b0 = lo + (int64_t)blockIdx.x * M32_TN;
+    const int row0 = blockIdx.y * M2L_TM;
+    const int64_t b0 = lo + (int64_t)blockIdx.x * M2L_TN;
     const int32_t* sl = slots + (int64_t)blockIdx.x * kSlotStride;
     const int ns = sl[0];
-    const int64_t per = (int64_t)Sk * Sk;   // rows and columns padded to Sk
-    float acc[4][4] = {};
-    for (int si = 0; si < ns; ++si) {
+    const int64_t RR = (int64_t)R * R;
+    const int nk = R / M2L_TK;
+    const int nsteps = ns * nk;
+    // each thread moves 8 elements of A and 8 of B per chunk: element e = tid + 256 i
+    T ra[8], rb[8];
+    auto fetch = [&](int step) {
+        const int si = step / nk, k0 = (step % nk) * M2L_TK;
         const int slot = sl[1 + si];
-        __syncthreads();
-        if (tid < M32_TN) {
-            int64_t b = b0 + tid;
-            src[tid] = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
+        const T* Op = Tm + (int64_t)slot * RR;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int e = tid + 256 * i;
+            int rr = e / M2L_TK, kk = e % M2L_TK;   // rr < 64: matrix row, and box column for B
+            int row = row0 + rr;
+            ra[i] = (row < R) ? Op[(int64_t)row * R + k0 + kk] : T(0);
+            int64_t b = b0 + rr;
+            int a = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
+            rb[i] = (a >= 0) ? c[(int64_t)a * R + k0 + kk] : T(0);
         }
-        const float* Op = M + slot * per;
-        for (int k0 = 0; k0 < Sk; k0 += M32_TK) {
-            __syncthreads();
-            for (int e = tid; e < M32_TM * M32_TK; e += 256) {
-                int rr = e / M32_TK, kk = e % M32_TK;
-                int row = row0 + rr;
-                As[kk][rr] = (row < S) ? Op[(int64_t)row * Sk + k0 + kk] : 0.f;
-            }
-            for (int e = tid; e < M32_TN * M32_TK; e += 256) {
-                int cc = e / M32_TK, kk = e % M32_TK;
-                int k = k0 + kk;
-                int a = src[cc];
-                Bs[kk][cc] = (a >= 0 && k < S) ? (float)phi[(int64_t)a * S + k] : 0.f;
-            }
-            __syncthreads();
+    };
+    T acc[4][4] = {};
+    if (nsteps > 0) fetch(0);
+    for (int step = 0; step < nsteps; ++step) {
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            int e = tid + 256 * i;
+            As[e % M2L_TK][e / M2L_TK] = ra[i];
+            Bs[e % M2L_TK][e / M2L_TK] = rb[i];
+        }
+        __syncthreads();
+        if (step + 1 < nsteps) fetch(step + 1);
 #pragma unroll 8
-            for (int kk = 0; kk < M32_TK; ++kk) {
-                float av[4], bv[4];
+        for (int kk = 0; kk < M2L_TK; ++kk) {
+            T av[4], bv[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-            }
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
         }
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         int row = row0 + ty + 16 * i;
-        if (row >= S) continue;
+        if (row >= R) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int64_t b = b0 + tx + 16 * j;
             if (b >= hi) continue;
-            chk[b * S + row] = (double)acc[i][j];
+            d[b * R + row] = acc[i][j];
         }
     }
 }
 
+__global__ void k_to_f32(const double* in, float* out, int64_t n) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) out[e] = (float)in[e];
+}
+
 // S2L for the X list: downward check potential of B (x_j = c_B + 1.2 r_B s_j) from the
 // sources of every leaf A in X(B). One block per box.
-template <bool MIXED>
+template <bool MIXED, class TC>
 __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxes, const int32_t* xoff,
-                                               const int32_t* xitems, const double* q, double* chk) {
+                                               const int32_t* xitems, const double* q, TC* chk) {
     const int B = boxes[blockIdx.x];
     const int S = E.S;
     const double r = half_width(E, E.level[B]);
@@ -559,7 +534,7 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
                 }
             }
         }
-        if (j < S) chk[(int64_t)B * S + j] += MIXED ? acc32.value() : acc64;
+        if (j < S) chk[(int64_t)B * S + j] = (TC)(MIXED ? acc32.value() : acc64);
     }
 }
 
@@ -567,10 +542,10 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
 // and the W list (y = c_A + 1.2 r_A s_k, density phi_u). One block per leaf, one thread
 // per target point. Writes far[i] for every point of the leaf.
 constexpr int L2P_T = 64;
-template <bool MIXED>
+template <bool MIXED, class TD>
 __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves, const int32_t* woff,
-                                             const int32_t* witems, const double* phi_d,
-                                             const double* phi_u, double* far) {
+                                             const int32_t* witems, const TD* phi_d,
+                                             const TD* phi_u, double* far) {
     const int B = leaves[blockIdx.x];
     const int S = E.S;
     const int lev = E.level[B];
@@ -591,7 +566,7 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
         for (int li = 0; li < nsrc_lists; ++li) {
             int A;
             double rad;
-            const double* dens;
+            const TD* dens;
             if (li == 0) {
                 if (lev < 2) continue;
                 A = B;
@@ -610,7 +585,7 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
                 for (int e = threadIdx.x; e < ns; e += L2P_T) {
                     const double* sv = E.surf + 3 * (s0 + e);
                     double y0 = d[0] + rad * sv[0], y1 = d[1] + rad * sv[1], y2 = d[2] + rad * sv[2];
-                    double ph = dens[(int64_t)A * S + s0 + e];
+                    double ph = (double)dens[(int64_t)A * S + s0 + e];
                     if (MIXED) s32[e] = make_float4((float)y0, (float)y1, (float)y2, (float)ph);
                     else {
                         s64[e][0] = y0; s64[e][1] = y1; s64[e][2] = y2; s64[e][3] = ph;
@@ -754,17 +729,124 @@ static void mark(Plan& p, int k) {
     if (p.timing) cudaEventRecord(p.ev[k], p.stream);
 }
 
+template <class T> static const T* sel(const DevBuf& d64, const DevBuf& d32);
+template <> const double* sel<double>(const DevBuf& d64, const DevBuf&) { return ptr<double>(d64); }
+template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return ptr<float>(d32); }
+
+template <class T>
+static int launch_apply(cudaStream_t st, const T* Op, int Mo, int Ki, const int32_t* src, const int32_t* dst,
+                        int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc) {
+    if (count <= 0) return KIFMM_OK;
+    dim3 g(nbk(count, AP_TN), nbk(Mo, AP_TM));
+    k_apply<T><<<g, 256, 0, st>>>(Op, Mo, Ki, src, dst, base, count, in, ldi, out, ldo, acc);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+// Far field: upward pass (FP64 in both forms), M2L, downward pass and the leaves'
+// downward equivalent densities, in type T (FP64 form: double; mixed form: float).
+template <class T>
+static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
+    Tree& t = p.tree;
+    cudaStream_t st = p.stream;
+    const int S = p.S, R = p.R, L = t.nlevels;
+    const bool mixed = p.precision == KIFMM_MIXED;
+    double* cu = ptr<double>(p.cu);
+    T* dd = ptr<T>(p.dd);
+    T* phid = ptr<T>(p.phid);
+#define RUN(x)     \
+    do {           \
+        KF_TRY(x); \
+        ++nl;      \
+    } while (0)
+    // ---- upward: S2M check potentials, c = Sigma^+ U^T chk (Eq. (s2m)), then M2M (Eq. (m2m))
+    KF_CUDA(cudaMemsetAsync(cu, 0, (size_t)t.nboxes * R * 8, st));
+    if (p.n_p2m > 0) {
+        if (mixed) k_p2m<true><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
+        else k_p2m<false><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
+        KF_LAUNCH();
+        ++nl;
+    }
+    for (int l = 2; l < L; ++l) {
+        auto& LL = p.lv[l];
+        if (LL.n_leaf > 0)
+            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), R, S, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs),
+                                     0, LL.n_leaf, ptr<double>(p.chk), S, cu, R, 0));
+    }
+    mark(p, 2);
+    for (int l = L - 2; l >= 2; --l) {
+        auto& LL = p.lv[l];
+        for (int o = 0; o < 8; ++o)
+            if (LL.n_m2m[o] > 0)
+                RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A) + (int64_t)o * R * R, R, R,
+                                         ptr<int32_t>(LL.m2m_src[o]), ptr<int32_t>(LL.m2m_dst[o]), 0, LL.n_m2m[o], cu,
+                                         R, cu, R, 1));
+    }
+    mark(p, 3);
+    // ---- M2L in coefficients (Eq. (m2l))
+    const T* c = nullptr;
+    if (mixed) {
+        int64_t m = (int64_t)t.nboxes * R;
+        k_to_f32<<<nbk(m, 256), 256, 0, st>>>(cu, ptr<float>(p.cu32), m);
+        KF_LAUNCH();
+        ++nl;
+        c = reinterpret_cast<const T*>(ptr<float>(p.cu32));
+    } else {
+        c = reinterpret_cast<const T*>(cu);
+    }
+    for (int l = 2; l < L; ++l) {
+        auto& LL = p.lv[l];
+        if (LL.n_tiles == 0) continue;
+        dim3 g(LL.n_tiles, nbk(R, M2L_TM));
+        k_m2l<T><<<g, 256, 0, st>>>(sel<T>(p.ops[l].T, p.ops[l].T32), R, ptr<int32_t>(p.vtab),
+                                    ptr<int32_t>(LL.m2l_slots), t.level_start[l], t.level_start[l + 1], c, dd);
+        KF_LAUNCH();
+        ++nl;
+    }
+    mark(p, 4);
+    // ---- downward: S2L from the X list, L2L (Eq. (l2l)), then phi^d = U Sigma^+ d (Eq. (s2l))
+    for (int l = 2; l < L; ++l) {
+        auto& LL = p.lv[l];
+        const LevelOps& op = p.ops[l];
+        if (LL.n_x > 0) {
+            k_s2l_x<(sizeof(T) == 4), T><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
+                                                                  ptr<int32_t>(p.lists[3].items), ptr<double>(p.q),
+                                                                  ptr<T>(p.chkx));
+            KF_LAUNCH();
+            ++nl;
+            RUN(launch_apply<T>(st, sel<T>(op.Vt, op.Vt32), R, S, ptr<int32_t>(LL.xboxes), ptr<int32_t>(LL.xboxes), 0,
+                                LL.n_x, ptr<T>(p.chkx), S, dd, R, 1));
+        }
+        if (l >= 3) {
+            auto& LP = p.lv[l - 1];
+            const LevelOps& pop = p.ops[l - 1];
+            for (int o = 0; o < 8; ++o)
+                if (LP.n_m2m[o] > 0)
+                    RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32) + (int64_t)o * R * R, R, R,
+                                        ptr<int32_t>(LP.m2m_dst[o]), ptr<int32_t>(LP.m2m_src[o]), 0, LP.n_m2m[o], dd,
+                                        R, dd, R, 1));
+        }
+        if (LL.n_leaf > 0)
+            RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), S, R, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
+                                LL.n_leaf, dd, R, phid, S, 0));
+    }
+    // upward equivalent densities phi^u = V c for the W list
+    if (p.phiu.p) {
+        for (int l = 2; l < L; ++l) {
+            const LevelOps& op = p.ops[l];
+            RUN(launch_apply<T>(st, sel<T>(op.Vb, op.Vb32), S, R, nullptr, nullptr, t.level_start[l],
+                                (int)(t.level_start[l + 1] - t.level_start[l]), c, R, ptr<T>(p.phiu), S, 0));
+        }
+    }
+#undef RUN
+    return KIFMM_OK;
+}
+
 int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     int64_t nl = 0;   // kernels launched by this evaluation
-#define EV_LAUNCH() \
-    do {             \
-        KF_LAUNCH(); \
-        ++nl;        \
-    } while (0)
     Tree& t = p.tree;
     cudaStream_t st = p.stream;
     const int64_t n = t.n;
-    const int S = p.S;
     const bool mixed = p.precision == KIFMM_MIXED;
     EvalView E = make_view(p);
     mark(p, 0);
@@ -774,101 +856,28 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     else
         k_scatter_q<float><<<nbk(n, 256), 256, 0, st>>>((const float*)I, ptr<int32_t>(t.perm), ptr<double>(p.w),
                                                         n, ptr<double>(p.Isort), ptr<double>(p.q));
-    EV_LAUNCH();
+    KF_LAUNCH();
+    ++nl;
     mark(p, 1);
-    const int L = t.nlevels;
-    double* chk = ptr<double>(p.chk);
-    double* phu = ptr<double>(p.phi_u);
-    double* phd = ptr<double>(p.phi_d);
-    if (L > 2) {
-        // ---- upward pass: S2M at the leaves, then M2M and the check-to-equivalent solve
-        int64_t lo2 = t.level_start[2];
-        KF_CUDA(cudaMemsetAsync(chk + lo2 * S, 0, (size_t)(t.nboxes - lo2) * S * 8, st));
-        if (p.n_p2m > 0) {
-            if (mixed) k_p2m<true><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), chk);
-            else k_p2m<false><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), chk);
-            EV_LAUNCH();
-        }
-        mark(p, 2);
-        for (int l = L - 1; l >= 2; --l) {
-            auto& LL = p.lv[l];
-            const LevelOps& op = p.ops[l];
-            if (l + 1 < L) {
-                for (int o = 0; o < 8; ++o) {
-                    if (LL.n_m2m[o] == 0) continue;
-                    dim3 g(nbk(LL.n_m2m[o], AP_TN), nbk(S, AP_TM));
-                    k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.m2m) + (int64_t)o * S * S, S,
-                                                 ptr<int32_t>(LL.m2m_src[o]), ptr<int32_t>(LL.m2m_dst[o]), 0,
-                                                 LL.n_m2m[o], phu, chk, 1);
-                    EV_LAUNCH();
-                }
-            }
-            dim3 g(nbk(LL.n_all, AP_TN), nbk(S, AP_TM));
-            k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.uc2ue), S, nullptr, nullptr, t.level_start[l], LL.n_all,
-                                         chk, phu, 0);
-            EV_LAUNCH();
-        }
-        mark(p, 3);
-        // ---- downward pass
-        for (int l = 2; l < L; ++l) {
-            auto& LL = p.lv[l];
-            const LevelOps& op = p.ops[l];
-            int64_t lo = t.level_start[l], hi = t.level_start[l + 1];
-            if (LL.n_tiles > 0) {
-                if (mixed) {
-                    dim3 g(LL.n_tiles, nbk(S, M32_TM));
-                    k_m2l32<<<g, 256, 0, st>>>(ptr<float>(op.m2l_hi), S, p.Sp, ptr<int32_t>(p.vtab),
-                                               ptr<int32_t>(LL.m2l_slots), lo, hi, phu, chk);
-                } else {
-                    dim3 g(LL.n_tiles, nbk(S, AP_TM));
-                    k_m2l64<<<g, 256, 0, st>>>(ptr<double>(op.m2l), S, ptr<int32_t>(p.vtab),
-                                               ptr<int32_t>(LL.m2l_slots), lo, hi, phu, chk);
-                }
-                EV_LAUNCH();
-            }
-        }
-        mark(p, 4);
-        for (int l = 2; l < L; ++l) {
-            auto& LL = p.lv[l];
-            const LevelOps& op = p.ops[l];
-            if (LL.n_x > 0) {
-                if (mixed) k_s2l_x<true><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
-                                                                  ptr<int32_t>(p.lists[3].items), ptr<double>(p.q), chk);
-                else k_s2l_x<false><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
-                                                              ptr<int32_t>(p.lists[3].items), ptr<double>(p.q), chk);
-                EV_LAUNCH();
-            }
-            if (l >= 3) {   // L2L from the parents at level l - 1
-                auto& LP = p.lv[l - 1];
-                const LevelOps& pop = p.ops[l - 1];
-                for (int o = 0; o < 8; ++o) {
-                    if (LP.n_m2m[o] == 0) continue;
-                    dim3 g(nbk(LP.n_m2m[o], AP_TN), nbk(S, AP_TM));
-                    // src = parent (dst list of M2M), dst = child (src list of M2M)
-                    k_apply64<<<g, 256, 0, st>>>(ptr<double>(pop.l2l) + (int64_t)o * S * S, S,
-                                                 ptr<int32_t>(LP.m2m_dst[o]), ptr<int32_t>(LP.m2m_src[o]), 0,
-                                                 LP.n_m2m[o], phd, chk, 1);
-                    EV_LAUNCH();
-                }
-            }
-            dim3 g(nbk(LL.n_all, AP_TN), nbk(S, AP_TM));
-            k_apply64<<<g, 256, 0, st>>>(ptr<double>(op.dc2de), S, nullptr, nullptr, t.level_start[l], LL.n_all,
-                                         chk, phd, 0);
-            EV_LAUNCH();
-        }
+    if (t.nlevels > 2) {
+        if (mixed) KF_TRY(run_far<float>(p, E, nl));
+        else KF_TRY(run_far<double>(p, E, nl));
     } else {
         mark(p, 2);
         mark(p, 3);
         mark(p, 4);
     }
     mark(p, 5);
-    // ---- targets
+    // ---- targets: local expansion and W list, then the near field, self term and output
     if (p.nleaves > 0) {
-        if (mixed) k_l2p<true><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<int32_t>(p.lists[2].off),
-                                                                     ptr<int32_t>(p.lists[2].items), phd, phu, ptr<double>(p.far));
-        else k_l2p<false><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<int32_t>(p.lists[2].off),
-                                                                 ptr<int32_t>(p.lists[2].items), phd, phu, ptr<double>(p.far));
-        EV_LAUNCH();
+        const int32_t* wo = ptr<int32_t>(p.lists[2].off);
+        const int32_t* wi = ptr<int32_t>(p.lists[2].items);
+        if (mixed) k_l2p<true, float><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),
+                                                                            ptr<float>(p.phiu), ptr<double>(p.far));
+        else k_l2p<false, double><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<double>(p.phid),
+                                                                         ptr<double>(p.phiu), ptr<double>(p.far));
+        KF_LAUNCH();
+        ++nl;
     }
     mark(p, 6);
     {
@@ -891,11 +900,11 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
                 k_p2p<false, float><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
                                                             ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (float*)S_out);
         }
-        EV_LAUNCH();
+        KF_LAUNCH();
+        ++nl;
     }
     mark(p, 7);
     p.eval_launches = nl;
-#undef EV_LAUNCH
     return KIFMM_OK;
 }
 

@@ -84,14 +84,17 @@ struct Csr {
 struct LevelOps {
     int level = 0;
     double r = 0;        // box half-width
-    int rank = 0;        // kept rank of the pseudo-inverse
-    DevBuf uc2ue;        // f64[S*S]  pinv(K(x^{u}, y^{u})): upward check -> equivalent
-    DevBuf dc2de;        // f64[S*S]  pinv(K(x^{d}, y^{d})): downward check -> equivalent
-    DevBuf m2m;          // f64[8*S*S] K(x^{P,u}, y^{C_o,u}), this level = parent level
-    DevBuf l2l;          // f64[8*S*S] K(x^{C_o,d}, y^{P,d}), this level = parent level
-    DevBuf m2l;          // f64[343*S*S] K(x^{B,d}, y^{A,u}), c_A - c_B = 2 r delta
-    DevBuf m2l_hi;       // f32[343*Sp*Sp] TF32-rounded high part (mixed), K-padded
-    DevBuf m2l_lo;       // f32[343*Sp*Sp] residual low part (mixed)
+    int rank = 0;        // kept rank r of the truncated SVD of K(x^{B,u}, y^{B,u})
+    // FP64 basis matrices, R = padded coefficient count (zero beyond the rank)
+    DevBuf G1;           // [R][S] Sigma^+ U^T: upward check potential -> coefficients c
+    DevBuf Vb;           // [S][R] V: coefficients c -> upward equivalent density
+    DevBuf Ub;           // [S][R] U Sigma^+: coefficients d -> downward equivalent density
+    DevBuf Vt;           // [R][S] V^T: downward check potential -> coefficients d
+    DevBuf T;            // [343][R][R] M2L in coefficients, V^T K(x^{B,d}, y^{A,u}) V
+    DevBuf A;            // [8][R][R] M2M in coefficients, parent level = this level
+    DevBuf Lo;           // [8][R][R] L2L in coefficients, parent level = this level
+    // FP32 copies (mixed form)
+    DevBuf T32, Ub32, Vb32, Vt32, Lo32;
 };
 
 struct Plan {
@@ -100,7 +103,7 @@ struct Plan {
     double pinv_eps = 1e-5;
     cudaStream_t stream = nullptr;
     double a = 0, b = 0;
-    int m0 = 6, S = 152, Sp = 152;
+    int m0 = 6, S = 152, Sp = 152, R = 32;   // R: padded coefficient count
     int leaf_size = 64;
     Tree tree;
     Csr lists[4];                 // U, V, W, X
@@ -118,17 +121,16 @@ struct Plan {
     int64_t nleaves = 0;
     DevBuf p2m_boxes;      // i32: leaves of level >= 2
     int64_t n_p2m = 0;
-    // eval workspace
+    // eval workspace (T = f64 in the FP64 form, f32 in the mixed form)
     DevBuf q;          // f64[n]  I*h^3 (sorted)
     DevBuf Isort;      // f64[n]
-    DevBuf chk;        // f64[nb*S] check potentials (up and down share)
-    DevBuf phi_u;      // f64[nb*S]
-    DevBuf phi_d;      // f64[nb*S]
-    DevBuf phiu_hi;    // f32[nb*Sp] (mixed)
-    DevBuf phiu_lo;    // f32[nb*Sp]
-    DevBuf chk32;      // f32[nb*Sp] M2L output (mixed)
-    DevBuf phid32;     // f32[nb*S]  (mixed) downward density in FP32 for L2P
-    DevBuf phiu32;     // f32[nb*S]  (mixed) upward density in FP32 for M2P
+    DevBuf chk;        // f64[nb*S] upward check potentials of the leaves (S2M)
+    DevBuf chkx;       // T[nb*S]  downward check potentials from the X list (S2L)
+    DevBuf cu;         // f64[nb*R] upward coefficients c
+    DevBuf cu32;       // f32[nb*R] (mixed) FP32 copy of c for M2L and the W list
+    DevBuf dd;         // T[nb*R]  downward coefficients d
+    DevBuf phid;       // T[nb*S]  downward equivalent densities of the leaves
+    DevBuf phiu;       // T[nb*S]  upward equivalent densities (only when W lists exist)
     DevBuf far;        // f64[n] far-field part at the sorted points
     DevBuf host_I;     // staging for kifmm_eval_host (n * 8 bytes each)
     DevBuf host_S;

@@ -134,23 +134,30 @@ __global__ void svd_sigma(const double* Aall, int S, double eps, double* sig_all
     }
 }
 
-// Truncated pseudo-inverse, row-major: P[j*S + i] = sum_k V[j][k] U[i][k] / sigma_k,
-// with U[i][k] = A[i][k] / sigma_k (A holds U Sigma). T = transposed output (P^T).
-__global__ void svd_pinv(const double* Aall, const double* Vall, const double* sig_all, int S,
-                         double* P, double* PT) {
-    const double* A = Aall + (int64_t)blockIdx.y * S * S;
-    const double* V = Vall + (int64_t)blockIdx.y * S * S;
-    const double* sig = sig_all + (int64_t)blockIdx.y * S;
+// Basis matrices of the truncated SVD A_l = K(x^{B,u}, y^{B,u}) = U Sigma V^T (kept columns
+// listed in idx, r of them), padded with zeros to R coefficients:
+//   G1 = Sigma^+ U^T (R x S)  upward check potential -> coefficients c   (phi^u = V c)
+//   Vb = V           (S x R)  coefficients -> upward equivalent density
+//   Ub = U Sigma^+   (S x R)  coefficients d -> downward equivalent density (phi^d = Ub d)
+//   Vt = V^T         (R x S)  downward check potential -> coefficients d
+// The downward system K(x^{B,d}, y^{B,d}) is A_l^T (the surfaces swap roles and K is
+// symmetric), so its truncated pseudo-inverse is U Sigma^+ V^T = Ub Vt.
+__global__ void svd_basis(const double* Acol, const double* Vcol, const double* sig, const int* idx, int r,
+                          int S, int R, double* G1, double* Vb, double* Ub, double* Vt) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)S * S) return;
-    int j = (int)(e / S), i = (int)(e % S);
-    double acc = 0;
-    for (int k = 0; k < S; ++k) {
+    if (e >= (int64_t)S * R) return;
+    int i = (int)(e / R), j = (int)(e % R);   // i < S, j < R
+    double vb = 0, ub = 0;
+    if (j < r) {
+        int k = idx[j];
         double s = sig[k];
-        if (s > 0.0) acc += V[(int64_t)k * S + j] * A[(int64_t)k * S + i] / (s * s);
+        vb = Vcol[(int64_t)k * S + i];
+        ub = Acol[(int64_t)k * S + i] / (s * s);
     }
-    P[(int64_t)blockIdx.y * S * S + e] = acc;
-    PT[(int64_t)blockIdx.y * S * S + (int64_t)i * S + j] = acc;
+    Vb[(int64_t)i * R + j] = vb;
+    Ub[(int64_t)i * R + j] = ub;
+    G1[(int64_t)j * S + i] = ub;
+    Vt[(int64_t)j * S + i] = vb;
 }
 
 __global__ void transpose_to_colmajor(const double* in, double* out, int S, int nmat) {
@@ -162,19 +169,49 @@ __global__ void transpose_to_colmajor(const double* in, double* out, int S, int 
     out[m * S * S + (int64_t)j * S + i] = in[e];
 }
 
-// M2L matrices for the mixed path in FP32, rows and columns padded to Sp with zeros.
-__global__ void split_m2l(const double* m2l, int S, int Sp, float* hi, float* lo) {
+// Batched FP64 GEMM for the plan: C[b] = A[b] (M x K) * B[b] (K x N), row-major,
+// batch strides sA/sB/sC (sA = 0 or sB = 0 shares a factor). 16 x 16 tiles.
+__global__ void gemm64_batched(int M, int N, int K, const double* A, int lda, int64_t sA, const double* B,
+                               int ldb, int64_t sB, double* C, int ldc, int64_t sC) {
+    __shared__ double As[16][17], Bs[16][17];
+    const double* a = A + blockIdx.z * sA;
+    const double* b = B + blockIdx.z * sB;
+    double* c = C + blockIdx.z * sC;
+    int row = blockIdx.y * 16 + threadIdx.y, col = blockIdx.x * 16 + threadIdx.x;
+    double acc = 0;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        int ka = k0 + threadIdx.x, kb = k0 + threadIdx.y;
+        As[threadIdx.y][threadIdx.x] = (row < M && ka < K) ? a[(int64_t)row * lda + ka] : 0.0;
+        Bs[threadIdx.y][threadIdx.x] = (kb < K && col < N) ? b[(int64_t)kb * ldb + col] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc += As[threadIdx.y][k] * Bs[k][threadIdx.x];
+        __syncthreads();
+    }
+    if (row < M && col < N) c[(int64_t)row * ldc + col] = acc;
+}
+
+__global__ void to_f32(const double* in, float* out, int64_t n) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t per = (int64_t)Sp * Sp;
-    if (e >= per * kOffsetSlots) return;
-    int64_t slot = e / per;
-    int i = (int)((e % per) / Sp), j = (int)(e % Sp);
-    double v = (i < S && j < S) ? m2l[slot * S * S + (int64_t)i * S + j] : 0.0;
-    hi[e] = (float)v;
-    if (lo) lo[e] = (float)(v - (double)(float)v);
+    if (e < n) out[e] = (float)in[e];
 }
 
 static inline unsigned nb(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+static int gemm64(cudaStream_t st, int M, int N, int K, const double* A, int lda, int64_t sA, const double* B,
+                  int ldb, int64_t sB, double* C, int ldc, int64_t sC, int batch) {
+    dim3 g(nb(N, 16), nb(M, 16), batch);
+    gemm64_batched<<<g, dim3(16, 16), 0, st>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+static int f32_copy(cudaStream_t st, const DevBuf& src, DevBuf& dst, int64_t n) {
+    KF_TRY(dev_alloc(dst, n * 4));
+    to_f32<<<nb(n, 256), 256, 0, st>>>(ptr<double>(src), ptr<float>(dst), n);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
 
 int build_operators(Plan& p) {
     cudaStream_t st = p.stream;
@@ -186,66 +223,79 @@ int build_operators(Plan& p) {
     KF_LAUNCH();
     p.ops.clear();
     p.ops.resize(std::max(L, 1));
+    p.R = 32;
     if (L <= 2) return KIFMM_OK;   // no box has a far field
 
     const int nlev = L - 2;        // levels 2 .. L-1
     const int64_t SS = (int64_t)S * S;
-    DevBuf A, V, sig, rank, conv, shifts, P, PT;
+    DevBuf A, V, sig, rank, conv, shifts, tmp, z, idxb;
     KF_TRY(dev_alloc(A, nlev * SS * 8));
     KF_TRY(dev_alloc(V, nlev * SS * 8));
     KF_TRY(dev_alloc(sig, nlev * S * 8));
     KF_TRY(dev_alloc(rank, nlev * 4));
     KF_TRY(dev_alloc(conv, nlev * 4));
-    KF_TRY(dev_alloc(P, nlev * SS * 8));
-    KF_TRY(dev_alloc(PT, nlev * SS * 8));
     KF_TRY(dev_alloc(shifts, kOffsetSlots * 3 * 8));
-    double zero3[3] = {0, 0, 0};
-    DevBuf z;
+    KF_TRY(dev_alloc(tmp, SS * 8));
     KF_TRY(dev_alloc(z, 3 * 8));
+    KF_TRY(dev_alloc(idxb, S * 4));
+    double zero3[3] = {0, 0, 0};
     KF_CUDA(cudaMemcpyAsync(z.p, zero3, 24, cudaMemcpyHostToDevice, st));
-    // upward check-to-equivalent systems K(x^{B,u}, y^{B,u}) for every level
+    // ---- upward check-to-equivalent systems K(x^{B,u}, y^{B,u}) and their SVDs
     for (int l = 2; l < L; ++l) {
         double r = p.tree.side / (double)(2ll << l);
         p.ops[l].level = l;
         p.ops[l].r = r;
-        DevBuf tmp;
-        KF_TRY(dev_alloc(tmp, SS * 8));
-        surface_kmat<<<dim3(nb(SS, 256), 1), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r,
-                                                           kRInner * r, ptr<double>(z), kp,
-                                                           ptr<double>(tmp), SS);
+        surface_kmat<<<dim3(nb(SS, 256), 1), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * r,
+                                                           ptr<double>(z), kp, ptr<double>(tmp), SS);
         KF_LAUNCH();
         transpose_to_colmajor<<<nb(SS, 256), 256, 0, st>>>(ptr<double>(tmp), ptr<double>(A) + (l - 2) * SS, S, 1);
         KF_LAUNCH();
-        KF_CUDA(cudaStreamSynchronize(st));
-        dev_free(tmp);
     }
     jacobi_svd<<<nlev, 1024, 0, st>>>(ptr<double>(A), ptr<double>(V), S, 60, ptr<int>(conv));
     KF_LAUNCH();
     svd_sigma<<<nlev, 256, 0, st>>>(ptr<double>(A), S, p.pinv_eps, ptr<double>(sig), ptr<int>(rank));
     KF_LAUNCH();
-    svd_pinv<<<dim3(nb(SS, 256), nlev), 256, 0, st>>>(ptr<double>(A), ptr<double>(V), ptr<double>(sig), S,
-                                                      ptr<double>(P), ptr<double>(PT));
-    KF_LAUNCH();
-    std::vector<int> hrank(nlev), hconv(nlev);
-    KF_CUDA(cudaMemcpyAsync(hrank.data(), rank.p, nlev * 4, cudaMemcpyDeviceToHost, st));
+    std::vector<double> hsig((size_t)nlev * S);
+    std::vector<int> hconv(nlev);
+    KF_CUDA(cudaMemcpyAsync(hsig.data(), sig.p, hsig.size() * 8, cudaMemcpyDeviceToHost, st));
     KF_CUDA(cudaMemcpyAsync(hconv.data(), conv.p, nlev * 4, cudaMemcpyDeviceToHost, st));
     KF_CUDA(cudaStreamSynchronize(st));
+    // kept singular values per level, in decreasing order (ties by index)
+    std::vector<std::vector<int>> keep(L);
+    int rmax = 1;
     for (int l = 2; l < L; ++l) {
         if (hconv[l - 2] < 0) {
             set_error("kifmm_plan: Jacobi SVD did not converge at level " + std::to_string(l));
             return KIFMM_ERR_NUMERIC;
         }
-        LevelOps& op = p.ops[l];
-        op.rank = hrank[l - 2];
-        KF_TRY(dev_alloc(op.uc2ue, SS * 8));
-        KF_TRY(dev_alloc(op.dc2de, SS * 8));
-        KF_CUDA(cudaMemcpyAsync(op.uc2ue.p, ptr<double>(P) + (l - 2) * SS, SS * 8, cudaMemcpyDeviceToDevice, st));
-        // K is symmetric, so G(x^{B,d}, y^{B,d}) = G(x^{B,u}, y^{B,u})^T (the downward check
-        // surface is the upward equivalent one and vice versa) and its pseudo-inverse is
-        // the transpose of the upward one.
-        KF_CUDA(cudaMemcpyAsync(op.dc2de.p, ptr<double>(PT) + (l - 2) * SS, SS * 8, cudaMemcpyDeviceToDevice, st));
+        const double* s = hsig.data() + (size_t)(l - 2) * S;
+        for (int k = 0; k < S; ++k)
+            if (s[k] > 0.0) keep[l].push_back(k);
+        std::stable_sort(keep[l].begin(), keep[l].end(), [&](int x, int y) { return s[x] > s[y]; });
+        p.ops[l].rank = (int)keep[l].size();
+        rmax = std::max(rmax, p.ops[l].rank);
     }
-    // M2L: 343 offset slots per level (the 27 near slots stay zero)
+    const int R = (rmax + 31) / 32 * 32;
+    p.R = R;
+    const int64_t SR = (int64_t)S * R, RR = (int64_t)R * R;
+    for (int l = 2; l < L; ++l) {
+        LevelOps& op = p.ops[l];
+        KF_CUDA(cudaMemcpyAsync(idxb.p, keep[l].data(), keep[l].size() * 4, cudaMemcpyHostToDevice, st));
+        KF_TRY(dev_alloc(op.G1, SR * 8));
+        KF_TRY(dev_alloc(op.Vb, SR * 8));
+        KF_TRY(dev_alloc(op.Ub, SR * 8));
+        KF_TRY(dev_alloc(op.Vt, SR * 8));
+        svd_basis<<<nb(SR, 256), 256, 0, st>>>(ptr<double>(A) + (l - 2) * SS, ptr<double>(V) + (l - 2) * SS,
+                                               ptr<double>(sig) + (l - 2) * S, ptr<int>(idxb), op.rank, S, R,
+                                               ptr<double>(op.G1), ptr<double>(op.Vb), ptr<double>(op.Ub),
+                                               ptr<double>(op.Vt));
+        KF_LAUNCH();
+        KF_CUDA(cudaStreamSynchronize(st));   // idxb is reused by the next level
+    }
+    // ---- M2L in coefficients: T_{l,delta} = V^T K(x^{B,d}, y^{A,u}) V, c_A - c_B = 2 r delta
+    DevBuf m2l, w;
+    KF_TRY(dev_alloc(m2l, kOffsetSlots * SS * 8));
+    KF_TRY(dev_alloc(w, kOffsetSlots * SR * 8));
     std::vector<double> sh(kOffsetSlots * 3);
     for (int l = 2; l < L; ++l) {
         LevelOps& op = p.ops[l];
@@ -254,60 +304,70 @@ int build_operators(Plan& p) {
             for (int dy = -3; dy <= 3; ++dy)
                 for (int dx = -3; dx <= 3; ++dx) {
                     int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
-                    // target (downward check, centre c_B = 0) minus source centre c_A = 2 r delta
                     sh[3 * sl + 0] = -2.0 * r * dx;
                     sh[3 * sl + 1] = -2.0 * r * dy;
                     sh[3 * sl + 2] = -2.0 * r * dz;
                 }
         KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, st));
-        KF_TRY(dev_alloc(op.m2l, kOffsetSlots * SS * 8));
-        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(
-            ptr<double>(p.surf), S, kRInner * r, kRInner * r, ptr<double>(shifts), kp, ptr<double>(op.m2l), SS);
+        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * r, kRInner * r,
+                                                                     ptr<double>(shifts), kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
-        // zero the 27 near slots (|delta|_inf <= 1)
-        for (int dz = -1; dz <= 1; ++dz)
+        for (int dz = -1; dz <= 1; ++dz)   // near slots are never used: zero them
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
                     int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
-                    KF_CUDA(cudaMemsetAsync(ptr<double>(op.m2l) + sl * SS, 0, SS * 8, st));
+                    KF_CUDA(cudaMemsetAsync(ptr<double>(m2l) + sl * SS, 0, SS * 8, st));
                 }
-        if (p.precision == KIFMM_MIXED) {
-            int64_t per = (int64_t)p.Sp * p.Sp;
-            KF_TRY(dev_alloc(op.m2l_hi, kOffsetSlots * per * 4));
-            split_m2l<<<nb(kOffsetSlots * per, 256), 256, 0, st>>>(ptr<double>(op.m2l), S, p.Sp,
-                                                                  ptr<float>(op.m2l_hi), nullptr);
-            KF_LAUNCH();
-        }
-        // M2M / L2L from this level (parent) to level l+1 (children)
-        if (l + 1 < L) {
-            double rc = r / 2.0;
-            for (int o = 0; o < 8; ++o) {
-                double cc[3] = {rc * (2.0 * (o & 1) - 1.0), rc * (2.0 * ((o >> 1) & 1) - 1.0),
-                                rc * (2.0 * ((o >> 2) & 1) - 1.0)};
-                // M2M: target = parent upward check (centre 0), source = child equivalent at cc
-                sh[3 * o + 0] = -cc[0];
-                sh[3 * o + 1] = -cc[1];
-                sh[3 * o + 2] = -cc[2];
-                // L2L: target = child downward check at cc, source = parent equivalent at 0
-                sh[24 + 3 * o + 0] = cc[0];
-                sh[24 + 3 * o + 1] = cc[1];
-                sh[24 + 3 * o + 2] = cc[2];
-            }
-            KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), 48 * 8, cudaMemcpyHostToDevice, st));
-            KF_TRY(dev_alloc(op.m2m, 8 * SS * 8));
-            KF_TRY(dev_alloc(op.l2l, 8 * SS * 8));
-            surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * rc,
-                                                              ptr<double>(shifts), kp, ptr<double>(op.m2m), SS);
-            KF_LAUNCH();
-            surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * rc, kROuter * r,
-                                                              ptr<double>(shifts) + 24, kp, ptr<double>(op.l2l), SS);
-            KF_LAUNCH();
-        }
+        KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(op.Vb), R, 0, ptr<double>(w), R, SR,
+                      kOffsetSlots));
+        KF_TRY(dev_alloc(op.T, kOffsetSlots * RR * 8));
+        KF_TRY(gemm64(st, R, R, S, ptr<double>(op.Vt), S, 0, ptr<double>(w), R, SR, ptr<double>(op.T), R, RR,
+                      kOffsetSlots));
         KF_CUDA(cudaStreamSynchronize(st));
     }
+    // ---- M2M and L2L in coefficients, parent level l -> child level l + 1
+    //   A_{l,o}  = G1_l  K(x^{P,u}, y^{C_o,u}) Vb_{l+1}
+    //   Lo_{l,o} = Vt_{l+1} K(x^{C_o,d}, y^{P,d}) Ub_l
+    for (int l = 2; l + 1 < L; ++l) {
+        LevelOps& op = p.ops[l];
+        LevelOps& ch = p.ops[l + 1];
+        double r = op.r, rc = r / 2.0;
+        for (int o = 0; o < 8; ++o) {
+            double cc[3] = {rc * (2.0 * (o & 1) - 1.0), rc * (2.0 * ((o >> 1) & 1) - 1.0),
+                            rc * (2.0 * ((o >> 2) & 1) - 1.0)};
+            for (int k = 0; k < 3; ++k) {
+                sh[3 * o + k] = -cc[k];        // M2M: parent check (centre 0) - child equivalent at cc
+                sh[24 + 3 * o + k] = cc[k];    // L2L: child check at cc - parent equivalent at 0
+            }
+        }
+        KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), 48 * 8, cudaMemcpyHostToDevice, st));
+        KF_TRY(dev_alloc(op.A, 8 * RR * 8));
+        KF_TRY(dev_alloc(op.Lo, 8 * RR * 8));
+        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * rc,
+                                                          ptr<double>(shifts), kp, ptr<double>(m2l), SS);
+        KF_LAUNCH();
+        KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(ch.Vb), R, 0, ptr<double>(w), R, SR, 8));
+        KF_TRY(gemm64(st, R, R, S, ptr<double>(op.G1), S, 0, ptr<double>(w), R, SR, ptr<double>(op.A), R, RR, 8));
+        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * rc, kROuter * r,
+                                                          ptr<double>(shifts) + 24, kp, ptr<double>(m2l), SS);
+        KF_LAUNCH();
+        KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(op.Ub), R, 0, ptr<double>(w), R, SR, 8));
+        KF_TRY(gemm64(st, R, R, S, ptr<double>(ch.Vt), S, 0, ptr<double>(w), R, SR, ptr<double>(op.Lo), R, RR, 8));
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
+    // ---- FP32 copies for the mixed form's FP32 phases (M2L, L2L, S2L, local/W evaluation)
+    if (p.precision == KIFMM_MIXED) {
+        for (int l = 2; l < L; ++l) {
+            LevelOps& op = p.ops[l];
+            KF_TRY(f32_copy(st, op.T, op.T32, kOffsetSlots * RR));
+            KF_TRY(f32_copy(st, op.Ub, op.Ub32, SR));
+            KF_TRY(f32_copy(st, op.Vb, op.Vb32, SR));
+            KF_TRY(f32_copy(st, op.Vt, op.Vt32, SR));
+            if (l + 1 < L) KF_TRY(f32_copy(st, op.Lo, op.Lo32, 8 * RR));
+        }
+    }
     KF_CUDA(cudaStreamSynchronize(st));
-    dev_free(A); dev_free(V); dev_free(sig); dev_free(rank); dev_free(conv);
-    dev_free(P); dev_free(PT); dev_free(shifts); dev_free(z);
+    for (DevBuf* d : {&A, &V, &sig, &rank, &conv, &shifts, &tmp, &z, &idxb, &m2l, &w}) dev_free(*d);
     return KIFMM_OK;
 }
 
