@@ -152,8 +152,11 @@ typedef struct {
     double pinv_rank_min;       /* smallest kept rank over the levels' pseudo-inverses */
     int64_t eval_launches;      /* kernels launched by one kifmm_eval of this plan */
     int64_t p2p_pairs;          /* near-field pair evaluations of one kifmm_eval */
+    int64_t m2l_tensor;         /* 1 if M2L runs on the tensor cores (mixed form) */
+    int64_t device_error;       /* nonzero if a bounded device wait ran out (synchronises) */
 } kifmm_info;
 
+/* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */
 int kifmm_get_info(kifmm_plan_t plan, kifmm_info* info);
 
 /* Copies the tree to caller-allocated host arrays (any pointer may be NULL):

@@ -37,10 +37,11 @@ static void free_plan(Plan* p) {
             dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->dd, &p->phid, &p->phiu,
-                      &p->far, &p->wleaves, &p->host_I, &p->host_S})
+                      &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err})
         dev_free(*b);
     for (auto& L : p->lv) {
-        for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes})
+        for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
+                          &L.m2l_slots128})
             dev_free(*b);
         for (int o = 0; o < 8; ++o) {
             dev_free(L.m2m_src[o]);
@@ -158,6 +159,13 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     if (rc) return fail(rc);
     rc = build_self_terms(*p, cell_h, uniform_h);
     if (rc) return fail(rc);
+    {
+        const char* m2l = std::getenv("KIFMM_M2L");
+        p->m2l_tensor = p->precision == KIFMM_MIXED && m2l_tc_supported(p->R) && !(m2l && std::string(m2l) == "simt");
+    }
+    rc = dev_alloc(p->err, 16);
+    if (rc) return fail(rc);
+    if (cudaMemsetAsync(p->err.p, 0, 16, p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     rc = build_eval_data(*p);
     if (rc) return fail(rc);
     rc = dev_alloc(p->host_I, n * 8);
@@ -300,6 +308,14 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     for (int l = 2; l < p.tree.nlevels; ++l) rmin = std::min(rmin, p.ops[l].rank);
     info->pinv_rank_min = rmin;
     info->eval_launches = p.eval_launches;
+    info->m2l_tensor = p.m2l_tensor ? 1 : 0;
+    info->device_error = 0;
+    if (p.err.p) {
+        int e = 0;
+        KF_CUDA(cudaMemcpyAsync(&e, p.err.p, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+        KF_CUDA(cudaStreamSynchronize(p.stream));
+        info->device_error = e;
+    }
     info->p2p_pairs = p.p2p_pairs;
     return KIFMM_OK;
 }

@@ -208,6 +208,15 @@ int build_eval_data(Plan& p) {
             m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, ptr<int32_t>(L.m2l_slots));
             KF_LAUNCH();
         }
+        if (p.m2l_tensor) {
+            L.n_tiles128 = (int)((cnt + 127) / 128);
+            KF_TRY(dev_alloc(L.m2l_slots128, (size_t)std::max(L.n_tiles128, 1) * kSlotStride * 4));
+            if (L.n_tiles128 > 0) {
+                m2l_tile_slots<<<L.n_tiles128, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128,
+                                                             ptr<int32_t>(L.m2l_slots128));
+                KF_LAUNCH();
+            }
+        }
         // leaves of this level
         select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 1, 2,
                                                     ptr<int32_t>(flag) + lo);
@@ -797,6 +806,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     for (int l = 2; l < L; ++l) {
         auto& LL = p.lv[l];
         if (LL.n_tiles == 0) continue;
+        if (sizeof(T) == 4 && p.m2l_tensor) {
+            KF_TRY(launch_m2l_tc(st, ptr<float>(p.ops[l].T32), R, ptr<int32_t>(p.vtab), ptr<int32_t>(LL.m2l_slots128),
+                                 t.level_start[l], t.level_start[l + 1], reinterpret_cast<const float*>(c),
+                                 reinterpret_cast<float*>(dd), ptr<int>(p.err)));
+            ++nl;
+            continue;
+        }
         dim3 g(LL.n_tiles, nbk(R, M2L_TM));
         k_m2l<T><<<g, 256, 0, st>>>(sel<T>(p.ops[l].T, p.ops[l].T32), R, ptr<int32_t>(p.vtab),
                                     ptr<int32_t>(LL.m2l_slots), t.level_start[l], t.level_start[l + 1], c, dd);

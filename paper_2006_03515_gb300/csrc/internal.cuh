@@ -142,11 +142,14 @@ struct Plan {
         DevBuf m2m_src[8]; DevBuf m2m_dst[8]; int n_m2m[8] = {0};   // child (src), parent (dst)
         DevBuf m2l_tiles;  int n_tiles = 0;      // tile -> first box (tiles of kM2LTile boxes)
         DevBuf m2l_slots;  DevBuf m2l_slot_off;  // per tile: list of active offset slots
+        DevBuf m2l_slots128; int n_tiles128 = 0;  // the same for tiles of 128 boxes (tensor-core M2L)
         DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
     };
     std::vector<LevelLists> lv;
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
     int64_t eval_launches = 0;   // kernels of the last evaluation
+    bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
+    DevBuf err;                  // int: device-side error code (bounded waits)
     int64_t p2p_pairs = 0;       // near-field pairs of one evaluation
     // timing
     bool timing = false;
@@ -169,6 +172,10 @@ int device_scan_i32(const int32_t* in, int32_t* out, int64_t n, int32_t* total_h
 // operators.cu
 int build_operators(Plan& p);
 int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
+// m2l_tc.cu
+int m2l_tc_supported(int R);
+int launch_m2l_tc(cudaStream_t st, const float* Tm, int R, const int32_t* vtab, const int32_t* slots, int64_t lo,
+                  int64_t hi, const float* c, float* d, int* err);
 // eval.cu
 int build_eval_data(Plan& p);
 int run_eval(Plan& p, const void* I, void* S, int dtype, double C);

@@ -51,7 +51,7 @@ class _Info(ctypes.Structure):
                 ("surface_points", ctypes.c_int32), ("n_leaves", ctypes.c_int64),
                 ("list_len", ctypes.c_int64 * 4), ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("pinv_rank_min", ctypes.c_double), ("eval_launches", ctypes.c_int64),
-                ("p2p_pairs", ctypes.c_int64)]
+                ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64)]
 
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
@@ -178,7 +178,8 @@ class Plan:
         return dict(n_points=inf.n_points, n_boxes=inf.n_boxes, n_levels=inf.n_levels,
                     surface_points=inf.surface_points, n_leaves=inf.n_leaves, list_len=list(inf.list_len),
                     origin=list(inf.origin), side=inf.side, pinv_rank_min=int(inf.pinv_rank_min),
-                    eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs))
+                    eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs),
+                    m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error))
 
     def tree(self):
         inf = self.info()

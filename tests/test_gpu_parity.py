@@ -222,3 +222,21 @@ def test_given_root_cube(kf):
     np.testing.assert_array_equal(p.tree()["keys"], t.keys)
     with pytest.raises(kf.KifmmError):
         _plan(kf, pts, h, 8, 6, a, b, root=(0.2, 0.0, 0.0, 1.0))
+
+
+def test_tensor_core_m2l_against_simt_and_fp64(kf, monkeypatch):
+    # the mixed form's M2L runs on tcgen05 (3xTF32); the SIMT FP32 M2L is the cross-check
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(15.2)
+    s64 = _plan(kf, pts, h, 64, 6, a, b).eval(_dev(I)).cpu().numpy()
+    p_tc = _plan(kf, pts, h, 64, 6, a, b, precision="mixed")
+    assert p_tc.info()["m2l_tensor"]
+    s_tc = p_tc.eval(_dev(I)).cpu().numpy()
+    assert p_tc.info()["device_error"] == 0
+    monkeypatch.setenv("KIFMM_M2L", "simt")
+    p_simt = _plan(kf, pts, h, 64, 6, a, b, precision="mixed")
+    assert not p_simt.info()["m2l_tensor"]
+    s_simt = p_simt.eval(_dev(I)).cpu().numpy()
+    assert _relerr(s_tc, s64) <= 1e-6
+    assert _relerr(s_simt, s64) <= 1e-6
+    assert _relerr(s_tc, s_simt) <= 1e-6
