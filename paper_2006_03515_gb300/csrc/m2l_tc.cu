@@ -89,23 +89,33 @@ __device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo
 
 // d[b] = sum_slots T[slot] c[src(b, slot)] for the boxes [lo + 128*blockIdx.x, +128) of one level.
 // Dynamic shared memory: 2 stages x (A_hi, A_lo: 128 x 128 B; B_hi, B_lo: R x 128 B), 1024-aligned.
-__global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm, int R, const int32_t* __restrict__ vtab,
+// Tensor memory: two accumulators of R columns, ACC apart (ACC = R rounded up to a power
+// of two). The MMAs of one
+// slot go to one accumulator (restarted at its first k-step); while the next slot's MMAs
+// run, every thread adds its row-half of the finished accumulator into FP32 registers
+// with round-to-nearest additions. The tensor core's internal accumulation therefore
+// spans one slot (R/8 x 3 MMAs) instead of the whole V list. NC = R / 32.
+template <int NC>
+__global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm, const int32_t* __restrict__ vtab,
                                                     const int32_t* __restrict__ slots, int64_t lo, int64_t hi,
                                                     const float* __restrict__ c, float* __restrict__ d, int* err) {
+    constexpr int R = 32 * NC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar[2];     // shared-memory stage s free again
+    __shared__ uint64_t accbar[2];   // accumulator j holds a finished slot
     __shared__ uint32_t tmem_base;
     __shared__ int bad;
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int a_bytes = TC_M * 128, b_bytes = R * 128;
-    const int stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    constexpr int a_bytes = TC_M * 128, b_bytes = R * 128;
+    constexpr int stage_bytes = 2 * a_bytes + 2 * b_bytes;
     const int64_t b0 = lo + (int64_t)blockIdx.x * TC_M;
     const int32_t* sl = slots + (int64_t)blockIdx.x * 344;
     const int ns = sl[0];
-    const int nk = R / TC_KC;
+    constexpr int nk = R / TC_KC;
     const int total = ns * nk;
-    const int ncols = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
+    constexpr int ACC = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
+    constexpr uint32_t ncols = 2 * ACC;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -114,8 +124,10 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm
     }
     if (tid == 0) {
         bad = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])));
+        for (int k = 0; k < 2; ++k) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[k])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accbar[k])));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -123,10 +135,40 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = tf32_idesc(TC_M, R);
-    uint32_t phase[2] = {0u, 0u};
+    uint32_t phase[2] = {0u, 0u}, aphase[2] = {0u, 0u};
+    // this thread's share of the result: row 32*(warp%4)+lane, columns [half*R/2, +R/2)
+    const int q = warp & 3, half = warp >> 2;
+    const uint32_t t_row = (uint32_t)(32 * q) << 16;
+    const int col0 = half * (R / 2);
+    float acc[R / 2];
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) acc[k] = 0.f;
+
+    // adds accumulator j (finished slot) into acc[]
+    auto drain = [&](int j) -> bool {
+        const bool ok = mbar_wait(smem_u32(&accbar[j]), aphase[j]);
+        aphase[j] ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int cc = 0; cc < R / 2; cc += 16) {
+            uint32_t v[16];
+            const uint32_t ta = tmem + t_row + (uint32_t)(j * ACC + col0 + cc);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int k = 0; k < 16; ++k) acc[cc + k] += __uint_as_float(v[k]);
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        return ok;
+    };
 
     for (int it = 0; it < total; ++it) {
         const int s = it & 1;
+        const int si = it / nk, kc = it % nk;
         unsigned char* A_hi = base + s * stage_bytes;
         unsigned char* A_lo = A_hi + a_bytes;
         unsigned char* B_hi = A_lo + a_bytes;
@@ -139,8 +181,8 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm
                 break;
             }
         }
-        const int slot = sl[1 + it / nk];
-        const int k0 = (it % nk) * TC_KC;
+        const int slot = sl[1 + si];
+        const int k0 = kc * TC_KC;
         // A: 128 gathered rows x 8 chunks of 16 bytes
         for (int e = tid; e < TC_M * 8; e += TC_T) {
             const int row = e >> 3, j = e & 7;
@@ -162,52 +204,41 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
+            const uint32_t dacc = tmem + (uint32_t)((si & 1) * ACC);
 #pragma unroll
             for (int k = 0; k < TC_KC / 8; ++k) {
                 const uint32_t ko = 32u * k;   // 8 TF32 = 32 bytes along K inside the swizzle atom
-                const uint32_t acc = (it > 0 || k > 0) ? 1u : 0u;
-                mma_tf32(tmem, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
-                mma_tf32(tmem, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                mma_tf32(tmem, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                const uint32_t first = (kc > 0 || k > 0) ? 1u : 0u;
+                mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first);
+                mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                mma_tf32(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
             }
             mma_commit(smem_u32(&mbar[s]));
+            if (kc == nk - 1) mma_commit(smem_u32(&accbar[si & 1]));
+        }
+        if (kc == 0 && si >= 1) {   // the previous slot's accumulator, while this slot's MMAs run
+            const int timed_out = drain((si - 1) & 1) ? 0 : 1;
+            if (__syncthreads_or(timed_out)) {
+                if (tid == 0) bad = 1;
+                break;
+            }
         }
     }
-    // drain: every used stage has exactly one commit not yet waited for (its last one);
-    // after a timeout the same bounded waits let the MMAs in flight finish before the
-    // tensor memory is freed
+    // drain: the last slot's accumulator, then the last commit of each used stage (also
+    // after a timeout, so that the MMAs in flight finish before the tensor memory is freed)
     __syncthreads();
     int timed_out = 0;
+    if (!bad && ns > 0 && !drain((ns - 1) & 1)) timed_out = 1;
     for (int s = 0; s < 2; ++s)
         if (s < total && !mbar_wait(smem_u32(&mbar[s]), phase[s])) timed_out = 1;
     if (__syncthreads_or(timed_out) && tid == 0) bad = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (!bad) {
-        // epilogue: warp w reads lanes 32*(w%4) .. +31 (rows), columns of its half
-        const int q = warp & 3, half = warp >> 2;
-        const int row = 32 * q + lane;
-        const int64_t b = b0 + row;
-        const int c0 = half * (R / 2), c1 = c0 + R / 2;
-        for (int col = c0; col < c1; col += 16) {
-            uint32_t v[16];
-            const uint32_t ta = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)col;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (b < hi) {
-                float4* o = reinterpret_cast<float4*>(d + b * R + col);
-                if (total == 0) {
-                    for (int k = 0; k < 4; ++k) o[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                } else {
-                    for (int k = 0; k < 4; ++k)
-                        o[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
-                                           __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
-                }
-            }
+        const int64_t b = b0 + 32 * q + lane;
+        if (b < hi) {
+            float4* o = reinterpret_cast<float4*>(d + b * R + col0);
+#pragma unroll
+            for (int k = 0; k < R / 8; ++k) o[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
         }
     } else if (tid == 0) {
         atomicExch(err, 1);
@@ -221,19 +252,35 @@ size_t m2l_tc_smem(int R) { return 1024 + 2 * (size_t)(2 * TC_M * 128 + 2 * R * 
 
 int m2l_tc_supported(int R) { return (R % 32 == 0 && R >= 32 && R <= 256 && m2l_tc_smem(R) <= 227 * 1024) ? 1 : 0; }
 
-int launch_m2l_tc(cudaStream_t st, const float* Tm, int R, const int32_t* vtab, const int32_t* slots, int64_t lo,
-                  int64_t hi, const float* c, float* d, int* err) {
-    const size_t smem = m2l_tc_smem(R);
-    static int configured_bytes = 0;
-    if ((int)smem > configured_bytes) {
-        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured_bytes = (int)smem;
+template <int NC>
+static int launch_nc(cudaStream_t st, const float* Tm, const int32_t* vtab, const int32_t* slots, int64_t lo,
+                     int64_t hi, const float* c, float* d, int* err, int64_t ntiles) {
+    const size_t smem = m2l_tc_smem(32 * NC);
+    static bool configured = false;   // one attribute per instantiation (its size never changes)
+    if (!configured) {
+        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
     }
-    const int64_t ntiles = (hi - lo + TC_M - 1) / TC_M;
-    if (ntiles <= 0) return KIFMM_OK;
-    k_m2l_tc<<<(unsigned)ntiles, TC_T, smem, st>>>(Tm, R, vtab, slots, lo, hi, c, d, err);
+    k_m2l_tc<NC><<<(unsigned)ntiles, TC_T, smem, st>>>(Tm, vtab, slots, lo, hi, c, d, err);
     KF_LAUNCH();
     return KIFMM_OK;
+}
+
+int launch_m2l_tc(cudaStream_t st, const float* Tm, int R, const int32_t* vtab, const int32_t* slots, int64_t lo,
+                  int64_t hi, const float* c, float* d, int* err) {
+    const int64_t ntiles = (hi - lo + TC_M - 1) / TC_M;
+    if (ntiles <= 0) return KIFMM_OK;
+    switch (R / 32) {
+        case 1: return launch_nc<1>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 2: return launch_nc<2>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 3: return launch_nc<3>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 4: return launch_nc<4>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 5: return launch_nc<5>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 6: return launch_nc<6>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 7: return launch_nc<7>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 8: return launch_nc<8>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
+    }
 }
 
 }  // namespace kifmm
