@@ -33,15 +33,16 @@ static void free_plan(Plan* p) {
     }
     dev_free(p->vtab);
     for (auto& o : p->ops)
-        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.A, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32})
+        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.A, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32,
+                          &o.Thi, &o.Tlo})
             dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
-                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->dd, &p->phid, &p->phiu,
+                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err})
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
-                          &L.m2l_slots128})
+                          &L.m2l_slots128, &L.m2l_boxes})
             dev_free(*b);
         for (int o = 0; o < 8; ++o) {
             dev_free(L.m2m_src[o]);
@@ -159,10 +160,6 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     if (rc) return fail(rc);
     rc = build_self_terms(*p, cell_h, uniform_h);
     if (rc) return fail(rc);
-    {
-        const char* m2l = std::getenv("KIFMM_M2L");
-        p->m2l_tensor = p->precision == KIFMM_MIXED && m2l_tc_supported(p->R) && !(m2l && std::string(m2l) == "simt");
-    }
     rc = dev_alloc(p->err, 16);
     if (rc) return fail(rc);
     if (cudaMemsetAsync(p->err.p, 0, 16, p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);

@@ -71,17 +71,20 @@ __global__ void m2m_fill(const int32_t* child, const int32_t* flag, const int32_
 
 constexpr int kSlotStride = 344;   // per M2L tile: [count, slot_0, slot_1, ...]
 
-// active offset slots of a tile of consecutive boxes (union of their V lists)
-__global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int tb, int32_t* slots) {
+// active offset slots of a tile of boxes (union of their V lists): boxes lo + tile*tb + k,
+// or list[tile*tb + k] when a box list is given (k < tb, within the level's hi - lo boxes)
+__global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int tb, const int32_t* list,
+                               int32_t* slots) {
     int tile = blockIdx.x;
     __shared__ int mask[kOffsetSlots];
     for (int s = threadIdx.x; s < kOffsetSlots; s += blockDim.x) mask[s] = 0;
     __syncthreads();
-    int64_t b0 = lo + (int64_t)tile * tb;
     for (int e = threadIdx.x; e < tb * kOffsetSlots; e += blockDim.x) {
-        int64_t b = b0 + e / kOffsetSlots;
+        int64_t k = (int64_t)tile * tb + e / kOffsetSlots;
         int s = e % kOffsetSlots;
-        if (b < hi && vtab[b * kOffsetSlots + s] >= 0) mask[s] = 1;
+        if (k >= hi - lo) continue;
+        int64_t b = list ? list[k] : lo + k;
+        if (vtab[b * kOffsetSlots + s] >= 0) mask[s] = 1;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -90,6 +93,13 @@ __global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int 
             if (mask[s]) slots[(int64_t)tile * kSlotStride + 1 + n++] = s;
         slots[(int64_t)tile * kSlotStride] = n;
     }
+}
+
+__global__ void octant_flags(const int32_t* anchor, int64_t lo, int64_t hi, int oc, int32_t* flag) {
+    int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= hi) return;
+    int o = (anchor[3 * b] & 1) | ((anchor[3 * b + 1] & 1) << 1) | ((anchor[3 * b + 2] & 1) << 2);
+    flag[b - lo] = (o == oc) ? 1 : 0;
 }
 
 __global__ void nonempty_boxes(const int32_t* off, int64_t lo, int64_t hi, int min_level,
@@ -205,17 +215,29 @@ int build_eval_data(Plan& p) {
         L.n_tiles = (int)((cnt + tb - 1) / tb);
         KF_TRY(dev_alloc(L.m2l_slots, (size_t)std::max(L.n_tiles, 1) * kSlotStride * 4));
         if (L.n_tiles > 0) {
-            m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, ptr<int32_t>(L.m2l_slots));
+            m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, nullptr, ptr<int32_t>(L.m2l_slots));
             KF_LAUNCH();
         }
-        if (p.m2l_tensor) {
+        if (p.m2l_tensor && cnt > 0) {
+            // boxes grouped by their octant inside the parent (same set of V offsets), Morton
+            // order within a group; tiles of 128 over this order
+            KF_TRY(dev_alloc(L.m2l_boxes, (size_t)cnt * 4));
+            int32_t done = 0;
+            for (int oc = 0; oc < 8; ++oc) {
+                octant_flags<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.anchor), lo, hi, oc, ptr<int32_t>(flag));
+                KF_LAUNCH();
+                int32_t nsel = 0;
+                KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), cnt, &nsel, st, scan_tmp));
+                compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), lo, cnt,
+                                                              ptr<int32_t>(L.m2l_boxes) + done);
+                KF_LAUNCH();
+                done += nsel;
+            }
             L.n_tiles128 = (int)((cnt + 127) / 128);
             KF_TRY(dev_alloc(L.m2l_slots128, (size_t)std::max(L.n_tiles128, 1) * kSlotStride * 4));
-            if (L.n_tiles128 > 0) {
-                m2l_tile_slots<<<L.n_tiles128, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128,
-                                                             ptr<int32_t>(L.m2l_slots128));
-                KF_LAUNCH();
-            }
+            m2l_tile_slots<<<L.n_tiles128, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128, ptr<int32_t>(L.m2l_boxes),
+                                                         ptr<int32_t>(L.m2l_slots128));
+            KF_LAUNCH();
         }
         // leaves of this level
         select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 1, 2,
@@ -254,6 +276,10 @@ int build_eval_data(Plan& p) {
     KF_TRY(dev_alloc(p.phid, (size_t)nb * S * ts));
     KF_CUDA(cudaMemsetAsync(p.phid.p, 0, (size_t)nb * S * ts, st));
     if (p.precision == KIFMM_MIXED) KF_TRY(dev_alloc(p.cu32, (size_t)nb * R * 4));
+    if (p.m2l_tensor) {
+        KF_TRY(dev_alloc(p.chi, (size_t)nb * R * 4));
+        KF_TRY(dev_alloc(p.clo, (size_t)nb * R * 4));
+    }
     if (p.lists[3].len > 0) KF_TRY(dev_alloc(p.chkx, (size_t)nb * S * ts));
     if (p.lists[2].len > 0) {
         KF_TRY(dev_alloc(p.phiu, (size_t)nb * S * ts));
@@ -800,6 +826,10 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         KF_LAUNCH();
         ++nl;
         c = reinterpret_cast<const T*>(ptr<float>(p.cu32));
+        if (p.m2l_tensor) {
+            KF_TRY(m2l_tc_split(st, cu, m, ptr<float>(p.chi), ptr<float>(p.clo)));
+            ++nl;
+        }
     } else {
         c = reinterpret_cast<const T*>(cu);
     }
@@ -807,8 +837,9 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         auto& LL = p.lv[l];
         if (LL.n_tiles == 0) continue;
         if (sizeof(T) == 4 && p.m2l_tensor) {
-            KF_TRY(launch_m2l_tc(st, ptr<float>(p.ops[l].T32), R, ptr<int32_t>(p.vtab), ptr<int32_t>(LL.m2l_slots128),
-                                 t.level_start[l], t.level_start[l + 1], reinterpret_cast<const float*>(c),
+            KF_TRY(launch_m2l_tc(st, ptr<float>(p.ops[l].Thi), ptr<float>(p.ops[l].Tlo), R, ptr<int32_t>(LL.m2l_boxes),
+                                 (int)(t.level_start[l + 1] - t.level_start[l]), ptr<int32_t>(p.vtab),
+                                 ptr<int32_t>(LL.m2l_slots128), ptr<float>(p.chi), ptr<float>(p.clo),
                                  reinterpret_cast<float*>(dd), ptr<int>(p.err)));
             ++nl;
             continue;

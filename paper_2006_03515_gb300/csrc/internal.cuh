@@ -95,6 +95,8 @@ struct LevelOps {
     DevBuf Lo;           // [8][R][R] L2L in coefficients, parent level = this level
     // FP32 copies (mixed form)
     DevBuf T32, Ub32, Vb32, Vt32, Lo32;
+    // tensor-core M2L operands: TF32 hi/lo of T, [slot][k-chunk][row][128-byte swizzled row]
+    DevBuf Thi, Tlo;
 };
 
 struct Plan {
@@ -127,7 +129,8 @@ struct Plan {
     DevBuf chk;        // f64[nb*S] upward check potentials of the leaves (S2M)
     DevBuf chkx;       // T[nb*S]  downward check potentials from the X list (S2L)
     DevBuf cu;         // f64[nb*R] upward coefficients c
-    DevBuf cu32;       // f32[nb*R] (mixed) FP32 copy of c for M2L and the W list
+    DevBuf cu32;       // f32[nb*R] (mixed) FP32 copy of c for the SIMT M2L and the W list
+    DevBuf chi, clo;   // f32[nb*R] (mixed, tensor-core M2L) TF32 hi/lo parts of c
     DevBuf dd;         // T[nb*R]  downward coefficients d
     DevBuf phid;       // T[nb*S]  downward equivalent densities of the leaves
     DevBuf phiu;       // T[nb*S]  upward equivalent densities (only when W lists exist)
@@ -142,7 +145,8 @@ struct Plan {
         DevBuf m2m_src[8]; DevBuf m2m_dst[8]; int n_m2m[8] = {0};   // child (src), parent (dst)
         DevBuf m2l_tiles;  int n_tiles = 0;      // tile -> first box (tiles of kM2LTile boxes)
         DevBuf m2l_slots;  DevBuf m2l_slot_off;  // per tile: list of active offset slots
-        DevBuf m2l_slots128; int n_tiles128 = 0;  // the same for tiles of 128 boxes (tensor-core M2L)
+        DevBuf m2l_boxes;                          // boxes of the level grouped by octant (tensor-core M2L)
+        DevBuf m2l_slots128; int n_tiles128 = 0;  // active offset slots per tile of 128 grouped boxes
         DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
     };
     std::vector<LevelLists> lv;
@@ -174,8 +178,10 @@ int build_operators(Plan& p);
 int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
 // m2l_tc.cu
 int m2l_tc_supported(int R);
-int launch_m2l_tc(cudaStream_t st, const float* Tm, int R, const int32_t* vtab, const int32_t* slots, int64_t lo,
-                  int64_t hi, const float* c, float* d, int* err);
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, float* Thi, float* Tlo);
+int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float* clo);
+int launch_m2l_tc(cudaStream_t st, const float* Thi, const float* Tlo, int R, const int32_t* boxes, int nbox,
+                  const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err);
 // eval.cu
 int build_eval_data(Plan& p);
 int run_eval(Plan& p, const void* I, void* S, int dtype, double C);

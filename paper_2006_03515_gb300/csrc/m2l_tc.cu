@@ -2,28 +2,38 @@
 //
 // In the coefficient basis the translation of one level is, for every target box B,
 //   d[B] = sum over the offset slots of V(B):  T[slot] c[A(B, slot)],
-// T[slot] (R x R) shared by every pair with that relative offset. One CTA takes a tile of
-// 128 consecutive boxes of a level and keeps D[128 x R] (boxes x output coefficients) in
-// tensor memory across all slots of the tile. Per slot and 32-wide k-chunk the CTA
-// gathers the 128 source rows c[A] (A operand, K-major) and the chunk of T[slot]
-// (B operand, K-major), splits each FP32 value x into x_hi = tf32(x) and
-// x_lo = tf32(x - x_hi) while writing them to shared memory in the 128-byte swizzled
-// layout, and one thread issues 4 k-steps x 3 MMAs (hi*hi + hi*lo + lo*hi).
-// Two shared-memory stages alternate; an mbarrier per stage (tcgen05.commit) tells the
-// producers when the tensor core has finished reading a stage. Every wait is bounded: on
-// timeout the kernel records an error code, frees its tensor memory and returns.
+// with T[slot] (R x R) shared by every pair with that relative offset. One CTA takes a
+// tile of 128 target boxes of a level (boxes grouped by their octant inside the parent,
+// so that the tile's boxes share one set of about 189 offsets) and, per offset slot and
+// 32-wide k-chunk, multiplies the gathered source rows c[A] (A operand, 128 x 32) by the
+// chunk of T[slot] (B operand, R x 32), both K-major in the 128-byte swizzled layout, as
+// hi*hi + hi*lo + lo*hi TF32 MMAs (x = x_hi + x_lo, both TF32).
+//
+// Roles (warp specialization, 11 warps):
+//  * warps 8-9, producers: per iteration each thread gathers two source rows with
+//    16-byte cp.async copies (hi and lo, zero-filled where the box has no source at this
+//    offset); thread 0 of warp 8 also moves the pre-swizzled B chunk with two 1-D bulk
+//    copies. Completion arrives on the stage's "full" mbarrier.
+//  * warp 10, lane 0: waits for a full stage, issues 4 k-steps x 3 MMAs into the slot's
+//    tensor-memory accumulator and commits the stage's "empty" mbarrier; after the last
+//    chunk of a slot it commits the accumulator's "ready" mbarrier.
+//  * warps 0-7, epilogue: two accumulators alternate between slots; the epilogue adds a
+//    finished one into FP32 registers (round-to-nearest) and releases it. The tensor
+//    core's own accumulation thus spans one slot, not the whole V list.
+// Every wait is bounded; a timeout sets an abort flag that ends the other roles' waits,
+// records an error code, and the tensor memory is freed before the CTA exits.
 #include "internal.cuh"
 
 namespace kifmm {
 
-constexpr int TC_M = 128;          // boxes per tile = MMA M
-constexpr int TC_T = 256;          // threads per CTA
-constexpr int TC_KC = 32;          // k-chunk: 32 FP32 = one 128-byte swizzle atom per row
-constexpr uint32_t TC_SPIN = 1u << 26;
+constexpr int TC_M = 128;                 // target boxes per tile = MMA M
+constexpr int TC_KC = 32;                 // k-chunk: 32 FP32 = one 128-byte swizzle row
+constexpr int TC_EPI = 256;               // epilogue threads (warps 0-7)
+constexpr int TC_PROD = 64;               // producer threads (warps 8-9), two source rows each
+constexpr int TC_THREADS = TC_EPI + TC_PROD + 32;
+constexpr uint32_t TC_SPIN = 1u << 20;   // a normal wait needs a few hundred polls
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint32_t tf32_rna(float x) {
     uint32_t u;
@@ -31,10 +41,16 @@ __device__ __forceinline__ uint32_t tf32_rna(float x) {
     return u;
 }
 
-// Shared-memory matrix descriptor (tcgen05): K-major operand, 128-byte swizzle, rows of
-// 128 bytes grouped by 8 (1024-byte atoms). start >> 4 in bits [0,14), leading byte
-// offset >> 4 in [16,30) (unused for this layout), stride byte offset >> 4 in [32,46)
-// (= 1024 between 8-row groups), fixed 0b01 in [46,48), swizzle mode 2 (128B) in [61,64).
+// Byte offset of (row, k) inside a [rows x 32 FP32] tile in the 128-byte swizzled layout:
+// rows of 128 bytes, 16-byte chunk j of row r stored at chunk j ^ (r mod 8).
+__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
+    return (uint32_t)row * 128u + (uint32_t)((((k >> 2) ^ (row & 7)) << 4) | ((k & 3) << 2));
+}
+
+// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits [0,14), leading byte
+// offset >> 4 in [16,30) (not used by this layout), stride byte offset >> 4 in [32,46)
+// (1024 bytes between 8-row groups), fixed 0b001 in [46,49), swizzle mode 2 = 128-byte
+// swizzle in [61,64).
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     uint64_t d = 0;
     d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -63,7 +79,17 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Bounded wait for the phase of the given parity; gives up on timeout or when another
+// role has raised the abort flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, volatile int* abort_flag) {
     for (uint32_t it = 0; it < TC_SPIN; ++it) {
         uint32_t ok;
         asm volatile(
@@ -72,61 +98,85 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
             : "r"(mbar), "r"(parity)
             : "memory");
         if (ok) return true;
+        if ((it & 255u) == 255u && *abort_flag) return false;
     }
+    *abort_flag = 1;
     return false;
 }
 
-// Split 4 FP32 values into TF32 hi/lo and store them at the swizzled position of
-// (row, 16-byte chunk j) of two 128-byte-row tiles.
-__device__ __forceinline__ void store_split(unsigned char* hi, unsigned char* lo, int row, int j, float4 v) {
-    const uint32_t off = (uint32_t)row * 128u + (uint32_t)((j ^ (row & 7)) * 16);
-    uint32_t h0 = tf32_rna(v.x), h1 = tf32_rna(v.y), h2 = tf32_rna(v.z), h3 = tf32_rna(v.w);
-    uint32_t l0 = tf32_rna(v.x - __uint_as_float(h0)), l1 = tf32_rna(v.y - __uint_as_float(h1));
-    uint32_t l2 = tf32_rna(v.z - __uint_as_float(h2)), l3 = tf32_rna(v.w - __uint_as_float(h3));
-    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h0, h1, h2, h3);
-    *reinterpret_cast<uint4*>(lo + off) = make_uint4(l0, l1, l2, l3);
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
 }
 
-// d[b] = sum_slots T[slot] c[src(b, slot)] for the boxes [lo + 128*blockIdx.x, +128) of one level.
-// Dynamic shared memory: 2 stages x (A_hi, A_lo: 128 x 128 B; B_hi, B_lo: R x 128 B), 1024-aligned.
-// Tensor memory: two accumulators of R columns, ACC apart (ACC = R rounded up to a power
-// of two). The MMAs of one
-// slot go to one accumulator (restarted at its first k-step); while the next slot's MMAs
-// run, every thread adds its row-half of the finished accumulator into FP32 registers
-// with round-to-nearest additions. The tensor core's internal accumulation therefore
-// spans one slot (R/8 x 3 MMAs) instead of the whole V list. NC = R / 32.
-template <int NC>
-__global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm, const int32_t* __restrict__ vtab,
-                                                    const int32_t* __restrict__ slots, int64_t lo, int64_t hi,
-                                                    const float* __restrict__ c, float* __restrict__ d, int* err) {
+// ------------------------------------------------------------------------------------
+// plan and per-evaluation operand preparation
+// ------------------------------------------------------------------------------------
+// T (FP64 [343][R][R]) -> Thi/Tlo (FP32, TF32-rounded) in the order
+// [slot][k-chunk][row][128-byte swizzled row], so that one chunk of one slot is a
+// contiguous R*128-byte image of the shared-memory B tile.
+__global__ void k_swizzle_T(const double* T, int R, float* Thi, float* Tlo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t RR = (int64_t)R * R;
+    if (e >= (int64_t)kOffsetSlots * RR) return;
+    const int64_t slot = e / RR;
+    const int row = (int)((e % RR) / R), k = (int)(e % R);
+    const float x = (float)T[e];
+    const uint32_t h = tf32_rna(x);
+    const uint32_t l = tf32_rna(x - __uint_as_float(h));
+    const int64_t byte = slot * RR * 4 + (int64_t)(k / TC_KC) * R * 128 + sw128_off(row, k % TC_KC);
+    reinterpret_cast<uint32_t*>(Thi)[byte / 4] = h;
+    reinterpret_cast<uint32_t*>(Tlo)[byte / 4] = l;
+}
+
+// upward coefficients (FP64) -> TF32 hi/lo pair of their FP32 value
+__global__ void k_split_c(const double* c, int64_t n, float* chi, float* clo) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float x = (float)c[e];
+    const uint32_t h = tf32_rna(x);
+    chi[e] = __uint_as_float(h);
+    clo[e] = __uint_as_float(tf32_rna(x - __uint_as_float(h)));
+}
+
+// ------------------------------------------------------------------------------------
+// the kernel
+// ------------------------------------------------------------------------------------
+template <int NC, int NS>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_m2l_tc(const float* __restrict__ Thi, const float* __restrict__ Tlo, const int32_t* __restrict__ boxes, int nbox,
+             const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const float* __restrict__ chi,
+             const float* __restrict__ clo, float* __restrict__ d, int* err) {
     constexpr int R = 32 * NC;
+    constexpr int NK = R / TC_KC;
+    constexpr int A_BYTES = TC_M * 128, B_BYTES = R * 128;
+    constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
+    constexpr int ACC = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
+    constexpr uint32_t NCOLS = 2 * ACC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t mbar[2];     // shared-memory stage s free again
-    __shared__ uint64_t accbar[2];   // accumulator j holds a finished slot
+    __shared__ uint64_t full[NS], empty[NS], ready[2], freed[2];
     __shared__ uint32_t tmem_base;
-    __shared__ int bad;
+    __shared__ volatile int abort_flag;
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr int a_bytes = TC_M * 128, b_bytes = R * 128;
-    constexpr int stage_bytes = 2 * a_bytes + 2 * b_bytes;
-    const int64_t b0 = lo + (int64_t)blockIdx.x * TC_M;
+    const int t0 = blockIdx.x * TC_M;
     const int32_t* sl = slots + (int64_t)blockIdx.x * 344;
     const int ns = sl[0];
-    constexpr int nk = R / TC_KC;
-    const int total = ns * nk;
-    constexpr int ACC = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
-    constexpr uint32_t ncols = 2 * ACC;
+    const int total = ns * NK;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(ncols));
+                     "r"(NCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        bad = 0;
-        for (int k = 0; k < 2; ++k) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[k])));
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&accbar[k])));
+        abort_flag = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&full[s]), TC_PROD + 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(smem_u32(&ready[j]), 1);
+            mbar_init(smem_u32(&freed[j]), TC_EPI);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -134,151 +184,200 @@ __global__ void __launch_bounds__(TC_T, 1) k_m2l_tc(const float* __restrict__ Tm
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tf32_idesc(TC_M, R);
-    uint32_t phase[2] = {0u, 0u}, aphase[2] = {0u, 0u};
-    // this thread's share of the result: row 32*(warp%4)+lane, columns [half*R/2, +R/2)
-    const int q = warp & 3, half = warp >> 2;
-    const uint32_t t_row = (uint32_t)(32 * q) << 16;
-    const int col0 = half * (R / 2);
-    float acc[R / 2];
-#pragma unroll
-    for (int k = 0; k < R / 2; ++k) acc[k] = 0.f;
 
-    // adds accumulator j (finished slot) into acc[]
-    auto drain = [&](int j) -> bool {
-        const bool ok = mbar_wait(smem_u32(&accbar[j]), aphase[j]);
-        aphase[j] ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp >= 8 && warp < 10) {
+        // ---------------- producers ----------------
+        const int p = tid - TC_EPI;          // 0..63: rows p and p + 64 of the tile
+        int box2[2];
+        for (int h = 0; h < 2; ++h) box2[h] = (t0 + p + 64 * h < nbox) ? boxes[t0 + p + 64 * h] : -1;
+        for (int it = 0; it < total; ++it) {
+            const int s = it % NS;
+            if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NS - 1) & 1), &abort_flag)) break;
+            const int slot = sl[1 + it / NK];
+            const int k0 = (it % NK) * TC_KC;
+            unsigned char* st = base + s * STAGE;
+            if (p == 0) {   // B: two pre-swizzled bulk copies (hi, lo) of R x 128 bytes
+                const uint32_t fb = smem_u32(&full[s]);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * B_BYTES)
+                             : "memory");
+                const int64_t off = (int64_t)slot * R * R + (int64_t)(k0 / TC_KC) * R * TC_KC;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(st + 2 * A_BYTES)),
+                    "l"(Thi + off), "r"(B_BYTES), "r"(fb)
+                    : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(st + 2 * A_BYTES + B_BYTES)),
+                    "l"(Tlo + off), "r"(B_BYTES), "r"(fb)
+                    : "memory");
+            }
+            // A: rows p, p + 64 = c[source of the row's box at this slot], chunk k0..k0+31, hi and lo
+            const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
 #pragma unroll
-        for (int cc = 0; cc < R / 2; cc += 16) {
-            uint32_t v[16];
-            const uint32_t ta = tmem + t_row + (uint32_t)(j * ACC + col0 + cc);
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int h = 0; h < 2; ++h) {
+                const int row = p + 64 * h;
+                const int a = box2[h] >= 0 ? vtab[(int64_t)box2[h] * kOffsetSlots + slot] : -1;
+                const uint32_t nbytes = a >= 0 ? 16u : 0u;   // 0: zero fill
+                const int64_t src = (int64_t)(a >= 0 ? a : 0) * R + k0;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) acc[cc + k] += __uint_as_float(v[k]);
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t o = sw128_off(row, 4 * j);
+                    cp_async16(ah + o, chi + src + 4 * j, nbytes);
+                    cp_async16(al + o, clo + src + 4 * j, nbytes);
+                }
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        return ok;
-    };
-
-    for (int it = 0; it < total; ++it) {
-        const int s = it & 1;
-        const int si = it / nk, kc = it % nk;
-        unsigned char* A_hi = base + s * stage_bytes;
-        unsigned char* A_lo = A_hi + a_bytes;
-        unsigned char* B_hi = A_lo + a_bytes;
-        unsigned char* B_lo = B_hi + b_bytes;
-        if (it >= 2) {   // the MMAs of iteration it-2 read this stage: wait until they are done
-            const int timed_out = mbar_wait(smem_u32(&mbar[s]), phase[s]) ? 0 : 1;
-            phase[s] ^= 1u;
-            if (__syncthreads_or(timed_out)) {   // uniform decision for the whole CTA
-                if (tid == 0) bad = 1;
-                break;
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    } else if (warp == 10) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tf32_idesc(TC_M, R);
+            uint32_t fphase[NS] = {};
+            for (int si = 0; si < ns && !abort_flag; ++si) {
+                const int j = si & 1;
+                if (si >= 2 && !mbar_wait(smem_u32(&freed[j]), (uint32_t)(((si - 2) >> 1) & 1), &abort_flag)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t dacc = tmem + (uint32_t)(j * ACC);
+                bool ok = true;
+                for (int kc = 0; kc < NK; ++kc) {
+                    const int it = si * NK + kc, s = it % NS;
+                    if (!mbar_wait(smem_u32(&full[s]), fphase[s], &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fphase[s] ^= 1u;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned char* st = base + s * STAGE;
+                    const uint32_t ah = smem_u32(st), al = ah + A_BYTES, bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
+#pragma unroll
+                    for (int k = 0; k < TC_KC / 8; ++k) {
+                        const uint32_t ko = 32u * k;   // 8 TF32 = 32 bytes along K inside the swizzle row
+                        const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                        mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
+                        mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                        mma_tf32(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(&ready[j]));
             }
         }
-        const int slot = sl[1 + si];
-        const int k0 = kc * TC_KC;
-        // A: 128 gathered rows x 8 chunks of 16 bytes
-        for (int e = tid; e < TC_M * 8; e += TC_T) {
-            const int row = e >> 3, j = e & 7;
-            const int64_t b = b0 + row;
-            const int a = (b < hi) ? vtab[b * kOffsetSlots + slot] : -1;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a >= 0) v = *reinterpret_cast<const float4*>(c + (int64_t)a * R + k0 + 4 * j);
-            store_split(A_hi, A_lo, row, j, v);
-        }
-        // B: R rows of T[slot] x 8 chunks
-        const float* Ts = Tm + (int64_t)slot * R * R;
-        for (int e = tid; e < R * 8; e += TC_T) {
-            const int row = e >> 3, j = e & 7;
-            float4 v = *reinterpret_cast<const float4*>(Ts + (int64_t)row * R + k0 + 4 * j);
-            store_split(B_hi, B_lo, row, j, v);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+        __syncwarp();
+    } else {
+        // ---------------- epilogue: warps 0-7 ----------------
+        const int q = warp & 3, half = warp >> 2;
+        const uint32_t t_row = (uint32_t)(32 * q) << 16;
+        const int col0 = half * (R / 2);
+        float acc[R / 2];
+#pragma unroll
+        for (int k = 0; k < R / 2; ++k) acc[k] = 0.f;
+        for (int si = 0; si < ns; ++si) {
+            const int j = si & 1;
+            const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((si >> 1) & 1), &abort_flag);
+            if (__any_sync(0xffffffffu, !ok)) break;   // warp-uniform exit (tcgen05.ld is .sync.aligned)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(A_hi), al = smem_u32(A_lo), bh = smem_u32(B_hi), bl = smem_u32(B_lo);
-            const uint32_t dacc = tmem + (uint32_t)((si & 1) * ACC);
 #pragma unroll
-            for (int k = 0; k < TC_KC / 8; ++k) {
-                const uint32_t ko = 32u * k;   // 8 TF32 = 32 bytes along K inside the swizzle atom
-                const uint32_t first = (kc > 0 || k > 0) ? 1u : 0u;
-                mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, first);
-                mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                mma_tf32(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+            for (int cc = 0; cc < R / 2; cc += 16) {
+                uint32_t v[16];
+                const uint32_t ta = tmem + t_row + (uint32_t)(j * ACC + col0 + cc);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int k = 0; k < 16; ++k) acc[cc + k] += __uint_as_float(v[k]);
             }
-            mma_commit(smem_u32(&mbar[s]));
-            if (kc == nk - 1) mma_commit(smem_u32(&accbar[si & 1]));
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&freed[j]));
         }
-        if (kc == 0 && si >= 1) {   // the previous slot's accumulator, while this slot's MMAs run
-            const int timed_out = drain((si - 1) & 1) ? 0 : 1;
-            if (__syncthreads_or(timed_out)) {
-                if (tid == 0) bad = 1;
-                break;
-            }
-        }
-    }
-    // drain: the last slot's accumulator, then the last commit of each used stage (also
-    // after a timeout, so that the MMAs in flight finish before the tensor memory is freed)
-    __syncthreads();
-    int timed_out = 0;
-    if (!bad && ns > 0 && !drain((ns - 1) & 1)) timed_out = 1;
-    for (int s = 0; s < 2; ++s)
-        if (s < total && !mbar_wait(smem_u32(&mbar[s]), phase[s])) timed_out = 1;
-    if (__syncthreads_or(timed_out) && tid == 0) bad = 1;
-    __syncthreads();
-    if (!bad) {
-        const int64_t b = b0 + 32 * q + lane;
-        if (b < hi) {
-            float4* o = reinterpret_cast<float4*>(d + b * R + col0);
+        const int bi = t0 + 32 * q + lane;
+        if (!abort_flag && bi < nbox) {
+            float4* o = reinterpret_cast<float4*>(d + (int64_t)boxes[bi] * R + col0);
 #pragma unroll
             for (int k = 0; k < R / 8; ++k) o[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
         }
-    } else if (tid == 0) {
-        atomicExch(err, 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
+    if (abort_flag && tid == 0) atomicExch(err, 1);
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOLS));
 }
 
-size_t m2l_tc_smem(int R) { return 1024 + 2 * (size_t)(2 * TC_M * 128 + 2 * R * 128); }
+// ------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------
+static int stages_for(int R) {
+    const size_t stage = 2 * (size_t)TC_M * 128 + 2 * (size_t)R * 128;
+    const size_t avail = 227 * 1024 - 1024 - 1024;
+    int ns = (int)(avail / stage);
+    return ns > 4 ? 4 : ns;
+}
 
-int m2l_tc_supported(int R) { return (R % 32 == 0 && R >= 32 && R <= 256 && m2l_tc_smem(R) <= 227 * 1024) ? 1 : 0; }
+size_t m2l_tc_smem(int R) {
+    const size_t stage = 2 * (size_t)TC_M * 128 + 2 * (size_t)R * 128;
+    return 1024 + (size_t)stages_for(R) * stage;
+}
 
-template <int NC>
-static int launch_nc(cudaStream_t st, const float* Tm, const int32_t* vtab, const int32_t* slots, int64_t lo,
-                     int64_t hi, const float* c, float* d, int* err, int64_t ntiles) {
-    const size_t smem = m2l_tc_smem(32 * NC);
-    static bool configured = false;   // one attribute per instantiation (its size never changes)
-    if (!configured) {
-        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured = true;
-    }
-    k_m2l_tc<NC><<<(unsigned)ntiles, TC_T, smem, st>>>(Tm, vtab, slots, lo, hi, c, d, err);
+int m2l_tc_supported(int R) { return (R % 32 == 0 && R >= 32 && R <= 256 && stages_for(R) >= 2) ? 1 : 0; }
+
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, float* Thi, float* Tlo) {
+    const int64_t n = (int64_t)kOffsetSlots * R * R;
+    k_swizzle_T<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, R, Thi, Tlo);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
-int launch_m2l_tc(cudaStream_t st, const float* Tm, int R, const int32_t* vtab, const int32_t* slots, int64_t lo,
-                  int64_t hi, const float* c, float* d, int* err) {
-    const int64_t ntiles = (hi - lo + TC_M - 1) / TC_M;
-    if (ntiles <= 0) return KIFMM_OK;
+int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float* clo) {
+    k_split_c<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, n, chi, clo);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+template <int NC, int NS>
+static int launch_cfg(cudaStream_t st, const float* Thi, const float* Tlo, const int32_t* boxes, int nbox,
+                      const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d,
+                      int* err) {
+    const size_t smem = m2l_tc_smem(32 * NC);
+    static bool configured = false;   // one attribute per instantiation (its size never changes)
+    if (!configured) {
+        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    const int ntiles = (nbox + TC_M - 1) / TC_M;
+    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+template <int NC>
+static int launch_nc(cudaStream_t st, const float* Thi, const float* Tlo, const int32_t* boxes, int nbox,
+                     const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
+    switch (stages_for(32 * NC)) {
+        case 2: return launch_cfg<NC, 2>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 3: return launch_cfg<NC, 3>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        default: return launch_cfg<NC, 4>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+    }
+}
+
+int launch_m2l_tc(cudaStream_t st, const float* Thi, const float* Tlo, int R, const int32_t* boxes, int nbox,
+                  const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
+    if (nbox <= 0) return KIFMM_OK;
     switch (R / 32) {
-        case 1: return launch_nc<1>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 2: return launch_nc<2>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 3: return launch_nc<3>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 4: return launch_nc<4>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 5: return launch_nc<5>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 6: return launch_nc<6>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 7: return launch_nc<7>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
-        case 8: return launch_nc<8>(st, Tm, vtab, slots, lo, hi, c, d, err, ntiles);
+        case 1: return launch_nc<1>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 2: return launch_nc<2>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 3: return launch_nc<3>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 4: return launch_nc<4>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 5: return launch_nc<5>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 6: return launch_nc<6>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 7: return launch_nc<7>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 8: return launch_nc<8>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
         default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
     }
 }

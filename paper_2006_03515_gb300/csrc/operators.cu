@@ -2,6 +2,8 @@
 // (Eqs. (s2m), (m2m), (m2l), (l2l), (s2l) of the paper), their truncated-SVD
 // pseudo-inverses, and the self-cell values of the discrete kernel G (Sec. 3).
 #include <algorithm>
+#include <cstdlib>
+#include <string>
 #include <cmath>
 
 #include "internal.cuh"
@@ -277,6 +279,10 @@ int build_operators(Plan& p) {
     }
     const int R = (rmax + 31) / 32 * 32;
     p.R = R;
+    {
+        const char* m2l = std::getenv("KIFMM_M2L");
+        p.m2l_tensor = p.precision == KIFMM_MIXED && m2l_tc_supported(R) && !(m2l && std::string(m2l) == "simt");
+    }
     const int64_t SR = (int64_t)S * R, RR = (int64_t)R * R;
     for (int l = 2; l < L; ++l) {
         LevelOps& op = p.ops[l];
@@ -359,7 +365,13 @@ int build_operators(Plan& p) {
     if (p.precision == KIFMM_MIXED) {
         for (int l = 2; l < L; ++l) {
             LevelOps& op = p.ops[l];
-            KF_TRY(f32_copy(st, op.T, op.T32, kOffsetSlots * RR));
+            if (p.m2l_tensor) {
+                KF_TRY(dev_alloc(op.Thi, kOffsetSlots * RR * 4));
+                KF_TRY(dev_alloc(op.Tlo, kOffsetSlots * RR * 4));
+                KF_TRY(m2l_tc_prepare(st, ptr<double>(op.T), R, ptr<float>(op.Thi), ptr<float>(op.Tlo)));
+            } else {
+                KF_TRY(f32_copy(st, op.T, op.T32, kOffsetSlots * RR));
+            }
             KF_TRY(f32_copy(st, op.Ub, op.Ub32, SR));
             KF_TRY(f32_copy(st, op.Vb, op.Vb32, SR));
             KF_TRY(f32_copy(st, op.Vt, op.Vt32, SR));
