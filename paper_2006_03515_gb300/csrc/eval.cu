@@ -218,27 +218,6 @@ int build_eval_data(Plan& p) {
             m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, nullptr, ptr<int32_t>(L.m2l_slots));
             KF_LAUNCH();
         }
-        if (p.m2l_tensor && cnt > 0) {
-            // boxes grouped by their octant inside the parent (same set of V offsets), Morton
-            // order within a group; tiles of 128 over this order
-            KF_TRY(dev_alloc(L.m2l_boxes, (size_t)cnt * 4));
-            int32_t done = 0;
-            for (int oc = 0; oc < 8; ++oc) {
-                octant_flags<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.anchor), lo, hi, oc, ptr<int32_t>(flag));
-                KF_LAUNCH();
-                int32_t nsel = 0;
-                KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), cnt, &nsel, st, scan_tmp));
-                compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), lo, cnt,
-                                                              ptr<int32_t>(L.m2l_boxes) + done);
-                KF_LAUNCH();
-                done += nsel;
-            }
-            L.n_tiles128 = (int)((cnt + 127) / 128);
-            KF_TRY(dev_alloc(L.m2l_slots128, (size_t)std::max(L.n_tiles128, 1) * kSlotStride * 4));
-            m2l_tile_slots<<<L.n_tiles128, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128, ptr<int32_t>(L.m2l_boxes),
-                                                         ptr<int32_t>(L.m2l_slots128));
-            KF_LAUNCH();
-        }
         // leaves of this level
         select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 1, 2,
                                                     ptr<int32_t>(flag) + lo);
@@ -263,6 +242,48 @@ int build_eval_data(Plan& p) {
                                                       ptr<int32_t>(L.xboxes));
         KF_LAUNCH();
         L.n_x = tot;
+    }
+    // tensor-core M2L: tiles of 128 boxes over all levels, deepest level first; within a
+    // level the boxes are grouped by their octant inside the parent (one set of offsets)
+    if (p.m2l_tensor) {
+        int64_t nbx = 0;
+        int ntiles = 0;
+        for (int l = 2; l < t.nlevels; ++l) {
+            int64_t c = t.level_start[l + 1] - t.level_start[l];
+            nbx += c;
+            ntiles += (int)((c + 127) / 128);
+        }
+        KF_TRY(dev_alloc(p.tc_boxes, (size_t)std::max<int64_t>(nbx, 1) * 4));
+        KF_TRY(dev_alloc(p.tc_slots, (size_t)std::max(ntiles, 1) * kSlotStride * 4));
+        KF_TRY(dev_alloc(p.tc_tiles, (size_t)std::max(ntiles, 1) * sizeof(int4)));
+        std::vector<int4> tiles;
+        int64_t off = 0;
+        for (int l = t.nlevels - 1; l >= 2; --l) {
+            const int64_t lo = t.level_start[l], hi = t.level_start[l + 1], cnt = hi - lo;
+            if (cnt <= 0) continue;
+            int32_t done = 0;
+            for (int oc = 0; oc < 8; ++oc) {
+                octant_flags<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.anchor), lo, hi, oc, ptr<int32_t>(flag));
+                KF_LAUNCH();
+                int32_t nsel = 0;
+                KF_TRY(device_scan_i32(ptr<int32_t>(flag), ptr<int32_t>(pos), cnt, &nsel, st, scan_tmp));
+                compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag), ptr<int32_t>(pos), lo, cnt,
+                                                              ptr<int32_t>(p.tc_boxes) + off + done);
+                KF_LAUNCH();
+                done += nsel;
+            }
+            const int nt = (int)((cnt + 127) / 128);
+            m2l_tile_slots<<<nt, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128, ptr<int32_t>(p.tc_boxes) + off,
+                                               ptr<int32_t>(p.tc_slots) + (int64_t)tiles.size() * kSlotStride);
+            KF_LAUNCH();
+            for (int k = 0; k < nt; ++k)
+                tiles.push_back(make_int4(l, (int)(off + 128 * k), (int)std::min<int64_t>(128, cnt - 128 * k), 0));
+            off += cnt;
+        }
+        p.tc_ntiles = (int)tiles.size();
+        if (!tiles.empty())
+            KF_CUDA(cudaMemcpyAsync(p.tc_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        KF_CUDA(cudaStreamSynchronize(st));
     }
     // workspace
     const int R = p.R;
@@ -388,7 +409,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
 // Tile: 64 rows x 32 boxes, k-chunks of 16; each thread 2 rows x 4 boxes.
 constexpr int AP_TM = 64, AP_TN = 32, AP_TK = 16;
 template <class T>
-__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int Mo, int Ki, const int32_t* src,
+__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int ldop, int Mo, int Ki, const int32_t* src,
                                                const int32_t* dst, int64_t base, int count,
                                                const T* __restrict__ in, int ldi, T* out, int ldo, int accumulate) {
     __shared__ T As[AP_TK][AP_TM + 1];
@@ -400,7 +421,7 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int Mo,
         for (int e = tid; e < AP_TM * AP_TK; e += 256) {
             int rr = e / AP_TK, kk = e % AP_TK;
             int row = row0 + rr, k = k0 + kk;
-            As[kk][rr] = (row < Mo && k < Ki) ? Op[(int64_t)row * Ki + k] : T(0);
+            As[kk][rr] = (row < Mo && k < Ki) ? Op[(int64_t)row * ldop + k] : T(0);
         }
         for (int e = tid; e < AP_TN * AP_TK; e += 256) {
             int cc = e / AP_TK, kk = e % AP_TK;
@@ -742,6 +763,88 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(EvalView E, const int32_t* leaves
     }
 }
 
+// Near field, mixed form: the same sum as k_p2p<true> with two targets per thread, so that
+// every source read from shared memory serves two pair evaluations. 128 threads per leaf:
+// lane = target pair (targets t and t + 32 of a 64-target chunk), warp = source group.
+// Sources carry q * norm, so a pair costs (e^{-aR} - e^{-bR}) * (q norm) / R^3.
+constexpr int P2Q_T = 128, P2Q_GRP = 4;
+__device__ __forceinline__ void p2q_pair(const float4& x, const float4& v, const KParams& kp, Kahan& acc) {
+    const float dx = x.x - v.x, dy = x.y - v.y, dz = x.z - v.z;
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    const float rinv = rsqrt_approx(r2);
+    const float R = r2 * rinv;
+    const float w = v.w * rinv * rinv * rinv;
+    const float val = exp_diff_f32(R, kp) * w;
+    acc.add(r2 > 0.f ? val : 0.f);   // j == i gives r2 == 0 exactly; points are distinct
+}
+
+template <class TO>
+__global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* leaves, const int32_t* uoff,
+                                                     const int32_t* uitems, const double* q, const double* far,
+                                                     const double* sigma, const double* Is, const int32_t* perm,
+                                                     double C, TO* out) {
+    const int B = leaves[blockIdx.x];
+    const double* cB = E.centre + 3 * (int64_t)B;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* s32 = reinterpret_cast<float4*>(smem_raw);
+    __shared__ double red[P2Q_GRP][64];
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    const int tp = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int u0 = uoff[B], u1 = uoff[B + 1];
+    const float nrm = E.kp.norm_f;
+    for (int t0 = p0; t0 < p1; t0 += 64) {
+        const int i0 = t0 + tp, i1 = t0 + tp + 32;
+        const bool a0 = i0 < p1, a1 = i1 < p1;
+        const float4 far4 = make_float4(1e30f, 1e30f, 1e30f, 0.f);   // inactive slot: never near a source
+        const float4 x0 = a0 ? E.loc[i0] : far4, x1 = a1 ? E.loc[i1] : far4;
+        Kahan k0, k1;
+        int ui = u0, uoffs = 0;
+        while (ui < u1) {
+            __syncthreads();
+            int ns = 0, wi = ui, wo = uoffs;
+            while (wi < u1 && ns < P2P_CHUNK) {
+                const int A = uitems[wi];
+                const int aa = E.pstart[A], ab = E.pend[A];
+                const int take = min(ab - aa - wo, P2P_CHUNK - ns);
+                const double* cA = E.centre + 3 * (int64_t)A;
+                const float d0 = (float)(cA[0] - cB[0]), d1 = (float)(cA[1] - cB[1]), d2 = (float)(cA[2] - cB[2]);
+                for (int e = threadIdx.x; e < take; e += P2Q_T) {
+                    const float4 v = E.loc[aa + wo + e];
+                    s32[ns + e] = make_float4(v.x + d0, v.y + d1, v.z + d2, (float)q[aa + wo + e] * nrm);
+                }
+                ns += take;
+                wo += take;
+                if (wo >= ab - aa) {
+                    ++wi;
+                    wo = 0;
+                }
+            }
+            __syncthreads();
+#pragma unroll 4
+            for (int e = g; e < ns; e += P2Q_GRP) {
+                const float4 v = s32[e];
+                p2q_pair(x0, v, E.kp, k0);
+                p2q_pair(x1, v, E.kp, k1);
+            }
+            ui = wi;
+            uoffs = wo;
+        }
+        red[g][tp] = k0.value();
+        red[g][tp + 32] = k1.value();
+        __syncthreads();
+        if (g < 2) {
+            const int tl = tp + 32 * g;
+            const int i = t0 + tl;
+            if (i < p1) {
+                double s = 0;
+                for (int k = 0; k < P2Q_GRP; ++k) s += red[k][tl];
+                out[perm[i]] = (TO)(C * (s + far[i] + sigma[i] * Is[i]));
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------------------------
 // driver
 // ------------------------------------------------------------------------------------
@@ -768,12 +871,13 @@ template <class T> static const T* sel(const DevBuf& d64, const DevBuf& d32);
 template <> const double* sel<double>(const DevBuf& d64, const DevBuf&) { return ptr<double>(d64); }
 template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return ptr<float>(d32); }
 
+// Op has row stride ldop; only its leading Mo x Ki block is applied (the rest is zero padding).
 template <class T>
-static int launch_apply(cudaStream_t st, const T* Op, int Mo, int Ki, const int32_t* src, const int32_t* dst,
+static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, const int32_t* src, const int32_t* dst,
                         int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc) {
     if (count <= 0) return KIFMM_OK;
     dim3 g(nbk(count, AP_TN), nbk(Mo, AP_TM));
-    k_apply<T><<<g, 256, 0, st>>>(Op, Mo, Ki, src, dst, base, count, in, ldi, out, ldo, acc);
+    k_apply<T><<<g, 256, 0, st>>>(Op, ldop, Mo, Ki, src, dst, base, count, in, ldi, out, ldo, acc);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -805,7 +909,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     for (int l = 2; l < L; ++l) {
         auto& LL = p.lv[l];
         if (LL.n_leaf > 0)
-            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), R, S, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs),
+            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs),
                                      0, LL.n_leaf, ptr<double>(p.chk), S, cu, R, 0));
     }
     mark(p, 2);
@@ -813,7 +917,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         auto& LL = p.lv[l];
         for (int o = 0; o < 8; ++o)
             if (LL.n_m2m[o] > 0)
-                RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A) + (int64_t)o * R * R, R, R,
+                RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A) + (int64_t)o * R * R, R, p.ops[l].rank, p.ops[l + 1].rank,
                                          ptr<int32_t>(LL.m2m_src[o]), ptr<int32_t>(LL.m2m_dst[o]), 0, LL.n_m2m[o], cu,
                                          R, cu, R, 1));
     }
@@ -833,22 +937,26 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     } else {
         c = reinterpret_cast<const T*>(cu);
     }
-    for (int l = 2; l < L; ++l) {
-        auto& LL = p.lv[l];
-        if (LL.n_tiles == 0) continue;
-        if (sizeof(T) == 4 && p.m2l_tensor) {
-            KF_TRY(launch_m2l_tc(st, ptr<float>(p.ops[l].Thi), ptr<float>(p.ops[l].Tlo), R, ptr<int32_t>(LL.m2l_boxes),
-                                 (int)(t.level_start[l + 1] - t.level_start[l]), ptr<int32_t>(p.vtab),
-                                 ptr<int32_t>(LL.m2l_slots128), ptr<float>(p.chi), ptr<float>(p.clo),
-                                 reinterpret_cast<float*>(dd), ptr<int>(p.err)));
-            ++nl;
-            continue;
+    if (sizeof(T) == 4 && p.m2l_tensor) {
+        M2LTables tabs{};
+        for (int l = 2; l < L; ++l) {
+            tabs.hi[l] = ptr<float>(p.ops[l].Thi);
+            tabs.lo[l] = ptr<float>(p.ops[l].Tlo);
         }
-        dim3 g(LL.n_tiles, nbk(R, M2L_TM));
-        k_m2l<T><<<g, 256, 0, st>>>(sel<T>(p.ops[l].T, p.ops[l].T32), R, ptr<int32_t>(p.vtab),
-                                    ptr<int32_t>(LL.m2l_slots), t.level_start[l], t.level_start[l + 1], c, dd);
-        KF_LAUNCH();
+        KF_TRY(launch_m2l_tc(st, tabs, R, ptr<int4>(p.tc_tiles), p.tc_ntiles, ptr<int32_t>(p.tc_boxes),
+                             ptr<int32_t>(p.vtab), ptr<int32_t>(p.tc_slots), ptr<float>(p.chi), ptr<float>(p.clo),
+                             reinterpret_cast<float*>(dd), ptr<int>(p.err)));
         ++nl;
+    } else {
+        for (int l = 2; l < L; ++l) {
+            auto& LL = p.lv[l];
+            if (LL.n_tiles == 0) continue;
+            dim3 g(LL.n_tiles, nbk(R, M2L_TM));
+            k_m2l<T><<<g, 256, 0, st>>>(sel<T>(p.ops[l].T, p.ops[l].T32), R, ptr<int32_t>(p.vtab),
+                                        ptr<int32_t>(LL.m2l_slots), t.level_start[l], t.level_start[l + 1], c, dd);
+            KF_LAUNCH();
+            ++nl;
+        }
     }
     mark(p, 4);
     // ---- downward: S2L from the X list, L2L (Eq. (l2l)), then phi^d = U Sigma^+ d (Eq. (s2l))
@@ -861,7 +969,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                                   ptr<T>(p.chkx));
             KF_LAUNCH();
             ++nl;
-            RUN(launch_apply<T>(st, sel<T>(op.Vt, op.Vt32), R, S, ptr<int32_t>(LL.xboxes), ptr<int32_t>(LL.xboxes), 0,
+            RUN(launch_apply<T>(st, sel<T>(op.Vt, op.Vt32), S, op.rank, S, ptr<int32_t>(LL.xboxes), ptr<int32_t>(LL.xboxes), 0,
                                 LL.n_x, ptr<T>(p.chkx), S, dd, R, 1));
         }
         if (l >= 3) {
@@ -869,19 +977,19 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             const LevelOps& pop = p.ops[l - 1];
             for (int o = 0; o < 8; ++o)
                 if (LP.n_m2m[o] > 0)
-                    RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32) + (int64_t)o * R * R, R, R,
+                    RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32) + (int64_t)o * R * R, R, op.rank, pop.rank,
                                         ptr<int32_t>(LP.m2m_dst[o]), ptr<int32_t>(LP.m2m_src[o]), 0, LP.n_m2m[o], dd,
                                         R, dd, R, 1));
         }
         if (LL.n_leaf > 0)
-            RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), S, R, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
+            RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), R, S, op.rank, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
                                 LL.n_leaf, dd, R, phid, S, 0));
     }
     // upward equivalent densities phi^u = V c for the W list
     if (p.phiu.p) {
         for (int l = 2; l < L; ++l) {
             const LevelOps& op = p.ops[l];
-            RUN(launch_apply<T>(st, sel<T>(op.Vb, op.Vb32), S, R, nullptr, nullptr, t.level_start[l],
+            RUN(launch_apply<T>(st, sel<T>(op.Vb, op.Vb32), R, S, op.rank, nullptr, nullptr, t.level_start[l],
                                 (int)(t.level_start[l + 1] - t.level_start[l]), c, R, ptr<T>(p.phiu), S, 0));
         }
     }
@@ -934,10 +1042,10 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         unsigned g = (unsigned)p.nleaves;
         if (mixed) {
             if (dtype == KIFMM_F64)
-                k_p2p<true, double><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                k_p2p_mixed<double><<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
                                                             ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (double*)S_out);
             else
-                k_p2p<true, float><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                k_p2p_mixed<float><<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
                                                            ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (float*)S_out);
         } else {
             if (dtype == KIFMM_F64)

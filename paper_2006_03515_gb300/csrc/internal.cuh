@@ -153,6 +153,10 @@ struct Plan {
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
     int64_t eval_launches = 0;   // kernels of the last evaluation
     bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
+    DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
+    DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
+    DevBuf tc_slots;             // [tile][344] active offset slots
+    int tc_ntiles = 0;
     DevBuf err;                  // int: device-side error code (bounded waits)
     int64_t p2p_pairs = 0;       // near-field pairs of one evaluation
     // timing
@@ -180,7 +184,11 @@ int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
 int m2l_tc_supported(int R);
 int m2l_tc_prepare(cudaStream_t st, const double* T, int R, float* Thi, float* Tlo);
 int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float* clo);
-int launch_m2l_tc(cudaStream_t st, const float* Thi, const float* Tlo, int R, const int32_t* boxes, int nbox,
+struct M2LTables {                 // per-level TF32 hi/lo M2L tables for the tensor-core kernel
+    const float* hi[kMaxLevel + 1];
+    const float* lo[kMaxLevel + 1];
+};
+int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err);
 // eval.cu
 int build_eval_data(Plan& p);

@@ -10,6 +10,8 @@ namespace kifmm {
 struct KParams {
     double a, b, bma, norm;   // norm = 1 / (4 pi ln(b/a))
     float a_l2e, bma_l2e, bma_f, norm_f;   // FP32 forms: a*log2(e), (b-a)*log2(e), b-a, norm
+    float b_l2e;                           // b*log2(e)
+    float r_series;                        // 0.5 / (b - a): below it 1 - e^{-(b-a)R} uses the series
 };
 
 inline KParams make_kparams(double a, double b) {
@@ -23,6 +25,8 @@ inline KParams make_kparams(double a, double b) {
     k.bma_l2e = (float)((b - a) * l2e);
     k.bma_f = (float)(b - a);
     k.norm_f = (float)k.norm;
+    k.b_l2e = (float)(b * l2e);
+    k.r_series = (float)(0.5 / (b - a));
     return k;
 }
 
@@ -69,6 +73,14 @@ __device__ __forceinline__ float kern_f32(float r2, const KParams& k) {
     const float ea = ex2_approx(-k.a_l2e * R);
     const float m1 = one_minus_exp_neg(k.bma_f * R, k.bma_l2e * R);
     return ea * m1 * k.norm_f * (rinv * rinv * rinv);
+}
+
+// e^{-aR} - e^{-bR} in FP32. For (b-a)R >= 0.5 the plain difference of the two
+// exponentials (relative error amplified at most 1/(1 - e^{-0.5}) = 2.5x); below, the
+// factored form e^{-aR} (1 - e^{-(b-a)R}) with the series for the bracket.
+__device__ __forceinline__ float exp_diff_f32(float R, const KParams& k) {
+    if (R < k.r_series) return ex2_approx(-k.a_l2e * R) * one_minus_exp_neg(k.bma_f * R, k.bma_l2e * R);
+    return ex2_approx(-k.a_l2e * R) - ex2_approx(-k.b_l2e * R);
 }
 
 }  // namespace kifmm

@@ -143,7 +143,7 @@ __global__ void k_split_c(const double* c, int64_t n, float* chi, float* clo) {
 // ------------------------------------------------------------------------------------
 template <int NC, int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_m2l_tc(const float* __restrict__ Thi, const float* __restrict__ Tlo, const int32_t* __restrict__ boxes, int nbox,
+    k_m2l_tc(M2LTables tabs, const int4* __restrict__ tiles, const int32_t* __restrict__ all_boxes,
              const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const float* __restrict__ chi,
              const float* __restrict__ clo, float* __restrict__ d, int* err) {
     constexpr int R = 32 * NC;
@@ -156,10 +156,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     __shared__ uint64_t full[NS], empty[NS], ready[2], freed[2];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    __shared__ int sl[344];   // [count, slot_0, ...] of this tile
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int t0 = blockIdx.x * TC_M;
-    const int32_t* sl = slots + (int64_t)blockIdx.x * 344;
+    const int4 tile = tiles[blockIdx.x];   // level, first box (index into all_boxes), box count
+    const float* __restrict__ Thi = tabs.hi[tile.x];
+    const float* __restrict__ Tlo = tabs.lo[tile.x];
+    const int32_t* __restrict__ boxes = all_boxes + tile.y;
+    const int nbox = tile.z;
+    const int t0 = 0;
+    for (int e = tid; e < 344; e += TC_THREADS) sl[e] = slots[(int64_t)blockIdx.x * 344 + e];
+    __syncthreads();
     const int ns = sl[0];
     const int total = ns * NK;
 
@@ -190,8 +197,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int p = tid - TC_EPI;          // 0..63: rows p and p + 64 of the tile
         int box2[2];
         for (int h = 0; h < 2; ++h) box2[h] = (t0 + p + 64 * h < nbox) ? boxes[t0 + p + 64 * h] : -1;
+        // source box of each row for the current slot; the next slot's are fetched one slot
+        // ahead so that the index load is off the critical path
+        auto lookup = [&](int si, int h) -> int {
+            return (si < ns && box2[h] >= 0) ? vtab[(int64_t)box2[h] * kOffsetSlots + sl[1 + si]] : -1;
+        };
+        int acur[2] = {lookup(0, 0), lookup(0, 1)};
+        int anext[2] = {lookup(1, 0), lookup(1, 1)};
         for (int it = 0; it < total; ++it) {
             const int s = it % NS;
+            if (it % NK == 0 && it > 0) {
+                const int si = it / NK;
+                acur[0] = anext[0];
+                acur[1] = anext[1];
+                anext[0] = lookup(si + 1, 0);
+                anext[1] = lookup(si + 1, 1);
+            }
             if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NS - 1) & 1), &abort_flag)) break;
             const int slot = sl[1 + it / NK];
             const int k0 = (it % NK) * TC_KC;
@@ -217,7 +238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int row = p + 64 * h;
-                const int a = box2[h] >= 0 ? vtab[(int64_t)box2[h] * kOffsetSlots + slot] : -1;
+                const int a = acur[h];
                 const uint32_t nbytes = a >= 0 ? 16u : 0u;   // 0: zero fill
                 const int64_t src = (int64_t)(a >= 0 ? a : 0) * R + k0;
 #pragma unroll
@@ -341,7 +362,7 @@ int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float*
 }
 
 template <int NC, int NS>
-static int launch_cfg(cudaStream_t st, const float* Thi, const float* Tlo, const int32_t* boxes, int nbox,
+static int launch_cfg(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
                       const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d,
                       int* err) {
     const size_t smem = m2l_tc_smem(32 * NC);
@@ -350,34 +371,33 @@ static int launch_cfg(cudaStream_t st, const float* Thi, const float* Tlo, const
         KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    const int ntiles = (nbox + TC_M - 1) / TC_M;
-    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots, chi, clo, d, err);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
 template <int NC>
-static int launch_nc(cudaStream_t st, const float* Thi, const float* Tlo, const int32_t* boxes, int nbox,
+static int launch_nc(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
                      const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
     switch (stages_for(32 * NC)) {
-        case 2: return launch_cfg<NC, 2>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 3: return launch_cfg<NC, 3>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        default: return launch_cfg<NC, 4>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 2: return launch_cfg<NC, 2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 3: return launch_cfg<NC, 3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        default: return launch_cfg<NC, 4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
     }
 }
 
-int launch_m2l_tc(cudaStream_t st, const float* Thi, const float* Tlo, int R, const int32_t* boxes, int nbox,
+int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
-    if (nbox <= 0) return KIFMM_OK;
+    if (ntiles <= 0) return KIFMM_OK;
     switch (R / 32) {
-        case 1: return launch_nc<1>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 2: return launch_nc<2>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 3: return launch_nc<3>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 4: return launch_nc<4>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 5: return launch_nc<5>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 6: return launch_nc<6>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 7: return launch_nc<7>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
-        case 8: return launch_nc<8>(st, Thi, Tlo, boxes, nbox, vtab, slots, chi, clo, d, err);
+        case 1: return launch_nc<1>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 2: return launch_nc<2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 3: return launch_nc<3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 4: return launch_nc<4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 5: return launch_nc<5>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 6: return launch_nc<6>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 7: return launch_nc<7>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 8: return launch_nc<8>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
         default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
     }
 }
