@@ -179,6 +179,36 @@ int kifmm_get_sigma(kifmm_plan_t plan, double* sigma);
  * L2P+M2P, P2P]. Returns the number of phases written (<= cap). */
 int kifmm_get_phase_times(kifmm_plan_t plan, float* ms, int cap);
 
+/* ---- evaluation without device allocation ---- */
+
+/* Largest point count kifmm_direct_noalloc accepts (its fixed work space: 8 bytes per point). */
+#define KIFMM_NOALLOC_MAX_POINTS 65536
+
+/*
+ * The same sum as kifmm_eval for cells of one edge h, evaluated directly (every pair,
+ * FP64) and without allocating device memory:
+ *   S_dev[i] = C * ( sum_{j != i} K(|x_i - x_j|) I_j h^3  +  sigma(h) I_i ).
+ * The paper has no counterpart of this entry point. It serves callers that cannot
+ * allocate device memory when they need S: a stream that is being captured into a CUDA
+ * graph, a real-time loop that forbids allocation after start-up, or a process whose
+ * device memory belongs to another allocator. Its only work space is a fixed array in
+ * device memory (KIFMM_NOALLOC_MAX_POINTS + 32 doubles, about 512 KB) that every GPU
+ * loading this library holds until the process exits.
+ *
+ *   points_dev  device, n x 3 FP64 cell centres (distinct); n <= KIFMM_NOALLOC_MAX_POINTS
+ *   h           cell edge (> 0); a, b as in kifmm_plan; C scale; self_mode as kifmm_opts
+ *   I_dev, S_dev  device, n FP64 each (S fully overwritten)
+ *   stream      cudaStream_t (NULL = default stream); the call is asynchronous on it.
+ * The first call on a device looks up the work space's device address (with that
+ * device current); make that first call before any stream capture. Every call shares
+ * the work space and writes it before reading it, so nothing carries over from one call
+ * to the next, but calls that overlap on the GPU (other streams, other threads) race on
+ * it and must be serialised by the caller. Returns KIFMM_ERR_ARG for n beyond the limit
+ * or invalid arguments, KIFMM_ERR_CUDA if a launch fails. Calls no cudaMalloc/cudaFree.
+ */
+int kifmm_direct_noalloc(const double* points_dev, int64_t n, double h, const double* I_dev, double* S_dev,
+                         double a, double b, double C, int self_mode, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 
 #include "internal.cuh"
 #include "kernel.cuh"
+#include "selfcell.cuh"
 
 namespace kifmm {
 
@@ -386,92 +387,19 @@ int build_operators(Plan& p) {
 // ------------------------------------------------------------------------------------
 // self-cell values sigma(h) (discrete kernel G, i == j)
 // ------------------------------------------------------------------------------------
-// E1(x), x > 0: Abramowitz & Stegun 5.1.11 (power series) for x <= 1, and the
-// continued fraction 5.1.22 in its even-contracted form, evaluated with the
-// modified Lentz method, for x > 1.
-__device__ double e1_dev(double x) {
-    if (x <= 1.0) {
-        double s = 0.0, term = 1.0;
-        for (int n = 1; n < 60; ++n) {
-            term *= -x / n;
-            double add = -term / n;
-            s += add;
-            if (fabs(add) < 1e-18 * fmax(1.0, fabs(s))) break;
-        }
-        return -0.57721566490153286061 - log(x) + s;
-    }
-    const double tiny = 1e-300;
-    double bq = x + 1.0, c = 1.0 / tiny, d = 1.0 / bq, h = d;
-    for (int i = 1; i < 10000; ++i) {
-        double an = -(double)i * i;
-        bq += 2.0;
-        d = 1.0 / (an * d + bq);
-        c = bq + an / c;
-        double del = c * d;
-        h *= del;
-        if (fabs(del - 1.0) < 1e-16) break;
-    }
-    return h * exp(-x);
-}
-
-// Gauss-Legendre nodes/weights on [-1, 1] by Newton's method on the three-term
-// recurrence of the Legendre polynomials.
 __global__ void gauss_legendre(int n, double* x, double* w) {
     int i = threadIdx.x;
-    if (i >= n) return;
-    double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
-    double pp = 0;
-    for (int it = 0; it < 100; ++it) {
-        double p1 = 1.0, p2 = 0.0;
-        for (int k = 1; k <= n; ++k) {
-            double p3 = p2;
-            p2 = p1;
-            p1 = ((2.0 * k - 1.0) * z * p2 - (k - 1.0) * p3) / k;
-        }
-        pp = n * (z * p1 - p2) / (z * z - 1.0);
-        double z1 = z;
-        z = z1 - p1 / pp;
-        if (fabs(z - z1) < 1e-16) break;
-    }
-    x[i] = -z;
-    w[i] = 2.0 / ((1.0 - z * z) * pp * pp);
+    if (i < n) gl_node(n, i, &x[i], &w[i]);
 }
 
-// One block per distinct cell edge h: sigma = 6 * sum_{ij} w_i w_j (h/2)/R^3 F(R) / (4 pi ln(b/a)),
-// R = sqrt(u_i^2 + u_j^2 + h^2/4), u = (h/2) t, F(R) = ln(b/a) + E1(bR) - E1(aR)  (cell_exact);
-// or the paper's 2-point Gauss-Legendre value h^3 * 3 g(rho) / (pi * 3h^2), rho = h/2.
+// One block (256 threads) per distinct cell edge.
 __global__ void self_sigma(const double* hs, int nh, double a, double b, int mode, int nq,
                            const double* gx, const double* gw, double* out) {
     int k = blockIdx.x;
     if (k >= nh) return;
-    double h = hs[k];
-    double lba = log(b / a);
-    if (mode == KIFMM_SELF_PAPER_GL2) {
-        if (threadIdx.x == 0) {
-            double s2 = 3.0 * h * h;
-            double rho = sqrt(s2 / 12.0);
-            double g = (exp(-a * rho) - exp(-b * rho)) / (rho * lba);
-            out[k] = h * h * h * 3.0 * g / (3.14159265358979323846 * s2);
-        }
-        return;
-    }
     __shared__ double red[256];
-    double acc = 0;
-    for (int e = threadIdx.x; e < nq * nq; e += blockDim.x) {
-        int i = e / nq, j = e % nq;
-        double ui = 0.5 * h * gx[i], uj = 0.5 * h * gx[j];
-        double wi = 0.5 * h * gw[i], wj = 0.5 * h * gw[j];
-        double R = sqrt(ui * ui + uj * uj + 0.25 * h * h);
-        double F = lba + e1_dev(b * R) - e1_dev(a * R);
-        acc += wi * wj * (0.5 * h) / (R * R * R) * F;
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[k] = 6.0 * red[0] / (4.0 * 3.14159265358979323846 * lba);
+    double s = self_sigma_block(hs[k], a, b, mode, nq, gx, gw, red);
+    if (threadIdx.x == 0) out[k] = s;
 }
 
 __global__ void h_bits(const double* h, const int32_t* perm, int64_t n, uint64_t* key, int32_t* val) {

@@ -56,7 +56,7 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
            "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
-           "kifmm_get_sigma", "kifmm_get_phase_times"]
+           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc"]
 
 _lib = None
 
@@ -89,8 +89,10 @@ def load():
     L.kifmm_get_list.argtypes = [vp, i32, vp, vp]
     L.kifmm_get_sigma.argtypes = [vp, vp]
     L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
+    L.kifmm_direct_noalloc.argtypes = [vp, i64, dbl, vp, vp, dbl, dbl, dbl, i32, vp]
     for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_get_info",
-                 "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times"):
+                 "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times",
+                 "kifmm_direct_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -220,6 +222,23 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_MAX_POINTS = 65536
+
+
+def direct_noalloc(points, h, I, a, b, C=1.0, S=None, self_mode="cell_exact", stream=None):
+    """Direct FP64 sum for cells of one edge h through kifmm_direct_noalloc, which uses a
+    fixed device work space instead of allocating (for callers that cannot allocate, e.g.
+    inside a stream capture). points, I (and S) are CUDA float64 tensors; n <= 65536."""
+    import torch
+    pts = points.contiguous()
+    if S is None:
+        S = torch.empty_like(I)
+    _check(load().kifmm_direct_noalloc(ctypes.c_void_p(pts.data_ptr()), int(pts.shape[0]), float(h),
+                                       ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(S.data_ptr()), float(a),
+                                       float(b), float(C), SELF_MODE[self_mode], _stream_ptr(stream)))
+    return S
 
 
 def eval_batch(plans, Is, Ss, C=None, capture=False):
