@@ -43,7 +43,7 @@ static void free_plan(Plan* p) {
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
-                          &L.m2l_slots128, &L.m2l_boxes})
+                          &L.m2l_slots128, &L.m2l_boxes, &L.parents, &L.par_kids})
             dev_free(*b);
         for (int o = 0; o < 8; ++o) {
             dev_free(L.m2m_src[o]);

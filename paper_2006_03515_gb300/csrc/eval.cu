@@ -95,6 +95,13 @@ __global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int 
     }
 }
 
+__global__ void kid_table(const int32_t* child, const int32_t* parents, int n, int32_t* kids) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int P = parents[k];
+    for (int o = 0; o < 8; ++o) kids[(int64_t)o * n + k] = child[8 * (int64_t)P + o];
+}
+
 __global__ void octant_flags(const int32_t* anchor, int64_t lo, int64_t hi, int oc, int32_t* flag) {
     int64_t b = lo + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= hi) return;
@@ -217,6 +224,25 @@ int build_eval_data(Plan& p) {
         if (L.n_tiles > 0) {
             m2l_tile_slots<<<L.n_tiles, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, tb, nullptr, ptr<int32_t>(L.m2l_slots));
             KF_LAUNCH();
+        }
+        // non-leaf boxes of this level and their children per octant (-1: empty octant)
+        select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 0, 2,
+                                                    ptr<int32_t>(flag) + lo);
+        KF_LAUNCH();
+        {
+            int32_t npar = 0;
+            KF_TRY(device_scan_i32(ptr<int32_t>(flag) + lo, ptr<int32_t>(pos), cnt, &npar, st, scan_tmp));
+            KF_TRY(dev_alloc(L.parents, (size_t)std::max(npar, 1) * 4));
+            KF_TRY(dev_alloc(L.par_kids, (size_t)std::max(npar, 1) * 8 * 4));
+            compact_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(flag) + lo, ptr<int32_t>(pos), lo, cnt,
+                                                          ptr<int32_t>(L.parents));
+            KF_LAUNCH();
+            if (npar > 0) {
+                kid_table<<<nbk(npar, 256), 256, 0, st>>>(ptr<int32_t>(t.child), ptr<int32_t>(L.parents), npar,
+                                                          ptr<int32_t>(L.par_kids));
+                KF_LAUNCH();
+            }
+            L.n_par = npar;
         }
         // leaves of this level
         select_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(t.level), ptr<int32_t>(t.leaf), lo, hi, 1, 2,
@@ -403,56 +429,64 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
     }
 }
 
-// out[dst(c)][row] (+)= sum_k Op[row][k] * in[src(c)][k] for row < Mo, k < Ki, c < count:
-// one translation matrix applied to many boxes (a GEMM whose columns are gathered and
-// scattered by box index). src/dst NULL means the contiguous range base + c.
-// Tile: 64 rows x 32 boxes, k-chunks of 16; each thread 2 rows x 4 boxes.
-constexpr int AP_TM = 64, AP_TN = 32, AP_TK = 16;
-template <class T>
-__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int ldop, int Mo, int Ki, const int32_t* src,
-                                               const int32_t* dst, int64_t base, int count,
-                                               const T* __restrict__ in, int ldi, T* out, int ldo, int accumulate) {
-    __shared__ T As[AP_TK][AP_TM + 1];
-    __shared__ T Bs[AP_TK][AP_TN + 1];
-    const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-    const int row0 = blockIdx.y * AP_TM, col0 = blockIdx.x * AP_TN;
-    T acc[2][4] = {};
-    for (int k0 = 0; k0 < Ki; k0 += AP_TK) {
-        for (int e = tid; e < AP_TM * AP_TK; e += 256) {
-            int rr = e / AP_TK, kk = e % AP_TK;
-            int row = row0 + rr, k = k0 + kk;
-            As[kk][rr] = (row < Mo && k < Ki) ? Op[(int64_t)row * ldop + k] : T(0);
-        }
-        for (int e = tid; e < AP_TN * AP_TK; e += 256) {
-            int cc = e / AP_TK, kk = e % AP_TK;
-            int col = col0 + cc, k = k0 + kk;
-            T v = T(0);
-            if (col < count && k < Ki) {
-                int64_t b = src ? src[col] : base + col;
-                v = in[b * ldi + k];
+// out[dst(c)][row] (+)= sum_t sum_k Op_t[row][k] * in[src_t(c)][k] for row < Mo, k < Ki,
+// c < count: translation matrices applied to many boxes (a GEMM whose columns are gathered
+// and scattered by box index). Op_t = Op + t * op_stride (row stride ldop), t < nterm;
+// src_t(c) = src[t * count + c] (-1: no term), or base + c when src is NULL; dst NULL means
+// base + c. Tile TM = 16*RM rows x TN = 16*CN boxes, k-chunks of 16; each thread RM x CN.
+constexpr int AP_TK = 16;
+template <class T, int RM, int CN>
+__global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t op_stride, int ldop, int nterm,
+                                               int Mo, int Ki, const int32_t* src, const int32_t* dst, int64_t base,
+                                               int count, const T* __restrict__ in, int ldi, T* out, int ldo,
+                                               int accumulate) {
+    constexpr int TM = 16 * RM, TN = 16 * CN;
+    __shared__ T As[AP_TK][TM + 1];
+    __shared__ T Bs[AP_TK][TN + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    T acc[RM][CN] = {};
+    for (int t = 0; t < nterm; ++t) {
+        const T* Opt = Op + (int64_t)t * op_stride;
+        for (int k0 = 0; k0 < Ki; k0 += AP_TK) {
+            for (int e = tid; e < TM * AP_TK; e += 256) {
+                int rr = e / AP_TK, kk = e % AP_TK;
+                int row = row0 + rr, k = k0 + kk;
+                As[kk][rr] = (row < Mo && k < Ki) ? Opt[(int64_t)row * ldop + k] : T(0);
             }
-            Bs[kk][cc] = v;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < AP_TK; ++kk) {
-            T a0 = As[kk][ty], a1 = As[kk][ty + 32];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                T bv = Bs[kk][tx + 8 * j];
-                acc[0][j] += a0 * bv;
-                acc[1][j] += a1 * bv;
+            for (int e = tid; e < TN * AP_TK; e += 256) {
+                int cc = e / AP_TK, kk = e % AP_TK;
+                int col = col0 + cc, k = k0 + kk;
+                T v = T(0);
+                if (col < count && k < Ki) {
+                    int64_t b = src ? (int64_t)src[(int64_t)t * count + col] : base + col;
+                    if (b >= 0) v = in[b * ldi + k];
+                }
+                Bs[kk][cc] = v;
             }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < AP_TK; ++kk) {
+                T av[RM], bv[CN];
+#pragma unroll
+                for (int i = 0; i < RM; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < CN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < RM; ++i)
+#pragma unroll
+                    for (int j = 0; j < CN; ++j) acc[i][j] += av[i] * bv[j];
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        int row = row0 + ty + 32 * i;
+    for (int i = 0; i < RM; ++i) {
+        int row = row0 + ty + 16 * i;
         if (row >= Mo) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            int col = col0 + tx + 8 * j;
+        for (int j = 0; j < CN; ++j) {
+            int col = col0 + tx + 16 * j;
             if (col >= count) continue;
             int64_t b = dst ? dst[col] : base + col;
             T* o = out + b * ldo + row;
@@ -460,6 +494,10 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int ldo
         }
     }
 }
+// tile shapes: FP64 48 x 32 (3 x 2 per thread; ranks near 141 pad to 144), FP32 64 x 64
+template <class T> struct ApplyShape;
+template <> struct ApplyShape<double> { static constexpr int RM = 3, CN = 2; };
+template <> struct ApplyShape<float> { static constexpr int RM = 4, CN = 4; };
 
 // M2L (Eq. (m2l)) in coefficients: d[B] = sum over V(B) of T[slot] c[A], for a tile of
 // M2L_TN consecutive boxes of one level, looping over the tile's active offset slots;
@@ -874,10 +912,13 @@ template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return p
 // Op has row stride ldop; only its leading Mo x Ki block is applied (the rest is zero padding).
 template <class T>
 static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, const int32_t* src, const int32_t* dst,
-                        int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc) {
+                        int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc, int nterm = 1,
+                        int64_t op_stride = 0) {
     if (count <= 0) return KIFMM_OK;
-    dim3 g(nbk(count, AP_TN), nbk(Mo, AP_TM));
-    k_apply<T><<<g, 256, 0, st>>>(Op, ldop, Mo, Ki, src, dst, base, count, in, ldi, out, ldo, acc);
+    constexpr int RM = ApplyShape<T>::RM, CN = ApplyShape<T>::CN;
+    dim3 g(nbk(count, 16 * CN), nbk(Mo, 16 * RM));
+    k_apply<T, RM, CN><<<g, 256, 0, st>>>(Op, op_stride, ldop, nterm, Mo, Ki, src, dst, base, count, in, ldi, out,
+                                          ldo, acc);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -913,13 +954,12 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                      0, LL.n_leaf, ptr<double>(p.chk), S, cu, R, 0));
     }
     mark(p, 2);
-    for (int l = L - 2; l >= 2; --l) {
+    for (int l = L - 2; l >= 2; --l) {   // parents at level l, 8 octant terms per parent
         auto& LL = p.lv[l];
-        for (int o = 0; o < 8; ++o)
-            if (LL.n_m2m[o] > 0)
-                RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A) + (int64_t)o * R * R, R, p.ops[l].rank, p.ops[l + 1].rank,
-                                         ptr<int32_t>(LL.m2m_src[o]), ptr<int32_t>(LL.m2m_dst[o]), 0, LL.n_m2m[o], cu,
-                                         R, cu, R, 1));
+        if (LL.n_par > 0)
+            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A), R, p.ops[l].rank, p.ops[l + 1].rank,
+                                     ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par, cu, R, cu, R, 0,
+                                     8, (int64_t)R * R));
     }
     mark(p, 3);
     // ---- M2L in coefficients (Eq. (m2l))

@@ -148,6 +148,8 @@ struct Plan {
         DevBuf m2l_boxes;                          // boxes of the level grouped by octant (tensor-core M2L)
         DevBuf m2l_slots128; int n_tiles128 = 0;  // active offset slots per tile of 128 grouped boxes
         DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
+        DevBuf parents;    int n_par = 0;        // non-leaf boxes of the level
+        DevBuf par_kids;                         // [8][n_par] child per octant, -1 if empty
     };
     std::vector<LevelLists> lv;
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
