@@ -132,6 +132,20 @@ int kifmm_eval_host(kifmm_plan_t plan, const void* I_host, void* S_host, int dty
 int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I_dev, void* const* S_dev,
                      int count, int dtype, const double* C, int capture);
 
+/*
+ * Autotuner: picks the leaf size m for a point set by measurement. For each of the
+ * ncand candidate leaf sizes it builds a plan (same points, cell sizes, m0, a, b, opts),
+ * runs one untimed and `reps` timed evaluations of a unit source on the plan's stream
+ * (CUDA events) and keeps the fastest. The leaf size trades near-field pairs (P2P,
+ * ~27 m per point) against the number of boxes (M2L, M2M, L2L per box), so its best value
+ * depends on N, the pressure and the precision. Writes the best candidate to *best_leaf
+ * and, if ms_out is not NULL, the mean time of each candidate (ms) to ms_out[0..ncand).
+ * Allocates and frees its own temporary device buffers. Statuses as kifmm_plan.
+ */
+int kifmm_autotune(const double* points_dev, int64_t n, const double* cell_h_dev, double uniform_h,
+                   const int* leaf_candidates, int ncand, int surface_order, double a, double b,
+                   const kifmm_opts* opts, int reps, int* best_leaf, float* ms_out);
+
 /* Frees every device buffer of the plan (synchronising its stream). NULL is a no-op. */
 void kifmm_destroy(kifmm_plan_t plan);
 

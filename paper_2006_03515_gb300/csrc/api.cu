@@ -43,7 +43,8 @@ static void free_plan(Plan* p) {
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
-                          &L.m2l_slots128, &L.m2l_boxes, &L.parents, &L.par_kids})
+                          &L.m2l_slots128, &L.m2l_boxes, &L.parents, &L.par_kids,
+                          &L.l2l_src, &L.l2l_dst, &L.l2l_off})
             dev_free(*b);
         for (int o = 0; o < 8; ++o) {
             dev_free(L.m2m_src[o]);
@@ -280,6 +281,61 @@ int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I, void* const* S, 
     p0.graph_key = key;
     KF_CUDA(cudaGraphLaunch(p0.graph_exec, st));
     return KIFMM_OK;
+}
+
+__global__ void k_fill_ones(double* x, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = 1.0;
+}
+
+int kifmm_autotune(const double* points, int64_t n, const double* cell_h, double uniform_h, const int* cand,
+                   int ncand, int surface_order, double a, double b, const kifmm_opts* opts_in, int reps,
+                   int* best_leaf, float* ms_out) {
+    if (!cand || ncand < 1 || !best_leaf || reps < 1) {
+        set_error("kifmm_autotune: need candidates, ncand >= 1, reps >= 1 and best_leaf");
+        return KIFMM_ERR_ARG;
+    }
+    kifmm_opts o;
+    if (opts_in) o = *opts_in;
+    else kifmm_default_opts(&o);
+    cudaStream_t st = (cudaStream_t)o.stream;
+    DevBuf I, S;
+    KF_TRY(dev_alloc(I, (size_t)std::max<int64_t>(n, 1) * 8));
+    int rc = dev_alloc(S, (size_t)std::max<int64_t>(n, 1) * 8);
+    if (rc) { dev_free(I); return rc; }
+    k_fill_ones<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ptr<double>(I), n);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best = 3.0e38f;
+    *best_leaf = -1;
+    rc = KIFMM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = KIFMM_ERR_CUDA;
+    for (int k = 0; k < ncand && rc == KIFMM_OK; ++k) {
+        kifmm_plan_t p = nullptr;
+        rc = kifmm_plan(&p, points, n, cell_h, uniform_h, cand[k], surface_order, a, b, &o);
+        if (rc) break;
+        rc = kifmm_eval(p, I.p, S.p, KIFMM_F64, 1.0);
+        float ms = 0.f;
+        if (!rc) {
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < reps && !rc; ++r) rc = kifmm_eval(p, I.p, S.p, KIFMM_F64, 1.0);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = rc ? rc : KIFMM_ERR_CUDA;
+            ms /= reps;
+        }
+        kifmm_destroy(p);
+        if (rc) break;
+        if (ms_out) ms_out[k] = ms;
+        if (ms < best) {
+            best = ms;
+            *best_leaf = cand[k];
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(I);
+    dev_free(S);
+    return rc;
 }
 
 void kifmm_destroy(kifmm_plan_t h) {

@@ -217,6 +217,24 @@ int build_eval_data(Plan& p) {
             KF_LAUNCH();
             L.n_m2m[o] = tot;
         }
+        {   // the same pairs concatenated over the octants, for the batched L2L launch
+            int32_t hoff[9] = {0};
+            for (int o = 0; o < 8; ++o) hoff[o + 1] = hoff[o] + L.n_m2m[o];
+            KF_TRY(dev_alloc(L.l2l_src, (size_t)std::max(hoff[8], 1) * 4));
+            KF_TRY(dev_alloc(L.l2l_dst, (size_t)std::max(hoff[8], 1) * 4));
+            KF_TRY(dev_alloc(L.l2l_off, 9 * 4));
+            L.l2l_max = 0;
+            for (int o = 0; o < 8; ++o) {
+                if (L.n_m2m[o] == 0) continue;
+                KF_CUDA(cudaMemcpyAsync(ptr<int32_t>(L.l2l_src) + hoff[o], L.m2m_dst[o].p, L.n_m2m[o] * 4,
+                                        cudaMemcpyDeviceToDevice, st));   // parents
+                KF_CUDA(cudaMemcpyAsync(ptr<int32_t>(L.l2l_dst) + hoff[o], L.m2m_src[o].p, L.n_m2m[o] * 4,
+                                        cudaMemcpyDeviceToDevice, st));   // children
+                L.l2l_max = std::max(L.l2l_max, L.n_m2m[o]);
+            }
+            KF_CUDA(cudaMemcpyAsync(L.l2l_off.p, hoff, 9 * 4, cudaMemcpyHostToDevice, st));
+            KF_CUDA(cudaStreamSynchronize(st));
+        }
         // M2L tiles and their active offset slots
         int tb = kM2LTile;
         L.n_tiles = (int)((cnt + tb - 1) / tb);
@@ -435,12 +453,22 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
 // src_t(c) = src[t * count + c] (-1: no term), or base + c when src is NULL; dst NULL means
 // base + c. Tile TM = 16*RM rows x TN = 16*CN boxes, k-chunks of 16; each thread RM x CN.
 constexpr int AP_TK = 16;
+// With zoff != NULL the launch is a batch over blockIdx.z: batch z uses Op + z * zstride and
+// the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch).
 template <class T, int RM, int CN>
 __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t op_stride, int ldop, int nterm,
                                                int Mo, int Ki, const int32_t* src, const int32_t* dst, int64_t base,
                                                int count, const T* __restrict__ in, int ldi, T* out, int ldo,
-                                               int accumulate) {
+                                               int accumulate, const int32_t* zoff, int64_t zstride) {
     constexpr int TM = 16 * RM, TN = 16 * CN;
+    if (zoff) {
+        const int z = blockIdx.z;
+        Op += (int64_t)z * zstride;
+        src += zoff[z];
+        dst += zoff[z];
+        count = zoff[z + 1] - zoff[z];
+        if ((int)(blockIdx.x * TN) >= count) return;
+    }
     __shared__ T As[AP_TK][TM + 1];
     __shared__ T Bs[AP_TK][TN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -805,7 +833,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(EvalView E, const int32_t* leaves
 // every source read from shared memory serves two pair evaluations. 128 threads per leaf:
 // lane = target pair (targets t and t + 32 of a 64-target chunk), warp = source group.
 // Sources carry q * norm, so a pair costs (e^{-aR} - e^{-bR}) * (q norm) / R^3.
-constexpr int P2Q_T = 128, P2Q_GRP = 4;
+constexpr int P2Q_T = 128, P2Q_GRP = 4, P2Q_CHUNK = 1024;   // 16 KB of sources per block
 __device__ __forceinline__ void p2q_pair(const float4& x, const float4& v, const KParams& kp, Kahan& acc) {
     const float dx = x.x - v.x, dy = x.y - v.y, dz = x.z - v.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
@@ -840,10 +868,10 @@ __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* 
         while (ui < u1) {
             __syncthreads();
             int ns = 0, wi = ui, wo = uoffs;
-            while (wi < u1 && ns < P2P_CHUNK) {
+            while (wi < u1 && ns < P2Q_CHUNK) {
                 const int A = uitems[wi];
                 const int aa = E.pstart[A], ab = E.pend[A];
-                const int take = min(ab - aa - wo, P2P_CHUNK - ns);
+                const int take = min(ab - aa - wo, P2Q_CHUNK - ns);
                 const double* cA = E.centre + 3 * (int64_t)A;
                 const float d0 = (float)(cA[0] - cB[0]), d1 = (float)(cA[1] - cB[1]), d2 = (float)(cA[2] - cB[2]);
                 for (int e = threadIdx.x; e < take; e += P2Q_T) {
@@ -913,12 +941,12 @@ template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return p
 template <class T>
 static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, const int32_t* src, const int32_t* dst,
                         int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc, int nterm = 1,
-                        int64_t op_stride = 0) {
+                        int64_t op_stride = 0, const int32_t* zoff = nullptr, int nz = 1, int64_t zstride = 0) {
     if (count <= 0) return KIFMM_OK;
     constexpr int RM = ApplyShape<T>::RM, CN = ApplyShape<T>::CN;
-    dim3 g(nbk(count, 16 * CN), nbk(Mo, 16 * RM));
+    dim3 g(nbk(count, 16 * CN), nbk(Mo, 16 * RM), nz);
     k_apply<T, RM, CN><<<g, 256, 0, st>>>(Op, op_stride, ldop, nterm, Mo, Ki, src, dst, base, count, in, ldi, out,
-                                          ldo, acc);
+                                          ldo, acc, zoff, zstride);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -1015,11 +1043,10 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         if (l >= 3) {
             auto& LP = p.lv[l - 1];
             const LevelOps& pop = p.ops[l - 1];
-            for (int o = 0; o < 8; ++o)
-                if (LP.n_m2m[o] > 0)
-                    RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32) + (int64_t)o * R * R, R, op.rank, pop.rank,
-                                        ptr<int32_t>(LP.m2m_dst[o]), ptr<int32_t>(LP.m2m_src[o]), 0, LP.n_m2m[o], dd,
-                                        R, dd, R, 1));
+            if (LP.l2l_max > 0)   // one launch, batched over the 8 child octants
+                RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32), R, op.rank, pop.rank, ptr<int32_t>(LP.l2l_src),
+                                    ptr<int32_t>(LP.l2l_dst), 0, LP.l2l_max, dd, R, dd, R, 1, 1, 0,
+                                    ptr<int32_t>(LP.l2l_off), 8, (int64_t)R * R));
         }
         if (LL.n_leaf > 0)
             RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), R, S, op.rank, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
@@ -1076,7 +1103,7 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     }
     mark(p, 6);
     {
-        size_t smem = (size_t)P2P_CHUNK * 16;
+        size_t smem = (size_t)(mixed ? P2Q_CHUNK : P2P_CHUNK) * 16;
         const int32_t* uo = ptr<int32_t>(p.lists[0].off);
         const int32_t* ui = ptr<int32_t>(p.lists[0].items);
         unsigned g = (unsigned)p.nleaves;

@@ -150,6 +150,8 @@ struct Plan {
         DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
         DevBuf parents;    int n_par = 0;        // non-leaf boxes of the level
         DevBuf par_kids;                         // [8][n_par] child per octant, -1 if empty
+        DevBuf l2l_src, l2l_dst, l2l_off;        // (parent, child) pairs concatenated over octants
+        int l2l_max = 0;                         // largest octant batch
     };
     std::vector<LevelLists> lv;
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list

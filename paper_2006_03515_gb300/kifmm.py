@@ -56,7 +56,7 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
            "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
-           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc"]
+           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune"]
 
 _lib = None
 
@@ -90,9 +90,10 @@ def load():
     L.kifmm_get_sigma.argtypes = [vp, vp]
     L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
     L.kifmm_direct_noalloc.argtypes = [vp, i64, dbl, vp, vp, dbl, dbl, dbl, i32, vp]
+    L.kifmm_autotune.argtypes = [vp, i64, vp, dbl, vp, i32, i32, dbl, dbl, ctypes.POINTER(_Opts), i32, vp, vp]
     for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_get_info",
                  "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times",
-                 "kifmm_direct_noalloc"):
+                 "kifmm_direct_noalloc", "kifmm_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -222,6 +223,33 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def autotune(points, h, candidates=(32, 48, 64, 96, 128), surface_order=6, a=None, b=None, precision="mixed",
+             self_mode="cell_exact", pinv_eps=1e-5, reps=3, stream=None):
+    """Leaf size chosen by timing kifmm_eval for each candidate (kifmm_autotune).
+    Returns (best_leaf, {leaf: ms})."""
+    import torch
+    L = load()
+    pts = points.detach().to(torch.float64).contiguous()
+    hp, uh = None, 0.0
+    if isinstance(h, torch.Tensor):
+        hh = h.detach().to(device=pts.device, dtype=torch.float64).contiguous()
+        hp = ctypes.c_void_p(hh.data_ptr())
+    else:
+        uh = float(h)
+    o = _Opts()
+    L.kifmm_default_opts(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.self_mode = SELF_MODE[self_mode]
+    o.pinv_eps = float(pinv_eps)
+    o.stream = _stream_ptr(stream)
+    cand = (ctypes.c_int * len(candidates))(*[int(c) for c in candidates])
+    ms = (ctypes.c_float * len(candidates))()
+    best = ctypes.c_int(-1)
+    _check(L.kifmm_autotune(ctypes.c_void_p(pts.data_ptr()), int(pts.shape[0]), hp, uh, cand, len(candidates),
+                            int(surface_order), float(a), float(b), ctypes.byref(o), int(reps), ctypes.byref(best), ms))
+    return best.value, {int(c): float(t) for c, t in zip(candidates, ms)}
 
 
 NOALLOC_MAX_POINTS = 65536

@@ -105,6 +105,29 @@ def random_cloud(n, seed, L=1.0, h=None):
     return pts, np.full(n, h), rng.random(n) + 0.1
 
 
+def two_channel_field(k, n_min=80, n_max=158, base_seed=3515):
+    """Field k of the batched workload: a uniform n^3 grid on [0, 1]^3 with n drawn from
+    N = n^3 log-uniform in [n_min^3, n_max^3]; two streamer channels of length 0.5 cm
+    centred at z = 0.5, at x = 0.5 -/+ d/2 (d ~ U[0.2, 0.8] cm), the second tilted by
+    theta ~ U[0, 30] degrees about y, each with a Gaussian head at its upper tip; pressure
+    drawn from {760, 76} Torr. Returns (points, h, I, p_torr)."""
+    rng = np.random.Generator(np.random.PCG64(base_seed + k))
+    logN = rng.uniform(3 * np.log(n_min), 3 * np.log(n_max))
+    n = int(round(np.exp(logN / 3.0)))
+    d = rng.uniform(0.2, 0.8)
+    theta = rng.uniform(0.0, 30.0)
+    p = float(rng.choice([760.0, 76.0]))
+    pts, h = uniform_grid(n, 1.0)
+    x1, x2 = 0.5 - d / 2, 0.5 + d / 2
+    I = streamer_source(pts, axis_xy=(x1, 0.5), z_range=(0.25, 0.75), radius=0.05, i_channel=1e21,
+                        head=(x1, 0.5, 0.75), head_sigma=0.02, i_head=1e23, noise_sigma=0.0)
+    th = np.deg2rad(theta)
+    head2 = (x2 + 0.5 * np.sin(th), 0.5, 0.25 + 0.5 * np.cos(th))
+    I = I + streamer_source(pts, axis_xy=(x2, 0.5), z_range=(0.25, 0.75), radius=0.05, i_channel=1e21,
+                            head=head2, head_sigma=0.02, i_head=1e23, noise_sigma=0.0, tilt_deg=theta)
+    return pts, np.full(len(pts), h), I, p
+
+
 PRESSURES = {  # p (Torr) -> p_O2 (Torr); p_O2 = 0.2 p except the paper's 150 Torr at 760
     "760/150": (760.0, 150.0),
     "760": (760.0, 152.0),

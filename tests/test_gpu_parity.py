@@ -240,3 +240,91 @@ def test_tensor_core_m2l_against_simt_and_fp64(kf, monkeypatch):
     assert _relerr(s_tc, s64) <= 1e-6
     assert _relerr(s_simt, s64) <= 1e-6
     assert _relerr(s_tc, s_simt) <= 1e-6
+
+
+def test_autotune_picks_a_candidate(kf):
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(152.0)
+    best, times = kf.autotune(_dev(pts), float(h[0]), candidates=(16, 32, 64, 128), a=a, b=b, reps=2)
+    assert best in (16, 32, 64, 128) and all(t > 0 for t in times.values())
+    assert times[best] == min(times.values())
+    s64 = _plan(kf, pts, h, best, 6, a, b).eval(_dev(I)).cpu().numpy()
+    s32 = _plan(kf, pts, h, best, 6, a, b, precision="mixed").eval(_dev(I)).cpu().numpy()
+    assert _relerr(s32, s64) <= 1e-6
+
+
+def test_batched_uneven_fields_graph_captured(kf):
+    # the batched workload at reduced size: uneven fields (two tilted channels each, two
+    # pressures) evaluated back to back in one CUDA graph, against per-field evaluation
+    import torch
+    st = torch.cuda.Stream()
+    fields = [W.two_channel_field(k, n_min=18, n_max=34) for k in range(6)]
+    assert len({len(f[0]) for f in fields}) > 2 and {f[3] for f in fields} == {760.0, 76.0}
+    with torch.cuda.stream(st):
+        plans, Is, refs, Cs = [], [], [], []
+        for pts, h, I, p in fields:
+            a, b = K.absorption_coefficients(0.2 * p)
+            pl = _plan(kf, pts, h, 32, 6, a, b, precision="mixed", stream=st)
+            plans.append(pl)
+            Is.append(_dev(I))
+            Cs.append(K.source_scale(p))
+            refs.append(pl.eval(Is[-1], C=Cs[-1]).clone())
+        Ss = [torch.empty_like(x) for x in Is]
+        for _ in range(2):
+            kf.eval_batch(plans, Is, Ss, C=Cs, capture=True)
+            st.synchronize()
+            for s, r in zip(Ss, refs):
+                assert torch.equal(s, r)
+    # one field against the FP64 form
+    pts, h, I, p = fields[0]
+    a, b = K.absorption_coefficients(0.2 * p)
+    s64 = _plan(kf, pts, h, 32, 6, a, b).eval(_dev(I), C=Cs[0]).cpu().numpy()
+    assert _relerr(refs[0].cpu().numpy(), s64) <= 1e-6
+
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
+
+
+def test_full_size_uniform_128(kf):
+    # 128^3 cell centres (2,097,152 points), Gaussian source, p = 760 Torr, p_O2 = 152, m0 = 6,
+    # leaf 64 (the benchmark's workload and launch configuration)
+    pts, h, I = W.config_uniform(128)
+    a, b = K.absorption_coefficients(152.0)
+    C = K.source_scale(760.0)
+    Id = _dev(I)
+    s64 = _plan(kf, pts, h, 64, 6, a, b).eval(Id, C=C)
+    s32 = _plan(kf, pts, h, 64, 6, a, b, precision="mixed").eval(Id, C=C)
+    import torch
+    assert float(torch.linalg.norm(s32 - s64) / torch.linalg.norm(s64)) <= 1e-6
+    # sampled outputs against the direct sum (the FMM's own approximation error, the paper's
+    # E_V magnitude), and the whole field against the FFT form of the same sum
+    idx = _sample(len(pts), 512, 1)
+    ref = D.direct_sum(pts, h, I, a, b, C, targets=idx)
+    got = s64.cpu().numpy()
+    e_direct = _relerr(got[idx], ref)
+    full = D.fft_uniform(I.reshape(128, 128, 128), h[0], a, b, C).ravel()
+    np.testing.assert_allclose(full[idx], ref, rtol=1e-10)
+    e_full = _relerr(got, full)
+    assert e_direct < 1e-2 and e_full < 1e-2, (e_direct, e_full)
+
+
+def test_full_size_adaptive(kf):
+    # two-level refined grid on a 2 cm cube: base h = 1/64, 8x finer around the head
+    # (3,219,819 points), channel + head + log-normal noise, p = 760 Torr, p_O2 = 150
+    pts, h, I = W.config_adaptive()
+    assert len(pts) == 3219819
+    a, b = K.absorption_coefficients(150.0)
+    C = K.source_scale(760.0)
+    Id = _dev(I)
+    p64 = _plan(kf, pts, h, 64, 6, a, b, uniform=False)
+    info = p64.info()
+    assert info["list_len"][2] > 0 and info["list_len"][3] > 0   # W and X lists in use
+    s64 = p64.eval(Id, C=C)
+    s32 = _plan(kf, pts, h, 64, 6, a, b, uniform=False, precision="mixed").eval(Id, C=C)
+    import torch
+    assert float(torch.linalg.norm(s32 - s64) / torch.linalg.norm(s64)) <= 1e-6
+    fine = np.nonzero(h < h.max())[0]
+    idx = np.concatenate([_sample(len(pts), 128, 2), fine[_sample(len(fine), 128, 3)]])
+    ref = D.direct_sum(pts, h, I, a, b, C, targets=idx)
+    assert _relerr(s64.cpu().numpy()[idx], ref) < 2e-2
