@@ -30,6 +30,17 @@ L2_FLUSH_BYTES = 512 << 20
 SM_COUNT = 152
 MUFU_PER_SM_CLK = 16.0
 MUFU_PER_PAIR = 3.0     # rsqrt + two exp2 per pair in the FP32 kernel
+TF32_OVER_BF16 = 0.5    # nominal dense TF32 / BF16 tensor rate
+FP64_TFLOPS = 1.0       # FP64 FMA rate of this machine's GB300 (measured, microbenchmark)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def parse():
@@ -264,16 +275,27 @@ def main():
     phases = ["scatter", "P2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
     ph_ms = {k: v / args.steps for k, v in zip(phases, phase_sum)}
     dom = max(ph_ms, key=ph_ms.get)
+    peaks = measured_peaks()
     sm_clk = 2070.0
-    if dom == "P2P":
-        achieved = info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3) / 1e9
-        peak = SM_COUNT * MUFU_PER_SM_CLK / MUFU_PER_PAIR * sm_clk * 1e6 / 1e9
-        roof = {"kernel": "k_p2p (near-field pair sum)", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "Gpair/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "MUFU: 152 SMs x 16 /clk x 2070 MHz / 3 MUFU per pair (derived)"}
-    else:
-        roof = {"kernel": dom, "bound": "alu", "achieved": None, "peak": None, "unit": None, "frac": None,
-                "traffic": None}
+    # rooflines of the three heavy kernels; the dominant one is "roofline"
+    p2p_ach = info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3) / 1e9
+    p2p_peak = SM_COUNT * MUFU_PER_SM_CLK / MUFU_PER_PAIR * sm_clk * 1e6 / 1e9
+    tf32_peak = peaks.get("bf16_tflops", 1947.8) * TF32_OVER_BF16
+    m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
+    up_ach = info["upward_flops"] / ((ph_ms["P2M"] + ph_ms["M2M+UC2UE"]) * 1e-3) / 1e12
+    roofs = {
+        "P2P": {"kernel": "k_p2p_mixed (near-field pair sum, FP32)", "bound": "alu", "achieved": p2p_ach,
+                "peak": p2p_peak, "unit": "Gpair/s", "frac": p2p_ach / p2p_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 16 MUFU/clk x 2070 MHz / 3 MUFU per pair"},
+        "M2L": {"kernel": "k_m2l_tc (tcgen05 3xTF32, coefficient basis)", "bound": "tensor", "achieved": m2l_ach,
+                "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (tf32_peak / 3.0), "traffic": None,
+                "peak_source": "of measured: bf16_tflops x 0.5 (TF32/BF16 nominal) / 3 MMAs per product"},
+        "upward": {"kernel": "k_apply<double> (P2M projection + M2M, FP64)", "bound": "fp64", "achieved": up_ach,
+                   "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": up_ach / FP64_TFLOPS, "traffic": None,
+                   "peak_source": "FP64 FMA rate measured by a microbenchmark on this pool's GB300"},
+    }
+    key = "P2P" if dom == "P2P" else ("M2L" if dom == "M2L" else "upward")
+    roof = dict(roofs[key])
     gpu_launches = launches_per_step * args.steps
     line = {"metric": "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)", "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
@@ -285,7 +307,7 @@ def main():
                        "n_points": npts, "l2": "512 MB buffer written between timed steps",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "gate_rel_l2_mixed_vs_fp64": gate, "fp64": fp64, "plan_s": plan_s,
-            "phase_ms": ph_ms, "roofline": roof, "clocks": clk, "gpu_launches": gpu_launches,
+            "phase_ms": ph_ms, "roofline": roof, "rooflines": roofs, "clocks": clk, "gpu_launches": gpu_launches,
             "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": npts * 8,
                     "d2h_bytes_per_step": npts * 8, "matches_device_result": e2e_ok}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

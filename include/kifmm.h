@@ -168,6 +168,8 @@ typedef struct {
     int64_t p2p_pairs;          /* near-field pair evaluations of one kifmm_eval */
     int64_t m2l_tensor;         /* 1 if M2L runs on the tensor cores (mixed form) */
     int64_t device_error;       /* nonzero if a bounded device wait ran out (synchronises) */
+    double m2l_flops;           /* algorithmic M2L flop of one kifmm_eval: 2 r_l^2 per V pair */
+    double upward_flops;        /* upward pseudo-inverse work: 2 r_l S per leaf + 2 r_l r_(l+1) per child */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */

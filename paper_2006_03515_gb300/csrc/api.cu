@@ -363,6 +363,17 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     info->pinv_rank_min = rmin;
     info->eval_launches = p.eval_launches;
     info->m2l_tensor = p.m2l_tensor ? 1 : 0;
+    info->m2l_flops = p.m2l_flops;
+    {
+        double up = 0;
+        for (int l = 2; l < p.tree.nlevels; ++l) {
+            up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_leaf;
+            if (l + 1 < p.tree.nlevels)
+                up += 2.0 * p.ops[l].rank * p.ops[l + 1].rank *
+                      (double)(p.tree.level_start[l + 2] - p.tree.level_start[l + 1]);
+        }
+        info->upward_flops = up;
+    }
     info->device_error = 0;
     if (p.err.p) {
         int e = 0;

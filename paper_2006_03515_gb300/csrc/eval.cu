@@ -95,6 +95,14 @@ __global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int 
     }
 }
 
+// V-list entries per level (algorithmic M2L work)
+__global__ void count_v_per_level(const int32_t* voff, const int32_t* level, int64_t nb, unsigned long long* cnt) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    const int n = voff[b + 1] - voff[b];
+    if (n > 0) atomicAdd(&cnt[level[b]], (unsigned long long)n);
+}
+
 __global__ void kid_table(const int32_t* child, const int32_t* parents, int n, int32_t* kids) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
@@ -195,6 +203,21 @@ int build_eval_data(Plan& p) {
         KF_CUDA(cudaStreamSynchronize(st));
         p.p2p_pairs = (int64_t)h;
         dev_free(cnt);
+    }
+    {   // algorithmic work of one evaluation: M2L 2 r_l^2 per V pair; FP64 upward 2 r_l S per
+        // leaf (projection) and 2 r_l r_{l+1} per child (M2M)
+        DevBuf cnt;
+        KF_TRY(dev_alloc(cnt, 32 * 8));
+        KF_CUDA(cudaMemsetAsync(cnt.p, 0, 32 * 8, st));
+        count_v_per_level<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(p.lists[1].off), ptr<int32_t>(t.level), nb,
+                                                         ptr<unsigned long long>(cnt));
+        KF_LAUNCH();
+        unsigned long long hc[32];
+        KF_CUDA(cudaMemcpyAsync(hc, cnt.p, 32 * 8, cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        dev_free(cnt);
+        p.m2l_flops = 0;
+        for (int l = 2; l < t.nlevels; ++l) p.m2l_flops += 2.0 * p.ops[l].rank * p.ops[l].rank * (double)hc[l];
     }
     p.lv.clear();
     p.lv.resize(t.nlevels);

@@ -163,6 +163,8 @@ struct Plan {
     int tc_ntiles = 0;
     DevBuf err;                  // int: device-side error code (bounded waits)
     int64_t p2p_pairs = 0;       // near-field pairs of one evaluation
+    double m2l_flops = 0;        // algorithmic M2L flop of one evaluation (2 r^2 per V pair)
+    double up_flops = 0;         // FP64 upward flop (projection 2 r S per leaf, M2M 2 r r' per child)
     // timing
     bool timing = false;
     cudaEvent_t ev[9] = {};

@@ -51,7 +51,8 @@ class _Info(ctypes.Structure):
                 ("surface_points", ctypes.c_int32), ("n_leaves", ctypes.c_int64),
                 ("list_len", ctypes.c_int64 * 4), ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("pinv_rank_min", ctypes.c_double), ("eval_launches", ctypes.c_int64),
-                ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64)]
+                ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64),
+                ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double)]
 
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
@@ -182,7 +183,8 @@ class Plan:
                     surface_points=inf.surface_points, n_leaves=inf.n_leaves, list_len=list(inf.list_len),
                     origin=list(inf.origin), side=inf.side, pinv_rank_min=int(inf.pinv_rank_min),
                     eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs),
-                    m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error))
+                    m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error),
+                    m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops))
 
     def tree(self):
         inf = self.info()
