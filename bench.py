@@ -34,6 +34,14 @@ TF32_OVER_BF16 = 0.5    # nominal dense TF32 / BF16 tensor rate
 FP64_TFLOPS = 1.0       # FP64 FMA rate of this machine's GB300 (measured, microbenchmark)
 
 
+METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
+
+
+def workload_name(args):
+    return ("uniform %d^3 cell centres, 1 cm cube, Gaussian 1e22 exp(-r^2/0.1^2), p=%g Torr, pO2=%g, m0=%d, "
+            "leaf %d, %s" % (args.n, args.p, 0.2 * args.p, args.m0, args.leaf, args.precision))
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -156,12 +164,12 @@ def run_reference(args):
     value = len(pts) / (ms * 1e-3)
     sample = ("oracle KIFMM evaluation (FP64, numpy + C/OpenMP) on a %d^3 sample of the workload "
               "(same 1 cm cube, source, pressure, m0=%d, leaf %d); plan excluded" % (n, args.m0, args.leaf))
-    line = {"impl": "reference", "metric": "S_ph points/s (KIFMM evaluation)", "value": value,
+    line = {"impl": "reference", "metric": METRIC, "value": value,
             "unit": "points/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "uniform %d^3 cell centres (sample of the %d^3 workload)" % (n, args.n),
-                       "n_points": len(pts), "m0": args.m0, "leaf": args.leaf, "p_torr": args.p},
+            "config": {"workload": workload_name(args), "sample": "uniform %d^3 cell centres of the same cube" % n,
+                       "n_points": len(pts), "l2": "host run (no GPU)", "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": "points/s", "cores": D.c_threads(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -297,13 +305,11 @@ def main():
     key = "P2P" if dom == "P2P" else ("M2L" if dom == "M2L" else "upward")
     roof = dict(roofs[key])
     gpu_launches = launches_per_step * args.steps
-    line = {"metric": "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)", "value": value, "unit": "points/s",
+    line = {"metric": METRIC, "value": value, "unit": "points/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": "uniform %d^3 cell centres, 1 cm cube, Gaussian 1e22 exp(-r^2/0.1^2), "
-                                   "p=%g Torr, pO2=%g, m0=%d, leaf %d, %s" % (args.n, args.p, p_o2, args.m0,
-                                                                             args.leaf, args.precision),
+            "config": {"workload": workload_name(args),
                        "n_points": npts, "l2": "512 MB buffer written between timed steps",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "gate_rel_l2_mixed_vs_fp64": gate, "fp64": fp64, "plan_s": plan_s,
