@@ -195,6 +195,59 @@ int kifmm_get_sigma(kifmm_plan_t plan, double* sigma);
  * L2P+M2P, P2P]. Returns the number of phases written (<= cap). */
 int kifmm_get_phase_times(kifmm_plan_t plan, float* ms, int cap);
 
+/* ---- learned surrogate: 3D spectral neural operator ---- */
+
+/*
+ * A spectral neural operator on an n^3 grid that maps u = log(1 + I) to log(1 + S); the
+ * paper has no learned part (it stands in for the solve inside a time loop, with the FMM as
+ * judge and fallback). Layers: lift 1 -> width; `layers` times z = SpecConv(v) + W v + b,
+ * v = GELU(z) (no GELU after the last); projection width -> proj_width (GELU) -> 1.
+ * SpecConv keeps the frequencies {0..m-1} U {n-m..n-1} on the first two axes and {0..m-1}
+ * on the last (the real field's conjugate half), mixes channels per frequency with a complex
+ * width x width matrix (BF16 weights, FP32 accumulation) and transforms back.
+ * Limits: n >= 4, 1 <= modes <= n/2, width <= 64, proj_width <= 128.
+ * Fields are device FP32 arrays [batch][n^3], point index i*n^2 + j*n + k (k = last axis).
+ * Parameters form one flat FP32 vector (order: lift W, b; per layer R real, R imag
+ * ([(2m)(2m)m][width][width]), W [width][width], b; then Q1 [proj][width], q1, Q2, q2).
+ * The model owns its device memory (allocated by sno_create, all activations for
+ * max_batch fields) and runs its work on `stream`; calls on one model must not overlap.
+ * Errors: KIFMM_ERR_ARG for bad sizes or pointers, KIFMM_ERR_OOM, KIFMM_ERR_CUDA.
+ */
+typedef struct sno_model_s* sno_model_t;
+int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int proj_width, int max_batch,
+               void* stream);
+void sno_destroy(sno_model_t model);
+int64_t sno_num_params(sno_model_t model);
+/* host copies of the flat parameter / gradient vectors (sno_num_params floats) */
+int sno_set_params(sno_model_t model, const float* theta_host);
+int sno_get_params(sno_model_t model, float* theta_host);
+int sno_get_grads(sno_model_t model, float* grad_host);
+/* parameters to / from a file ("SNO1" header with the model's sizes, then the FP32 vector);
+   loading checks the sizes against the model's and resets the optimiser state */
+int sno_save(sno_model_t model, const char* path);
+int sno_load(sno_model_t model, const char* path);
+/* 1: spectral weights used in BF16 (default); 0: in FP32 (gradient checks) */
+int sno_set_bf16(sno_model_t model, int on);
+/* y = network(u) for `batch` fields (batch <= max_batch) */
+int sno_forward(sno_model_t model, const float* u_dev, float* y_dev, int batch);
+/* mean squared error of network(u) against t, and its gradient (kept in the model) */
+int sno_loss_grad(sno_model_t model, const float* u_dev, const float* t_dev, int batch, double* loss_host);
+/* one Adam step with the gradient of the last sno_loss_grad */
+int sno_adam_step(sno_model_t model, float lr, float beta1, float beta2, float eps);
+
+/*
+ * Surrogate-first solve: S = exp(network(log(1 + I))) - 1 on the plan's points,
+ * which must be the model's n^3 grid in the model's index order (FP64 I and S on the
+ * device, caller order). The result is judged against the direct sum of the discrete
+ * integral (the plan's kernel, self terms and C) at k_samples (1..4096) targets drawn from
+ * `seed`; when the judged relative L2 error exceeds tol, kifmm_eval's result replaces it.
+ * *used_fallback is set to 1 in that case and *judged_err to the judged error. The network
+ * is trained on targets that already include C. Runs on the plan's stream and returns
+ * after the judge (host synchronisation).
+ */
+int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, double* S_dev, double C, double tol,
+                int k_samples, uint64_t seed, int* used_fallback, double* judged_err);
+
 /* ---- evaluation without device allocation ---- */
 
 /* Largest point count kifmm_direct_noalloc accepts (its fixed work space: 8 bytes per point). */

@@ -65,6 +65,10 @@ struct kifmm_plan_s {
     Plan* p;
 };
 
+namespace kifmm {
+Plan* kifmm_plan_internal(kifmm_plan_t h) { return h ? h->p : nullptr; }
+}  // namespace kifmm
+
 extern "C" {
 
 void kifmm_default_opts(kifmm_opts* o) {

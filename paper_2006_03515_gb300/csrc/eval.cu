@@ -1087,6 +1087,15 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     return KIFMM_OK;
 }
 
+// q = I h^3 and I in sorted order (used by the surrogate's judge)
+int kifmm_scatter_weights(Plan& p, const double* I) {
+    const int64_t n = p.tree.n;
+    k_scatter_q<double><<<nbk(n, 256), 256, 0, p.stream>>>(I, ptr<int32_t>(p.tree.perm), ptr<double>(p.w), n,
+                                                            ptr<double>(p.Isort), ptr<double>(p.q));
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
 int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     int64_t nl = 0;   // kernels launched by this evaluation
     Tree& t = p.tree;

@@ -196,6 +196,9 @@ struct M2LTables {                 // per-level TF32 hi/lo M2L tables for the te
 };
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err);
+// api.cu / eval.cu helpers for the surrogate
+Plan* kifmm_plan_internal(kifmm_plan_t h);
+int kifmm_scatter_weights(Plan& p, const double* I);
 // eval.cu
 int build_eval_data(Plan& p);
 int run_eval(Plan& p, const void* I, void* S, int dtype, double C);

@@ -57,7 +57,10 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
            "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
-           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune"]
+           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
+           "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
+           "sno_save", "sno_load",
+           "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"]
 
 _lib = None
 
@@ -96,6 +99,7 @@ def load():
                  "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times",
                  "kifmm_direct_noalloc", "kifmm_autotune"):
         getattr(L, name).restype = ctypes.c_int
+    _load_sno(L)
     _lib = L
     return L
 
@@ -282,3 +286,160 @@ def eval_batch(plans, Is, Ss, C=None, capture=False):
     cc = (ctypes.c_double * n)(*([1.0] * n if C is None else [float(c) for c in C]))
     _check(load().kifmm_eval_batch(ph, ip, sp, n, dt, cc, 1 if capture else 0))
     return Ss
+
+
+def _load_sno(L):
+    vp, i64, i32, dbl, flt = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_float
+    L.sno_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32, i32, i32, vp]
+    L.sno_destroy.argtypes = [vp]
+    L.sno_destroy.restype = None
+    L.sno_num_params.argtypes = [vp]
+    L.sno_num_params.restype = i64
+    L.sno_set_params.argtypes = [vp, vp]
+    L.sno_get_params.argtypes = [vp, vp]
+    L.sno_get_grads.argtypes = [vp, vp]
+    L.sno_save.argtypes = [vp, ctypes.c_char_p]
+    L.sno_load.argtypes = [vp, ctypes.c_char_p]
+    L.sno_set_bf16.argtypes = [vp, i32]
+    L.sno_forward.argtypes = [vp, vp, vp, i32]
+    L.sno_loss_grad.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dbl)]
+    L.sno_adam_step.argtypes = [vp, flt, flt, flt, flt]
+    L.photo_solve.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, ctypes.POINTER(i32),
+                              ctypes.POINTER(dbl)]
+    for name in ("sno_create", "sno_save", "sno_load", "sno_set_params", "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_forward",
+                 "sno_loss_grad", "sno_adam_step", "photo_solve"):
+        getattr(L, name).restype = ctypes.c_int
+
+
+class SNO:
+    """The spectral neural operator surrogate (sno_* in kifmm.h): grid n^3, ``width``
+    channels, ``modes`` frequencies per axis, ``layers`` spectral layers, projection width
+    ``proj``. Fields are CUDA float32 tensors of shape (batch, n^3) or (n^3,)."""
+
+    def __init__(self, n, width=32, modes=8, layers=4, proj=64, max_batch=8, stream=None):
+        L = load()
+        self.n, self.width, self.modes, self.layers, self.proj, self.max_batch = n, width, modes, layers, proj, max_batch
+        self._h = ctypes.c_void_p()
+        self._stream = stream
+        _check(L.sno_create(ctypes.byref(self._h), int(n), int(width), int(modes), int(layers), int(proj),
+                            int(max_batch), _stream_ptr(stream)))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def num_params(self):
+        return int(load().sno_num_params(self._h))
+
+    def layout(self):
+        """(name, shape) of each parameter block in the flat vector's order."""
+        C, m, P = self.width, self.modes, self.proj
+        K = (2 * m) * (2 * m) * m
+        lay = [("Wl", (C,)), ("bl", (C,))]
+        for l in range(self.layers):
+            lay += [("Rr%d" % l, (K, C, C)), ("Ri%d" % l, (K, C, C)), ("W%d" % l, (C, C)), ("b%d" % l, (C,))]
+        return lay + [("Q1", (P, C)), ("q1", (P,)), ("Q2", (P,)), ("q2", (1,))]
+
+    def init_params(self, seed=0):
+        """Seeded initial parameters (scaled normal weights, zero biases)."""
+        import numpy as np
+        rng = np.random.Generator(np.random.PCG64(seed))
+        parts = []
+        C = self.width
+        for name, shp in self.layout():
+            k = int(np.prod(shp))
+            if name.startswith("b") or name in ("q1", "q2"):
+                parts.append(np.zeros(k))
+            elif name == "Wl":
+                parts.append(rng.standard_normal(k))
+            elif name.startswith("R"):
+                parts.append(rng.standard_normal(k) * (1.0 / C))
+            elif name == "Q1":
+                parts.append(rng.standard_normal(k) / np.sqrt(C))
+            elif name == "Q2":
+                parts.append(rng.standard_normal(k) / np.sqrt(self.proj))
+            else:
+                parts.append(rng.standard_normal(k) / np.sqrt(C))
+        theta = np.concatenate(parts).astype(np.float32)
+        self.set_params(theta)
+        return theta
+
+    def set_params(self, theta):
+        import numpy as np
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        if t.size != self.num_params():
+            raise ValueError("expected %d parameters" % self.num_params())
+        _check(load().sno_set_params(self._h, t.ctypes.data_as(ctypes.c_void_p)))
+
+    def params(self):
+        import numpy as np
+        t = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().sno_get_params(self._h, t.ctypes.data_as(ctypes.c_void_p)))
+        return t
+
+    def grads(self):
+        import numpy as np
+        g = np.empty(self.num_params(), dtype=np.float32)
+        _check(load().sno_get_grads(self._h, g.ctypes.data_as(ctypes.c_void_p)))
+        return g
+
+    def set_bf16(self, on):
+        _check(load().sno_set_bf16(self._h, 1 if on else 0))
+
+    def save(self, path):
+        _check(load().sno_save(self._h, os.fsencode(path)))
+
+    def load(self, path):
+        _check(load().sno_load(self._h, os.fsencode(path)))
+
+    def _batch(self, u):
+        import torch
+        if not (isinstance(u, torch.Tensor) and u.is_cuda and u.dtype == torch.float32 and u.is_contiguous()):
+            raise TypeError("fields must be contiguous CUDA float32 tensors")
+        if u.numel() % (self.n ** 3):
+            raise ValueError("field size is not a multiple of n^3")
+        return u.numel() // (self.n ** 3)
+
+    def forward(self, u, y=None):
+        import torch
+        B = self._batch(u)
+        if y is None:
+            y = torch.empty_like(u)
+        _check(load().sno_forward(self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(y.data_ptr()), B))
+        return y
+
+    def loss_grad(self, u, t):
+        B = self._batch(u)
+        if t.shape != u.shape:
+            raise ValueError("target shape differs from input shape")
+        loss = ctypes.c_double()
+        _check(load().sno_loss_grad(self._h, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(t.data_ptr()), B,
+                                    ctypes.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        _check(load().sno_adam_step(self._h, float(lr), float(beta1), float(beta2), float(eps)))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().sno_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def photo_solve(plan, model, I, S=None, C=1.0, tol=0.05, k_samples=256, seed=0):
+    """Surrogate-first solve (photo_solve in kifmm.h). I, S: CUDA float64 tensors (N,).
+    Returns (S, used_fallback, judged_error)."""
+    import torch
+    if S is None:
+        S = torch.empty_like(I)
+    fb = ctypes.c_int()
+    err = ctypes.c_double()
+    _check(load().photo_solve(plan.handle, model.handle, ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(S.data_ptr()),
+                              float(C), float(tol), int(k_samples), int(seed), ctypes.byref(fb), ctypes.byref(err)))
+    return S, bool(fb.value), err.value

@@ -134,3 +134,18 @@ PRESSURES = {  # p (Torr) -> p_O2 (Torr); p_O2 = 0.2 p except the paper's 150 To
     "76": (76.0, 15.2),
     "7.6": (7.6, 1.52),
 }
+
+
+def gaussian_mixture(points, seed, n_blobs=(1, 4), sigma=(0.03, 0.12), log10_amp=(20.0, 23.0), L=1.0):
+    """Sum of 1-4 Gaussian blobs with centres uniform in the inner 80 % of [0, L]^3, widths
+    uniform in ``sigma`` (cm) and amplitudes log-uniform in 10^log10_amp (training fields of
+    the surrogate)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = int(rng.integers(n_blobs[0], n_blobs[1] + 1))
+    I = np.zeros(points.shape[0])
+    for _ in range(k):
+        c = L * (0.1 + 0.8 * rng.random(3))
+        s = rng.uniform(*sigma)
+        amp = 10.0 ** rng.uniform(*log10_amp)
+        I += gaussian(points, c, s, amp)
+    return I

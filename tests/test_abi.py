@@ -10,13 +10,14 @@ import pytest
 from paper_2006_03515_gb300 import build, kifmm
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ERR_ARG = -1
 
 
 def _declared():
     names = []
     for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
         txt = open(hdr).read()
-        names += re.findall(r"^\s*(?:int|void|const char\s*\*)\s+(kifmm_\w+)\s*\(", txt, re.M)
+        names += re.findall(r"^\s*(?:int|int64_t|void|const char\s*\*)\s+(\w+)\s*\(", txt, re.M)
     return sorted(set(names))
 
 
@@ -83,3 +84,17 @@ def test_physics_constants():
     a, b = kifmm.absorption(150.0)
     assert a == pytest.approx(5.25, rel=1e-15) and b == 300.0
     assert kifmm.scale_c(760.0) == pytest.approx(0.06 * 30.0 / 790.0)
+
+
+def test_sno_rejects_bad_sizes_on_the_host(lib):
+    h = ctypes.c_void_p()
+    for n, width, modes, layers, proj, mb in [(3, 4, 1, 1, 4, 1), (8, 65, 2, 1, 4, 1), (8, 4, 5, 1, 4, 1),
+                                              (8, 4, 0, 1, 4, 1), (8, 4, 2, 0, 4, 1), (8, 4, 2, 1, 129, 1),
+                                              (8, 4, 2, 1, 4, 0)]:
+        assert lib.sno_create(ctypes.byref(h), n, width, modes, layers, proj, mb, None) == ERR_ARG
+        assert not h.value
+    assert lib.sno_num_params(None) == -1
+    assert lib.sno_forward(None, None, None, 1) == ERR_ARG
+    assert lib.sno_loss_grad(None, None, None, 1, None) == ERR_ARG
+    assert lib.sno_save(None, b"x") == ERR_ARG
+    assert lib.photo_solve(None, None, None, None, 1.0, 1e-2, 256, 0, None, None) == ERR_ARG

@@ -213,3 +213,34 @@ def test_kifmm_accuracy_32cube(m0, tol):
     got = KF.kifmm(pts, h, I, 64, m0, a, b)
     err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
     assert err < tol
+
+
+# ---- surrogate oracle -----------------------------------------------------------------------
+def test_sno_spectral_conv_equals_masked_fft():
+    # with R = identity at every retained mode, SpecConv is the low-pass projection of v onto
+    # the retained modes: numpy's real FFT, zeroing every other mode, and the inverse FFT
+    from oracle import sno
+    n, m, C = 8, 3, 2
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal((C, n, n, n))
+    K = (2 * m) * (2 * m) * m
+    Rr = np.tile(np.eye(C), (K, 1, 1))
+    Ri = np.zeros_like(Rr)
+    got = sno.spec_conv(v, Rr, Ri, n, m)
+    F = np.fft.rfftn(v, axes=(1, 2, 3))
+    mask = np.zeros(F.shape[1:], dtype=bool)
+    kx, ky, kz = sno.mode_sets(n, m)
+    mask[np.ix_(kx, ky, kz)] = True
+    ref = np.fft.irfftn(np.where(mask[None], F, 0.0), s=(n, n, n), axes=(1, 2, 3))
+    np.testing.assert_allclose(got, ref, atol=1e-12)
+
+
+def test_sno_forward_shapes_and_linear_limit():
+    # with every weight zero but the lift and a unit projection path, the network is affine
+    from oracle import sno
+    n, m, C, L, P = 6, 2, 3, 2, 4
+    lay = sno.param_layout(C, m, L, P)
+    theta = np.zeros(sum(int(np.prod(s)) for _, s in lay))
+    u = np.random.default_rng(1).standard_normal((n, n, n))
+    y = sno.forward(theta, u, C, m, L, P)
+    assert y.shape == (n, n, n) and np.all(y == 0.0)
