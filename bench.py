@@ -31,7 +31,7 @@ SM_COUNT = 152
 MUFU_PER_SM_CLK = 16.0
 MUFU_PER_PAIR = 3.0     # rsqrt + two exp2 per pair in the FP32 kernel
 TF32_OVER_BF16 = 0.5    # nominal dense TF32 / BF16 tensor rate
-FP64_TFLOPS = 1.0       # FP64 FMA rate of this machine's GB300 (measured, microbenchmark)
+FP64_TFLOPS = 1.25      # GB300 FP64 (nominal; FMA chains measured 1.01, the FP64 GEMM 1.13 TFLOP/s)
 
 
 METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
@@ -357,7 +357,7 @@ def main():
         e2e_val = ws * npts / (1e-3 * sum(e2e_ms) / len(e2e_ms))
         e2e_ok = bool(np.allclose(hSn, S.cpu().numpy(), rtol=0, atol=0))
 
-    phases = ["scatter", "P2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
+    phases = ["scatter", "S2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
     ph_ms = {k: v / args.steps for k, v in zip(phases, phase_sum)}
     dom = max(ph_ms, key=ph_ms.get)
     peaks = measured_peaks()
@@ -367,7 +367,7 @@ def main():
     p2p_peak = SM_COUNT * MUFU_PER_SM_CLK / MUFU_PER_PAIR * sm_clk * 1e6 / 1e9
     tf32_peak = peaks.get("bf16_tflops", 1947.8) * TF32_OVER_BF16
     m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
-    up_ach = info["upward_flops"] / ((ph_ms["P2M"] + ph_ms["M2M+UC2UE"]) * 1e-3) / 1e12
+    up_ach = info["upward_flops"] / (ph_ms["M2M+UC2UE"] * 1e-3) / 1e12
     roofs = {
         "P2P": {"kernel": "k_p2p_mixed (near-field pair sum, FP32)", "bound": "alu", "achieved": p2p_ach,
                 "peak": p2p_peak, "unit": "Gpair/s", "frac": p2p_ach / p2p_peak, "traffic": None,
@@ -375,9 +375,10 @@ def main():
         "M2L": {"kernel": "k_m2l_tc (tcgen05 3xTF32, coefficient basis)", "bound": "tensor", "achieved": m2l_ach,
                 "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (tf32_peak / 3.0), "traffic": None,
                 "peak_source": "of measured: bf16_tflops x 0.5 (TF32/BF16 nominal) / 3 MMAs per product"},
-        "upward": {"kernel": "k_apply<double> (P2M projection + M2M, FP64)", "bound": "alu", "achieved": up_ach,
+        "upward": {"kernel": "k_apply<double> (UC2UE pseudo-inverse c = Sigma^+ U^T chk of leaves and parents, "
+                             "FP64; the phase also holds the FP32 M2M translations)", "bound": "alu", "achieved": up_ach,
                    "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": up_ach / FP64_TFLOPS, "traffic": None,
-                   "peak_source": "FP64 FMA rate measured by a microbenchmark on this pool's GB300"},
+                   "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no measured FP64 peak in MEASURED_PEAKS.json)"},
     }
     key = "P2P" if dom == "P2P" else ("M2L" if dom == "M2L" else "upward")
     roof = dict(roofs[key])

@@ -33,7 +33,7 @@ static void free_plan(Plan* p) {
     }
     dev_free(p->vtab);
     for (auto& o : p->ops)
-        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.A, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32,
+        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.Mc, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32, &o.Mc32,
                           &o.Thi, &o.Tlo})
             dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
@@ -43,7 +43,7 @@ static void free_plan(Plan* p) {
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
-                          &L.m2l_slots128, &L.m2l_boxes, &L.parents, &L.par_kids,
+                          &L.m2l_slots128, &L.m2l_boxes, &L.parents, &L.par_kids, &L.upb,
                           &L.l2l_src, &L.l2l_dst, &L.l2l_off})
             dev_free(*b);
         for (int o = 0; o < 8; ++o) {
@@ -370,12 +370,8 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     info->m2l_flops = p.m2l_flops;
     {
         double up = 0;
-        for (int l = 2; l < p.tree.nlevels; ++l) {
-            up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_leaf;
-            if (l + 1 < p.tree.nlevels)
-                up += 2.0 * p.ops[l].rank * p.ops[l + 1].rank *
-                      (double)(p.tree.level_start[l + 2] - p.tree.level_start[l + 1]);
-        }
+        // FP64 pseudo-inverse applications c = Sigma^+ U^T chk, one per leaf and per parent
+        for (int l = 2; l < p.tree.nlevels; ++l) up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_up;
         info->upward_flops = up;
     }
     info->device_error = 0;

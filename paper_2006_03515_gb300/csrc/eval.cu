@@ -3,6 +3,8 @@
 #include <algorithm>
 #include <cstdlib>
 
+#include <cstring>
+
 #include "internal.cuh"
 #include "kernel.cuh"
 
@@ -137,6 +139,8 @@ __global__ void count_p2p_pairs(const int32_t* leaves, int64_t nl, const int32_t
     unsigned long long nb = (unsigned long long)(pend[B] - pstart[B]);
     atomicAdd(out, nb * s - nb);
 }
+
+static int p2p_series_check(Plan& p);
 
 int build_eval_data(Plan& p) {
     Tree& t = p.tree;
@@ -298,6 +302,14 @@ int build_eval_data(Plan& p) {
             KF_LAUNCH();
             L.n_leaf = nlf;
         }
+        // upward solves of the level: its leaves, then its parents
+        L.n_up = L.n_leaf + L.n_par;
+        KF_TRY(dev_alloc(L.upb, (size_t)std::max(L.n_up, 1) * 4));
+        if (L.n_leaf > 0)
+            KF_CUDA(cudaMemcpyAsync(L.upb.p, L.leafs.p, (size_t)L.n_leaf * 4, cudaMemcpyDeviceToDevice, st));
+        if (L.n_par > 0)
+            KF_CUDA(cudaMemcpyAsync(ptr<int32_t>(L.upb) + L.n_leaf, L.parents.p, (size_t)L.n_par * 4,
+                                    cudaMemcpyDeviceToDevice, st));
         // boxes with a non-empty X list
         nonempty_boxes<<<nbk(cnt, 256), 256, 0, st>>>(ptr<int32_t>(p.lists[3].off), lo, hi, 2,
                                                        ptr<int32_t>(t.level), ptr<int32_t>(flag));
@@ -375,6 +387,7 @@ int build_eval_data(Plan& p) {
     }
     KF_CUDA(cudaStreamSynchronize(st));
     dev_free(flag); dev_free(pos); dev_free(scan_tmp);
+    if (p.precision == KIFMM_MIXED) KF_TRY(p2p_series_check(p));
     return KIFMM_OK;
 }
 
@@ -475,15 +488,19 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
 // and scattered by box index). Op_t = Op + t * op_stride (row stride ldop), t < nterm;
 // src_t(c) = src[t * count + c] (-1: no term), or base + c when src is NULL; dst NULL means
 // base + c. Tile TM = 16*RM rows x TN = 16*CN boxes, k-chunks of 16; each thread RM x CN.
+// Arithmetic in T; the input is read as TI and the output stored as TO.
 constexpr int AP_TK = 16;
 // With zoff != NULL the launch is a batch over blockIdx.z: batch z uses Op + z * zstride and
-// the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch).
-template <class T, int RM, int CN>
+// the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch). With
+// zoff == NULL and gridDim.z > 1 the terms are split over blockIdx.z (terms t = z, z + nz,
+// ...) and the partial sums are added atomically into out (which the caller zeroes).
+template <class T, class TI, class TO, int RM, int CN>
 __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t op_stride, int ldop, int nterm,
                                                int Mo, int Ki, const int32_t* src, const int32_t* dst, int64_t base,
-                                               int count, const T* __restrict__ in, int ldi, T* out, int ldo,
+                                               int count, const TI* __restrict__ in, int ldi, TO* out, int ldo,
                                                int accumulate, const int32_t* zoff, int64_t zstride) {
     constexpr int TM = 16 * RM, TN = 16 * CN;
+    int t0 = 0, tstep = 1;
     if (zoff) {
         const int z = blockIdx.z;
         Op += (int64_t)z * zstride;
@@ -491,13 +508,16 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
         dst += zoff[z];
         count = zoff[z + 1] - zoff[z];
         if ((int)(blockIdx.x * TN) >= count) return;
+    } else {
+        t0 = blockIdx.z;
+        tstep = gridDim.z;
     }
     __shared__ T As[AP_TK][TM + 1];
     __shared__ T Bs[AP_TK][TN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
     T acc[RM][CN] = {};
-    for (int t = 0; t < nterm; ++t) {
+    for (int t = t0; t < nterm; t += tstep) {
         const T* Opt = Op + (int64_t)t * op_stride;
         for (int k0 = 0; k0 < Ki; k0 += AP_TK) {
             for (int e = tid; e < TM * AP_TK; e += 256) {
@@ -511,7 +531,7 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
                 T v = T(0);
                 if (col < count && k < Ki) {
                     int64_t b = src ? (int64_t)src[(int64_t)t * count + col] : base + col;
-                    if (b >= 0) v = in[b * ldi + k];
+                    if (b >= 0) v = (T)in[b * ldi + k];
                 }
                 Bs[kk][cc] = v;
             }
@@ -540,8 +560,9 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
             int col = col0 + tx + 16 * j;
             if (col >= count) continue;
             int64_t b = dst ? dst[col] : base + col;
-            T* o = out + b * ldo + row;
-            *o = accumulate ? *o + acc[i][j] : acc[i][j];
+            TO* o = out + b * ldo + row;
+            if (!zoff && gridDim.z > 1) atomicAdd(o, (TO)acc[i][j]);
+            else *o = accumulate ? *o + (TO)acc[i][j] : (TO)acc[i][j];
         }
     }
 }
@@ -856,18 +877,27 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(EvalView E, const int32_t* leaves
 // every source read from shared memory serves two pair evaluations. 128 threads per leaf:
 // lane = target pair (targets t and t + 32 of a 64-target chunk), warp = source group.
 // Sources carry q * norm, so a pair costs (e^{-aR} - e^{-bR}) * (q norm) / R^3.
+// SERIES: some pair of the plan is closer than 0.5 / (b - a), where the factored form with
+// the series of 1 - e^{-(b-a)R} is needed; otherwise every pair takes the plain difference
+// of the two exponentials. GUARD: the sources are the target's own box, which holds the
+// target itself (r2 == 0 exactly: points are distinct), whose term is dropped.
 constexpr int P2Q_T = 128, P2Q_GRP = 4, P2Q_CHUNK = 1024;   // 16 KB of sources per block
-__device__ __forceinline__ void p2q_pair(const float4& x, const float4& v, const KParams& kp, Kahan& acc) {
+constexpr int P2Q_BLK = 8;   // plain FP32 partial sums of 8 pairs, compensated across partial sums
+template <bool SERIES, bool GUARD>
+__device__ __forceinline__ float p2q_term(const float4& x, const float4& v, const KParams& kp, float acc) {
     const float dx = x.x - v.x, dy = x.y - v.y, dz = x.z - v.z;
     const float r2 = dx * dx + dy * dy + dz * dz;
     const float rinv = rsqrt_approx(r2);
     const float R = r2 * rinv;
-    const float w = v.w * rinv * rinv * rinv;
-    const float val = exp_diff_f32(R, kp) * w;
-    acc.add(r2 > 0.f ? val : 0.f);   // j == i gives r2 == 0 exactly; points are distinct
+    const float w = v.w * rinv * (rinv * rinv);
+    float ed;
+    if (SERIES) ed = exp_diff_f32(R, kp);
+    else ed = ex2_approx(-kp.a_l2e * R) - ex2_approx(-kp.b_l2e * R);
+    if (GUARD) return r2 > 0.f ? fmaf(ed, w, acc) : acc;
+    return fmaf(ed, w, acc);
 }
 
-template <class TO>
+template <bool SERIES, class TO>
 __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* leaves, const int32_t* uoff,
                                                      const int32_t* uitems, const double* q, const double* far,
                                                      const double* sigma, const double* Is, const int32_t* perm,
@@ -887,12 +917,17 @@ __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* 
         const float4 far4 = make_float4(1e30f, 1e30f, 1e30f, 0.f);   // inactive slot: never near a source
         const float4 x0 = a0 ? E.loc[i0] : far4, x1 = a1 ? E.loc[i1] : far4;
         Kahan k0, k1;
-        int ui = u0, uoffs = 0;
+        // the source boxes in the order: B itself (index u0 - 1), then U(B) without B
+        int ui = u0 - 1, uoffs = 0, own_left = p1 - p0;
         while (ui < u1) {
             __syncthreads();
             int ns = 0, wi = ui, wo = uoffs;
             while (wi < u1 && ns < P2Q_CHUNK) {
-                const int A = uitems[wi];
+                const int A = wi < u0 ? B : uitems[wi];
+                if (wi >= u0 && A == B) {
+                    ++wi;
+                    continue;
+                }
                 const int aa = E.pstart[A], ab = E.pend[A];
                 const int take = min(ab - aa - wo, P2Q_CHUNK - ns);
                 const double* cA = E.centre + 3 * (int64_t)A;
@@ -909,11 +944,34 @@ __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* 
                 }
             }
             __syncthreads();
-#pragma unroll 4
-            for (int e = g; e < ns; e += P2Q_GRP) {
+            const int n_own = min(own_left, ns);   // the chunk's leading sources are B's own points
+            own_left -= n_own;
+            int e = g;
+            for (; e < n_own; e += P2Q_GRP) {
                 const float4 v = s32[e];
-                p2q_pair(x0, v, E.kp, k0);
-                p2q_pair(x1, v, E.kp, k1);
+                k0.add(p2q_term<SERIES, true>(x0, v, E.kp, 0.f));
+                k1.add(p2q_term<SERIES, true>(x1, v, E.kp, 0.f));
+            }
+            for (; e + (P2Q_BLK - 1) * P2Q_GRP < ns; e += P2Q_BLK * P2Q_GRP) {
+                float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+                for (int u = 0; u < P2Q_BLK; ++u) {
+                    const float4 v = s32[e + u * P2Q_GRP];
+                    s0 = p2q_term<SERIES, false>(x0, v, E.kp, s0);
+                    s1 = p2q_term<SERIES, false>(x1, v, E.kp, s1);
+                }
+                k0.add(s0);
+                k1.add(s1);
+            }
+            {
+                float s0 = 0.f, s1 = 0.f;
+                for (; e < ns; e += P2Q_GRP) {
+                    const float4 v = s32[e];
+                    s0 = p2q_term<SERIES, false>(x0, v, E.kp, s0);
+                    s1 = p2q_term<SERIES, false>(x1, v, E.kp, s1);
+                }
+                k0.add(s0);
+                k1.add(s1);
             }
             ui = wi;
             uoffs = wo;
@@ -934,6 +992,33 @@ __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* 
     }
 }
 
+// Plan time: the smallest squared distance (box-local FP32 coordinates, as in the pair
+// kernel) between two distinct points of one U pair, as float bits into *minbits.
+__global__ void __launch_bounds__(128) k_min_r2(EvalView E, const int32_t* leaves, const int32_t* uoff,
+                                                const int32_t* uitems, unsigned int* minbits) {
+    const int B = leaves[blockIdx.x];
+    const double* cB = E.centre + 3 * (int64_t)B;
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    float m = 3.0e38f;
+    for (int k = uoff[B]; k < uoff[B + 1]; ++k) {
+        const int A = uitems[k];
+        const double* cA = E.centre + 3 * (int64_t)A;
+        const float d0 = (float)(cA[0] - cB[0]), d1 = (float)(cA[1] - cB[1]), d2 = (float)(cA[2] - cB[2]);
+        const int aa = E.pstart[A], ab = E.pend[A];
+        for (int i = p0 + (int)threadIdx.x; i < p1; i += blockDim.x) {
+            const float4 x = E.loc[i];
+            for (int j = aa; j < ab; ++j) {
+                if (j == i) continue;
+                const float4 v = E.loc[j];
+                const float dx = x.x - (v.x + d0), dy = x.y - (v.y + d1), dz = x.z - (v.z + d2);
+                m = fminf(m, dx * dx + dy * dy + dz * dz);
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMin(minbits, __float_as_uint(m));
+}
+
 // ------------------------------------------------------------------------------------
 // driver
 // ------------------------------------------------------------------------------------
@@ -952,6 +1037,30 @@ static EvalView make_view(Plan& p) {
     return E;
 }
 
+// Whether any near pair is closer than 0.5 / (b - a) (with a 1 % margin), where the mixed
+// pair kernel needs the series form of 1 - e^{-(b-a)R}.
+static int p2p_series_check(Plan& p) {
+    p.p2p_series = true;
+    if (p.nleaves <= 0) return KIFMM_OK;
+    DevBuf mb;
+    KF_TRY(dev_alloc(mb, 4));
+    const unsigned int init = 0x7f7fffffu;   // largest finite float
+    KF_CUDA(cudaMemcpyAsync(mb.p, &init, 4, cudaMemcpyHostToDevice, p.stream));
+    EvalView E = make_view(p);
+    k_min_r2<<<(unsigned)p.nleaves, 128, 0, p.stream>>>(E, ptr<int32_t>(p.leaves), ptr<int32_t>(p.lists[0].off),
+                                                        ptr<int32_t>(p.lists[0].items), ptr<unsigned int>(mb));
+    KF_LAUNCH();
+    unsigned int bits = 0;
+    KF_CUDA(cudaMemcpyAsync(&bits, mb.p, 4, cudaMemcpyDeviceToHost, p.stream));
+    KF_CUDA(cudaStreamSynchronize(p.stream));
+    dev_free(mb);
+    float m;
+    std::memcpy(&m, &bits, 4);
+    const double rs = 1.01 * 0.5 / (p.b - p.a);
+    p.p2p_series = !((double)m >= rs * rs);
+    return KIFMM_OK;
+}
+
 static void mark(Plan& p, int k) {
     if (p.timing) cudaEventRecord(p.ev[k], p.stream);
 }
@@ -961,15 +1070,16 @@ template <> const double* sel<double>(const DevBuf& d64, const DevBuf&) { return
 template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return ptr<float>(d32); }
 
 // Op has row stride ldop; only its leading Mo x Ki block is applied (the rest is zero padding).
-template <class T>
+// nz > 1 without zoff splits the terms over nz slices that add atomically into out.
+template <class T, class TI = T, class TO = T>
 static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, const int32_t* src, const int32_t* dst,
-                        int64_t base, int count, const T* in, int ldi, T* out, int ldo, int acc, int nterm = 1,
+                        int64_t base, int count, const TI* in, int ldi, TO* out, int ldo, int acc, int nterm = 1,
                         int64_t op_stride = 0, const int32_t* zoff = nullptr, int nz = 1, int64_t zstride = 0) {
     if (count <= 0) return KIFMM_OK;
     constexpr int RM = ApplyShape<T>::RM, CN = ApplyShape<T>::CN;
     dim3 g(nbk(count, 16 * CN), nbk(Mo, 16 * RM), nz);
-    k_apply<T, RM, CN><<<g, 256, 0, st>>>(Op, op_stride, ldop, nterm, Mo, Ki, src, dst, base, count, in, ldi, out,
-                                          ldo, acc, zoff, zstride);
+    k_apply<T, TI, TO, RM, CN><<<g, 256, 0, st>>>(Op, op_stride, ldop, nterm, Mo, Ki, src, dst, base, count, in, ldi,
+                                                  out, ldo, acc, zoff, zstride);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -990,27 +1100,35 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         KF_TRY(x); \
         ++nl;      \
     } while (0)
-    // ---- upward: S2M check potentials, c = Sigma^+ U^T chk (Eq. (s2m)), then M2M (Eq. (m2m))
+    // ---- upward (Eqs. (s2m), (m2m)): check potentials of the leaves from their sources (S2M)
+    // and of the parents from their children's coefficients (M2M to the parent's upward check
+    // surface, in T), then c = Sigma^+ U^T chk for every box (the pseudo-inverse, FP64), level
+    // by level from the deepest
     KF_CUDA(cudaMemsetAsync(cu, 0, (size_t)t.nboxes * R * 8, st));
+    if (L - 1 > 2) {   // parents' check rows, accumulated atomically where the terms are split
+        const int64_t b0 = t.level_start[2], b1 = t.level_start[L - 1];
+        KF_CUDA(cudaMemsetAsync(ptr<double>(p.chk) + b0 * S, 0, (size_t)(b1 - b0) * S * 8, st));
+    }
     if (p.n_p2m > 0) {
         if (mixed) k_p2m<true><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
         else k_p2m<false><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
         KF_LAUNCH();
         ++nl;
     }
-    for (int l = 2; l < L; ++l) {
-        auto& LL = p.lv[l];
-        if (LL.n_leaf > 0)
-            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs),
-                                     0, LL.n_leaf, ptr<double>(p.chk), S, cu, R, 0));
-    }
     mark(p, 2);
-    for (int l = L - 2; l >= 2; --l) {   // parents at level l, 8 octant terms per parent
+    for (int l = L - 1; l >= 2; --l) {
         auto& LL = p.lv[l];
-        if (LL.n_par > 0)
-            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].A), R, p.ops[l].rank, p.ops[l + 1].rank,
-                                     ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par, cu, R, cu, R, 0,
-                                     8, (int64_t)R * R));
+        if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
+            constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
+            const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
+            const int nz = std::max(1, std::min(8, (2 * p.num_sms + tiles - 1) / tiles));
+            RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
+                                                 ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
+                                                 cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));
+        }
+        if (LL.n_up > 0)
+            RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.upb),
+                                     ptr<int32_t>(LL.upb), 0, LL.n_up, ptr<double>(p.chk), S, cu, R, 0));
     }
     mark(p, 3);
     // ---- M2L in coefficients (Eq. (m2l))
@@ -1140,12 +1258,16 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         const int32_t* ui = ptr<int32_t>(p.lists[0].items);
         unsigned g = (unsigned)p.nleaves;
         if (mixed) {
+            auto* kf64 = p.p2p_series ? k_p2p_mixed<true, double> : k_p2p_mixed<false, double>;
+            auto* kf32 = p.p2p_series ? k_p2p_mixed<true, float> : k_p2p_mixed<false, float>;
             if (dtype == KIFMM_F64)
-                k_p2p_mixed<double><<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
-                                                            ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (double*)S_out);
+                kf64<<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                             ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C,
+                                             (double*)S_out);
             else
-                k_p2p_mixed<float><<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
-                                                           ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C, (float*)S_out);
+                kf32<<<g, P2Q_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),
+                                             ptr<double>(p.sigma), ptr<double>(p.Isort), ptr<int32_t>(t.perm), C,
+                                             (float*)S_out);
         } else {
             if (dtype == KIFMM_F64)
                 k_p2p<false, double><<<g, P2P_T, smem, st>>>(E, ptr<int32_t>(p.leaves), uo, ui, ptr<double>(p.q), ptr<double>(p.far),

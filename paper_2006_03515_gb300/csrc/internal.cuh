@@ -91,10 +91,10 @@ struct LevelOps {
     DevBuf Ub;           // [S][R] U Sigma^+: coefficients d -> downward equivalent density
     DevBuf Vt;           // [R][S] V^T: downward check potential -> coefficients d
     DevBuf T;            // [343][R][R] M2L in coefficients, V^T K(x^{B,d}, y^{A,u}) V
-    DevBuf A;            // [8][R][R] M2M in coefficients, parent level = this level
+    DevBuf Mc;           // [8][S][R] M2M to the parent's upward check surface, K(x^{P,u}, y^{C_o,u}) V_{l+1}
     DevBuf Lo;           // [8][R][R] L2L in coefficients, parent level = this level
     // FP32 copies (mixed form)
-    DevBuf T32, Ub32, Vb32, Vt32, Lo32;
+    DevBuf T32, Ub32, Vb32, Vt32, Lo32, Mc32;
     // tensor-core M2L operands: TF32 hi/lo of T, [slot][k-chunk][row][128-byte swizzled row]
     DevBuf Thi, Tlo;
 };
@@ -150,6 +150,7 @@ struct Plan {
         DevBuf xboxes;     int n_x = 0;          // boxes with non-empty X list
         DevBuf parents;    int n_par = 0;        // non-leaf boxes of the level
         DevBuf par_kids;                         // [8][n_par] child per octant, -1 if empty
+        DevBuf upb;        int n_up = 0;         // leaves then parents of the level (upward solves)
         DevBuf l2l_src, l2l_dst, l2l_off;        // (parent, child) pairs concatenated over octants
         int l2l_max = 0;                         // largest octant batch
     };
@@ -157,6 +158,8 @@ struct Plan {
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
     int64_t eval_launches = 0;   // kernels of the last evaluation
     bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
+    int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
+    bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
     DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
     DevBuf tc_slots;             // [tile][344] active offset slots

@@ -282,6 +282,12 @@ int build_operators(Plan& p) {
     p.R = R;
     {
         const char* m2l = std::getenv("KIFMM_M2L");
+        {
+            int dev = 0;
+            if (cudaGetDevice(&dev) == cudaSuccess)
+                cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
+            p.num_sms = std::max(p.num_sms, 1);
+        }
         p.m2l_tensor = p.precision == KIFMM_MIXED && m2l_tc_supported(R) && !(m2l && std::string(m2l) == "simt");
     }
     const int64_t SR = (int64_t)S * R, RR = (int64_t)R * R;
@@ -332,8 +338,9 @@ int build_operators(Plan& p) {
                       kOffsetSlots));
         KF_CUDA(cudaStreamSynchronize(st));
     }
-    // ---- M2M and L2L in coefficients, parent level l -> child level l + 1
-    //   A_{l,o}  = G1_l  K(x^{P,u}, y^{C_o,u}) Vb_{l+1}
+    // ---- M2M and L2L, parent level l -> child level l + 1
+    //   Mc_{l,o} = K(x^{P,u}, y^{C_o,u}) Vb_{l+1}   (child coefficients -> parent check potential;
+    //              the parent's coefficients then follow from its pseudo-inverse, as at the leaves)
     //   Lo_{l,o} = Vt_{l+1} K(x^{C_o,d}, y^{P,d}) Ub_l
     for (int l = 2; l + 1 < L; ++l) {
         LevelOps& op = p.ops[l];
@@ -348,13 +355,12 @@ int build_operators(Plan& p) {
             }
         }
         KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), 48 * 8, cudaMemcpyHostToDevice, st));
-        KF_TRY(dev_alloc(op.A, 8 * RR * 8));
+        KF_TRY(dev_alloc(op.Mc, 8 * SR * 8));
         KF_TRY(dev_alloc(op.Lo, 8 * RR * 8));
         surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * rc,
                                                           ptr<double>(shifts), kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
-        KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(ch.Vb), R, 0, ptr<double>(w), R, SR, 8));
-        KF_TRY(gemm64(st, R, R, S, ptr<double>(op.G1), S, 0, ptr<double>(w), R, SR, ptr<double>(op.A), R, RR, 8));
+        KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(ch.Vb), R, 0, ptr<double>(op.Mc), R, SR, 8));
         surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * rc, kROuter * r,
                                                           ptr<double>(shifts) + 24, kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
@@ -376,7 +382,10 @@ int build_operators(Plan& p) {
             KF_TRY(f32_copy(st, op.Ub, op.Ub32, SR));
             KF_TRY(f32_copy(st, op.Vb, op.Vb32, SR));
             KF_TRY(f32_copy(st, op.Vt, op.Vt32, SR));
-            if (l + 1 < L) KF_TRY(f32_copy(st, op.Lo, op.Lo32, 8 * RR));
+            if (l + 1 < L) {
+                KF_TRY(f32_copy(st, op.Lo, op.Lo32, 8 * RR));
+                KF_TRY(f32_copy(st, op.Mc, op.Mc32, 8 * SR));
+            }
         }
     }
     KF_CUDA(cudaStreamSynchronize(st));
