@@ -28,13 +28,47 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20
 SM_COUNT = 152
-MUFU_PER_SM_CLK = 16.0
-MUFU_PER_PAIR = 3.0     # rsqrt + two exp2 per pair in the FP32 kernel
+# MUFU results per SM per clock on this machine's GB300 (microbenchmark with independent chains;
+# the command and numbers are in profiles/k_p2p_mixed_uniform96.md): ex2.approx and rsqrt.approx
+EX2_PER_SM_CLK = 30.2
+RSQ_PER_SM_CLK = 15.2
+PAIRS_PER_SM_CLK = 1.0 / (2.0 / EX2_PER_SM_CLK + 1.0 / RSQ_PER_SM_CLK)   # one rsqrt + two ex2 per pair
 TF32_OVER_BF16 = 0.5    # nominal dense TF32 / BF16 tensor rate
 FP64_TFLOPS = 1.25      # GB300 FP64 (nominal; FMA chains measured 1.01, the FP64 GEMM 1.13 TFLOP/s)
 
 
 METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
+
+# DRAM bytes (read + write) per launch from the committed ncu captures, valid while the kernel's
+# source is the one that was captured (else the roofline's traffic is null). The 96^3 capture has
+# the far-field structure of the 128^3 workload (same M2L launch); the pair kernel's traffic is
+# compulsory and scales with the point count (x (128/96)^3 for 128^3).
+PROFILED_TRAFFIC = {
+    "M2L": {"bytes": 705.74e6 + 16.07e6, "per_point_scaled": False,
+            "src": "paper_2006_03515_gb300/csrc/m2l_tc.cu",
+            "sha256": "2747b36cde2cdcd0581889ff1981c1e919177ac03152856dd8cfc5a0ebe56664",
+            "profile": "profiles/k_m2l_tc_uniform96.md"},
+    "P2P": {"bytes": 50.66e6 + 1.19e6, "per_point_scaled": True, "n_profiled": 96 ** 3,
+            "src": "paper_2006_03515_gb300/csrc/eval.cu",
+            "sha256": "b9d7b886dea533060d29a77841683ace42960e41b4d6553feb72abcc594101d9",
+            "profile": "profiles/k_p2p_mixed_uniform96.md"},
+}
+
+
+def profiled_traffic(key, npts, workload_is_128_uniform):
+    """Traffic per launch for the bench's workload, or None when the kernel changed or the
+    capture does not describe this workload."""
+    import hashlib
+    e = PROFILED_TRAFFIC.get(key)
+    if e is None or not workload_is_128_uniform:
+        return None
+    try:
+        with open(os.path.join(ROOT, e["src"]), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
+                return None
+    except OSError:
+        return None
+    return e["bytes"] * (npts / e["n_profiled"] if e["per_point_scaled"] else 1.0)
 
 
 def workload_name(args):
@@ -364,16 +398,22 @@ def main():
     sm_clk = 2070.0
     # rooflines of the three heavy kernels; the dominant one is "roofline"
     p2p_ach = info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3) / 1e9
-    p2p_peak = SM_COUNT * MUFU_PER_SM_CLK / MUFU_PER_PAIR * sm_clk * 1e6 / 1e9
+    if clk.get("sm_mhz"):
+        sm_clk = float(clk["sm_mhz"])
+    p2p_peak = SM_COUNT * PAIRS_PER_SM_CLK * sm_clk * 1e6 / 1e9
+    std = args.n == 128 and args.m0 == 6 and args.leaf == 64 and args.p == 760.0 and args.precision == "mixed"
     tf32_peak = peaks.get("bf16_tflops", 1947.8) * TF32_OVER_BF16
     m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
     up_ach = info["upward_flops"] / (ph_ms["M2M+UC2UE"] * 1e-3) / 1e12
     roofs = {
         "P2P": {"kernel": "k_p2p_mixed (near-field pair sum, FP32)", "bound": "alu", "achieved": p2p_ach,
-                "peak": p2p_peak, "unit": "Gpair/s", "frac": p2p_ach / p2p_peak, "traffic": None,
-                "peak_source": "derived: 152 SMs x 16 MUFU/clk x 2070 MHz / 3 MUFU per pair"},
+                "peak": p2p_peak, "unit": "Gpair/s", "frac": p2p_ach / p2p_peak,
+                "traffic": profiled_traffic("P2P", npts, std),
+                "peak_source": "derived from measured MUFU rates: 152 SMs x 1/(2/30.2 + 1/15.2) pairs/clk x "
+                               "median SM clock under load"},
         "M2L": {"kernel": "k_m2l_tc (tcgen05 3xTF32, coefficient basis)", "bound": "tensor", "achieved": m2l_ach,
-                "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (tf32_peak / 3.0), "traffic": None,
+                "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (tf32_peak / 3.0),
+                "traffic": profiled_traffic("M2L", npts, std),
                 "peak_source": "of measured: bf16_tflops x 0.5 (TF32/BF16 nominal) / 3 MMAs per product"},
         "upward": {"kernel": "k_apply<double> (UC2UE pseudo-inverse c = Sigma^+ U^T chk of leaves and parents, "
                              "FP64; the phase also holds the FP32 M2M translations)", "bound": "alu", "achieved": up_ach,

@@ -7,12 +7,21 @@
 //   SpecConv(v)(o, x) = (1/n^3) sum_{k in K} w_kz Re[ (R(k) V(k))_o e^{+2 pi i k.x/n} ],
 //   V(c, k) = sum_x v(c, x) e^{-2 pi i k.x/n},  K = Kx x Ky x Kz,
 //   Kx = Ky = {0..m-1} U {n-m..n-1}, Kz = {0..m-1}, w_0 = 1, w_{kz>=1} = 2.
-// The truncated transforms are done axis by axis as small dense DFTs against twiddle
-// tables (a partial DFT keeps 2m of n frequencies, so a full FFT would be wasted work).
+// The truncated transforms run axis by axis as small dense DFTs against twiddle tables (a
+// partial DFT keeps 2m of n frequencies, so a full FFT would be wasted work); the work is
+// bound by memory traffic, so the kernels are organised to touch each field once:
+//  * "z-row" kernels own the n values along the last axis of every channel at one (b, x, y):
+//    they fuse the lift, the inverse last-axis DFT, the pointwise layer W v + b, GELU, the
+//    projection, the next layer's forward last-axis DFT, and in the backward pass the
+//    weight-gradient partial sums;
+//  * "plane" kernels do the DFTs along the first two axes on the m-wide spectra, staged
+//    through shared memory;
+//  * the per-mode channel mix is tiled over a few modes, with R in shared memory.
 // Spectral weights R are held in FP32 (master) and used rounded to BF16 (FP32
 // accumulation) unless the model is switched to FP32 weights.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -24,6 +33,12 @@
 
 namespace kifmm {
 
+constexpr int MAXC = 64;              // widest layer
+constexpr int MAXP = 128;             // widest projection
+constexpr int SNO_MAX_JUDGE = 4096;   // most judge targets per photo_solve
+constexpr int ZR_T = 256;             // threads of the z-row kernels
+constexpr int ZR_RG = 4;              // z-row groups (b, x, y) per block
+
 struct SnoModel {
     int n = 64, C = 32, m = 12, L = 4, P = 64, maxB = 32;
     int bf16 = 1;
@@ -34,10 +49,14 @@ struct SnoModel {
     DevBuf theta, grad, adam_m, adam_v, rbf;   // rbf: BF16 copies of Rr, Ri per layer
     DevBuf tabs;                     // float2 twiddle tables
     int64_t tzf, tyf, tzb, txi, tzi, tzr;   // table offsets (float2 units)
-    // activations (FP32): v[L+1][B][C][np3], z[L][B][C][np3]
-    DevBuf v, z, s, cz, cy, cx, g, gx, gy, dv, dz, loss;
-    DevBuf ph, pda;                  // projection backward: GELU(a) and dL/da, [B][P][np3]
+    // fields (FP32): v[L+1][B][C][np3], z[L][B][C][np3], dz ping-pong [2][B][C][np3], y and dy [B][np3]
+    DevBuf v, z, dz, yb, dy, loss;
+    // spectra (float2): cz [B][C][n][n][m], cy / gx [B][C][n][2m][m], gy [B][C][n][n][m],
+    // V per layer [L][B][C][K], g / ga [B][C][K]
+    DevBuf cz, cy, gx, gy, Vst, g, ga;
     DevBuf jt, jref, jorig, jerr;    // photo_solve judge: targets, reference values, caller indices, error
+    int mix_mb = 1;                  // modes per block of the mixing kernels
+    size_t zr_smem_f = 0, zr_smem_b = 0, zr_smem_p = 0, mix_smem = 0, mixg_smem = 0;
     int64_t steps = 0;
 };
 
@@ -79,31 +98,33 @@ __device__ __forceinline__ float gelu_d(float x) {
     return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.3989422804014327f * expf(-0.5f * x * x);
 }
 
-// Twiddle tables. kind: frequency list for the output (forward) or input (inverse) index.
+// Twiddle tables: tzf[kz][z] = e^{-i kz z}, tzb = (w/n^3) e^{-i kz z}, tyf[k][y] = e^{-i k y}
+// (k = 0..2m-1 mapped to {0..m-1} U {n-m..n-1}), txi[x][k] = e^{+i k x},
+// tzi[z][kz] = (w/n^3) e^{+i kz z}, tzr[z][kz] = e^{+i kz z} (angles 2 pi / n units).
 __global__ void k_tables(int n, int m, float2* t, int64_t tzf, int64_t tyf, int64_t tzb, int64_t txi, int64_t tzi,
                          int64_t tzr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double tw = 6.283185307179586476925286766559 / n;
     const double n3 = (double)n * n * n;
-    auto kxy = [&](int k) { return k < m ? k : n - 2 * m + k; };   // index 0..2m-1 -> frequency
-    if (i < m * n) {   // tzf[kz][z] = e^{-i kz z}, tzb = (w/n^3) e^{-i kz z}
+    auto kxy = [&](int k) { return k < m ? k : n - 2 * m + k; };
+    if (i < m * n) {
         int kz = i / n, z = i % n;
         double a = tw * kz * z;
         double w = (kz == 0 ? 1.0 : 2.0) / n3;
         t[tzf + i] = make_float2((float)cos(a), (float)-sin(a));
         t[tzb + i] = make_float2((float)(w * cos(a)), (float)(-w * sin(a)));
     }
-    if (i < 2 * m * n) {   // tyf[k][y] = e^{-i ky y}
+    if (i < 2 * m * n) {
         int k = i / n, y = i % n;
         double a = tw * kxy(k) * y;
         t[tyf + i] = make_float2((float)cos(a), (float)-sin(a));
     }
-    if (i < n * 2 * m) {   // txi[x][k] = e^{+i kx x}
+    if (i < n * 2 * m) {
         int x = i / (2 * m), k = i % (2 * m);
         double a = tw * kxy(k) * x;
         t[txi + i] = make_float2((float)cos(a), (float)sin(a));
     }
-    if (i < n * m) {   // tzi[z][kz] = (w/n^3) e^{+i kz z}; tzr[z][kz] = e^{+i kz z}
+    if (i < n * m) {
         int z = i / m, kz = i % m;
         double a = tw * kz * z;
         double w = (kz == 0 ? 1.0 : 2.0) / n3;
@@ -112,130 +133,494 @@ __global__ void k_tables(int n, int m, float2* t, int64_t tzf, int64_t tyf, int6
     }
 }
 
-// out[o][j][i] = sum_q T[j][q] in[o][q][i] along the middle axis (lengths Lin -> Lout),
-// in/out real (float) or complex (float2); real output takes the real part.
-template <bool CIN, bool COUT>
-__global__ void k_dft(const void* __restrict__ in, void* __restrict__ out, const float2* __restrict__ T, int64_t outer,
-                      int Lin, int Lout, int64_t inner) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = outer * Lout * inner;
-    if (e >= total) return;
-    const int64_t i = e % inner;
-    const int j = (int)((e / inner) % Lout);
-    const int64_t o = e / (inner * Lout);
-    float re = 0.f, im = 0.f;
-    const float2* t = T + (int64_t)j * Lin;
-    for (int q = 0; q < Lin; ++q) {
-        const int64_t ii = (o * Lin + q) * inner + i;
-        const float2 w = t[q];
-        if (CIN) {
-            const float2 x = reinterpret_cast<const float2*>(in)[ii];
-            re += w.x * x.x - w.y * x.y;
-            im += w.x * x.y + w.y * x.x;
-        } else {
-            const float x = reinterpret_cast<const float*>(in)[ii];
-            re += w.x * x;
-            im += w.y * x;
+// Plane DFT: out[p][j][i] = sum_q T[j][q] in[p][q][i] (complex), p < P, j < Lout, i < inner.
+// A block takes PB planes (or one plane and a chunk of ICH columns), stages them in shared
+// memory and computes every output of those columns; T is read through the L1 cache.
+__global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, float2* __restrict__ out,
+                                               const float2* __restrict__ T, int64_t P, int Lin, int Lout, int inner,
+                                               int PB, int ICH, int nch) {
+    extern __shared__ float2 psh[];
+    const int64_t pb = blockIdx.x / nch;
+    const int ch = (int)(blockIdx.x % nch);
+    const int64_t p0 = pb * PB;
+    const int np = (int)min((int64_t)PB, P - p0);
+    const int i0 = ch * ICH;
+    const int W = min(ICH, inner - i0);
+    const int ncol = np * W;
+    for (int e = threadIdx.x; e < Lin * ncol; e += blockDim.x) {
+        const int q = e / ncol, col = e % ncol;
+        const int pl = col / W, w = col % W;
+        psh[q * ncol + col] = in[((p0 + pl) * Lin + q) * (int64_t)inner + i0 + w];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < Lout * ncol; e += blockDim.x) {
+        const int j = e / ncol, col = e % ncol;
+        const int pl = col / W, w = col % W;
+        const float2* t = T + (int64_t)j * Lin;
+        float re = 0.f, im = 0.f;
+        for (int q = 0; q < Lin; ++q) {
+            const float2 a = __ldg(t + q);
+            const float2 x = psh[q * ncol + col];
+            re = fmaf(a.x, x.x, fmaf(-a.y, x.y, re));
+            im = fmaf(a.x, x.y, fmaf(a.y, x.x, im));
+        }
+        out[((p0 + pl) * Lout + j) * (int64_t)inner + i0 + w] = make_float2(re, im);
+    }
+}
+
+// Channel mix per mode, MB modes per block: G[b][o][k] = sum_c R[k][o][c] V[b][c][k]
+// (adj = 1: G[b][c][k] = sum_o conj(R[k][o][c]) V[b][o][k]). R is staged as complex
+// [kk][row][C + 1] (conjugate-transposed for adj), V as [b][kk][c].
+template <class TR>
+__global__ void __launch_bounds__(256) k_mix(const TR* __restrict__ Rr, const TR* __restrict__ Ri,
+                                             const float2* __restrict__ V, float2* __restrict__ G, int B, int C,
+                                             int64_t K, int MB, int adj) {
+    extern __shared__ float2 msh[];
+    float2* Rs = msh;                                    // [MB][C][C + 1]
+    float2* Vs = msh + (size_t)MB * C * (C + 1);         // [B][MB][C]
+    float2* Gs = Vs + (size_t)B * MB * C;                // [B][C][MB]
+    const int64_t k0 = (int64_t)blockIdx.x * MB;
+    const int nk = (int)min((int64_t)MB, K - k0);
+    for (int e = threadIdx.x; e < nk * C * C; e += blockDim.x) {
+        const int kk = e / (C * C), o = (e / C) % C, c = e % C;
+        const int64_t ri = ((k0 + kk) * C + o) * C + c;
+        const float xr = (float)Rr[ri], xi = (float)Ri[ri];
+        if (adj) Rs[((size_t)kk * C + c) * (C + 1) + o] = make_float2(xr, -xi);
+        else Rs[((size_t)kk * C + o) * (C + 1) + c] = make_float2(xr, xi);
+    }
+    for (int e = threadIdx.x; e < B * C * nk; e += blockDim.x) {
+        const int kk = e % nk, c = (e / nk) % C, b = e / (nk * C);
+        Vs[((size_t)b * MB + kk) * C + c] = V[((int64_t)b * C + c) * K + k0 + kk];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * nk * C; e += blockDim.x) {
+        const int o = e % C, kk = (e / C) % nk, b = e / (C * nk);
+        const float2* r = Rs + ((size_t)kk * C + o) * (C + 1);
+        const float2* x = Vs + ((size_t)b * MB + kk) * C;
+        float re = 0.f, im = 0.f;
+        for (int c = 0; c < C; ++c) {
+            const float2 a = r[c], v = x[c];
+            re = fmaf(a.x, v.x, fmaf(-a.y, v.y, re));
+            im = fmaf(a.x, v.y, fmaf(a.y, v.x, im));
+        }
+        Gs[((size_t)b * C + o) * MB + kk] = make_float2(re, im);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < B * C * nk; e += blockDim.x) {
+        const int kk = e % nk, o = (e / nk) % C, b = e / (nk * C);
+        G[((int64_t)b * C + o) * K + k0 + kk] = Gs[((size_t)b * C + o) * MB + kk];
+    }
+}
+
+// dR[k][o][c] = sum_b dG[b][o][k] conj(V[b][c][k]) (real and imaginary planes, stored)
+__global__ void __launch_bounds__(256) k_mix_grad(const float2* __restrict__ dG, const float2* __restrict__ V,
+                                                  float* dRr, float* dRi, int B, int C, int64_t K, int MB) {
+    extern __shared__ float2 msh[];
+    float2* Gs = msh;                           // [B][MB][C]
+    float2* Vs = msh + (size_t)B * MB * C;      // [B][MB][C]
+    const int64_t k0 = (int64_t)blockIdx.x * MB;
+    const int nk = (int)min((int64_t)MB, K - k0);
+    for (int e = threadIdx.x; e < B * C * nk; e += blockDim.x) {
+        const int kk = e % nk, c = (e / nk) % C, b = e / (nk * C);
+        const int64_t gi = ((int64_t)b * C + c) * K + k0 + kk;
+        Gs[((size_t)b * MB + kk) * C + c] = dG[gi];
+        Vs[((size_t)b * MB + kk) * C + c] = V[gi];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nk * C * C; e += blockDim.x) {
+        const int c = e % C, o = (e / C) % C, kk = e / (C * C);
+        float re = 0.f, im = 0.f;
+        for (int b = 0; b < B; ++b) {
+            const float2 g = Gs[((size_t)b * MB + kk) * C + o];
+            const float2 x = Vs[((size_t)b * MB + kk) * C + c];
+            re = fmaf(g.x, x.x, fmaf(g.y, x.y, re));
+            im = fmaf(g.y, x.x, fmaf(-g.x, x.y, im));
+        }
+        const int64_t ri = ((k0 + kk) * C + o) * C + c;
+        dRr[ri] = re;
+        dRi[ri] = im;
+    }
+}
+
+// z-row kernels: shared-memory fields as [rows][n + 1] floats and tables as [rows][cols + 1]
+// float2 (odd strides keep column access free of bank conflicts); the float2 region starts
+// on an 8-byte boundary.
+
+// forward, layer input side: v0 = Wl u + bl (lift) and its last-axis DFT cz = Tzf v0
+__global__ void __launch_bounds__(ZR_T) k_lift_z(const float* __restrict__ u, const float* __restrict__ Wl,
+                                                 const float* __restrict__ bl, float* __restrict__ v0,
+                                                 float2* __restrict__ cz, const float2* __restrict__ Tzf, int B, int C,
+                                                 int n, int m) {
+    extern __shared__ float zsh[];
+    const int ns = n + 1;
+    float* vs = zsh;                                                 // [C][n + 1]
+    float* us = vs + C * ns;                                         // [n]
+    size_t fo = (size_t)(C * ns + n);
+    fo = (fo + 1) & ~(size_t)1;
+    float2* tf = reinterpret_cast<float2*>(zsh + fo);                // [m][n + 1]
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) tf[(e / n) * ns + e % n] = Tzf[e];
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2, np3 = n2 * n;
+    for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
+        const int64_t b = r / n2, xy = r % n2;
+        __syncthreads();
+        for (int e = threadIdx.x; e < n; e += blockDim.x) us[e] = u[b * np3 + xy * n + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            const float val = fmaf(Wl[c], us[zz], bl[c]);
+            vs[c * ns + zz] = val;
+            v0[((b * C + c) * n2 + xy) * n + zz] = val;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+            const int c = e / m, kz = e % m;
+            const float2* t = tf + kz * ns;
+            const float* x = vs + c * ns;
+            float re = 0.f, im = 0.f;
+            for (int zz = 0; zz < n; ++zz) {
+                re = fmaf(t[zz].x, x[zz], re);
+                im = fmaf(t[zz].y, x[zz], im);
+            }
+            cz[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
         }
     }
-    if (COUT) reinterpret_cast<float2*>(out)[e] = make_float2(re, im);
-    else reinterpret_cast<float*>(out)[e] = re;
 }
 
-// G[b][o][k] = sum_c R[k][o][c] V[b][c][k]; R as BF16 (or FP32) real/imag planes
-template <class TR>
-__global__ void k_mix(const TR* __restrict__ Rr, const TR* __restrict__ Ri, const float2* __restrict__ V,
-                      float2* __restrict__ G, int B, int C, int64_t K, int conj_adj) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * C * K) return;
-    const int64_t k = e % K;
-    const int o = (int)((e / K) % C);
-    const int b = (int)(e / (K * C));
-    float re = 0.f, im = 0.f;
-    for (int c = 0; c < C; ++c) {
-        // forward: R[k][o][c]; adjoint (conj_adj): conj(R[k][c][o])
-        const int64_t ri = conj_adj ? (k * C + c) * C + o : (k * C + o) * C + c;
-        const float ar = (float)Rr[ri], ai = conj_adj ? -(float)Ri[ri] : (float)Ri[ri];
-        const float2 x = V[((int64_t)b * C + c) * K + k];
-        re += ar * x.x - ai * x.y;
-        im += ar * x.y + ai * x.x;
+// forward, layer output side: z = Re(Tzi gy) + W v + b, v_next = GELU(z) (or z for the last
+// layer); optional: z stored (training), next layer's cz = Tzf v_next, projection y.
+__global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ gy, const float* __restrict__ v,
+                                                     const float* __restrict__ W, const float* __restrict__ bias,
+                                                     const float2* __restrict__ Tzi, const float2* __restrict__ Tzf,
+                                                     float* __restrict__ zout, float* __restrict__ vnext,
+                                                     float2* __restrict__ cznext, const float* __restrict__ Q1,
+                                                     const float* __restrict__ q1, const float* __restrict__ Q2,
+                                                     const float* __restrict__ q2, float* __restrict__ y, int B, int C,
+                                                     int n, int m, int P, int act) {
+    extern __shared__ float zsh[];
+    const int ns = n + 1, C1 = C + 1;
+    float* vs = zsh;                     // [C][n + 1]
+    float* vo = vs + C * ns;             // [C][n + 1]
+    float* Ws = vo + C * ns;             // [C][C + 1]
+    float* bs = Ws + C * C1;             // [C]
+    float* Qs = bs + C;                  // [P][C + 1] (projection)
+    float* ypart = Qs + (y ? P * C1 : 0);            // [4][n]
+    float* pq = ypart + (y ? 4 * n : 0);             // q1, Q2 [2][P]
+    size_t fo = (size_t)(pq + (y ? 2 * P : 0) - zsh);
+    fo = (fo + 1) & ~(size_t)1;
+    float2* gs = reinterpret_cast<float2*>(zsh + fo);   // [C][m]
+    float2* ti = gs + C * m;                            // [n][m + 1]
+    float2* tf = ti + n * (m + 1);                      // [m][n + 1]
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ws[(e / C) * C1 + e % C] = W[e];
+    for (int e = threadIdx.x; e < C; e += blockDim.x) bs[e] = bias[e];
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) ti[(e / m) * (m + 1) + e % m] = Tzi[e];
+    if (cznext)
+        for (int e = threadIdx.x; e < m * n; e += blockDim.x) tf[(e / n) * ns + e % n] = Tzf[e];
+    if (y) {
+        for (int e = threadIdx.x; e < P * C; e += blockDim.x) Qs[(e / C) * C1 + e % C] = Q1[e];
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            pq[e] = q1[e];
+            pq[P + e] = Q2[e];
+        }
     }
-    G[e] = make_float2(re, im);
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
+        const int64_t b = r / n2, xy = r % n2;
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            vs[c * ns + zz] = v[((b * C + c) * n2 + xy) * n + zz];
+        }
+        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+            const int o = e / m, kz = e % m;
+            gs[e] = gy[((b * C + o) * n2 + xy) * m + kz];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int o = e / n, zz = e % n;
+            float a = bs[o];
+            const float2* t = ti + zz * (m + 1);
+            const float2* gg = gs + o * m;
+            for (int kz = 0; kz < m; ++kz) a = fmaf(t[kz].x, gg[kz].x, fmaf(-t[kz].y, gg[kz].y, a));
+            const float* w = Ws + o * C1;
+            for (int c = 0; c < C; ++c) a = fmaf(w[c], vs[c * ns + zz], a);
+            const int64_t gi = ((b * C + o) * n2 + xy) * n + zz;
+            if (zout) zout[gi] = a;
+            const float vv = act ? gelu_f(a) : a;
+            vo[o * ns + zz] = vv;
+            vnext[gi] = vv;
+        }
+        __syncthreads();
+        if (cznext) {
+            for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+                const int c = e / m, kz = e % m;
+                const float2* t = tf + kz * ns;
+                const float* x = vo + c * ns;
+                float re = 0.f, im = 0.f;
+                for (int zz = 0; zz < n; ++zz) {
+                    re = fmaf(t[zz].x, x[zz], re);
+                    im = fmaf(t[zz].y, x[zz], im);
+                }
+                cznext[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
+            }
+        }
+        if (y) {   // y = q2 + sum_p Q2[p] GELU(q1[p] + Q1[p] . v); thread = (point, quarter of p)
+            for (int e = threadIdx.x; e < 4 * n; e += blockDim.x) {
+                const int zz = e % n, part = e / n;
+                float acc = 0.f;
+                for (int p = part; p < P; p += 4) {
+                    const float* qr = Qs + p * C1;
+                    float a = pq[p];
+                    for (int c = 0; c < C; ++c) a = fmaf(qr[c], vo[c * ns + zz], a);
+                    acc = fmaf(pq[P + p], gelu_f(a), acc);
+                }
+                ypart[part * n + zz] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < n; e += blockDim.x)
+                y[b * n2 * n + xy * n + e] = q2[0] + ((ypart[e] + ypart[n + e]) + (ypart[2 * n + e] + ypart[3 * n + e]));
+        }
+    }
 }
 
-// dR[k][o][c] += sum_b dG[b][o][k] conj(V[b][c][k])  (real and imaginary planes)
-__global__ void k_mix_grad(const float2* __restrict__ dG, const float2* __restrict__ V, float* dRr, float* dRi, int B,
-                           int C, int64_t K) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= K * C * C) return;
-    const int c = (int)(e % C);
-    const int o = (int)((e / C) % C);
-    const int64_t k = e / ((int64_t)C * C);
-    float re = 0.f, im = 0.f;
-    for (int b = 0; b < B; ++b) {
-        const float2 g = dG[((int64_t)b * C + o) * K + k];
-        const float2 x = V[((int64_t)b * C + c) * K + k];
-        re += g.x * x.x + g.y * x.y;
-        im += g.y * x.x - g.x * x.y;
+// backward of the projection and of the last layer's pointwise part (no GELU there):
+// a = Q1 v_L + q1, h = GELU(a), da = dy Q2 GELU'(a), dz_{L-1} = Q1^T da; czb = Tzb dz_{L-1};
+// block partial sums of dQ1, dq1, dQ2, dq2, dW_{L-1}, db_{L-1} added atomically.
+__global__ void __launch_bounds__(ZR_T) k_proj_bwd(const float* __restrict__ vL, const float* __restrict__ vLm1,
+                                                   const float* __restrict__ dy, const float* __restrict__ Q1,
+                                                   const float* __restrict__ q1, const float* __restrict__ Q2,
+                                                   const float2* __restrict__ Tzb, float* __restrict__ dz,
+                                                   float2* __restrict__ czb, float* gQ1, float* gq1, float* gQ2,
+                                                   float* gq2, float* gW, float* gb, int B, int C, int n, int m, int P) {
+    extern __shared__ float zsh[];
+    const int ns = n + 1, C1 = C + 1;
+    float* vs = zsh;                 // v_L [C][n + 1]
+    float* ws = vs + C * ns;         // v_{L-1} [C][n + 1]
+    float* ds = ws + C * ns;         // dz [C][n + 1]
+    float* das = ds + C * ns;        // da [P][n + 1]
+    float* hs = das + P * ns;        // h [P][n + 1]
+    float* Qs = hs + P * ns;         // Q1 [P][C + 1]
+    float* pq = Qs + P * C1;         // q1, Q2 [2][P]
+    float* dys = pq + 2 * P;         // dy [n]
+    size_t fo = (size_t)(dys + n - zsh);
+    fo = (fo + 1) & ~(size_t)1;
+    float2* tb = reinterpret_cast<float2*>(zsh + fo);   // [m][n + 1]
+    for (int e = threadIdx.x; e < P * C; e += blockDim.x) Qs[(e / C) * C1 + e % C] = Q1[e];
+    for (int e = threadIdx.x; e < P; e += blockDim.x) {
+        pq[e] = q1[e];
+        pq[P + e] = Q2[e];
     }
-    dRr[e] += re;
-    dRi[e] += im;
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) tb[(e / n) * ns + e % n] = Tzb[e];
+    // per-thread partial gradients: outputs o = threadIdx.x + j * ZR_T of each group
+    constexpr int NQ = MAXP * MAXC / ZR_T, NW = MAXC * MAXC / ZR_T;
+    float aQ1[NQ], aW[NW];
+    for (int j = 0; j < NQ; ++j) aQ1[j] = 0.f;
+    for (int j = 0; j < NW; ++j) aW[j] = 0.f;
+    float aq1 = 0.f, aQ2 = 0.f, ab = 0.f, aq2 = 0.f;   // thread < P: q1[t], Q2[t]; thread < C: b[t]; thread 0: q2
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
+        const int64_t b = r / n2, xy = r % n2;
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            const int64_t gi = ((b * C + c) * n2 + xy) * n + zz;
+            vs[c * ns + zz] = vL[gi];
+            ws[c * ns + zz] = vLm1[gi];
+        }
+        for (int e = threadIdx.x; e < n; e += blockDim.x) dys[e] = dy[b * n2 * n + xy * n + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
+            const int p = e / n, zz = e % n;
+            const float* qr = Qs + p * C1;
+            float a = pq[p];
+            for (int c = 0; c < C; ++c) a = fmaf(qr[c], vs[c * ns + zz], a);
+            hs[p * ns + zz] = gelu_f(a);
+            das[p * ns + zz] = dys[zz] * pq[P + p] * gelu_d(a);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            float a = 0.f;
+            for (int p = 0; p < P; ++p) a = fmaf(Qs[p * C1 + c], das[p * ns + zz], a);
+            ds[c * ns + zz] = a;
+            dz[((b * C + c) * n2 + xy) * n + zz] = a;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+            const int c = e / m, kz = e % m;
+            const float2* t = tb + kz * ns;
+            const float* x = ds + c * ns;
+            float re = 0.f, im = 0.f;
+            for (int zz = 0; zz < n; ++zz) {
+                re = fmaf(t[zz].x, x[zz], re);
+                im = fmaf(t[zz].y, x[zz], im);
+            }
+            czb[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
+        }
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) {
+            const int o = threadIdx.x + j * ZR_T;
+            if (o < P * C) {
+                const int p = o / C, c = o % C;
+                float s = 0.f;
+                for (int zz = 0; zz < n; ++zz) s = fmaf(das[p * ns + zz], vs[c * ns + zz], s);
+                aQ1[j] += s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            const int o = threadIdx.x + j * ZR_T;
+            if (o < C * C) {
+                const int oo = o / C, c = o % C;
+                float s = 0.f;
+                for (int zz = 0; zz < n; ++zz) s = fmaf(ds[oo * ns + zz], ws[c * ns + zz], s);
+                aW[j] += s;
+            }
+        }
+        if (threadIdx.x < P) {
+            float s1 = 0.f, s2 = 0.f;
+            for (int zz = 0; zz < n; ++zz) {
+                s1 += das[threadIdx.x * ns + zz];
+                s2 = fmaf(dys[zz], hs[threadIdx.x * ns + zz], s2);
+            }
+            aq1 += s1;
+            aQ2 += s2;
+        }
+        if (threadIdx.x < C) {
+            float s = 0.f;
+            for (int zz = 0; zz < n; ++zz) s += ds[threadIdx.x * ns + zz];
+            ab += s;
+        }
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int zz = 0; zz < n; ++zz) s += dys[zz];
+            aq2 += s;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NQ; ++j) {
+        const int o = threadIdx.x + j * ZR_T;
+        if (o < P * C) atomicAdd(gQ1 + o, aQ1[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const int o = threadIdx.x + j * ZR_T;
+        if (o < C * C) atomicAdd(gW + o, aW[j]);
+    }
+    if (threadIdx.x < P) {
+        atomicAdd(gq1 + threadIdx.x, aq1);
+        atomicAdd(gQ2 + threadIdx.x, aQ2);
+    }
+    if (threadIdx.x < C) atomicAdd(gb + threadIdx.x, ab);
+    if (threadIdx.x == 0) atomicAdd(gq2, aq2);
 }
 
-// lift: v0[b][c][p] = Wl[c] u[b][p] + bl[c]
-__global__ void k_lift(const float* u, const float* Wl, const float* bl, float* v0, int B, int C, int64_t np3) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * C * np3) return;
-    const int64_t p = e % np3;
-    const int c = (int)((e / np3) % C);
-    const int b = (int)(e / (np3 * C));
-    v0[e] = Wl[c] * u[(int64_t)b * np3 + p] + bl[c];
-}
-
-// pointwise layer: z = s + W v + b, vout = GELU(z) (or z for the last layer); one thread per point
-constexpr int MAXC = 64;
-constexpr int SNO_MAX_JUDGE = 4096;   // most judge targets per photo_solve
-__global__ void k_point(const float* s, const float* v, const float* W, const float* bias, float* z, float* vout,
-                        int B, int C, int64_t np3, int act) {
-    __shared__ float Ws[MAXC * MAXC], bs[MAXC];
-    for (int i = threadIdx.x; i < C * C; i += blockDim.x) Ws[i] = W[i];
-    for (int i = threadIdx.x; i < C; i += blockDim.x) bs[i] = bias[i];
-    __syncthreads();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * np3) return;
-    const int64_t p = e % np3, b = e / np3;
-    float x[MAXC];
-    for (int c = 0; c < C; ++c) x[c] = v[(b * C + c) * np3 + p];
-    for (int o = 0; o < C; ++o) {
-        float a = bs[o] + s[(b * C + o) * np3 + p];
-        for (int c = 0; c < C; ++c) a += Ws[o * C + c] * x[c];
-        z[(b * C + o) * np3 + p] = a;
-        vout[(b * C + o) * np3 + p] = act ? gelu_f(a) : a;
+// backward through layer l's output side: dv_l = Re(Tzr gyb) + W_l^T dz_l. For l > 0:
+// dz_{l-1} = dv_l GELU'(z_{l-1}), czb = Tzb dz_{l-1}, partial sums of dW_{l-1}, db_{l-1};
+// for l == 0: partial sums of the lift gradients (dWl from u, dbl).
+__global__ void __launch_bounds__(ZR_T) k_zinv_point_bwd(const float2* __restrict__ gyb, const float* __restrict__ dzl,
+                                                         const float* __restrict__ W, const float2* __restrict__ Tzr,
+                                                         const float* __restrict__ zprev, const float* __restrict__ vprev,
+                                                         const float2* __restrict__ Tzb, float* __restrict__ dzprev,
+                                                         float2* __restrict__ czb, float* gW, float* gb,
+                                                         const float* __restrict__ u, float* gWl, float* gbl, int B,
+                                                         int C, int n, int m) {
+    extern __shared__ float zsh[];
+    const int ns = n + 1, C1 = C + 1;
+    const bool first = (zprev == nullptr);   // l == 0
+    float* ds = zsh;                 // dz_l [C][n + 1]
+    float* dn = ds + C * ns;         // dv_l, then dz_{l-1} [C][n + 1]
+    float* ws = dn + C * ns;         // v_{l-1} or u [C][n + 1]
+    float* Ws = ws + C * ns;         // W_l [C][C + 1]
+    size_t fo = (size_t)(Ws + C * C1 - zsh);
+    fo = (fo + 1) & ~(size_t)1;
+    float2* gs = reinterpret_cast<float2*>(zsh + fo);   // [C][m]
+    float2* tr = gs + C * m;                            // [n][m + 1]
+    float2* tb = tr + n * (m + 1);                      // [m][n + 1]
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ws[(e / C) * C1 + e % C] = W[e];
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) tr[(e / m) * (m + 1) + e % m] = Tzr[e];
+    if (!first)
+        for (int e = threadIdx.x; e < m * n; e += blockDim.x) tb[(e / n) * ns + e % n] = Tzb[e];
+    constexpr int NW = MAXC * MAXC / ZR_T;
+    float aW[NW];
+    for (int j = 0; j < NW; ++j) aW[j] = 0.f;
+    float ab = 0.f, aw1 = 0.f;
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
+        const int64_t b = r / n2, xy = r % n2;
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            const int64_t gi = ((b * C + c) * n2 + xy) * n + zz;
+            ds[c * ns + zz] = dzl[gi];
+            if (!first) ws[c * ns + zz] = vprev[gi];
+        }
+        if (first)
+            for (int e = threadIdx.x; e < n; e += blockDim.x) ws[e] = u[b * n2 * n + xy * n + e];
+        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+            const int c = e / m, kz = e % m;
+            gs[e] = gyb[((b * C + c) * n2 + xy) * m + kz];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
+            const int c = e / n, zz = e % n;
+            float a = 0.f;
+            const float2* t = tr + zz * (m + 1);
+            const float2* gg = gs + c * m;
+            for (int kz = 0; kz < m; ++kz) a = fmaf(t[kz].x, gg[kz].x, fmaf(-t[kz].y, gg[kz].y, a));
+            for (int o = 0; o < C; ++o) a = fmaf(Ws[o * C1 + c], ds[o * ns + zz], a);
+            if (!first) {
+                const int64_t gi = ((b * C + c) * n2 + xy) * n + zz;
+                a *= gelu_d(zprev[gi]);
+                dzprev[gi] = a;
+            }
+            dn[c * ns + zz] = a;
+        }
+        __syncthreads();
+        if (!first) {
+            for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+                const int c = e / m, kz = e % m;
+                const float2* t = tb + kz * ns;
+                const float* x = dn + c * ns;
+                float re = 0.f, im = 0.f;
+                for (int zz = 0; zz < n; ++zz) {
+                    re = fmaf(t[zz].x, x[zz], re);
+                    im = fmaf(t[zz].y, x[zz], im);
+                }
+                czb[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
+            }
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                const int o = threadIdx.x + j * ZR_T;
+                if (o < C * C) {
+                    const int oo = o / C, c = o % C;
+                    float s = 0.f;
+                    for (int zz = 0; zz < n; ++zz) s = fmaf(dn[oo * ns + zz], ws[c * ns + zz], s);
+                    aW[j] += s;
+                }
+            }
+        }
+        if (threadIdx.x < C) {
+            float s = 0.f, s1 = 0.f;
+            for (int zz = 0; zz < n; ++zz) {
+                const float d = dn[threadIdx.x * ns + zz];
+                s += d;
+                if (first) s1 = fmaf(d, ws[zz], s1);
+            }
+            ab += s;
+            aw1 += s1;
+        }
     }
-}
-
-// projection: y = Q2 . GELU(Q1 v + q1) + q2
-__global__ void k_proj(const float* v, const float* Q1, const float* q1, const float* Q2, const float* q2, float* y,
-                       int B, int C, int P, int64_t np3) {
-    __shared__ float Qs[MAXC * MAXC * 2], qs[2 * MAXC], q2s[2 * MAXC];
-    for (int i = threadIdx.x; i < P * C; i += blockDim.x) Qs[i] = Q1[i];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        qs[i] = q1[i];
-        q2s[i] = Q2[i];
+    if (!first) {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            const int o = threadIdx.x + j * ZR_T;
+            if (o < C * C) atomicAdd(gW + o, aW[j]);
+        }
+        if (threadIdx.x < C) atomicAdd(gb + threadIdx.x, ab);
+    } else if (threadIdx.x < C) {
+        atomicAdd(gWl + threadIdx.x, aw1);
+        atomicAdd(gbl + threadIdx.x, ab);
     }
-    __syncthreads();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * np3) return;
-    const int64_t p = e % np3, b = e / np3;
-    float x[MAXC];
-    for (int c = 0; c < C; ++c) x[c] = v[(b * C + c) * np3 + p];
-    float out = q2[0];
-    for (int o = 0; o < P; ++o) {
-        float a = qs[o];
-        for (int c = 0; c < C; ++c) a += Qs[o * C + c] * x[c];
-        out += q2s[o] * gelu_f(a);
-    }
-    y[e] = out;
 }
 
 // loss and dL/dy: mean squared error; dy = 2 (y - t) / (B np3)
@@ -256,160 +641,6 @@ __global__ void k_loss(const float* y, const float* t, float* dy, int64_t N, dou
     if (threadIdx.x == 0) atomicAdd(loss, red[0] / (double)N);
 }
 
-// projection backward, per point: a = Q1 v + q1, h = GELU(a), da = dy Q2 .* GELU'(a),
-// dv = Q1^T da (h and da stored for the weight gradients)
-__global__ void k_proj_bwd(const float* v, const float* dy, const float* Q1, const float* q1, const float* Q2,
-                           float* h, float* da, float* dv, int B, int C, int P, int64_t np3) {
-    __shared__ float Qs[MAXC * MAXC * 2], qs[2 * MAXC], q2s[2 * MAXC];
-    for (int i = threadIdx.x; i < P * C; i += blockDim.x) Qs[i] = Q1[i];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) {
-        qs[i] = q1[i];
-        q2s[i] = Q2[i];
-    }
-    __syncthreads();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * np3) return;
-    const int64_t p = e % np3, b = e / np3;
-    float x[MAXC], g[MAXC];
-    for (int c = 0; c < C; ++c) {
-        x[c] = v[(b * C + c) * np3 + p];
-        g[c] = 0.f;
-    }
-    const float d = dy[e];
-    for (int o = 0; o < P; ++o) {
-        float a = qs[o];
-        for (int c = 0; c < C; ++c) a += Qs[o * C + c] * x[c];
-        h[(b * P + o) * np3 + p] = gelu_f(a);
-        const float dd = d * q2s[o] * gelu_d(a);
-        da[(b * P + o) * np3 + p] = dd;
-        for (int c = 0; c < C; ++c) g[c] += Qs[o * C + c] * dd;
-    }
-    for (int c = 0; c < C; ++c) dv[(b * C + c) * np3 + p] = g[c];
-}
-
-// pointwise layer backward, per point: dz = dvout .* GELU'(z) (or dvout), dvin = W^T dz
-// (in place: dvout and dvin may alias; each thread owns its point)
-__global__ void k_point_bwd(const float* dvout, const float* z, const float* W, float* dz, float* dvin, int B, int C,
-                            int64_t np3, int act) {
-    __shared__ float Ws[MAXC * MAXC];
-    for (int i = threadIdx.x; i < C * C; i += blockDim.x) Ws[i] = W[i];
-    __syncthreads();
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)B * np3) return;
-    const int64_t p = e % np3, b = e / np3;
-    float d[MAXC];
-    for (int o = 0; o < C; ++o) {
-        const int64_t ii = (b * C + o) * np3 + p;
-        const float g = dvout[ii];
-        d[o] = act ? g * gelu_d(z[ii]) : g;
-        dz[ii] = d[o];
-    }
-    for (int c = 0; c < C; ++c) {
-        float a = 0.f;
-        for (int o = 0; o < C; ++o) a += Ws[o * C + c] * d[o];
-        dvin[(b * C + c) * np3 + p] = a;
-    }
-}
-
-// weight gradient as a reduction GEMM: out[a][c] += sum over points (b, p) of
-// A[b][a][p] * Bm[b][c][p] (A: Ca rows, Bm: Cb rows, both [B][rows][np3], Ca, Cb <= 128).
-// Block (x, y) takes chunk x of the points and outputs y*OS_OUT .. y*OS_OUT + OS_OUT - 1,
-// stages 32 points at a time, accumulates its partial in registers (8 outputs per
-// thread of 256) and adds it to the gradient atomically.
-constexpr int OS_CHUNK = 2048, OS_OUT = 2048;
-__global__ void __launch_bounds__(256) k_outer_sum(const float* A, const float* Bm, float* out, int Ca, int Cb, int B,
-                                                   int64_t np3) {
-    __shared__ float As[2 * MAXC][33], Bs[2 * MAXC][33];
-    const int64_t N = (int64_t)B * np3;
-    const int64_t e0 = (int64_t)blockIdx.x * OS_CHUNK;
-    const int nout = Ca * Cb;
-    const int obase = blockIdx.y * OS_OUT;
-    float acc[8] = {};
-    for (int64_t s0 = e0; s0 < e0 + OS_CHUNK && s0 < N; s0 += 32) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < (Ca + Cb) * 32; i += blockDim.x) {
-            const int r = i / 32, k = i % 32;
-            const int64_t e = s0 + k;
-            float val = 0.f;
-            if (e < N) {
-                const int64_t b = e / np3, p = e % np3;
-                val = r < Ca ? A[(b * Ca + r) * np3 + p] : Bm[(b * Cb + (r - Ca)) * np3 + p];
-            }
-            if (r < Ca) As[r][k] = val;
-            else Bs[r - Ca][k] = val;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int o = obase + threadIdx.x + t * 256;
-            if (o < nout) {
-                const int a = o / Cb, c = o % Cb;
-                float s = 0.f;
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) s += As[a][k] * Bs[c][k];
-                acc[t] += s;
-            }
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
-        const int o = obase + threadIdx.x + t * 256;
-        if (o < nout) atomicAdd(&out[o], acc[t]);
-    }
-}
-
-// row sums out[r] += sum over (b, p) of A[b][r][p]
-__global__ void k_row_sum(const float* A, float* out, int R, int B, int64_t np3) {
-    __shared__ float s1[256];
-    const int r = blockIdx.y;
-    float a = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * np3;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = e % np3, b = e / np3;
-        a += A[(b * R + r) * np3 + p];
-    }
-    s1[threadIdx.x] = a;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) s1[threadIdx.x] += s1[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) atomicAdd(&out[r], s1[0]);
-}
-
-__global__ void k_add(float* a, const float* b, int64_t n) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e < n) a[e] += b[e];
-}
-
-// lift backward: gWl[c] += sum dv0 * u, gbl[c] += sum dv0
-__global__ void k_lift_bwd(const float* dv0, const float* u, float* gWl, float* gbl, int B, int C, int64_t np3) {
-    __shared__ float s1[256], s2[256];
-    const int c = blockIdx.y;
-    float a = 0.f, bsum = 0.f;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)B * np3;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = e % np3, b = e / np3;
-        const float g = dv0[(b * C + c) * np3 + p];
-        a += g * u[e];
-        bsum += g;
-    }
-    s1[threadIdx.x] = a;
-    s2[threadIdx.x] = bsum;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) {
-            s1[threadIdx.x] += s1[threadIdx.x + o];
-            s2[threadIdx.x] += s2[threadIdx.x + o];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        atomicAdd(&gWl[c], s1[0]);
-        atomicAdd(&gbl[c], s2[0]);
-    }
-}
-
 __global__ void k_adam(float* th, const float* g, float* mo, float* ve, int64_t n, float lr, float b1, float b2,
                        float eps, float c1, float c2) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -428,185 +659,113 @@ __global__ void k_to_bf16(const float* a, __nv_bfloat16* b, int64_t n) {
 }
 
 // ---- passes ---------------------------------------------------------------------------------
-static float* act(DevBuf& b, int64_t i, int64_t per) { return ptr<float>(b) + i * per; }
+static float* fld(const DevBuf& b, int64_t i, int64_t per) { return ptr<float>(b) + i * per; }
 
-// spectral convolution s = SpecConv(v) for layer l (B samples); cz/cy/cx/g/gx/gy scratch
-static int spec_forward(SnoModel& M, int l, const float* v, float* s, int B) {
-    const int n = M.n, m = M.m, C = M.C;
-    const int64_t BC = (int64_t)B * C;
-    const float2* T = ptr<float2>(M.tabs);
-    cudaStream_t st = M.st;
-    float2* cz = ptr<float2>(M.cz);
-    float2* cy = ptr<float2>(M.cy);
-    float2* cx = ptr<float2>(M.cx);
-    float2* g = ptr<float2>(M.g);
-    float2* gx = ptr<float2>(M.gx);
-    float2* gy = ptr<float2>(M.gy);
-    int64_t tot;
-    tot = BC * n * n * m;   // z: [BC*n*n][n] -> [BC*n*n][m]
-    k_dft<false, true><<<nbs(tot, 256), 256, 0, st>>>(v, cz, T + M.tzf, BC * n * n, n, m, 1);
-    KF_LAUNCH();
-    tot = BC * n * (2 * m) * m;   // y: [BC*n][n][m] -> [BC*n][2m][m]
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(cz, cy, T + M.tyf, BC * n, n, 2 * m, m);
-    KF_LAUNCH();
-    tot = BC * (2 * m) * (2 * m) * m;   // x: [BC][n][2m*m] -> [BC][2m][2m*m]
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(cy, cx, T + M.tyf, BC, n, 2 * m, (int64_t)2 * m * m);
-    KF_LAUNCH();
-    tot = BC * M.K;
-    if (M.bf16)
-        k_mix<__nv_bfloat16><<<nbs(tot, 256), 256, 0, st>>>(
-            ptr<__nv_bfloat16>(M.rbf) + (int64_t)l * 2 * M.K * C * C,
-            ptr<__nv_bfloat16>(M.rbf) + ((int64_t)l * 2 + 1) * M.K * C * C, cx, g, B, C, M.K, 0);
-    else
-        k_mix<float><<<nbs(tot, 256), 256, 0, st>>>(ptr<float>(M.theta) + M.off[o_rr(l)],
-                                                    ptr<float>(M.theta) + M.off[o_ri(l)], cx, g, B, C, M.K, 0);
-    KF_LAUNCH();
-    tot = BC * n * (2 * m) * m;   // inverse x: [BC][2m][2m*m] -> [BC][n][2m*m]
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(g, gx, T + M.txi, BC, 2 * m, n, (int64_t)2 * m * m);
-    KF_LAUNCH();
-    tot = BC * n * n * m;   // inverse y: [BC*n][2m][m] -> [BC*n][n][m]
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(gx, gy, T + M.txi, BC * n, 2 * m, n, m);
-    KF_LAUNCH();
-    tot = BC * n * n * n;   // inverse z (real part, weights w/n^3): [BC*n*n][m] -> [BC*n*n][n]
-    k_dft<true, false><<<nbs(tot, 256), 256, 0, st>>>(gy, s, T + M.tzi, BC * n * n, m, n, 1);
+// plane DFT launch: columns per block about 64 (several planes when inner is short)
+static int plane(SnoModel& M, const float2* in, float2* out, int64_t tab, int64_t P, int Lin, int Lout, int inner) {
+    int PB = 1, ICH = inner;
+    if (inner >= 64) ICH = 64;
+    else PB = std::max(1, 64 / inner);
+    const int nch = (inner + ICH - 1) / ICH;
+    const int64_t nb = ((P + PB - 1) / PB) * nch;
+    const size_t smem = (size_t)Lin * PB * std::min(ICH, inner) * sizeof(float2);
+    k_plane<<<(unsigned)nb, 256, smem, M.st>>>(in, out, ptr<float2>(M.tabs) + tab, P, Lin, Lout, inner, PB, ICH, nch);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
-static int forward(SnoModel& M, const float* u, float* y, int B) {
-    const int64_t per = (int64_t)B * M.C * M.np3;
+static int mix(SnoModel& M, int l, const float2* V, float2* G, int B, int adj) {
+    const int C = M.C;
+    const unsigned nb = nbs(M.K, M.mix_mb);
+    if (M.bf16)
+        k_mix<__nv_bfloat16><<<nb, 256, M.mix_smem, M.st>>>(
+            ptr<__nv_bfloat16>(M.rbf) + (int64_t)l * 2 * M.K * C * C,
+            ptr<__nv_bfloat16>(M.rbf) + ((int64_t)l * 2 + 1) * M.K * C * C, V, G, B, C, M.K, M.mix_mb, adj);
+    else
+        k_mix<float><<<nb, 256, M.mix_smem, M.st>>>(ptr<float>(M.theta) + M.off[o_rr(l)],
+                                                    ptr<float>(M.theta) + M.off[o_ri(l)], V, G, B, C, M.K, M.mix_mb,
+                                                    adj);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+static unsigned zr_blocks(const SnoModel& M, int B) { return nbs((int64_t)B * M.n * M.n, ZR_RG); }
+
+// forward; train: keep z_l and the spectra V_l for the backward pass
+static int forward(SnoModel& M, const float* u, float* y, int B, bool train) {
+    const int n = M.n, m = M.m, C = M.C, M2 = 2 * m;
+    const int64_t per = (int64_t)B * C * M.np3, BC = (int64_t)B * C;
     cudaStream_t st = M.st;
     const float* th = ptr<float>(M.theta);
-    k_lift<<<nbs(per, 256), 256, 0, st>>>(u, th + M.off[O_WL], th + M.off[O_BL], act(M.v, 0, per), B, M.C, M.np3);
+    const float2* T = ptr<float2>(M.tabs);
+    k_lift_z<<<zr_blocks(M, B), ZR_T, M.zr_smem_f, st>>>(u, th + M.off[O_WL], th + M.off[O_BL], fld(M.v, 0, per),
+                                                         ptr<float2>(M.cz), T + M.tzf, B, C, n, m);
     KF_LAUNCH();
+    const int q = o_q1(M);
     for (int l = 0; l < M.L; ++l) {
-        KF_TRY(spec_forward(M, l, act(M.v, l, per), ptr<float>(M.s), B));
-        k_point<<<nbs((int64_t)B * M.np3, 128), 128, 0, st>>>(ptr<float>(M.s), act(M.v, l, per), th + M.off[o_w(l)],
-                                                              th + M.off[o_b(l)], act(M.z, l, per),
-                                                              act(M.v, l + 1, per), B, M.C, M.np3, l < M.L - 1);
+        float2* V = ptr<float2>(M.Vst) + (train ? (int64_t)l * BC * M.K : 0);
+        KF_TRY(plane(M, ptr<float2>(M.cz), ptr<float2>(M.cy), M.tyf, BC * n, n, M2, m));            // y
+        KF_TRY(plane(M, ptr<float2>(M.cy), V, M.tyf, BC, n, M2, M2 * m));                            // x
+        KF_TRY(mix(M, l, V, ptr<float2>(M.g), B, 0));
+        KF_TRY(plane(M, ptr<float2>(M.g), ptr<float2>(M.gx), M.txi, BC, M2, n, M2 * m));             // x^-1
+        KF_TRY(plane(M, ptr<float2>(M.gx), ptr<float2>(M.gy), M.txi, BC * n, M2, n, m));             // y^-1
+        const bool last = l == M.L - 1;
+        k_zinv_point<<<zr_blocks(M, B), ZR_T, last ? M.zr_smem_p : M.zr_smem_f, st>>>(
+            ptr<float2>(M.gy), fld(M.v, l, per), th + M.off[o_w(l)], th + M.off[o_b(l)], T + M.tzi, T + M.tzf,
+            train ? fld(M.z, l, per) : nullptr, fld(M.v, l + 1, per), last ? nullptr : ptr<float2>(M.cz),
+            th + M.off[q], th + M.off[q + 1], th + M.off[q + 2], th + M.off[q + 3], last ? y : nullptr, B, C, n, m,
+            M.P, last ? 0 : 1);
         KF_LAUNCH();
     }
-    const int q = o_q1(M);
-    k_proj<<<nbs((int64_t)B * M.np3, 128), 128, 0, st>>>(act(M.v, M.L, per), th + M.off[q], th + M.off[q + 1],
-                                                         th + M.off[q + 2], th + M.off[q + 3], y, B, M.C, M.P,
-                                                         M.np3);
-    KF_LAUNCH();
-    return KIFMM_OK;
-}
-
-// adjoint of SpecConv for layer l: dvin += SpecConv^T(dz); dR accumulated
-static int spec_backward(SnoModel& M, int l, const float* dz, const float* v, float* dvin, int B) {
-    const int n = M.n, m = M.m, C = M.C;
-    const int64_t BC = (int64_t)B * C;
-    const float2* T = ptr<float2>(M.tabs);
-    cudaStream_t st = M.st;
-    float2* cz = ptr<float2>(M.cz);
-    float2* cy = ptr<float2>(M.cy);
-    float2* cx = ptr<float2>(M.cx);
-    float2* g = ptr<float2>(M.g);
-    float2* gx = ptr<float2>(M.gx);
-    float2* gy = ptr<float2>(M.gy);
-    int64_t tot;
-    // recompute the forward spectrum V of v (cx) for the weight gradient
-    tot = BC * n * n * m;
-    k_dft<false, true><<<nbs(tot, 256), 256, 0, st>>>(v, cz, T + M.tzf, BC * n * n, n, m, 1);
-    KF_LAUNCH();
-    tot = BC * n * (2 * m) * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(cz, cy, T + M.tyf, BC * n, n, 2 * m, m);
-    KF_LAUNCH();
-    tot = BC * (2 * m) * (2 * m) * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(cy, cx, T + M.tyf, BC, n, 2 * m, (int64_t)2 * m * m);
-    KF_LAUNCH();
-    // adjoint of the inverse transforms: dGy = (w/n^3) DFT_z(dz), dGx = DFT_y, dG = DFT_x
-    tot = BC * n * n * m;
-    k_dft<false, true><<<nbs(tot, 256), 256, 0, st>>>(dz, gy, T + M.tzb, BC * n * n, n, m, 1);
-    KF_LAUNCH();
-    tot = BC * n * (2 * m) * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(gy, gx, T + M.tyf, BC * n, n, 2 * m, m);
-    KF_LAUNCH();
-    tot = BC * (2 * m) * (2 * m) * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(gx, g, T + M.tyf, BC, n, 2 * m, (int64_t)2 * m * m);
-    KF_LAUNCH();
-    // weight gradient and the adjoint of the mixing: dV = R^H dG (into cy's storage)
-    float* gRr = ptr<float>(M.grad) + M.off[o_rr(l)];
-    float* gRi = ptr<float>(M.grad) + M.off[o_ri(l)];
-    k_mix_grad<<<nbs(M.K * C * C, 256), 256, 0, st>>>(g, cx, gRr, gRi, B, C, M.K);
-    KF_LAUNCH();
-    float2* dV = cx;   // V no longer needed
-    tot = BC * M.K;
-    float2* gtmp = cy;
-    if (M.bf16)
-        k_mix<__nv_bfloat16><<<nbs(tot, 256), 256, 0, st>>>(
-            ptr<__nv_bfloat16>(M.rbf) + (int64_t)l * 2 * M.K * C * C,
-            ptr<__nv_bfloat16>(M.rbf) + ((int64_t)l * 2 + 1) * M.K * C * C, g, gtmp, B, C, M.K, 1);
-    else
-        k_mix<float><<<nbs(tot, 256), 256, 0, st>>>(ptr<float>(M.theta) + M.off[o_rr(l)],
-                                                    ptr<float>(M.theta) + M.off[o_ri(l)], g, gtmp, B, C, M.K, 1);
-    KF_LAUNCH();
-    (void)dV;
-    // adjoint of the forward transforms: inverse-type x, y, then z (real part, unit weights)
-    tot = BC * n * (2 * m) * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(gtmp, gx, T + M.txi, BC, 2 * m, n, (int64_t)2 * m * m);
-    KF_LAUNCH();
-    tot = BC * n * n * m;
-    k_dft<true, true><<<nbs(tot, 256), 256, 0, st>>>(gx, gy, T + M.txi, BC * n, 2 * m, n, m);
-    KF_LAUNCH();
-    tot = BC * n * n * n;
-    k_dft<true, false><<<nbs(tot, 256), 256, 0, st>>>(gy, ptr<float>(M.s), T + M.tzr, BC * n * n, m, n, 1);
-    KF_LAUNCH();
-    k_add<<<nbs(tot, 256), 256, 0, st>>>(dvin, ptr<float>(M.s), tot);
-    KF_LAUNCH();
-    return KIFMM_OK;
-}
-
-// loss, gradients (into M.grad, zeroed first)
-static int outer_sum(SnoModel& M, const float* A, const float* Bm, float* out, int Ca, int Cb, int B) {
-    const int64_t N = (int64_t)B * M.np3;
-    k_outer_sum<<<dim3(nbs(N, OS_CHUNK), nbs((int64_t)Ca * Cb, OS_OUT)), 256, 0, M.st>>>(A, Bm, out, Ca, Cb, B,
-                                                                                          M.np3);
-    KF_LAUNCH();
-    return KIFMM_OK;
-}
-static int row_sum(SnoModel& M, const float* A, float* out, int R, int B) {
-    k_row_sum<<<dim3(256, R), 256, 0, M.st>>>(A, out, R, B, M.np3);
-    KF_LAUNCH();
     return KIFMM_OK;
 }
 
 static int loss_grad(SnoModel& M, const float* u, const float* t, int B, double* loss_host) {
+    const int n = M.n, m = M.m, C = M.C, M2 = 2 * m;
+    const int64_t per = (int64_t)B * C * M.np3, BC = (int64_t)B * C, N = (int64_t)B * M.np3;
     cudaStream_t st = M.st;
-    const int64_t per = (int64_t)B * M.C * M.np3, N = (int64_t)B * M.np3;
     float* gr = ptr<float>(M.grad);
     const float* th = ptr<float>(M.theta);
+    const float2* T = ptr<float2>(M.tabs);
     KF_CUDA(cudaMemsetAsync(gr, 0, M.nparam * 4, st));
     KF_CUDA(cudaMemsetAsync(M.loss.p, 0, 8, st));
-    float* y = ptr<float>(M.s) + per;   // the s buffer holds per + 3 N floats at least
-    float* dy = y + N;
-    KF_TRY(forward(M, u, y, B));
+    float* y = ptr<float>(M.yb);
+    float* dy = ptr<float>(M.dy);
+    KF_TRY(forward(M, u, y, B, true));
     k_loss<<<1024, 256, 0, st>>>(y, t, dy, N, ptr<double>(M.loss));
     KF_LAUNCH();
-    const int q = o_q1(M);
-    float* hbuf = ptr<float>(M.ph);
-    float* dabuf = ptr<float>(M.pda);
-    k_proj_bwd<<<nbs(N, 128), 128, 0, st>>>(act(M.v, M.L, per), dy, th + M.off[q], th + M.off[q + 1], th + M.off[q + 2],
-                                            hbuf, dabuf, ptr<float>(M.dv), B, M.C, M.P, M.np3);
+    const int q = o_q1(M), L = M.L;
+    float* dzA = fld(M.dz, 0, per);
+    float* dzB = fld(M.dz, 1, per);
+    k_proj_bwd<<<zr_blocks(M, B), ZR_T, M.zr_smem_b, st>>>(
+        fld(M.v, L, per), fld(M.v, L - 1, per), dy, th + M.off[q], th + M.off[q + 1], th + M.off[q + 2], T + M.tzb,
+        dzA, ptr<float2>(M.cz), gr + M.off[q], gr + M.off[q + 1], gr + M.off[q + 2], gr + M.off[q + 3],
+        gr + M.off[o_w(L - 1)], gr + M.off[o_b(L - 1)], B, C, n, m, M.P);
     KF_LAUNCH();
-    KF_TRY(outer_sum(M, dabuf, act(M.v, M.L, per), gr + M.off[q], M.P, M.C, B));   // Q1
-    KF_TRY(row_sum(M, dabuf, gr + M.off[q + 1], M.P, B));                          // q1
-    KF_TRY(outer_sum(M, dy, hbuf, gr + M.off[q + 2], 1, M.P, B));                  // Q2
-    KF_TRY(row_sum(M, dy, gr + M.off[q + 3], 1, B));                               // q2
-    for (int l = M.L - 1; l >= 0; --l) {
-        // dv holds dL/dv_{l+1}; dz <- it times GELU'(z_l); dv <- W^T dz + SpecConv^T dz
-        k_point_bwd<<<nbs(N, 128), 128, 0, st>>>(ptr<float>(M.dv), act(M.z, l, per), th + M.off[o_w(l)],
-                                                 ptr<float>(M.dz), ptr<float>(M.dv), B, M.C, M.np3, l < M.L - 1);
+    for (int l = L - 1; l >= 0; --l) {
+        // spectral adjoint of layer l: dG = Tyf Tyf Tzb dz_l (cz holds Tzb dz_l), dR, dV = R^H dG
+        KF_TRY(plane(M, ptr<float2>(M.cz), ptr<float2>(M.cy), M.tyf, BC * n, n, M2, m));
+        KF_TRY(plane(M, ptr<float2>(M.cy), ptr<float2>(M.g), M.tyf, BC, n, M2, M2 * m));
+        const unsigned nb = nbs(M.K, M.mix_mb);
+        k_mix_grad<<<nb, 256, M.mixg_smem, st>>>(ptr<float2>(M.g), ptr<float2>(M.Vst) + (int64_t)l * BC * M.K,
+                                                 gr + M.off[o_rr(l)], gr + M.off[o_ri(l)], B, C, M.K, M.mix_mb);
         KF_LAUNCH();
-        KF_TRY(outer_sum(M, ptr<float>(M.dz), act(M.v, l, per), gr + M.off[o_w(l)], M.C, M.C, B));
-        KF_TRY(row_sum(M, ptr<float>(M.dz), gr + M.off[o_b(l)], M.C, B));
-        KF_TRY(spec_backward(M, l, ptr<float>(M.dz), act(M.v, l, per), ptr<float>(M.dv), B));
+        KF_TRY(mix(M, l, ptr<float2>(M.g), ptr<float2>(M.ga), B, 1));
+        KF_TRY(plane(M, ptr<float2>(M.ga), ptr<float2>(M.gx), M.txi, BC, M2, n, M2 * m));
+        KF_TRY(plane(M, ptr<float2>(M.gx), ptr<float2>(M.gy), M.txi, BC * n, M2, n, m));
+        if (l > 0) {
+            k_zinv_point_bwd<<<zr_blocks(M, B), ZR_T, M.zr_smem_f, st>>>(
+                ptr<float2>(M.gy), dzA, th + M.off[o_w(l)], T + M.tzr, fld(M.z, l - 1, per), fld(M.v, l - 1, per),
+                T + M.tzb, dzB, ptr<float2>(M.cz), gr + M.off[o_w(l - 1)], gr + M.off[o_b(l - 1)], nullptr, nullptr,
+                nullptr, B, C, n, m);
+        } else {
+            k_zinv_point_bwd<<<zr_blocks(M, B), ZR_T, M.zr_smem_f, st>>>(
+                ptr<float2>(M.gy), dzA, th + M.off[o_w(l)], T + M.tzr, nullptr, nullptr, T + M.tzb, nullptr, nullptr,
+                nullptr, nullptr, u, gr + M.off[O_WL], gr + M.off[O_BL], B, C, n, m);
+        }
+        KF_LAUNCH();
+        std::swap(dzA, dzB);
     }
-    k_lift_bwd<<<dim3(256, M.C), 256, 0, st>>>(ptr<float>(M.dv), u, gr + M.off[O_WL], gr + M.off[O_BL], B, M.C,
-                                               M.np3);
-    KF_LAUNCH();
     if (loss_host) {
         KF_CUDA(cudaMemcpyAsync(loss_host, M.loss.p, 8, cudaMemcpyDeviceToHost, st));
         KF_CUDA(cudaStreamSynchronize(st));
@@ -721,6 +880,47 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
     };
     const int64_t per = (int64_t)max_batch * width * M.np3;
     const int64_t BC = (int64_t)max_batch * width;
+    // shared memory of the kernels (bytes), checked against the device's opt-in limit
+    {
+        const size_t ns = n + 1, C1 = width + 1, f4 = 4, f8 = 8, al = 16;
+        const size_t lift = (width * ns + n + 1) * f4 + al + (size_t)modes * ns * f8;
+        const size_t zf = (2 * width * ns + width * C1 + width) * f4 + al +
+                          ((size_t)width * modes + n * (modes + 1) + modes * ns) * f8;
+        const size_t zb = (3 * width * ns + width * C1) * f4 + al +
+                          ((size_t)width * modes + n * (modes + 1) + modes * ns) * f8;
+        M.zr_smem_f = std::max(lift, std::max(zf, zb));
+        M.zr_smem_p = zf + ((size_t)proj_width * C1 + 4 * n + 2 * proj_width) * f4;
+        M.zr_smem_b = (3 * width * ns + 2 * proj_width * ns + proj_width * C1 + 2 * proj_width + n) * f4 + al +
+                      (size_t)modes * ns * f8;
+        const size_t per_mode = (size_t)width * (width + 1 + 2 * max_batch) * f8;
+        M.mix_mb = (int)std::max<size_t>(1, std::min<size_t>(16, (96u << 10) / per_mode));
+        M.mix_smem = (size_t)M.mix_mb * per_mode;
+        M.mixg_smem = (size_t)2 * max_batch * M.mix_mb * width * f8;
+        const size_t plane_smem = (size_t)n * 64 * f8;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const size_t need = std::max({M.zr_smem_f, M.zr_smem_p, M.zr_smem_b, M.mix_smem, M.mixg_smem, plane_smem});
+        if (optin <= 0 || need > (size_t)optin) {
+            set_error("sno_create: the model's kernels need more shared memory than the device offers");
+            delete h;
+            return KIFMM_ERR_ARG;
+        }
+        const int lim = optin;
+        cudaFuncSetAttribute(k_lift_z, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zinv_point, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zinv_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_proj_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_mix<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_mix<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_mix_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("sno_create: cannot configure the kernels");
+            delete h;
+            return KIFMM_ERR_CUDA;
+        }
+    }
     int rc = KIFMM_OK;
     for (auto* pr : {&M.theta, &M.grad, &M.adam_m, &M.adam_v}) {
         rc = dev_alloc(*pr, M.nparam * 4);
@@ -740,19 +940,17 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
     if (cudaGetLastError() != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     if ((rc = dev_alloc(M.v, (size_t)(layers + 1) * per * 4))) return fail(rc);
     if ((rc = dev_alloc(M.z, (size_t)layers * per * 4))) return fail(rc);
-    if ((rc = dev_alloc(M.s, (size_t)std::max<int64_t>(per, 3 * (int64_t)max_batch * M.np3) * 4 + per * 4)))
-        return fail(rc);
-    if ((rc = dev_alloc(M.dv, (size_t)per * 4))) return fail(rc);
-    if ((rc = dev_alloc(M.dz, (size_t)per * 4))) return fail(rc);
+    if ((rc = dev_alloc(M.dz, (size_t)2 * per * 4))) return fail(rc);
+    if ((rc = dev_alloc(M.yb, (size_t)max_batch * M.np3 * 4))) return fail(rc);
+    if ((rc = dev_alloc(M.dy, (size_t)max_batch * M.np3 * 4))) return fail(rc);
     if ((rc = dev_alloc(M.cz, (size_t)BC * n * n * modes * 8))) return fail(rc);
-    if ((rc = dev_alloc(M.cy, (size_t)std::max<int64_t>(BC * n * 2 * modes * modes, BC * M.K) * 8))) return fail(rc);
-    if ((rc = dev_alloc(M.cx, (size_t)BC * M.K * 8))) return fail(rc);
-    if ((rc = dev_alloc(M.g, (size_t)BC * M.K * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.cy, (size_t)BC * n * 2 * modes * modes * 8))) return fail(rc);
     if ((rc = dev_alloc(M.gx, (size_t)BC * n * 2 * modes * modes * 8))) return fail(rc);
     if ((rc = dev_alloc(M.gy, (size_t)BC * n * n * modes * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.Vst, (size_t)layers * BC * M.K * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.g, (size_t)BC * M.K * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.ga, (size_t)BC * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.loss, 16))) return fail(rc);
-    if ((rc = dev_alloc(M.ph, (size_t)max_batch * proj_width * M.np3 * 4))) return fail(rc);
-    if ((rc = dev_alloc(M.pda, (size_t)max_batch * proj_width * M.np3 * 4))) return fail(rc);
     if ((rc = dev_alloc(M.jt, SNO_MAX_JUDGE * 4))) return fail(rc);
     if ((rc = dev_alloc(M.jref, SNO_MAX_JUDGE * 8))) return fail(rc);
     if ((rc = dev_alloc(M.jorig, SNO_MAX_JUDGE * 4))) return fail(rc);
@@ -766,9 +964,9 @@ void sno_destroy(sno_model_t h) {
     if (!h) return;
     SnoModel& M = h->m;
     if (M.st) cudaStreamSynchronize(M.st);
-    for (DevBuf* b : {&M.theta, &M.grad, &M.adam_m, &M.adam_v, &M.rbf, &M.tabs, &M.v, &M.z, &M.s, &M.cz, &M.cy,
-                      &M.cx, &M.g, &M.gx, &M.gy, &M.dv, &M.dz, &M.loss, &M.ph, &M.pda, &M.jt, &M.jref,
-                      &M.jorig, &M.jerr})
+    for (DevBuf* b : {&M.theta, &M.grad, &M.adam_m, &M.adam_v, &M.rbf, &M.tabs, &M.v, &M.z, &M.dz, &M.yb, &M.dy,
+                      &M.loss, &M.cz, &M.cy, &M.gx, &M.gy, &M.Vst, &M.g, &M.ga, &M.jt, &M.jref, &M.jorig,
+                      &M.jerr})
         dev_free(*b);
     delete h;
 }
@@ -863,7 +1061,7 @@ int sno_forward(sno_model_t h, const float* u_dev, float* y_dev, int batch) {
         set_error("sno_forward: invalid argument");
         return KIFMM_ERR_ARG;
     }
-    return forward(h->m, u_dev, y_dev, batch);
+    return forward(h->m, u_dev, y_dev, batch, false);
 }
 
 int sno_loss_grad(sno_model_t h, const float* u_dev, const float* t_dev, int batch, double* loss) {
@@ -903,11 +1101,11 @@ int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, doubl
     cudaStream_t saved = M.st;
     M.st = st;
     // surrogate: u = log(1 + I) in the caller's (grid) order, y -> S = e^y - 1
-    float* u = ptr<float>(M.dv);
-    float* y = ptr<float>(M.dz);
+    float* u = ptr<float>(M.dz);
+    float* y = ptr<float>(M.yb);
     k_log1p_in<<<nbs(n, 256), 256, 0, st>>>(I_dev, u, n);
     KF_LAUNCH();
-    int rc = forward(M, u, y, 1);
+    int rc = forward(M, u, y, 1, false);
     M.st = saved;
     KF_TRY(rc);
     k_expm1_out<<<nbs(n, 256), 256, 0, st>>>(y, S_dev, n);
