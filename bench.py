@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20
 SM_COUNT = 152
-# MUFU results per SM per clock on this machine's GB300 (microbenchmark with independent chains;
-# the command and numbers are in profiles/k_p2p_mixed_uniform96.md): ex2.approx and rsqrt.approx
+# MUFU results per SM per clock on this machine's GB300, measured by
+# paper_2006_03515_gb300/probes/unit_rates.cu (independent chains): ex2.approx and rsqrt.approx
 EX2_PER_SM_CLK = 30.2
 RSQ_PER_SM_CLK = 15.2
 PAIRS_PER_SM_CLK = 1.0 / (2.0 / EX2_PER_SM_CLK + 1.0 / RSQ_PER_SM_CLK)   # one rsqrt + two ex2 per pair
@@ -39,7 +39,7 @@ FP64_TFLOPS = 1.25      # GB300 FP64 (nominal; FMA chains measured 1.01, the FP6
 
 METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 
-# DRAM bytes (read + write) per launch from the committed ncu captures, valid while the kernel's
+# DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, valid while the kernel's
 # source is the one that was captured (else the roofline's traffic is null). The 96^3 capture has
 # the far-field structure of the 128^3 workload (same M2L launch); the pair kernel's traffic is
 # compulsory and scales with the point count (x (128/96)^3 for 128^3).
