@@ -33,7 +33,6 @@ SM_COUNT = 152
 EX2_PER_SM_CLK = 30.2
 RSQ_PER_SM_CLK = 15.2
 PAIRS_PER_SM_CLK = 1.0 / (2.0 / EX2_PER_SM_CLK + 1.0 / RSQ_PER_SM_CLK)   # one rsqrt + two ex2 per pair
-TF32_OVER_BF16 = 0.5    # nominal dense TF32 / BF16 tensor rate
 FP64_TFLOPS = 1.25      # GB300 FP64 (nominal; FMA chains measured 1.01, the FP64 GEMM 1.13 TFLOP/s)
 
 
@@ -402,7 +401,7 @@ def main():
         sm_clk = float(clk["sm_mhz"])
     p2p_peak = SM_COUNT * PAIRS_PER_SM_CLK * sm_clk * 1e6 / 1e9
     std = args.n == 128 and args.m0 == 6 and args.leaf == 64 and args.p == 760.0 and args.precision == "mixed"
-    tf32_peak = peaks.get("bf16_tflops", 1947.8) * TF32_OVER_BF16
+    f16_peak = peaks.get("bf16_tflops", 1947.8)   # dense FP16 and BF16 share the tensor rate
     m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
     up_ach = info["upward_flops"] / (ph_ms["M2M+UC2UE"] * 1e-3) / 1e12
     roofs = {
@@ -411,10 +410,11 @@ def main():
                 "traffic": profiled_traffic("P2P", npts, std),
                 "peak_source": "derived from measured MUFU rates: 152 SMs x 1/(2/30.2 + 1/15.2) pairs/clk x "
                                "median SM clock under load"},
-        "M2L": {"kernel": "k_m2l_tc (tcgen05 3xTF32, coefficient basis)", "bound": "tensor", "achieved": m2l_ach,
-                "peak": tf32_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (tf32_peak / 3.0),
+        "M2L": {"kernel": "k_m2l_tc (tcgen05 kind::f16, 3-term FP16 split with power-of-two scaling, "
+                          "coefficient basis)", "bound": "tensor", "achieved": m2l_ach,
+                "peak": f16_peak / 3.0, "unit": "TFLOP/s", "frac": m2l_ach / (f16_peak / 3.0),
                 "traffic": profiled_traffic("M2L", npts, std),
-                "peak_source": "of measured: bf16_tflops x 0.5 (TF32/BF16 nominal) / 3 MMAs per product"},
+                "peak_source": "of measured: bf16_tflops (dense FP16 = BF16 rate) / 3 MMAs per product"},
         "upward": {"kernel": "k_apply<double> (UC2UE pseudo-inverse c = Sigma^+ U^T chk of leaves and parents, "
                              "FP64; the phase also holds the FP32 M2M translations)", "bound": "alu", "achieved": up_ach,
                    "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": up_ach / FP64_TFLOPS, "traffic": None,

@@ -37,7 +37,7 @@ static void free_plan(Plan* p) {
                           &o.Thi, &o.Tlo})
             dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
-                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->dd, &p->phid, &p->phiu,
+                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
                       &p->tc_tiles, &p->tc_boxes, &p->tc_slots})
         dev_free(*b);

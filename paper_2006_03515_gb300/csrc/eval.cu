@@ -377,8 +377,9 @@ int build_eval_data(Plan& p) {
     KF_CUDA(cudaMemsetAsync(p.phid.p, 0, (size_t)nb * S * ts, st));
     if (p.precision == KIFMM_MIXED) KF_TRY(dev_alloc(p.cu32, (size_t)nb * R * 4));
     if (p.m2l_tensor) {
-        KF_TRY(dev_alloc(p.chi, (size_t)nb * R * 4));
-        KF_TRY(dev_alloc(p.clo, (size_t)nb * R * 4));
+        KF_TRY(dev_alloc(p.chi, (size_t)nb * R * 2));
+        KF_TRY(dev_alloc(p.clo, (size_t)nb * R * 2));
+        KF_TRY(dev_alloc(p.cexp, (size_t)nb * 4));
     }
     if (p.lists[3].len > 0) KF_TRY(dev_alloc(p.chkx, (size_t)nb * S * ts));
     if (p.lists[2].len > 0) {
@@ -1140,7 +1141,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         ++nl;
         c = reinterpret_cast<const T*>(ptr<float>(p.cu32));
         if (p.m2l_tensor) {
-            KF_TRY(m2l_tc_split(st, cu, m, ptr<float>(p.chi), ptr<float>(p.clo)));
+            KF_TRY(m2l_tc_split(st, cu, t.nboxes, R, p.chi.p, p.clo.p, ptr<int>(p.cexp)));
             ++nl;
         }
     } else {
@@ -1149,11 +1150,12 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     if (sizeof(T) == 4 && p.m2l_tensor) {
         M2LTables tabs{};
         for (int l = 2; l < L; ++l) {
-            tabs.hi[l] = ptr<float>(p.ops[l].Thi);
-            tabs.lo[l] = ptr<float>(p.ops[l].Tlo);
+            tabs.hi[l] = p.ops[l].Thi.p;
+            tabs.lo[l] = p.ops[l].Tlo.p;
+            tabs.sT[l] = p.ops[l].tc_sT;
         }
         KF_TRY(launch_m2l_tc(st, tabs, R, ptr<int4>(p.tc_tiles), p.tc_ntiles, ptr<int32_t>(p.tc_boxes),
-                             ptr<int32_t>(p.vtab), ptr<int32_t>(p.tc_slots), ptr<float>(p.chi), ptr<float>(p.clo),
+                             ptr<int32_t>(p.vtab), ptr<int32_t>(p.tc_slots), p.chi.p, p.clo.p, ptr<int>(p.cexp),
                              reinterpret_cast<float*>(dd), ptr<int>(p.err)));
         ++nl;
     } else {

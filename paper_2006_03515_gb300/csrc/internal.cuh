@@ -95,8 +95,9 @@ struct LevelOps {
     DevBuf Lo;           // [8][R][R] L2L in coefficients, parent level = this level
     // FP32 copies (mixed form)
     DevBuf T32, Ub32, Vb32, Vt32, Lo32, Mc32;
-    // tensor-core M2L operands: TF32 hi/lo of T, [slot][k-chunk][row][128-byte swizzled row]
+    // tensor-core M2L operands: FP16 hi/lo of T 2^tc_sT, [slot][k-chunk][row][128-byte swizzled row]
     DevBuf Thi, Tlo;
+    int tc_sT = 0;
 };
 
 struct Plan {
@@ -130,7 +131,8 @@ struct Plan {
     DevBuf chkx;       // T[nb*S]  downward check potentials from the X list (S2L)
     DevBuf cu;         // f64[nb*R] upward coefficients c
     DevBuf cu32;       // f32[nb*R] (mixed) FP32 copy of c for the SIMT M2L and the W list
-    DevBuf chi, clo;   // f32[nb*R] (mixed, tensor-core M2L) TF32 hi/lo parts of c
+    DevBuf chi, clo;   // f16[nb*R] (mixed, tensor-core M2L) hi/lo parts of c 2^cexp
+    DevBuf cexp;       // i32[nb] per-box power-of-two scale of chi/clo
     DevBuf dd;         // T[nb*R]  downward coefficients d
     DevBuf phid;       // T[nb*S]  downward equivalent densities of the leaves
     DevBuf phiu;       // T[nb*S]  upward equivalent densities (only when W lists exist)
@@ -191,14 +193,17 @@ int build_operators(Plan& p);
 int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
 // m2l_tc.cu
 int m2l_tc_supported(int R);
-int m2l_tc_prepare(cudaStream_t st, const double* T, int R, float* Thi, float* Tlo);
-int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float* clo);
-struct M2LTables {                 // per-level TF32 hi/lo M2L tables for the tensor-core kernel
-    const float* hi[kMaxLevel + 1];
-    const float* lo[kMaxLevel + 1];
+int64_t m2l_tc_table_elems(int R);   // FP16 elements of one level's Thi (or Tlo)
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out);
+int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp);
+struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the tensor-core kernel
+    const void* hi[kMaxLevel + 1];
+    const void* lo[kMaxLevel + 1];
+    int sT[kMaxLevel + 1];         // the tables hold T 2^sT
 };
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
-                  const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err);
+                  const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
+                  int* err);
 // api.cu / eval.cu helpers for the surrogate
 Plan* kifmm_plan_internal(kifmm_plan_t h);
 int kifmm_scatter_weights(Plan& p, const double* I);

@@ -1,33 +1,43 @@
-// M2L (Eq. (m2l)) on the 5th-generation tensor cores, split 3xTF32 with FP32 accumulation.
+// M2L (Eq. (m2l)) on the 5th-generation tensor cores: a 3-term FP16 split with FP32
+// accumulation (x = x_hi + x_lo, both FP16 with the 11-bit significand of TF32, products
+// hi*hi + hi*lo + lo*hi), so the result carries the accuracy of a 3xTF32 product at half
+// the operand bytes and twice the MMA rate of kind::tf32. FP16's exponent range is handled by
+// exact power-of-two scaling: each box's coefficient row c[A] by 2^{e_A} and each level's T
+// table by 2^{e_T} (largest magnitude near 2^14); the epilogue undoes 2^{e_A + e_T} per slot.
 //
 // In the coefficient basis the translation of one level is, for every target box B,
 //   d[B] = sum over the offset slots of V(B):  T[slot] c[A(B, slot)],
 // with T[slot] (R x R) shared by every pair with that relative offset. One CTA takes a
 // tile of 128 target boxes of a level (boxes grouped by their octant inside the parent,
 // so that the tile's boxes share one set of about 189 offsets) and, per offset slot and
-// 32-wide k-chunk, multiplies the gathered source rows c[A] (A operand, 128 x 32) by the
-// chunk of T[slot] (B operand, R x 32), both K-major in the 128-byte swizzled layout, as
-// hi*hi + hi*lo + lo*hi TF32 MMAs (x = x_hi + x_lo, both TF32).
+// 64-wide k-chunk, multiplies the gathered source rows c[A] (A operand, 128 x 64) by the
+// chunk of T[slot] (B operand, R x 64), both K-major in the 128-byte swizzled layout.
 //
 // Roles (warp specialization, 11 warps):
 //  * warps 8-9, producers: per iteration each thread gathers two source rows with
 //    16-byte cp.async copies (hi and lo, zero-filled where the box has no source at this
 //    offset); thread 0 of warp 8 also moves the pre-swizzled B chunk with two 1-D bulk
 //    copies. Completion arrives on the stage's "full" mbarrier.
-//  * warp 10, lane 0: waits for a full stage, issues 4 k-steps x 3 MMAs into the slot's
+//  * warp 10, lane 0: waits for a full stage, issues its k-steps x 3 MMAs into the slot's
 //    tensor-memory accumulator and commits the stage's "empty" mbarrier; after the last
 //    chunk of a slot it commits the accumulator's "ready" mbarrier.
-//  * warps 0-7, epilogue: two accumulators alternate between slots; the epilogue adds a
-//    finished one into FP32 registers (round-to-nearest) and releases it. The tensor
-//    core's own accumulation thus spans one slot, not the whole V list.
+//  * warps 0-7, epilogue: two accumulators alternate between slots; the epilogue scales a
+//    finished one by the slot's 2^{-(e_A + e_T)} into FP32 registers (round-to-nearest) and
+//    releases it. The tensor core's own accumulation thus spans one slot, not the V list.
 // Every wait is bounded; a timeout sets an abort flag that ends the other roles' waits,
 // records an error code, and the tensor memory is freed before the CTA exits.
+#include <cuda_fp16.h>
+
+#include <cmath>
+#include <cstring>
+
 #include "internal.cuh"
 
 namespace kifmm {
 
 constexpr int TC_M = 128;                 // target boxes per tile = MMA M
-constexpr int TC_KC = 32;                 // k-chunk: 32 FP32 = one 128-byte swizzle row
+constexpr int TC_KH = 64;                 // k-chunk: 64 FP16 = one 128-byte swizzle row
+constexpr int TC_HI_EXP = 14;             // scaled operands keep their largest magnitude near 2^14
 constexpr int TC_EPI = 256;               // epilogue threads (warps 0-7)
 constexpr int TC_PROD = 64;               // producer threads (warps 8-9), two source rows each
 constexpr int TC_THREADS = TC_EPI + TC_PROD + 32;
@@ -35,16 +45,17 @@ constexpr uint32_t TC_SPIN = 1u << 20;   // a normal wait needs a few hundred po
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ uint32_t tf32_rna(float x) {
-    uint32_t u;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
-    return u;
+// Byte offset of (row, k) inside a [rows x 64 FP16] tile in the 128-byte swizzled layout:
+// rows of 128 bytes, 16-byte chunk j of row r stored at chunk j ^ (r mod 8).
+__host__ __device__ __forceinline__ uint32_t sw128_off_h(int row, int k) {
+    return (uint32_t)row * 128u + (uint32_t)((((k >> 3) ^ (row & 7)) << 4) | ((k & 7) << 1));
 }
 
-// Byte offset of (row, k) inside a [rows x 32 FP32] tile in the 128-byte swizzled layout:
-// rows of 128 bytes, 16-byte chunk j of row r stored at chunk j ^ (r mod 8).
-__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
-    return (uint32_t)row * 128u + (uint32_t)((((k >> 2) ^ (row & 7)) << 4) | ((k & 3) << 2));
+// 2^e as a float for integer e (0 below the normal range, infinity above it)
+__device__ __forceinline__ float pow2i(int e) {
+    if (e < -126) return 0.f;
+    if (e > 127) return __int_as_float(0x7f800000);
+    return __int_as_float((127 + e) << 23);
 }
 
 // Shared-memory matrix descriptor (tcgen05): start >> 4 in bits [0,14), leading byte
@@ -61,16 +72,16 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9 and
-// 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor, kind::f16: D FP32 (bits 4-5 = 1), A and B FP16 (bits 7-9 and
+// 10-12 = 0), both K-major, N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
         "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
@@ -111,31 +122,55 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32
 // ------------------------------------------------------------------------------------
 // plan and per-evaluation operand preparation
 // ------------------------------------------------------------------------------------
-// T (FP64 [343][R][R]) -> Thi/Tlo (FP32, TF32-rounded) in the order
-// [slot][k-chunk][row][128-byte swizzled row], so that one chunk of one slot is a
-// contiguous R*128-byte image of the shared-memory B tile.
-__global__ void k_swizzle_T(const double* T, int R, float* Thi, float* Tlo) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t RR = (int64_t)R * R;
-    if (e >= (int64_t)kOffsetSlots * RR) return;
-    const int64_t slot = e / RR;
-    const int row = (int)((e % RR) / R), k = (int)(e % R);
-    const float x = (float)T[e];
-    const uint32_t h = tf32_rna(x);
-    const uint32_t l = tf32_rna(x - __uint_as_float(h));
-    const int64_t byte = slot * RR * 4 + (int64_t)(k / TC_KC) * R * 128 + sw128_off(row, k % TC_KC);
-    reinterpret_cast<uint32_t*>(Thi)[byte / 4] = h;
-    reinterpret_cast<uint32_t*>(Tlo)[byte / 4] = l;
+// largest |T| of a level's table, as the bits of a non-negative double (ordered like integers)
+__global__ void k_absmax(const double* x, int64_t n, unsigned long long* out) {
+    double m = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
-// upward coefficients (FP64) -> TF32 hi/lo pair of their FP32 value
-__global__ void k_split_c(const double* c, int64_t n, float* chi, float* clo) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
-    const float x = (float)c[e];
-    const uint32_t h = tf32_rna(x);
-    chi[e] = __uint_as_float(h);
-    clo[e] = __uint_as_float(tf32_rna(x - __uint_as_float(h)));
+// T (FP64 [343][R][R]) * 2^sT -> Thi/Tlo (FP16) in the order [slot][k-chunk][row][128-byte
+// swizzled row of 64 FP16], k >= R zero, so that one chunk of one slot is a contiguous
+// R*128-byte image of the shared-memory B tile.
+__global__ void k_swizzle_T(const double* T, int R, int NK, int sT, __half* Thi, __half* Tlo) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)R * NK * TC_KH;
+    if (e >= (int64_t)kOffsetSlots * per) return;
+    const int64_t slot = e / per;
+    const int row = (int)((e % per) / (NK * TC_KH)), k = (int)(e % (NK * TC_KH));
+    const float x = k < R ? (float)ldexp(T[(slot * R + row) * R + k], sT) : 0.f;
+    const __half h = __float2half_rn(x);
+    const __half l = __float2half_rn(x - __half2float(h));
+    const int64_t byte = (slot * NK + k / TC_KH) * (int64_t)R * 128 + sw128_off_h(row, k % TC_KH);
+    Thi[byte / 2] = h;
+    Tlo[byte / 2] = l;
+}
+
+// upward coefficients (FP64, rows of R) -> their FP32 values scaled by 2^{e_b} per box (largest
+// magnitude near 2^14), split into FP16 hi/lo; one warp per box
+__global__ void k_split_c(const double* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp) {
+    const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (b >= nb) return;
+    const double* row = c + b * R;
+    float m = 0.f;
+    for (int k = lane; k < R; k += 32) m = fmaxf(m, fabsf((float)row[k]));
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = 0;
+    if (m > 0.f) {
+        int ex;
+        frexpf(m, &ex);             // m = f 2^ex, f in [0.5, 1)
+        e = TC_HI_EXP + 1 - ex;     // m 2^e in [2^13, 2^14)
+    }
+    for (int k = lane; k < R; k += 32) {
+        const float x = ldexpf((float)row[k], e);
+        const __half h = __float2half_rn(x);
+        chi[b * R + k] = h;
+        clo[b * R + k] = __float2half_rn(x - __half2float(h));
+    }
+    if (lane == 0) cexp[b] = e;
 }
 
 // ------------------------------------------------------------------------------------
@@ -144,10 +179,10 @@ __global__ void k_split_c(const double* c, int64_t n, float* chi, float* clo) {
 template <int NC, int NS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(M2LTables tabs, const int4* __restrict__ tiles, const int32_t* __restrict__ all_boxes,
-             const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const float* __restrict__ chi,
-             const float* __restrict__ clo, float* __restrict__ d, int* err) {
+             const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const __half* __restrict__ chi,
+             const __half* __restrict__ clo, const int* __restrict__ cexp, float* __restrict__ d, int* err) {
     constexpr int R = 32 * NC;
-    constexpr int NK = R / TC_KC;
+    constexpr int NK = (R + TC_KH - 1) / TC_KH;
     constexpr int A_BYTES = TC_M * 128, B_BYTES = R * 128;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
     constexpr int ACC = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
@@ -160,8 +195,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 tile = tiles[blockIdx.x];   // level, first box (index into all_boxes), box count
-    const float* __restrict__ Thi = tabs.hi[tile.x];
-    const float* __restrict__ Tlo = tabs.lo[tile.x];
+    const __half* __restrict__ Thi = reinterpret_cast<const __half*>(tabs.hi[tile.x]);
+    const __half* __restrict__ Tlo = reinterpret_cast<const __half*>(tabs.lo[tile.x]);
+    const int sT = tabs.sT[tile.x];
     const int32_t* __restrict__ boxes = all_boxes + tile.y;
     const int nbox = tile.z;
     const int t0 = 0;
@@ -215,13 +251,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             }
             if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NS - 1) & 1), &abort_flag)) break;
             const int slot = sl[1 + it / NK];
-            const int k0 = (it % NK) * TC_KC;
+            const int kc = it % NK;
+            const int k0 = kc * TC_KH;
+            const int kvalid = min(TC_KH, R - k0);
             unsigned char* st = base + s * STAGE;
             if (p == 0) {   // B: two pre-swizzled bulk copies (hi, lo) of R x 128 bytes
                 const uint32_t fb = smem_u32(&full[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * B_BYTES)
                              : "memory");
-                const int64_t off = (int64_t)slot * R * R + (int64_t)(k0 / TC_KC) * R * TC_KC;
+                const int64_t off = ((int64_t)slot * NK + kc) * R * TC_KH;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(st + 2 * A_BYTES)),
@@ -233,7 +271,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     "l"(Tlo + off), "r"(B_BYTES), "r"(fb)
                     : "memory");
             }
-            // A: rows p, p + 64 = c[source of the row's box at this slot], chunk k0..k0+31, hi and lo
+            // A: rows p, p + 64 = c[source of the row's box at this slot], chunk k0..k0+kvalid-1,
+            // hi and lo (8 FP16 per 16-byte copy)
             const uint32_t ah = smem_u32(st), al = smem_u32(st + A_BYTES);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -242,10 +281,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 const uint32_t nbytes = a >= 0 ? 16u : 0u;   // 0: zero fill
                 const int64_t src = (int64_t)(a >= 0 ? a : 0) * R + k0;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t o = sw128_off(row, 4 * j);
-                    cp_async16(ah + o, chi + src + 4 * j, nbytes);
-                    cp_async16(al + o, clo + src + 4 * j, nbytes);
+                for (int j = 0; j < TC_KH / 8; ++j) {
+                    if (8 * j < kvalid) {
+                        const uint32_t o = sw128_off_h(row, 8 * j);
+                        cp_async16(ah + o, chi + src + 8 * j, nbytes);
+                        cp_async16(al + o, clo + src + 8 * j, nbytes);
+                    }
                 }
             }
             asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
@@ -254,7 +295,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 10) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = tf32_idesc(TC_M, R);
+            const uint32_t idesc = f16_idesc(TC_M, R);
             uint32_t fphase[NS] = {};
             for (int si = 0; si < ns && !abort_flag; ++si) {
                 const int j = si & 1;
@@ -272,13 +313,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                     const unsigned char* st = base + s * STAGE;
                     const uint32_t ah = smem_u32(st), al = ah + A_BYTES, bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
-#pragma unroll
-                    for (int k = 0; k < TC_KC / 8; ++k) {
-                        const uint32_t ko = 32u * k;   // 8 TF32 = 32 bytes along K inside the swizzle row
+                    const int ksteps = min(TC_KH, R - kc * TC_KH) / 16;
+                    for (int k = 0; k < ksteps; ++k) {
+                        const uint32_t ko = 32u * k;   // 16 FP16 = 32 bytes along K inside the swizzle row
                         const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
-                        mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
-                        mma_tf32(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                        mma_tf32(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                        mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
+                        mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                        mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
                     }
                     mma_commit(smem_u32(&empty[s]));
                 }
@@ -295,8 +336,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float acc[R / 2];
 #pragma unroll
         for (int k = 0; k < R / 2; ++k) acc[k] = 0.f;
+        // this row's box and the scale 2^{-(e_A + e_T)} of its source at each slot (one slot ahead)
+        const int brow = t0 + 32 * q + lane;
+        const int bbox = brow < nbox ? boxes[brow] : -1;
+        auto slot_scale = [&](int si) -> float {
+            if (si >= ns || bbox < 0) return 0.f;
+            const int a = vtab[(int64_t)bbox * kOffsetSlots + sl[1 + si]];
+            return a >= 0 ? pow2i(-(cexp[a] + sT)) : 0.f;
+        };
+        float fnext = slot_scale(0);
         for (int si = 0; si < ns; ++si) {
             const int j = si & 1;
+            const float f = fnext;
+            fnext = slot_scale(si + 1);
             const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((si >> 1) & 1), &abort_flag);
             if (__any_sync(0xffffffffu, !ok)) break;   // warp-uniform exit (tcgen05.ld is .sync.aligned)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -313,7 +365,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int k = 0; k < 16; ++k) acc[cc + k] += __uint_as_float(v[k]);
+                for (int k = 0; k < 16; ++k) acc[cc + k] = fmaf(__uint_as_float(v[k]), f, acc[cc + k]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&freed[j]));
@@ -348,56 +400,81 @@ size_t m2l_tc_smem(int R) {
 
 int m2l_tc_supported(int R) { return (R % 32 == 0 && R >= 32 && R <= 256 && stages_for(R) >= 2) ? 1 : 0; }
 
-int m2l_tc_prepare(cudaStream_t st, const double* T, int R, float* Thi, float* Tlo) {
+int64_t m2l_tc_table_elems(int R) { return (int64_t)kOffsetSlots * ((R + TC_KH - 1) / TC_KH) * R * TC_KH; }
+
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out) {
     const int64_t n = (int64_t)kOffsetSlots * R * R;
-    k_swizzle_T<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(T, R, Thi, Tlo);
+    DevBuf mx;
+    KF_TRY(dev_alloc(mx, 8));
+    KF_CUDA(cudaMemsetAsync(mx.p, 0, 8, st));
+    k_absmax<<<1024, 256, 0, st>>>(T, n, ptr<unsigned long long>(mx));
+    KF_LAUNCH();
+    unsigned long long bits = 0;
+    KF_CUDA(cudaMemcpyAsync(&bits, mx.p, 8, cudaMemcpyDeviceToHost, st));
+    KF_CUDA(cudaStreamSynchronize(st));
+    dev_free(mx);
+    double m;
+    std::memcpy(&m, &bits, 8);
+    int ex = 0;
+    if (m > 0.0) std::frexp(m, &ex);
+    const int sT = m > 0.0 ? TC_HI_EXP + 1 - ex : 0;   // max |T| 2^sT in [2^13, 2^14)
+    *sT_out = sT;
+    const int NK = (R + TC_KH - 1) / TC_KH;
+    const int64_t ne = m2l_tc_table_elems(R);
+    k_swizzle_T<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(T, R, NK, sT, reinterpret_cast<__half*>(Thi),
+                                                              reinterpret_cast<__half*>(Tlo));
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
-int m2l_tc_split(cudaStream_t st, const double* c, int64_t n, float* chi, float* clo) {
-    k_split_c<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c, n, chi, clo);
+int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp) {
+    k_split_c<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
+                                                                 reinterpret_cast<__half*>(clo), cexp);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
 template <int NC, int NS>
 static int launch_cfg(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
-                      const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d,
-                      int* err) {
+                      const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
+                      float* d, int* err) {
     const size_t smem = m2l_tc_smem(32 * NC);
     static bool configured = false;   // one attribute per instantiation (its size never changes)
     if (!configured) {
         KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots, chi, clo, d, err);
+    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots,
+                                                        reinterpret_cast<const __half*>(chi),
+                                                        reinterpret_cast<const __half*>(clo), cexp, d, err);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
 template <int NC>
 static int launch_nc(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
-                     const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
+                     const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
+                     float* d, int* err) {
     switch (stages_for(32 * NC)) {
-        case 2: return launch_cfg<NC, 2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 3: return launch_cfg<NC, 3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        default: return launch_cfg<NC, 4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 2: return launch_cfg<NC, 2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 3: return launch_cfg<NC, 3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        default: return launch_cfg<NC, 4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
     }
 }
 
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
-                  const int32_t* vtab, const int32_t* slots, const float* chi, const float* clo, float* d, int* err) {
+                  const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
+                  int* err) {
     if (ntiles <= 0) return KIFMM_OK;
     switch (R / 32) {
-        case 1: return launch_nc<1>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 2: return launch_nc<2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 3: return launch_nc<3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 4: return launch_nc<4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 5: return launch_nc<5>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 6: return launch_nc<6>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 7: return launch_nc<7>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
-        case 8: return launch_nc<8>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, d, err);
+        case 1: return launch_nc<1>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 2: return launch_nc<2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 3: return launch_nc<3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 4: return launch_nc<4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 5: return launch_nc<5>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 6: return launch_nc<6>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 7: return launch_nc<7>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 8: return launch_nc<8>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
         default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
     }
 }

@@ -373,9 +373,9 @@ int build_operators(Plan& p) {
         for (int l = 2; l < L; ++l) {
             LevelOps& op = p.ops[l];
             if (p.m2l_tensor) {
-                KF_TRY(dev_alloc(op.Thi, kOffsetSlots * RR * 4));
-                KF_TRY(dev_alloc(op.Tlo, kOffsetSlots * RR * 4));
-                KF_TRY(m2l_tc_prepare(st, ptr<double>(op.T), R, ptr<float>(op.Thi), ptr<float>(op.Tlo)));
+                KF_TRY(dev_alloc(op.Thi, (size_t)m2l_tc_table_elems(R) * 2));
+                KF_TRY(dev_alloc(op.Tlo, (size_t)m2l_tc_table_elems(R) * 2));
+                KF_TRY(m2l_tc_prepare(st, ptr<double>(op.T), R, op.Thi.p, op.Tlo.p, &op.tc_sT));
             } else {
                 KF_TRY(f32_copy(st, op.T, op.T32, kOffsetSlots * RR));
             }
