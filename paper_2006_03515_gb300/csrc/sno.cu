@@ -153,18 +153,30 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
         psh[q * ncol + col] = in[((p0 + pl) * Lin + q) * (int64_t)inner + i0 + w];
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < Lout * ncol; e += blockDim.x) {
-        const int j = e / ncol, col = e % ncol;
+    // each thread: 4 consecutive outputs j0..j0+3 of one column (the column's input is read
+    // once per q; T[j][q] is uniform across the warp's columns)
+    const int njb = (Lout + 3) / 4;
+    for (int e = threadIdx.x; e < njb * ncol; e += blockDim.x) {
+        const int jb = e / ncol, col = e % ncol;
         const int pl = col / W, w = col % W;
-        const float2* t = T + (int64_t)j * Lin;
-        float re = 0.f, im = 0.f;
+        const int j0 = 4 * jb;
+        const int nj = min(4, Lout - j0);
+        const float2* t0 = T + (int64_t)j0 * Lin;
+        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
         for (int q = 0; q < Lin; ++q) {
-            const float2 a = __ldg(t + q);
             const float2 x = psh[q * ncol + col];
-            re = fmaf(a.x, x.x, fmaf(-a.y, x.y, re));
-            im = fmaf(a.x, x.y, fmaf(a.y, x.x, im));
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (u < nj) {
+                    const float2 a = __ldg(t0 + (int64_t)u * Lin + q);
+                    re[u] = fmaf(a.x, x.x, fmaf(-a.y, x.y, re[u]));
+                    im[u] = fmaf(a.x, x.y, fmaf(a.y, x.x, im[u]));
+                }
+            }
         }
-        out[((p0 + pl) * Lout + j) * (int64_t)inner + i0 + w] = make_float2(re, im);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (u < nj) out[((p0 + pl) * Lout + j0 + u) * (int64_t)inner + i0 + w] = make_float2(re[u], im[u]);
     }
 }
 
@@ -244,7 +256,34 @@ __global__ void __launch_bounds__(256) k_mix_grad(const float2* __restrict__ dG,
 
 // z-row kernels: shared-memory fields as [rows][n + 1] floats and tables as [rows][cols + 1]
 // float2 (odd strides keep column access free of bank conflicts); the float2 region starts
-// on an 8-byte boundary.
+// on an 8-byte boundary. Inner products are register-blocked (several outputs per thread
+// share each shared-memory load).
+
+// out[c][kz] = sum_z tf[kz][z] X[c][z] for c < C, kz < m (X real [C][n + 1], tf [m][n + 1]);
+// a thread takes one c and the pair kz, kz + mh. Written to dst + (c * rs) + kz.
+__device__ __forceinline__ void zfwd_rows(const float* X, const float2* tf, int C, int n, int m, float2* dst,
+                                          int64_t rs) {
+    const int ns = n + 1, mh = (m + 1) / 2;
+    for (int e = threadIdx.x; e < C * mh; e += blockDim.x) {
+        const int k0 = e % mh, c = e / mh;
+        const int k1 = k0 + mh;
+        const bool h1 = k1 < m;
+        const float2* t0 = tf + k0 * ns;
+        const float2* t1 = tf + (h1 ? k1 : k0) * ns;
+        const float* x = X + c * ns;
+        float r0 = 0.f, i0 = 0.f, r1 = 0.f, i1 = 0.f;
+        for (int zz = 0; zz < n; ++zz) {
+            const float xv = x[zz];
+            const float2 a = t0[zz], b = t1[zz];
+            r0 = fmaf(a.x, xv, r0);
+            i0 = fmaf(a.y, xv, i0);
+            r1 = fmaf(b.x, xv, r1);
+            i1 = fmaf(b.y, xv, i1);
+        }
+        dst[c * rs + k0] = make_float2(r0, i0);
+        if (h1) dst[c * rs + k1] = make_float2(r1, i1);
+    }
+}
 
 // forward, layer input side: v0 = Wl u + bl (lift) and its last-axis DFT cz = Tzf v0
 __global__ void __launch_bounds__(ZR_T) k_lift_z(const float* __restrict__ u, const float* __restrict__ Wl,
@@ -272,22 +311,13 @@ __global__ void __launch_bounds__(ZR_T) k_lift_z(const float* __restrict__ u, co
             v0[((b * C + c) * n2 + xy) * n + zz] = val;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
-            const int c = e / m, kz = e % m;
-            const float2* t = tf + kz * ns;
-            const float* x = vs + c * ns;
-            float re = 0.f, im = 0.f;
-            for (int zz = 0; zz < n; ++zz) {
-                re = fmaf(t[zz].x, x[zz], re);
-                im = fmaf(t[zz].y, x[zz], im);
-            }
-            cz[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
-        }
+        zfwd_rows(vs, tf, C, n, m, cz + (b * C * n2 + xy) * m, n2 * m);
     }
 }
 
 // forward, layer output side: z = Re(Tzi gy) + W v + b, v_next = GELU(z) (or z for the last
 // layer); optional: z stored (training), next layer's cz = Tzf v_next, projection y.
+// Main loop: a thread takes channels o0..o0+3 at the two points zp and zp + n/2.
 __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ gy, const float* __restrict__ v,
                                                      const float* __restrict__ W, const float* __restrict__ bias,
                                                      const float2* __restrict__ Tzi, const float2* __restrict__ Tzf,
@@ -323,6 +353,7 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ 
         }
     }
     const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    const int zb = (n + 1) / 2, obn = (C + 3) / 4;
     for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
         const int64_t b = r / n2, xy = r % n2;
         __syncthreads();
@@ -335,34 +366,55 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ 
             gs[e] = gy[((b * C + o) * n2 + xy) * m + kz];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
-            const int o = e / n, zz = e % n;
-            float a = bs[o];
-            const float2* t = ti + zz * (m + 1);
-            const float2* gg = gs + o * m;
-            for (int kz = 0; kz < m; ++kz) a = fmaf(t[kz].x, gg[kz].x, fmaf(-t[kz].y, gg[kz].y, a));
-            const float* w = Ws + o * C1;
-            for (int c = 0; c < C; ++c) a = fmaf(w[c], vs[c * ns + zz], a);
-            const int64_t gi = ((b * C + o) * n2 + xy) * n + zz;
-            if (zout) zout[gi] = a;
-            const float vv = act ? gelu_f(a) : a;
-            vo[o * ns + zz] = vv;
-            vnext[gi] = vv;
-        }
-        __syncthreads();
-        if (cznext) {
-            for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
-                const int c = e / m, kz = e % m;
-                const float2* t = tf + kz * ns;
-                const float* x = vo + c * ns;
-                float re = 0.f, im = 0.f;
-                for (int zz = 0; zz < n; ++zz) {
-                    re = fmaf(t[zz].x, x[zz], re);
-                    im = fmaf(t[zz].y, x[zz], im);
+        for (int e = threadIdx.x; e < obn * zb; e += blockDim.x) {
+            const int z0 = e % zb, o0 = 4 * (e / zb);
+            const int z1 = z0 + zb < n ? z0 + zb : z0;
+            int oc[4];
+            float a0[4], a1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                oc[u] = min(o0 + u, C - 1);
+                a0[u] = a1[u] = bs[oc[u]];
+            }
+            const float2* t0 = ti + z0 * (m + 1);
+            const float2* t1 = ti + z1 * (m + 1);
+            for (int kz = 0; kz < m; ++kz) {
+                const float2 ta = t0[kz], tb = t1[kz];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 g = gs[oc[u] * m + kz];
+                    a0[u] = fmaf(ta.x, g.x, fmaf(-ta.y, g.y, a0[u]));
+                    a1[u] = fmaf(tb.x, g.x, fmaf(-tb.y, g.y, a1[u]));
                 }
-                cznext[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
+            }
+            for (int c = 0; c < C; ++c) {
+                const float x0 = vs[c * ns + z0], x1 = vs[c * ns + z1];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float w = Ws[oc[u] * C1 + c];
+                    a0[u] = fmaf(w, x0, a0[u]);
+                    a1[u] = fmaf(w, x1, a1[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (o0 + u >= C) break;
+                const int o = o0 + u;
+                const int64_t g0 = ((b * C + o) * n2 + xy) * n;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && z1 == z0) break;
+                    const int zz = h ? z1 : z0;
+                    const float av = h ? a1[u] : a0[u];
+                    if (zout) zout[g0 + zz] = av;
+                    const float vv = act ? gelu_f(av) : av;
+                    vo[o * ns + zz] = vv;
+                    vnext[g0 + zz] = vv;
+                }
             }
         }
+        __syncthreads();
+        if (cznext) zfwd_rows(vo, tf, C, n, m, cznext + (b * C * n2 + xy) * m, n2 * m);
         if (y) {   // y = q2 + sum_p Q2[p] GELU(q1[p] + Q1[p] . v); thread = (point, quarter of p)
             for (int e = threadIdx.x; e < 4 * n; e += blockDim.x) {
                 const int zz = e % n, part = e / n;
@@ -381,6 +433,52 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ 
         }
     }
 }
+
+// Sum over the row of X[i][z] Y[j][z] for a thread's 2 x 2 tiles of (i, j) (i < NI, j < NJ),
+// accumulated into acc[4 * t + 2 * di + dj] for tile t = threadIdx.x + t * ZR_T.
+template <int NT>
+__device__ __forceinline__ void tile_sums(const float* X, const float* Y, int NI, int NJ, int n, float* acc) {
+    const int ns = n + 1, nti = (NI + 1) / 2, ntj = (NJ + 1) / 2;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int tt = threadIdx.x + t * ZR_T;
+        if (tt >= nti * ntj) break;
+        const int i0 = 2 * (tt / ntj), j0 = 2 * (tt % ntj);
+        const float* x0 = X + i0 * ns;
+        const float* x1 = X + min(i0 + 1, NI - 1) * ns;
+        const float* y0 = Y + j0 * ns;
+        const float* y1 = Y + min(j0 + 1, NJ - 1) * ns;
+        float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+        for (int zz = 0; zz < n; ++zz) {
+            const float a = x0[zz], bb = x1[zz], c = y0[zz], d = y1[zz];
+            s00 = fmaf(a, c, s00);
+            s01 = fmaf(a, d, s01);
+            s10 = fmaf(bb, c, s10);
+            s11 = fmaf(bb, d, s11);
+        }
+        acc[4 * t] += s00;
+        acc[4 * t + 1] += s01;
+        acc[4 * t + 2] += s10;
+        acc[4 * t + 3] += s11;
+    }
+}
+template <int NT>
+__device__ __forceinline__ void tile_flush(const float* acc, int NI, int NJ, float* g) {
+    const int nti = (NI + 1) / 2, ntj = (NJ + 1) / 2;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        const int tt = threadIdx.x + t * ZR_T;
+        if (tt >= nti * ntj) break;
+        const int i0 = 2 * (tt / ntj), j0 = 2 * (tt % ntj);
+#pragma unroll
+        for (int di = 0; di < 2; ++di)
+#pragma unroll
+            for (int dj = 0; dj < 2; ++dj)
+                if (i0 + di < NI && j0 + dj < NJ) atomicAdd(g + (i0 + di) * NJ + j0 + dj, acc[4 * t + 2 * di + dj]);
+    }
+}
+constexpr int NT_Q = (MAXP / 2) * (MAXC / 2) / ZR_T;   // 2 x 2 tiles per thread of a P x C sum
+constexpr int NT_W = (MAXC / 2) * (MAXC / 2) / ZR_T;   // and of a C x C sum
 
 // backward of the projection and of the last layer's pointwise part (no GELU there):
 // a = Q1 v_L + q1, h = GELU(a), da = dy Q2 GELU'(a), dz_{L-1} = Q1^T da; czb = Tzb dz_{L-1};
@@ -410,13 +508,14 @@ __global__ void __launch_bounds__(ZR_T) k_proj_bwd(const float* __restrict__ vL,
         pq[P + e] = Q2[e];
     }
     for (int e = threadIdx.x; e < m * n; e += blockDim.x) tb[(e / n) * ns + e % n] = Tzb[e];
-    // per-thread partial gradients: outputs o = threadIdx.x + j * ZR_T of each group
-    constexpr int NQ = MAXP * MAXC / ZR_T, NW = MAXC * MAXC / ZR_T;
-    float aQ1[NQ], aW[NW];
-    for (int j = 0; j < NQ; ++j) aQ1[j] = 0.f;
-    for (int j = 0; j < NW; ++j) aW[j] = 0.f;
+    float aQ1[4 * NT_Q], aW[4 * NT_W];
+#pragma unroll
+    for (int j = 0; j < 4 * NT_Q; ++j) aQ1[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4 * NT_W; ++j) aW[j] = 0.f;
     float aq1 = 0.f, aQ2 = 0.f, ab = 0.f, aq2 = 0.f;   // thread < P: q1[t], Q2[t]; thread < C: b[t]; thread 0: q2
     const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    const int zb = (n + 1) / 2;
     for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
         const int64_t b = r / n2, xy = r % n2;
         __syncthreads();
@@ -428,54 +527,73 @@ __global__ void __launch_bounds__(ZR_T) k_proj_bwd(const float* __restrict__ vL,
         }
         for (int e = threadIdx.x; e < n; e += blockDim.x) dys[e] = dy[b * n2 * n + xy * n + e];
         __syncthreads();
-        for (int e = threadIdx.x; e < P * n; e += blockDim.x) {
-            const int p = e / n, zz = e % n;
-            const float* qr = Qs + p * C1;
-            float a = pq[p];
-            for (int c = 0; c < C; ++c) a = fmaf(qr[c], vs[c * ns + zz], a);
-            hs[p * ns + zz] = gelu_f(a);
-            das[p * ns + zz] = dys[zz] * pq[P + p] * gelu_d(a);
+        // a for projection rows p0..p0+3 at points z0, z1
+        for (int e = threadIdx.x; e < ((P + 3) / 4) * zb; e += blockDim.x) {
+            const int z0 = e % zb, p0 = 4 * (e / zb);
+            const int z1 = z0 + zb < n ? z0 + zb : z0;
+            int pc[4];
+            float a0[4], a1[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                pc[u] = min(p0 + u, P - 1);
+                a0[u] = a1[u] = pq[pc[u]];
+            }
+            for (int c = 0; c < C; ++c) {
+                const float x0 = vs[c * ns + z0], x1 = vs[c * ns + z1];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float w = Qs[pc[u] * C1 + c];
+                    a0[u] = fmaf(w, x0, a0[u]);
+                    a1[u] = fmaf(w, x1, a1[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (p0 + u >= P) break;
+                const int p = p0 + u;
+                hs[p * ns + z0] = gelu_f(a0[u]);
+                das[p * ns + z0] = dys[z0] * pq[P + p] * gelu_d(a0[u]);
+                if (z1 != z0) {
+                    hs[p * ns + z1] = gelu_f(a1[u]);
+                    das[p * ns + z1] = dys[z1] * pq[P + p] * gelu_d(a1[u]);
+                }
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
-            const int c = e / n, zz = e % n;
-            float a = 0.f;
-            for (int p = 0; p < P; ++p) a = fmaf(Qs[p * C1 + c], das[p * ns + zz], a);
-            ds[c * ns + zz] = a;
-            dz[((b * C + c) * n2 + xy) * n + zz] = a;
+        // dz = Q1^T da for channels c0..c0+3 at points z0, z1
+        for (int e = threadIdx.x; e < ((C + 3) / 4) * zb; e += blockDim.x) {
+            const int z0 = e % zb, c0 = 4 * (e / zb);
+            const int z1 = z0 + zb < n ? z0 + zb : z0;
+            int cc[4];
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cc[u] = min(c0 + u, C - 1);
+            for (int p = 0; p < P; ++p) {
+                const float x0 = das[p * ns + z0], x1 = das[p * ns + z1];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float w = Qs[p * C1 + cc[u]];
+                    a0[u] = fmaf(w, x0, a0[u]);
+                    a1[u] = fmaf(w, x1, a1[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (c0 + u >= C) break;
+                const int c = c0 + u;
+                const int64_t g0 = ((b * C + c) * n2 + xy) * n;
+                ds[c * ns + z0] = a0[u];
+                dz[g0 + z0] = a0[u];
+                if (z1 != z0) {
+                    ds[c * ns + z1] = a1[u];
+                    dz[g0 + z1] = a1[u];
+                }
+            }
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
-            const int c = e / m, kz = e % m;
-            const float2* t = tb + kz * ns;
-            const float* x = ds + c * ns;
-            float re = 0.f, im = 0.f;
-            for (int zz = 0; zz < n; ++zz) {
-                re = fmaf(t[zz].x, x[zz], re);
-                im = fmaf(t[zz].y, x[zz], im);
-            }
-            czb[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
-        }
-#pragma unroll
-        for (int j = 0; j < NQ; ++j) {
-            const int o = threadIdx.x + j * ZR_T;
-            if (o < P * C) {
-                const int p = o / C, c = o % C;
-                float s = 0.f;
-                for (int zz = 0; zz < n; ++zz) s = fmaf(das[p * ns + zz], vs[c * ns + zz], s);
-                aQ1[j] += s;
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            const int o = threadIdx.x + j * ZR_T;
-            if (o < C * C) {
-                const int oo = o / C, c = o % C;
-                float s = 0.f;
-                for (int zz = 0; zz < n; ++zz) s = fmaf(ds[oo * ns + zz], ws[c * ns + zz], s);
-                aW[j] += s;
-            }
-        }
+        zfwd_rows(ds, tb, C, n, m, czb + (b * C * n2 + xy) * m, n2 * m);
+        tile_sums<NT_Q>(das, vs, P, C, n, aQ1);    // dQ1[p][c] += sum_z da[p][z] v_L[c][z]
+        tile_sums<NT_W>(ds, ws, C, C, n, aW);      // dW[o][c] += sum_z dz[o][z] v_{L-1}[c][z]
         if (threadIdx.x < P) {
             float s1 = 0.f, s2 = 0.f;
             for (int zz = 0; zz < n; ++zz) {
@@ -496,16 +614,8 @@ __global__ void __launch_bounds__(ZR_T) k_proj_bwd(const float* __restrict__ vL,
             aq2 += s;
         }
     }
-#pragma unroll
-    for (int j = 0; j < NQ; ++j) {
-        const int o = threadIdx.x + j * ZR_T;
-        if (o < P * C) atomicAdd(gQ1 + o, aQ1[j]);
-    }
-#pragma unroll
-    for (int j = 0; j < NW; ++j) {
-        const int o = threadIdx.x + j * ZR_T;
-        if (o < C * C) atomicAdd(gW + o, aW[j]);
-    }
+    tile_flush<NT_Q>(aQ1, P, C, gQ1);
+    tile_flush<NT_W>(aW, C, C, gW);
     if (threadIdx.x < P) {
         atomicAdd(gq1 + threadIdx.x, aq1);
         atomicAdd(gQ2 + threadIdx.x, aQ2);
@@ -540,11 +650,12 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point_bwd(const float2* __restric
     for (int e = threadIdx.x; e < n * m; e += blockDim.x) tr[(e / m) * (m + 1) + e % m] = Tzr[e];
     if (!first)
         for (int e = threadIdx.x; e < m * n; e += blockDim.x) tb[(e / n) * ns + e % n] = Tzb[e];
-    constexpr int NW = MAXC * MAXC / ZR_T;
-    float aW[NW];
-    for (int j = 0; j < NW; ++j) aW[j] = 0.f;
+    float aW[4 * NT_W];
+#pragma unroll
+    for (int j = 0; j < 4 * NT_W; ++j) aW[j] = 0.f;
     float ab = 0.f, aw1 = 0.f;
     const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    const int zb = (n + 1) / 2;
     for (int64_t r = (int64_t)blockIdx.x * ZR_RG; r < min(rows, (int64_t)(blockIdx.x + 1) * ZR_RG); ++r) {
         const int64_t b = r / n2, xy = r % n2;
         __syncthreads();
@@ -561,61 +672,70 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point_bwd(const float2* __restric
             gs[e] = gyb[((b * C + c) * n2 + xy) * m + kz];
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < C * n; e += blockDim.x) {
-            const int c = e / n, zz = e % n;
-            float a = 0.f;
-            const float2* t = tr + zz * (m + 1);
-            const float2* gg = gs + c * m;
-            for (int kz = 0; kz < m; ++kz) a = fmaf(t[kz].x, gg[kz].x, fmaf(-t[kz].y, gg[kz].y, a));
-            for (int o = 0; o < C; ++o) a = fmaf(Ws[o * C1 + c], ds[o * ns + zz], a);
-            if (!first) {
-                const int64_t gi = ((b * C + c) * n2 + xy) * n + zz;
-                a *= gelu_d(zprev[gi]);
-                dzprev[gi] = a;
+        // dv for channels c0..c0+3 at points z0, z1
+        for (int e = threadIdx.x; e < ((C + 3) / 4) * zb; e += blockDim.x) {
+            const int z0 = e % zb, c0 = 4 * (e / zb);
+            const int z1 = z0 + zb < n ? z0 + zb : z0;
+            int cc[4];
+            float a0[4] = {0.f, 0.f, 0.f, 0.f}, a1[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int uu = 0; uu < 4; ++uu) cc[uu] = min(c0 + uu, C - 1);
+            const float2* t0 = tr + z0 * (m + 1);
+            const float2* t1 = tr + z1 * (m + 1);
+            for (int kz = 0; kz < m; ++kz) {
+                const float2 ta = t0[kz], tb2 = t1[kz];
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    const float2 g = gs[cc[uu] * m + kz];
+                    a0[uu] = fmaf(ta.x, g.x, fmaf(-ta.y, g.y, a0[uu]));
+                    a1[uu] = fmaf(tb2.x, g.x, fmaf(-tb2.y, g.y, a1[uu]));
+                }
             }
-            dn[c * ns + zz] = a;
+            for (int o = 0; o < C; ++o) {
+                const float x0 = ds[o * ns + z0], x1 = ds[o * ns + z1];
+#pragma unroll
+                for (int uu = 0; uu < 4; ++uu) {
+                    const float w = Ws[o * C1 + cc[uu]];
+                    a0[uu] = fmaf(w, x0, a0[uu]);
+                    a1[uu] = fmaf(w, x1, a1[uu]);
+                }
+            }
+#pragma unroll
+            for (int uu = 0; uu < 4; ++uu) {
+                if (c0 + uu >= C) break;
+                const int c = c0 + uu;
+                const int64_t g0 = ((b * C + c) * n2 + xy) * n;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    if (h == 1 && z1 == z0) break;
+                    const int zz = h ? z1 : z0;
+                    float av = h ? a1[uu] : a0[uu];
+                    if (!first) {
+                        av *= gelu_d(zprev[g0 + zz]);
+                        dzprev[g0 + zz] = av;
+                    }
+                    dn[c * ns + zz] = av;
+                }
+            }
         }
         __syncthreads();
         if (!first) {
-            for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
-                const int c = e / m, kz = e % m;
-                const float2* t = tb + kz * ns;
-                const float* x = dn + c * ns;
-                float re = 0.f, im = 0.f;
-                for (int zz = 0; zz < n; ++zz) {
-                    re = fmaf(t[zz].x, x[zz], re);
-                    im = fmaf(t[zz].y, x[zz], im);
-                }
-                czb[((b * C + c) * n2 + xy) * m + kz] = make_float2(re, im);
-            }
-#pragma unroll
-            for (int j = 0; j < NW; ++j) {
-                const int o = threadIdx.x + j * ZR_T;
-                if (o < C * C) {
-                    const int oo = o / C, c = o % C;
-                    float s = 0.f;
-                    for (int zz = 0; zz < n; ++zz) s = fmaf(dn[oo * ns + zz], ws[c * ns + zz], s);
-                    aW[j] += s;
-                }
-            }
+            zfwd_rows(dn, tb, C, n, m, czb + (b * C * n2 + xy) * m, n2 * m);
+            tile_sums<NT_W>(dn, ws, C, C, n, aW);   // dW_{l-1}[o][c] += sum_z dz_{l-1}[o][z] v_{l-1}[c][z]
         }
         if (threadIdx.x < C) {
-            float s = 0.f, s1 = 0.f;
+            float sum = 0.f, s1 = 0.f;
             for (int zz = 0; zz < n; ++zz) {
                 const float d = dn[threadIdx.x * ns + zz];
-                s += d;
+                sum += d;
                 if (first) s1 = fmaf(d, ws[zz], s1);
             }
-            ab += s;
+            ab += sum;
             aw1 += s1;
         }
     }
     if (!first) {
-#pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            const int o = threadIdx.x + j * ZR_T;
-            if (o < C * C) atomicAdd(gW + o, aW[j]);
-        }
+        tile_flush<NT_W>(aW, C, C, gW);
         if (threadIdx.x < C) atomicAdd(gb + threadIdx.x, ab);
     } else if (threadIdx.x < C) {
         atomicAdd(gWl + threadIdx.x, aw1);
