@@ -493,15 +493,19 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
 constexpr int AP_TK = 16;
 // With zoff != NULL the launch is a batch over blockIdx.z: batch z uses Op + z * zstride and
 // the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch). With
-// zoff == NULL and gridDim.z > 1 the terms are split over blockIdx.z (terms t = z, z + nz,
-// ...) and the partial sums are added atomically into out (which the caller zeroes).
+// zoff == NULL and gridDim.z > 1 the work items (term, k-chunk), taken term-major, are split
+// into gridDim.z contiguous ranges and the partial sums are added atomically into out
+// (which the caller zeroes). The next item's operands are loaded into registers while the
+// current one is multiplied.
 template <class T, class TI, class TO, int RM, int CN>
 __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t op_stride, int ldop, int nterm,
                                                int Mo, int Ki, const int32_t* src, const int32_t* dst, int64_t base,
                                                int count, const TI* __restrict__ in, int ldi, TO* out, int ldo,
                                                int accumulate, const int32_t* zoff, int64_t zstride) {
     constexpr int TM = 16 * RM, TN = 16 * CN;
-    int t0 = 0, tstep = 1;
+    const int nkc = (Ki + AP_TK - 1) / AP_TK;
+    int it0 = 0, it1 = nterm * nkc;
+    const bool split = !zoff && gridDim.z > 1;
     if (zoff) {
         const int z = blockIdx.z;
         Op += (int64_t)z * zstride;
@@ -509,48 +513,65 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
         dst += zoff[z];
         count = zoff[z + 1] - zoff[z];
         if ((int)(blockIdx.x * TN) >= count) return;
-    } else {
-        t0 = blockIdx.z;
-        tstep = gridDim.z;
+    } else if (split) {
+        const int per = (it1 + gridDim.z - 1) / gridDim.z;
+        it0 = min(it1, (int)blockIdx.z * per);
+        it1 = min(it1, it0 + per);
     }
     __shared__ T As[AP_TK][TM + 1];
     __shared__ T Bs[AP_TK][TN + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
     T acc[RM][CN] = {};
-    for (int t = t0; t < nterm; t += tstep) {
+    T ra[RM], rb[CN];
+    auto load = [&](int it) {
+        const int t = it / nkc, k0 = (it % nkc) * AP_TK;
         const T* Opt = Op + (int64_t)t * op_stride;
-        for (int k0 = 0; k0 < Ki; k0 += AP_TK) {
-            for (int e = tid; e < TM * AP_TK; e += 256) {
-                int rr = e / AP_TK, kk = e % AP_TK;
-                int row = row0 + rr, k = k0 + kk;
-                As[kk][rr] = (row < Mo && k < Ki) ? Opt[(int64_t)row * ldop + k] : T(0);
-            }
-            for (int e = tid; e < TN * AP_TK; e += 256) {
-                int cc = e / AP_TK, kk = e % AP_TK;
-                int col = col0 + cc, k = k0 + kk;
-                T v = T(0);
-                if (col < count && k < Ki) {
-                    int64_t b = src ? (int64_t)src[(int64_t)t * count + col] : base + col;
-                    if (b >= 0) v = (T)in[b * ldi + k];
-                }
-                Bs[kk][cc] = v;
-            }
-            __syncthreads();
 #pragma unroll
-            for (int kk = 0; kk < AP_TK; ++kk) {
-                T av[RM], bv[CN];
-#pragma unroll
-                for (int i = 0; i < RM; ++i) av[i] = As[kk][ty + 16 * i];
-#pragma unroll
-                for (int j = 0; j < CN; ++j) bv[j] = Bs[kk][tx + 16 * j];
-#pragma unroll
-                for (int i = 0; i < RM; ++i)
-#pragma unroll
-                    for (int j = 0; j < CN; ++j) acc[i][j] += av[i] * bv[j];
-            }
-            __syncthreads();
+        for (int i = 0; i < RM; ++i) {
+            const int e = tid + 256 * i;
+            const int row = row0 + e / AP_TK, k = k0 + e % AP_TK;
+            ra[i] = (row < Mo && k < Ki) ? Opt[(int64_t)row * ldop + k] : T(0);
         }
+#pragma unroll
+        for (int j = 0; j < CN; ++j) {
+            const int e = tid + 256 * j;
+            const int col = col0 + e / AP_TK, k = k0 + e % AP_TK;
+            T v = T(0);
+            if (col < count && k < Ki) {
+                const int64_t b = src ? (int64_t)src[(int64_t)t * count + col] : base + col;
+                if (b >= 0) v = (T)in[b * ldi + k];
+            }
+            rb[j] = v;
+        }
+    };
+    if (it0 < it1) load(it0);
+    for (int it = it0; it < it1; ++it) {
+#pragma unroll
+        for (int i = 0; i < RM; ++i) {
+            const int e = tid + 256 * i;
+            As[e % AP_TK][e / AP_TK] = ra[i];
+        }
+#pragma unroll
+        for (int j = 0; j < CN; ++j) {
+            const int e = tid + 256 * j;
+            Bs[e % AP_TK][e / AP_TK] = rb[j];
+        }
+        __syncthreads();
+        if (it + 1 < it1) load(it + 1);
+#pragma unroll
+        for (int kk = 0; kk < AP_TK; ++kk) {
+            T av[RM], bv[CN];
+#pragma unroll
+            for (int i = 0; i < RM; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < CN; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < RM; ++i)
+#pragma unroll
+                for (int j = 0; j < CN; ++j) acc[i][j] += av[i] * bv[j];
+        }
+        __syncthreads();
     }
 #pragma unroll
     for (int i = 0; i < RM; ++i) {
@@ -562,7 +583,7 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
             if (col >= count) continue;
             int64_t b = dst ? dst[col] : base + col;
             TO* o = out + b * ldo + row;
-            if (!zoff && gridDim.z > 1) atomicAdd(o, (TO)acc[i][j]);
+            if (split) atomicAdd(o, (TO)acc[i][j]);
             else *o = accumulate ? *o + (TO)acc[i][j] : (TO)acc[i][j];
         }
     }
@@ -1122,14 +1143,19 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
-            const int nz = std::max(1, std::min(8, (2 * p.num_sms + tiles - 1) / tiles));
+            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (2 * p.num_sms + tiles - 1) / tiles));
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
                                                  cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));
         }
-        if (LL.n_up > 0)
+        if (LL.n_up > 0) {   // c = Sigma^+ U^T chk; the K range split over z on small levels (cu is zeroed)
+            constexpr int RMd = ApplyShape<double>::RM, CNd = ApplyShape<double>::CN;
+            const int tiles = (int)(nbk(LL.n_up, 16 * CNd) * nbk(p.ops[l].rank, 16 * RMd));
+            const int nz = std::max(1, std::min((S + AP_TK - 1) / AP_TK, (2 * p.num_sms + tiles - 1) / tiles));
             RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.upb),
-                                     ptr<int32_t>(LL.upb), 0, LL.n_up, ptr<double>(p.chk), S, cu, R, 0));
+                                     ptr<int32_t>(LL.upb), 0, LL.n_up, ptr<double>(p.chk), S, cu, R, 0, 1, 0, nullptr,
+                                     nz));
+        }
     }
     mark(p, 3);
     // ---- M2L in coefficients (Eq. (m2l))

@@ -36,6 +36,32 @@ def make_dataset(plan, pts, C, count, seed=0):
     return U, T
 
 
+def init_from_data(model, U, T, seed=0):
+    """Seeded initial parameters matched to the data's scale: the lift maps u to zero mean
+    and unit variance, the output bias starts at the mean target and the last projection
+    is small, so the first steps learn the field's shape rather than its offset."""
+    import numpy as np
+    theta = model.init_params(seed)
+    lay = model.layout()
+    off, o = {}, 0
+    for name, shp in lay:
+        k = int(np.prod(shp))
+        off[name] = (o, k)
+        o += k
+    mu, sd = float(U.mean()), float(U.std()) + 1e-6
+    o, k = off["Wl"]
+    theta[o:o + k] /= sd
+    wl = theta[o:o + k].copy()
+    o, k = off["bl"]
+    theta[o:o + k] = -wl * mu
+    o, k = off["Q2"]
+    theta[o:o + k] *= 0.1
+    o, k = off["q2"]
+    theta[o:o + k] = float(T.mean())
+    model.set_params(theta)
+    return theta
+
+
 def train(model, U, T, steps, batch=4, lr=1e-3, seed=0, log_every=0):
     """Adam on the mean squared error over random mini-batches; returns the loss history."""
     import torch
