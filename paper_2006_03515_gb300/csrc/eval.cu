@@ -437,7 +437,14 @@ struct Kahan {
 // S2M (Eq. (s2m), first step): upward check potential of a leaf from its own sources.
 // One block per leaf; check points x_j = c_B + 2.6 r s_j, sources relative to c_B.
 constexpr int P2M_T = 160;
-template <bool MIXED>
+// FP32 kernel without the series branch: valid where (b - a) R >= 0.5 for every pair
+__device__ __forceinline__ float kern_plain_f32(float r2, const KParams& k) {
+    const float rinv = rsqrt_approx(r2);
+    const float R = r2 * rinv;
+    return (ex2_approx(-k.a_l2e * R) - ex2_approx(-k.b_l2e * R)) * k.norm_f * (rinv * (rinv * rinv));
+}
+// SER: some source of a leaf may lie closer than 0.5 / (b - a) to its check surface
+template <bool MIXED, bool SER>
 __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes, const double* q, double* chk) {
     const int B = boxes[blockIdx.x];
     const int S = E.S;
@@ -468,10 +475,23 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
             __syncthreads();
             if (MIXED) {
                 const float x0 = (float)xj[0], x1 = (float)xj[1], x2 = (float)xj[2];
-                for (int e = 0; e < ns; ++e) {
+                int e = 0;
+                for (; e + 7 < ns; e += 8) {   // plain FP32 sums of 8 terms, compensated across blocks
+                    float part = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const float4 v = sp32[e + u];
+                        const float dx = x0 - v.x, dy = x1 - v.y, dz = x2 - v.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        part = fmaf(SER ? kern_f32(r2, E.kp) : kern_plain_f32(r2, E.kp), v.w, part);
+                    }
+                    acc32.add(part);
+                }
+                for (; e < ns; ++e) {
                     const float4 v = sp32[e];
                     const float dx = x0 - v.x, dy = x1 - v.y, dz = x2 - v.z;
-                    acc32.add(kern_f32(dx * dx + dy * dy + dz * dz, E.kp) * v.w);
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    acc32.add((SER ? kern_f32(r2, E.kp) : kern_plain_f32(r2, E.kp)) * v.w);
                 }
             } else {
                 for (int e = 0; e < ns; ++e) {
@@ -730,7 +750,9 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
 // and the W list (y = c_A + 1.2 r_A s_k, density phi_u). One block per leaf, one thread
 // per target point. Writes far[i] for every point of the leaf.
 constexpr int L2P_T = 64;
-template <bool MIXED, class TD>
+// SER: some target of a leaf may lie closer than 0.5 / (b - a) to its downward equivalent
+// surface (the W-list sources always take the series-safe form)
+template <bool MIXED, bool SER, class TD>
 __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves, const int32_t* woff,
                                              const int32_t* witems, const TD* phi_d,
                                              const TD* phi_u, double* far) {
@@ -782,10 +804,24 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
                 __syncthreads();
                 if (!act) continue;
                 if (MIXED) {
-                    for (int e = 0; e < ns; ++e) {
+                    const bool plain = !SER && li == 0;
+                    int e = 0;
+                    for (; e + 7 < ns; e += 8) {   // plain FP32 sums of 8 terms, compensated across blocks
+                        float part = 0.f;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float4 v = s32[e + u];
+                            const float dx = xl.x - v.x, dy = xl.y - v.y, dz = xl.z - v.z;
+                            const float r2 = dx * dx + dy * dy + dz * dz;
+                            part = fmaf(plain ? kern_plain_f32(r2, E.kp) : kern_f32(r2, E.kp), v.w, part);
+                        }
+                        acc32.add(part);
+                    }
+                    for (; e < ns; ++e) {
                         const float4 v = s32[e];
                         const float dx = xl.x - v.x, dy = xl.y - v.y, dz = xl.z - v.z;
-                        acc32.add(kern_f32(dx * dx + dy * dy + dz * dz, E.kp) * v.w);
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        acc32.add((plain ? kern_plain_f32(r2, E.kp) : kern_f32(r2, E.kp)) * v.w);
                     }
                 } else {
                     for (int e = 0; e < ns; ++e) {
@@ -1080,6 +1116,12 @@ static int p2p_series_check(Plan& p) {
     std::memcpy(&m, &bits, 4);
     const double rs = 1.01 * 0.5 / (p.b - p.a);
     p.p2p_series = !((double)m >= rs * rs);
+    // leaves' points lie within their box (half-width r), their check / equivalent surfaces
+    // at kROuter r: every such pair is at least (kROuter - 1) r apart
+    double rmin = 1e300;
+    for (int l = 2; l < p.tree.nlevels; ++l)
+        if (p.lv[l].n_leaf > 0) rmin = std::min(rmin, p.tree.side / (double)(2LL << l));
+    p.far_series = !((kROuter - 1.0) * rmin >= rs);
     return KIFMM_OK;
 }
 
@@ -1132,8 +1174,8 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         KF_CUDA(cudaMemsetAsync(ptr<double>(p.chk) + b0 * S, 0, (size_t)(b1 - b0) * S * 8, st));
     }
     if (p.n_p2m > 0) {
-        if (mixed) k_p2m<true><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
-        else k_p2m<false><<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
+        auto* kp2m = !mixed ? k_p2m<false, true> : (p.far_series ? k_p2m<true, true> : k_p2m<true, false>);
+        kp2m<<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
         KF_LAUNCH();
         ++nl;
     }
@@ -1272,10 +1314,14 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     if (p.nleaves > 0) {
         const int32_t* wo = ptr<int32_t>(p.lists[2].off);
         const int32_t* wi = ptr<int32_t>(p.lists[2].items);
-        if (mixed) k_l2p<true, float><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),
-                                                                            ptr<float>(p.phiu), ptr<double>(p.far));
-        else k_l2p<false, double><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<double>(p.phid),
-                                                                         ptr<double>(p.phiu), ptr<double>(p.far));
+        if (mixed) {
+            auto* kl2p = p.far_series ? k_l2p<true, true, float> : k_l2p<true, false, float>;
+            kl2p<<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),
+                                                        ptr<float>(p.phiu), ptr<double>(p.far));
+        } else {
+            k_l2p<false, true, double><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(
+                E, ptr<int32_t>(p.leaves), wo, wi, ptr<double>(p.phid), ptr<double>(p.phiu), ptr<double>(p.far));
+        }
         KF_LAUNCH();
         ++nl;
     }

@@ -162,6 +162,7 @@ struct Plan {
     bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
+    bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
     DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
     DevBuf tc_slots;             // [tile][344] active offset slots

@@ -56,7 +56,8 @@ struct SnoModel {
     DevBuf cz, cy, gx, gy, Vst, g, ga;
     DevBuf jt, jref, jorig, jerr;    // photo_solve judge: targets, reference values, caller indices, error
     int mix_mb = 1;                  // modes per block of the mixing kernels
-    size_t zr_smem_f = 0, zr_smem_b = 0, zr_smem_p = 0, mix_smem = 0, mixg_smem = 0;
+    size_t zr_smem_f = 0, zr_smem_b = 0, zr_smem_p = 0, mix_smem = 0, mixg_smem = 0, zf_smem = 0;
+    int num_sms = 1;
     int64_t steps = 0;
 };
 
@@ -153,30 +154,38 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
         psh[q * ncol + col] = in[((p0 + pl) * Lin + q) * (int64_t)inner + i0 + w];
     }
     __syncthreads();
-    // each thread: 4 consecutive outputs j0..j0+3 of one column (the column's input is read
-    // once per q; T[j][q] is uniform across the warp's columns)
-    const int njb = (Lout + 3) / 4;
-    for (int e = threadIdx.x; e < njb * ncol; e += blockDim.x) {
-        const int jb = e / ncol, col = e % ncol;
-        const int pl = col / W, w = col % W;
-        const int j0 = 4 * jb;
-        const int nj = min(4, Lout - j0);
+    // each thread: 8 consecutive outputs j0..j0+7 of two columns (col, col + ncol/2); the
+    // columns' inputs are read once per q and T[j][q] is uniform across the warp
+    const int njb = (Lout + 7) / 8, nch2 = (ncol + 1) / 2;
+    for (int e = threadIdx.x; e < njb * nch2; e += blockDim.x) {
+        const int jb = e / nch2, c0 = e % nch2;
+        const int c1 = c0 + nch2 < ncol ? c0 + nch2 : c0;
+        const int j0 = 8 * jb;
+        const int nj = min(8, Lout - j0);
         const float2* t0 = T + (int64_t)j0 * Lin;
-        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int q = 0; q < Lin; ++q) {
-            const float2 x = psh[q * ncol + col];
+        float re[2][8], im[2][8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u < nj) {
-                    const float2 a = __ldg(t0 + (int64_t)u * Lin + q);
-                    re[u] = fmaf(a.x, x.x, fmaf(-a.y, x.y, re[u]));
-                    im[u] = fmaf(a.x, x.y, fmaf(a.y, x.x, im[u]));
-                }
+        for (int u = 0; u < 8; ++u) re[0][u] = im[0][u] = re[1][u] = im[1][u] = 0.f;
+        for (int q = 0; q < Lin; ++q) {
+            const float2 x0 = psh[q * ncol + c0], x1 = psh[q * ncol + c1];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float2 a = __ldg(t0 + (int64_t)min(u, nj - 1) * Lin + q);
+                re[0][u] = fmaf(a.x, x0.x, fmaf(-a.y, x0.y, re[0][u]));
+                im[0][u] = fmaf(a.x, x0.y, fmaf(a.y, x0.x, im[0][u]));
+                re[1][u] = fmaf(a.x, x1.x, fmaf(-a.y, x1.y, re[1][u]));
+                im[1][u] = fmaf(a.x, x1.y, fmaf(a.y, x1.x, im[1][u]));
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (u < nj) out[((p0 + pl) * Lout + j0 + u) * (int64_t)inner + i0 + w] = make_float2(re[u], im[u]);
+        for (int h = 0; h < 2; ++h) {
+            if (h == 1 && c1 == c0) break;
+            const int col = h ? c1 : c0;
+            const int pl = col / W, w = col % W;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (u < nj) out[((p0 + pl) * Lout + j0 + u) * (int64_t)inner + i0 + w] = make_float2(re[h][u], im[h][u]);
+        }
     }
 }
 
@@ -430,6 +439,213 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ 
             __syncthreads();
             for (int e = threadIdx.x; e < n; e += blockDim.x)
                 y[b * n2 * n + xy * n + e] = q2[0] + ((ypart[e] + ypart[n + e]) + (ypart[2 * n + e] + ypart[3 * n + e]));
+        }
+    }
+}
+
+// Forward, layer output side, tiled: a block takes FR row groups (b, x, y) at a time. Per
+// row group a thread computes an 8-channel x 4-point tile of z = Re(Tzi gy) + W v + b from
+// float4 shared loads (8 x 4 outputs per 12 loads), stores v_next (GELU unless the last
+// layer) over v in shared memory, then the next layer's cz = Tzf v_next (4 channels x 4 kz
+// per thread) or the projection y (8 projection rows x 4 points per thread). Needs n and
+// the width to be multiples of 4.
+constexpr int FR = 4;
+__global__ void __launch_bounds__(ZR_T) k_zrow_fwd(const float2* __restrict__ gy, const float* __restrict__ v,
+                                                   const float* __restrict__ W, const float* __restrict__ bias,
+                                                   const float2* __restrict__ Tzi, const float2* __restrict__ Tzf,
+                                                   float* __restrict__ zout, float* __restrict__ vnext,
+                                                   float2* __restrict__ cznext, const float* __restrict__ Q1,
+                                                   const float* __restrict__ q1, const float* __restrict__ Q2,
+                                                   const float* __restrict__ q2, float* __restrict__ y, int B, int C,
+                                                   int n, int m, int P, int act, int fr) {
+    extern __shared__ __align__(16) float zsh[];
+    const int nz4 = n + 4, C4 = C + 4, mt = m + 1, nt = n + 2;
+    float* vs = zsh;                               // [FR][C][n + 4]
+    float* Ws = vs + FR * C * nz4;                 // [C][C + 4]
+    float* bs = Ws + C * C4;                       // [C]
+    float* Qs = bs + C;                            // [P][C + 4] (projection)
+    float* pq = Qs + (y ? P * C4 : 0);             // q1, Q2 [2][P]
+    float* ys = pq + (y ? 2 * P : 0);              // [FR][n]
+    size_t fo = (size_t)(ys + (y ? FR * n : 0) - zsh);
+    fo = (fo + 3) & ~(size_t)3;
+    float2* gs = reinterpret_cast<float2*>(zsh + fo);   // [FR][C][m]
+    float2* ti = gs + FR * C * m;                        // [n][m + 1]
+    float2* tf = ti + n * mt;                            // [m][n + 2]
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ws[(e / C) * C4 + e % C] = W[e];
+    for (int e = threadIdx.x; e < C; e += blockDim.x) bs[e] = bias[e];
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) ti[(e / m) * mt + e % m] = Tzi[e];
+    if (cznext)
+        for (int e = threadIdx.x; e < m * n; e += blockDim.x) tf[(e / n) * nt + e % n] = Tzf[e];
+    if (y) {
+        for (int e = threadIdx.x; e < P * C; e += blockDim.x) Qs[(e / C) * C4 + e % C] = Q1[e];
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            pq[e] = q1[e];
+            pq[P + e] = Q2[e];
+        }
+    }
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    const int nzb = n / 4, nob = (C + 7) / 8, n4 = n / 4;
+    for (int64_t r0 = (int64_t)blockIdx.x * fr; r0 < rows; r0 += (int64_t)gridDim.x * fr) {
+        const int nr = (int)min((int64_t)fr, rows - r0);   // fr row groups: one tile per thread
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * C * n4; e += blockDim.x) {   // v rows, float4
+            const int q4 = e % n4, c = (e / n4) % C, rg = e / (n4 * C);
+            const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+            reinterpret_cast<float4*>(vs + (rg * C + c) * nz4)[q4] =
+                reinterpret_cast<const float4*>(v + ((b * C + c) * n2 + xy) * n)[q4];
+        }
+        for (int e = threadIdx.x; e < nr * C * m; e += blockDim.x) {
+            const int kz = e % m, o = (e / m) % C, rg = e / (m * C);
+            const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+            gs[e] = gy[((b * C + o) * n2 + xy) * m + kz];
+        }
+        if (y)
+            for (int e = threadIdx.x; e < FR * n; e += blockDim.x) ys[e] = 0.f;
+        __syncthreads();
+        // z tiles: 8 channels x 4 points per thread, kept in registers across the sync
+        float acc[1][8][4];
+        const int nitems = nr * nob * nzb;
+        if (threadIdx.x < nitems) {
+            const int k = 0, e = threadIdx.x;
+            const int zb = e % nzb, ob = (e / nzb) % nob, rg = e / (nzb * nob);
+            const int z0 = 4 * zb, o0 = 8 * ob;
+            int oc[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                oc[j] = min(o0 + j, C - 1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[k][j][i] = bs[oc[j]];
+            }
+            const float2* g = gs + rg * C * m;
+            for (int kz = 0; kz < m; ++kz) {
+                float2 t[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) t[i] = ti[(z0 + i) * mt + kz];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float2 gg = g[oc[j] * m + kz];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[k][j][i] = fmaf(t[i].x, gg.x, fmaf(-t[i].y, gg.y, acc[k][j][i]));
+                }
+            }
+            const float* vr = vs + rg * C * nz4 + z0;
+            for (int c = 0; c < C; c += 4) {
+                float4 x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = *reinterpret_cast<const float4*>(vr + (c + i) * nz4);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float4 w = *reinterpret_cast<const float4*>(Ws + oc[j] * C4 + c);
+                    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[k][j][0] = fmaf(wv[i], x[i].x, acc[k][j][0]);
+                        acc[k][j][1] = fmaf(wv[i], x[i].y, acc[k][j][1]);
+                        acc[k][j][2] = fmaf(wv[i], x[i].z, acc[k][j][2]);
+                        acc[k][j][3] = fmaf(wv[i], x[i].w, acc[k][j][3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // every tile is in registers: v_next may overwrite v in shared memory
+        if (threadIdx.x < nitems) {
+            const int k = 0, e = threadIdx.x;
+            const int zb = e % nzb, ob = (e / nzb) % nob, rg = e / (nzb * nob);
+            const int z0 = 4 * zb, o0 = 8 * ob;
+            const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int o = o0 + j;
+                if (o >= C) break;
+                const int64_t gi = ((b * C + o) * n2 + xy) * n + z0;
+                float4 a = make_float4(acc[k][j][0], acc[k][j][1], acc[k][j][2], acc[k][j][3]);
+                if (zout) *reinterpret_cast<float4*>(zout + gi) = a;
+                if (act) a = make_float4(gelu_f(a.x), gelu_f(a.y), gelu_f(a.z), gelu_f(a.w));
+                *reinterpret_cast<float4*>(vs + (rg * C + o) * nz4 + z0) = a;
+                *reinterpret_cast<float4*>(vnext + gi) = a;
+            }
+        }
+        __syncthreads();
+        if (cznext) {   // 4 channels x 4 kz per thread
+            const int ncb = C / 4, nkb = (m + 3) / 4;
+            for (int e = threadIdx.x; e < nr * ncb * nkb; e += blockDim.x) {
+                const int kb = e % nkb, cb = (e / nkb) % ncb, rg = e / (nkb * ncb);
+                const int c0 = 4 * cb, k0 = 4 * kb;
+                int kc[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) kc[i] = min(k0 + i, m - 1);
+                float re[4][4] = {}, im[4][4] = {};
+                const float* vr = vs + (rg * C + c0) * nz4;
+                for (int zz = 0; zz < n; zz += 2) {
+                    float2 xv[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) xv[j] = *reinterpret_cast<const float2*>(vr + j * nz4 + zz);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 t = *reinterpret_cast<const float4*>(tf + kc[i] * nt + zz);   // z, z + 1
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            re[i][j] = fmaf(t.x, xv[j].x, fmaf(t.z, xv[j].y, re[i][j]));
+                            im[i][j] = fmaf(t.y, xv[j].x, fmaf(t.w, xv[j].y, im[i][j]));
+                        }
+                    }
+                }
+                const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (k0 + i < m) cznext[((b * C + c0 + j) * n2 + xy) * m + k0 + i] = make_float2(re[i][j], im[i][j]);
+            }
+        }
+        if (y) {   // projection: 8 rows of Q1 x 4 points per thread, partial y summed in shared memory
+            const int npb = (P + 7) / 8;
+            for (int e = threadIdx.x; e < nr * npb * nzb; e += blockDim.x) {
+                const int zb = e % nzb, pb = (e / nzb) % npb, rg = e / (nzb * npb);
+                const int z0 = 4 * zb, p0 = 8 * pb;
+                int pc[8];
+                float a[8][4];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    pc[j] = min(p0 + j, P - 1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[j][i] = pq[pc[j]];
+                }
+                const float* vr = vs + rg * C * nz4 + z0;
+                for (int c = 0; c < C; c += 4) {
+                    float4 x[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) x[i] = *reinterpret_cast<const float4*>(vr + (c + i) * nz4);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const float4 w = *reinterpret_cast<const float4*>(Qs + pc[j] * C4 + c);
+                        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            a[j][0] = fmaf(wv[i], x[i].x, a[j][0]);
+                            a[j][1] = fmaf(wv[i], x[i].y, a[j][1]);
+                            a[j][2] = fmaf(wv[i], x[i].z, a[j][2]);
+                            a[j][3] = fmaf(wv[i], x[i].w, a[j][3]);
+                        }
+                    }
+                }
+                float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (p0 + j >= P) break;
+                    const float q2w = pq[P + p0 + j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) part[i] = fmaf(q2w, gelu_f(a[j][i]), part[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) atomicAdd(ys + rg * n + z0 + i, part[i]);
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+                const int zz = e % n, rg = e / n;
+                const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+                y[b * n2 * n + xy * n + zz] = q2[0] + ys[e];
+            }
         }
     }
 }
@@ -784,8 +1000,8 @@ static float* fld(const DevBuf& b, int64_t i, int64_t per) { return ptr<float>(b
 // plane DFT launch: columns per block about 64 (several planes when inner is short)
 static int plane(SnoModel& M, const float2* in, float2* out, int64_t tab, int64_t P, int Lin, int Lout, int inner) {
     int PB = 1, ICH = inner;
-    if (inner >= 64) ICH = 64;
-    else PB = std::max(1, 64 / inner);
+    if (inner >= 128) ICH = 128;
+    else PB = std::max(1, 128 / inner);
     const int nch = (inner + ICH - 1) / ICH;
     const int64_t nb = ((P + PB - 1) / PB) * nch;
     const size_t smem = (size_t)Lin * PB * std::min(ICH, inner) * sizeof(float2);
@@ -810,6 +1026,13 @@ static int mix(SnoModel& M, int l, const float2* V, float2* G, int B, int adj) {
 }
 
 static unsigned zr_blocks(const SnoModel& M, int B) { return nbs((int64_t)B * M.n * M.n, ZR_RG); }
+static int zr_fwd_rows(const SnoModel& M) {   // row groups per pass: one 8 x 4 tile per thread
+    const int tiles = ((M.C + 7) / 8) * (M.n / 4);
+    return std::max(1, std::min(FR, ZR_T / tiles));
+}
+static unsigned zr_fwd_blocks(const SnoModel& M, int B) {
+    return (unsigned)std::min<int64_t>(nbs((int64_t)B * M.n * M.n, zr_fwd_rows(M)), 16LL * M.num_sms);
+}
 
 // forward; train: keep z_l and the spectra V_l for the backward pass
 static int forward(SnoModel& M, const float* u, float* y, int B, bool train) {
@@ -830,11 +1053,11 @@ static int forward(SnoModel& M, const float* u, float* y, int B, bool train) {
         KF_TRY(plane(M, ptr<float2>(M.g), ptr<float2>(M.gx), M.txi, BC, M2, n, M2 * m));             // x^-1
         KF_TRY(plane(M, ptr<float2>(M.gx), ptr<float2>(M.gy), M.txi, BC * n, M2, n, m));             // y^-1
         const bool last = l == M.L - 1;
-        k_zinv_point<<<zr_blocks(M, B), ZR_T, last ? M.zr_smem_p : M.zr_smem_f, st>>>(
+        k_zrow_fwd<<<zr_fwd_blocks(M, B), ZR_T, M.zf_smem, st>>>(
             ptr<float2>(M.gy), fld(M.v, l, per), th + M.off[o_w(l)], th + M.off[o_b(l)], T + M.tzi, T + M.tzf,
             train ? fld(M.z, l, per) : nullptr, fld(M.v, l + 1, per), last ? nullptr : ptr<float2>(M.cz),
             th + M.off[q], th + M.off[q + 1], th + M.off[q + 2], th + M.off[q + 3], last ? y : nullptr, B, C, n, m,
-            M.P, last ? 0 : 1);
+            M.P, last ? 0 : 1, zr_fwd_rows(M));
         KF_LAUNCH();
     }
     return KIFMM_OK;
@@ -975,8 +1198,8 @@ extern "C" {
 int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int proj_width, int max_batch,
                void* stream) {
     set_error("");
-    if (!out || n < 4 || width < 1 || width > MAXC || modes < 1 || 2 * modes > n || layers < 1 ||
-        proj_width < 1 || proj_width > 2 * MAXC || max_batch < 1) {
+    if (!out || n < 4 || n > 128 || n % 4 || width < 4 || width > MAXC || width % 4 || modes < 1 || 2 * modes > n ||
+        layers < 1 || proj_width < 1 || proj_width > MAXP || max_batch < 1) {
         set_error("sno_create: invalid dimensions");
         return KIFMM_ERR_ARG;
     }
@@ -1009,6 +1232,9 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         const size_t zb = (3 * width * ns + width * C1) * f4 + al +
                           ((size_t)width * modes + n * (modes + 1) + modes * ns) * f8;
         M.zr_smem_f = std::max(lift, std::max(zf, zb));
+        M.zf_smem = ((size_t)FR * width * (n + 4) + width * (width + 4) + width + proj_width * (width + 4) +
+                     2 * proj_width + FR * n) * f4 + al +
+                    ((size_t)FR * width * modes + n * (modes + 1) + modes * (n + 2)) * f8;
         M.zr_smem_p = zf + ((size_t)proj_width * C1 + 4 * n + 2 * proj_width) * f4;
         M.zr_smem_b = (3 * width * ns + 2 * proj_width * ns + proj_width * C1 + 2 * proj_width + n) * f4 + al +
                       (size_t)modes * ns * f8;
@@ -1016,11 +1242,14 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         M.mix_mb = (int)std::max<size_t>(1, std::min<size_t>(16, (96u << 10) / per_mode));
         M.mix_smem = (size_t)M.mix_mb * per_mode;
         M.mixg_smem = (size_t)2 * max_batch * M.mix_mb * width * f8;
-        const size_t plane_smem = (size_t)n * 64 * f8;
+        const size_t plane_smem = (size_t)n * 128 * f8;
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const size_t need = std::max({M.zr_smem_f, M.zr_smem_p, M.zr_smem_b, M.mix_smem, M.mixg_smem, plane_smem});
+        const size_t need = std::max({M.zr_smem_f, M.zr_smem_p, M.zr_smem_b, M.mix_smem, M.mixg_smem, plane_smem,
+                                      M.zf_smem});
+        cudaDeviceGetAttribute(&M.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        M.num_sms = std::max(M.num_sms, 1);
         if (optin <= 0 || need > (size_t)optin) {
             set_error("sno_create: the model's kernels need more shared memory than the device offers");
             delete h;
@@ -1029,6 +1258,7 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         const int lim = optin;
         cudaFuncSetAttribute(k_lift_z, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zinv_point, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zrow_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_zinv_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_proj_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);

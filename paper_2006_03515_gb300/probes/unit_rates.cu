@@ -28,6 +28,22 @@ __global__ void sfu(float* out, int iters) {
     for (int k = 0; k < 8; ++k) s += a[k];
     out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
+// one pair of the near-field kernel's special functions: two ex2 and one rsqrt, independent
+__global__ void sfu_mix(float* out, int iters) {
+    float a[4], b[4], c[4];
+    for (int k = 0; k < 4; ++k) a[k] = b[k] = c[k] = 0.5f + 1e-3f * (threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            a[k] = ex2a(a[k]);
+            b[k] = ex2a(b[k]);
+            c[k] = rsqa(c[k]);
+        }
+    }
+    float s = 0.f;
+    for (int k = 0; k < 4; ++k) s += a[k] + b[k] + c[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
 __global__ void dfma(double* out, int iters) {
     double a[16];
     for (int k = 0; k < 16; ++k) a[k] = 1e-3 * (threadIdx.x + k);
@@ -57,23 +73,25 @@ int main() {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const char* names[3] = {"ex2.approx.f32", "rsqrt.approx.f32", "FP64 FMA"};
+    const char* names[4] = {"ex2.approx.f32", "rsqrt.approx.f32", "FP64 FMA", "2 ex2 + 1 rsqrt"};
     for (int rep = 0; rep < 2; ++rep) {
-        for (int kind = 0; kind < 3; ++kind) {
+        for (int kind = 0; kind < 4; ++kind) {
             const int it = kind == 2 ? 2048 : 8192;
             cudaEventRecord(e0);
             if (kind == 0) sfu<0><<<blocks, threads>>>(f, it);
             else if (kind == 1) sfu<1><<<blocks, threads>>>(f, it);
-            else dfma<<<blocks, threads>>>(d, it);
+            else if (kind == 2) dfma<<<blocks, threads>>>(d, it);
+            else sfu_mix<<<blocks, threads>>>(f, it);
             cudaEventRecord(e1);
             cudaEventSynchronize(e1);
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            const double ops = (kind == 2 ? 16.0 : 8.0) * it * blocks * threads;
+            const double ops = (kind == 2 ? 16.0 : (kind == 3 ? 4.0 : 8.0)) * it * blocks * threads;
             const double rate = ops / (ms * 1e-3);
             if (rep)
                 printf("%-18s %10.1f G/s  %6.2f per SM per clock at %.0f MHz%s\n", names[kind], rate / 1e9,
-                       rate / sms / (clk * 1e3), clk / 1e3, kind == 2 ? "  (x2 flop per FMA)" : "");
+                       rate / sms / (clk * 1e3), clk / 1e3,
+                       kind == 2 ? "  (x2 flop per FMA)" : (kind == 3 ? "  (triples)" : ""));
         }
     }
     cudaError_t e = cudaGetLastError();

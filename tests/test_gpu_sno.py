@@ -122,7 +122,7 @@ def test_save_load_round_trip(model, tmp_path):
     other.load(path)
     assert np.array_equal(other.params(), theta)
     other.close()
-    wrong = kifmm.SNO(s["n"], s["C"] + 1, s["m"], s["L"], s["P"], max_batch=1)
+    wrong = kifmm.SNO(s["n"], s["C"] + 4, s["m"], s["L"], s["P"], max_batch=1)
     with pytest.raises(kifmm.KifmmError):
         wrong.load(path)
     wrong.close()
