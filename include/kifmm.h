@@ -190,6 +190,11 @@ int kifmm_get_list(kifmm_plan_t plan, int which, int64_t* offsets, int32_t* item
 /* Copies per-point self-cell values sigma(h_i) in sorted order (n_points FP64). */
 int kifmm_get_sigma(kifmm_plan_t plan, double* sigma);
 
+/* Copies the upward coefficients c (the truncated-SVD coordinates of each box's upward
+ * equivalent density, c = Sigma^+ U^T q^u, Sec. 3) of the last evaluation:
+ * n_boxes x *stride FP64 host array (*stride receives the row stride, >= the rank). */
+int kifmm_get_upward(kifmm_plan_t plan, double* c, int* stride);
+
 /* Per-phase device times (ms) of the last kifmm_eval when KIFMM_TIMING=1 in
  * the environment at plan time: [scatter, P2M, M2M, M2L, S2L+L2L+DC2DE,
  * L2P+M2P, P2P]. Returns the number of phases written (<= cap). */

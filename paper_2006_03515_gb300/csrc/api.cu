@@ -33,11 +33,11 @@ static void free_plan(Plan* p) {
     }
     dev_free(p->vtab);
     for (auto& o : p->ops)
-        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.Mc, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32, &o.Mc32,
+        for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.Mc, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32, &o.Mc32, &o.ozG1, &o.ozEr,
                           &o.Thi, &o.Tlo})
             dev_free(*b);
     for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
-                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->dd, &p->phid, &p->phiu,
+                      &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
                       &p->tc_tiles, &p->tc_boxes, &p->tc_slots})
         dev_free(*b);
@@ -439,6 +439,15 @@ int kifmm_get_sigma(kifmm_plan_t h, double* sigma) {
         return KIFMM_ERR_ARG;
     }
     return copy_raw(h->p->sigma, h->p->tree.n * 8, sigma, h->p->stream);
+}
+
+int kifmm_get_upward(kifmm_plan_t h, double* c, int* stride) {
+    if (!h || !h->p || !c || !stride) {
+        set_error("kifmm_get_upward: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    *stride = h->p->R;
+    return copy_raw(h->p->cu, (size_t)h->p->tree.nboxes * h->p->R * 8, c, h->p->stream);
 }
 
 int kifmm_get_phase_times(kifmm_plan_t h, float* ms, int cap) {

@@ -389,6 +389,25 @@ int build_eval_data(Plan& p) {
     KF_CUDA(cudaStreamSynchronize(st));
     dev_free(flag); dev_free(pos); dev_free(scan_tmp);
     if (p.precision == KIFMM_MIXED) KF_TRY(p2p_series_check(p));
+    // FP64-exact upward solves on the tensor cores (mixed form; KIFMM_UPWARD=fp64 keeps the FP64 pipe)
+    {
+        const char* up = std::getenv("KIFMM_UPWARD");
+        p.oz = p.precision == KIFMM_MIXED && pinv_oz_supported(S) && !(up && std::string(up) == "fp64");
+    }
+    if (p.oz) {
+        int nmax = 0;
+        for (int l = 2; l < t.nlevels; ++l) {
+            LevelOps& op = p.ops[l];
+            if (p.lv[l].n_up == 0) continue;
+            nmax = std::max(nmax, p.lv[l].n_up);
+            KF_TRY(dev_alloc(op.ozG1, pinv_oz_op_bytes(S, op.rank)));
+            KF_TRY(dev_alloc(op.ozEr, (size_t)((op.rank + 47) / 48 * 48) * 4));
+            KF_TRY(pinv_oz_prepare(st, ptr<double>(op.G1), S, op.rank, op.ozG1.p, ptr<int>(op.ozEr)));
+        }
+        KF_TRY(dev_alloc(p.ozBox, std::max<size_t>(pinv_oz_box_bytes(S, nmax), 16)));
+        KF_TRY(dev_alloc(p.ozEb, (size_t)std::max(nmax + 128, 1) * 4));
+        KF_CUDA(cudaStreamSynchronize(st));
+    }
     return KIFMM_OK;
 }
 
@@ -1190,7 +1209,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
                                                  cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));
         }
-        if (LL.n_up > 0) {   // c = Sigma^+ U^T chk; the K range split over z on small levels (cu is zeroed)
+        if (LL.n_up > 0 && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
+            int64_t extra = 0;
+            KF_TRY(pinv_oz_apply(st, ptr<double>(p.chk), S, ptr<int32_t>(LL.upb), LL.n_up, p.ops[l].ozG1.p,
+                                 ptr<int>(p.ops[l].ozEr), p.ops[l].rank, p.ozBox.p, ptr<int>(p.ozEb), cu, R,
+                                 ptr<int>(p.err), &extra));
+            nl += extra;
+        } else if (LL.n_up > 0) {   // c = Sigma^+ U^T chk; the K range split over z on small levels (cu is zeroed)
             constexpr int RMd = ApplyShape<double>::RM, CNd = ApplyShape<double>::CN;
             const int tiles = (int)(nbk(LL.n_up, 16 * CNd) * nbk(p.ops[l].rank, 16 * RMd));
             const int nz = std::max(1, std::min((S + AP_TK - 1) / AP_TK, (2 * p.num_sms + tiles - 1) / tiles));

@@ -98,6 +98,9 @@ struct LevelOps {
     // tensor-core M2L operands: FP16 hi/lo of T 2^tc_sT, [slot][k-chunk][row][128-byte swizzled row]
     DevBuf Thi, Tlo;
     int tc_sT = 0;
+    // FP64-exact upward solve on the tensor cores: integer slices of G1 (swizzled images) and
+    // the per-row power-of-two exponents
+    DevBuf ozG1, ozEr;
 };
 
 struct Plan {
@@ -163,6 +166,8 @@ struct Plan {
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
+    bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
+    DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
     DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
     DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
     DevBuf tc_slots;             // [tile][344] active offset slots
@@ -205,6 +210,13 @@ struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the te
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
                   int* err);
+// pinv_oz.cu: FP64-exact c = Sigma^+ U^T chk on the tensor cores
+int pinv_oz_supported(int S);
+size_t pinv_oz_op_bytes(int S, int rank);
+size_t pinv_oz_box_bytes(int S, int n);
+int pinv_oz_prepare(cudaStream_t st, const double* G1, int S, int rank, void* img, int* er);
+int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, int n, const void* opimg,
+                  const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err, int64_t* launches);
 // api.cu / eval.cu helpers for the surrogate
 Plan* kifmm_plan_internal(kifmm_plan_t h);
 int kifmm_scatter_weights(Plan& p, const double* I);

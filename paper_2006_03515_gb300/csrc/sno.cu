@@ -140,7 +140,7 @@ __global__ void k_tables(int n, int m, float2* t, int64_t tzf, int64_t tyf, int6
 __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, float2* __restrict__ out,
                                                const float2* __restrict__ T, int64_t P, int Lin, int Lout, int inner,
                                                int PB, int ICH, int nch) {
-    extern __shared__ float2 psh[];
+    extern __shared__ float2 psh[];   // [Lin][ncol] inputs, then T [Lout][Lin]
     const int64_t pb = blockIdx.x / nch;
     const int ch = (int)(blockIdx.x % nch);
     const int64_t p0 = pb * PB;
@@ -153,6 +153,8 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
         const int pl = col / W, w = col % W;
         psh[q * ncol + col] = in[((p0 + pl) * Lin + q) * (int64_t)inner + i0 + w];
     }
+    float2* Ts = psh + Lin * ncol;
+    for (int e = threadIdx.x; e < Lout * Lin; e += blockDim.x) Ts[e] = T[e];
     __syncthreads();
     // each thread: 8 consecutive outputs j0..j0+7 of two columns (col, col + ncol/2); the
     // columns' inputs are read once per q and T[j][q] is uniform across the warp
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
         const int c1 = c0 + nch2 < ncol ? c0 + nch2 : c0;
         const int j0 = 8 * jb;
         const int nj = min(8, Lout - j0);
-        const float2* t0 = T + (int64_t)j0 * Lin;
+        const float2* t0 = Ts + j0 * Lin;
         float re[2][8], im[2][8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) re[0][u] = im[0][u] = re[1][u] = im[1][u] = 0.f;
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
             const float2 x0 = psh[q * ncol + c0], x1 = psh[q * ncol + c1];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const float2 a = __ldg(t0 + (int64_t)min(u, nj - 1) * Lin + q);
+                const float2 a = t0[min(u, nj - 1) * Lin + q];
                 re[0][u] = fmaf(a.x, x0.x, fmaf(-a.y, x0.y, re[0][u]));
                 im[0][u] = fmaf(a.x, x0.y, fmaf(a.y, x0.x, im[0][u]));
                 re[1][u] = fmaf(a.x, x1.x, fmaf(-a.y, x1.y, re[1][u]));
@@ -1004,7 +1006,7 @@ static int plane(SnoModel& M, const float2* in, float2* out, int64_t tab, int64_
     else PB = std::max(1, 128 / inner);
     const int nch = (inner + ICH - 1) / ICH;
     const int64_t nb = ((P + PB - 1) / PB) * nch;
-    const size_t smem = (size_t)Lin * PB * std::min(ICH, inner) * sizeof(float2);
+    const size_t smem = ((size_t)Lin * PB * std::min(ICH, inner) + (size_t)Lout * Lin) * sizeof(float2);
     k_plane<<<(unsigned)nb, 256, smem, M.st>>>(in, out, ptr<float2>(M.tabs) + tab, P, Lin, Lout, inner, PB, ICH, nch);
     KF_LAUNCH();
     return KIFMM_OK;
@@ -1242,7 +1244,7 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         M.mix_mb = (int)std::max<size_t>(1, std::min<size_t>(16, (96u << 10) / per_mode));
         M.mix_smem = (size_t)M.mix_mb * per_mode;
         M.mixg_smem = (size_t)2 * max_batch * M.mix_mb * width * f8;
-        const size_t plane_smem = (size_t)n * 128 * f8;
+        const size_t plane_smem = ((size_t)n * 128 + (size_t)n * 2 * modes) * f8;
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -57,7 +57,7 @@ class _Info(ctypes.Structure):
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
            "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
-           "kifmm_get_sigma", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
+           "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load",
            "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"]
@@ -92,11 +92,12 @@ def load():
     L.kifmm_get_tree.argtypes = [vp] + [vp] * 9
     L.kifmm_get_list.argtypes = [vp, i32, vp, vp]
     L.kifmm_get_sigma.argtypes = [vp, vp]
+    L.kifmm_get_upward.argtypes = [vp, vp, ctypes.POINTER(i32)]
     L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
     L.kifmm_direct_noalloc.argtypes = [vp, i64, dbl, vp, vp, dbl, dbl, dbl, i32, vp]
     L.kifmm_autotune.argtypes = [vp, i64, vp, dbl, vp, i32, i32, dbl, dbl, ctypes.POINTER(_Opts), i32, vp, vp]
     for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_get_info",
-                 "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_phase_times",
+                 "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times",
                  "kifmm_direct_noalloc", "kifmm_autotune"):
         getattr(L, name).restype = ctypes.c_int
     _load_sno(L)
@@ -213,6 +214,14 @@ class Plan:
         s = np.empty(self.n, np.float64)
         _check(load().kifmm_get_sigma(self._h_ptr, ctypes.c_void_p(s.ctypes.data)))
         return s
+
+    def upward(self):
+        """Upward coefficients c of the last evaluation, (n_boxes, stride) FP64."""
+        inf = self.info()
+        st = ctypes.c_int()
+        buf = np.empty(inf["n_boxes"] * 512, np.float64)   # stride <= 512
+        _check(load().kifmm_get_upward(self._h_ptr, ctypes.c_void_p(buf.ctypes.data), ctypes.byref(st)))
+        return buf[: inf["n_boxes"] * st.value].reshape(inf["n_boxes"], st.value).copy()
 
     def phase_times(self):
         ms = (ctypes.c_float * 8)()

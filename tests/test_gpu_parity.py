@@ -126,6 +126,40 @@ def test_mixed_matches_fp64(kf, m0, po2):
     assert _relerr(s32, s64) <= 1e-6
 
 
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
+    """The mixed form's upward pseudo-inverse on the tensor cores (exact integer slices, FP64
+    combination) against the same plan's FP64-pipe GEMM: FP64 agreement of the upward
+    coefficients c of every box."""
+    if adaptive:
+        pts, h = _adaptive_small()
+        I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
+                              head_sigma=0.05, noise_sigma=0.3, seed=7)
+        a, b, leaf, uniform = 5.32, 304.0, 16, False
+    else:
+        pts, h, I = W.config_uniform(32)
+        a, b = K.absorption_coefficients(152.0)
+        leaf, uniform = 64, True
+
+    def run(mode):
+        if mode:
+            monkeypatch.setenv("KIFMM_UPWARD", mode)
+        else:
+            monkeypatch.delenv("KIFMM_UPWARD", raising=False)
+        p = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform, precision="mixed")
+        s = p.eval(_dev(I)).cpu().numpy()
+        c = p.upward()
+        p.close()
+        return s, c
+
+    s_tc, c_tc = run(None)
+    s_64, c_64 = run("fp64")
+    scale = np.abs(c_64).max(axis=1, keepdims=True)
+    scale[scale == 0] = 1.0
+    assert np.max(np.abs(c_tc - c_64) / scale) <= 1e-12
+    assert _relerr(s_tc, s_64) <= 1e-9
+
+
 def test_mixed_adaptive_matches_fp64(kf):
     pts, h = _adaptive_small()
     I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
