@@ -44,32 +44,45 @@ static inline size_t oz_smem(int S) { return 1024 + oz_b_bytes(S) + (size_t)OZ_N
 
 int pinv_oz_supported(int S) { return oz_smem(S) <= 227 * 1024 ? 1 : 0; }
 
-// Slices of one row v[0..S) (FP64) written as FP16 integers into the swizzled image
-// img + slice * slice_stride + (k / 64) * chunk_stride + sw128(row, k % 64); returns e.
-__device__ __forceinline__ void oz_slice_row(const double* v, int S, int KP, double scale_e, __half* img,
+// Slices of one row v[0..S) written as FP16 integers into the swizzled image
+// img + slice * slice_stride + (k / 64) * chunk_stride + sw128(row, k % 64), in integer
+// arithmetic only (FP64 throughput is scarce): each value becomes the 54-bit fixed-point
+// integer X = round(v 2^{54 - e}) (|X| < 2^54), split into balanced base-64 digits
+// X = sum_i a_i 64^{9-i}, rounding each digit to nearest (|a_1| <= 64, |a_i| <= 32 after).
+__device__ __forceinline__ void oz_slice_row(const double* v, int S, int KP, int e, __half* img,
                                              int64_t slice_stride, int64_t chunk_stride, int row, int lane) {
     for (int k = lane; k < KP; k += 32) {
-        double x = k < S ? v[k] * scale_e : 0.0;
+        long long X = 0;
+        if (k < S) {
+            const long long bits = __double_as_longlong(v[k]);
+            const int ex = (int)((bits >> 52) & 0x7FF);
+            if (ex != 0) {   // zero and subnormal values (below 2^-1022) count as zero
+                const long long m = (bits & ((1LL << 52) - 1)) | (1LL << 52);
+                const int sh = ex - 1021 - e;   // X = m 2^sh
+                if (sh >= 0) X = m << sh;
+                else if (sh > -64) X = (m + (1LL << (-sh - 1))) >> (-sh);
+                if (bits < 0) X = -X;
+            }
+        }
         const int64_t base = (int64_t)(k / OZ_KC) * chunk_stride;
         const uint32_t off = sw128_off_h(row, k % OZ_KC) / 2;
 #pragma unroll
         for (int i = 0; i < OZ_S; ++i) {
-            const double t = x * 64.0;
-            const double a = rint(t);
-            x = t - a;
-            img[(int64_t)i * slice_stride + base + off] = __double2half((double)a);
+            const int s = OZ_W * (OZ_S - 1 - i);   // 48, 42, ..., 0
+            const long long a = s > 0 ? (X + (1LL << (s - 1))) >> s : X;
+            X -= a << s;
+            img[(int64_t)i * slice_stride + base + off] = __int2half_rn((int)a);
         }
     }
 }
 
-// largest |v[k]| of a row as a power-of-two exponent: |v| 2^-e < 1 (0 for a zero row)
+// power-of-two exponent of a row's largest magnitude: |v| 2^-e < 1 (0 for a zero row),
+// from the exponent fields alone
 __device__ __forceinline__ int oz_row_exp(const double* v, int S, int lane) {
-    double m = 0.0;
-    for (int k = lane; k < S; k += 32) m = fmax(m, fabs(v[k]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    int e = 0;
-    if (m > 0.0) frexp(m, &e);   // m = f 2^e, f in [0.5, 1)
-    return e;
+    int mx = 0;
+    for (int k = lane; k < S; k += 32) mx = max(mx, (int)((__double_as_longlong(v[k]) >> 52) & 0x7FF));
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    return mx ? mx - 1022 : 0;   // |v| < 2^(mx - 1022)
 }
 
 // operator image: [row tile][slice][K-chunk][48 rows][128-byte row]; one warp per row
@@ -84,10 +97,10 @@ __global__ void k_oz_slice_op(const double* G1, int S, int rank, int ntile, __ha
     if (r < rank) {
         const double* v = G1 + (int64_t)r * S;
         const int e = oz_row_exp(v, S, lane);
-        oz_slice_row(v, S, KP, ldexp(1.0, -e), base, slice_stride, chunk_stride, row, lane);
+        oz_slice_row(v, S, KP, e, base, slice_stride, chunk_stride, row, lane);
         if (lane == 0) er[r] = e;
     } else {
-        oz_slice_row(G1, 0, KP, 0.0, base, slice_stride, chunk_stride, row, lane);   // zero row
+        oz_slice_row(G1, 0, KP, 0, base, slice_stride, chunk_stride, row, lane);   // zero row
         if (lane == 0) er[r] = 0;
     }
 }
@@ -106,12 +119,18 @@ __global__ void k_oz_slice_boxes(const double* chk, int S, const int32_t* boxes,
     if (p < n) {
         const double* v = chk + (int64_t)boxes[p] * S;
         const int e = oz_row_exp(v, S, lane);
-        oz_slice_row(v, S, KP, ldexp(1.0, -e), base, slice_stride, chunk_stride, row, lane);
+        oz_slice_row(v, S, KP, e, base, slice_stride, chunk_stride, row, lane);
         if (lane == 0) eb[p] = e;
     } else {
-        oz_slice_row(chk, 0, KP, 0.0, base, slice_stride, chunk_stride, row, lane);
+        oz_slice_row(chk, 0, KP, 0, base, slice_stride, chunk_stride, row, lane);
         if (lane == 0) eb[p] = 0;
     }
+}
+
+// 2^k as a double (exponent bits in the normal range, ldexp outside it)
+__device__ __forceinline__ double pow2d(int k) {
+    if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
+    return ldexp(1.0, k);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -224,11 +243,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         const bool ok = mbar_wait(smem_u32(&done), 0, &abort_flag);
         if (!__any_sync(0xffffffffu, !ok)) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            double acc[24];
+            // level sums are exact integers below 2^22 in FP32: read them as integers (magic-number
+            // add) and combine exactly in 64-bit integers, levels 2..6 (hi) and 7..10 (lo)
+            long long hi[24], lo[24];
 #pragma unroll
-            for (int c = 0; c < 24; ++c) acc[c] = 0.0;
-            for (int L = OZ_S - 1; L >= 0; --L) {   // smallest terms first
-                const double sc = ldexp(1.0, -OZ_W * (L + 2));
+            for (int c = 0; c < 24; ++c) hi[c] = lo[c] = 0;
+            for (int L = 0; L < OZ_S; ++L) {
                 uint32_t v[24];
                 const uint32_t ta = tmem + t_row + (uint32_t)(L * OZ_N + 24 * half);
                 asm volatile(
@@ -245,15 +265,23 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     : "r"(ta + 16u));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int c = 0; c < 24; ++c) acc[c] = fma((double)__uint_as_float(v[c]), sc, acc[c]);
+                for (int c = 0; c < 24; ++c) {
+                    const long long P = (long long)(__float_as_int(__uint_as_float(v[c]) + 12582912.0f) - 0x4B400000);
+                    if (L <= 4) hi[c] += P << (OZ_W * (4 - L));
+                    else lo[c] += P << (OZ_W * (8 - L));
+                }
             }
             const int p = bt * OZ_M + 32 * q + lane;
             if (p < n) {
                 const int e_b = eb[p];
                 double* o = cu + (int64_t)boxes[p] * R + r0 + 24 * half;
 #pragma unroll
-                for (int c = 0; c < 24; ++c)
-                    if (r0 + 24 * half + c < rank) o[c] = ldexp(acc[c], e_b + ers[24 * half + c]);
+                for (int c = 0; c < 24; ++c) {
+                    if (r0 + 24 * half + c >= rank) break;
+                    // c = 2^{e_b + e_r} (hi 2^-36 + lo 2^-60)
+                    const int E = e_b + ers[24 * half + c];
+                    o[c] = fma((double)hi[c], pow2d(E - 36), (double)lo[c] * pow2d(E - 60));
+                }
             }
         }
     }
