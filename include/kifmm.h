@@ -169,7 +169,8 @@ typedef struct {
     int64_t m2l_tensor;         /* 1 if M2L runs on the tensor cores (mixed form) */
     int64_t device_error;       /* nonzero if a bounded device wait ran out (synchronises) */
     double m2l_flops;           /* algorithmic M2L flop of one kifmm_eval: 2 r_l^2 per V pair */
-    double upward_flops;        /* upward pseudo-inverse work: 2 r_l S per leaf + 2 r_l r_(l+1) per child */
+    double upward_flops;        /* upward pseudo-inverse work (FP64-equivalent): 2 r_l S per leaf and parent */
+    double upward_mma_flops;    /* FP16 tensor-core flop executed for it by the exact slice products (0 on the FP64 pipe) */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */

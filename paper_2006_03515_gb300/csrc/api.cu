@@ -373,6 +373,10 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
         // FP64 pseudo-inverse applications c = Sigma^+ U^T chk, one per leaf and per parent
         for (int l = 2; l < p.tree.nlevels; ++l) up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_up;
         info->upward_flops = up;
+        double mma = 0;
+        if (p.oz)
+            for (int l = 2; l < p.tree.nlevels; ++l) mma += pinv_oz_mma_flops(p.S, p.ops[l].rank, p.lv[l].n_up);
+        info->upward_mma_flops = mma;
     }
     info->device_error = 0;
     if (p.err.p) {

@@ -1204,7 +1204,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
-            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (2 * p.num_sms + tiles - 1) / tiles));
+            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms + tiles - 1) / tiles));
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
                                                  cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));

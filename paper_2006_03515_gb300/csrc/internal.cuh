@@ -214,6 +214,7 @@ int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* til
 int pinv_oz_supported(int S);
 size_t pinv_oz_op_bytes(int S, int rank);
 size_t pinv_oz_box_bytes(int S, int n);
+double pinv_oz_mma_flops(int S, int rank, int n);   // tensor-core flop of one level's solve
 int pinv_oz_prepare(cudaStream_t st, const double* G1, int S, int rank, void* img, int* er);
 int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, int n, const void* opimg,
                   const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err, int64_t* launches);

@@ -295,6 +295,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 // host side
 // ------------------------------------------------------------------------------------
 size_t pinv_oz_op_bytes(int S, int rank) { return (size_t)((rank + OZ_N - 1) / OZ_N) * oz_b_bytes(S); }
+double pinv_oz_mma_flops(int S, int rank, int n) {
+    if (n <= 0) return 0.0;
+    const double pairs = OZ_S * (OZ_S + 1) / 2;   // slice pairs with i + j <= 10
+    return pairs * 2.0 * OZ_M * OZ_N * oz_kp(S) * ((n + OZ_M - 1) / OZ_M) * ((rank + OZ_N - 1) / OZ_N);
+}
 size_t pinv_oz_box_bytes(int S, int n) { return (size_t)OZ_S * ((n + OZ_M - 1) / OZ_M) * oz_nk(S) * OZ_M * 128; }
 
 int pinv_oz_prepare(cudaStream_t st, const double* G1, int S, int rank, void* img, int* er) {

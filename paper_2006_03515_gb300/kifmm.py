@@ -52,7 +52,8 @@ class _Info(ctypes.Structure):
                 ("list_len", ctypes.c_int64 * 4), ("origin", ctypes.c_double * 3), ("side", ctypes.c_double),
                 ("pinv_rank_min", ctypes.c_double), ("eval_launches", ctypes.c_int64),
                 ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64),
-                ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double)]
+                ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double),
+                ("upward_mma_flops", ctypes.c_double)]
 
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
@@ -189,7 +190,8 @@ class Plan:
                     origin=list(inf.origin), side=inf.side, pinv_rank_min=int(inf.pinv_rank_min),
                     eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs),
                     m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error),
-                    m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops))
+                    m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops),
+                    upward_mma_flops=float(inf.upward_mma_flops))
 
     def tree(self):
         inf = self.info()

@@ -208,7 +208,8 @@ def test_float32_io_and_host_path(kf):
     s32 = p.eval(_dev(I).to(torch.float32)).cpu().numpy()
     assert _relerr(s32.astype(np.float64), s64) < 1e-6
     sh = p.eval_host(I)
-    np.testing.assert_array_equal(sh, s64)
+    # small levels add split partial sums atomically, in an order that may vary between evaluations
+    np.testing.assert_allclose(sh, s64, rtol=1e-12, atol=0)
 
 
 def test_batch_and_graph_replay(kf):
@@ -229,8 +230,8 @@ def test_batch_and_graph_replay(kf):
                 s.zero_()
             kf.eval_batch(plans, Is, Ss, capture=capture)
             st.synchronize()
-            for s, r in zip(Ss, refs):
-                assert torch.equal(s, r)
+            for s, r in zip(Ss, refs):   # small levels add split partial sums atomically (order may vary)
+                assert torch.allclose(s, r, rtol=1e-12, atol=0)
 
 
 def test_duplicate_and_nonfinite_rejected(kf):
@@ -307,8 +308,8 @@ def test_batched_uneven_fields_graph_captured(kf):
         for _ in range(2):
             kf.eval_batch(plans, Is, Ss, C=Cs, capture=True)
             st.synchronize()
-            for s, r in zip(Ss, refs):
-                assert torch.equal(s, r)
+            for s, r in zip(Ss, refs):   # small levels add split partial sums atomically (order may vary)
+                assert torch.allclose(s, r, rtol=1e-12, atol=0)
     # one field against the FP64 form
     pts, h, I, p = fields[0]
     a, b = K.absorption_coefficients(0.2 * p)
