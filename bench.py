@@ -43,13 +43,13 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the pair kernel's traffic is
 # compulsory and scales with the point count (x (128/96)^3 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 705.74e6 + 16.07e6, "per_point_scaled": False,
+    "M2L": {"bytes": 296.78e6 + 16.40e6, "per_point_scaled": False,
             "src": "paper_2006_03515_gb300/csrc/m2l_tc.cu",
-            "sha256": "2747b36cde2cdcd0581889ff1981c1e919177ac03152856dd8cfc5a0ebe56664",
+            "sha256": "8583d28f6c6c042b56c73eaf85fe443c0af55a0d99ace9797d8d9fb1134c7b58",
             "profile": "profiles/k_m2l_tc_uniform96.md"},
-    "P2P": {"bytes": 50.66e6 + 1.19e6, "per_point_scaled": True, "n_profiled": 96 ** 3,
+    "P2P": {"bytes": 50.66e6 + 1.27e6, "per_point_scaled": True, "n_profiled": 96 ** 3,
             "src": "paper_2006_03515_gb300/csrc/eval.cu",
-            "sha256": "b9d7b886dea533060d29a77841683ace42960e41b4d6553feb72abcc594101d9",
+            "sha256": "96bdcd941c49677257cc4cd008606df417528f57461dda96f3db1bd023bf3316",
             "profile": "profiles/k_p2p_mixed_uniform96.md"},
 }
 
