@@ -375,7 +375,8 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
         info->upward_flops = up;
         double mma = 0;
         if (p.oz)
-            for (int l = 2; l < p.tree.nlevels; ++l) mma += pinv_oz_mma_flops(p.S, p.ops[l].rank, p.lv[l].n_up);
+            for (int l = 2; l < p.tree.nlevels; ++l)
+                if (p.lv[l].n_up > p.oz_min) mma += pinv_oz_mma_flops(p.S, p.ops[l].rank, p.lv[l].n_up);
         info->upward_mma_flops = mma;
     }
     info->device_error = 0;

@@ -393,6 +393,8 @@ int build_eval_data(Plan& p) {
     {
         const char* up = std::getenv("KIFMM_UPWARD");
         p.oz = p.precision == KIFMM_MIXED && pinv_oz_supported(S) && !(up && std::string(up) == "fp64");
+        const char* om = std::getenv("KIFMM_OZ_MIN");   // level-size threshold (tests use 0)
+        p.oz_min = om ? std::max(0, std::atoi(om)) : kOzMinBoxes;
     }
     if (p.oz) {
         int nmax = 0;
@@ -1209,7 +1211,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
                                                  cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));
         }
-        if (LL.n_up > 0 && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
+        if (LL.n_up > p.oz_min && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
             int64_t extra = 0;
             KF_TRY(pinv_oz_apply(st, ptr<double>(p.chk), S, ptr<int32_t>(LL.upb), LL.n_up, p.ops[l].ozG1.p,
                                  ptr<int>(p.ops[l].ozEr), p.ops[l].rank, p.ozBox.p, ptr<int>(p.ozEb), cu, R,

@@ -14,6 +14,10 @@ constexpr int kMaxLevel = 20;
 constexpr int kOffsetSlots = 343;   // (dx, dy, dz) in [-3, 3]^3
 constexpr double kRInner = 1.2;     // upward equivalent / downward check surface (box half-widths)
 constexpr double kROuter = 2.6;     // upward check / downward equivalent surface
+// Upward solves of levels with at most kOzMinBoxes boxes take the FP64-pipe GEMM with its K
+// range split over many CTAs: a tensor-core slice-product CTA needs about 45 us, which a
+// handful of CTAs cannot hide.
+constexpr int kOzMinBoxes = 1024;
 
 // ---- error plumbing ---------------------------------------------------------------
 void set_error(const std::string& msg);
@@ -168,6 +172,7 @@ struct Plan {
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
+    int oz_min = kOzMinBoxes;    // levels with more upward solves than this use the slice products
     DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
     DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
     DevBuf tc_slots;             // [tile][344] active offset slots

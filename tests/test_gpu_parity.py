@@ -141,6 +141,8 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
         a, b = K.absorption_coefficients(152.0)
         leaf, uniform = 64, True
 
+    monkeypatch.setenv("KIFMM_OZ_MIN", "0")   # every level through the slice products
+
     def run(mode):
         if mode:
             monkeypatch.setenv("KIFMM_UPWARD", mode)

@@ -244,3 +244,51 @@ def test_sno_forward_shapes_and_linear_limit():
     u = np.random.default_rng(1).standard_normal((n, n, n))
     y = sno.forward(theta, u, C, m, L, P)
     assert y.shape == (n, n, n) and np.all(y == 0.0)
+
+
+# ---- Chebyshev (volumetric) representation option -------------------------------------------
+def test_cheb_interpolation_reproduces_polynomials():
+    """Interpolation at p Chebyshev nodes is exact for polynomials of degree < p, per axis
+    and as a tensor product."""
+    from oracle import cheb
+    p = 6
+    x = np.linspace(-1.0, 1.0, 11)
+    for k in range(p):
+        got = cheb.s1(x, p) @ cheb.nodes1(p) ** k
+        assert np.max(np.abs(got - x ** k)) < 1e-12
+    rng = np.random.Generator(np.random.PCG64(5))
+    X = rng.uniform(-1.0, 1.0, (20, 3))
+    nd = cheb.nodes3(p)
+    f = lambda v: v[:, 0] ** 2 * v[:, 1] ** 5 - 3.0 * v[:, 2] ** 4 * v[:, 0] + 0.5
+    assert np.max(np.abs(cheb.s3(X, p) @ f(nd) - f(X))) < 1e-12
+
+
+def test_cheb_m2m_is_exact():
+    """M2M of the children's P2M equals the parent's own P2M (the parent's interpolation
+    weights are polynomials of degree < p in the children's coordinates)."""
+    from oracle import cheb
+    p = 5
+    rng = np.random.Generator(np.random.PCG64(9))
+    ops = cheb.ChebOperators(1.0, 2, p, 5.32, 304.0)
+    Wp = np.zeros(p ** 3)
+    direct = np.zeros(p ** 3)
+    for o in range(8):
+        c = 0.5 * (2.0 * np.array([(o & 1), (o >> 1) & 1, (o >> 2) & 1]) - 1.0)   # parent units
+        y = c + 0.5 * rng.uniform(-1.0, 1.0, (7, 3))
+        q = rng.uniform(0.1, 1.0, 7)
+        Wc = cheb.s3((y - c) / 0.5, p).T @ q
+        Wp += ops.m2m[o] @ Wc
+        direct += cheb.s3(y, p).T @ q
+    assert np.max(np.abs(Wp - direct)) <= 1e-12 * np.max(np.abs(direct))
+
+
+def test_cheb_fmm_converges_to_the_direct_sum():
+    """The Chebyshev-representation FMM approaches the direct sum as p grows (16^3 cube,
+    760 Torr, Gaussian source): p = 4 -> 1e-4, p = 6 -> 3.4e-6, p = 8 -> 4.4e-8."""
+    from oracle import cheb
+    pts, h, I = W.config_uniform(16)
+    a, b = K.absorption_coefficients(150.0)
+    ref = D.direct_sum(pts, h, I, a, b)
+    err = [np.linalg.norm(cheb.fmm(pts, h, I, 8, p, a, b) - ref) / np.linalg.norm(ref) for p in (4, 6)]
+    assert err[1] < 0.1 * err[0]
+    assert err[1] <= 1e-5
