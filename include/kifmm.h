@@ -51,6 +51,7 @@ typedef enum {
 
 typedef enum { KIFMM_FP64 = 0, KIFMM_MIXED = 1 } kifmm_precision;
 typedef enum { KIFMM_SELF_CELL_EXACT = 0, KIFMM_SELF_PAPER_GL2 = 1 } kifmm_self_mode;
+typedef enum { KIFMM_REPR_SURFACE = 0, KIFMM_REPR_CHEB = 1 } kifmm_repr;
 typedef enum { KIFMM_F32 = 0, KIFMM_F64 = 1 } kifmm_dtype;
 
 typedef struct {
@@ -74,10 +75,16 @@ typedef struct {
     double root[4];
     /* cudaStream_t on which the plan runs all of its work (NULL = default stream). */
     void* stream;
+    /* Far-field representation. KIFMM_REPR_SURFACE (default): the paper's equivalent and
+     * check surfaces with m0 = surface_order (Sec. 3). KIFMM_REPR_CHEB: values at the
+     * p^3 tensor Chebyshev nodes of each box, p = surface_order (2..10), with polynomial
+     * interpolation in place of the pseudo-inverses (a volumetric representation, not in
+     * the paper, that reaches the direct sum to ~1e-7 at p = 8). */
+    int repr;
 } kifmm_opts;
 
 /* Fills *opts with the defaults above (FP64, cell-exact self term, eps 1e-5,
- * automatic root, default stream). */
+ * automatic root, default stream, surface representation). */
 void kifmm_default_opts(kifmm_opts* opts);
 
 /*
@@ -158,7 +165,7 @@ typedef struct {
     int64_t n_points;
     int64_t n_boxes;
     int32_t n_levels;
-    int32_t surface_points;     /* S = m0^3 - (m0-2)^3 */
+    int32_t surface_points;     /* S = m0^3 - (m0-2)^3 (Chebyshev representation: p^3) */
     int64_t n_leaves;
     int64_t list_len[4];        /* total entries of U, V, W, X */
     double origin[3];

@@ -36,7 +36,7 @@ static void free_plan(Plan* p) {
         for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.Mc, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32, &o.Mc32, &o.ozG1, &o.ozEr,
                           &o.Thi, &o.Tlo})
             dev_free(*b);
-    for (DevBuf* b : {&p->surf, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
+    for (DevBuf* b : {&p->surf, &p->ctab, &p->ctab32, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
                       &p->tc_tiles, &p->tc_boxes, &p->tc_slots})
@@ -102,8 +102,16 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         set_error("kifmm_plan: uniform_h must be finite and > 0 when cell_h is NULL");
         return KIFMM_ERR_ARG;
     }
-    if (leaf_size < 1 || surface_order < 3 || surface_order > 12) {
+    if (o.repr != KIFMM_REPR_SURFACE && o.repr != KIFMM_REPR_CHEB) {
+        set_error("kifmm_plan: unknown repr");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.repr == KIFMM_REPR_SURFACE && (leaf_size < 1 || surface_order < 3 || surface_order > 12)) {
         set_error("kifmm_plan: need leaf_size >= 1 and 3 <= surface_order <= 12");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.repr == KIFMM_REPR_CHEB && (leaf_size < 1 || surface_order < 2 || surface_order > 10)) {
+        set_error("kifmm_plan: need leaf_size >= 1 and 2 <= p <= 10 for the Chebyshev representation");
         return KIFMM_ERR_ARG;
     }
     if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) {
@@ -138,8 +146,10 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     p->a = a;
     p->b = b;
     p->m0 = surface_order;
-    p->S = surface_order * surface_order * surface_order -
-           (surface_order - 2) * (surface_order - 2) * (surface_order - 2);
+    p->cheb = o.repr == KIFMM_REPR_CHEB;
+    p->S = p->cheb ? surface_order * surface_order * surface_order
+                   : surface_order * surface_order * surface_order -
+                         (surface_order - 2) * (surface_order - 2) * (surface_order - 2);
     p->Sp = (p->S + 31) / 32 * 32;
     p->leaf_size = leaf_size;
     p->tree.n = n;
@@ -371,7 +381,9 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     {
         double up = 0;
         // FP64 pseudo-inverse applications c = Sigma^+ U^T chk, one per leaf and per parent
-        for (int l = 2; l < p.tree.nlevels; ++l) up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_up;
+        // (none in the Chebyshev representation)
+        if (!p.cheb)
+            for (int l = 2; l < p.tree.nlevels; ++l) up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_up;
         info->upward_flops = up;
         double mma = 0;
         if (p.oz)

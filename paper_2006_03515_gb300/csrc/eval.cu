@@ -4,8 +4,10 @@
 #include <cstdlib>
 
 #include <cstring>
+#include <type_traits>
 
 #include "internal.cuh"
+#include "cheb.cuh"
 #include "kernel.cuh"
 
 namespace kifmm {
@@ -373,16 +375,18 @@ int build_eval_data(Plan& p) {
     KF_TRY(dev_alloc(p.chk, (size_t)nb * S * 8));
     KF_TRY(dev_alloc(p.cu, (size_t)nb * R * 8));
     KF_TRY(dev_alloc(p.dd, (size_t)nb * R * ts));
-    KF_TRY(dev_alloc(p.phid, (size_t)nb * S * ts));
-    KF_CUDA(cudaMemsetAsync(p.phid.p, 0, (size_t)nb * S * ts, st));
+    if (!p.cheb) {   // the Chebyshev representation reads the node values d and c in place
+        KF_TRY(dev_alloc(p.phid, (size_t)nb * S * ts));
+        KF_CUDA(cudaMemsetAsync(p.phid.p, 0, (size_t)nb * S * ts, st));
+    }
     if (p.precision == KIFMM_MIXED) KF_TRY(dev_alloc(p.cu32, (size_t)nb * R * 4));
     if (p.m2l_tensor) {
         KF_TRY(dev_alloc(p.chi, (size_t)nb * R * 2));
         KF_TRY(dev_alloc(p.clo, (size_t)nb * R * 2));
         KF_TRY(dev_alloc(p.cexp, (size_t)nb * 4));
     }
-    if (p.lists[3].len > 0) KF_TRY(dev_alloc(p.chkx, (size_t)nb * S * ts));
-    if (p.lists[2].len > 0) {
+    if (p.lists[3].len > 0 && !p.cheb) KF_TRY(dev_alloc(p.chkx, (size_t)nb * S * ts));
+    if (p.lists[2].len > 0 && !p.cheb) {
         KF_TRY(dev_alloc(p.phiu, (size_t)nb * S * ts));
         KF_CUDA(cudaMemsetAsync(p.phiu.p, 0, (size_t)nb * S * ts, st));
     }
@@ -392,7 +396,7 @@ int build_eval_data(Plan& p) {
     // FP64-exact upward solves on the tensor cores (mixed form; KIFMM_UPWARD=fp64 keeps the FP64 pipe)
     {
         const char* up = std::getenv("KIFMM_UPWARD");
-        p.oz = p.precision == KIFMM_MIXED && pinv_oz_supported(S) && !(up && std::string(up) == "fp64");
+        p.oz = p.precision == KIFMM_MIXED && !p.cheb && pinv_oz_supported(S) && !(up && std::string(up) == "fp64");
         const char* om = std::getenv("KIFMM_OZ_MIN");   // level-size threshold (tests use 0)
         p.oz_min = om ? std::max(0, std::atoi(om)) : kOzMinBoxes;
     }
@@ -423,10 +427,17 @@ struct EvalView {
     const int32_t* level;
     const int32_t* pstart;
     const int32_t* pend;
-    const double* surf;     // unit lattice (3*S)
+    const double* surf;     // unit lattice (3*S); Chebyshev representation: the unit nodes
     double side;
     int S;
     KParams kp;
+    double rf_dchk;         // radius of the downward check surface in half-widths (Chebyshev: 1)
+    double rf_ueq;          // radius of the upward equivalent surface in half-widths (Chebyshev: 1)
+    int ldu;                // row stride of the upward densities read by the W list
+    int cheb;               // Chebyshev representation: the local part of L2P is interpolation
+    int cp;                 // Chebyshev order p
+    const double* ctab;     // Chebyshev weight table c_k T_k(xbar_n), row stride kChebTab
+    const float* ctab32;
 };
 
 __device__ __forceinline__ double half_width(const EvalView& E, int lev) {
@@ -715,10 +726,12 @@ __global__ void k_to_f32(const double* in, float* out, int64_t n) {
 }
 
 // S2L for the X list: downward check potential of B (x_j = c_B + 1.2 r_B s_j) from the
-// sources of every leaf A in X(B). One block per box.
+// sources of every leaf A in X(B). One block per box. Row B of chk (stride ldc) is
+// written, or added to when acc != 0 (the Chebyshev representation adds the values at
+// B's nodes, x_j = c_B + r_B xbar_j, straight into B's local node values).
 template <bool MIXED, class TC>
 __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxes, const int32_t* xoff,
-                                               const int32_t* xitems, const double* q, TC* chk) {
+                                               const int32_t* xitems, const double* q, TC* chk, int ldc, int acc) {
     const int B = boxes[blockIdx.x];
     const int S = E.S;
     const double r = half_width(E, E.level[B]);
@@ -728,7 +741,7 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
     for (int j0 = 0; j0 < S; j0 += P2M_T) {
         const int j = j0 + threadIdx.x;
         double xj[3];
-        for (int k = 0; k < 3; ++k) xj[k] = kRInner * r * E.surf[3 * min(j, S - 1) + k];
+        for (int k = 0; k < 3; ++k) xj[k] = E.rf_dchk * r * E.surf[3 * min(j, S - 1) + k];
         Kahan acc32;
         double acc64 = 0;
         for (int xi = xoff[B]; xi < xoff[B + 1]; ++xi) {
@@ -763,7 +776,11 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
                 }
             }
         }
-        if (j < S) chk[(int64_t)B * S + j] = (TC)(MIXED ? acc32.value() : acc64);
+        if (j < S) {
+            TC* o = chk + (int64_t)B * ldc + j;
+            const TC v = (TC)(MIXED ? acc32.value() : acc64);
+            *o = acc ? *o + v : v;   // one block per box: no other writer of row B
+        }
     }
 }
 
@@ -798,15 +815,17 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
             int A;
             double rad;
             const TD* dens;
+            int ld = S;
             if (li == 0) {
-                if (lev < 2) continue;
+                if (lev < 2 || E.cheb) continue;   // Chebyshev: interpolation in k_l2p_cheb
                 A = B;
                 rad = kROuter * half_width(E, lev);
                 dens = phi_d;
             } else {
                 A = witems[woff[B] + li - 1];
-                rad = kRInner * half_width(E, E.level[A]);
+                rad = E.rf_ueq * half_width(E, E.level[A]);
                 dens = phi_u;
+                ld = E.ldu;
             }
             const double* cA = E.centre + 3 * (int64_t)A;
             const double d[3] = {cA[0] - cB[0], cA[1] - cB[1], cA[2] - cB[2]};
@@ -816,7 +835,7 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
                 for (int e = threadIdx.x; e < ns; e += L2P_T) {
                     const double* sv = E.surf + 3 * (s0 + e);
                     double y0 = d[0] + rad * sv[0], y1 = d[1] + rad * sv[1], y2 = d[2] + rad * sv[2];
-                    double ph = (double)dens[(int64_t)A * S + s0 + e];
+                    double ph = (double)dens[(int64_t)A * ld + s0 + e];
                     if (MIXED) s32[e] = make_float4((float)y0, (float)y1, (float)y2, (float)ph);
                     else {
                         s64[e][0] = y0; s64[e][1] = y1; s64[e][2] = y2; s64[e][3] = ph;
@@ -853,6 +872,114 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
             }
         }
         if (act) far[i] = MIXED ? acc32.value() : acc64;
+    }
+}
+
+// ------------------------------------------------------------------------------------
+// Chebyshev representation: P2M and the local part of L2P are interpolations
+// ------------------------------------------------------------------------------------
+// P2M: W_m = sum_j S3(xbar_m, (y_j - c_B) / r_B) q_j for a leaf B, written to out row B
+// (stride ldo). One block per leaf; the per-axis weights of a chunk of sources are
+// tabulated in shared memory (q_j folded into the x axis), one thread per node m.
+constexpr int CP_T = 128, CP_CH = 64;
+template <bool MIXED>
+__global__ void __launch_bounds__(CP_T) k_p2m_cheb(EvalView E, const int32_t* boxes, const double* q, double* out,
+                                                 int ldo) {
+    using F = typename std::conditional<MIXED, float, double>::type;
+    const int B = boxes[blockIdx.x];
+    const int S = E.S, p = E.cp;
+    const double r = half_width(E, E.level[B]);
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    const double* c = E.centre + 3 * (int64_t)B;
+    const F* tab = MIXED ? (const F*)E.ctab32 : (const F*)E.ctab;
+    __shared__ F w[3][CP_CH][kChebMaxP];
+    for (int j0 = 0; j0 < S; j0 += CP_T) {
+        const int j = j0 + threadIdx.x;
+        const int jj = min(j, S - 1);
+        const int mx = jj % p, my = (jj / p) % p, mz = jj / (p * p);
+        Kahan acc32;
+        double acc64 = 0;
+        for (int s0 = p0; s0 < p1; s0 += CP_CH) {
+            const int ns = min(CP_CH, p1 - s0);
+            __syncthreads();
+            for (int t = threadIdx.x; t < 3 * ns; t += CP_T) {
+                const int e = t / 3, a = t % 3;
+                F u;
+                if (MIXED) {
+                    const float4 v = E.loc[s0 + e];
+                    u = (F)((a == 0 ? v.x : a == 1 ? v.y : v.z) / (float)r);
+                } else {
+                    u = (F)((E.pts[3 * (int64_t)(s0 + e) + a] - c[a]) / r);
+                }
+                F tk[kChebMaxP];
+                cheb_T(u, p, tk);
+                const F sc = a == 0 ? (F)q[s0 + e] : F(1);
+                for (int n = 0; n < p; ++n) w[a][e][n] = sc * cheb_S(tk, p, tab + n * kChebTab);
+            }
+            __syncthreads();
+            if (MIXED) {
+                int e = 0;
+                for (; e + 7 < ns; e += 8) {   // plain FP32 sums of 8 terms, compensated across blocks
+                    float part = 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) part = fmaf((float)(w[0][e + u][mx] * w[1][e + u][my]), (float)w[2][e + u][mz], part);
+                    acc32.add(part);
+                }
+                for (; e < ns; ++e) acc32.add((float)(w[0][e][mx] * w[1][e][my] * w[2][e][mz]));
+            } else {
+                for (int e = 0; e < ns; ++e) acc64 += (double)w[0][e][mx] * (double)w[1][e][my] * (double)w[2][e][mz];
+            }
+        }
+        if (j < S) out[(int64_t)B * ldo + j] = MIXED ? acc32.value() : acc64;
+    }
+}
+
+// L2P, local part: far[i] += sum_m S3(xbar_m, (x_i - c_B) / r_B) g^B_m for every point of a
+// leaf B at level >= 2 (g row B of stride ldg), summed axis by axis (x innermost). One
+// block per leaf, one thread per target; the node values of B and each thread's per-axis
+// weights sit in shared memory.
+template <bool MIXED, class TD>
+__global__ void __launch_bounds__(L2P_T) k_l2p_cheb(EvalView E, const int32_t* leaves, const TD* g, int ldg,
+                                                  double* far) {
+    using F = typename std::conditional<MIXED, float, double>::type;
+    const int B = leaves[blockIdx.x];
+    const int lev = E.level[B];
+    if (lev < 2) return;
+    const int S = E.S, p = E.cp;
+    const double r = half_width(E, lev);
+    const double* cB = E.centre + 3 * (int64_t)B;
+    const F* tab = MIXED ? (const F*)E.ctab32 : (const F*)E.ctab;
+    __shared__ F gs[kChebMaxP * kChebMaxP * kChebMaxP];
+    __shared__ F sw[3][kChebMaxP][L2P_T];
+    for (int m = threadIdx.x; m < S; m += L2P_T) gs[m] = (F)g[(int64_t)B * ldg + m];
+    __syncthreads();
+    const int p0 = E.pstart[B], p1 = E.pend[B];
+    const int tx = threadIdx.x;
+    for (int i = p0 + tx; i < p1; i += L2P_T) {
+        for (int a = 0; a < 3; ++a) {
+            F u;
+            if (MIXED) {
+                const float4 v = E.loc[i];
+                u = (F)((a == 0 ? v.x : a == 1 ? v.y : v.z) / (float)r);
+            } else {
+                u = (F)((E.pts[3 * (int64_t)i + a] - cB[a]) / r);
+            }
+            F tk[kChebMaxP];
+            cheb_T(u, p, tk);
+            for (int n = 0; n < p; ++n) sw[a][n][tx] = cheb_S(tk, p, tab + n * kChebTab);
+        }
+        F acc = 0;
+        for (int mz = 0; mz < p; ++mz) {
+            F accy = 0;
+            for (int my = 0; my < p; ++my) {
+                const F* row = gs + (mz * p + my) * p;
+                F accx = 0;
+                for (int mx = 0; mx < p; ++mx) accx += sw[0][mx][tx] * row[mx];
+                accy += sw[1][my][tx] * accx;
+            }
+            acc += sw[2][mz][tx] * accy;
+        }
+        far[i] += (double)acc;
     }
 }
 
@@ -1113,6 +1240,13 @@ static EvalView make_view(Plan& p) {
     E.side = p.tree.side;
     E.S = p.S;
     E.kp = make_kparams(p.a, p.b);
+    E.cheb = p.cheb ? 1 : 0;
+    E.rf_dchk = p.cheb ? 1.0 : kRInner;
+    E.rf_ueq = p.cheb ? 1.0 : kRInner;
+    E.ldu = p.cheb ? p.R : p.S;
+    E.cp = p.m0;
+    E.ctab = ptr<double>(p.ctab);
+    E.ctab32 = ptr<float>(p.ctab32);
     return E;
 }
 
@@ -1194,7 +1328,12 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         const int64_t b0 = t.level_start[2], b1 = t.level_start[L - 1];
         KF_CUDA(cudaMemsetAsync(ptr<double>(p.chk) + b0 * S, 0, (size_t)(b1 - b0) * S * 8, st));
     }
-    if (p.n_p2m > 0) {
+    if (p.n_p2m > 0 && p.cheb) {   // node weights of the leaves, straight into c
+        auto* kp2m = mixed ? k_p2m_cheb<true> : k_p2m_cheb<false>;
+        kp2m<<<(unsigned)p.n_p2m, CP_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), cu, R);
+        KF_LAUNCH();
+        ++nl;
+    } else if (p.n_p2m > 0) {
         auto* kp2m = !mixed ? k_p2m<false, true> : (p.far_series ? k_p2m<true, true> : k_p2m<true, false>);
         kp2m<<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
         KF_LAUNCH();
@@ -1207,10 +1346,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
             const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms + tiles - 1) / tiles));
+            // (Chebyshev: the parents' node weights W^P = sum_o M_o W^{C_o}, straight into c)
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
-                                                 cu, R, ptr<double>(p.chk), S, 0, 8, (int64_t)S * R, nullptr, nz)));
+                                                 cu, R, p.cheb ? cu : ptr<double>(p.chk), p.cheb ? R : S, 0, 8,
+                                                 (int64_t)S * R, nullptr, nz)));
         }
+        if (p.cheb) continue;   // no pseudo-inverse
         if (LL.n_up > p.oz_min && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
             int64_t extra = 0;
             KF_TRY(pinv_oz_apply(st, ptr<double>(p.chk), S, ptr<int32_t>(LL.upb), LL.n_up, p.ops[l].ozG1.p,
@@ -1269,14 +1411,16 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     for (int l = 2; l < L; ++l) {
         auto& LL = p.lv[l];
         const LevelOps& op = p.ops[l];
-        if (LL.n_x > 0) {
+        if (LL.n_x > 0) {   // Chebyshev: the values at B's nodes add straight into d
             k_s2l_x<(sizeof(T) == 4), T><<<LL.n_x, P2M_T, 0, st>>>(E, ptr<int32_t>(LL.xboxes), ptr<int32_t>(p.lists[3].off),
                                                                   ptr<int32_t>(p.lists[3].items), ptr<double>(p.q),
-                                                                  ptr<T>(p.chkx));
+                                                                  p.cheb ? dd : ptr<T>(p.chkx), p.cheb ? R : S,
+                                                                  p.cheb ? 1 : 0);
             KF_LAUNCH();
             ++nl;
-            RUN(launch_apply<T>(st, sel<T>(op.Vt, op.Vt32), S, op.rank, S, ptr<int32_t>(LL.xboxes), ptr<int32_t>(LL.xboxes), 0,
-                                LL.n_x, ptr<T>(p.chkx), S, dd, R, 1));
+            if (!p.cheb)
+                RUN(launch_apply<T>(st, sel<T>(op.Vt, op.Vt32), S, op.rank, S, ptr<int32_t>(LL.xboxes),
+                                    ptr<int32_t>(LL.xboxes), 0, LL.n_x, ptr<T>(p.chkx), S, dd, R, 1));
         }
         if (l >= 3) {
             auto& LP = p.lv[l - 1];
@@ -1286,12 +1430,12 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                     ptr<int32_t>(LP.l2l_dst), 0, LP.l2l_max, dd, R, dd, R, 1, 1, 0,
                                     ptr<int32_t>(LP.l2l_off), 8, (int64_t)R * R));
         }
-        if (LL.n_leaf > 0)
+        if (LL.n_leaf > 0 && !p.cheb)
             RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), R, S, op.rank, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
                                 LL.n_leaf, dd, R, phid, S, 0));
     }
-    // upward equivalent densities phi^u = V c for the W list
-    if (p.phiu.p) {
+    // upward equivalent densities phi^u = V c for the W list (Chebyshev: the W list reads c)
+    if (p.phiu.p && !p.cheb) {
         for (int l = 2; l < L; ++l) {
             const LevelOps& op = p.ops[l];
             RUN(launch_apply<T>(st, sel<T>(op.Vb, op.Vb32), R, S, op.rank, nullptr, nullptr, t.level_start[l],
@@ -1341,16 +1485,30 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     if (p.nleaves > 0) {
         const int32_t* wo = ptr<int32_t>(p.lists[2].off);
         const int32_t* wi = ptr<int32_t>(p.lists[2].items);
+        // Chebyshev: the W list reads the node weights c (stride R) and the local part
+        // interpolates d in a second kernel
         if (mixed) {
             auto* kl2p = p.far_series ? k_l2p<true, true, float> : k_l2p<true, false, float>;
             kl2p<<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),
-                                                        ptr<float>(p.phiu), ptr<double>(p.far));
+                                                        p.cheb ? ptr<float>(p.cu32) : ptr<float>(p.phiu),
+                                                        ptr<double>(p.far));
         } else {
             k_l2p<false, true, double><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(
-                E, ptr<int32_t>(p.leaves), wo, wi, ptr<double>(p.phid), ptr<double>(p.phiu), ptr<double>(p.far));
+                E, ptr<int32_t>(p.leaves), wo, wi, ptr<double>(p.phid), p.cheb ? ptr<double>(p.cu) : ptr<double>(p.phiu),
+                ptr<double>(p.far));
         }
         KF_LAUNCH();
         ++nl;
+        if (p.cheb && t.nlevels > 2) {
+            if (mixed)
+                k_l2p_cheb<true, float><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<float>(p.dd),
+                                                                              p.R, ptr<double>(p.far));
+            else
+                k_l2p_cheb<false, double><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves),
+                                                                                ptr<double>(p.dd), p.R, ptr<double>(p.far));
+            KF_LAUNCH();
+            ++nl;
+        }
     }
     mark(p, 6);
     {

@@ -119,7 +119,8 @@ struct Plan {
     Csr lists[4];                 // U, V, W, X
     DevBuf vtab;                  // i32[nb * 343]: source box of V(B) at offset slot, -1 if none
     std::vector<LevelOps> ops;    // indexed by level (entries below 2 unused)
-    DevBuf surf;                  // f64[3*S] unit lattice
+    DevBuf surf;                  // f64[3*S] unit lattice (Chebyshev representation: the p^3 nodes)
+    DevBuf ctab, ctab32;          // f64 / f32 [p][10]: c_k T_k(node_n), c_0 = 1/p, c_k = 2/p (Chebyshev only)
     // per-point data in sorted order
     DevBuf pts;       // f64[3n] sorted coordinates
     DevBuf loc32;     // f32[4n] coordinates relative to the leaf centre (x, y, z, pad)
@@ -169,6 +170,7 @@ struct Plan {
     bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
+    bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents

@@ -9,6 +9,7 @@
 #include "internal.cuh"
 #include "kernel.cuh"
 #include "selfcell.cuh"
+#include "cheb.cuh"
 
 namespace kifmm {
 
@@ -216,7 +217,151 @@ static int f32_copy(cudaStream_t st, const DevBuf& src, DevBuf& dst, int64_t n) 
     return KIFMM_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Chebyshev-node representation: nodes, weight table, interpolation and M2L matrices
+// ------------------------------------------------------------------------------------
+// The p^3 tensor nodes (x fastest) and tab[n][k] = c_k T_k(xbar_n); one thread per node.
+__global__ void cheb_nodes(int p, double* s, double* tab, float* tab32) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = p * p * p;
+    if (m < p * kChebTab) {
+        const int n = m / kChebTab, k = m % kChebTab;
+        double v = 0.0;
+        if (k < p) v = (k == 0 ? 1.0 : 2.0) / p * cos(k * (2 * n + 1) * 3.14159265358979323846 / (2.0 * p));
+        tab[m] = v;
+        tab32[m] = (float)v;
+    }
+    if (m < S) {
+        const int idx[3] = {m % p, (m / p) % p, m / (p * p)};
+        for (int a = 0; a < 3; ++a) s[3 * m + a] = cos((2 * idx[a] + 1) * 3.14159265358979323846 / (2.0 * p));
+    }
+}
+
+// M2M for child octant o (parent level -> itself, level independent):
+//   M_o[n][m] = S3(xbar_n, 0.5 (2 o - 1) + 0.5 xbar_m)  (child node m in parent units)
+// stored as Mc [8][S][R] (rows parent nodes) and, for L2L, its transpose Lo [8][R][R]
+// (rows child nodes); the padding is zeroed by the caller.
+__global__ void cheb_m2m(int p, int S, int R, const double* s, const double* tab, double* Mc, double* Lo) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 8LL * S * S) return;
+    const int o = (int)(e / ((int64_t)S * S));
+    const int n = (int)((e / S) % S), m = (int)(e % S);
+    const int nidx[3] = {n % p, (n / p) % p, n / (p * p)};
+    double v = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double x = 0.5 * (2.0 * ((o >> a) & 1) - 1.0) + 0.5 * s[3 * m + a];
+        double t[kChebMaxP];
+        cheb_T(x, p, t);
+        v *= cheb_S(t, p, tab + nidx[a] * kChebTab);
+    }
+    Mc[((int64_t)o * S + n) * R + m] = v;
+    Lo[((int64_t)o * R + m) * R + n] = v;
+}
+
+// out[mat][i][j] = in[mat][i][j] for i, j < S (row stride S -> R); the padding stays zero.
+__global__ void pad_square(const double* in, int S, int R, int nmat, double* out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)nmat * S * S) return;
+    const int64_t mat = e / ((int64_t)S * S);
+    const int i = (int)((e / S) % S), j = (int)(e % S);
+    out[(mat * R + i) * R + j] = in[e];
+}
+
+// Operators of the Chebyshev representation. No pseudo-inverse: a box's values are its
+// node weights (the coefficients c, d of the surface form with rank S), so the G1, Vb, Ub,
+// Vt steps of the evaluation become the identity and are skipped there.
+//   M2L: T_{l,delta}[m][n] = K(|r xbar_m - (2 r delta + r xbar_n)|)  (B's nodes, A's nodes)
+//   M2M: Mc_{l,o} = M_o, L2L: Lo_{l,o} = M_o^T (the same at every level)
+static int build_operators_cheb(Plan& p) {
+    cudaStream_t st = p.stream;
+    const int S = p.S, pc = p.m0;
+    const int L = p.tree.nlevels;
+    const KParams kp = make_kparams(p.a, p.b);
+    KF_TRY(dev_alloc(p.surf, 3 * S * sizeof(double)));
+    KF_TRY(dev_alloc(p.ctab, kChebMaxP * kChebTab * sizeof(double)));
+    KF_TRY(dev_alloc(p.ctab32, kChebMaxP * kChebTab * sizeof(float)));
+    cheb_nodes<<<nb(std::max(S, pc * kChebTab), 128), 128, 0, st>>>(pc, ptr<double>(p.surf), ptr<double>(p.ctab),
+                                                                     ptr<float>(p.ctab32));
+    KF_LAUNCH();
+    p.ops.clear();
+    p.ops.resize(std::max(L, 1));
+    const int R = (S + 31) / 32 * 32;
+    p.R = R;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev);
+        p.num_sms = std::max(p.num_sms, 1);
+        const char* m2l = std::getenv("KIFMM_M2L");
+        p.m2l_tensor = p.precision == KIFMM_MIXED && m2l_tc_supported(R) && !(m2l && std::string(m2l) == "simt");
+    }
+    if (L <= 2) return KIFMM_OK;   // no box has a far field
+    const int64_t SS = (int64_t)S * S, RR = (int64_t)R * R;
+    DevBuf m2l, shifts, mc, lo;
+    KF_TRY(dev_alloc(m2l, kOffsetSlots * SS * 8));
+    KF_TRY(dev_alloc(shifts, kOffsetSlots * 3 * 8));
+    KF_TRY(dev_alloc(mc, 8 * (int64_t)S * R * 8));
+    KF_TRY(dev_alloc(lo, 8 * RR * 8));
+    KF_CUDA(cudaMemsetAsync(mc.p, 0, 8 * (int64_t)S * R * 8, st));
+    KF_CUDA(cudaMemsetAsync(lo.p, 0, 8 * RR * 8, st));
+    cheb_m2m<<<nb(8 * SS, 256), 256, 0, st>>>(pc, S, R, ptr<double>(p.surf), ptr<double>(p.ctab), ptr<double>(mc),
+                                              ptr<double>(lo));
+    KF_LAUNCH();
+    std::vector<double> sh(kOffsetSlots * 3);
+    for (int l = 2; l < L; ++l) {
+        LevelOps& op = p.ops[l];
+        const double r = p.tree.side / (double)(2ll << l);
+        op.level = l;
+        op.r = r;
+        op.rank = S;
+        for (int dz = -3; dz <= 3; ++dz)
+            for (int dy = -3; dy <= 3; ++dy)
+                for (int dx = -3; dx <= 3; ++dx) {
+                    const int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                    sh[3 * sl + 0] = -2.0 * r * dx;
+                    sh[3 * sl + 1] = -2.0 * r * dy;
+                    sh[3 * sl + 2] = -2.0 * r * dz;
+                }
+        KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, st));
+        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(ptr<double>(p.surf), S, r, r, ptr<double>(shifts),
+                                                                     kp, ptr<double>(m2l), SS);
+        KF_LAUNCH();
+        for (int dz = -1; dz <= 1; ++dz)   // near slots are never used: zero them
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    const int sl = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
+                    KF_CUDA(cudaMemsetAsync(ptr<double>(m2l) + sl * SS, 0, SS * 8, st));
+                }
+        KF_TRY(dev_alloc(op.T, kOffsetSlots * RR * 8));
+        KF_CUDA(cudaMemsetAsync(op.T.p, 0, kOffsetSlots * RR * 8, st));
+        pad_square<<<nb(kOffsetSlots * SS, 256), 256, 0, st>>>(ptr<double>(m2l), S, R, kOffsetSlots, ptr<double>(op.T));
+        KF_LAUNCH();
+        if (l + 1 < L) {
+            KF_TRY(dev_alloc(op.Mc, 8 * (int64_t)S * R * 8));
+            KF_TRY(dev_alloc(op.Lo, 8 * RR * 8));
+            KF_CUDA(cudaMemcpyAsync(op.Mc.p, mc.p, 8 * (int64_t)S * R * 8, cudaMemcpyDeviceToDevice, st));
+            KF_CUDA(cudaMemcpyAsync(op.Lo.p, lo.p, 8 * RR * 8, cudaMemcpyDeviceToDevice, st));
+        }
+        if (p.precision == KIFMM_MIXED) {
+            if (p.m2l_tensor) {
+                KF_TRY(dev_alloc(op.Thi, (size_t)m2l_tc_table_elems(R) * 2));
+                KF_TRY(dev_alloc(op.Tlo, (size_t)m2l_tc_table_elems(R) * 2));
+                KF_TRY(m2l_tc_prepare(st, ptr<double>(op.T), R, op.Thi.p, op.Tlo.p, &op.tc_sT));
+            } else {
+                KF_TRY(f32_copy(st, op.T, op.T32, kOffsetSlots * RR));
+            }
+            if (l + 1 < L) {
+                KF_TRY(f32_copy(st, op.Lo, op.Lo32, 8 * RR));
+                KF_TRY(f32_copy(st, op.Mc, op.Mc32, 8 * (int64_t)S * R));
+            }
+        }
+        KF_CUDA(cudaStreamSynchronize(st));   // shifts and m2l are reused by the next level
+    }
+    for (DevBuf* d : {&m2l, &shifts, &mc, &lo}) dev_free(*d);
+    return KIFMM_OK;
+}
+
 int build_operators(Plan& p) {
+    if (p.cheb) return build_operators_cheb(p);
     cudaStream_t st = p.stream;
     const int S = p.S;
     const int L = p.tree.nlevels;

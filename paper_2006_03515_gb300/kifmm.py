@@ -20,6 +20,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOU
           -5: "ERR_DUPLICATE_POINT", -6: "ERR_NONFINITE", -7: "ERR_NUMERIC"}
 PRECISION = {"fp64": KIFMM_FP64, "mixed": KIFMM_MIXED}
 SELF_MODE = {"cell_exact": KIFMM_SELF_CELL_EXACT, "paper_gl2": KIFMM_SELF_PAPER_GL2}
+REPR = {"surface": 0, "cheb": 1}
 
 # Absorption of O2 (Eq. (gfun)): chi_min, chi_max in 1/(cm Torr).
 CHI_MIN, CHI_MAX = 0.035, 2.0
@@ -43,7 +44,8 @@ class KifmmError(RuntimeError):
 
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
-                ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p)]
+                ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
+                ("repr", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -122,7 +124,7 @@ class Plan:
     """A KIFMM plan over fixed points (outline step 1 and the operators)."""
 
     def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
-                 self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None):
+                 self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface"):
         import torch
         L = load()
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
@@ -145,6 +147,7 @@ class Plan:
         o.precision = PRECISION[precision]
         o.self_mode = SELF_MODE[self_mode]
         o.pinv_eps = float(pinv_eps)
+        o.repr = REPR[repr]
         if root is not None:
             o.has_root = 1
             for k in range(4):
