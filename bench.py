@@ -71,8 +71,9 @@ def profiled_traffic(key, npts, workload_is_128_uniform):
 
 
 def workload_name(args):
-    return ("uniform %d^3 cell centres, 1 cm cube, Gaussian 1e22 exp(-r^2/0.1^2), p=%g Torr, pO2=%g, m0=%d, "
-            "leaf %d, %s" % (args.n, args.p, 0.2 * args.p, args.m0, args.leaf, args.precision))
+    rep = "m0=%d" % args.m0 if args.repr == "surface" else "Chebyshev p=%d" % args.m0
+    return ("uniform %d^3 cell centres, 1 cm cube, Gaussian 1e22 exp(-r^2/0.1^2), p=%g Torr, pO2=%g, %s, "
+            "leaf %d, %s" % (args.n, args.p, 0.2 * args.p, rep, args.leaf, args.precision))
 
 
 def measured_peaks():
@@ -95,6 +96,10 @@ def parse():
     ap.add_argument("--leaf", type=int, default=64)
     ap.add_argument("--p", type=float, default=760.0, help="gas pressure (Torr); p_O2 = 0.2 p")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--repr", default="surface", choices=["surface", "cheb"],
+                    help="far-field representation of the timed plan (cheb: --m0 is the Chebyshev order p)")
+    ap.add_argument("--no-cheb", action="store_true", help="skip the Chebyshev-representation measurement")
+    ap.add_argument("--cheb-p", type=int, default=8, help="Chebyshev order of that measurement")
     ap.add_argument("--cpu-n", type=int, default=48, help="grid of the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
@@ -216,6 +221,56 @@ def run_reference(args):
     return 0
 
 
+def cheb_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
+    """The same workload with the Chebyshev-node representation (order args.cheb_p), mixed
+    form: plan time, evaluation time (CUDA events, L2 flushed between steps), phase times,
+    the M2L rate, and the mixed result against one FP64 evaluation of the same plan."""
+    import torch
+    from paper_2006_03515_gb300 import kifmm
+    npts = dpts.shape[0]
+    t0 = time.perf_counter()
+    pl = kifmm.Plan(dpts, hval, args.leaf, args.cheb_p, a, b, precision="mixed", stream=stream, repr="cheb")
+    torch.cuda.synchronize(dev)
+    plan_s = time.perf_counter() - t0
+    S = torch.empty_like(dI)
+    for _ in range(3):
+        pl.eval(dI, S, C=C)
+    steps = max(3, min(args.steps, 10))
+    ms, phase_sum = [], None
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.eval(dI, S, C=C)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ph = pl.phase_times()
+        phase_sum = ph if phase_sum is None else [x + y for x, y in zip(phase_sum, ph)]
+    info = pl.info()
+    phases = ["scatter", "P2M", "M2M", "M2L", "X+L2L", "L2P+W", "P2P"]
+    ph_ms = {k: v / steps for k, v in zip(phases, phase_sum)}
+    m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
+    out = {"p": args.cheb_p, "nodes": info["surface_points"], "precision": "mixed", "plan_s": plan_s,
+           "ms": sum(ms) / len(ms), "points_per_s": npts / (1e-3 * sum(ms) / len(ms)), "phase_ms": ph_ms,
+           "m2l": {"path": "tcgen05 FP16x3" if info["m2l_tensor"] else "SIMT FP32", "tflops": m2l_ach,
+                   "flops": info["m2l_flops"]}}
+    if not args.no_fp64:
+        p64 = kifmm.Plan(dpts, hval, args.leaf, args.cheb_p, a, b, precision="fp64", stream=stream, repr="cheb")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S64 = p64.eval(dI, C=C)
+        e1.record(stream)
+        e1.synchronize()
+        out["fp64_ms"] = e0.elapsed_time(e1)
+        out["gate_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(S - S64) / torch.linalg.norm(S64))
+        p64.close()
+        del S64
+    pl.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def surrogate_bench(args, dev, stream, peaks):
     """The learned surrogate on an n^3 grid (width 32, 12 modes, 4 layers, projection 64):
     KIFMM-labelled data generation, training for a fixed time budget, batched inference
@@ -329,14 +384,16 @@ def main():
         dI = torch.as_tensor(I, device=dev)
         S = torch.empty_like(dI)
         t0 = time.perf_counter()
-        plan = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision=args.precision, stream=stream)
+        plan = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision=args.precision, stream=stream,
+                          repr=args.repr)
         torch.cuda.synchronize(dev)
         plan_s = time.perf_counter() - t0
         info = plan.info()
         gate = None
         fp64 = None
         if not args.no_fp64 and args.precision == "mixed":
-            p64 = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision="fp64", stream=stream)
+            p64 = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision="fp64", stream=stream,
+                             repr=args.repr)
             S64 = p64.eval(dI, C=C)
             plan.eval(dI, S, C=C)
             torch.cuda.synchronize(dev)
@@ -415,7 +472,8 @@ def main():
     if clk.get("sm_mhz"):
         sm_clk = float(clk["sm_mhz"])
     p2p_peak = SM_COUNT * PAIRS_PER_SM_CLK * sm_clk * 1e6 / 1e9
-    std = args.n == 128 and args.m0 == 6 and args.leaf == 64 and args.p == 760.0 and args.precision == "mixed"
+    std = (args.n == 128 and args.m0 == 6 and args.leaf == 64 and args.p == 760.0 and args.precision == "mixed"
+           and args.repr == "surface")
     f16_peak = peaks.get("bf16_tflops", 1947.8)   # dense FP16 and BF16 share the tensor rate
     m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
     up_ach = info["upward_flops"] / (ph_ms["M2M+UC2UE"] * 1e-3) / 1e12
@@ -442,6 +500,13 @@ def main():
                     "achieved": up_ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": up_ach / FP64_TFLOPS,
                     "traffic": None, "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}),
     }
+    if not info["m2l_tensor"]:   # SIMT M2L (FP64 form, or a coefficient count the tensor path does not take)
+        fp_peak = (SM_COUNT * 128 * 2 * sm_clk * 1e6 / 1e12 if args.precision == "mixed" else FP64_TFLOPS)
+        roofs["M2L"] = {"kernel": "k_m2l (SIMT, %s)" % ("FP32" if args.precision == "mixed" else "FP64"),
+                        "bound": "alu", "achieved": m2l_ach, "peak": fp_peak, "unit": "TFLOP/s",
+                        "frac": m2l_ach / fp_peak, "traffic": None,
+                        "peak_source": ("152 SMs x 128 FP32 FMA lanes x 2 x median SM clock under load"
+                                        if args.precision == "mixed" else "GB300 FP64 nominal 1.25 TFLOP/s")}
     key = "P2P" if dom == "P2P" else ("M2L" if dom == "M2L" else "upward")
     roof = dict(roofs[key])
     gpu_launches = launches_per_step * args.steps
@@ -456,6 +521,12 @@ def main():
             "phase_ms": ph_ms, "roofline": roof, "rooflines": roofs, "clocks": clk, "gpu_launches": gpu_launches,
             "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": npts * 8,
                     "d2h_bytes_per_step": npts * 8, "matches_device_result": e2e_ok}}
+    if not args.no_cheb and args.repr == "surface":
+        try:
+            with torch.cuda.stream(stream):
+                line["cheb"] = cheb_bench(args, dev, stream, dpts, float(h[0]), dI, C, a, b, flush, peaks)
+        except Exception as exc:    # the headline line is printed whatever happens here
+            line["cheb"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if not args.no_surrogate:
         try:
             with torch.cuda.stream(stream):

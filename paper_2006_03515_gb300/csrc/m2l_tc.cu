@@ -9,9 +9,10 @@
 //   d[B] = sum over the offset slots of V(B):  T[slot] c[A(B, slot)],
 // with T[slot] (R x R) shared by every pair with that relative offset. One CTA takes a
 // tile of 128 target boxes of a level (boxes grouped by their octant inside the parent,
-// so that the tile's boxes share one set of about 189 offsets) and, per offset slot and
-// 64-wide k-chunk, multiplies the gathered source rows c[A] (A operand, 128 x 64) by the
-// chunk of T[slot] (B operand, R x 64), both K-major in the 128-byte swizzled layout.
+// so that the tile's boxes share one set of about 189 offsets) and a block of NT <= 256
+// output rows (one block when R <= 256), and, per offset slot and 64-wide k-chunk,
+// multiplies the gathered source rows c[A] (A operand, 128 x 64) by the chunk's rows of
+// T[slot] (B operand, NT x 64), both K-major in the 128-byte swizzled layout.
 //
 // Roles (warp specialization, 11 warps):
 //  * warps 8-9, producers: per iteration each thread gathers two source rows with
@@ -100,16 +101,20 @@ __global__ void k_split_c(const double* c, int64_t nb, int R, __half* chi, __hal
 // ------------------------------------------------------------------------------------
 // the kernel
 // ------------------------------------------------------------------------------------
-template <int NC, int NS>
+// R = NB NT coefficients per box; each CTA computes the NT = 32 NC output rows
+// n0 = blockIdx.y NT .. of its tile (NB > 1 where R exceeds the MMA's N of 256).
+template <int NC, int NS, int NB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(M2LTables tabs, const int4* __restrict__ tiles, const int32_t* __restrict__ all_boxes,
              const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const __half* __restrict__ chi,
              const __half* __restrict__ clo, const int* __restrict__ cexp, float* __restrict__ d, int* err) {
-    constexpr int R = 32 * NC;
+    constexpr int NT = 32 * NC;
+    constexpr int R = NB * NT;
     constexpr int NK = (R + TC_KH - 1) / TC_KH;
-    constexpr int A_BYTES = TC_M * 128, B_BYTES = R * 128;
+    const int n0 = blockIdx.y * NT;
+    constexpr int A_BYTES = TC_M * 128, B_BYTES = NT * 128;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    constexpr int ACC = R <= 32 ? 32 : (R <= 64 ? 64 : (R <= 128 ? 128 : 256));
+    constexpr int ACC = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
     constexpr uint32_t NCOLS = 2 * ACC;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full[NS], empty[NS], ready[2], freed[2];
@@ -179,11 +184,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const int k0 = kc * TC_KH;
             const int kvalid = min(TC_KH, R - k0);
             unsigned char* st = base + s * STAGE;
-            if (p == 0) {   // B: two pre-swizzled bulk copies (hi, lo) of R x 128 bytes
+            if (p == 0) {   // B: two pre-swizzled bulk copies (hi, lo) of rows n0 .. n0 + NT - 1, 128 bytes each
                 const uint32_t fb = smem_u32(&full[s]);
                 asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * B_BYTES)
                              : "memory");
-                const int64_t off = ((int64_t)slot * NK + kc) * R * TC_KH;
+                const int64_t off = (((int64_t)slot * NK + kc) * R + n0) * TC_KH;
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                         smem_u32(st + 2 * A_BYTES)),
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     } else if (warp == 10) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
-            const uint32_t idesc = f16_idesc(TC_M, R);
+            const uint32_t idesc = f16_idesc(TC_M, NT);
             uint32_t fphase[NS] = {};
             for (int si = 0; si < ns && !abort_flag; ++si) {
                 const int j = si & 1;
@@ -256,10 +261,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // ---------------- epilogue: warps 0-7 ----------------
         const int q = warp & 3, half = warp >> 2;
         const uint32_t t_row = (uint32_t)(32 * q) << 16;
-        const int col0 = half * (R / 2);
-        float acc[R / 2];
+        const int col0 = half * (NT / 2);
+        float acc[NT / 2];
 #pragma unroll
-        for (int k = 0; k < R / 2; ++k) acc[k] = 0.f;
+        for (int k = 0; k < NT / 2; ++k) acc[k] = 0.f;
         // this row's box and the scale 2^{-(e_A + e_T)} of its source at each slot (one slot ahead)
         const int brow = t0 + 32 * q + lane;
         const int bbox = brow < nbox ? boxes[brow] : -1;
@@ -277,7 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (__any_sync(0xffffffffu, !ok)) break;   // warp-uniform exit (tcgen05.ld is .sync.aligned)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-            for (int cc = 0; cc < R / 2; cc += 16) {
+            for (int cc = 0; cc < NT / 2; cc += 16) {
                 uint32_t v[16];
                 const uint32_t ta = tmem + t_row + (uint32_t)(j * ACC + col0 + cc);
                 asm volatile(
@@ -296,9 +301,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         }
         const int bi = t0 + 32 * q + lane;
         if (!abort_flag && bi < nbox) {
-            float4* o = reinterpret_cast<float4*>(d + (int64_t)boxes[bi] * R + col0);
+            float4* o = reinterpret_cast<float4*>(d + (int64_t)boxes[bi] * R + n0 + col0);
 #pragma unroll
-            for (int k = 0; k < R / 8; ++k) o[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+            for (int k = 0; k < NT / 8; ++k) o[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -322,7 +327,17 @@ size_t m2l_tc_smem(int R) {
     return 1024 + (size_t)stages_for(R) * stage;
 }
 
-int m2l_tc_supported(int R) { return (R % 32 == 0 && R >= 32 && R <= 256 && stages_for(R) >= 2) ? 1 : 0; }
+// row blocks per tile: the MMA's N is at most 256
+static int row_blocks(int R) { return (R + 255) / 256; }
+
+// coefficient counts with a compiled kernel: R <= 256 in one row block, and the Chebyshev
+// counts 384, 512, 768, 1024 in blocks of 192 or 256 rows
+int m2l_tc_supported(int R) {
+    if (R % 32 != 0 || R < 32) return 0;
+    if (R > 256 && R != 384 && R != 512 && R != 768 && R != 1024) return 0;
+    const int nb = row_blocks(R);
+    return (R % (32 * nb) == 0 && stages_for(R / nb) >= 2) ? 1 : 0;
+}
 
 int64_t m2l_tc_table_elems(int R) { return (int64_t)kOffsetSlots * ((R + TC_KH - 1) / TC_KH) * R * TC_KH; }
 
@@ -358,31 +373,31 @@ int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi,
     return KIFMM_OK;
 }
 
-template <int NC, int NS>
+template <int NC, int NS, int NB>
 static int launch_cfg(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
                       const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
                       float* d, int* err) {
     const size_t smem = m2l_tc_smem(32 * NC);
     static bool configured = false;   // one attribute per instantiation (its size never changes)
     if (!configured) {
-        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    k_m2l_tc<NC, NS><<<ntiles, TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots,
+    k_m2l_tc<NC, NS, NB><<<dim3(ntiles, NB), TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots,
                                                         reinterpret_cast<const __half*>(chi),
                                                         reinterpret_cast<const __half*>(clo), cexp, d, err);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
-template <int NC>
+template <int NC, int NB>
 static int launch_nc(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
                      const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
                      float* d, int* err) {
     switch (stages_for(32 * NC)) {
-        case 2: return launch_cfg<NC, 2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 3: return launch_cfg<NC, 3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        default: return launch_cfg<NC, 4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 2: return launch_cfg<NC, 2, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 3: return launch_cfg<NC, 3, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        default: return launch_cfg<NC, 4, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
     }
 }
 
@@ -390,17 +405,23 @@ int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* til
                   const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
                   int* err) {
     if (ntiles <= 0) return KIFMM_OK;
-    switch (R / 32) {
-        case 1: return launch_nc<1>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 2: return launch_nc<2>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 3: return launch_nc<3>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 4: return launch_nc<4>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 5: return launch_nc<5>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 6: return launch_nc<6>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 7: return launch_nc<7>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 8: return launch_nc<8>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+#define KF_M2L_TC(NC, NB) return launch_nc<NC, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err)
+    switch (m2l_tc_supported(R) ? R : 0) {
+        case 32: KF_M2L_TC(1, 1);
+        case 64: KF_M2L_TC(2, 1);
+        case 96: KF_M2L_TC(3, 1);
+        case 128: KF_M2L_TC(4, 1);
+        case 160: KF_M2L_TC(5, 1);
+        case 192: KF_M2L_TC(6, 1);
+        case 224: KF_M2L_TC(7, 1);
+        case 256: KF_M2L_TC(8, 1);
+        case 384: KF_M2L_TC(6, 2);    // Chebyshev p = 7
+        case 512: KF_M2L_TC(8, 2);    // p = 8
+        case 768: KF_M2L_TC(8, 3);    // p = 9
+        case 1024: KF_M2L_TC(8, 4);   // p = 10
         default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
     }
+#undef KF_M2L_TC
 }
 
 }  // namespace kifmm

@@ -1,6 +1,8 @@
 // Plan, part 2: equivalent/check surfaces, the per-level translation matrices
 // (Eqs. (s2m), (m2m), (m2l), (l2l), (s2l) of the paper), their truncated-SVD
 // pseudo-inverses, and the self-cell values of the discrete kernel G (Sec. 3).
+// For the Chebyshev-node representation: the nodes, interpolation and node-to-node M2L
+// matrices instead of surfaces and pseudo-inverses.
 #include <algorithm>
 #include <cstdlib>
 #include <string>
@@ -285,7 +287,10 @@ static int build_operators_cheb(Plan& p) {
     KF_LAUNCH();
     p.ops.clear();
     p.ops.resize(std::max(L, 1));
-    const int R = (S + 31) / 32 * 32;
+    // R: S rounded up so that the tensor-core M2L's row blocks (at most 256 rows) are whole
+    // multiples of 32
+    const int nblk = (S + 255) / 256;
+    const int R = (S + 32 * nblk - 1) / (32 * nblk) * (32 * nblk);
     p.R = R;
     {
         int dev = 0;
