@@ -40,17 +40,17 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, valid while the kernel's
 # source is the one that was captured (else the roofline's traffic is null). The 96^3 capture has
-# the far-field structure of the 128^3 workload (same M2L launch); the pair kernel's traffic is
-# compulsory and scales with the point count (x (128/96)^3 for 128^3).
+# the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
+# shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 296.78e6 + 16.40e6, "per_point_scaled": False,
+    "M2L": {"bytes": 300.30e6 + 16.05e6, "per_point_scaled": False,
             "src": "paper_2006_03515_gb300/csrc/m2l_tc.cu",
-            "sha256": "8583d28f6c6c042b56c73eaf85fe443c0af55a0d99ace9797d8d9fb1134c7b58",
+            "sha256": "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb",
             "profile": "profiles/k_m2l_tc_uniform96.md"},
-    "P2P": {"bytes": 50.66e6 + 1.27e6, "per_point_scaled": True, "n_profiled": 96 ** 3,
+    "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
             "src": "paper_2006_03515_gb300/csrc/eval.cu",
-            "sha256": "96bdcd941c49677257cc4cd008606df417528f57461dda96f3db1bd023bf3316",
-            "profile": "profiles/k_p2p_mixed_uniform96.md"},
+            "sha256": "c7914a2182442cee84b7828a60a1144a3b79ad05c15fd664140143cf8d566076",
+            "profile": "profiles/k_p2p_mixed_uniform64.md"},
 }
 
 
