@@ -500,6 +500,15 @@ def main():
                     "achieved": up_ach, "peak": FP64_TFLOPS, "unit": "TFLOP/s", "frac": up_ach / FP64_TFLOPS,
                     "traffic": None, "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}),
     }
+    if info.get("near_tensor"):   # uniform lattice: near field as 27 per-offset matrices on the tensor cores
+        nf_ach = 2.0 * info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3) / 1e12
+        roofs["P2P"] = {"kernel": "k_m2l_tc on the 27 near-offset kernel matrices (R = 64 cells per leaf; the phase "
+                                  "also holds the weight split and the output combination)",
+                        "bound": "tensor", "achieved": nf_ach, "peak": f16_peak / 3.0, "unit": "TFLOP/s",
+                        "frac": nf_ach / (f16_peak / 3.0), "traffic": None,
+                        "pairs_per_s": info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3),
+                        "peak_source": "of measured: bf16_tflops (dense FP16 = BF16 rate) / 3 MMAs per product; "
+                                       "achieved = 2 flop per near pair over the whole near-field phase"}
     if not info["m2l_tensor"]:   # SIMT M2L (FP64 form, or a coefficient count the tensor path does not take)
         fp_peak = (SM_COUNT * 128 * 2 * sm_clk * 1e6 / 1e12 if args.precision == "mixed" else FP64_TFLOPS)
         roofs["M2L"] = {"kernel": "k_m2l (SIMT, %s)" % ("FP32" if args.precision == "mixed" else "FP64"),

@@ -178,6 +178,8 @@ typedef struct {
     double m2l_flops;           /* algorithmic M2L flop of one kifmm_eval: 2 r_l^2 per V pair */
     double upward_flops;        /* upward pseudo-inverse work (FP64-equivalent): 2 r_l S per leaf and parent */
     double upward_mma_flops;    /* FP16 tensor-core flop executed for it by the exact slice products (0 on the FP64 pipe) */
+    int64_t near_tensor;        /* 1 if the near field runs on the tensor cores: mixed form, points on a uniform
+                                 * lattice with full leaves of one level (per-offset kernel matrices) */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */

@@ -39,7 +39,8 @@ static void free_plan(Plan* p) {
     for (DevBuf* b : {&p->surf, &p->ctab, &p->ctab32, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
-                      &p->tc_tiles, &p->tc_boxes, &p->tc_slots})
+                      &p->tc_tiles, &p->tc_boxes, &p->tc_slots, &p->nf_utab, &p->nf_Thi, &p->nf_Tlo, &p->nf_tiles,
+                      &p->nf_slots, &p->nf_boxes, &p->nf_qhi, &p->nf_qlo, &p->nf_qexp, &p->nf_near})
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
@@ -179,6 +180,7 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     rc = dev_alloc(p->err, 16);
     if (rc) return fail(rc);
     if (cudaMemsetAsync(p->err.p, 0, 16, p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    p->uniform_h = cell_h ? 0.0 : uniform_h;
     rc = build_eval_data(*p);
     if (rc) return fail(rc);
     rc = dev_alloc(p->host_I, n * 8);
@@ -377,6 +379,7 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     info->pinv_rank_min = rmin;
     info->eval_launches = p.eval_launches;
     info->m2l_tensor = p.m2l_tensor ? 1 : 0;
+    info->near_tensor = p.near_tc ? 1 : 0;
     info->m2l_flops = p.m2l_flops;
     {
         double up = 0;

@@ -73,7 +73,6 @@ __global__ void m2m_fill(const int32_t* child, const int32_t* flag, const int32_
     dst[pos[k]] = (int32_t)b;
 }
 
-constexpr int kSlotStride = 344;   // per M2L tile: [count, slot_0, slot_1, ...]
 
 // active offset slots of a tile of boxes (union of their V lists): boxes lo + tile*tb + k,
 // or list[tile*tb + k] when a box list is given (k < tb, within the level's hi - lo boxes)
@@ -393,6 +392,7 @@ int build_eval_data(Plan& p) {
     KF_CUDA(cudaStreamSynchronize(st));
     dev_free(flag); dev_free(pos); dev_free(scan_tmp);
     if (p.precision == KIFMM_MIXED) KF_TRY(p2p_series_check(p));
+    KF_TRY(near_tc_plan(p));
     // FP64-exact upward solves on the tensor cores (mixed form; KIFMM_UPWARD=fp64 keeps the FP64 pipe)
     {
         const char* up = std::getenv("KIFMM_UPWARD");
@@ -1511,7 +1511,9 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         }
     }
     mark(p, 6);
-    {
+    if (mixed && p.near_tc) {   // uniform lattice: near field as per-offset contractions on the tensor cores
+        KF_TRY(near_tc_eval(p, ptr<double>(p.far), C, S_out, dtype, nl));
+    } else {
         size_t smem = (size_t)(mixed ? P2Q_CHUNK : P2P_CHUNK) * 16;
         const int32_t* uo = ptr<int32_t>(p.lists[0].off);
         const int32_t* ui = ptr<int32_t>(p.lists[0].items);

@@ -12,6 +12,7 @@ namespace kifmm {
 constexpr int kKeyBits = 21;
 constexpr int kMaxLevel = 20;
 constexpr int kOffsetSlots = 343;   // (dx, dy, dz) in [-3, 3]^3
+constexpr int kSlotStride = 344;    // per tensor-core translation tile: [count, slot_0, slot_1, ...]
 constexpr double kRInner = 1.2;     // upward equivalent / downward check surface (box half-widths)
 constexpr double kROuter = 2.6;     // upward check / downward equivalent surface
 // Upward solves of levels with at most kOzMinBoxes boxes take the FP64-pipe GEMM with its K
@@ -171,6 +172,11 @@ struct Plan {
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
+    double uniform_h = 0;        // cell edge of a uniform-h plan (0: per-point h)
+    // near field on the tensor cores (mixed form, uniform lattice; near_tc.cu)
+    bool near_tc = false;
+    int nf_R = 0, nf_level = 0, nf_sT = 0, nf_ntiles = 0;
+    DevBuf nf_utab, nf_Thi, nf_Tlo, nf_tiles, nf_slots, nf_boxes, nf_qhi, nf_qlo, nf_qexp, nf_near;
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
@@ -217,6 +223,9 @@ struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the te
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
                   int* err);
+// near_tc.cu: near field on a uniform lattice
+int near_tc_plan(Plan& p);
+int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
 // pinv_oz.cu: FP64-exact c = Sigma^+ U^T chk on the tensor cores
 int pinv_oz_supported(int S);
 size_t pinv_oz_op_bytes(int S, int rank);

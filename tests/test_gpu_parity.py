@@ -9,7 +9,9 @@ Bars:
   agree to ~1e5 * 2.2e-16 = 2e-11 relative, and the tolerance leaves a factor 5;
 * mixed precision vs FP64 KIFMM: rel-L2 <= 1e-6 (the stated target of the method's
   mixed form: FP32 P2P / check and target evaluations, FP32-accumulated M2L, FP64
-  pseudo-inverse applications and L2L chain);
+  pseudo-inverse applications and L2L chain); on a uniform lattice of full leaves the near
+  field runs as per-offset kernel matrices on the tensor cores (FP16 x 3, FP32-accurate),
+  held to the same 1e-6 against the FP64 form and against the mixed pair kernel;
 * direct-sum parity of the FMM: the paper's own method error (E_V of 0.15-0.7 %
   at m0 = 6), asserted at < 1e-2 where the oracle FMM reaches it.
 """
@@ -160,6 +162,39 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
     scale[scale == 0] = 1.0
     assert np.max(np.abs(c_tc - c_64) / scale) <= 1e-12
     assert _relerr(s_tc, s_64) <= 1e-9
+
+
+@pytest.mark.parametrize("n,leaf", [(32, 64), (16, 512)])
+def test_near_field_on_tensor_cores(kf, monkeypatch, n, leaf):
+    # uniform lattice with full leaves (64 or 512 cells): the near field runs as 27 per-offset
+    # kernel matrices on the tensor cores; against the FP64 form and the mixed pair kernel
+    pts, h, I = W.config_uniform(n)
+    a, b = K.absorption_coefficients(152.0)
+    Id = _dev(I)
+    s64 = _plan(kf, pts, h, leaf, 6, a, b).eval(Id).cpu().numpy()
+    ptc = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
+    assert ptc.info()["near_tensor"]
+    stc = ptc.eval(Id).cpu().numpy()
+    monkeypatch.setenv("KIFMM_P2P", "generic")
+    pgen = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
+    assert not pgen.info()["near_tensor"]
+    sgen = pgen.eval(Id).cpu().numpy()
+    assert _relerr(stc, s64) <= 1e-6
+    assert _relerr(stc, sgen) <= 1e-6
+
+
+def test_near_field_lattice_detection(kf):
+    # not a lattice of full leaves: the pair kernel (8-cell leaves, a random cloud, the
+    # refined grid, per-point h)
+    a, b = 5.32, 304.0
+    pts, h, _ = W.config_uniform(16)
+    assert not _plan(kf, pts, h, 8, 6, a, b, precision="mixed").info()["near_tensor"]
+    pts, h = W.random_cloud(3000, 11)[:2]
+    assert not _plan(kf, pts, h, 64, 6, a, b, precision="mixed").info()["near_tensor"]
+    pts, h = _adaptive_small()
+    assert not _plan(kf, pts, h, 64, 6, a, b, precision="mixed", uniform=False).info()["near_tensor"]
+    pts, h, _ = W.config_uniform(32)
+    assert not _plan(kf, pts, h, 64, 6, a, b).info()["near_tensor"]   # FP64 form
 
 
 def test_mixed_adaptive_matches_fp64(kf):
