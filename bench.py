@@ -39,18 +39,24 @@ FP64_TFLOPS = 1.25      # GB300 FP64 (nominal; FMA chains measured 1.01, the FP6
 METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, valid while the kernel's
-# source is the one that was captured (else the roofline's traffic is null). The 96^3 capture has
+# sources are the ones that were captured (else the roofline's traffic is null). The 96^3 capture has
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
     "M2L": {"bytes": 300.30e6 + 16.05e6, "per_point_scaled": False,
-            "src": "paper_2006_03515_gb300/csrc/m2l_tc.cu",
-            "sha256": "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb",
+            "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
+                    "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
     "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
-            "src": "paper_2006_03515_gb300/csrc/eval.cu",
-            "sha256": "c7914a2182442cee84b7828a60a1144a3b79ad05c15fd664140143cf8d566076",
+            "src": {"paper_2006_03515_gb300/csrc/eval.cu":
+                    "7c96206c5ec6d23b9d7c5f19f7313d74b0847328b6c0ae8b2a05b23534fcb021"},
             "profile": "profiles/k_p2p_mixed_uniform64.md"},
+    "NEAR": {"bytes": 3.96e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
+             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
+                     "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb",
+                     "paper_2006_03515_gb300/csrc/near_tc.cu":
+                     "22103b78ca0b81fee7a906a94308437cee97341e2395af678e22bca6a691e193"},
+             "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
 
@@ -62,9 +68,10 @@ def profiled_traffic(key, npts, workload_is_128_uniform):
     if e is None or not workload_is_128_uniform:
         return None
     try:
-        with open(os.path.join(ROOT, e["src"]), "rb") as f:
-            if hashlib.sha256(f.read()).hexdigest() != e["sha256"]:
-                return None
+        for src, sha in e["src"].items():
+            with open(os.path.join(ROOT, src), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != sha:
+                    return None
     except OSError:
         return None
     return e["bytes"] * (npts / e["n_profiled"] if e["per_point_scaled"] else 1.0)
@@ -505,7 +512,7 @@ def main():
         roofs["P2P"] = {"kernel": "k_m2l_tc on the 27 near-offset kernel matrices (R = 64 cells per leaf; the phase "
                                   "also holds the weight split and the output combination)",
                         "bound": "tensor", "achieved": nf_ach, "peak": f16_peak / 3.0, "unit": "TFLOP/s",
-                        "frac": nf_ach / (f16_peak / 3.0), "traffic": None,
+                        "frac": nf_ach / (f16_peak / 3.0), "traffic": profiled_traffic("NEAR", npts, std),
                         "pairs_per_s": info["p2p_pairs"] / (ph_ms["P2P"] * 1e-3),
                         "peak_source": "of measured: bf16_tflops (dense FP16 = BF16 rate) / 3 MMAs per product; "
                                        "achieved = 2 flop per near pair over the whole near-field phase"}
