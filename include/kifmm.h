@@ -180,6 +180,8 @@ typedef struct {
     double upward_mma_flops;    /* FP16 tensor-core flop executed for it by the exact slice products (0 on the FP64 pipe) */
     int64_t near_tensor;        /* 1 if the near field runs on the tensor cores: mixed form, points on a uniform
                                  * lattice with full leaves of one level (per-offset kernel matrices) */
+    int64_t lattice_far;        /* 1 if, on such a lattice (surface form, no W / X lists), S2M and the local
+                                 * part of L2P apply one tabulated check-surface matrix to every leaf */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */

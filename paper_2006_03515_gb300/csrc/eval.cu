@@ -454,17 +454,6 @@ __global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, in
     q[k] = v * w[k];
 }
 
-// Kahan-compensated FP32 accumulator
-struct Kahan {
-    float s = 0.f, c = 0.f;
-    __device__ __forceinline__ void add(float v) {
-        float y = v - c;
-        float t = s + y;
-        c = (t - s) - y;
-        s = t;
-    }
-    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
-};
 
 // S2M (Eq. (s2m), first step): upward check potential of a leaf from its own sources.
 // One block per leaf; check points x_j = c_B + 2.6 r s_j, sources relative to c_B.
@@ -1333,6 +1322,9 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         kp2m<<<(unsigned)p.n_p2m, CP_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), cu, R);
         KF_LAUNCH();
         ++nl;
+    } else if (p.n_p2m > 0 && p.lat_far) {   // uniform lattice: one check matrix for every leaf
+        KF_TRY(lat_s2m(p));
+        ++nl;
     } else if (p.n_p2m > 0) {
         auto* kp2m = !mixed ? k_p2m<false, true> : (p.far_series ? k_p2m<true, true> : k_p2m<true, false>);
         kp2m<<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
@@ -1487,7 +1479,9 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         const int32_t* wi = ptr<int32_t>(p.lists[2].items);
         // Chebyshev: the W list reads the node weights c (stride R) and the local part
         // interpolates d in a second kernel
-        if (mixed) {
+        if (p.lat_far && t.nlevels > 2) {   // uniform lattice, no W list: the local expansion is one matrix
+            KF_TRY(lat_l2p(p));
+        } else if (mixed) {
             auto* kl2p = p.far_series ? k_l2p<true, true, float> : k_l2p<true, false, float>;
             kl2p<<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),
                                                         p.cheb ? ptr<float>(p.cu32) : ptr<float>(p.phiu),

@@ -177,6 +177,8 @@ struct Plan {
     bool near_tc = false;
     int nf_R = 0, nf_level = 0, nf_sT = 0, nf_ntiles = 0;
     DevBuf nf_utab, nf_Thi, nf_Tlo, nf_tiles, nf_slots, nf_boxes, nf_qhi, nf_qlo, nf_qexp, nf_near;
+    bool lat_far = false;        // S2M and local L2P on the same lattice (surface form, no W / X lists)
+    DevBuf lat_P;                // f32 [S][npl + 1]: K between the leaf's check surface and its cells
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
@@ -226,6 +228,8 @@ int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* til
 // near_tc.cu: near field on a uniform lattice
 int near_tc_plan(Plan& p);
 int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
+int lat_s2m(Plan& p);   // chk of every leaf (lat_far plans)
+int lat_l2p(Plan& p);   // far of every point from phi_d (lat_far plans)
 // pinv_oz.cu: FP64-exact c = Sigma^+ U^T chk on the tensor cores
 int pinv_oz_supported(int S);
 size_t pinv_oz_op_bytes(int S, int rank);

@@ -83,4 +83,16 @@ __device__ __forceinline__ float exp_diff_f32(float R, const KParams& k) {
     return ex2_approx(-k.a_l2e * R) - ex2_approx(-k.b_l2e * R);
 }
 
+// Kahan-compensated FP32 accumulator
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 }  // namespace kifmm

@@ -99,6 +99,152 @@ __global__ void k_nf_finish(const float* near, const double* far, const double* 
     out[perm[i]] = (TO)(C * ((double)near[i] + far[i] + sigma[i] * Is[i]));
 }
 
+// ------------------------------------------------------------------------------------
+// S2M and the local part of L2P on the same lattice: every leaf sees the same matrix
+//   P[j][i] = K(|2.6 r s_j - y_i|),  y_i = (c_i + 1/2) h - r  (leaf-centred coordinates),
+// between its check / downward equivalent surface (radius 2.6 r) and its own cells, so
+//   chk[B][j] = sum_i P[j][i] q[B][i]   and   far[B][i] = sum_j P[j][i] phi_d[B][j].
+// FP64 kernel values rounded once to FP32; sums in FP32 blocks of 8 terms, compensated
+// across blocks (as the kernels that evaluate the kernel do).
+// ------------------------------------------------------------------------------------
+__global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int nc, double r, double h, KParams kp,
+                            float* P) {
+    const int npl = nc * nc * nc;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * npl) return;
+    const int j = (int)(e / npl), i = (int)(e % npl);
+    const int ci = ref[i];
+    const int c3[3] = {ci % nc, (ci / nc) % nc, ci / (nc * nc)};
+    double d2 = 0;
+    for (int k = 0; k < 3; ++k) {
+        const double d = kROuter * r * surf[3 * j + k] - ((c3[k] + 0.5) * h - r);
+        d2 += d * d;
+    }
+    P[(int64_t)j * (npl + 1) + i] = (float)kern_f64(sqrt(d2), kp);
+}
+
+constexpr int LT_T = 128, LT_LV = 8;   // threads; leaves per pass of the S2M kernel
+constexpr int LT_LT = 4;               // leaves per thread and pass of the L2P kernel
+
+// the matrix into shared memory: 16-byte loads, several in flight per thread (n4 float4)
+__device__ __forceinline__ void lat_load(const float* __restrict__ P, float* Ps, int n4) {
+    const float4* src = reinterpret_cast<const float4*>(P);
+    float4* dst = reinterpret_cast<float4*>(Ps);
+    int e = threadIdx.x;
+    for (; e + 3 * LT_T < n4; e += 4 * LT_T) {
+        const float4 a = src[e], b = src[e + LT_T], c = src[e + 2 * LT_T], d = src[e + 3 * LT_T];
+        dst[e] = a;
+        dst[e + LT_T] = b;
+        dst[e + 2 * LT_T] = c;
+        dst[e + 3 * LT_T] = d;
+    }
+    for (; e < n4; e += LT_T) dst[e] = src[e];
+}
+
+// chk[leaf B][j] = sum_i P[j][i] q[B][i]; rows j over the threads (P rows padded to npl + 1
+// floats: conflict-free), LT_LV leaves per pass sharing each P load
+__global__ void __launch_bounds__(LT_T) k_lat_s2m(const float* __restrict__ P, int S, int npl,
+                                                  const int32_t* __restrict__ leaves, int64_t nl,
+                                                  const double* __restrict__ q, double* __restrict__ chk) {
+    extern __shared__ float lsm[];
+    float* Ps = lsm;                          // [S][npl + 1]
+    float* qs = Ps + (int64_t)S * (npl + 1);   // [LT_LV][npl]
+    lat_load(P, Ps, S * (npl + 1) / 4);
+    for (int64_t o0 = (int64_t)blockIdx.x * LT_LV; o0 < nl; o0 += (int64_t)gridDim.x * LT_LV) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < LT_LV * npl; e += LT_T) {
+            const int64_t o = o0 + e / npl;
+            qs[e] = o < nl ? (float)q[o * npl + e % npl] : 0.f;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < S; j += LT_T) {
+            const float* row = Ps + (int64_t)j * (npl + 1);
+            Kahan k[LT_LV];
+            for (int i0 = 0; i0 < npl; i0 += 8) {
+                float part[LT_LV] = {};
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float w = row[i0 + u];
+#pragma unroll
+                    for (int l = 0; l < LT_LV; ++l) part[l] = fmaf(w, qs[l * npl + i0 + u], part[l]);
+                }
+#pragma unroll
+                for (int l = 0; l < LT_LV; ++l) k[l].add(part[l]);
+            }
+#pragma unroll
+            for (int l = 0; l < LT_LV; ++l)
+                if (o0 + l < nl) chk[(int64_t)leaves[o0 + l] * S + j] = k[l].value();
+        }
+    }
+}
+
+// far[o npl + i] = sum_j P[j][i] phi_d[leaf B][j] for the leaves (ordinal o, box B); per
+// pass LT_T / npl thread groups of npl targets, each group LT_LT leaves
+__global__ void __launch_bounds__(LT_T) k_lat_l2p(const float* __restrict__ P, int S, int npl,
+                                                  const int32_t* __restrict__ leaves, int64_t nl,
+                                                  const float* __restrict__ phid, double* __restrict__ far) {
+    extern __shared__ float lsm[];
+    float* Ps = lsm;                          // [S][npl + 1]
+    float* ps = Ps + (int64_t)S * (npl + 1);   // [LT_T / npl * LT_LT][S]
+    const int lpp = LT_T / npl * LT_LT;
+    lat_load(P, Ps, S * (npl + 1) / 4);
+    const int grp = threadIdx.x / npl, i = threadIdx.x % npl;
+    for (int64_t o0 = (int64_t)blockIdx.x * lpp; o0 < nl; o0 += (int64_t)gridDim.x * lpp) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < lpp * S; e += LT_T) {
+            const int64_t o = o0 + e / S;
+            ps[e] = o < nl ? phid[(int64_t)leaves[o] * S + e % S] : 0.f;
+        }
+        __syncthreads();
+        const float* pr = ps + grp * LT_LT * S;
+        Kahan k[LT_LT];
+        int j = 0;
+        for (; j + 7 < S; j += 8) {
+            float part[LT_LT] = {};
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float w = Ps[(int64_t)(j + u) * (npl + 1) + i];
+#pragma unroll
+                for (int l = 0; l < LT_LT; ++l) part[l] = fmaf(w, pr[l * S + j + u], part[l]);
+            }
+#pragma unroll
+            for (int l = 0; l < LT_LT; ++l) k[l].add(part[l]);
+        }
+        for (; j < S; ++j) {
+            const float w = Ps[(int64_t)j * (npl + 1) + i];
+#pragma unroll
+            for (int l = 0; l < LT_LT; ++l) k[l].add(w * pr[l * S + j]);
+        }
+#pragma unroll
+        for (int l = 0; l < LT_LT; ++l) {
+            const int64_t o = o0 + grp * LT_LT + l;
+            if (o < nl) far[o * npl + i] = k[l].value();
+        }
+    }
+}
+
+static size_t lat_s2m_smem(int S, int npl) { return ((size_t)S * (npl + 1) + (size_t)LT_LV * npl) * 4; }
+static size_t lat_l2p_smem(int S, int npl) { return ((size_t)S * (npl + 1) + (size_t)(LT_T / npl) * LT_LT * S) * 4; }
+
+int lat_s2m(Plan& p) {
+    const unsigned g = (unsigned)std::min<int64_t>((p.nleaves + LT_LV - 1) / LT_LV, 8LL * p.num_sms);
+    k_lat_s2m<<<g, LT_T, lat_s2m_smem(p.S, p.nf_R), p.stream>>>(ptr<float>(p.lat_P), p.S, p.nf_R,
+                                                                ptr<int32_t>(p.leaves), p.nleaves, ptr<double>(p.q),
+                                                                ptr<double>(p.chk));
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+int lat_l2p(Plan& p) {
+    const int lpp = LT_T / p.nf_R * LT_LT;
+    const unsigned g = (unsigned)std::min<int64_t>((p.nleaves + lpp - 1) / lpp, 8LL * p.num_sms);
+    k_lat_l2p<<<g, LT_T, lat_l2p_smem(p.S, p.nf_R), p.stream>>>(ptr<float>(p.lat_P), p.S, p.nf_R,
+                                                                ptr<int32_t>(p.leaves), p.nleaves, ptr<float>(p.phid),
+                                                                ptr<double>(p.far));
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
 int near_tc_plan(Plan& p) {
     p.near_tc = false;
     const char* env = std::getenv("KIFMM_P2P");
@@ -186,6 +332,20 @@ int near_tc_plan(Plan& p) {
     KF_TRY(dev_alloc(p.nf_Thi, (size_t)m2l_tc_table_elems(R) * 2));
     KF_TRY(dev_alloc(p.nf_Tlo, (size_t)m2l_tc_table_elems(R) * 2));
     KF_TRY(m2l_tc_prepare(st, ptr<double>(T), R, p.nf_Thi.p, p.nf_Tlo.p, &p.nf_sT));
+    // S2M and local L2P on the lattice: surface form, leaves at level >= 2, no W / X lists
+    p.lat_far = false;
+    if (!p.cheb && lf >= 2 && p.lists[2].len == 0 && p.lists[3].len == 0 && LT_T % npl == 0 &&
+        ((int64_t)p.S * (npl + 1)) % 4 == 0 &&
+        lat_s2m_smem(p.S, npl) <= 96 * 1024 && lat_l2p_smem(p.S, npl) <= 96 * 1024) {
+        KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
+        KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));
+        k_lat_table<<<nbn((int64_t)p.S * npl, 256), 256, 0, st>>>(ptr<double>(p.surf), p.S, ptr<int32_t>(ref), nc, r, h,
+                                                                   make_kparams(p.a, p.b), ptr<float>(p.lat_P));
+        KF_LAUNCH();
+        for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
+            KF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        p.lat_far = true;
+    }
     // tiles of 128 leaves (ordinals), every tile over the 27 near slots
     const int ntiles = (int)((nl + 127) / 128);
     std::vector<int4> tiles(ntiles);

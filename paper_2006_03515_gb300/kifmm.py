@@ -55,7 +55,8 @@ class _Info(ctypes.Structure):
                 ("pinv_rank_min", ctypes.c_double), ("eval_launches", ctypes.c_int64),
                 ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64),
                 ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double),
-                ("upward_mma_flops", ctypes.c_double), ("near_tensor", ctypes.c_int64)]
+                ("upward_mma_flops", ctypes.c_double), ("near_tensor", ctypes.c_int64),
+                ("lattice_far", ctypes.c_int64)]
 
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
@@ -194,7 +195,8 @@ class Plan:
                     eval_launches=int(inf.eval_launches), p2p_pairs=int(inf.p2p_pairs),
                     m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error),
                     m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops),
-                    upward_mma_flops=float(inf.upward_mma_flops), near_tensor=bool(inf.near_tensor))
+                    upward_mma_flops=float(inf.upward_mma_flops), near_tensor=bool(inf.near_tensor),
+                    lattice_far=bool(inf.lattice_far))
 
     def tree(self):
         inf = self.info()

@@ -167,13 +167,15 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
 @pytest.mark.parametrize("n,leaf", [(32, 64), (16, 512)])
 def test_near_field_on_tensor_cores(kf, monkeypatch, n, leaf):
     # uniform lattice with full leaves (64 or 512 cells): the near field runs as 27 per-offset
-    # kernel matrices on the tensor cores; against the FP64 form and the mixed pair kernel
+    # kernel matrices on the tensor cores, and with 64-cell leaves S2M and the local L2P as one
+    # check-surface matrix per leaf; against the FP64 form and the mixed generic kernels
     pts, h, I = W.config_uniform(n)
     a, b = K.absorption_coefficients(152.0)
     Id = _dev(I)
     s64 = _plan(kf, pts, h, leaf, 6, a, b).eval(Id).cpu().numpy()
     ptc = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
     assert ptc.info()["near_tensor"]
+    assert ptc.info()["lattice_far"] == (leaf == 64)   # S2M / L2P matrices: leaves at level >= 2, 64 cells
     stc = ptc.eval(Id).cpu().numpy()
     monkeypatch.setenv("KIFMM_P2P", "generic")
     pgen = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
