@@ -204,7 +204,8 @@ int kifmm_get_sigma(kifmm_plan_t plan, double* sigma);
 
 /* Copies the upward coefficients c (the truncated-SVD coordinates of each box's upward
  * equivalent density, c = Sigma^+ U^T q^u, Sec. 3) of the last evaluation:
- * n_boxes x *stride FP64 host array (*stride receives the row stride, >= the rank). */
+ * n_boxes x *stride FP64 host array (*stride receives the row stride, >= the rank). With
+ * c == NULL only *stride is written, so that the caller can size the array. */
 int kifmm_get_upward(kifmm_plan_t plan, double* c, int* stride);
 
 /* Per-phase device times (ms) of the last kifmm_eval when KIFMM_TIMING=1 in

@@ -40,7 +40,7 @@ static void free_plan(Plan* p) {
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
                       &p->tc_tiles, &p->tc_boxes, &p->tc_slots, &p->nf_utab, &p->nf_Thi, &p->nf_Tlo, &p->nf_tiles,
-                      &p->nf_slots, &p->nf_boxes, &p->nf_qhi, &p->nf_qlo, &p->nf_qexp, &p->nf_near, &p->lat_P})
+                      &p->nf_slots, &p->nf_boxes, &p->nf_qhi, &p->nf_qlo, &p->nf_qexp, &p->nf_near, &p->lat_P, &p->lat_Mimg, &p->lat_Mer, &p->nf_ref})
         dev_free(*b);
     for (auto& L : p->lv) {
         for (DevBuf* b : {&L.all, &L.leafs, &L.nonleaf, &L.m2l_tiles, &L.m2l_slots, &L.m2l_slot_off, &L.xboxes,
@@ -386,13 +386,15 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
         double up = 0;
         // FP64 pseudo-inverse applications c = Sigma^+ U^T chk, one per leaf and per parent
         // (none in the Chebyshev representation)
-        if (!p.cheb)
-            for (int l = 2; l < p.tree.nlevels; ++l) up += 2.0 * p.ops[l].rank * p.S * p.lv[l].n_up;
+        if (!p.cheb)   // (the leaves of a lattice plan: 2 r npl each, from their weights)
+            for (int l = 2; l < p.tree.nlevels; ++l)
+                up += 2.0 * p.ops[l].rank * (p.lat_up && l == p.nf_level ? p.nf_R : p.S) * p.lv[l].n_up;
         info->upward_flops = up;
         double mma = 0;
         if (p.oz)
             for (int l = 2; l < p.tree.nlevels; ++l)
-                if (p.lv[l].n_up > p.oz_min) mma += pinv_oz_mma_flops(p.S, p.ops[l].rank, p.lv[l].n_up);
+                if (p.lv[l].n_up > p.oz_min)
+                    mma += pinv_oz_mma_flops(p.lat_up && l == p.nf_level ? p.nf_R : p.S, p.ops[l].rank, p.lv[l].n_up);
         info->upward_mma_flops = mma;
     }
     info->device_error = 0;
@@ -463,11 +465,12 @@ int kifmm_get_sigma(kifmm_plan_t h, double* sigma) {
 }
 
 int kifmm_get_upward(kifmm_plan_t h, double* c, int* stride) {
-    if (!h || !h->p || !c || !stride) {
+    if (!h || !h->p || !stride) {
         set_error("kifmm_get_upward: invalid argument");
         return KIFMM_ERR_ARG;
     }
     *stride = h->p->R;
+    if (!c) return KIFMM_OK;   // stride query
     return copy_raw(h->p->cu, (size_t)h->p->tree.nboxes * h->p->R * 8, c, h->p->stream);
 }
 

@@ -414,6 +414,7 @@ int build_eval_data(Plan& p) {
         KF_TRY(dev_alloc(p.ozEb, (size_t)std::max(nmax + 128, 1) * 4));
         KF_CUDA(cudaStreamSynchronize(st));
     }
+    KF_TRY(lat_up_plan(p));
     return KIFMM_OK;
 }
 
@@ -1323,8 +1324,10 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         KF_LAUNCH();
         ++nl;
     } else if (p.n_p2m > 0 && p.lat_far) {   // uniform lattice: one check matrix for every leaf
-        KF_TRY(lat_s2m(p));
-        ++nl;
+        if (!p.lat_up) {                      // (else the leaves' c come straight from q below)
+            KF_TRY(lat_s2m(p));
+            ++nl;
+        }
     } else if (p.n_p2m > 0) {
         auto* kp2m = !mixed ? k_p2m<false, true> : (p.far_series ? k_p2m<true, true> : k_p2m<true, false>);
         kp2m<<<(unsigned)p.n_p2m, P2M_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), ptr<double>(p.chk));
@@ -1345,9 +1348,11 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                  (int64_t)S * R, nullptr, nz)));
         }
         if (p.cheb) continue;   // no pseudo-inverse
-        if (LL.n_up > p.oz_min && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
+        if (p.lat_up && l == p.nf_level) {   // lattice leaves: c = (G1 P) q, FP64-exact on the tensor cores
+            KF_TRY(lat_up_apply(p, cu, nl));
+        } else if (LL.n_up > p.oz_min && p.oz) {   // c = Sigma^+ U^T chk, FP64-exact on the tensor cores
             int64_t extra = 0;
-            KF_TRY(pinv_oz_apply(st, ptr<double>(p.chk), S, ptr<int32_t>(LL.upb), LL.n_up, p.ops[l].ozG1.p,
+            KF_TRY(pinv_oz_apply(st, ptr<double>(p.chk), S, ptr<int32_t>(LL.upb), nullptr, LL.n_up, p.ops[l].ozG1.p,
                                  ptr<int>(p.ops[l].ozEr), p.ops[l].rank, p.ozBox.p, ptr<int>(p.ozEb), cu, R,
                                  ptr<int>(p.err), &extra));
             nl += extra;

@@ -176,9 +176,11 @@ struct Plan {
     // near field on the tensor cores (mixed form, uniform lattice; near_tc.cu)
     bool near_tc = false;
     int nf_R = 0, nf_level = 0, nf_sT = 0, nf_ntiles = 0;
-    DevBuf nf_utab, nf_Thi, nf_Tlo, nf_tiles, nf_slots, nf_boxes, nf_qhi, nf_qlo, nf_qexp, nf_near;
+    DevBuf nf_utab, nf_Thi, nf_Tlo, nf_tiles, nf_slots, nf_boxes, nf_qhi, nf_qlo, nf_qexp, nf_near, nf_ref;
     bool lat_far = false;        // S2M and local L2P on the same lattice (surface form, no W / X lists)
     DevBuf lat_P;                // f32 [S][npl + 1]: K between the leaf's check surface and its cells
+    bool lat_up = false;         // leaves' c = (G1 P) q on the tensor cores, FP64-exact (no leaf S2M)
+    DevBuf lat_Mimg, lat_Mer;    // slice image and row exponents of M = G1 P (rank x npl)
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
@@ -230,14 +232,18 @@ int near_tc_plan(Plan& p);
 int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
 int lat_s2m(Plan& p);   // chk of every leaf (lat_far plans)
 int lat_l2p(Plan& p);   // far of every point from phi_d (lat_far plans)
+int lat_up_plan(Plan& p);   // M = G1 P for the leaves' FP64-exact upward solve (after the slice set-up)
+int lat_up_apply(Plan& p, double* cu, int64_t& nl);   // c of every leaf = M q
 // pinv_oz.cu: FP64-exact c = Sigma^+ U^T chk on the tensor cores
 int pinv_oz_supported(int S);
 size_t pinv_oz_op_bytes(int S, int rank);
 size_t pinv_oz_box_bytes(int S, int n);
 double pinv_oz_mma_flops(int S, int rank, int n);   // tensor-core flop of one level's solve
 int pinv_oz_prepare(cudaStream_t st, const double* G1, int S, int rank, void* img, int* er);
-int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, int n, const void* opimg,
-                  const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err, int64_t* launches);
+// c[boxes[p]] = Op chk[in_rows ? in_rows[p] : boxes[p]] for p < n (rows of chk have S entries)
+int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, const int32_t* in_rows, int n,
+                  const void* opimg, const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err,
+                  int64_t* launches);
 // api.cu / eval.cu helpers for the surrogate
 Plan* kifmm_plan_internal(kifmm_plan_t h);
 int kifmm_scatter_weights(Plan& p, const double* I);

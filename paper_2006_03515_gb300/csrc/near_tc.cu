@@ -265,7 +265,8 @@ int near_tc_plan(Plan& p) {
     const int npl = nc * nc * nc, R = npl;
     if (R % 32 != 0 || !m2l_tc_supported(R) || (int64_t)npl * p.nleaves != t.n) return KIFMM_OK;
     const int64_t n = t.n, nl = p.nleaves;
-    DevBuf lidx, ref, bad;
+    DevBuf lidx, bad;
+    DevBuf& ref = p.nf_ref;   // kept for the leaves' upward operator
     KF_TRY(dev_alloc(lidx, n * 4));
     KF_TRY(dev_alloc(ref, npl * 4));
     KF_TRY(dev_alloc(bad, 4));
@@ -278,28 +279,24 @@ int near_tc_plan(Plan& p) {
     KF_CUDA(cudaMemcpyAsync(&p0, ptr<int32_t>(t.pstart) + first, 4, cudaMemcpyDeviceToHost, st));
     KF_CUDA(cudaStreamSynchronize(st));
     auto release = [&]() {
-        for (DevBuf* d : {&lidx, &ref, &bad}) dev_free(*d);
+        for (DevBuf* d : {&lidx, &bad}) dev_free(*d);
     };
-    if (p0 != 0) {   // then the first leaf holds points 0 .. npl - 1 (npl nleaves = n)
+    auto give_up = [&]() {
         release();
+        dev_free(ref);
         return KIFMM_OK;
-    }
+    };
+    if (p0 != 0) return give_up();   // else the first leaf holds points 0 .. npl - 1 (npl nleaves = n)
     std::vector<int32_t> href(npl);
     KF_CUDA(cudaMemcpyAsync(href.data(), lidx.p, npl * 4, cudaMemcpyDeviceToHost, st));
     int hbad = 0;
     KF_CUDA(cudaMemcpyAsync(&hbad, bad.p, 4, cudaMemcpyDeviceToHost, st));
     KF_CUDA(cudaStreamSynchronize(st));
-    if (hbad) {
-        release();
-        return KIFMM_OK;
-    }
+    if (hbad) return give_up();
     {
         std::vector<char> seen(npl, 0);
         for (int k = 0; k < npl; ++k) {
-            if (href[k] < 0 || href[k] >= npl || seen[href[k]]) {
-                release();
-                return KIFMM_OK;
-            }
+            if (href[k] < 0 || href[k] >= npl || seen[href[k]]) return give_up();
             seen[href[k]] = 1;
         }
     }
@@ -319,8 +316,7 @@ int near_tc_plan(Plan& p) {
     KF_CUDA(cudaStreamSynchronize(st));
     if (hbad) {
         dev_free(p.nf_utab);
-        release();
-        return KIFMM_OK;
+        return give_up();
     }
     // the 27 near-offset matrices, FP64, then their FP16 hi / lo images for the tensor cores
     DevBuf T;
@@ -377,6 +373,61 @@ int near_tc_plan(Plan& p) {
     p.nf_level = lf;
     p.nf_ntiles = ntiles;
     p.near_tc = true;
+    return KIFMM_OK;
+}
+
+// M[r][i] = sum_j G1[r][j] P[j][i] in FP64: the leaves' upward coefficients c = M q straight
+// from their weights (G1 the level's pseudo-inverse, P the check matrix of k_lat_table)
+__global__ void k_lat_M(const double* G1, int S, int rank, const double* surf, const int32_t* ref, int nc, double r,
+                        double h, KParams kp, double* M) {
+    const int npl = nc * nc * nc;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rank * npl) return;
+    const int rr = (int)(e / npl), i = (int)(e % npl);
+    const int ci = ref[i];
+    const double y[3] = {(ci % nc + 0.5) * h - r, ((ci / nc) % nc + 0.5) * h - r, (ci / (nc * nc) + 0.5) * h - r};
+    double sum = 0.0;
+    for (int j = 0; j < S; ++j) {
+        double d2 = 0;
+        for (int k = 0; k < 3; ++k) {
+            const double d = kROuter * r * surf[3 * j + k] - y[k];
+            d2 += d * d;
+        }
+        sum += G1[(int64_t)rr * S + j] * kern_f64(sqrt(d2), kp);
+    }
+    M[e] = sum;
+}
+
+int lat_up_plan(Plan& p) {
+    p.lat_up = false;
+    const int lf = p.nf_level, npl = p.nf_R;
+    if (!p.lat_far || !p.oz || lf < 2 || lf >= p.tree.nlevels || p.nleaves <= p.oz_min) return KIFMM_OK;
+    if (p.lv[lf].n_par != 0 || p.lv[lf].n_up != p.nleaves || !pinv_oz_supported(npl)) return KIFMM_OK;
+    cudaStream_t st = p.stream;
+    const LevelOps& op = p.ops[lf];
+    const double h = p.uniform_h, r = p.tree.side / (double)(2ll << lf);
+    const int nc = (int)std::lround(std::cbrt((double)npl));
+    DevBuf M;
+    KF_TRY(dev_alloc(M, (size_t)op.rank * npl * 8));
+    k_lat_M<<<nbn((int64_t)op.rank * npl, 128), 128, 0, st>>>(ptr<double>(op.G1), p.S, op.rank, ptr<double>(p.surf),
+                                                               ptr<int32_t>(p.nf_ref), nc, r, h, make_kparams(p.a, p.b),
+                                                               ptr<double>(M));
+    KF_LAUNCH();
+    KF_TRY(dev_alloc(p.lat_Mimg, pinv_oz_op_bytes(npl, op.rank)));
+    KF_TRY(dev_alloc(p.lat_Mer, (size_t)((op.rank + 47) / 48 * 48) * 4));
+    KF_TRY(pinv_oz_prepare(st, ptr<double>(M), npl, op.rank, p.lat_Mimg.p, ptr<int>(p.lat_Mer)));
+    KF_CUDA(cudaStreamSynchronize(st));
+    dev_free(M);
+    p.lat_up = true;
+    return KIFMM_OK;
+}
+
+int lat_up_apply(Plan& p, double* cu, int64_t& nl) {
+    int64_t extra = 0;
+    KF_TRY(pinv_oz_apply(p.stream, ptr<double>(p.q), p.nf_R, ptr<int32_t>(p.leaves), ptr<int32_t>(p.nf_boxes),
+                         (int)p.nleaves, p.lat_Mimg.p, ptr<int>(p.lat_Mer), p.ops[p.nf_level].rank, p.ozBox.p,
+                         ptr<int>(p.ozEb), cu, p.R, ptr<int>(p.err), &extra));
+    nl += extra;
     return KIFMM_OK;
 }
 

@@ -105,10 +105,10 @@ __global__ void k_oz_slice_op(const double* G1, int S, int rank, int ntile, __ha
     }
 }
 
-// box image: [slice][box tile][K-chunk][128 rows][128-byte row] for the boxes boxes[0..n);
-// rows beyond n are zero. One warp per row.
-__global__ void k_oz_slice_boxes(const double* chk, int S, const int32_t* boxes, int n, int nbt, __half* img,
-                                 int* eb) {
+// box image: [slice][box tile][K-chunk][128 rows][128-byte row] for the boxes boxes[0..n)
+// (input row in_rows[p] when given, else boxes[p]); rows beyond n are zero. One warp per row.
+__global__ void k_oz_slice_boxes(const double* chk, int S, const int32_t* boxes, const int32_t* in_rows, int n,
+                                 int nbt, __half* img, int* eb) {
     const int p = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (p >= nbt * OZ_M) return;
@@ -117,7 +117,7 @@ __global__ void k_oz_slice_boxes(const double* chk, int S, const int32_t* boxes,
     const int64_t chunk_stride = (int64_t)OZ_M * 64, slice_stride = (int64_t)nbt * NK * chunk_stride;
     __half* base = img + (int64_t)tile * NK * chunk_stride;
     if (p < n) {
-        const double* v = chk + (int64_t)boxes[p] * S;
+        const double* v = chk + (int64_t)(in_rows ? in_rows[p] : boxes[p]) * S;
         const int e = oz_row_exp(v, S, lane);
         oz_slice_row(v, S, KP, e, base, slice_stride, chunk_stride, row, lane);
         if (lane == 0) eb[p] = e;
@@ -328,12 +328,13 @@ static int launch_oz(cudaStream_t st, const void* bimg, const void* opimg, const
     return KIFMM_OK;
 }
 
-int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, int n, const void* opimg,
-                  const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err, int64_t* launches) {
+int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, const int32_t* in_rows, int n,
+                  const void* opimg, const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err,
+                  int64_t* launches) {
     if (n <= 0) return KIFMM_OK;
     const int nbt = (n + OZ_M - 1) / OZ_M;
     const int64_t th = (int64_t)nbt * OZ_M * 32;
-    k_oz_slice_boxes<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(chk, S, boxes, n, nbt,
+    k_oz_slice_boxes<<<(unsigned)((th + 255) / 256), 256, 0, st>>>(chk, S, boxes, in_rows, n, nbt,
                                                                     reinterpret_cast<__half*>(bimg), eb);
     KF_LAUNCH();
     switch (oz_nk(S)) {

@@ -226,9 +226,10 @@ class Plan:
         """Upward coefficients c of the last evaluation, (n_boxes, stride) FP64."""
         inf = self.info()
         st = ctypes.c_int()
-        buf = np.empty(inf["n_boxes"] * 512, np.float64)   # stride <= 512
+        _check(load().kifmm_get_upward(self._h_ptr, None, ctypes.byref(st)))
+        buf = np.empty(inf["n_boxes"] * st.value, np.float64)
         _check(load().kifmm_get_upward(self._h_ptr, ctypes.c_void_p(buf.ctypes.data), ctypes.byref(st)))
-        return buf[: inf["n_boxes"] * st.value].reshape(inf["n_boxes"], st.value).copy()
+        return buf.reshape(inf["n_boxes"], st.value)
 
     def phase_times(self):
         ms = (ctypes.c_float * 8)()

@@ -144,6 +144,7 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
         leaf, uniform = 64, True
 
     monkeypatch.setenv("KIFMM_OZ_MIN", "0")   # every level through the slice products
+    monkeypatch.setenv("KIFMM_P2P", "generic")   # both runs from the same check potentials
 
     def run(mode):
         if mode:
@@ -183,6 +184,27 @@ def test_near_field_on_tensor_cores(kf, monkeypatch, n, leaf):
     sgen = pgen.eval(Id).cpu().numpy()
     assert _relerr(stc, s64) <= 1e-6
     assert _relerr(stc, sgen) <= 1e-6
+
+
+def test_lattice_leaf_coefficients_match_fp64(kf, monkeypatch):
+    # on a lattice the leaves' upward coefficients come from their weights through M = G1 P
+    # (FP64, sliced exactly on the tensor cores); the FP64 form gets them from check
+    # potentials summed in FP64: both are FP64 evaluations of the same operator (reassociated),
+    # so they agree to FP64 rounding times the pseudo-inverse's condition (<= 1e5)
+    monkeypatch.setenv("KIFMM_OZ_MIN", "0")   # 512 leaves: below the default level size of the slices
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(152.0)
+    Id = _dev(I)
+    pm = _plan(kf, pts, h, 64, 6, a, b, precision="mixed")
+    assert pm.info()["lattice_far"]
+    assert pm.info()["upward_flops"] < _plan(kf, pts, h, 64, 6, a, b).info()["upward_flops"]   # leaves: r npl
+    pm.eval(Id)
+    p64 = _plan(kf, pts, h, 64, 6, a, b)
+    p64.eval(Id)
+    c_m, c_64 = pm.upward(), p64.upward()
+    leaves = np.nonzero(pm.tree()["leaf"])[0]
+    scale = np.abs(c_64[leaves]).max(axis=1, keepdims=True)
+    assert np.max(np.abs(c_m[leaves] - c_64[leaves]) / scale) <= 1e-8
 
 
 def test_near_field_lattice_detection(kf):
