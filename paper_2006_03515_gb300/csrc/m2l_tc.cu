@@ -22,9 +22,9 @@
 //  * warp 10, lane 0: waits for a full stage, issues its k-steps x 3 MMAs into the slot's
 //    tensor-memory accumulator and commits the stage's "empty" mbarrier; after the last
 //    chunk of a slot it commits the accumulator's "ready" mbarrier.
-//  * warps 0-7, epilogue: two accumulators alternate between slots; the epilogue scales a
-//    finished one by the slot's 2^{-(e_A + e_T)} into FP32 registers (round-to-nearest) and
-//    releases it. The tensor core's own accumulation thus spans one slot, not the V list.
+//  * warps 0-7, epilogue: a ring of up to four accumulators takes the slots in turn; the
+//    epilogue scales a finished one by the slot's 2^{-(e_A + e_T)} into FP32 registers
+//    (round-to-nearest) and releases it. The tensor core's own accumulation thus spans one slot, not the V list.
 // Every wait is bounded; a timeout sets an abort flag that ends the other roles' waits,
 // records an error code, and the tensor memory is freed before the CTA exits.
 #include <cuda_fp16.h>
@@ -114,10 +114,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int n0 = blockIdx.y * NT;
     constexpr int A_BYTES = TC_M * 128, B_BYTES = NT * 128;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    constexpr int ACC = NT <= 32 ? 32 : (NT <= 64 ? 64 : (NT <= 128 ? 128 : 256));
-    constexpr uint32_t NCOLS = 2 * ACC;
+    // a ring of NACC slot accumulators of ACC columns each in the 512 TMEM columns, so that the
+    // MMAs of a slot wait for the drain of the slot NACC back, not the one before last
+    constexpr int ACC = (NT + 31) / 32 * 32;
+    constexpr int NACC = 512 / ACC >= 4 ? 4 : 512 / ACC;
+    constexpr uint32_t NCOLS = NACC * ACC <= 32 ? 32 : (NACC * ACC <= 64 ? 64 : (NACC * ACC <= 128 ? 128 : (NACC * ACC <= 256 ? 256 : 512)));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t full[NS], empty[NS], ready[2], freed[2];
+    __shared__ uint64_t full[NS], empty[NS], ready[NACC], freed[NACC];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ int sl[344];   // [count, slot_0, ...] of this tile
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             mbar_init(smem_u32(&full[s]), TC_PROD + 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        for (int j = 0; j < 2; ++j) {
+        for (int j = 0; j < NACC; ++j) {
             mbar_init(smem_u32(&ready[j]), 1);
             mbar_init(smem_u32(&freed[j]), TC_EPI);
         }
@@ -227,8 +230,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             const uint32_t idesc = f16_idesc(TC_M, NT);
             uint32_t fphase[NS] = {};
             for (int si = 0; si < ns && !abort_flag; ++si) {
-                const int j = si & 1;
-                if (si >= 2 && !mbar_wait(smem_u32(&freed[j]), (uint32_t)(((si - 2) >> 1) & 1), &abort_flag)) break;
+                const int j = si % NACC;
+                if (si >= NACC && !mbar_wait(smem_u32(&freed[j]), (uint32_t)(((si - NACC) / NACC) & 1), &abort_flag))
+                    break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + (uint32_t)(j * ACC);
                 bool ok = true;
@@ -275,10 +279,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         };
         float fnext = slot_scale(0);
         for (int si = 0; si < ns; ++si) {
-            const int j = si & 1;
+            const int j = si % NACC;
             const float f = fnext;
             fnext = slot_scale(si + 1);
-            const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((si >> 1) & 1), &abort_flag);
+            const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((si / NACC) & 1), &abort_flag);
             if (__any_sync(0xffffffffu, !ok)) break;   // warp-uniform exit (tcgen05.ld is .sync.aligned)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
