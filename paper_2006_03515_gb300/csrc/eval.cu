@@ -1427,7 +1427,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                     ptr<int32_t>(LP.l2l_dst), 0, LP.l2l_max, dd, R, dd, R, 1, 1, 0,
                                     ptr<int32_t>(LP.l2l_off), 8, (int64_t)R * R));
         }
-        if (LL.n_leaf > 0 && !p.cheb)
+        if (LL.n_leaf > 0 && !p.cheb && !(p.lat_far && l == p.nf_level))   // (lattice leaves: L2P reads d)
             RUN(launch_apply<T>(st, sel<T>(op.Ub, op.Ub32), R, S, op.rank, ptr<int32_t>(LL.leafs), ptr<int32_t>(LL.leafs), 0,
                                 LL.n_leaf, dd, R, phid, S, 0));
     }

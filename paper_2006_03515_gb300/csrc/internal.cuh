@@ -179,6 +179,7 @@ struct Plan {
     DevBuf nf_utab, nf_Thi, nf_Tlo, nf_tiles, nf_slots, nf_boxes, nf_qhi, nf_qlo, nf_qexp, nf_near, nf_ref;
     bool lat_far = false;        // S2M and local L2P on the same lattice (surface form, no W / X lists)
     DevBuf lat_P;                // f32 [S][npl + 1]: K between the leaf's check surface and its cells
+    DevBuf lat_Q;                // f32 [R][npl + 1]: P^T Ub, the leaf's local expansion from its coefficients d
     bool lat_up = false;         // leaves' c = (G1 P) q on the tensor cores, FP64-exact (no leaf S2M)
     DevBuf lat_Mimg, lat_Mer;    // slice image and row exponents of M = G1 P (rank x npl)
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces
@@ -231,7 +232,7 @@ int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* til
 int near_tc_plan(Plan& p);
 int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
 int lat_s2m(Plan& p);   // chk of every leaf (lat_far plans)
-int lat_l2p(Plan& p);   // far of every point from phi_d (lat_far plans)
+int lat_l2p(Plan& p);   // far of every point from the leaves' d (lat_far plans)
 int lat_up_plan(Plan& p);   // M = G1 P for the leaves' FP64-exact upward solve (after the slice set-up)
 int lat_up_apply(Plan& p, double* cu, int64_t& nl);   // c of every leaf = M q
 // pinv_oz.cu: FP64-exact c = Sigma^+ U^T chk on the tensor cores

@@ -178,8 +178,30 @@ __global__ void __launch_bounds__(LT_T) k_lat_s2m(const float* __restrict__ P, i
     }
 }
 
-// far[o npl + i] = sum_j P[j][i] phi_d[leaf B][j] for the leaves (ordinal o, box B); per
-// pass LT_T / npl thread groups of npl targets, each group LT_LT leaves
+// Q[k][i] = sum_j P[j][i] Ub[j][k] in FP64, rounded once: the local expansion of a leaf
+// straight from its downward coefficients d (phi_d = Ub d), rows padded to npl + 1
+__global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+                        double h, KParams kp, float* Q) {
+    const int npl = nc * nc * nc;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)R * npl) return;
+    const int k = (int)(e / npl), i = (int)(e % npl);
+    const int ci = ref[i];
+    const double y[3] = {(ci % nc + 0.5) * h - r, ((ci / nc) % nc + 0.5) * h - r, (ci / (nc * nc) + 0.5) * h - r};
+    double sum = 0.0;
+    for (int j = 0; j < S; ++j) {
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = kROuter * r * surf[3 * j + a] - y[a];
+            d2 += d * d;
+        }
+        sum += kern_f64(sqrt(d2), kp) * Ub[(int64_t)j * R + k];
+    }
+    Q[(int64_t)k * (npl + 1) + i] = (float)sum;
+}
+
+// far[o npl + i] = sum_k Q[k][i] d[leaf B][k] for the leaves (ordinal o, box B), k < K (d rows
+// of stride K); per pass LT_T / npl thread groups of npl targets, each group LT_LT leaves
 __global__ void __launch_bounds__(LT_T) k_lat_l2p(const float* __restrict__ P, int S, int npl,
                                                   const int32_t* __restrict__ leaves, int64_t nl,
                                                   const float* __restrict__ phid, double* __restrict__ far) {
@@ -238,8 +260,8 @@ int lat_s2m(Plan& p) {
 int lat_l2p(Plan& p) {
     const int lpp = LT_T / p.nf_R * LT_LT;
     const unsigned g = (unsigned)std::min<int64_t>((p.nleaves + lpp - 1) / lpp, 8LL * p.num_sms);
-    k_lat_l2p<<<g, LT_T, lat_l2p_smem(p.S, p.nf_R), p.stream>>>(ptr<float>(p.lat_P), p.S, p.nf_R,
-                                                                ptr<int32_t>(p.leaves), p.nleaves, ptr<float>(p.phid),
+    k_lat_l2p<<<g, LT_T, lat_l2p_smem(p.R, p.nf_R), p.stream>>>(ptr<float>(p.lat_Q), p.R, p.nf_R,
+                                                                ptr<int32_t>(p.leaves), p.nleaves, ptr<float>(p.dd),
                                                                 ptr<double>(p.far));
     KF_LAUNCH();
     return KIFMM_OK;
@@ -331,12 +353,18 @@ int near_tc_plan(Plan& p) {
     // S2M and local L2P on the lattice: surface form, leaves at level >= 2, no W / X lists
     p.lat_far = false;
     if (!p.cheb && lf >= 2 && p.lists[2].len == 0 && p.lists[3].len == 0 && LT_T % npl == 0 &&
-        ((int64_t)p.S * (npl + 1)) % 4 == 0 &&
-        lat_s2m_smem(p.S, npl) <= 96 * 1024 && lat_l2p_smem(p.S, npl) <= 96 * 1024) {
+        ((int64_t)p.S * (npl + 1)) % 4 == 0 && ((int64_t)p.R * (npl + 1)) % 4 == 0 &&
+        lat_s2m_smem(p.S, npl) <= 96 * 1024 && lat_l2p_smem(p.R, npl) <= 96 * 1024) {
         KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));
         k_lat_table<<<nbn((int64_t)p.S * npl, 256), 256, 0, st>>>(ptr<double>(p.surf), p.S, ptr<int32_t>(ref), nc, r, h,
                                                                    make_kparams(p.a, p.b), ptr<float>(p.lat_P));
+        KF_LAUNCH();
+        KF_TRY(dev_alloc(p.lat_Q, (size_t)p.R * (npl + 1) * 4));
+        KF_CUDA(cudaMemsetAsync(p.lat_Q.p, 0, (size_t)p.R * (npl + 1) * 4, st));
+        k_lat_Q<<<nbn((int64_t)p.R * npl, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R, ptr<double>(p.surf),
+                                                               ptr<int32_t>(ref), nc, r, h, make_kparams(p.a, p.b),
+                                                               ptr<float>(p.lat_Q));
         KF_LAUNCH();
         for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
             KF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
