@@ -43,19 +43,19 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 300.30e6 + 16.05e6, "per_point_scaled": False,
+    "M2L": {"bytes": 298.49e6 + 16.35e6, "per_point_scaled": False,
             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                    "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb"},
+                    "837ac8f7aaae46c4879bac8f12da2434c7c90825c9193afdfc49dc526d7cb6ff"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
     "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
             "src": {"paper_2006_03515_gb300/csrc/eval.cu":
-                    "7c96206c5ec6d23b9d7c5f19f7313d74b0847328b6c0ae8b2a05b23534fcb021"},
+                    "27add4c5c6f89bc5081df57c5cc3f95224a7882530864fae517b59636790b1c6"},
             "profile": "profiles/k_p2p_mixed_uniform64.md"},
     "NEAR": {"bytes": 3.96e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                     "6b47b90ad6c2d57d4cd12b3df5632856589f4e5de13f836143bbc5f277f13fdb",
+                     "837ac8f7aaae46c4879bac8f12da2434c7c90825c9193afdfc49dc526d7cb6ff",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "22103b78ca0b81fee7a906a94308437cee97341e2395af678e22bca6a691e193"},
+                     "159f283307f77a604c237c7e3a0d8b176e5fd836ec7f4153e7d358ee06595854"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
