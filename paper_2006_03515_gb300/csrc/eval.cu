@@ -99,6 +99,34 @@ __global__ void m2l_tile_slots(const int32_t* vtab, int64_t lo, int64_t hi, int 
 }
 
 // V-list entries per level (algorithmic M2L work)
+// ptab[b][o] = parent of box b for its octant o inside the parent (boxes of level >= 3), -1 else
+__global__ void parent_tab(const int32_t* parent, const int32_t* anchor, const int32_t* level, int64_t nb,
+                           int32_t* ptab) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    for (int o = 0; o < 8; ++o) ptab[b * 8 + o] = -1;
+    if (level[b] < 3) return;
+    const int o = (anchor[3 * b] & 1) | ((anchor[3 * b + 1] & 1) << 1) | ((anchor[3 * b + 2] & 1) << 2);
+    ptab[b * 8 + o] = parent[b];
+}
+
+// L2L slots of a tile: the octants of its boxes (a tile may span two octant groups)
+__global__ void l2l_tile_slots(const int4* tiles, int ntiles, const int32_t* boxes, const int32_t* anchor,
+                               int32_t* slots) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntiles) return;
+    const int4 tl = tiles[t];
+    int mask = 0;
+    for (int k = 0; k < tl.z; ++k) {
+        const int b = boxes[tl.y + k];
+        mask |= 1 << ((anchor[3 * b] & 1) | ((anchor[3 * b + 1] & 1) << 1) | ((anchor[3 * b + 2] & 1) << 2));
+    }
+    int n = 0;
+    for (int o = 0; o < 8; ++o)
+        if (mask & (1 << o)) slots[(int64_t)t * kSlotStride + 1 + n++] = o;
+    slots[(int64_t)t * kSlotStride] = n;
+}
+
 __global__ void count_v_per_level(const int32_t* voff, const int32_t* level, int64_t nb, unsigned long long* cnt) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
@@ -356,6 +384,8 @@ int build_eval_data(Plan& p) {
             m2l_tile_slots<<<nt, 256, 0, st>>>(ptr<int32_t>(p.vtab), lo, hi, 128, ptr<int32_t>(p.tc_boxes) + off,
                                                ptr<int32_t>(p.tc_slots) + (int64_t)tiles.size() * kSlotStride);
             KF_LAUNCH();
+            p.tc_first[l] = (int)tiles.size();
+            p.tc_count[l] = nt;
             for (int k = 0; k < nt; ++k)
                 tiles.push_back(make_int4(l, (int)(off + 128 * k), (int)std::min<int64_t>(128, cnt - 128 * k), 0));
             off += cnt;
@@ -363,6 +393,28 @@ int build_eval_data(Plan& p) {
         p.tc_ntiles = (int)tiles.size();
         if (!tiles.empty())
             KF_CUDA(cudaMemcpyAsync(p.tc_tiles.p, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        // L2L through the same kernel: per child tile the parent at its octant's slot, the
+        // parent level's L2L matrices as FP16 hi / lo tables (KIFMM_L2L=simt keeps the SIMT apply)
+        const char* l2l = std::getenv("KIFMM_L2L");
+        p.l2l_tc = !(l2l && std::string(l2l) == "simt") && t.nlevels > 3 && !tiles.empty();
+        if (p.l2l_tc) {
+            KF_TRY(dev_alloc(p.ptab, (size_t)nb * 8 * 4));
+            parent_tab<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(t.parent), ptr<int32_t>(t.anchor),
+                                                      ptr<int32_t>(t.level), nb, ptr<int32_t>(p.ptab));
+            KF_LAUNCH();
+            KF_TRY(dev_alloc(p.l2l_slots, tiles.size() * kSlotStride * 4));
+            l2l_tile_slots<<<nbk((int64_t)tiles.size(), 128), 128, 0, st>>>(ptr<int4>(p.tc_tiles), (int)tiles.size(),
+                                                                            ptr<int32_t>(p.tc_boxes),
+                                                                            ptr<int32_t>(t.anchor),
+                                                                            ptr<int32_t>(p.l2l_slots));
+            KF_LAUNCH();
+            for (int l = 2; l + 1 < t.nlevels; ++l) {
+                LevelOps& op = p.ops[l];
+                KF_TRY(dev_alloc(op.Lhi, (size_t)m2l_tc_table_elems(p.R, 8) * 2));
+                KF_TRY(dev_alloc(op.Llo, (size_t)m2l_tc_table_elems(p.R, 8) * 2));
+                KF_TRY(m2l_tc_prepare(st, ptr<double>(op.Lo), p.R, op.Lhi.p, op.Llo.p, &op.l2l_sT, 8));
+            }
+        }
         KF_CUDA(cudaStreamSynchronize(st));
     }
     // workspace
@@ -1422,7 +1474,23 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         if (l >= 3) {
             auto& LP = p.lv[l - 1];
             const LevelOps& pop = p.ops[l - 1];
-            if (LP.l2l_max > 0)   // one launch, batched over the 8 child octants
+            if (LP.l2l_max > 0 && sizeof(T) == 4 && p.l2l_tc && p.tc_count[l] > 0) {
+                // tensor cores: the parents' d split into FP16 hi / lo (the M2L operand buffers, free
+                // by now), one slot per child octant, added onto the children's d
+                const int64_t lo = t.level_start[l - 1], cnt = t.level_start[l] - lo;
+                KF_TRY(m2l_tc_split_f32(st, reinterpret_cast<const float*>(dd) + lo * R, cnt, R,
+                                        static_cast<char*>(p.chi.p) + lo * R * 2, static_cast<char*>(p.clo.p) + lo * R * 2,
+                                        ptr<int>(p.cexp) + lo));
+                ++nl;
+                M2LTables tabs{};
+                tabs.hi[l] = pop.Lhi.p;
+                tabs.lo[l] = pop.Llo.p;
+                tabs.sT[l] = pop.l2l_sT;
+                RUN(launch_tc_translate(st, tabs, R, ptr<int4>(p.tc_tiles) + p.tc_first[l], p.tc_count[l],
+                                        ptr<int32_t>(p.tc_boxes), ptr<int32_t>(p.ptab), 8,
+                                        ptr<int32_t>(p.l2l_slots) + (int64_t)p.tc_first[l] * kSlotStride, p.chi.p,
+                                        p.clo.p, ptr<int>(p.cexp), reinterpret_cast<float*>(dd), 1, ptr<int>(p.err)));
+            } else if (LP.l2l_max > 0)   // one launch, batched over the 8 child octants
                 RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32), R, op.rank, pop.rank, ptr<int32_t>(LP.l2l_src),
                                     ptr<int32_t>(LP.l2l_dst), 0, LP.l2l_max, dd, R, dd, R, 1, 1, 0,
                                     ptr<int32_t>(LP.l2l_off), 8, (int64_t)R * R));

@@ -103,6 +103,9 @@ struct LevelOps {
     // tensor-core M2L operands: FP16 hi/lo of T 2^tc_sT, [slot][k-chunk][row][128-byte swizzled row]
     DevBuf Thi, Tlo;
     int tc_sT = 0;
+    // tensor-core L2L (parent level = this level): FP16 hi/lo of Lo 2^l2l_sT, 8 slots
+    DevBuf Lhi, Llo;
+    int l2l_sT = 0;
     // FP64-exact upward solve on the tensor cores: integer slices of G1 (swizzled images) and
     // the per-row power-of-two exponents
     DevBuf ozG1, ozEr;
@@ -169,6 +172,9 @@ struct Plan {
     DevBuf wleaves;   int n_wleaves = 0;      // leaves with non-empty W list
     int64_t eval_launches = 0;   // kernels of the last evaluation
     bool m2l_tensor = false;     // M2L on tcgen05 (mixed form)
+    bool l2l_tc = false;         // L2L through the same kernel (mixed form)
+    DevBuf ptab, l2l_slots;      // i32[nb][8] parent at the box's octant slot; per-tile L2L slot lists
+    int tc_first[kMaxLevel + 1] = {0}, tc_count[kMaxLevel + 1] = {0};   // M2L tiles of each level
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
@@ -217,9 +223,11 @@ int build_operators(Plan& p);
 int build_self_terms(Plan& p, const double* h_dev, double uniform_h);
 // m2l_tc.cu
 int m2l_tc_supported(int R);
-int64_t m2l_tc_table_elems(int R);   // FP16 elements of one level's Thi (or Tlo)
-int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out);
+int64_t m2l_tc_table_elems(int R, int nslots = kOffsetSlots);   // FP16 elements of one level's Thi (or Tlo)
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out,
+                   int nslots = kOffsetSlots);
 int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp);
+int m2l_tc_split_f32(cudaStream_t st, const float* c, int64_t nb, int R, void* chi, void* clo, int* cexp);
 struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the tensor-core kernel
     const void* hi[kMaxLevel + 1];
     const void* lo[kMaxLevel + 1];
@@ -228,6 +236,11 @@ struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the te
 int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
                   const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
                   int* err);
+// the same kernel with any source table stride (nslots slots per target box) and, with
+// accum != 0, the result added to d (L2L onto the M2L result)
+int launch_tc_translate(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles,
+                        const int32_t* boxes, const int32_t* vtab, int vstride, const int32_t* slots, const void* chi,
+                        const void* clo, const int* cexp, float* d, int accum, int* err);
 // near_tc.cu: near field on a uniform lattice
 int near_tc_plan(Plan& p);
 int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);

@@ -59,10 +59,10 @@ __global__ void k_absmax(const double* x, int64_t n, unsigned long long* out) {
 // T (FP64 [343][R][R]) * 2^sT -> Thi/Tlo (FP16) in the order [slot][k-chunk][row][128-byte
 // swizzled row of 64 FP16], k >= R zero, so that one chunk of one slot is a contiguous
 // R*128-byte image of the shared-memory B tile.
-__global__ void k_swizzle_T(const double* T, int R, int NK, int sT, __half* Thi, __half* Tlo) {
+__global__ void k_swizzle_T(const double* T, int R, int NK, int nslots, int sT, __half* Thi, __half* Tlo) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)R * NK * TC_KH;
-    if (e >= (int64_t)kOffsetSlots * per) return;
+    if (e >= (int64_t)nslots * per) return;
     const int64_t slot = e / per;
     const int row = (int)((e % per) / (NK * TC_KH)), k = (int)(e % (NK * TC_KH));
     const float x = k < R ? (float)ldexp(T[(slot * R + row) * R + k], sT) : 0.f;
@@ -75,11 +75,12 @@ __global__ void k_swizzle_T(const double* T, int R, int NK, int sT, __half* Thi,
 
 // upward coefficients (FP64, rows of R) -> their FP32 values scaled by 2^{e_b} per box (largest
 // magnitude near 2^14), split into FP16 hi/lo; one warp per box
-__global__ void k_split_c(const double* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp) {
+template <class TIN>
+__global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp) {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
-    const double* row = c + b * R;
+    const TIN* row = c + b * R;
     float m = 0.f;
     for (int k = lane; k < R; k += 32) m = fmaxf(m, fabsf((float)row[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -106,8 +107,9 @@ __global__ void k_split_c(const double* c, int64_t nb, int R, __half* chi, __hal
 template <int NC, int NS, int NB>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_m2l_tc(M2LTables tabs, const int4* __restrict__ tiles, const int32_t* __restrict__ all_boxes,
-             const int32_t* __restrict__ vtab, const int32_t* __restrict__ slots, const __half* __restrict__ chi,
-             const __half* __restrict__ clo, const int* __restrict__ cexp, float* __restrict__ d, int* err) {
+             const int32_t* __restrict__ vtab, int vstride, const int32_t* __restrict__ slots,
+             const __half* __restrict__ chi, const __half* __restrict__ clo, const int* __restrict__ cexp,
+             float* __restrict__ d, int accum, int* err) {
     constexpr int NT = 32 * NC;
     constexpr int R = NB * NT;
     constexpr int NK = (R + TC_KH - 1) / TC_KH;
@@ -168,7 +170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         // source box of each row for the current slot; the next slot's are fetched one slot
         // ahead so that the index load is off the critical path
         auto lookup = [&](int si, int h) -> int {
-            return (si < ns && box2[h] >= 0) ? vtab[(int64_t)box2[h] * kOffsetSlots + sl[1 + si]] : -1;
+            return (si < ns && box2[h] >= 0) ? vtab[(int64_t)box2[h] * vstride + sl[1 + si]] : -1;
         };
         int acur[2] = {lookup(0, 0), lookup(0, 1)};
         int anext[2] = {lookup(1, 0), lookup(1, 1)};
@@ -274,7 +276,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int bbox = brow < nbox ? boxes[brow] : -1;
         auto slot_scale = [&](int si) -> float {
             if (si >= ns || bbox < 0) return 0.f;
-            const int a = vtab[(int64_t)bbox * kOffsetSlots + sl[1 + si]];
+            const int a = vtab[(int64_t)bbox * vstride + sl[1 + si]];
             return a >= 0 ? pow2i(-(cexp[a] + sT)) : 0.f;
         };
         float fnext = slot_scale(0);
@@ -307,7 +309,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         if (!abort_flag && bi < nbox) {
             float4* o = reinterpret_cast<float4*>(d + (int64_t)boxes[bi] * R + n0 + col0);
 #pragma unroll
-            for (int k = 0; k < NT / 8; ++k) o[k] = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+            for (int k = 0; k < NT / 8; ++k) {
+                float4 v = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
+                if (accum) {   // add to the row already there (L2L onto the M2L result)
+                    const float4 u = o[k];
+                    v = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);
+                }
+                o[k] = v;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -343,10 +352,10 @@ int m2l_tc_supported(int R) {
     return (R % (32 * nb) == 0 && stages_for(R / nb) >= 2) ? 1 : 0;
 }
 
-int64_t m2l_tc_table_elems(int R) { return (int64_t)kOffsetSlots * ((R + TC_KH - 1) / TC_KH) * R * TC_KH; }
+int64_t m2l_tc_table_elems(int R, int nslots) { return (int64_t)nslots * ((R + TC_KH - 1) / TC_KH) * R * TC_KH; }
 
-int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out) {
-    const int64_t n = (int64_t)kOffsetSlots * R * R;
+int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out, int nslots) {
+    const int64_t n = (int64_t)nslots * R * R;
     DevBuf mx;
     KF_TRY(dev_alloc(mx, 8));
     KF_CUDA(cudaMemsetAsync(mx.p, 0, 8, st));
@@ -363,53 +372,75 @@ int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo
     const int sT = m > 0.0 ? TC_HI_EXP + 1 - ex : 0;   // max |T| 2^sT in [2^13, 2^14)
     *sT_out = sT;
     const int NK = (R + TC_KH - 1) / TC_KH;
-    const int64_t ne = m2l_tc_table_elems(R);
-    k_swizzle_T<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(T, R, NK, sT, reinterpret_cast<__half*>(Thi),
+    const int64_t ne = m2l_tc_table_elems(R, nslots);
+    k_swizzle_T<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(T, R, NK, nslots, sT, reinterpret_cast<__half*>(Thi),
                                                               reinterpret_cast<__half*>(Tlo));
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
 int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp) {
-    k_split_c<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
-                                                                 reinterpret_cast<__half*>(clo), cexp);
+    if (nb <= 0) return KIFMM_OK;
+    k_split_c<double><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
+                                                                         reinterpret_cast<__half*>(clo), cexp);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
+int m2l_tc_split_f32(cudaStream_t st, const float* c, int64_t nb, int R, void* chi, void* clo, int* cexp) {
+    if (nb <= 0) return KIFMM_OK;
+    k_split_c<float><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
+                                                                        reinterpret_cast<__half*>(clo), cexp);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+// Launch arguments other than the tile set: the source table (vtab, row stride vstride), the
+// per-tile slot lists, the split coefficients, the output and whether it is added to.
+struct TcArgs {
+    const int32_t* vtab;
+    int vstride;
+    const int32_t* slots;
+    const void* chi;
+    const void* clo;
+    const int* cexp;
+    float* d;
+    int accum;
+    int* err;
+};
+
 template <int NC, int NS, int NB>
 static int launch_cfg(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
-                      const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
-                      float* d, int* err) {
+                      const TcArgs& a) {
     const size_t smem = m2l_tc_smem(32 * NC);
     static bool configured = false;   // one attribute per instantiation (its size never changes)
     if (!configured) {
         KF_CUDA(cudaFuncSetAttribute(k_m2l_tc<NC, NS, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    k_m2l_tc<NC, NS, NB><<<dim3(ntiles, NB), TC_THREADS, smem, st>>>(tabs, tiles, boxes, vtab, slots,
-                                                        reinterpret_cast<const __half*>(chi),
-                                                        reinterpret_cast<const __half*>(clo), cexp, d, err);
+    k_m2l_tc<NC, NS, NB><<<dim3(ntiles, NB), TC_THREADS, smem, st>>>(
+        tabs, tiles, boxes, a.vtab, a.vstride, a.slots, reinterpret_cast<const __half*>(a.chi),
+        reinterpret_cast<const __half*>(a.clo), a.cexp, a.d, a.accum, a.err);
     KF_LAUNCH();
     return KIFMM_OK;
 }
 
 template <int NC, int NB>
 static int launch_nc(cudaStream_t st, const M2LTables& tabs, const int4* tiles, int ntiles, const int32_t* boxes,
-                     const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp,
-                     float* d, int* err) {
+                     const TcArgs& a) {
     switch (stages_for(32 * NC)) {
-        case 2: return launch_cfg<NC, 2, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        case 3: return launch_cfg<NC, 3, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
-        default: return launch_cfg<NC, 4, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err);
+        case 2: return launch_cfg<NC, 2, NB>(st, tabs, tiles, ntiles, boxes, a);
+        case 3: return launch_cfg<NC, 3, NB>(st, tabs, tiles, ntiles, boxes, a);
+        default: return launch_cfg<NC, 4, NB>(st, tabs, tiles, ntiles, boxes, a);
     }
 }
 
-int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
-                  const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
-                  int* err) {
+int launch_tc_translate(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles,
+                        const int32_t* boxes, const int32_t* vtab, int vstride, const int32_t* slots, const void* chi,
+                        const void* clo, const int* cexp, float* d, int accum, int* err) {
     if (ntiles <= 0) return KIFMM_OK;
-#define KF_M2L_TC(NC, NB) return launch_nc<NC, NB>(st, tabs, tiles, ntiles, boxes, vtab, slots, chi, clo, cexp, d, err)
+    const TcArgs a{vtab, vstride, slots, chi, clo, cexp, d, accum, err};
+#define KF_M2L_TC(NC, NB) return launch_nc<NC, NB>(st, tabs, tiles, ntiles, boxes, a)
     switch (m2l_tc_supported(R) ? R : 0) {
         case 32: KF_M2L_TC(1, 1);
         case 64: KF_M2L_TC(2, 1);
@@ -426,6 +457,12 @@ int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* til
         default: set_error("M2L tensor path: unsupported coefficient count"); return KIFMM_ERR_ARG;
     }
 #undef KF_M2L_TC
+}
+
+int launch_m2l_tc(cudaStream_t st, const M2LTables& tabs, int R, const int4* tiles, int ntiles, const int32_t* boxes,
+                  const int32_t* vtab, const int32_t* slots, const void* chi, const void* clo, const int* cexp, float* d,
+                  int* err) {
+    return launch_tc_translate(st, tabs, R, tiles, ntiles, boxes, vtab, kOffsetSlots, slots, chi, clo, cexp, d, 0, err);
 }
 
 }  // namespace kifmm

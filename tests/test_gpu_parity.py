@@ -221,6 +221,28 @@ def test_near_field_lattice_detection(kf):
     assert not _plan(kf, pts, h, 64, 6, a, b).info()["near_tensor"]   # FP64 form
 
 
+@pytest.mark.parametrize("adaptive", [False, True])
+def test_l2l_tensor_cores_against_simt(kf, monkeypatch, adaptive):
+    # L2L through the tensor-core translation kernel (parents' d split FP16 x 3, added onto the
+    # children's M2L result) against the SIMT FP32 apply and the FP64 form
+    if adaptive:
+        pts, h = _adaptive_small()
+        I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
+                              head_sigma=0.05, noise_sigma=0.3, seed=7)
+        a, b, leaf, uniform = 5.32, 304.0, 16, False
+    else:
+        pts, h, I = W.config_uniform(64)
+        a, b = K.absorption_coefficients(152.0)
+        leaf, uniform = 64, True
+    Id = _dev(I)
+    s64 = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform).eval(Id).cpu().numpy()
+    stc = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform, precision="mixed").eval(Id).cpu().numpy()
+    monkeypatch.setenv("KIFMM_L2L", "simt")
+    ssimt = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform, precision="mixed").eval(Id).cpu().numpy()
+    assert _relerr(stc, s64) <= 1e-6
+    assert _relerr(stc, ssimt) <= 1e-6
+
+
 def test_mixed_adaptive_matches_fp64(kf):
     pts, h = _adaptive_small()
     I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
