@@ -110,6 +110,24 @@ __global__ void parent_tab(const int32_t* parent, const int32_t* anchor, const i
     ptab[b * 8 + o] = parent[b];
 }
 
+// Mc [8][S][R] -> [8][R][R] (rows >= S zero), the square tables of the tensor-core kernel
+__global__ void pad_mc(const double* Mc, int S, int R, double* out) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 8LL * R * R) return;
+    const int64_t o = e / ((int64_t)R * R);
+    const int i = (int)((e / R) % R), j = (int)(e % R);
+    out[e] = i < S ? Mc[(o * S + i) * R + j] : 0.0;
+}
+
+// out[box][j] = (double) in[box][j], j < ncol, for the listed boxes (in rows of R floats)
+__global__ void rows_f2d(const int32_t* boxes, int n, const float* in, int R, double* out, int ldo, int ncol) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)n * ncol) return;
+    const int64_t b = boxes[e / ncol];
+    const int j = (int)(e % ncol);
+    out[b * ldo + j] = (double)in[b * R + j];
+}
+
 // L2L slots of a tile: the octants of its boxes (a tile may span two octant groups)
 __global__ void l2l_tile_slots(const int4* tiles, int ntiles, const int32_t* boxes, const int32_t* anchor,
                                int32_t* slots) {
@@ -414,6 +432,45 @@ int build_eval_data(Plan& p) {
                 KF_TRY(dev_alloc(op.Llo, (size_t)m2l_tc_table_elems(p.R, 8) * 2));
                 KF_TRY(m2l_tc_prepare(st, ptr<double>(op.Lo), p.R, op.Lhi.p, op.Llo.p, &op.l2l_sT, 8));
             }
+        }
+        // M2M translations likewise: per parent tile the 8 child octants as slots (the tree's child
+        // table is the source table), Mc padded to square tables, the result staged in FP32 and
+        // copied into the parents' check rows (KIFMM_M2M=simt keeps the SIMT apply). Surface form
+        // with S <= R only (the check rows must fit the square tables); the Chebyshev translations
+        // (K = p^3 = 512 at p = 8) would take 96 truncating accumulations per slot, a bias that
+        // compounds level by level up the tree.
+        const char* m2m = std::getenv("KIFMM_M2M");
+        p.m2m_tc = !(m2m && std::string(m2m) == "simt") && t.nlevels > 3 && !p.cheb && S <= p.R;   // square tables
+        if (p.m2m_tc) {
+            const int R = p.R;
+            std::vector<int4> mt;
+            DevBuf pad;
+            KF_TRY(dev_alloc(pad, (size_t)8 * R * R * 8));
+            for (int l = 2; l + 1 < t.nlevels; ++l) {
+                LevelOps& op = p.ops[l];
+                p.m2m_first[l] = (int)mt.size();
+                const int np = p.lv[l].n_par;
+                p.m2m_count[l] = (np + 127) / 128;
+                for (int k = 0; k < p.m2m_count[l]; ++k) mt.push_back(make_int4(l, 128 * k, std::min(128, np - 128 * k), 0));
+                if (np == 0) continue;
+                pad_mc<<<nbk(8LL * R * R, 256), 256, 0, st>>>(ptr<double>(op.Mc), S, R, ptr<double>(pad));
+                KF_LAUNCH();
+                KF_TRY(dev_alloc(op.Mhi, (size_t)m2l_tc_table_elems(R, 8) * 2));
+                KF_TRY(dev_alloc(op.Mlo, (size_t)m2l_tc_table_elems(R, 8) * 2));
+                KF_TRY(m2l_tc_prepare(st, ptr<double>(pad), R, op.Mhi.p, op.Mlo.p, &op.m2m_sT, 8));
+            }
+            dev_free(pad);
+            std::vector<int32_t> ms(std::max<size_t>(mt.size(), 1) * kSlotStride, 0);
+            for (size_t k = 0; k < mt.size(); ++k) {
+                ms[k * kSlotStride] = 8;
+                for (int o = 0; o < 8; ++o) ms[k * kSlotStride + 1 + o] = o;
+            }
+            KF_TRY(dev_alloc(p.m2m_tiles, std::max<size_t>(mt.size(), 1) * sizeof(int4)));
+            KF_TRY(dev_alloc(p.m2m_slots, ms.size() * 4));
+            KF_TRY(dev_alloc(p.stage32, (size_t)nb * R * 4));
+            if (!mt.empty())
+                KF_CUDA(cudaMemcpyAsync(p.m2m_tiles.p, mt.data(), mt.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+            KF_CUDA(cudaMemcpyAsync(p.m2m_slots.p, ms.data(), ms.size() * 4, cudaMemcpyHostToDevice, st));
         }
         KF_CUDA(cudaStreamSynchronize(st));
     }
@@ -1389,7 +1446,28 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     mark(p, 2);
     for (int l = L - 1; l >= 2; --l) {
         auto& LL = p.lv[l];
-        if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
+        if (LL.n_par > 0 && mixed && p.m2m_tc && p.m2m_count[l] > 0) {
+            // tensor cores: the children's c split FP16 x 3 (the M2L operand buffers, rewritten
+            // before M2L), 8 octant slots per parent tile, staged in FP32, copied to the check rows
+            const int64_t lo = t.level_start[l + 1], cnt = t.level_start[l + 2] - lo;
+            KF_TRY(m2l_tc_split(st, cu + lo * R, cnt, R, static_cast<char*>(p.chi.p) + lo * R * 2,
+                                static_cast<char*>(p.clo.p) + lo * R * 2, ptr<int>(p.cexp) + lo));
+            ++nl;
+            M2LTables tabs{};
+            tabs.hi[l] = p.ops[l].Mhi.p;
+            tabs.lo[l] = p.ops[l].Mlo.p;
+            tabs.sT[l] = p.ops[l].m2m_sT;
+            RUN(launch_tc_translate(st, tabs, R, ptr<int4>(p.m2m_tiles) + p.m2m_first[l], p.m2m_count[l],
+                                    ptr<int32_t>(LL.parents), ptr<int32_t>(t.child), 8,
+                                    ptr<int32_t>(p.m2m_slots) + (int64_t)p.m2m_first[l] * kSlotStride, p.chi.p,
+                                    p.clo.p, ptr<int>(p.cexp), ptr<float>(p.stage32), 0, ptr<int>(p.err)));
+            rows_f2d<<<nbk((int64_t)LL.n_par * S, 256), 256, 0, st>>>(ptr<int32_t>(LL.parents), LL.n_par,
+                                                                     ptr<float>(p.stage32), R,
+                                                                     p.cheb ? cu : ptr<double>(p.chk),
+                                                                     p.cheb ? R : S, S);
+            KF_LAUNCH();
+            ++nl;
+        } else if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
             const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms + tiles - 1) / tiles));

@@ -106,6 +106,9 @@ struct LevelOps {
     // tensor-core L2L (parent level = this level): FP16 hi/lo of Lo 2^l2l_sT, 8 slots
     DevBuf Lhi, Llo;
     int l2l_sT = 0;
+    // tensor-core M2M translations (parent level = this level): FP16 hi/lo of Mc (rows padded to R)
+    DevBuf Mhi, Mlo;
+    int m2m_sT = 0;
     // FP64-exact upward solve on the tensor cores: integer slices of G1 (swizzled images) and
     // the per-row power-of-two exponents
     DevBuf ozG1, ozEr;
@@ -175,6 +178,9 @@ struct Plan {
     bool l2l_tc = false;         // L2L through the same kernel (mixed form)
     DevBuf ptab, l2l_slots;      // i32[nb][8] parent at the box's octant slot; per-tile L2L slot lists
     int tc_first[kMaxLevel + 1] = {0}, tc_count[kMaxLevel + 1] = {0};   // M2L tiles of each level
+    bool m2m_tc = false;         // M2M translations through the same kernel (mixed form)
+    DevBuf m2m_tiles, m2m_slots, stage32;   // parent tiles per level, their 8 slots, FP32 staging [nb][R]
+    int m2m_first[kMaxLevel + 1] = {0}, m2m_count[kMaxLevel + 1] = {0};
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses

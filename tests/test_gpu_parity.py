@@ -223,8 +223,8 @@ def test_near_field_lattice_detection(kf):
 
 @pytest.mark.parametrize("adaptive", [False, True])
 def test_l2l_tensor_cores_against_simt(kf, monkeypatch, adaptive):
-    # L2L through the tensor-core translation kernel (parents' d split FP16 x 3, added onto the
-    # children's M2L result) against the SIMT FP32 apply and the FP64 form
+    # L2L and the M2M translations through the tensor-core translation kernel (FP16 x 3 splits;
+    # L2L added onto the children's M2L result) against the SIMT FP32 applies and the FP64 form
     if adaptive:
         pts, h = _adaptive_small()
         I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
@@ -238,6 +238,7 @@ def test_l2l_tensor_cores_against_simt(kf, monkeypatch, adaptive):
     s64 = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform).eval(Id).cpu().numpy()
     stc = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform, precision="mixed").eval(Id).cpu().numpy()
     monkeypatch.setenv("KIFMM_L2L", "simt")
+    monkeypatch.setenv("KIFMM_M2M", "simt")
     ssimt = _plan(kf, pts, h, leaf, 6, a, b, uniform=uniform, precision="mixed").eval(Id).cpu().numpy()
     assert _relerr(stc, s64) <= 1e-6
     assert _relerr(stc, ssimt) <= 1e-6
