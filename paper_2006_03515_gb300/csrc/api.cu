@@ -36,7 +36,7 @@ static void free_plan(Plan* p) {
         for (DevBuf* b : {&o.G1, &o.Vb, &o.Ub, &o.Vt, &o.T, &o.Mc, &o.Lo, &o.T32, &o.Ub32, &o.Vb32, &o.Vt32, &o.Lo32, &o.Mc32, &o.ozG1, &o.ozEr,
                           &o.Thi, &o.Tlo, &o.Lhi, &o.Llo, &o.Mhi, &o.Mlo})
             dev_free(*b);
-    for (DevBuf* b : {&p->surf, &p->ctab, &p->ctab32, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
+    for (DevBuf* b : {&p->surf, &p->ctab, &p->ctab32, &p->cheb_A, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
                       &p->tc_tiles, &p->tc_boxes, &p->tc_slots, &p->ptab, &p->l2l_slots, &p->m2m_tiles, &p->m2m_slots, &p->stage32, &p->nf_utab, &p->nf_Thi, &p->nf_Tlo, &p->nf_tiles,

@@ -1082,6 +1082,96 @@ __global__ void __launch_bounds__(L2P_T) k_l2p_cheb(EvalView E, const int32_t* l
     }
 }
 
+// Chebyshev M2M and L2L by the tensor-product structure of the interpolation:
+//   M_o = A[oz] (x) A[oy] (x) A[ox],  A[b][n][m] = S(0.5 (2b - 1) + 0.5 xbar_m, xbar_n),
+// applied as three passes of p-term sums (x, then y, then z): 3 p^4 instead of p^6 products.
+constexpr int KR_T = 256, KR_MAXS = kChebMaxP * kChebMaxP * kChebMaxP;
+// W^P = sum_o M_o W^{C_o} for the listed parents (node weights in cu, rows of stride R);
+// one block per parent, arithmetic in F
+template <class F>
+__global__ void __launch_bounds__(KR_T) k_cheb_m2m_kron(const int32_t* __restrict__ parents,
+                                                      const int32_t* __restrict__ child, const double* __restrict__ Ag,
+                                                      int p, double* cu, int R) {
+    const int P = parents[blockIdx.x];
+    const int S = p * p * p, p2 = p * p;
+    __shared__ F A[2 * kChebMaxP * kChebMaxP];
+    __shared__ F w[KR_MAXS], t1[KR_MAXS], t2[KR_MAXS];
+    for (int e = threadIdx.x; e < 2 * p2; e += KR_T) A[e] = (F)Ag[e];
+    F acc[(KR_MAXS + KR_T - 1) / KR_T] = {};
+    for (int o = 0; o < 8; ++o) {
+        const int C = child[8 * (int64_t)P + o];
+        if (C < 0) continue;   // the same for the whole block
+        const F* Ax = A + (o & 1) * p2;
+        const F* Ay = A + ((o >> 1) & 1) * p2;
+        const F* Az = A + ((o >> 2) & 1) * p2;
+        __syncthreads();
+        for (int n = threadIdx.x; n < S; n += KR_T) w[n] = (F)cu[(int64_t)C * R + n];
+        __syncthreads();
+        for (int n = threadIdx.x; n < S; n += KR_T) {   // t1[mz][my][nx] = sum_mx A_x[nx][mx] w[mz][my][mx]
+            const int nx = n % p, r = n - nx;
+            F v = 0;
+            for (int m = 0; m < p; ++m) v += Ax[nx * p + m] * w[r + m];
+            t1[n] = v;
+        }
+        __syncthreads();
+        for (int n = threadIdx.x; n < S; n += KR_T) {   // t2[mz][ny][nx] = sum_my A_y[ny][my] t1[mz][my][nx]
+            const int nx = n % p, ny = (n / p) % p, mz = n / p2;
+            F v = 0;
+            for (int m = 0; m < p; ++m) v += Ay[ny * p + m] * t1[mz * p2 + m * p + nx];
+            t2[n] = v;
+        }
+        __syncthreads();
+        for (int k = 0, n = threadIdx.x; n < S; ++k, n += KR_T) {   // += sum_mz A_z[nz][mz] t2[mz][ny][nx]
+            const int nz = n / p2, q = n % p2;
+            F v = 0;
+            for (int m = 0; m < p; ++m) v += Az[nz * p + m] * t2[m * p2 + q];
+            acc[k] += v;
+        }
+    }
+    for (int k = 0, n = threadIdx.x; n < S; ++k, n += KR_T) cu[(int64_t)P * R + n] = (double)acc[k];
+}
+
+// g^C += M_o^T g^P for the boxes lo .. lo + gridDim.x - 1 (all of one level >= 3; o the box's
+// octant in its parent), local node values in d (rows of stride R); one block per box
+template <class TD>
+__global__ void __launch_bounds__(KR_T) k_cheb_l2l_kron(int64_t lo, const int32_t* __restrict__ parent,
+                                                      const int32_t* __restrict__ anchor, const double* __restrict__ Ag,
+                                                      int p, TD* d, int R) {
+    using F = TD;
+    const int64_t C = lo + blockIdx.x;
+    const int P = parent[C];
+    const int o = (anchor[3 * C] & 1) | ((anchor[3 * C + 1] & 1) << 1) | ((anchor[3 * C + 2] & 1) << 2);
+    const int S = p * p * p, p2 = p * p;
+    __shared__ F A[2 * kChebMaxP * kChebMaxP];
+    __shared__ F g[KR_MAXS], t1[KR_MAXS], t2[KR_MAXS];
+    for (int e = threadIdx.x; e < 2 * p2; e += KR_T) A[e] = (F)Ag[e];
+    for (int n = threadIdx.x; n < S; n += KR_T) g[n] = d[(int64_t)P * R + n];
+    __syncthreads();
+    const F* Ax = A + (o & 1) * p2;
+    const F* Ay = A + ((o >> 1) & 1) * p2;
+    const F* Az = A + ((o >> 2) & 1) * p2;
+    for (int m = threadIdx.x; m < S; m += KR_T) {   // t1[nz][ny][mx] = sum_nx A_x[nx][mx] g[nz][ny][nx]
+        const int mx = m % p, r = m - mx;
+        F v = 0;
+        for (int n = 0; n < p; ++n) v += Ax[n * p + mx] * g[r + n];
+        t1[m] = v;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < S; m += KR_T) {   // t2[nz][my][mx] = sum_ny A_y[ny][my] t1[nz][ny][mx]
+        const int mx = m % p, my = (m / p) % p, nz = m / p2;
+        F v = 0;
+        for (int n = 0; n < p; ++n) v += Ay[n * p + my] * t1[nz * p2 + n * p + mx];
+        t2[m] = v;
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < S; m += KR_T) {   // d^C[mz][my][mx] += sum_nz A_z[nz][mz] t2[nz][my][mx]
+        const int mz = m / p2, q = m % p2;
+        F v = 0;
+        for (int n = 0; n < p; ++n) v += Az[n * p + mz] * t2[n * p2 + q];
+        d[C * R + m] += v;
+    }
+}
+
 // Near field (Eq. (nearfar), first sum) over U(B), plus the far part, the self term and
 // the scale C; writes the result in the caller's order. One block per leaf:
 // 64 targets x 4 source groups; sources staged in shared memory, B-local coordinates.
@@ -1446,7 +1536,16 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     mark(p, 2);
     for (int l = L - 1; l >= 2; --l) {
         auto& LL = p.lv[l];
-        if (LL.n_par > 0 && mixed && p.m2m_tc && p.m2m_count[l] > 0) {
+        if (LL.n_par > 0 && p.cheb) {   // Chebyshev: three 1-D passes per child, straight into c
+            if (mixed)
+                k_cheb_m2m_kron<float><<<LL.n_par, KR_T, 0, st>>>(ptr<int32_t>(LL.parents), ptr<int32_t>(t.child),
+                                                                  ptr<double>(p.cheb_A), p.m0, cu, R);
+            else
+                k_cheb_m2m_kron<double><<<LL.n_par, KR_T, 0, st>>>(ptr<int32_t>(LL.parents), ptr<int32_t>(t.child),
+                                                                   ptr<double>(p.cheb_A), p.m0, cu, R);
+            KF_LAUNCH();
+            ++nl;
+        } else if (LL.n_par > 0 && mixed && p.m2m_tc && p.m2m_count[l] > 0) {
             // tensor cores: the children's c split FP16 x 3 (the M2L operand buffers, rewritten
             // before M2L), 8 octant slots per parent tile, staged in FP32, copied to the check rows
             const int64_t lo = t.level_start[l + 1], cnt = t.level_start[l + 2] - lo;
@@ -1552,7 +1651,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         if (l >= 3) {
             auto& LP = p.lv[l - 1];
             const LevelOps& pop = p.ops[l - 1];
-            if (LP.l2l_max > 0 && sizeof(T) == 4 && p.l2l_tc && p.tc_count[l] > 0) {
+            if (LP.l2l_max > 0 && p.cheb) {   // Chebyshev: three 1-D passes per child
+                const int64_t lo = t.level_start[l], cnt = t.level_start[l + 1] - lo;
+                k_cheb_l2l_kron<T><<<(unsigned)cnt, KR_T, 0, st>>>(lo, ptr<int32_t>(t.parent), ptr<int32_t>(t.anchor),
+                                                                   ptr<double>(p.cheb_A), p.m0, dd, R);
+                KF_LAUNCH();
+                ++nl;
+            } else if (LP.l2l_max > 0 && sizeof(T) == 4 && p.l2l_tc && p.tc_count[l] > 0) {
                 // tensor cores: the parents' d split into FP16 hi / lo (the M2L operand buffers, free
                 // by now), one slot per child octant, added onto the children's d
                 const int64_t lo = t.level_start[l - 1], cnt = t.level_start[l] - lo;

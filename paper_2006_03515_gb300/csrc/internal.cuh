@@ -128,6 +128,7 @@ struct Plan {
     std::vector<LevelOps> ops;    // indexed by level (entries below 2 unused)
     DevBuf surf;                  // f64[3*S] unit lattice (Chebyshev representation: the p^3 nodes)
     DevBuf ctab, ctab32;          // f64 / f32 [p][10]: c_k T_k(node_n), c_0 = 1/p, c_k = 2/p (Chebyshev only)
+    DevBuf cheb_A;                // f64 [2][p][p]: 1-D factors of the M2M / L2L interpolation (Chebyshev only)
     // per-point data in sorted order
     DevBuf pts;       // f64[3n] sorted coordinates
     DevBuf loc32;     // f32[4n] coordinates relative to the leaf centre (x, y, z, pad)

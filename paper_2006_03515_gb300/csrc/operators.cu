@@ -260,6 +260,18 @@ __global__ void cheb_m2m(int p, int S, int R, const double* s, const double* tab
     Lo[((int64_t)o * R + m) * R + n] = v;
 }
 
+// The 1-D factors of M_o: A[b][n][m] = S(0.5 (2b - 1) + 0.5 xbar_m, xbar_n), b = 0, 1 (the
+// child in the lower / upper half of the parent along an axis); M_o = A[oz] (x) A[oy] (x) A[ox].
+__global__ void cheb_factors(int p, const double* tab, double* A) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 2 * p * p) return;
+    const int b = e / (p * p), n = (e / p) % p, m = e % p;
+    const double xm = cos((2 * m + 1) * 3.14159265358979323846 / (2.0 * p));
+    double t[kChebMaxP];
+    cheb_T(0.5 * (2.0 * b - 1.0) + 0.5 * xm, p, t);
+    A[e] = cheb_S(t, p, tab + n * kChebTab);
+}
+
 // out[mat][i][j] = in[mat][i][j] for i, j < S (row stride S -> R); the padding stays zero.
 __global__ void pad_square(const double* in, int S, int R, int nmat, double* out) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -308,6 +320,9 @@ static int build_operators_cheb(Plan& p) {
     KF_TRY(dev_alloc(lo, 8 * RR * 8));
     KF_CUDA(cudaMemsetAsync(mc.p, 0, 8 * (int64_t)S * R * 8, st));
     KF_CUDA(cudaMemsetAsync(lo.p, 0, 8 * RR * 8, st));
+    KF_TRY(dev_alloc(p.cheb_A, 2 * kChebMaxP * kChebMaxP * sizeof(double)));
+    cheb_factors<<<nb(2 * pc * pc, 128), 128, 0, st>>>(pc, ptr<double>(p.ctab), ptr<double>(p.cheb_A));
+    KF_LAUNCH();
     cheb_m2m<<<nb(8 * SS, 256), 256, 0, st>>>(pc, S, R, ptr<double>(p.surf), ptr<double>(p.ctab), ptr<double>(mc),
                                               ptr<double>(lo));
     KF_LAUNCH();
