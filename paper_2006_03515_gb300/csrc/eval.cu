@@ -1517,7 +1517,10 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         const int64_t b0 = t.level_start[2], b1 = t.level_start[L - 1];
         KF_CUDA(cudaMemsetAsync(ptr<double>(p.chk) + b0 * S, 0, (size_t)(b1 - b0) * S * 8, st));
     }
-    if (p.n_p2m > 0 && p.cheb) {   // node weights of the leaves, straight into c
+    if (p.n_p2m > 0 && p.cheb && p.lat_far) {   // lattice: one interpolation matrix for every leaf
+        KF_TRY(lat_s2m(p));
+        ++nl;
+    } else if (p.n_p2m > 0 && p.cheb) {   // node weights of the leaves, straight into c
         auto* kp2m = mixed ? k_p2m_cheb<true> : k_p2m_cheb<false>;
         kp2m<<<(unsigned)p.n_p2m, CP_T, 0, st>>>(E, ptr<int32_t>(p.p2m_boxes), ptr<double>(p.q), cu, R);
         KF_LAUNCH();
@@ -1735,7 +1738,7 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         const int32_t* wi = ptr<int32_t>(p.lists[2].items);
         // Chebyshev: the W list reads the node weights c (stride R) and the local part
         // interpolates d in a second kernel
-        if (p.lat_far && t.nlevels > 2) {   // uniform lattice, no W list: the local expansion is one matrix
+        if (p.lat_far && !p.cheb && t.nlevels > 2) {   // uniform lattice, no W list: the local part is one matrix from d
             KF_TRY(lat_l2p(p));
         } else if (mixed) {
             auto* kl2p = p.far_series ? k_l2p<true, true, float> : k_l2p<true, false, float>;
@@ -1749,7 +1752,7 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         }
         KF_LAUNCH();
         ++nl;
-        if (p.cheb && t.nlevels > 2) {
+        if (p.cheb && t.nlevels > 2) {   // (on a lattice the 512-row matrix kernel was slower than this)
             if (mixed)
                 k_l2p_cheb<true, float><<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), ptr<float>(p.dd),
                                                                               p.R, ptr<double>(p.far));

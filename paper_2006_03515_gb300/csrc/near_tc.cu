@@ -18,6 +18,7 @@
 
 #include "internal.cuh"
 #include "kernel.cuh"
+#include "cheb.cuh"
 
 namespace kifmm {
 
@@ -126,8 +127,10 @@ __global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int n
 constexpr int LT_T = 128, LT_LV = 8;   // threads; leaves per pass of the S2M kernel
 constexpr int LT_LT = 4;               // leaves per thread and pass of the L2P kernel
 
-// the matrix into shared memory: 16-byte loads, several in flight per thread (n4 float4)
-__device__ __forceinline__ void lat_load(const float* __restrict__ P, float* Ps, int n4) {
+// the matrix (n floats) into shared memory: 16-byte loads, several in flight per thread, and
+// the last n % 4 floats one by one
+__device__ __forceinline__ void lat_load(const float* __restrict__ P, float* Ps, int n) {
+    const int n4 = n / 4;
     const float4* src = reinterpret_cast<const float4*>(P);
     float4* dst = reinterpret_cast<float4*>(Ps);
     int e = threadIdx.x;
@@ -139,17 +142,18 @@ __device__ __forceinline__ void lat_load(const float* __restrict__ P, float* Ps,
         dst[e + 3 * LT_T] = d;
     }
     for (; e < n4; e += LT_T) dst[e] = src[e];
+    for (int k = 4 * n4 + threadIdx.x; k < n; k += LT_T) Ps[k] = P[k];
 }
 
 // chk[leaf B][j] = sum_i P[j][i] q[B][i]; rows j over the threads (P rows padded to npl + 1
 // floats: conflict-free), LT_LV leaves per pass sharing each P load
 __global__ void __launch_bounds__(LT_T) k_lat_s2m(const float* __restrict__ P, int S, int npl,
                                                   const int32_t* __restrict__ leaves, int64_t nl,
-                                                  const double* __restrict__ q, double* __restrict__ chk) {
+                                                  const double* __restrict__ q, double* __restrict__ chk, int ldo) {
     extern __shared__ float lsm[];
     float* Ps = lsm;                          // [S][npl + 1]
     float* qs = Ps + (int64_t)S * (npl + 1);   // [LT_LV][npl]
-    lat_load(P, Ps, S * (npl + 1) / 4);
+    lat_load(P, Ps, S * (npl + 1));
     for (int64_t o0 = (int64_t)blockIdx.x * LT_LV; o0 < nl; o0 += (int64_t)gridDim.x * LT_LV) {
         __syncthreads();
         for (int e = threadIdx.x; e < LT_LV * npl; e += LT_T) {
@@ -173,9 +177,30 @@ __global__ void __launch_bounds__(LT_T) k_lat_s2m(const float* __restrict__ P, i
             }
 #pragma unroll
             for (int l = 0; l < LT_LV; ++l)
-                if (o0 + l < nl) chk[(int64_t)leaves[o0 + l] * S + j] = k[l].value();
+                if (o0 + l < nl) chk[(int64_t)leaves[o0 + l] * ldo + j] = k[l].value();
         }
     }
+}
+
+// Chebyshev form on the lattice: P[m][i] = S3(xbar_m, u_i) and Q[m][i] = P[m][i] (the same
+// weights read the other way in L2P), u_i = ((c_i + 1/2) h - r) / r the cell centre in box units
+__global__ void k_lat_cheb_table(int p, const double* tab, const int32_t* ref, int nc, double r, double h, float* P,
+                                 float* Q) {
+    const int npl = nc * nc * nc, S = p * p * p;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)S * npl) return;
+    const int m = (int)(e / npl), i = (int)(e % npl);
+    const int ci = ref[i];
+    const int c3[3] = {ci % nc, (ci / nc) % nc, ci / (nc * nc)};
+    const int m3[3] = {m % p, (m / p) % p, m / (p * p)};
+    double w = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        double t[kChebMaxP];
+        cheb_T(((c3[a] + 0.5) * h - r) / r, p, t);
+        w *= cheb_S(t, p, tab + m3[a] * kChebTab);
+    }
+    P[(int64_t)m * (npl + 1) + i] = (float)w;
+    Q[(int64_t)m * (npl + 1) + i] = (float)w;
 }
 
 // Q[k][i] = sum_j P[j][i] Ub[j][k] in FP64, rounded once: the local expansion of a leaf
@@ -209,7 +234,7 @@ __global__ void __launch_bounds__(LT_T) k_lat_l2p(const float* __restrict__ P, i
     float* Ps = lsm;                          // [S][npl + 1]
     float* ps = Ps + (int64_t)S * (npl + 1);   // [LT_T / npl * LT_LT][S]
     const int lpp = LT_T / npl * LT_LT;
-    lat_load(P, Ps, S * (npl + 1) / 4);
+    lat_load(P, Ps, S * (npl + 1));
     const int grp = threadIdx.x / npl, i = threadIdx.x % npl;
     for (int64_t o0 = (int64_t)blockIdx.x * lpp; o0 < nl; o0 += (int64_t)gridDim.x * lpp) {
         __syncthreads();
@@ -248,11 +273,12 @@ __global__ void __launch_bounds__(LT_T) k_lat_l2p(const float* __restrict__ P, i
 static size_t lat_s2m_smem(int S, int npl) { return ((size_t)S * (npl + 1) + (size_t)LT_LV * npl) * 4; }
 static size_t lat_l2p_smem(int S, int npl) { return ((size_t)S * (npl + 1) + (size_t)(LT_T / npl) * LT_LT * S) * 4; }
 
-int lat_s2m(Plan& p) {
+int lat_s2m(Plan& p) {   // surface form: check potentials; Chebyshev: node weights straight into c
     const unsigned g = (unsigned)std::min<int64_t>((p.nleaves + LT_LV - 1) / LT_LV, 8LL * p.num_sms);
     k_lat_s2m<<<g, LT_T, lat_s2m_smem(p.S, p.nf_R), p.stream>>>(ptr<float>(p.lat_P), p.S, p.nf_R,
                                                                 ptr<int32_t>(p.leaves), p.nleaves, ptr<double>(p.q),
-                                                                ptr<double>(p.chk));
+                                                                p.cheb ? ptr<double>(p.cu) : ptr<double>(p.chk),
+                                                                p.cheb ? p.R : p.S);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -350,10 +376,26 @@ int near_tc_plan(Plan& p) {
     KF_TRY(dev_alloc(p.nf_Thi, (size_t)m2l_tc_table_elems(R) * 2));
     KF_TRY(dev_alloc(p.nf_Tlo, (size_t)m2l_tc_table_elems(R) * 2));
     KF_TRY(m2l_tc_prepare(st, ptr<double>(T), R, p.nf_Thi.p, p.nf_Tlo.p, &p.nf_sT));
-    // S2M and local L2P on the lattice: surface form, leaves at level >= 2, no W / X lists
+    // S2M (P2M) and local L2P on the lattice: leaves at level >= 2, no W / X lists. Surface
+    // form: the check matrix P and Q = P^T U Sigma^+; Chebyshev form: the interpolation
+    // weights S3(xbar_m, u_i) of the leaf's cells for P2M (its L2P keeps the interpolation
+    // kernel: with 512 rows the matrix kernel fits one block per SM and ran slower).
     p.lat_far = false;
+    const size_t lat_smem_max = 200 * 1024;
+    if (p.cheb && lf >= 2 && p.lists[2].len == 0 && p.lists[3].len == 0 && LT_T % npl == 0 &&
+        lat_s2m_smem(p.S, npl) <= lat_smem_max && lat_l2p_smem(p.R, npl) <= lat_smem_max) {
+        KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
+        KF_TRY(dev_alloc(p.lat_Q, (size_t)p.R * (npl + 1) * 4));
+        KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));
+        KF_CUDA(cudaMemsetAsync(p.lat_Q.p, 0, (size_t)p.R * (npl + 1) * 4, st));
+        k_lat_cheb_table<<<nbn((int64_t)p.S * npl, 128), 128, 0, st>>>(p.m0, ptr<double>(p.ctab), ptr<int32_t>(ref), nc,
+                                                                       r, h, ptr<float>(p.lat_P), ptr<float>(p.lat_Q));
+        KF_LAUNCH();
+        for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
+            KF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lat_smem_max));
+        p.lat_far = true;
+    }
     if (!p.cheb && lf >= 2 && p.lists[2].len == 0 && p.lists[3].len == 0 && LT_T % npl == 0 &&
-        ((int64_t)p.S * (npl + 1)) % 4 == 0 && ((int64_t)p.R * (npl + 1)) % 4 == 0 &&
         lat_s2m_smem(p.S, npl) <= 96 * 1024 && lat_l2p_smem(p.R, npl) <= 96 * 1024) {
         KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));

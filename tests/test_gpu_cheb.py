@@ -96,6 +96,7 @@ def test_mixed_cheb_matches_fp64(kf, p, po2):
     s64 = p64.eval(Id).cpu().numpy()
     s32 = p32.eval(Id).cpu().numpy()
     assert p32.info()["m2l_tensor"]
+    assert p32.info()["lattice_far"] and not p64.info()["lattice_far"]   # 64-cell leaves on a lattice
     p64.close()
     p32.close()
     assert _relerr(s32, s64) <= 1e-6
