@@ -1744,6 +1744,7 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         // interpolates d in a second kernel
         if (p.lat_far && !p.cheb && t.nlevels > 2) {   // uniform lattice, no W list: the local part is one matrix from d
             KF_TRY(lat_l2p(p));
+            if (p.lat_l2p_tc) ++nl;   // (the split of d, then the translation kernel)
         } else if (mixed) {
             auto* kl2p = p.far_series ? k_l2p<true, true, float> : k_l2p<true, false, float>;
             kl2p<<<(unsigned)p.nleaves, L2P_T, 0, st>>>(E, ptr<int32_t>(p.leaves), wo, wi, ptr<float>(p.phid),

@@ -193,6 +193,9 @@ struct Plan {
     bool lat_far = false;        // S2M and local L2P on the same lattice (surface form, no W / X lists)
     DevBuf lat_P;                // f32 [S][npl + 1]: K between the leaf's check surface and its cells
     DevBuf lat_Q;                // f32 [R][npl + 1]: P^T Ub, the leaf's local expansion from its coefficients d
+    bool lat_l2p_tc = false;     // that expansion through the tensor-core kernel (FP32 rows in lat_fst)
+    DevBuf lat_Thi, lat_Tlo, lat_iota, lat_slots, lat_fst;
+    int lat_sT = 0;
     bool lat_up = false;         // leaves' c = (G1 P) q on the tensor cores, FP64-exact (no leaf S2M)
     DevBuf lat_Mimg, lat_Mer;    // slice image and row exponents of M = G1 P (rank x npl)
     bool far_series = true;      // likewise for a leaf's points and its check / equivalent surfaces

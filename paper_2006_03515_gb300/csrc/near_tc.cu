@@ -91,13 +91,43 @@ __global__ void k_nf_table(const int32_t* ref, int nc, int R, double h, KParams 
     T[((int64_t)slot * R + i) * R + j] = rr > 0.0 ? kern_f64(rr, kp) : 0.0;
 }
 
-// S in the caller's order: C (near + far + sigma I)
+// S in the caller's order: C (near + far + sigma I); the far part from far[i], or, when fst is
+// given, from the FP32 rows of the tensor-core L2P (row of the leaf's box, npl cells, stride R)
 template <class TO>
-__global__ void k_nf_finish(const float* near, const double* far, const double* sigma, const double* Is,
-                            const int32_t* perm, int64_t n, double C, TO* out) {
+__global__ void k_nf_finish(const float* near, const double* far, const float* fst, const int32_t* leaves, int npl,
+                            int R, const double* sigma, const double* Is, const int32_t* perm, int64_t n, double C,
+                            TO* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    out[perm[i]] = (TO)(C * ((double)near[i] + far[i] + sigma[i] * Is[i]));
+    const double fa = fst ? (double)fst[(int64_t)leaves[i / npl] * R + i % npl] : far[i];
+    out[perm[i]] = (TO)(C * ((double)near[i] + fa + sigma[i] * Is[i]));
+}
+
+// T[i][k] = sum_j P[j][i] Ub[j][k] in FP64 for i < npl, k < R: the leaf's local expansion from
+// its d as the square table [1][R][R] of the tensor-core kernel (rows >= npl zero)
+__global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+                         double h, KParams kp, double* T) {
+    const int npl = nc * nc * nc;
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)npl * R) return;
+    const int i = (int)(e / R), k = (int)(e % R);
+    const int ci = ref[i];
+    const double y[3] = {(ci % nc + 0.5) * h - r, ((ci / nc) % nc + 0.5) * h - r, (ci / (nc * nc) + 0.5) * h - r};
+    double sum = 0.0;
+    for (int j = 0; j < S; ++j) {
+        double d2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            const double d = kROuter * r * surf[3 * j + a] - y[a];
+            d2 += d * d;
+        }
+        sum += kern_f64(sqrt(d2), kp) * Ub[(int64_t)j * R + k];
+    }
+    T[(int64_t)i * R + k] = sum;
+}
+
+__global__ void k_iota(int32_t* v, int64_t n) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) v[e] = (int32_t)e;
 }
 
 // ------------------------------------------------------------------------------------
@@ -284,6 +314,20 @@ int lat_s2m(Plan& p) {   // surface form: check potentials; Chebyshev: node weig
 }
 
 int lat_l2p(Plan& p) {
+    if (p.lat_l2p_tc) {   // tensor cores: the leaves' d split FP16 x 3, one slot (the leaf itself)
+        cudaStream_t st = p.stream;
+        const int R = p.R, lf = p.nf_level;
+        const int64_t lo = p.tree.level_start[lf], cnt = p.tree.level_start[lf + 1] - lo;
+        KF_TRY(m2l_tc_split_f32(st, ptr<float>(p.dd) + lo * R, cnt, R, static_cast<char*>(p.chi.p) + lo * R * 2,
+                                static_cast<char*>(p.clo.p) + lo * R * 2, ptr<int>(p.cexp) + lo));
+        M2LTables tabs{};
+        tabs.hi[lf] = p.lat_Thi.p;
+        tabs.lo[lf] = p.lat_Tlo.p;
+        tabs.sT[lf] = p.lat_sT;
+        return launch_tc_translate(st, tabs, R, ptr<int4>(p.nf_tiles), p.nf_ntiles, ptr<int32_t>(p.leaves),
+                                   ptr<int32_t>(p.lat_iota), 1, ptr<int32_t>(p.lat_slots), p.chi.p, p.clo.p,
+                                   ptr<int>(p.cexp), ptr<float>(p.lat_fst), 0, ptr<int>(p.err));
+    }
     const int lpp = LT_T / p.nf_R * LT_LT;
     const unsigned g = (unsigned)std::min<int64_t>((p.nleaves + lpp - 1) / lpp, 8LL * p.num_sms);
     k_lat_l2p<<<g, LT_T, lat_l2p_smem(p.R, p.nf_R), p.stream>>>(ptr<float>(p.lat_Q), p.R, p.nf_R,
@@ -411,6 +455,27 @@ int near_tc_plan(Plan& p) {
         for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
             KF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
         p.lat_far = true;
+        // the same local expansion through the tensor-core kernel (mixed form with the tensor M2L)
+        if (p.m2l_tensor) {
+            DevBuf QT;
+            const int64_t RR = (int64_t)p.R * p.R;
+            KF_TRY(dev_alloc(QT, RR * 8));
+            KF_CUDA(cudaMemsetAsync(QT.p, 0, RR * 8, st));
+            k_lat_QT<<<nbn((int64_t)npl * p.R, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R,
+                                                                    ptr<double>(p.surf), ptr<int32_t>(ref), nc, r, h,
+                                                                    make_kparams(p.a, p.b), ptr<double>(QT));
+            KF_LAUNCH();
+            KF_TRY(dev_alloc(p.lat_Thi, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
+            KF_TRY(dev_alloc(p.lat_Tlo, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
+            KF_TRY(m2l_tc_prepare(st, ptr<double>(QT), p.R, p.lat_Thi.p, p.lat_Tlo.p, &p.lat_sT, 1));
+            KF_TRY(dev_alloc(p.lat_iota, (size_t)t.nboxes * 4));
+            k_iota<<<nbn(t.nboxes, 256), 256, 0, st>>>(ptr<int32_t>(p.lat_iota), t.nboxes);
+            KF_LAUNCH();
+            KF_TRY(dev_alloc(p.lat_fst, (size_t)t.nboxes * p.R * 4));
+            KF_CUDA(cudaStreamSynchronize(st));
+            dev_free(QT);
+            p.lat_l2p_tc = true;
+        }
     }
     // tiles of 128 leaves (ordinals), every tile over the 27 near slots
     const int ntiles = (int)((nl + 127) / 128);
@@ -426,6 +491,12 @@ int near_tc_plan(Plan& p) {
                 for (int dx = -1; dx <= 1; ++dx) s[1 + c++] = (dx + 3) + 7 * (dy + 3) + 49 * (dz + 3);
     }
     for (int64_t o = 0; o < nl; ++o) ids[o] = (int32_t)o;
+    if (p.lat_l2p_tc) {   // one slot (0) per leaf tile
+        std::vector<int32_t> ls((size_t)ntiles * kSlotStride, 0);
+        for (int k = 0; k < ntiles; ++k) ls[(size_t)k * kSlotStride] = 1;
+        KF_TRY(dev_alloc(p.lat_slots, ls.size() * 4));
+        KF_CUDA(cudaMemcpyAsync(p.lat_slots.p, ls.data(), ls.size() * 4, cudaMemcpyHostToDevice, st));
+    }
     KF_TRY(dev_alloc(p.nf_tiles, tiles.size() * sizeof(int4)));
     KF_TRY(dev_alloc(p.nf_slots, slots.size() * 4));
     KF_TRY(dev_alloc(p.nf_boxes, ids.size() * 4));
@@ -514,14 +585,15 @@ int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int
                          ptr<int32_t>(p.nf_utab), ptr<int32_t>(p.nf_slots), p.nf_qhi.p, p.nf_qlo.p, ptr<int>(p.nf_qexp),
                          ptr<float>(p.nf_near), ptr<int>(p.err)));
     ++nl;
+    const float* fst = p.lat_l2p_tc && p.tree.nlevels > 2 ? ptr<float>(p.lat_fst) : nullptr;
     if (dtype == KIFMM_F64)
-        k_nf_finish<double><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, ptr<double>(p.sigma),
-                                                          ptr<double>(p.Isort), ptr<int32_t>(p.tree.perm), n, C,
-                                                          (double*)out);
+        k_nf_finish<double><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, fst, ptr<int32_t>(p.leaves),
+                                                          p.nf_R, p.R, ptr<double>(p.sigma), ptr<double>(p.Isort),
+                                                          ptr<int32_t>(p.tree.perm), n, C, (double*)out);
     else
-        k_nf_finish<float><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, ptr<double>(p.sigma),
-                                                         ptr<double>(p.Isort), ptr<int32_t>(p.tree.perm), n, C,
-                                                         (float*)out);
+        k_nf_finish<float><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, fst, ptr<int32_t>(p.leaves),
+                                                         p.nf_R, p.R, ptr<double>(p.sigma), ptr<double>(p.Isort),
+                                                         ptr<int32_t>(p.tree.perm), n, C, (float*)out);
     KF_LAUNCH();
     ++nl;
     return KIFMM_OK;
