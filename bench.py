@@ -43,9 +43,9 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 298.49e6 + 16.35e6, "per_point_scaled": False,
+    "M2L": {"bytes": 294.35e6 + 15.78e6, "per_point_scaled": False,
             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                    "837ac8f7aaae46c4879bac8f12da2434c7c90825c9193afdfc49dc526d7cb6ff"},
+                    "2ffb91f9a4dea07dc82e24e15bdf61e488af75b66461db81dc1f66a25cacfeb5"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
     "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
             "src": {"paper_2006_03515_gb300/csrc/eval.cu":
@@ -53,9 +53,9 @@ PROFILED_TRAFFIC = {
             "profile": "profiles/k_p2p_mixed_uniform64.md"},
     "NEAR": {"bytes": 3.96e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                     "837ac8f7aaae46c4879bac8f12da2434c7c90825c9193afdfc49dc526d7cb6ff",
+                     "2ffb91f9a4dea07dc82e24e15bdf61e488af75b66461db81dc1f66a25cacfeb5",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "159f283307f77a604c237c7e3a0d8b176e5fd836ec7f4153e7d358ee06595854"},
+                     "7cae7202a1f896bb7464b087e87ecfe7d5ae56537430f871ce0745f6280a02b8"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
