@@ -55,7 +55,7 @@ PROFILED_TRAFFIC = {
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
                      "2ffb91f9a4dea07dc82e24e15bdf61e488af75b66461db81dc1f66a25cacfeb5",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "7cae7202a1f896bb7464b087e87ecfe7d5ae56537430f871ce0745f6280a02b8"},
+                     "f08f41d9d97141fe66e00209fbdd2216de47a074e67bcb1ae3362ed1dab17eff"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 

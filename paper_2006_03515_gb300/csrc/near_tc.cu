@@ -11,6 +11,16 @@
 // The 27 matrices (R = nc^3 rows) go through the tensor-core translation kernel of M2L
 // (FP16 x 3 split, per-offset FP32 accumulators), with the leaves' weight rows as its
 // coefficient rows. Plans whose points are not such a lattice use the pair kernel.
+//
+// On the same lattice (leaves at level >= 2, no W or X lists) every leaf also shares the
+// operators between its cells and its own surfaces or nodes, tabulated here in FP64:
+//  * S2M: the check matrix P[j][i] = K(|2.6 r s_j - y_i|) (surface form), or the P2M
+//    interpolation weights S3(xbar_m, u_i) (Chebyshev form), applied per leaf in FP32;
+//  * the leaves' upward coefficients c = (G1 P) q, sliced exactly on the tensor cores like
+//    the other upward solves (surface form, FP64 accuracy, no check potentials);
+//  * the local part of L2P from the leaves' d through Q = P^T U Sigma^+ (surface form), on
+//    the tensor cores or in FP32.
+// In exact arithmetic each is the generic path's operator, reassociated.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
