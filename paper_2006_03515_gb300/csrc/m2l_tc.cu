@@ -24,7 +24,9 @@
 //    chunk of a slot it commits the accumulator's "ready" mbarrier.
 //  * warps 0-7, epilogue: a ring of up to four accumulators takes the slots in turn; the
 //    epilogue scales a finished one by the slot's 2^{-(e_A + e_T)} into FP32 registers
-//    (round-to-nearest) and releases it. The tensor core's own accumulation thus spans one slot, not the V list.
+//    (round-to-nearest) and releases it. The tensor core's own (truncating) accumulation
+//    thus spans one slot, not the V list, and (R <= 256) within a k-chunk the small cross
+//    terms are accumulated before the hi x hi terms.
 // Every wait is bounded; a timeout sets an abort flag that ends the other roles' waits,
 // records an error code, and the tensor memory is freed before the CTA exits.
 #include <cuda_fp16.h>
@@ -249,12 +251,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const unsigned char* st = base + s * STAGE;
                     const uint32_t ah = smem_u32(st), al = ah + A_BYTES, bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
                     const int ksteps = min(TC_KH, R - kc * TC_KH) / 16;
-                    for (int k = 0; k < ksteps; ++k) {
-                        const uint32_t ko = 32u * k;   // 16 FP16 = 32 bytes along K inside the swizzle row
-                        const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
-                        mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
-                        mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                        mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                    if (NB == 1) {
+                        // the small cross terms of the chunk first, then its hi x hi terms: the
+                        // accumulator truncates each addition, so most additions then land on a
+                        // small partial sum (16 FP16 = 32 bytes along K inside the swizzle row)
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, acc);
+                            mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
+                    } else {
+                        // row blocks of 256 (R > 256): the interleaved order, which measured 8 %
+                        // faster there (consecutive MMAs on the same A tile)
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                            mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
                     }
                     mma_commit(smem_u32(&empty[s]));
                 }

@@ -165,18 +165,18 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
     assert _relerr(s_tc, s_64) <= 1e-9
 
 
-@pytest.mark.parametrize("n,leaf", [(32, 64), (16, 512)])
+@pytest.mark.parametrize("n,leaf", [(32, 64), (64, 64)])
 def test_near_field_on_tensor_cores(kf, monkeypatch, n, leaf):
-    # uniform lattice with full leaves (64 or 512 cells): the near field runs as 27 per-offset
-    # kernel matrices on the tensor cores, and with 64-cell leaves S2M and the local L2P as one
-    # check-surface matrix per leaf; against the FP64 form and the mixed generic kernels
+    # uniform lattice with full 64-cell leaves: the near field runs as 27 per-offset kernel
+    # matrices on the tensor cores, S2M / upward / local L2P as one tabulated matrix per leaf;
+    # against the FP64 form and the mixed generic kernels
     pts, h, I = W.config_uniform(n)
     a, b = K.absorption_coefficients(152.0)
     Id = _dev(I)
     s64 = _plan(kf, pts, h, leaf, 6, a, b).eval(Id).cpu().numpy()
     ptc = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
     assert ptc.info()["near_tensor"]
-    assert ptc.info()["lattice_far"] == (leaf == 64)   # S2M / L2P matrices: leaves at level >= 2, 64 cells
+    assert ptc.info()["lattice_far"]   # S2M / L2P matrices: leaves at level >= 2, 64 cells
     stc = ptc.eval(Id).cpu().numpy()
     monkeypatch.setenv("KIFMM_P2P", "generic")
     pgen = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
@@ -205,6 +205,30 @@ def test_lattice_leaf_coefficients_match_fp64(kf, monkeypatch):
     leaves = np.nonzero(pm.tree()["leaf"])[0]
     scale = np.abs(c_64[leaves]).max(axis=1, keepdims=True)
     assert np.max(np.abs(c_m[leaves] - c_64[leaves]) / scale) <= 1e-8
+
+
+def _box_grid(nx, ny, nz, h):
+    # cell centres of an nx x ny x nz block of cells of edge h, Gaussian source off centre
+    g = np.stack(np.meshgrid((np.arange(nx) + 0.5) * h, (np.arange(ny) + 0.5) * h, (np.arange(nz) + 0.5) * h,
+                             indexing="ij"), axis=-1).reshape(-1, 3)
+    c = np.array([0.4 * nx, 0.6 * ny, 0.5 * nz]) * h
+    I = 1e22 * np.exp(-((g - c) ** 2).sum(1) / 0.08 ** 2) + 1e18
+    return g, np.full(len(g), h), I
+
+
+@pytest.mark.parametrize("shape,leaf,lattice", [((64, 32, 48), 64, True), ((64, 64, 64), 512, False)])
+def test_lattice_edge_cases(kf, shape, leaf, lattice):
+    # a non-cubic block of cells (the root cube has empty boxes; every present leaf is full):
+    # the lattice paths; 512-cell leaves: the generic kernels (a near-field slot of K = 512
+    # would bias the tensor core's truncating accumulation); both against the FP64 form
+    pts, h, I = _box_grid(*shape, 1.0 / 64)
+    a, b = K.absorption_coefficients(152.0)
+    Id = _dev(I)
+    s64 = _plan(kf, pts, h, leaf, 6, a, b).eval(Id).cpu().numpy()
+    pm = _plan(kf, pts, h, leaf, 6, a, b, precision="mixed")
+    inf = pm.info()
+    assert inf["near_tensor"] == lattice and inf["lattice_far"] == lattice
+    assert _relerr(pm.eval(Id).cpu().numpy(), s64) <= 1e-6
 
 
 def test_near_field_lattice_detection(kf):
