@@ -43,9 +43,9 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 294.35e6 + 15.78e6, "per_point_scaled": False,
+    "M2L": {"bytes": 296.56e6 + 16.29e6, "per_point_scaled": False,
             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                    "2ffb91f9a4dea07dc82e24e15bdf61e488af75b66461db81dc1f66a25cacfeb5"},
+                    "02e9ac452138dfe01856ae207ea80db09e4f48af65ad8afb9b3937696c6e36ad"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
     "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
             "src": {"paper_2006_03515_gb300/csrc/eval.cu":
@@ -53,9 +53,9 @@ PROFILED_TRAFFIC = {
             "profile": "profiles/k_p2p_mixed_uniform64.md"},
     "NEAR": {"bytes": 3.96e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                     "2ffb91f9a4dea07dc82e24e15bdf61e488af75b66461db81dc1f66a25cacfeb5",
+                     "02e9ac452138dfe01856ae207ea80db09e4f48af65ad8afb9b3937696c6e36ad",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "f08f41d9d97141fe66e00209fbdd2216de47a074e67bcb1ae3362ed1dab17eff"},
+                     "914f62148b784e5653cf51853129e14c8259477eea8672b2c0976c97a26e9196"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
