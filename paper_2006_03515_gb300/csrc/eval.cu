@@ -1605,10 +1605,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     // ---- M2L in coefficients (Eq. (m2l))
     const T* c = nullptr;
     if (mixed) {
-        int64_t m = (int64_t)t.nboxes * R;
-        k_to_f32<<<nbk(m, 256), 256, 0, st>>>(cu, ptr<float>(p.cu32), m);
-        KF_LAUNCH();
-        ++nl;
+        // the FP32 copy of c feeds the SIMT M2L and the W lists only
+        if (!p.m2l_tensor || p.lists[2].len > 0) {
+            int64_t m = (int64_t)t.nboxes * R;
+            k_to_f32<<<nbk(m, 256), 256, 0, st>>>(cu, ptr<float>(p.cu32), m);
+            KF_LAUNCH();
+            ++nl;
+        }
         c = reinterpret_cast<const T*>(ptr<float>(p.cu32));
         if (p.m2l_tensor) {
             KF_TRY(m2l_tc_split(st, cu, t.nboxes, R, p.chi.p, p.clo.p, ptr<int>(p.cexp)));
