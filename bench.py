@@ -107,6 +107,9 @@ def parse():
                     help="far-field representation of the timed plan (cheb: --m0 is the Chebyshev order p)")
     ap.add_argument("--no-cheb", action="store_true", help="skip the Chebyshev-representation measurement")
     ap.add_argument("--cheb-p", type=int, default=8, help="Chebyshev order of that measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
+    ap.add_argument("--batch-fields", type=int, default=8, help="fields of the batched workload")
+    ap.add_argument("--batch-lanes", type=int, default=4, help="concurrent lanes of the batched workload")
     ap.add_argument("--cpu-n", type=int, default=48, help="grid of the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
@@ -274,6 +277,74 @@ def cheb_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
         p64.close()
         del S64
     pl.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_bench(args, dev, stream, flush):
+    """The batched workload: args.batch_fields uneven two-channel streamer fields (uniform
+    grids of 80^3-158^3 cells, 760 or 76 Torr, m0 = 6, leaf 64, mixed form) evaluated as one
+    CUDA-graph batch, back to back on one stream and on concurrent lanes; CUDA events on the
+    launching stream, L2 flushed between steps, the lanes' results checked against the
+    sequential ones. Plans take the root cube aligned with each field's cell lattice
+    (origin at the grid's corner, side 4 h 2^k >= n h), so that the leaves inside the grid
+    are blocks of 4^3 cells (with the points' bounding cube as root, most of these grids
+    split into leaves of 14-30 cells); the default root is timed beside it."""
+    import math
+    import torch
+    from paper_2006_03515_gb300 import kifmm
+    from paper_2006_03515_gb300 import workloads as W
+    fields = []
+    for k in range(args.batch_fields):
+        pts, h, I, p = W.two_channel_field(k)
+        n = round(len(pts) ** (1 / 3))
+        side = float(h[0]) * 4 * 2 ** math.ceil(math.log2(n / 4))
+        fields.append((torch.as_tensor(pts, device=dev), float(h[0]), torch.as_tensor(I, device=dev), p, n, side))
+    Is = [f[2] for f in fields]
+    Cs = [kifmm.scale_c(f[3]) for f in fields]
+    npts = sum(int(x.shape[0]) for x in Is)
+    steps = max(3, min(args.steps, 10))
+
+    def plans_for(aligned):
+        t0 = time.perf_counter()
+        pl = [kifmm.Plan(f[0], f[1], 64, 6, *kifmm.absorption(0.2 * f[3]), precision="mixed", stream=stream,
+                         root=(0.0, 0.0, 0.0, f[5]) if aligned else None) for f in fields]
+        torch.cuda.synchronize(dev)
+        return pl, time.perf_counter() - t0
+
+    def timed(plans, lanes):
+        Ss = [torch.empty_like(x) for x in Is]
+        for _ in range(3):
+            kifmm.eval_batch(plans, Is, Ss, C=Cs, capture=True, lanes=lanes)
+        ms = []
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            kifmm.eval_batch(plans, Is, Ss, C=Cs, capture=True, lanes=lanes)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        t = statistics.median(ms)
+        return {"ms": t, "points_per_s": npts / (1e-3 * t)}, Ss
+
+    out = {"fields": len(fields), "points": npts, "sizes": [f[4] for f in fields],
+           "pressures_torr": [f[3] for f in fields], "capture": True}
+    plans, out["plan_s"] = plans_for(True)
+    out["lattice_fields"] = sum(1 for pl in plans if pl.info()["near_tensor"])
+    out["lanes1"], s1 = timed(plans, 1)
+    key = "lanes%d" % args.batch_lanes
+    out[key], sl = timed(plans, args.batch_lanes)
+    out["lanes_match_sequential"] = bool(all(
+        float(torch.linalg.norm(x - y) / torch.linalg.norm(y)) <= 1e-12 for x, y in zip(sl, s1)))
+    out["speedup_lanes"] = out["lanes1"]["ms"] / out[key]["ms"]
+    for pl in plans:
+        pl.close()
+    del s1, sl
+    plans, _ = plans_for(False)
+    out["default_root_" + key], _ = timed(plans, args.batch_lanes)
+    for pl in plans:
+        pl.close()
     torch.cuda.empty_cache()
     return out
 
@@ -543,6 +614,12 @@ def main():
                 line["cheb"] = cheb_bench(args, dev, stream, dpts, float(h[0]), dI, C, a, b, flush, peaks)
         except Exception as exc:    # the headline line is printed whatever happens here
             line["cheb"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    if not args.no_batch and args.repr == "surface":
+        try:
+            with torch.cuda.stream(stream):
+                line["batch"] = batch_bench(args, dev, stream, flush)
+        except Exception as exc:    # the headline line is printed whatever happens here
+            line["batch"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if not args.no_surrogate:
         try:
             with torch.cuda.stream(stream):

@@ -131,13 +131,30 @@ int kifmm_eval(kifmm_plan_t plan, const void* I_dev, void* S_dev, int dtype, dou
 int kifmm_eval_host(kifmm_plan_t plan, const void* I_host, void* S_host, int dtype, double C);
 
 /*
- * Evaluates `count` plans (each with its own I and S, possibly of different
- * sizes and pressures) back to back on plan[0]'s stream; with capture != 0 the
- * whole batch is recorded once into a CUDA graph held by plan[0] and replayed
- * on later calls with the same arguments.
+ * Evaluates `count` fields (each a plan with its own I and S, possibly of different
+ * sizes and pressures; the batched workload of many streamer fields) as one unit of
+ * work ordered on plan[0]'s stream.
+ *   lanes    1: the fields run back to back on plan[0]'s stream. lanes > 1 (at most
+ *            KIFMM_MAX_LANES): plan[0]'s stream forks into that many concurrent
+ *            streams owned by plan[0]; every distinct plan is placed on one lane
+ *            (largest fields first, each onto the lane with the fewest points so far;
+ *            entries repeating a plan share its lane and run in order, because they
+ *            share its workspace), and all lanes join back before the call's work
+ *            completes on plan[0]'s stream. Fields are independent, so the device
+ *            schedules one field's kernels beside another's (a small field's levels
+ *            and a large field's near field fill the SMs together). Results are those
+ *            of one kifmm_eval per field.
+ *   capture  != 0: the whole batch, fork and join included, is recorded once into a
+ *            CUDA graph held by plan[0] and replayed on later calls with the same
+ *            arguments (plans, buffers, count, dtype and lanes).
+ * Completion is ordered on plan[0]'s stream only: synchronise it (not the other
+ * plans' streams) before reading S or destroying a plan. Statuses: KIFMM_ERR_ARG
+ * (NULL plan or buffer, count < 1, lanes out of range, capture on the legacy default
+ * stream), KIFMM_ERR_CUDA.
  */
+#define KIFMM_MAX_LANES 8
 int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I_dev, void* const* S_dev,
-                     int count, int dtype, const double* C, int capture);
+                     int count, int dtype, const double* C, int capture, int lanes);
 
 /*
  * Autotuner: picks the leaf size m for a point set by measurement. For each of the

@@ -1,4 +1,5 @@
 // The C-ABI (include/kifmm.h): argument checks, plan lifetime, evaluation entry points.
+#include <algorithm>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -21,8 +22,8 @@ __global__ void gather_sorted_points(const double* pts, const int32_t* perm, int
 
 static void free_plan(Plan* p) {
     if (!p) return;
-    if (p->stream) cudaStreamSynchronize(p->stream);
-    else cudaDeviceSynchronize();
+    // a batch may have run this plan's work on another plan's lanes: wait for the device
+    cudaDeviceSynchronize();
     Tree& t = p->tree;
     for (DevBuf* b : {&t.keys, &t.perm, &t.level, &t.anchor, &t.mcode, &t.parent, &t.child, &t.pstart,
                       &t.pend, &t.leaf, &t.centre})
@@ -55,6 +56,8 @@ static void free_plan(Plan* p) {
     for (auto& e : p->ev)
         if (e) cudaEventDestroy(e);
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    for (auto s : p->lanes) cudaStreamDestroy(s);
+    for (auto e : p->lane_ev) cudaEventDestroy(e);
     delete p;
 }
 
@@ -233,9 +236,32 @@ int kifmm_eval_host(kifmm_plan_t h, const void* I_host, void* S_host, int dtype,
     return KIFMM_OK;
 }
 
+// Lane of each batch entry: distinct plans, largest first, each onto the lane with the
+// fewest points so far; entries repeating a plan take that plan's lane.
+static std::vector<int> assign_lanes(kifmm_plan_t* plans, int count, int lanes) {
+    std::vector<int> lane(count, -1), order;
+    for (int k = 0; k < count; ++k) {
+        bool first = true;
+        for (int j = 0; j < k && first; ++j) first = plans[j] != plans[k];
+        if (first) order.push_back(k);
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return plans[x]->p->tree.n > plans[y]->p->tree.n; });
+    std::vector<int64_t> load(lanes, 0);
+    for (int k : order) {
+        int best = 0;
+        for (int j = 1; j < lanes; ++j)
+            if (load[j] < load[best]) best = j;
+        load[best] += plans[k]->p->tree.n;
+        for (int j = 0; j < count; ++j)
+            if (plans[j] == plans[k]) lane[j] = best;
+    }
+    return lane;
+}
+
 int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I, void* const* S, int count, int dtype,
-                     const double* C, int capture) {
-    if (!plans || !I || !S || count < 1) {
+                     const double* C, int capture, int lanes) {
+    if (!plans || !I || !S || count < 1 || lanes < 1 || lanes > KIFMM_MAX_LANES) {
         set_error("kifmm_eval_batch: invalid argument");
         return KIFMM_ERR_ARG;
     }
@@ -246,28 +272,62 @@ int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I, void* const* S, 
         }
     Plan& p0 = *plans[0]->p;
     cudaStream_t st = p0.stream;
+    std::vector<int> lane_of = assign_lanes(plans, count, lanes);
+    int used = 0;
+    for (int l : lane_of) used = std::max(used, l + 1);
+    if (used > 1) {
+        while ((int)p0.lanes.size() < used) {
+            cudaStream_t s;
+            KF_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            p0.lanes.push_back(s);
+        }
+        while ((int)p0.lane_ev.size() < used + 1) {
+            cudaEvent_t e;
+            KF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            p0.lane_ev.push_back(e);
+        }
+    }
     std::vector<const void*> key;
-    key.reserve(3 * count + 2);
+    key.reserve(3 * count + 3);
     key.push_back((const void*)(intptr_t)count);
     key.push_back((const void*)(intptr_t)dtype);
+    key.push_back((const void*)(intptr_t)used);
     for (int k = 0; k < count; ++k) {
         key.push_back(plans[k]);
         key.push_back(I[k]);
         key.push_back(S[k]);
     }
+    auto run_one = [&](int k, cudaStream_t s) -> int {
+        Plan& pk = *plans[k]->p;
+        cudaStream_t saved = pk.stream;
+        bool saved_t = pk.timing;
+        pk.stream = s;
+        pk.timing = false;
+        int rc = run_eval(pk, I[k], S[k], dtype, C ? C[k] : 1.0);
+        pk.stream = saved;
+        pk.timing = saved_t;
+        return rc;
+    };
     auto launch_all = [&]() -> int {
-        for (int k = 0; k < count; ++k) {
-            Plan& pk = *plans[k]->p;
-            cudaStream_t saved = pk.stream;
-            bool saved_t = pk.timing;
-            pk.stream = st;
-            pk.timing = false;
-            int rc = run_eval(pk, I[k], S[k], dtype, C ? C[k] : 1.0);
-            pk.stream = saved;
-            pk.timing = saved_t;
-            if (rc) return rc;
+        if (used <= 1) {
+            for (int k = 0; k < count; ++k) KF_TRY(run_one(k, st));
+            return KIFMM_OK;
         }
-        return KIFMM_OK;
+        // fork: every lane waits for the work already ordered on plan[0]'s stream
+        KF_CUDA(cudaEventRecord(p0.lane_ev[0], st));
+        for (int j = 0; j < used; ++j) KF_CUDA(cudaStreamWaitEvent(p0.lanes[j], p0.lane_ev[0], 0));
+        int rc = KIFMM_OK;
+        for (int k = 0; k < count && rc == KIFMM_OK; ++k) rc = run_one(k, p0.lanes[lane_of[k]]);
+        // join every forked lane, also after a failure (a capture needs its forks joined)
+        for (int j = 0; j < used; ++j) {
+            cudaError_t e = cudaEventRecord(p0.lane_ev[1 + j], p0.lanes[j]);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p0.lane_ev[1 + j], 0);
+            if (e != cudaSuccess && rc == KIFMM_OK) {
+                set_error(std::string("kifmm_eval_batch: lane join: ") + cudaGetErrorString(e));
+                rc = KIFMM_ERR_CUDA;
+            }
+        }
+        return rc;
     };
     if (!capture) return launch_all();
     if (p0.graph_exec && p0.graph_key == key) {

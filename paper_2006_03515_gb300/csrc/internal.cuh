@@ -218,6 +218,9 @@ struct Plan {
     // batch graph
     cudaGraphExec_t graph_exec = nullptr;
     std::vector<const void*> graph_key;
+    // concurrent batch lanes owned by this plan: streams, and events [0] fork, [1 + j] join
+    std::vector<cudaStream_t> lanes;
+    std::vector<cudaEvent_t> lane_ev;
 };
 
 // tree.cu

@@ -16,6 +16,7 @@ _LIB_PATH = os.path.join(_HERE, "_build", "libkifmm.so")
 KIFMM_FP64, KIFMM_MIXED = 0, 1
 KIFMM_SELF_CELL_EXACT, KIFMM_SELF_PAPER_GL2 = 0, 1
 KIFMM_F32, KIFMM_F64 = 0, 1
+KIFMM_MAX_LANES = 8   # concurrent streams of one batch (kifmm_eval_batch)
 STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOUT",
           -5: "ERR_DUPLICATE_POINT", -6: "ERR_NONFINITE", -7: "ERR_NUMERIC"}
 PRECISION = {"fp64": KIFMM_FP64, "mixed": KIFMM_MIXED}
@@ -88,7 +89,7 @@ def load():
     L.kifmm_eval.argtypes = [vp, vp, vp, i32, dbl]
     L.kifmm_eval_host.argtypes = [vp, vp, vp, i32, dbl]
     L.kifmm_eval_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32,
-                                   ctypes.POINTER(dbl), i32]
+                                   ctypes.POINTER(dbl), i32, i32]
     L.kifmm_destroy.argtypes = [vp]
     L.kifmm_destroy.restype = None
     L.kifmm_last_error.restype = ctypes.c_char_p
@@ -292,8 +293,13 @@ def direct_noalloc(points, h, I, a, b, C=1.0, S=None, self_mode="cell_exact", st
     return S
 
 
-def eval_batch(plans, Is, Ss, C=None, capture=False):
-    """Evaluates several plans back to back on plans[0]'s stream (optionally as one CUDA graph)."""
+def eval_batch(plans, Is, Ss, C=None, capture=False, lanes=4):
+    """Evaluates several fields (plans) as one unit of work ordered on plans[0]'s stream.
+
+    With lanes > 1 the fields run concurrently on up to `lanes` streams forked from and
+    joined back to plans[0]'s stream (entries repeating a plan stay in order on one lane);
+    capture=True records the whole batch once as a CUDA graph and replays it afterwards.
+    """
     import torch
     n = len(plans)
     dt = {torch.float64: KIFMM_F64, torch.float32: KIFMM_F32}[Is[0].dtype]
@@ -301,7 +307,7 @@ def eval_batch(plans, Is, Ss, C=None, capture=False):
     ip = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Is])
     sp = (ctypes.c_void_p * n)(*[x.data_ptr() for x in Ss])
     cc = (ctypes.c_double * n)(*([1.0] * n if C is None else [float(c) for c in C]))
-    _check(load().kifmm_eval_batch(ph, ip, sp, n, dt, cc, 1 if capture else 0))
+    _check(load().kifmm_eval_batch(ph, ip, sp, n, dt, cc, 1 if capture else 0, int(lanes)))
     return Ss
 
 

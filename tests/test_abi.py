@@ -79,6 +79,19 @@ def test_eval_rejects_null(lib):
     lib.kifmm_destroy(None)
 
 
+def test_batch_rejects_bad_arguments(lib):
+    vp = ctypes.c_void_p
+    null = (vp * 2)(None, None)
+    c = (ctypes.c_double * 2)(1.0, 1.0)
+    for count, lanes in [(0, 1), (2, 0), (2, kifmm.KIFMM_MAX_LANES + 1), (-1, 2)]:
+        assert lib.kifmm_eval_batch(null, null, null, count, 1, c, 0, lanes) == ERR_ARG
+        assert "invalid argument" in lib.kifmm_last_error().decode()
+    assert lib.kifmm_eval_batch(null, null, null, 2, 1, c, 1, 2) == ERR_ARG
+    assert "NULL plan" in lib.kifmm_last_error().decode()
+    hdr = open(os.path.join(ROOT, "include", "kifmm.h")).read()
+    assert re.search(r"#define KIFMM_MAX_LANES (\d+)", hdr).group(1) == str(kifmm.KIFMM_MAX_LANES)
+
+
 def test_physics_constants():
     # Eq. (gfun) and Eq. (Ifun) with the parameters of Sec. 4.1
     a, b = kifmm.absorption(150.0)

@@ -332,14 +332,20 @@ def test_batch_and_graph_replay(kf):
             plans.append(p)
             Is.append(_dev(I))
             refs.append(p.eval(Is[-1]).clone())
+        # a repeated plan (its entries share the plan's workspace, so they share one lane and
+        # run in order); twice the source gives twice the field exactly (power-of-two scaling)
+        plans.append(plans[0])
+        Is.append(2 * Is[0])
+        refs.append(2 * refs[0])
         Ss = [torch.empty_like(x) for x in Is]
-        for capture in (False, True, True):
-            for s in Ss:
-                s.zero_()
-            kf.eval_batch(plans, Is, Ss, capture=capture)
-            st.synchronize()
-            for s, r in zip(Ss, refs):   # small levels add split partial sums atomically (order may vary)
-                assert torch.allclose(s, r, rtol=1e-12, atol=0)
+        for lanes in (1, 3, 8):
+            for capture in (False, True, True):
+                for s in Ss:
+                    s.zero_()
+                kf.eval_batch(plans, Is, Ss, capture=capture, lanes=lanes)
+                st.synchronize()
+                for s, r in zip(Ss, refs):   # small levels add split partial sums atomically
+                    assert torch.allclose(s, r, rtol=1e-12, atol=0)
 
 
 def test_duplicate_and_nonfinite_rejected(kf):
@@ -398,7 +404,8 @@ def test_autotune_picks_a_candidate(kf):
 
 def test_batched_uneven_fields_graph_captured(kf):
     # the batched workload at reduced size: uneven fields (two tilted channels each, two
-    # pressures) evaluated back to back in one CUDA graph, against per-field evaluation
+    # pressures) in one CUDA graph, back to back and on concurrent lanes, against per-field
+    # evaluation
     import torch
     st = torch.cuda.Stream()
     fields = [W.two_channel_field(k, n_min=18, n_max=34) for k in range(6)]
@@ -413,11 +420,14 @@ def test_batched_uneven_fields_graph_captured(kf):
             Cs.append(K.source_scale(p))
             refs.append(pl.eval(Is[-1], C=Cs[-1]).clone())
         Ss = [torch.empty_like(x) for x in Is]
-        for _ in range(2):
-            kf.eval_batch(plans, Is, Ss, C=Cs, capture=True)
-            st.synchronize()
-            for s, r in zip(Ss, refs):   # small levels add split partial sums atomically (order may vary)
-                assert torch.allclose(s, r, rtol=1e-12, atol=0)
+        for lanes in (1, 4, 1):
+            for _ in range(2):
+                for s in Ss:
+                    s.fill_(float("nan"))
+                kf.eval_batch(plans, Is, Ss, C=Cs, capture=True, lanes=lanes)
+                st.synchronize()
+                for s, r in zip(Ss, refs):   # small levels add split partial sums atomically
+                    assert torch.allclose(s, r, rtol=1e-12, atol=0)
     # one field against the FP64 form
     pts, h, I, p = fields[0]
     a, b = K.absorption_coefficients(0.2 * p)
