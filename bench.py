@@ -110,7 +110,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--batch-fields", type=int, default=8, help="fields of the batched workload")
     ap.add_argument("--batch-lanes", type=int, default=4, help="concurrent lanes of the batched workload")
-    ap.add_argument("--cpu-n", type=int, default=48, help="grid of the bounded CPU-oracle sample")
+    ap.add_argument("--cpu-n", type=int, default=64, help="grid of the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
