@@ -231,6 +231,27 @@ def test_lattice_edge_cases(kf, shape, leaf, lattice):
     assert _relerr(pm.eval(Id).cpu().numpy(), s64) <= 1e-6
 
 
+@pytest.mark.parametrize("n,lattice", [(40, True), (36, False)])
+def test_root_aligned_with_the_cell_lattice(kf, n, lattice):
+    # a given root cube aligned with the grid's cells (origin at its corner, side 4 h 2^k):
+    # at n = 40 every leaf is a full 4^3 block at one level (the lattice paths); at n = 36
+    # the far corner's 4^3 block stays a coarser leaf (generic kernels). FP64 form against
+    # the oracle with the same root, mixed form against the FP64 form.
+    pts, h, I = W.config_uniform(n)
+    a, b = K.absorption_coefficients(152.0)
+    side = 64 * h[0]
+    root = (0.0, 0.0, 0.0, side)
+    pl = KF.plan(pts, h, 64, 6, a, b, origin=np.zeros(3), side=side)
+    ref = KF.evaluate(pl, I)
+    Id = _dev(I)
+    s64 = _plan(kf, pts, h, 64, 6, a, b, root=root).eval(Id).cpu().numpy()
+    assert _relerr(s64, ref) <= 1e-10
+    pm = _plan(kf, pts, h, 64, 6, a, b, precision="mixed", root=root)
+    inf = pm.info()
+    assert inf["near_tensor"] == lattice and inf["lattice_far"] == lattice
+    assert _relerr(pm.eval(Id).cpu().numpy(), s64) <= 1e-6
+
+
 def test_near_field_lattice_detection(kf):
     # not a lattice of full leaves: the pair kernel (8-cell leaves, a random cloud, the
     # refined grid, per-point h)
