@@ -34,6 +34,16 @@ def gaussian(points, centre, sigma, amp):
     return amp * np.exp(-d2 / sigma ** 2)
 
 
+def multipeak(points, dims, amp=1.53e25, k=50.0):
+    """Multi-peak source of Sec. 4.3 (Eq. (multipeaksource)): amp sin^2(k pi x) sin^2(k pi y)
+    sin^2(k pi z) inside the middle half [d/4, 3d/4] of the domain along every axis (d =
+    ``dims``), zero outside."""
+    d = np.asarray(dims, dtype=np.float64)[None, :]
+    inside = np.all((points >= 0.25 * d) & (points <= 0.75 * d), axis=1)
+    v = amp * np.prod(np.sin(k * np.pi * points) ** 2, axis=1)
+    return np.where(inside, v, 0.0)
+
+
 def refined_grid(L=2.0, base_n=128, fine_factor=8, centre=(1.0, 1.0, 1.5), half_cells=6):
     """Two-level grid: base cells of edge L/base_n, and in the block of
     (2*half_cells+1)^3 base cells around ``centre`` each base cell replaced by
