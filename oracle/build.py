@@ -1,6 +1,6 @@
 """Builds the C part of the oracle (liboracle.so) in-tree with gcc + OpenMP.
 
-TEST INFRASTRUCTURE ONLY: the checker's own native code; building it is not using it."""
+TEST INFRASTRUCTURE ONLY: the oracle's own native code; building it is not using it."""
 import os
 import subprocess
 
