@@ -81,10 +81,19 @@ typedef struct {
      * interpolation in place of the pseudo-inverses (a volumetric representation, not in
      * the paper, that reaches the direct sum to ~1e-7 at p = 8). */
     int repr;
+    /* Radii of the surfaces of the surface representation, in box half-widths (Sec. 3,
+     * Fig. fmulloc): radii[0] for the upward equivalent and downward check surfaces,
+     * radii[1] for the upward check and downward equivalent surfaces. Default {1.2, 2.6},
+     * read off the paper's figure; {0, 0} also selects the default. Otherwise need
+     * 1 < radii[0] < radii[1] < 3 (the equivalent surface encloses the box and the check
+     * surface stays inside its near range); surfaces closer to those bounds, e.g.
+     * {1.05, 2.95}, represent this kernel more accurately at a lower kept rank.
+     * Ignored by the Chebyshev representation. */
+    double radii[2];
 } kifmm_opts;
 
 /* Fills *opts with the defaults above (FP64, cell-exact self term, eps 1e-5,
- * automatic root, default stream, surface representation). */
+ * automatic root, default stream, surface representation, radii {1.2, 2.6}). */
 void kifmm_default_opts(kifmm_opts* opts);
 
 /*

@@ -18,7 +18,9 @@ Surfaces (Fig. fmulloc, Fig. m2mm2ll2l): the m0 x m0 x m0 lattice on the boundar
 of [-1, 1]^3, scaled about the box centre. The radii are read off the figure
 coordinates (box half-width 0.8, surfaces at 0.96 and 2.08): the upward
 equivalent and downward check surfaces at 1.2 r, the upward check and
-downward equivalent surfaces at 2.6 r (r = half-width of the box).
+downward equivalent surfaces at 2.6 r (r = half-width of the box). Other radii
+(1 < inner < outer < 3: the equivalent surface encloses the box, the check surface
+stays inside its near range) are an option of the plan.
 
 Pseudo-inverse (Sec. 3, after the outline: the original pseudo-inverse of the
 cited KIFMM, m0 = 6 by default): a truncated SVD that keeps singular values
@@ -75,7 +77,9 @@ def _octant(o):
 class Operators:
     """Per-level matrices, all kernel values between surfaces (Eqs. (s2m)-(l2l))."""
 
-    def __init__(self, side, nlevels, m0, a, b, eps=1e-5):
+    def __init__(self, side, nlevels, m0, a, b, eps=1e-5, radii=(R_INNER, R_OUTER)):
+        self.r_in, self.r_out = float(radii[0]), float(radii[1])
+        r_in, r_out = self.r_in, self.r_out
         s = surface_lattice(m0)
         self.surf = s
         self.S = s.shape[0]
@@ -83,8 +87,8 @@ class Operators:
         for lev in range(2, nlevels):
             r = side / 2.0 ** (lev + 1)
             # Eq. (s2m): G(x^{B,u}, y^{B,u}); Eq. (s2l): G(x^{B,d}, y^{B,d})
-            self.uc2ue[lev] = truncated_pinv(kmat(R_OUTER * r * s, R_INNER * r * s, a, b), eps)
-            self.dc2de[lev] = truncated_pinv(kmat(R_INNER * r * s, R_OUTER * r * s, a, b), eps)
+            self.uc2ue[lev] = truncated_pinv(kmat(r_out * r * s, r_in * r * s, a, b), eps)
+            self.dc2de[lev] = truncated_pinv(kmat(r_in * r * s, r_out * r * s, a, b), eps)
             # Eq. (m2l): G(x^{B,d}, y^{A,u}) for c_A - c_B = 2 r delta
             for dz in range(-3, 4):
                 for dy in range(-3, 4):
@@ -93,23 +97,23 @@ class Operators:
                             continue
                         off = 2.0 * r * np.array([dx, dy, dz], dtype=np.float64)
                         self.m2l[(lev, _offset_index((dx, dy, dz)))] = kmat(
-                            R_INNER * r * s, off + R_INNER * r * s, a, b)
+                            r_in * r * s, off + r_in * r * s, a, b)
             if lev + 1 < nlevels:
                 rc = r / 2.0
                 for o in range(8):
                     cc = rc * (2.0 * _octant(o) - 1.0)   # child centre - parent centre
                     # Eq. (m2m): G(x^{P,u}, y^{C,u})
-                    self.m2m[(lev, o)] = kmat(R_OUTER * r * s, cc + R_INNER * rc * s, a, b)
+                    self.m2m[(lev, o)] = kmat(r_out * r * s, cc + r_in * rc * s, a, b)
                     # Eq. (l2l): G(x^{C,d}, y^{P,d})
-                    self.l2l[(lev, o)] = kmat(cc + R_INNER * rc * s, R_OUTER * r * s, a, b)
+                    self.l2l[(lev, o)] = kmat(cc + r_in * rc * s, r_out * r * s, a, b)
 
 
-def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None):
+def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii=(R_INNER, R_OUTER)):
     points = np.asarray(points, dtype=np.float64)
     h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
     t, perm = _t.build_tree(points, h, leaf_size, origin, side)
     U, V, W, X = _t.build_lists(t)
-    ops = Operators(t.side, t.nlevels, m0, a, b, eps)
+    ops = Operators(t.side, t.nlevels, m0, a, b, eps, radii)
     return dict(tree=t, perm=perm, U=U, V=V, W=W, X=X, ops=ops, points=points[perm],
                 h=h[perm], a=a, b=b, m0=m0)
 
@@ -132,7 +136,7 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
     for lev in range(t.nlevels - 1, 1, -1):
         for B in range(t.level_start[lev], t.level_start[lev + 1]):
             if t.leaf[B]:
-                xc = centre[B] + R_OUTER * rad[B] * s
+                xc = centre[B] + ops.r_out * rad[B] * s
                 sl = slice(t.pstart[B], t.pend[B])
                 chk = kmat(xc, pts[sl], a, b) @ q[sl]
             else:
@@ -160,7 +164,7 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
             sa = np.array([x[1] for x in pairs])
             np.add.at(chk, tb, phi_u[sa] @ ops.m2l[(lev, key)].T)
         for B in range(lo, hi):
-            xc = centre[B] + R_INNER * rad[B] * s
+            xc = centre[B] + ops.r_in * rad[B] * s
             for A in p["X"][B]:                      # S2L from the sources of leaf A
                 sl = slice(t.pstart[A], t.pend[A])
                 chk[B - lo] += kmat(xc, pts[sl], a, b) @ q[sl]
@@ -179,9 +183,9 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
         x = pts[sl]
         acc = np.zeros(x.shape[0])
         if t.level[B] >= 2:                          # local expansion
-            acc += kmat(x, centre[B] + R_OUTER * rad[B] * s, a, b) @ phi_d[B]
+            acc += kmat(x, centre[B] + ops.r_out * rad[B] * s, a, b) @ phi_d[B]
         for A in p["W"][B]:                          # W list: upward densities
-            acc += kmat(x, centre[A] + R_INNER * rad[A] * s, a, b) @ phi_u[A]
+            acc += kmat(x, centre[A] + ops.r_in * rad[A] * s, a, b) @ phi_u[A]
         src = np.concatenate([np.arange(t.pstart[A], t.pend[A]) for A in p["U"][B]])
         acc += pair_sum_c(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b)
         out[sl] = acc
@@ -191,5 +195,5 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
     return res
 
 
-def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5):
-    return evaluate(plan(points, h, leaf_size, m0, a, b, eps), I, C, mode)
+def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER)):
+    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii), I, C, mode)

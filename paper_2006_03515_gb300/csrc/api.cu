@@ -83,6 +83,8 @@ void kifmm_default_opts(kifmm_opts* o) {
     o->pinv_eps = 1e-5;
     o->has_root = 0;
     o->stream = nullptr;
+    o->radii[0] = kRInner;
+    o->radii[1] = kROuter;
 }
 
 const char* kifmm_last_error(void) { return g_last_error.c_str(); }
@@ -134,6 +136,14 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         set_error("kifmm_plan: pinv_eps must lie in (0, 1)");
         return KIFMM_ERR_ARG;
     }
+    if (o.radii[0] == 0.0 && o.radii[1] == 0.0) {
+        o.radii[0] = kRInner;
+        o.radii[1] = kROuter;
+    }
+    if (!(o.radii[0] > 1.0 && o.radii[1] > o.radii[0] && o.radii[1] < 3.0)) {
+        set_error("kifmm_plan: need 1 < radii[0] < radii[1] < 3");
+        return KIFMM_ERR_ARG;
+    }
     if (o.has_root && !(o.root[3] > 0.0 && std::isfinite(o.root[3]))) {
         set_error("kifmm_plan: root side must be finite and > 0");
         return KIFMM_ERR_ARG;
@@ -146,6 +156,8 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     p->precision = o.precision;
     p->self_mode = o.self_mode;
     p->pinv_eps = o.pinv_eps;
+    p->r_in = o.radii[0];
+    p->r_out = o.radii[1];
     p->stream = (cudaStream_t)o.stream;
     p->a = a;
     p->b = b;

@@ -543,6 +543,7 @@ struct EvalView {
     KParams kp;
     double rf_dchk;         // radius of the downward check surface in half-widths (Chebyshev: 1)
     double rf_ueq;          // radius of the upward equivalent surface in half-widths (Chebyshev: 1)
+    double rf_out;          // radius of the upward check / downward equivalent surface (surface form)
     int ldu;                // row stride of the upward densities read by the W list
     int cheb;               // Chebyshev representation: the local part of L2P is interpolation
     int cp;                 // Chebyshev order p
@@ -566,7 +567,7 @@ __global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, in
 
 
 // S2M (Eq. (s2m), first step): upward check potential of a leaf from its own sources.
-// One block per leaf; check points x_j = c_B + 2.6 r s_j, sources relative to c_B.
+// One block per leaf; check points x_j = c_B + r_out r s_j, sources relative to c_B.
 constexpr int P2M_T = 160;
 // Levels with fewer tensor-core tiles than this take the SIMT apply for M2M / L2L: a tile
 // walks its slots one pipeline stage at a time (about 1.2 us a stage), so a launch of a few
@@ -591,7 +592,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
     for (int j0 = 0; j0 < S; j0 += P2M_T) {
         const int j = j0 + threadIdx.x;
         double xj[3];
-        for (int k = 0; k < 3; ++k) xj[k] = kROuter * r * E.surf[3 * min(j, S - 1) + k];
+        for (int k = 0; k < 3; ++k) xj[k] = E.rf_out * r * E.surf[3 * min(j, S - 1) + k];
         Kahan acc32;
         double acc64 = 0;
         for (int s0 = p0; s0 < p1; s0 += 256) {
@@ -828,7 +829,7 @@ __global__ void k_to_f32(const double* in, float* out, int64_t n) {
     if (e < n) out[e] = (float)in[e];
 }
 
-// S2L for the X list: downward check potential of B (x_j = c_B + 1.2 r_B s_j) from the
+// S2L for the X list: downward check potential of B (x_j = c_B + r_in r_B s_j) from the
 // sources of every leaf A in X(B). One block per box. Row B of chk (stride ldc) is
 // written, or added to when acc != 0 (the Chebyshev representation adds the values at
 // B's nodes, x_j = c_B + r_B xbar_j, straight into B's local node values).
@@ -887,8 +888,8 @@ __global__ void __launch_bounds__(P2M_T) k_s2l_x(EvalView E, const int32_t* boxe
     }
 }
 
-// Targets, far part: local expansion of the leaf (y = c_B + 2.6 r_B s_k, density phi_d)
-// and the W list (y = c_A + 1.2 r_A s_k, density phi_u). One block per leaf, one thread
+// Targets, far part: local expansion of the leaf (y = c_B + r_out r_B s_k, density phi_d)
+// and the W list (y = c_A + r_in r_A s_k, density phi_u). One block per leaf, one thread
 // per target point. Writes far[i] for every point of the leaf.
 constexpr int L2P_T = 64;
 // SER: some target of a leaf may lie closer than 0.5 / (b - a) to its downward equivalent
@@ -922,7 +923,7 @@ __global__ void __launch_bounds__(L2P_T) k_l2p(EvalView E, const int32_t* leaves
             if (li == 0) {
                 if (lev < 2 || E.cheb) continue;   // Chebyshev: interpolation in k_l2p_cheb
                 A = B;
-                rad = kROuter * half_width(E, lev);
+                rad = E.rf_out * half_width(E, lev);
                 dens = phi_d;
             } else {
                 A = witems[woff[B] + li - 1];
@@ -1434,8 +1435,9 @@ static EvalView make_view(Plan& p) {
     E.S = p.S;
     E.kp = make_kparams(p.a, p.b);
     E.cheb = p.cheb ? 1 : 0;
-    E.rf_dchk = p.cheb ? 1.0 : kRInner;
-    E.rf_ueq = p.cheb ? 1.0 : kRInner;
+    E.rf_dchk = p.cheb ? 1.0 : p.r_in;
+    E.rf_ueq = p.cheb ? 1.0 : p.r_in;
+    E.rf_out = p.r_out;
     E.ldu = p.cheb ? p.R : p.S;
     E.cp = p.m0;
     E.ctab = ptr<double>(p.ctab);
@@ -1465,11 +1467,11 @@ static int p2p_series_check(Plan& p) {
     const double rs = 1.01 * 0.5 / (p.b - p.a);
     p.p2p_series = !((double)m >= rs * rs);
     // leaves' points lie within their box (half-width r), their check / equivalent surfaces
-    // at kROuter r: every such pair is at least (kROuter - 1) r apart
+    // at r_out r: every such pair is at least (r_out - 1) r apart
     double rmin = 1e300;
     for (int l = 2; l < p.tree.nlevels; ++l)
         if (p.lv[l].n_leaf > 0) rmin = std::min(rmin, p.tree.side / (double)(2LL << l));
-    p.far_series = !((kROuter - 1.0) * rmin >= rs);
+    p.far_series = !((p.r_out - 1.0) * rmin >= rs);
     return KIFMM_OK;
 }
 

@@ -13,8 +13,8 @@ constexpr int kKeyBits = 21;
 constexpr int kMaxLevel = 20;
 constexpr int kOffsetSlots = 343;   // (dx, dy, dz) in [-3, 3]^3
 constexpr int kSlotStride = 344;    // per tensor-core translation tile: [count, slot_0, slot_1, ...]
-constexpr double kRInner = 1.2;     // upward equivalent / downward check surface (box half-widths)
-constexpr double kROuter = 2.6;     // upward check / downward equivalent surface
+constexpr double kRInner = 1.2;     // default upward equivalent / downward check surface (box half-widths)
+constexpr double kROuter = 2.6;     // default upward check / downward equivalent surface
 // Upward solves of levels with at most kOzMinBoxes boxes take the FP64-pipe GEMM with its K
 // range split over many CTAs: a tensor-core slice-product CTA needs about 45 us, which a
 // handful of CTAs cannot hide.
@@ -118,6 +118,7 @@ struct Plan {
     int precision = KIFMM_FP64;
     int self_mode = KIFMM_SELF_CELL_EXACT;
     double pinv_eps = 1e-5;
+    double r_in = kRInner, r_out = kROuter;   // surface radii in box half-widths
     cudaStream_t stream = nullptr;
     double a = 0, b = 0;
     int m0 = 6, S = 152, Sp = 152, R = 32;   // R: padded coefficient count

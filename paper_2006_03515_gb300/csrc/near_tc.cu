@@ -14,7 +14,7 @@
 //
 // On the same lattice (leaves at level >= 2, no W or X lists) every leaf also shares the
 // operators between its cells and its own surfaces or nodes, tabulated here in FP64:
-//  * S2M: the check matrix P[j][i] = K(|2.6 r s_j - y_i|) (surface form), or the P2M
+//  * S2M: the check matrix P[j][i] = K(|r_out r s_j - y_i|) (surface form), or the P2M
 //    interpolation weights S3(xbar_m, u_i) (Chebyshev form), applied per leaf in FP32;
 //  * the leaves' upward coefficients c = (G1 P) q, sliced exactly on the tensor cores like
 //    the other upward solves (surface form, FP64 accuracy, no check potentials);
@@ -115,7 +115,7 @@ __global__ void k_nf_finish(const float* near, const double* far, const float* f
 
 // T[i][k] = sum_j P[j][i] Ub[j][k] in FP64 for i < npl, k < R: the leaf's local expansion from
 // its d as the square table [1][R][R] of the tensor-core kernel (rows >= npl zero)
-__global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+__global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r, double ro,
                          double h, KParams kp, double* T) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -127,7 +127,7 @@ __global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, con
     for (int j = 0; j < S; ++j) {
         double d2 = 0;
         for (int a = 0; a < 3; ++a) {
-            const double d = kROuter * r * surf[3 * j + a] - y[a];
+            const double d = ro * r * surf[3 * j + a] - y[a];
             d2 += d * d;
         }
         sum += kern_f64(sqrt(d2), kp) * Ub[(int64_t)j * R + k];
@@ -142,13 +142,13 @@ __global__ void k_iota(int32_t* v, int64_t n) {
 
 // ------------------------------------------------------------------------------------
 // S2M and the local part of L2P on the same lattice: every leaf sees the same matrix
-//   P[j][i] = K(|2.6 r s_j - y_i|),  y_i = (c_i + 1/2) h - r  (leaf-centred coordinates),
-// between its check / downward equivalent surface (radius 2.6 r) and its own cells, so
+//   P[j][i] = K(|ro r s_j - y_i|),  y_i = (c_i + 1/2) h - r  (leaf-centred coordinates),
+// between its check / downward equivalent surface (radius ro r) and its own cells, so
 //   chk[B][j] = sum_i P[j][i] q[B][i]   and   far[B][i] = sum_j P[j][i] phi_d[B][j].
 // FP64 kernel values rounded once to FP32; sums in FP32 blocks of 8 terms, compensated
 // across blocks (as the kernels that evaluate the kernel do).
 // ------------------------------------------------------------------------------------
-__global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int nc, double r, double h, KParams kp,
+__global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int nc, double r, double ro, double h, KParams kp,
                             float* P) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -158,7 +158,7 @@ __global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int n
     const int c3[3] = {ci % nc, (ci / nc) % nc, ci / (nc * nc)};
     double d2 = 0;
     for (int k = 0; k < 3; ++k) {
-        const double d = kROuter * r * surf[3 * j + k] - ((c3[k] + 0.5) * h - r);
+        const double d = ro * r * surf[3 * j + k] - ((c3[k] + 0.5) * h - r);
         d2 += d * d;
     }
     P[(int64_t)j * (npl + 1) + i] = (float)kern_f64(sqrt(d2), kp);
@@ -245,7 +245,7 @@ __global__ void k_lat_cheb_table(int p, const double* tab, const int32_t* ref, i
 
 // Q[k][i] = sum_j P[j][i] Ub[j][k] in FP64, rounded once: the local expansion of a leaf
 // straight from its downward coefficients d (phi_d = Ub d), rows padded to npl + 1
-__global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+__global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r, double ro,
                         double h, KParams kp, float* Q) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -257,7 +257,7 @@ __global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, cons
     for (int j = 0; j < S; ++j) {
         double d2 = 0;
         for (int a = 0; a < 3; ++a) {
-            const double d = kROuter * r * surf[3 * j + a] - y[a];
+            const double d = ro * r * surf[3 * j + a] - y[a];
             d2 += d * d;
         }
         sum += kern_f64(sqrt(d2), kp) * Ub[(int64_t)j * R + k];
@@ -455,13 +455,14 @@ int near_tc_plan(Plan& p) {
         lat_s2m_smem(p.S, npl) <= 96 * 1024 && lat_l2p_smem(p.R, npl) <= 96 * 1024) {
         KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));
-        k_lat_table<<<nbn((int64_t)p.S * npl, 256), 256, 0, st>>>(ptr<double>(p.surf), p.S, ptr<int32_t>(ref), nc, r, h,
-                                                                   make_kparams(p.a, p.b), ptr<float>(p.lat_P));
+        k_lat_table<<<nbn((int64_t)p.S * npl, 256), 256, 0, st>>>(ptr<double>(p.surf), p.S, ptr<int32_t>(ref), nc, r,
+                                                                   p.r_out, h, make_kparams(p.a, p.b),
+                                                                   ptr<float>(p.lat_P));
         KF_LAUNCH();
         KF_TRY(dev_alloc(p.lat_Q, (size_t)p.R * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_Q.p, 0, (size_t)p.R * (npl + 1) * 4, st));
         k_lat_Q<<<nbn((int64_t)p.R * npl, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R, ptr<double>(p.surf),
-                                                               ptr<int32_t>(ref), nc, r, h, make_kparams(p.a, p.b),
+                                                               ptr<int32_t>(ref), nc, r, p.r_out, h, make_kparams(p.a, p.b),
                                                                ptr<float>(p.lat_Q));
         KF_LAUNCH();
         for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
@@ -474,7 +475,7 @@ int near_tc_plan(Plan& p) {
             KF_TRY(dev_alloc(QT, RR * 8));
             KF_CUDA(cudaMemsetAsync(QT.p, 0, RR * 8, st));
             k_lat_QT<<<nbn((int64_t)npl * p.R, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R,
-                                                                    ptr<double>(p.surf), ptr<int32_t>(ref), nc, r, h,
+                                                                    ptr<double>(p.surf), ptr<int32_t>(ref), nc, r, p.r_out, h,
                                                                     make_kparams(p.a, p.b), ptr<double>(QT));
             KF_LAUNCH();
             KF_TRY(dev_alloc(p.lat_Thi, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
@@ -532,7 +533,7 @@ int near_tc_plan(Plan& p) {
 // M[r][i] = sum_j G1[r][j] P[j][i] in FP64: the leaves' upward coefficients c = M q straight
 // from their weights (G1 the level's pseudo-inverse, P the check matrix of k_lat_table)
 __global__ void k_lat_M(const double* G1, int S, int rank, const double* surf, const int32_t* ref, int nc, double r,
-                        double h, KParams kp, double* M) {
+                        double ro, double h, KParams kp, double* M) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)rank * npl) return;
@@ -543,7 +544,7 @@ __global__ void k_lat_M(const double* G1, int S, int rank, const double* surf, c
     for (int j = 0; j < S; ++j) {
         double d2 = 0;
         for (int k = 0; k < 3; ++k) {
-            const double d = kROuter * r * surf[3 * j + k] - y[k];
+            const double d = ro * r * surf[3 * j + k] - y[k];
             d2 += d * d;
         }
         sum += G1[(int64_t)rr * S + j] * kern_f64(sqrt(d2), kp);
@@ -563,7 +564,7 @@ int lat_up_plan(Plan& p) {
     DevBuf M;
     KF_TRY(dev_alloc(M, (size_t)op.rank * npl * 8));
     k_lat_M<<<nbn((int64_t)op.rank * npl, 128), 128, 0, st>>>(ptr<double>(op.G1), p.S, op.rank, ptr<double>(p.surf),
-                                                               ptr<int32_t>(p.nf_ref), nc, r, h, make_kparams(p.a, p.b),
+                                                               ptr<int32_t>(p.nf_ref), nc, r, p.r_out, h, make_kparams(p.a, p.b),
                                                                ptr<double>(M));
     KF_LAUNCH();
     KF_TRY(dev_alloc(p.lat_Mimg, pinv_oz_op_bytes(npl, op.rank)));

@@ -413,7 +413,7 @@ int build_operators(Plan& p) {
         double r = p.tree.side / (double)(2ll << l);
         p.ops[l].level = l;
         p.ops[l].r = r;
-        surface_kmat<<<dim3(nb(SS, 256), 1), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * r,
+        surface_kmat<<<dim3(nb(SS, 256), 1), 256, 0, st>>>(ptr<double>(p.surf), S, p.r_out * r, p.r_in * r,
                                                            ptr<double>(z), kp, ptr<double>(tmp), SS);
         KF_LAUNCH();
         transpose_to_colmajor<<<nb(SS, 256), 256, 0, st>>>(ptr<double>(tmp), ptr<double>(A) + (l - 2) * SS, S, 1);
@@ -487,7 +487,7 @@ int build_operators(Plan& p) {
                     sh[3 * sl + 2] = -2.0 * r * dz;
                 }
         KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), sh.size() * 8, cudaMemcpyHostToDevice, st));
-        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * r, kRInner * r,
+        surface_kmat<<<dim3(nb(SS, 256), kOffsetSlots), 256, 0, st>>>(ptr<double>(p.surf), S, p.r_in * r, p.r_in * r,
                                                                      ptr<double>(shifts), kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
         for (int dz = -1; dz <= 1; ++dz)   // near slots are never used: zero them
@@ -522,11 +522,11 @@ int build_operators(Plan& p) {
         KF_CUDA(cudaMemcpyAsync(shifts.p, sh.data(), 48 * 8, cudaMemcpyHostToDevice, st));
         KF_TRY(dev_alloc(op.Mc, 8 * SR * 8));
         KF_TRY(dev_alloc(op.Lo, 8 * RR * 8));
-        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kROuter * r, kRInner * rc,
+        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, p.r_out * r, p.r_in * rc,
                                                           ptr<double>(shifts), kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
         KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(ch.Vb), R, 0, ptr<double>(op.Mc), R, SR, 8));
-        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, kRInner * rc, kROuter * r,
+        surface_kmat<<<dim3(nb(SS, 256), 8), 256, 0, st>>>(ptr<double>(p.surf), S, p.r_in * rc, p.r_out * r,
                                                           ptr<double>(shifts) + 24, kp, ptr<double>(m2l), SS);
         KF_LAUNCH();
         KF_TRY(gemm64(st, S, R, S, ptr<double>(m2l), S, SS, ptr<double>(op.Ub), R, 0, ptr<double>(w), R, SR, 8));

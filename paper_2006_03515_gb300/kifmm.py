@@ -46,7 +46,7 @@ class KifmmError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
-                ("repr", ctypes.c_int)]
+                ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2)]
 
 
 class _Info(ctypes.Structure):
@@ -126,7 +126,8 @@ class Plan:
     """A KIFMM plan over fixed points (outline step 1 and the operators)."""
 
     def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
-                 self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface"):
+                 self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface",
+                 surface_radii=None):
         import torch
         L = load()
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
@@ -154,6 +155,8 @@ class Plan:
             o.has_root = 1
             for k in range(4):
                 o.root[k] = float(root[k])
+        if surface_radii is not None:   # (inner, outer) in box half-widths; default (1.2, 2.6)
+            o.radii[0], o.radii[1] = float(surface_radii[0]), float(surface_radii[1])
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.stream = _stream_ptr(self.stream)
         self.precision = precision

@@ -41,6 +41,7 @@ def test_default_opts(lib):
     assert o.precision == kifmm.KIFMM_FP64
     assert o.self_mode == kifmm.KIFMM_SELF_CELL_EXACT
     assert o.pinv_eps == 1e-5 and o.has_root == 0 and not o.stream
+    assert tuple(o.radii) == (1.2, 2.6)
 
 
 def _plan(lib, **kw):
@@ -70,6 +71,13 @@ def test_plan_rejects_bad_options(lib):
     o.has_root = 1
     o.root[3] = -1.0
     assert _plan(lib, opts=ctypes.byref(o)) == -1
+    # surface radii: 1 < inner < outer < 3
+    for radii in [(1.0, 2.6), (1.2, 1.1), (1.2, 3.0), (0.0, 2.6), (float("nan"), 2.6), (1.2, float("inf"))]:
+        o = kifmm._Opts()
+        lib.kifmm_default_opts(ctypes.byref(o))
+        o.radii[0], o.radii[1] = radii
+        assert _plan(lib, opts=ctypes.byref(o)) == -1
+        assert "radii" in lib.kifmm_last_error().decode()
 
 
 def test_eval_rejects_null(lib):

@@ -115,6 +115,44 @@ def test_fp64_kifmm_matches_oracle_adaptive(kf, case):
     assert _relerr(got, ref) <= 1e-10
 
 
+@pytest.mark.parametrize("case", ["uniform16_leaf8", "adaptive_leaf16"])
+def test_surface_radii_option_matches_oracle(kf, case):
+    # surfaces at 1.05 r and 2.95 r (plan option; the default 1.2 / 2.6 is read off
+    # Fig. fmulloc): the FP64 form against the oracle built with the same radii
+    pts, h, leaf, uni = CASES[case]()
+    I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
+                          head_sigma=0.05, noise_sigma=0.3, seed=7)
+    a, b = 5.32, 304.0
+    radii = (1.05, 2.95)
+    ref = KF.kifmm(pts, h, I, leaf, 6, a, b, radii=radii)
+    got = _plan(kf, pts, h, leaf, 6, a, b, uniform=uni, surface_radii=radii).eval(_dev(I)).cpu().numpy()
+    assert _relerr(got, ref) <= 1e-10
+
+
+def test_surface_radii_option_accuracy_and_mixed(kf):
+    # 32^3 at 760 Torr (p_O2 150): surfaces at 1.05 / 2.95 r keep a lower rank and follow the
+    # whole discrete sum (FFT oracle) far closer than the default 1.2 / 2.6 r (oracle: 1.8e-4
+    # against 3.3e-3); the mixed form (lattice paths, tensor-core M2L at the lower rank)
+    # stays within 1e-6 of the FP64 form
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(150.0)
+    C = K.source_scale(760.0)
+    ref = D.fft_uniform(I.reshape(32, 32, 32), h[0], a, b, C).ravel()
+    Id = _dev(I)
+    p_def = _plan(kf, pts, h, 64, 6, a, b)
+    p_r = _plan(kf, pts, h, 64, 6, a, b, surface_radii=(1.05, 2.95))
+    assert p_r.info()["pinv_rank_min"] < p_def.info()["pinv_rank_min"]
+    e_def = _relerr(p_def.eval(Id, C=C).cpu().numpy(), ref)
+    s_r = p_r.eval(Id, C=C).cpu().numpy()
+    e_r = _relerr(s_r, ref)
+    assert e_r < 1e-3 and e_r < e_def / 5, (e_r, e_def)
+    pm = _plan(kf, pts, h, 64, 6, a, b, precision="mixed", surface_radii=(1.05, 2.95))
+    inf = pm.info()
+    assert inf["m2l_tensor"] and inf["near_tensor"] and inf["lattice_far"]
+    assert _relerr(pm.eval(Id, C=C).cpu().numpy(), s_r) <= 1e-6
+    assert pm.info()["device_error"] == 0
+
+
 @pytest.mark.parametrize("m0", [4, 6, 8])
 @pytest.mark.parametrize("po2", [152.0, 15.2, 1.52])
 def test_mixed_matches_fp64(kf, m0, po2):
