@@ -55,7 +55,7 @@ PROFILED_TRAFFIC = {
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
                      "02e9ac452138dfe01856ae207ea80db09e4f48af65ad8afb9b3937696c6e36ad",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "914f62148b784e5653cf51853129e14c8259477eea8672b2c0976c97a26e9196"},
+                     "631c78d191c65df6df2bce139946743a8c7c9a6d4d7e61b272428b0d93ea169b"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 

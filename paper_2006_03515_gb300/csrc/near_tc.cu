@@ -115,8 +115,8 @@ __global__ void k_nf_finish(const float* near, const double* far, const float* f
 
 // T[i][k] = sum_j P[j][i] Ub[j][k] in FP64 for i < npl, k < R: the leaf's local expansion from
 // its d as the square table [1][R][R] of the tensor-core kernel (rows >= npl zero)
-__global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r, double ro,
-                         double h, KParams kp, double* T) {
+__global__ void k_lat_QT(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+                         double ro, double h, KParams kp, double* T) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)npl * R) return;
@@ -148,8 +148,8 @@ __global__ void k_iota(int32_t* v, int64_t n) {
 // FP64 kernel values rounded once to FP32; sums in FP32 blocks of 8 terms, compensated
 // across blocks (as the kernels that evaluate the kernel do).
 // ------------------------------------------------------------------------------------
-__global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int nc, double r, double ro, double h, KParams kp,
-                            float* P) {
+__global__ void k_lat_table(const double* surf, int S, const int32_t* ref, int nc, double r, double ro, double h,
+                            KParams kp, float* P) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)S * npl) return;
@@ -245,8 +245,8 @@ __global__ void k_lat_cheb_table(int p, const double* tab, const int32_t* ref, i
 
 // Q[k][i] = sum_j P[j][i] Ub[j][k] in FP64, rounded once: the local expansion of a leaf
 // straight from its downward coefficients d (phi_d = Ub d), rows padded to npl + 1
-__global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r, double ro,
-                        double h, KParams kp, float* Q) {
+__global__ void k_lat_Q(const double* Ub, int S, int R, const double* surf, const int32_t* ref, int nc, double r,
+                        double ro, double h, KParams kp, float* Q) {
     const int npl = nc * nc * nc;
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)R * npl) return;
@@ -462,7 +462,8 @@ int near_tc_plan(Plan& p) {
         KF_TRY(dev_alloc(p.lat_Q, (size_t)p.R * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_Q.p, 0, (size_t)p.R * (npl + 1) * 4, st));
         k_lat_Q<<<nbn((int64_t)p.R * npl, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R, ptr<double>(p.surf),
-                                                               ptr<int32_t>(ref), nc, r, p.r_out, h, make_kparams(p.a, p.b),
+                                                               ptr<int32_t>(ref), nc, r, p.r_out, h,
+                                                               make_kparams(p.a, p.b),
                                                                ptr<float>(p.lat_Q));
         KF_LAUNCH();
         for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
@@ -475,7 +476,8 @@ int near_tc_plan(Plan& p) {
             KF_TRY(dev_alloc(QT, RR * 8));
             KF_CUDA(cudaMemsetAsync(QT.p, 0, RR * 8, st));
             k_lat_QT<<<nbn((int64_t)npl * p.R, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R,
-                                                                    ptr<double>(p.surf), ptr<int32_t>(ref), nc, r, p.r_out, h,
+                                                                    ptr<double>(p.surf), ptr<int32_t>(ref), nc, r,
+                                                                    p.r_out, h,
                                                                     make_kparams(p.a, p.b), ptr<double>(QT));
             KF_LAUNCH();
             KF_TRY(dev_alloc(p.lat_Thi, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
@@ -564,7 +566,8 @@ int lat_up_plan(Plan& p) {
     DevBuf M;
     KF_TRY(dev_alloc(M, (size_t)op.rank * npl * 8));
     k_lat_M<<<nbn((int64_t)op.rank * npl, 128), 128, 0, st>>>(ptr<double>(op.G1), p.S, op.rank, ptr<double>(p.surf),
-                                                               ptr<int32_t>(p.nf_ref), nc, r, p.r_out, h, make_kparams(p.a, p.b),
+                                                               ptr<int32_t>(p.nf_ref), nc, r, p.r_out, h,
+                                                               make_kparams(p.a, p.b),
                                                                ptr<double>(M));
     KF_LAUNCH();
     KF_TRY(dev_alloc(p.lat_Mimg, pinv_oz_op_bytes(npl, op.rank)));
