@@ -101,10 +101,14 @@ def test_batch_rejects_bad_arguments(lib):
 
 
 def test_physics_constants():
-    # Eq. (gfun) and Eq. (Ifun) with the parameters of Sec. 4.1
-    a, b = kifmm.absorption(150.0)
+    # Eq. (gfun) and Eq. (Ifun) with the parameters the paper prints (Sec. 2.1, Sec. 4.1)
+    from golden import read as G
+    c = G.paper_constants()
+    assert (kifmm.CHI_MIN, kifmm.CHI_MAX) == (c["chi_min"], c["chi_max"])
+    a, b = kifmm.absorption(c["p_O2"])
     assert a == pytest.approx(5.25, rel=1e-15) and b == 300.0
-    assert kifmm.scale_c(760.0) == pytest.approx(0.06 * 30.0 / 790.0)
+    C = c["xi"] * c["omega_over_alpha"] * c["p_q"] / (c["p"] + c["p_q"])
+    assert kifmm.scale_c(c["p"]) == pytest.approx(C, rel=1e-15)
 
 
 def test_sno_rejects_bad_sizes_on_the_host(lib):

@@ -21,6 +21,7 @@ import pytest
 from oracle import direct as D
 from oracle import kernel as K
 from paper_2006_03515_gb300 import workloads as W
+from golden import read as G
 
 pytestmark = pytest.mark.gpu
 
@@ -64,8 +65,12 @@ def test_paper_accuracy_full_size(kf, case):
     e_v, e_d = _errors(out["fp64"], ref, pts, x0, delta)
     e_vc, e_dc = _errors(out["cheb8"], ref, pts, x0, delta)
     mixed = float(np.linalg.norm(out["mixed"] - out["fp64"]) / np.linalg.norm(out["fp64"]))
-    print("\n%s: surface m0=6 E_V %.3f %% E_delta %.3f %%; mixed vs fp64 %.2e; Chebyshev p=8 E_V %.2e %% "
-          "E_delta %.2e %%" % (case, 100 * e_v, 100 * e_d, mixed, 100 * e_vc, 100 * e_dc))
+    paper_ev, paper_ed = G.paper_fmm_errors()[case]
+    print("\n%s: surface m0=6 E_V %.3f %% E_delta %.3f %% (paper %.2f %%, %.2f %%); mixed vs fp64 %.2e; "
+          "Chebyshev p=8 E_V %.2e %% E_delta %.2e %%" % (case, 100 * e_v, 100 * e_d, 100 * paper_ev, 100 * paper_ed,
+                                                        mixed, 100 * e_vc, 100 * e_dc))
     assert e_v <= 3e-2 and e_d <= 1e-1
     assert mixed <= 1e-6
     assert e_vc <= 1e-5 and e_dc <= 1e-5
+    # the Chebyshev option beats the paper's own FMM by two orders of magnitude or more
+    assert e_vc <= paper_ev / 100 and e_dc <= paper_ed / 100

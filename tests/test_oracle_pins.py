@@ -1,7 +1,8 @@
-"""The oracle pinned to things other than itself: library special functions, closed
-forms (Frullani's integral, the uniformly emitting ball), an independent quadrature
-of the self-cell integral, brute force on tiny inputs, the uniform-grid FFT
-convolution, symmetries, and the list definitions by exhaustive enumeration."""
+"""The oracle pinned to things other than itself: the constants the paper prints
+(tests/golden), library special functions, closed forms (Frullani's integral, the
+uniformly emitting ball), an independent quadrature of the self-cell integral, brute
+force on tiny inputs, the uniform-grid FFT convolution, symmetries, and the list
+definitions by exhaustive enumeration."""
 import math
 
 import numpy as np
@@ -13,8 +14,24 @@ from oracle import kernel as K
 from oracle import kifmm as KF
 from oracle import tree as T
 from paper_2006_03515_gb300 import workloads as W
+from golden import read as G
 
 PRESSURES = [(5.25, 300.0), (5.32, 304.0), (0.532, 30.4), (0.0532, 3.04)]
+
+
+# ---- constants ------------------------------------------------------------------------------
+
+def test_constants_are_the_papers():
+    # chi_min, chi_max (Sec. 2.1), p_q, xi, omega/alpha, p, p_O2 (Sec. 4.1) as printed
+    c = G.paper_constants()
+    assert K.CHI_MIN == c["chi_min"] and K.CHI_MAX == c["chi_max"]
+    a, b = K.absorption_coefficients(c["p_O2"])
+    assert a == pytest.approx(5.25, rel=1e-15) and b == pytest.approx(300.0, rel=1e-15)
+    C = c["xi"] * c["omega_over_alpha"] * c["p_q"] / (c["p"] + c["p_q"])   # Eq. (Ifun)
+    assert K.source_scale(c["p"]) == pytest.approx(C, rel=1e-15)
+    errs = G.paper_fmm_errors()
+    assert set(errs) >= {"gaussian_0.4cm", "gaussian_0.04cm", "multipeak_0.4cm"}
+    assert all(0 < ev < 0.01 and 0 < ed < 0.02 for ev, ed in errs.values())
 
 
 # ---- kernel and E1 -----------------------------------------------------------------------
