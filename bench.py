@@ -129,6 +129,22 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(ms, ws):
+    """The slowest rank's time (ms): the whole job ends when it does."""
+    if ws <= 1:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t[0])
+
+
+def whole_job_rate(npts, ws, ms):
+    """Points per second of all ranks together: every rank evaluates its own npts-point
+    field (replicas, weak scaling) in ms."""
+    return ws * npts / (ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons every 200 ms during the timed region."""
 
@@ -514,12 +530,8 @@ def main():
         clk = clocks.stop()
         launches_per_step = plan.info()["eval_launches"]
         step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        ms = sum(step_ms) / len(step_ms)
-        if ws > 1:
-            t = torch.tensor([ms], dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t[0])
-        value = ws * npts / (ms * 1e-3)
+        ms = max_over_ranks(sum(step_ms) / len(step_ms), ws)
+        value = whole_job_rate(npts, ws, ms)
 
         # end to end through the public API with host buffers (pinned), copies inside the timed region
         hI = torch.empty(npts, dtype=torch.float64, pin_memory=True)
@@ -537,7 +549,7 @@ def main():
             e1.synchronize()
             if k >= 2:
                 e2e_ms.append(e0.elapsed_time(e1))
-        e2e_val = ws * npts / (1e-3 * sum(e2e_ms) / len(e2e_ms))
+        e2e_val = whole_job_rate(npts, ws, max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws))
         e2e_ok = bool(np.allclose(hSn, S.cpu().numpy(), rtol=1e-12, atol=0))   # split partial sums add atomically
 
     phases = ["scatter", "S2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
