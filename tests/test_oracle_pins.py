@@ -232,6 +232,21 @@ def test_kifmm_accuracy_32cube(m0, tol):
     assert err < tol
 
 
+def test_kifmm_surface_radii_option():
+    # the radii option: the figure's radii given explicitly reproduce the default exactly;
+    # surfaces at 1.05 r and 2.95 r (closer to the box and to the edge of its near range)
+    # follow the direct sum far closer on the 16^3 grid (about 3e-3 -> 2e-4)
+    pts, h, I = W.config_uniform(16)
+    a, b = K.absorption_coefficients(150.0)
+    ref = D.direct_sum(pts, h, I, a, b)
+    s_def = KF.kifmm(pts, h, I, 8, 6, a, b)
+    np.testing.assert_array_equal(KF.kifmm(pts, h, I, 8, 6, a, b, radii=(1.2, 2.6)), s_def)
+    s_near = KF.kifmm(pts, h, I, 8, 6, a, b, radii=(1.05, 2.95))
+    e_def = np.linalg.norm(s_def - ref) / np.linalg.norm(ref)
+    e_near = np.linalg.norm(s_near - ref) / np.linalg.norm(ref)
+    assert e_near < e_def / 5 and e_near < 1e-3, (e_near, e_def)
+
+
 # ---- surrogate oracle -----------------------------------------------------------------------
 def test_sno_spectral_conv_equals_masked_fft():
     # with R = identity at every retained mode, SpecConv is the low-pass projection of v onto
