@@ -2,9 +2,10 @@
 // local-expansion and W-list evaluation at the targets, near-field P2P, and the self term.
 #include <algorithm>
 #include <cstdlib>
-
 #include <cstring>
 #include <type_traits>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "internal.cuh"
 #include "cheb.cuh"
@@ -1475,8 +1476,19 @@ static int p2p_series_check(Plan& p) {
     return KIFMM_OK;
 }
 
+// Phase boundaries of one evaluation: k = 0..7 opens phase k (scatter, S2M, M2M + UC2UE, M2L,
+// S2L + L2L + DC2DE, L2P + M2P, P2P) and closes the open one. A CUDA event per boundary when
+// the plan times its phases, and a named NVTX range per phase on the host (no-ops unless a
+// profiler is attached; a range left open by a failed evaluation closes at the next mark).
+static const char* const kPhaseNames[7] = {"kifmm scatter", "kifmm S2M", "kifmm M2M+UC2UE", "kifmm M2L",
+                                           "kifmm S2L+L2L+DC2DE", "kifmm L2P+M2P", "kifmm P2P"};
 static void mark(Plan& p, int k) {
     if (p.timing) cudaEventRecord(p.ev[k], p.stream);
+    if (p.nvtx_range) {
+        nvtxRangeEnd(p.nvtx_range);
+        p.nvtx_range = 0;
+    }
+    if (k < 7) p.nvtx_range = nvtxRangeStartA(kPhaseNames[k]);
 }
 
 template <class T> static const T* sel(const DevBuf& d64, const DevBuf& d32);

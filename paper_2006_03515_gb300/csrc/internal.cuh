@@ -214,6 +214,7 @@ struct Plan {
     // timing
     bool timing = false;
     cudaEvent_t ev[9] = {};
+    uint64_t nvtx_range = 0;     // open NVTX range of the current phase (0: none)
     float phase_ms[8] = {0};
     int n_phases = 0;
     // batch graph
