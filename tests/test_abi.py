@@ -4,6 +4,7 @@ import ctypes
 import glob
 import os
 import re
+import subprocess
 
 import pytest
 
@@ -33,6 +34,37 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert sorted(kifmm.EXPORTS) == names
+
+
+def test_argtypes_match_the_header(lib):
+    # every declared entry point: the binding passes as many arguments as the header takes
+    hdr = open(os.path.join(ROOT, "include", "kifmm.h")).read()
+    decls = re.findall(r"^\s*(?:int|int64_t|void|const char\s*\*)\s+(\w+)\s*\(([^;]*?)\)\s*;", hdr, re.M | re.S)
+    assert len(decls) == len(_declared())
+    for name, params in decls:
+        params = re.sub(r"/\*.*?\*/", "", params, flags=re.S).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        assert len(getattr(lib, name).argtypes or []) == n, name
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # kifmm_opts and kifmm_info as the C compiler lays them out against the ctypes mirrors
+    opts = [f[0] for f in kifmm._Opts._fields_]
+    info = [f[0] for f in kifmm._Info._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "kifmm.h"', "int main(void) {"]
+    src.append('printf("%zu\\n", sizeof(kifmm_opts));')
+    src += ['printf("%%zu\\n", offsetof(kifmm_opts, %s));' % f for f in opts]
+    src.append('printf("%zu\\n", sizeof(kifmm_info));')
+    src += ['printf("%%zu\\n", offsetof(kifmm_info, %s));' % f for f in info]
+    src.append("return 0; }")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)])
+    got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    want = [ctypes.sizeof(kifmm._Opts)] + [getattr(kifmm._Opts, f).offset for f in opts]
+    want += [ctypes.sizeof(kifmm._Info)] + [getattr(kifmm._Info, f).offset for f in info]
+    assert got == want
 
 
 def test_default_opts(lib):
