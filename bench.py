@@ -107,6 +107,7 @@ def parse():
                     help="far-field representation of the timed plan (cheb: --m0 is the Chebyshev order p)")
     ap.add_argument("--no-cheb", action="store_true", help="skip the Chebyshev-representation measurement")
     ap.add_argument("--cheb-p", type=int, default=8, help="Chebyshev order of that measurement")
+    ap.add_argument("--no-radii", action="store_true", help="skip the surface-radii option measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--batch-fields", type=int, default=8, help="fields of the batched workload")
     ap.add_argument("--batch-lanes", type=int, default=4, help="concurrent lanes of the batched workload")
@@ -245,6 +246,57 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def radii_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
+    """The same workload with the surface radii option at 1.05 / 2.95 box half-widths
+    (mixed form): kept rank, plan time, evaluation time (CUDA events, L2 flushed between
+    steps), phase times, the M2L rate, and the mixed result against one FP64 evaluation of
+    the same radii."""
+    import torch
+    from paper_2006_03515_gb300 import kifmm
+    radii = (1.05, 2.95)
+    npts = dpts.shape[0]
+    t0 = time.perf_counter()
+    pl = kifmm.Plan(dpts, hval, args.leaf, args.m0, a, b, precision="mixed", stream=stream, surface_radii=radii)
+    torch.cuda.synchronize(dev)
+    plan_s = time.perf_counter() - t0
+    S = torch.empty_like(dI)
+    for _ in range(3):
+        pl.eval(dI, S, C=C)
+    steps = max(3, min(args.steps, 10))
+    ms, phase_sum = [], None
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pl.eval(dI, S, C=C)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        ph = pl.phase_times()
+        phase_sum = ph if phase_sum is None else [x + y for x, y in zip(phase_sum, ph)]
+    info = pl.info()
+    phases = ["scatter", "S2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P"]
+    ph_ms = {k: v / steps for k, v in zip(phases, phase_sum)}
+    f16_peak = peaks.get("bf16_tflops", 1947.8)
+    m2l_ach = info["m2l_flops"] / (ph_ms["M2L"] * 1e-3) / 1e12
+    t = sum(ms) / len(ms)
+    out = {"radii": list(radii), "precision": "mixed", "rank_min": info["pinv_rank_min"], "plan_s": plan_s,
+           "ms": t, "points_per_s": npts / (1e-3 * t), "phase_ms": ph_ms,
+           "m2l": {"path": "tcgen05 FP16x3" if info["m2l_tensor"] else "SIMT FP32", "tflops": m2l_ach,
+                   "frac": m2l_ach / (f16_peak / 3.0), "flops": info["m2l_flops"]},
+           "near_tensor": bool(info["near_tensor"]), "lattice_far": bool(info["lattice_far"])}
+    if not args.no_fp64:
+        p64 = kifmm.Plan(dpts, hval, args.leaf, args.m0, a, b, precision="fp64", stream=stream, surface_radii=radii)
+        S64 = p64.eval(dI, C=C)
+        torch.cuda.synchronize(dev)
+        out["gate_rel_l2_mixed_vs_fp64"] = float(torch.linalg.norm(S - S64) / torch.linalg.norm(S64))
+        p64.close()
+        del S64
+    pl.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def cheb_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
@@ -626,6 +678,12 @@ def main():
                 line["cheb"] = cheb_bench(args, dev, stream, dpts, float(h[0]), dI, C, a, b, flush, peaks)
         except Exception as exc:    # the headline line is printed whatever happens here
             line["cheb"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    if not args.no_radii and args.repr == "surface":
+        try:
+            with torch.cuda.stream(stream):
+                line["radii"] = radii_bench(args, dev, stream, dpts, float(h[0]), dI, C, a, b, flush, peaks)
+        except Exception as exc:    # the headline line is printed whatever happens here
+            line["radii"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if not args.no_batch and args.repr == "surface":
         try:
             with torch.cuda.stream(stream):
