@@ -270,6 +270,13 @@ int sno_get_grads(sno_model_t model, float* grad_host);
    loading checks the sizes against the model's and resets the optimiser state */
 int sno_save(sno_model_t model, const char* path);
 int sno_load(sno_model_t model, const char* path);
+/* training checkpoint to / from a file ("SNO2" header with the model's sizes, the Adam step
+   count, then the FP32 parameters and Adam's two moment vectors): training resumed from a
+   checkpoint takes the same steps as training that never stopped. Loading checks the sizes
+   against the model's. Statuses: KIFMM_ERR_ARG (NULL, unreadable or mismatched file),
+   KIFMM_ERR_CUDA. */
+int sno_save_checkpoint(sno_model_t model, const char* path);
+int sno_load_checkpoint(sno_model_t model, const char* path);
 /* 1: spectral weights used in BF16 (default); 0: in FP32 (gradient checks) */
 int sno_set_bf16(sno_model_t model, int on);
 /* y = network(u) for `batch` fields (batch <= max_batch) */

@@ -1402,6 +1402,64 @@ int sno_load(sno_model_t h, const char* path) {
     return sno_set_params(h, th.data());
 }
 
+// checkpoint: "SNO2", the sizes as in "SNO1", int64 parameter count, int64 Adam step count,
+// then the FP32 parameters and Adam's first and second moments (training resumes exactly)
+int sno_save_checkpoint(sno_model_t h, const char* path) {
+    set_error("");
+    if (!h || !path) return KIFMM_ERR_ARG;
+    SnoModel& M = h->m;
+    const size_t np = (size_t)M.nparam;
+    std::vector<float> buf(3 * np);
+    KF_CUDA(cudaMemcpyAsync(buf.data(), M.theta.p, np * 4, cudaMemcpyDeviceToHost, M.st));
+    KF_CUDA(cudaMemcpyAsync(buf.data() + np, M.adam_m.p, np * 4, cudaMemcpyDeviceToHost, M.st));
+    KF_CUDA(cudaMemcpyAsync(buf.data() + 2 * np, M.adam_v.p, np * 4, cudaMemcpyDeviceToHost, M.st));
+    KF_CUDA(cudaStreamSynchronize(M.st));
+    FILE* fp = fopen(path, "wb");
+    if (!fp) {
+        set_error("sno_save_checkpoint: cannot open the file");
+        return KIFMM_ERR_ARG;
+    }
+    const int32_t hdr[6] = {0x324f4e53, M.n, M.C, M.m, M.L, M.P};
+    bool ok = fwrite(hdr, 4, 6, fp) == 6 && fwrite(&M.nparam, 8, 1, fp) == 1 && fwrite(&M.steps, 8, 1, fp) == 1 &&
+              fwrite(buf.data(), 4, buf.size(), fp) == buf.size();
+    ok = (fclose(fp) == 0) && ok;
+    if (!ok) {
+        set_error("sno_save_checkpoint: write failed");
+        return KIFMM_ERR_ARG;
+    }
+    return KIFMM_OK;
+}
+
+int sno_load_checkpoint(sno_model_t h, const char* path) {
+    set_error("");
+    if (!h || !path) return KIFMM_ERR_ARG;
+    SnoModel& M = h->m;
+    FILE* fp = fopen(path, "rb");
+    if (!fp) {
+        set_error("sno_load_checkpoint: cannot open the file");
+        return KIFMM_ERR_ARG;
+    }
+    const size_t np = (size_t)M.nparam;
+    int32_t hdr[6] = {0};
+    int64_t nfile = -1, steps = -1;
+    std::vector<float> buf(3 * np);
+    bool ok = fread(hdr, 4, 6, fp) == 6 && fread(&nfile, 8, 1, fp) == 1 && fread(&steps, 8, 1, fp) == 1;
+    ok = ok && hdr[0] == 0x324f4e53 && hdr[1] == M.n && hdr[2] == M.C && hdr[3] == M.m && hdr[4] == M.L &&
+         hdr[5] == M.P && nfile == M.nparam && steps >= 0;
+    ok = ok && fread(buf.data(), 4, buf.size(), fp) == buf.size();
+    fclose(fp);
+    if (!ok) {
+        set_error("sno_load_checkpoint: not a checkpoint of this model's shape");
+        return KIFMM_ERR_ARG;
+    }
+    KF_TRY(sno_set_params(h, buf.data()));   // parameters and their BF16 copies (clears the moments)
+    KF_CUDA(cudaMemcpyAsync(M.adam_m.p, buf.data() + np, np * 4, cudaMemcpyHostToDevice, M.st));
+    KF_CUDA(cudaMemcpyAsync(M.adam_v.p, buf.data() + 2 * np, np * 4, cudaMemcpyHostToDevice, M.st));
+    KF_CUDA(cudaStreamSynchronize(M.st));
+    M.steps = steps;
+    return KIFMM_OK;
+}
+
 int sno_set_bf16(sno_model_t h, int on) {
     if (!h) return KIFMM_ERR_ARG;
     h->m.bf16 = on ? 1 : 0;

@@ -64,7 +64,7 @@ EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", 
            "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
            "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
-           "sno_save", "sno_load",
+           "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
            "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"]
 
 _lib = None
@@ -326,14 +326,17 @@ def _load_sno(L):
     L.sno_get_grads.argtypes = [vp, vp]
     L.sno_save.argtypes = [vp, ctypes.c_char_p]
     L.sno_load.argtypes = [vp, ctypes.c_char_p]
+    L.sno_save_checkpoint.argtypes = [vp, ctypes.c_char_p]
+    L.sno_load_checkpoint.argtypes = [vp, ctypes.c_char_p]
     L.sno_set_bf16.argtypes = [vp, i32]
     L.sno_forward.argtypes = [vp, vp, vp, i32]
     L.sno_loss_grad.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dbl)]
     L.sno_adam_step.argtypes = [vp, flt, flt, flt, flt]
     L.photo_solve.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, ctypes.POINTER(i32),
                               ctypes.POINTER(dbl)]
-    for name in ("sno_create", "sno_save", "sno_load", "sno_set_params", "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_forward",
-                 "sno_loss_grad", "sno_adam_step", "photo_solve"):
+    for name in ("sno_create", "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint", "sno_set_params",
+                 "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step",
+                 "photo_solve"):
         getattr(L, name).restype = ctypes.c_int
 
 
@@ -417,6 +420,13 @@ class SNO:
 
     def load(self, path):
         _check(load().sno_load(self._h, os.fsencode(path)))
+
+    def save_checkpoint(self, path):
+        """Parameters, Adam moments and step count (training resumes exactly)."""
+        _check(load().sno_save_checkpoint(self._h, os.fsencode(path)))
+
+    def load_checkpoint(self, path):
+        _check(load().sno_load_checkpoint(self._h, os.fsencode(path)))
 
     def _batch(self, u):
         import torch

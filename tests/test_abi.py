@@ -154,4 +154,5 @@ def test_sno_rejects_bad_sizes_on_the_host(lib):
     assert lib.sno_forward(None, None, None, 1) == ERR_ARG
     assert lib.sno_loss_grad(None, None, None, 1, None) == ERR_ARG
     assert lib.sno_save(None, b"x") == ERR_ARG
+    assert lib.sno_save_checkpoint(None, b"x") == ERR_ARG and lib.sno_load_checkpoint(None, b"x") == ERR_ARG
     assert lib.photo_solve(None, None, None, None, 1.0, 1e-2, 256, 0, None, None) == ERR_ARG

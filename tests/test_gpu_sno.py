@@ -128,6 +128,53 @@ def test_save_load_round_trip(model, tmp_path):
     wrong.close()
 
 
+def test_checkpoint_resumes_training(tmp_path):
+    # a checkpoint holds the parameters, Adam's moments and its step count: one step after
+    # resuming matches the step of the run that never stopped (up to the order of the
+    # gradient's atomic sums), and differs from a restart with the parameters alone
+    s = SHAPE
+
+    def sno():
+        return kifmm.SNO(s["n"], s["C"], s["m"], s["L"], s["P"], max_batch=2)
+
+    u = _cuda(_fields(2, s["n"], 42))
+    t = _cuda(0.5 * _fields(2, s["n"], 43))
+    M = sno()
+    M.set_params(_random_theta(s["C"], s["m"], s["L"], s["P"], 41))
+    for _ in range(3):
+        M.loss_grad(u, t)
+        M.adam_step(lr=1e-3)
+    ckpt, params_only = str(tmp_path / "ckpt.bin"), str(tmp_path / "params.bin")
+    M.save_checkpoint(ckpt)
+    M.save(params_only)
+    th3 = M.params()
+    M.loss_grad(u, t)
+    M.adam_step(lr=1e-3)
+    cont = M.params()
+    R = sno()
+    R.load_checkpoint(ckpt)
+    assert np.array_equal(R.params(), th3)
+    R.loss_grad(u, t)
+    R.adam_step(lr=1e-3)
+    F = sno()
+    F.load(params_only)   # parameters only: the moments and the step count start afresh
+    F.loss_grad(u, t)
+    F.adam_step(lr=1e-3)
+    d_resumed = float(np.abs(R.params() - cont).max())
+    d_fresh = float(np.abs(F.params() - cont).max())
+    assert d_fresh > 0 and d_resumed <= 1e-2 * d_fresh, (d_resumed, d_fresh)
+    # the two file kinds are not interchangeable, and the sizes must match
+    with pytest.raises(kifmm.KifmmError):
+        F.load(ckpt)
+    with pytest.raises(kifmm.KifmmError):
+        F.load_checkpoint(params_only)
+    wrong = kifmm.SNO(s["n"], s["C"] + 4, s["m"], s["L"], s["P"], max_batch=1)
+    with pytest.raises(kifmm.KifmmError):
+        wrong.load_checkpoint(ckpt)
+    for x in (M, R, F, wrong):
+        x.close()
+
+
 def test_training_reduces_the_loss():
     import torch
     n = 16
