@@ -148,6 +148,7 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         set_error("kifmm_plan: root side must be finite and > 0");
         return KIFMM_ERR_ARG;
     }
+    AllocFaultScope fault_scope;
     Plan* p = new (std::nothrow) Plan();
     if (!p) {
         set_error("kifmm_plan: host allocation failed");

@@ -55,6 +55,11 @@ struct DevBuf {
     size_t bytes = 0;
 };
 int dev_alloc(DevBuf& b, size_t bytes);
+// Scope of kifmm_plan in which KIFMM_FAIL_ALLOC=k fails the k-th device allocation (tests)
+struct AllocFaultScope {
+    AllocFaultScope();
+    ~AllocFaultScope();
+};
 void dev_free(DevBuf& b);
 template <class T> T* ptr(const DevBuf& b) { return reinterpret_cast<T*>(b.p); }
 

@@ -3,6 +3,7 @@
 // adaptive lists of the kernel-independent FMM the paper builds on).
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 
 #include "internal.cuh"
@@ -12,9 +13,25 @@ namespace kifmm {
 // ------------------------------------------------------------------------------------
 // generic helpers
 // ------------------------------------------------------------------------------------
+// Allocation-failure injection for the tests of the error paths: inside one kifmm_plan call,
+// KIFMM_FAIL_ALLOC=k makes the k-th device allocation report an out-of-memory error.
+static thread_local long g_alloc_count = 0, g_alloc_fail_at = 0;
+
+AllocFaultScope::AllocFaultScope() {
+    const char* f = std::getenv("KIFMM_FAIL_ALLOC");
+    g_alloc_count = 0;
+    g_alloc_fail_at = f ? std::max(0L, std::atol(f)) : 0;
+}
+
+AllocFaultScope::~AllocFaultScope() { g_alloc_fail_at = 0; }
+
 int dev_alloc(DevBuf& b, size_t bytes) {
     dev_free(b);
     if (bytes == 0) bytes = 16;
+    if (g_alloc_fail_at > 0 && ++g_alloc_count == g_alloc_fail_at) {
+        set_error("device allocation " + std::to_string(g_alloc_fail_at) + " failed (injected)");
+        return KIFMM_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(&b.p, bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();

@@ -407,6 +407,32 @@ def test_batch_and_graph_replay(kf):
                     assert torch.allclose(s, r, rtol=1e-12, atol=0)
 
 
+def test_allocation_failures_are_reported_and_recovered(kf, monkeypatch):
+    # host-side fault injection (no device fault): the k-th device allocation of a plan
+    # reports out-of-memory; no plan is returned, its partial state is freed, and plans
+    # made afterwards are unaffected
+    pts, h, I = W.config_uniform(16)
+    a, b = 5.32, 304.0
+    Id = _dev(I)
+    ref = _plan(kf, pts, h, 8, 6, a, b, precision="mixed").eval(Id).cpu().numpy()
+    failed = 0
+    for k in (1, 2, 3, 5, 8, 13, 21, 34, 55, 89, 144, 233):
+        monkeypatch.setenv("KIFMM_FAIL_ALLOC", str(k))
+        try:
+            p = _plan(kf, pts, h, 8, 6, a, b, precision="mixed")
+        except kf.KifmmError as e:
+            assert e.code == -2, str(e)
+            failed += 1
+            continue
+        monkeypatch.delenv("KIFMM_FAIL_ALLOC")
+        np.testing.assert_allclose(p.eval(Id).cpu().numpy(), ref, rtol=1e-12, atol=0)
+        p.close()
+    assert failed >= 5
+    monkeypatch.delenv("KIFMM_FAIL_ALLOC", raising=False)
+    again = _plan(kf, pts, h, 8, 6, a, b, precision="mixed").eval(Id).cpu().numpy()
+    np.testing.assert_allclose(again, ref, rtol=1e-12, atol=0)
+
+
 def test_duplicate_and_nonfinite_rejected(kf):
     pts, h, I = W.random_cloud(100, 3)
     bad = pts.copy()
