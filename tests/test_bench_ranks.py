@@ -1,6 +1,8 @@
-"""bench.py's multi-rank path on the CPU: two gloo ranks on 127.0.0.1 agree on the slowest
-rank's time and on the whole-job rate (replicas, weak scaling); the reference arm's
-non-zero ranks exit 0 without work."""
+"""bench.py's host-side contract on the CPU: two gloo ranks on 127.0.0.1 agree on the
+slowest rank's time and on the whole-job rate (replicas, weak scaling); the reference arm
+prints one JSON line with the contract's keys on rank 0, and its other ranks exit 0
+without work."""
+import json
 import multiprocessing as mp
 import os
 import socket
@@ -51,3 +53,19 @@ def test_reference_arm_other_ranks_exit_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
                         "--steps", "1", "--warmup", "1"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_reference_arm_prints_the_contract_line():
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "1"], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+                "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 1 and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+    assert "workload" in d["config"]
