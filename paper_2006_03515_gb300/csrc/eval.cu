@@ -18,15 +18,6 @@ static inline unsigned nbk(int64_t n, int t) { return (unsigned)((n + t - 1) / t
 // ------------------------------------------------------------------------------------
 // plan-time data for the evaluation
 // ------------------------------------------------------------------------------------
-__global__ void gather_points(const double* pts, const int32_t* perm, int64_t n, double* out) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    int64_t i = perm[k];
-    out[3 * k] = pts[3 * i];
-    out[3 * k + 1] = pts[3 * i + 1];
-    out[3 * k + 2] = pts[3 * i + 2];
-}
-
 __global__ void mark_leaf_points(const int32_t* leaf, const int32_t* pstart, const int32_t* pend,
                                  int64_t nb, int32_t* leaf_of) {
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
