@@ -143,6 +143,37 @@ def sigma_paper_gl2(h, a, b):
     return h ** 3 * 3.0 * g / (math.pi * s2)
 
 
+def sigma_box_exact(hx, hy, hz, a, b, nodes=64):
+    """Exact integral of K over a rectangular cell hx x hy x hz centred on the singularity
+    (the cells of the Sec. 4.2 grid are not cubic). The same solid-angle form as
+    ``sigma_cell_exact``, face by face: the pair of faces normal to axis k (half-width
+    h_k / 2) contributes 2 int (h_k/2) / R^3 F(R) du dv over the other two half-widths,
+    R = sqrt(u^2 + v^2 + h_k^2 / 4)."""
+    t, w = np.polynomial.legendre.leggauss(nodes)
+    hs = (float(hx), float(hy), float(hz))
+    lnba = math.log(b / a)
+    total = 0.0
+    for k in range(3):
+        hk = hs[k]
+        hi, hj = [hs[m] for m in range(3) if m != k]
+        u, wu = 0.5 * hi * t, 0.5 * hi * w
+        v, wv = 0.5 * hj * t, 0.5 * hj * w
+        U, V = np.meshgrid(u, v, indexing="ij")
+        R = np.sqrt(U * U + V * V + 0.25 * hk * hk)
+        F = lnba + np.vectorize(expint_e1)(b * R) - np.vectorize(expint_e1)(a * R)
+        total += 2.0 * float(np.sum(np.outer(wu, wv) * (0.5 * hk) / R ** 3 * F))
+    return total / (4.0 * math.pi * lnba)
+
+
+def sigma_box_paper_gl2(hx, hy, hz, a, b):
+    """The paper's i == j value for a rectangular cell times its volume:
+    hx hy hz * 3 g(rho) / (pi sum h^2), rho = sqrt(sum h^2 / 12) (Sec. 3, discrete G)."""
+    s2 = hx * hx + hy * hy + hz * hz
+    rho = math.sqrt(s2 / 12.0)
+    g = (math.exp(-a * rho) - math.exp(-b * rho)) / (rho * math.log(b / a))
+    return hx * hy * hz * 3.0 * g / (math.pi * s2)
+
+
 SELF_MODES = ("cell_exact", "paper_gl2")
 
 

@@ -120,6 +120,84 @@ def test_sigma_paper_gl2_is_2pt_gauss_legendre(a, b):
     assert K.sigma_paper_gl2(h, a, b) == pytest.approx(s, rel=1e-13)
 
 
+# ---- rectangular cells (the Sec. 4.2 grid) ---------------------------------------------------
+def _sigma_box_duffy(hs, a, b, n=48):
+    """Self-cell integral of a rectangular cell by the volume route: six pyramids with apex
+    at the centre, y = t (u, v, h_k/2) over the face normal to axis k, dy = t^2 (h_k/2) dt du dv;
+    Gauss-Legendre in t, u, v on the kernel itself."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    t, wt = 0.5 * (x + 1), 0.5 * w
+    tot = 0.0
+    for k in range(3):
+        hk = hs[k]
+        hi, hj = [hs[m] for m in range(3) if m != k]
+        U, V = np.meshgrid(0.5 * hi * x, 0.5 * hj * x, indexing="ij")
+        WU = np.outer(0.5 * hi * w, 0.5 * hj * w)
+        Rf = np.sqrt(U * U + V * V + 0.25 * hk * hk)
+        for tk, wk in zip(t, wt):
+            tot += 2.0 * wk * np.sum(WU * K.kernel(tk * Rf, a, b) * tk * tk * (0.5 * hk))
+    return tot
+
+
+@pytest.mark.parametrize("a,b", PRESSURES)
+def test_sigma_box_reduces_to_the_cube(a, b):
+    for h in (1.0 / 32, 1.0 / 512):
+        assert K.sigma_box_exact(h, h, h, a, b) == pytest.approx(K.sigma_cell_exact(h, a, b), rel=1e-13)
+        assert K.sigma_box_paper_gl2(h, h, h, a, b) == pytest.approx(K.sigma_paper_gl2(h, a, b), rel=1e-14)
+
+
+@pytest.mark.parametrize("a,b", [(0.35, 20.0), (5.6, 320.0)])
+@pytest.mark.parametrize("hs", [(0.25 / 256, 0.25 / 256, 1.4 / 320), (0.002, 0.003, 0.005)])
+def test_sigma_box_independent(a, b, hs):
+    # the Sec. 4.2 cell (0.25/256 x 0.25/256 x 1.4/320 cm) and a fully rectangular one,
+    # at p_O2 = 10 and 160 Torr; the face-flux form against the volume quadrature, and
+    # invariance under a permutation of the axes
+    ref = _sigma_box_duffy(hs, a, b, n=96)   # the elongated cell needs more volume nodes
+    got = K.sigma_box_exact(*hs, a, b)
+    assert got == pytest.approx(ref, rel=2e-10)
+    assert K.sigma_box_exact(hs[1], hs[2], hs[0], a, b) == pytest.approx(got, rel=1e-13)
+
+
+def test_sigma_box_paper_gl2_is_2pt_gauss_legendre():
+    # the paper's value for a rectangular cell: the 2-point Gauss-Legendre rule per axis,
+    # all 8 nodes at distance sqrt(sum h^2 / 12)
+    a, b = 2.0, 120.0
+    hs = (0.001, 0.002, 0.004)
+    x, w = np.polynomial.legendre.leggauss(2)
+    s = 0.0
+    for i in range(2):
+        for j in range(2):
+            for k in range(2):
+                y = [0.5 * hs[0] * x[i], 0.5 * hs[1] * x[j], 0.5 * hs[2] * x[k]]
+                s += (0.125 * hs[0] * hs[1] * hs[2]) * w[i] * w[j] * w[k] * float(K.kernel(math.hypot(*y), a, b))
+    assert K.sigma_box_paper_gl2(*hs, a, b) == pytest.approx(s, rel=1e-13)
+
+
+def test_sigma_box_large_cell_is_unit_mass():
+    assert K.sigma_box_exact(40.0, 30.0, 50.0, 5.25, 300.0) == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("mode", K.SELF_MODES)
+def test_fft_box_grid_equals_brute_force(mode):
+    # rectangular cells: weights I hx hy hz, pairs at the midpoint rule, the cell's own term
+    hx, hy, hz = 0.01, 0.012, 0.03
+    nx, ny, nz = 6, 5, 4
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    pts = np.stack([(x.ravel() + 0.5) * hx, (y.ravel() + 0.5) * hy, (z.ravel() + 0.5) * hz], axis=1)
+    I = np.random.default_rng(4).random(len(pts)) * 1e3
+    a, b = 0.532, 30.4
+    sig = K.sigma_box_exact(hx, hy, hz, a, b) if mode == "cell_exact" else K.sigma_box_paper_gl2(hx, hy, hz, a, b)
+    ref = np.empty(len(pts))
+    for i in range(len(pts)):
+        d = np.linalg.norm(pts - pts[i], axis=1)
+        d[i] = 1.0
+        kv = K.kernel(d, a, b)
+        kv[i] = 0.0
+        ref[i] = 0.7 * (np.sum(kv * I) * hx * hy * hz + sig * I[i])
+    got = D.fft_box_grid(I.reshape(nz, ny, nx), (hx, hy, hz), a, b, 0.7, mode).ravel()
+    np.testing.assert_allclose(got, ref, rtol=1e-11)
+
+
 # ---- direct sum ---------------------------------------------------------------------------
 def _tiny(seed=3, n=40):
     rng = np.random.default_rng(seed)
