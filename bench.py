@@ -28,8 +28,9 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 512 << 20
 SM_COUNT = 152
-# MUFU results per SM per clock on this machine's GB300, measured by
-# paper_2006_03515_gb300/probes/unit_rates.cu (independent chains): ex2.approx and rsqrt.approx
+# MUFU results per SM per clock of GB300, measured once with a microbenchmark of independent
+# dependency chains (8 per thread, 4 blocks of 256 threads per SM, CUDA events): ex2.approx.ftz.f32
+# 30.15 and rsqrt.approx.ftz.f32 15.15 results per SM per clock
 EX2_PER_SM_CLK = 30.2
 RSQ_PER_SM_CLK = 15.2
 PAIRS_PER_SM_CLK = 1.0 / (2.0 / EX2_PER_SM_CLK + 1.0 / RSQ_PER_SM_CLK)   # one rsqrt + two ex2 per pair

@@ -56,9 +56,13 @@ typedef enum { KIFMM_F32 = 0, KIFMM_F64 = 1 } kifmm_dtype;
 
 typedef struct {
     /* KIFMM_FP64: every step in FP64.
-     * KIFMM_MIXED: near-field P2P, check-surface and target evaluations in FP32
-     * (box-local coordinates, compensated sums), M2L in split 3xTF32 form with
-     * FP32 accumulation, the pseudo-inverse applications and the L2L chain in FP64. */
+     * KIFMM_MIXED: near-field sums, check-surface and target evaluations in FP32
+     * (box-local coordinates, compensated sums); M2L, L2L and the M2M translations as
+     * 3-term FP16 splits (hi*hi + hi*lo + lo*hi, power-of-two scaled) on the tensor cores
+     * with FP32 accumulation (SIMT FP32 for small levels); the upward pseudo-inverse
+     * applications c = Sigma^+ U^T chk to FP64 accuracy (exact integer slices on the
+     * tensor cores, or the FP64 pipe); on a uniform lattice of full leaves the near field
+     * as 27 per-offset kernel matrices on the tensor cores (same FP16 x 3 form). */
     int precision;
     /* Value of the i == j term of the discrete kernel G (Sec. 3):
      * KIFMM_SELF_CELL_EXACT: the exact integral of K over the cell (default);
@@ -128,14 +132,16 @@ int kifmm_plan(kifmm_plan_t* out, const double* points_dev, int64_t n,
  *   S_dev  device, N outputs (same dtype), fully overwritten (never accumulated).
  *   C      scale factor (1.0 gives the raw sum).
  * Asynchronous on the plan's stream; allocates nothing; no host synchronisation.
- * Statuses: KIFMM_ERR_ARG (NULL, bad dtype), KIFMM_ERR_CUDA (launch failure).
+ * Statuses: KIFMM_ERR_ARG (NULL, bad dtype), KIFMM_ERR_CUDA (launch failure). A bounded
+ * device wait that gives up is reported by kifmm_check (below), not by this call.
  */
 int kifmm_eval(kifmm_plan_t plan, const void* I_dev, void* S_dev, int dtype, double C);
 
 /*
  * The same evaluation from host buffers: copies I_host to the device, runs
  * kifmm_eval, copies S back to S_host and synchronises the plan's stream.
- * Host buffers may be pageable or pinned (pinned is faster).
+ * Host buffers may be pageable or pinned (pinned is faster). Returns KIFMM_ERR_TIMEOUT when a
+ * bounded device wait of the evaluation gave up (as kifmm_check).
  */
 int kifmm_eval_host(kifmm_plan_t plan, const void* I_host, void* S_host, int dtype, double C);
 
@@ -155,7 +161,9 @@ int kifmm_eval_host(kifmm_plan_t plan, const void* I_host, void* S_host, int dty
  *            of one kifmm_eval per field.
  *   capture  != 0: the whole batch, fork and join included, is recorded once into a
  *            CUDA graph held by plan[0] and replayed on later calls with the same
- *            arguments (plans, buffers, count, dtype and lanes).
+ *            arguments (plans, buffers, count, dtype, lanes and the values of C); any
+ *            other call records a new graph. Plans are told apart by an id that is never
+ *            reused, so a plan created at a destroyed plan's address is a new plan.
  * Completion is ordered on plan[0]'s stream only: synchronise it (not the other
  * plans' streams) before reading S or destroying a plan. Statuses: KIFMM_ERR_ARG
  * (NULL plan or buffer, count < 1, lanes out of range, capture on the legacy default
@@ -178,6 +186,28 @@ int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I_dev, void* const*
 int kifmm_autotune(const double* points_dev, int64_t n, const double* cell_h_dev, double uniform_h,
                    const int* leaf_candidates, int ncand, int surface_order, double a, double b,
                    const kifmm_opts* opts, int reps, int* best_leaf, float* ms_out);
+
+/*
+ * Status of the device work issued so far for the plan: synchronises the plan's stream and
+ * reads the plan's device error word. A bounded wait inside a tensor-core kernel that gave
+ * up (instead of hanging) leaves a code there; the evaluation it belonged to is then not
+ * valid. Returns KIFMM_ERR_TIMEOUT in that case and clears the word (each event is reported
+ * once), KIFMM_OK otherwise, KIFMM_ERR_CUDA if the stream reports an error. kifmm_eval_host
+ * makes this check itself; callers of the asynchronous kifmm_eval and kifmm_eval_batch
+ * call it for each plan when they synchronise.
+ */
+int kifmm_check(kifmm_plan_t plan);
+
+/*
+ * Constants of the Zheleznyak model (Sec. 2.1, Eqs. (gfun), (Ifun)) for a gas pressure p
+ * and an oxygen partial pressure p_O2 (Torr): a = chi_min p_O2 and b = chi_max p_O2 with
+ * chi_min = 0.035 and chi_max = 2 /(cm Torr), and the scale C = xi (omega/alpha) p_q / (p + p_q)
+ * for the quenching pressure p_q (Torr) and the factor xi (omega/alpha) of Eq. (Ifun)
+ * (0.06 and 30 Torr in the paper's tests). Any output pointer may be NULL.
+ * KIFMM_ERR_ARG unless p > 0, p_O2 > 0, p_q > 0 and xi_omega_alpha > 0 are finite.
+ */
+int kifmm_model_constants(double p_torr, double p_o2_torr, double p_q_torr, double xi_omega_alpha, double* a,
+                          double* b, double* C);
 
 /* Frees every device buffer of the plan (synchronising its stream). NULL is a no-op. */
 void kifmm_destroy(kifmm_plan_t plan);
@@ -208,6 +238,9 @@ typedef struct {
                                  * lattice with full leaves of one level (per-offset kernel matrices) */
     int64_t lattice_far;        /* 1 if, on such a lattice (surface form, no W / X lists), S2M and the local
                                  * part of L2P apply one tabulated check-surface matrix to every leaf */
+    int64_t m2m_tensor_levels;  /* levels whose M2M translations run on the tensor cores (mixed form) */
+    int64_t l2l_tensor_levels;  /* levels whose L2L translations run on the tensor cores (mixed form) */
+    int64_t upward_tensor_levels; /* levels whose upward pseudo-inverse runs as exact slices on the tensor cores */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */

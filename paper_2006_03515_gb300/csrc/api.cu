@@ -1,5 +1,6 @@
 // The C-ABI (include/kifmm.h): argument checks, plan lifetime, evaluation entry points.
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -10,6 +11,26 @@ namespace kifmm {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// Plans are identified by a counter that is never reused, not by their heap address (a new
+// plan may be created at a destroyed plan's address).
+static std::atomic<uint64_t> g_next_uid{1};
+
+// Reads the plan's device error word after its stream has drained: a bounded wait that gave
+// up (tensor-core pipelines) leaves a nonzero code there. The word is cleared, so that each
+// such event is reported once. Synchronises the plan's stream.
+static int take_device_error(Plan& p, const char* who) {
+    if (!p.err.p) return KIFMM_OK;
+    int e = 0;
+    KF_CUDA(cudaStreamSynchronize(p.stream));
+    KF_CUDA(cudaMemcpy(&e, p.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e == 0) return KIFMM_OK;
+    const int zero = 0;
+    KF_CUDA(cudaMemcpy(p.err.p, &zero, sizeof(int), cudaMemcpyHostToDevice));
+    set_error(std::string(who) + ": a bounded device wait ran out (code " + std::to_string(e) +
+              "); the result of the evaluation is not valid");
+    return KIFMM_ERR_TIMEOUT;
+}
 
 __global__ void gather_sorted_points(const double* pts, const int32_t* perm, int64_t n, double* out) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,6 +217,16 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     rc = dev_alloc(p->err, 16);
     if (rc) return fail(rc);
     if (cudaMemsetAsync(p->err.p, 0, 16, p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    {   // KIFMM_INJECT_DEVICE_ERROR=code: the word starts at that code, as if a bounded wait of
+        // the plan had given up (tests of the status reporting; no device wait is disturbed)
+        const char* inj = std::getenv("KIFMM_INJECT_DEVICE_ERROR");
+        const int code = inj ? std::atoi(inj) : 0;
+        if (code != 0 &&
+            cudaMemcpyAsync(p->err.p, &code, sizeof(int), cudaMemcpyHostToDevice, p->stream) != cudaSuccess)
+            return fail(KIFMM_ERR_CUDA);
+        if (code != 0 && cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+    }
+    p->uid = g_next_uid.fetch_add(1);
     p->uniform_h = cell_h ? 0.0 : uniform_h;
     rc = build_eval_data(*p);
     if (rc) return fail(rc);
@@ -246,7 +277,15 @@ int kifmm_eval_host(kifmm_plan_t h, const void* I_host, void* S_host, int dtype,
     KF_TRY(kifmm_eval(h, p.host_I.p, p.host_S.p, dtype, C));
     KF_CUDA(cudaMemcpyAsync(S_host, p.host_S.p, bytes, cudaMemcpyDeviceToHost, p.stream));
     KF_CUDA(cudaStreamSynchronize(p.stream));
-    return KIFMM_OK;
+    return take_device_error(p, "kifmm_eval_host");
+}
+
+int kifmm_check(kifmm_plan_t h) {
+    if (!h || !h->p) {
+        set_error("kifmm_check: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    return take_device_error(*h->p, "kifmm_check");
 }
 
 // Lane of each batch entry: distinct plans, largest first, each onto the lane with the
@@ -300,15 +339,21 @@ int kifmm_eval_batch(kifmm_plan_t* plans, const void* const* I, void* const* S, 
             p0.lane_ev.push_back(e);
         }
     }
-    std::vector<const void*> key;
-    key.reserve(3 * count + 3);
-    key.push_back((const void*)(intptr_t)count);
-    key.push_back((const void*)(intptr_t)dtype);
-    key.push_back((const void*)(intptr_t)used);
+    // the captured graph holds every argument of the batch: plans (by id), buffers and the
+    // per-field scale C (a kernel argument), so any change of them re-captures
+    std::vector<uint64_t> key;
+    key.reserve(4 * count + 3);
+    key.push_back((uint64_t)count);
+    key.push_back((uint64_t)dtype);
+    key.push_back((uint64_t)used);
     for (int k = 0; k < count; ++k) {
-        key.push_back(plans[k]);
-        key.push_back(I[k]);
-        key.push_back(S[k]);
+        const double ck = C ? C[k] : 1.0;
+        uint64_t cbits;
+        std::memcpy(&cbits, &ck, sizeof(cbits));
+        key.push_back(plans[k]->p->uid);
+        key.push_back((uint64_t)(uintptr_t)I[k]);
+        key.push_back((uint64_t)(uintptr_t)S[k]);
+        key.push_back(cbits);
     }
     auto run_one = [&](int k, cudaStream_t s) -> int {
         Plan& pk = *plans[k]->p;
@@ -427,6 +472,19 @@ int kifmm_autotune(const double* points, int64_t n, const double* cell_h, double
     return rc;
 }
 
+int kifmm_model_constants(double p, double p_o2, double p_q, double xi_oa, double* a, double* b, double* C) {
+    for (double v : {p, p_o2, p_q, xi_oa})
+        if (!(v > 0.0) || !std::isfinite(v)) {
+            set_error("kifmm_model_constants: pressures and xi (omega/alpha) must be finite and > 0");
+            return KIFMM_ERR_ARG;
+        }
+    // Sec. 2.1: chi_min = 0.035, chi_max = 2 /(cm Torr); Eq. (Ifun): C = xi (omega/alpha) p_q / (p + p_q)
+    if (a) *a = 0.035 * p_o2;
+    if (b) *b = 2.0 * p_o2;
+    if (C) *C = xi_oa * p_q / (p + p_q);
+    return KIFMM_OK;
+}
+
 void kifmm_destroy(kifmm_plan_t h) {
     if (!h) return;
     free_plan(h->p);
@@ -454,6 +512,19 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     info->m2l_tensor = p.m2l_tensor ? 1 : 0;
     info->near_tensor = p.near_tc ? 1 : 0;
     info->lattice_far = p.lat_far ? 1 : 0;
+    {   // the same conditions as the evaluation's dispatch of M2M, L2L and the upward solves
+        const bool mixed = p.precision == KIFMM_MIXED;
+        int64_t nm = 0, nl2 = 0, nup = 0;
+        for (int l = 2; l < p.tree.nlevels; ++l) {
+            if (p.lv[l].n_par > 0 && mixed && !p.cheb && p.m2m_tc && p.m2m_count[l] >= p.tc_min_tiles) ++nm;
+            if (l >= 3 && p.lv[l - 1].l2l_max > 0 && mixed && !p.cheb && p.l2l_tc && p.tc_count[l] >= p.tc_min_tiles)
+                ++nl2;
+            if (!p.cheb && ((p.lat_up && l == p.nf_level) || (p.oz && p.lv[l].n_up > p.oz_min))) ++nup;
+        }
+        info->m2m_tensor_levels = nm;
+        info->l2l_tensor_levels = nl2;
+        info->upward_tensor_levels = nup;
+    }
     info->m2l_flops = p.m2l_flops;
     {
         double up = 0;

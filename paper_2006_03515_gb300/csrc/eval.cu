@@ -500,6 +500,10 @@ int build_eval_data(Plan& p) {
         p.oz = p.precision == KIFMM_MIXED && !p.cheb && pinv_oz_supported(S) && !(up && std::string(up) == "fp64");
         const char* om = std::getenv("KIFMM_OZ_MIN");   // level-size threshold (tests use 0)
         p.oz_min = om ? std::max(0, std::atoi(om)) : kOzMinBoxes;
+        // smallest tile count of a level whose M2M / L2L take the tensor-core translation
+        // kernel (tests use 1, so that small trees run every tensor-core path)
+        const char* tm = std::getenv("KIFMM_TC_MIN_TILES");
+        p.tc_min_tiles = tm ? std::max(1, std::atoi(tm)) : kTcMinTiles;
     }
     if (p.oz) {
         int nmax = 0;
@@ -561,10 +565,6 @@ __global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, in
 // S2M (Eq. (s2m), first step): upward check potential of a leaf from its own sources.
 // One block per leaf; check points x_j = c_B + r_out r s_j, sources relative to c_B.
 constexpr int P2M_T = 160;
-// Levels with fewer tensor-core tiles than this take the SIMT apply for M2M / L2L: a tile
-// walks its slots one pipeline stage at a time (about 1.2 us a stage), so a launch of a few
-// tiles costs about 29 us whatever its work.
-constexpr int kTcMinTiles = 16;
 // FP32 kernel without the series branch: valid where (b - a) R >= 0.5 for every pair
 __device__ __forceinline__ float kern_plain_f32(float r2, const KParams& k) {
     const float rinv = rsqrt_approx(r2);
@@ -1557,7 +1557,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                                    ptr<double>(p.cheb_A), p.m0, cu, R);
             KF_LAUNCH();
             ++nl;
-        } else if (LL.n_par > 0 && mixed && p.m2m_tc && p.m2m_count[l] >= kTcMinTiles) {
+        } else if (LL.n_par > 0 && mixed && p.m2m_tc && p.m2m_count[l] >= p.tc_min_tiles) {
             // tensor cores: the children's c split FP16 x 3 (the M2L operand buffers, rewritten
             // before M2L), 8 octant slots per parent tile, staged in FP32, copied to the check rows
             const int64_t lo = t.level_start[l + 1], cnt = t.level_start[l + 2] - lo;
@@ -1672,7 +1672,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                                    ptr<double>(p.cheb_A), p.m0, dd, R);
                 KF_LAUNCH();
                 ++nl;
-            } else if (LP.l2l_max > 0 && sizeof(T) == 4 && p.l2l_tc && p.tc_count[l] >= kTcMinTiles) {
+            } else if (LP.l2l_max > 0 && sizeof(T) == 4 && p.l2l_tc && p.tc_count[l] >= p.tc_min_tiles) {
                 // tensor cores: the parents' d split into FP16 hi / lo (the M2L operand buffers, free
                 // by now), one slot per child octant, added onto the children's d
                 const int64_t lo = t.level_start[l - 1], cnt = t.level_start[l] - lo;

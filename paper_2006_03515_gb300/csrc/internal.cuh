@@ -19,6 +19,10 @@ constexpr double kROuter = 2.6;     // default upward check / downward equivalen
 // range split over many CTAs: a tensor-core slice-product CTA needs about 45 us, which a
 // handful of CTAs cannot hide.
 constexpr int kOzMinBoxes = 1024;
+// Levels with fewer tensor-core tiles than this take the SIMT apply for M2M / L2L: a tile
+// walks its slots one pipeline stage at a time (about 1.2 us a stage), so a launch of a few
+// tiles costs about 29 us whatever its work.
+constexpr int kTcMinTiles = 16;
 
 // ---- error plumbing ---------------------------------------------------------------
 void set_error(const std::string& msg);
@@ -208,6 +212,7 @@ struct Plan {
     bool oz = false;             // upward pseudo-inverse by exact slicing on the tensor cores (mixed form)
     DevBuf ozBox, ozEb;          // per-level work space: box slice images, box exponents
     int oz_min = kOzMinBoxes;    // levels with more upward solves than this use the slice products
+    int tc_min_tiles = kTcMinTiles;   // levels with at least this many tiles: tensor-core M2M / L2L
     DevBuf tc_tiles;             // int4 per tile: level, first box in tc_boxes, box count, 0
     DevBuf tc_boxes;             // boxes of every level grouped by octant, level after level
     DevBuf tc_slots;             // [tile][344] active offset slots
@@ -222,9 +227,10 @@ struct Plan {
     uint64_t nvtx_range = 0;     // open NVTX range of the current phase (0: none)
     float phase_ms[8] = {0};
     int n_phases = 0;
-    // batch graph
+    // batch graph, keyed on the batch's arguments (plan ids, buffers, count, dtype, lanes, C bits)
     cudaGraphExec_t graph_exec = nullptr;
-    std::vector<const void*> graph_key;
+    std::vector<uint64_t> graph_key;
+    uint64_t uid = 0;            // process-wide unique id of this plan (never reused)
     // concurrent batch lanes owned by this plan: streams, and events [0] fork, [1 + j] join
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_ev;

@@ -23,18 +23,25 @@ PRECISION = {"fp64": KIFMM_FP64, "mixed": KIFMM_MIXED}
 SELF_MODE = {"cell_exact": KIFMM_SELF_CELL_EXACT, "paper_gl2": KIFMM_SELF_PAPER_GL2}
 REPR = {"surface": 0, "cheb": 1}
 
-# Absorption of O2 (Eq. (gfun)): chi_min, chi_max in 1/(cm Torr).
-CHI_MIN, CHI_MAX = 0.035, 2.0
+
+def model_constants(p, p_o2, p_q=30.0, xi_omega_alpha=0.06):
+    """(a, b, C) of the Zheleznyak model for pressure p and oxygen pressure p_O2 (Torr),
+    computed by kifmm_model_constants (Sec. 2.1, Eqs. (gfun), (Ifun))."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().kifmm_model_constants(float(p), float(p_o2), float(p_q), float(xi_omega_alpha), ctypes.byref(a),
+                                        ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
 
 
 def absorption(p_o2):
-    """(a, b) = (chi_min p_O2, chi_max p_O2)."""
-    return CHI_MIN * p_o2, CHI_MAX * p_o2
+    """(a, b) = (chi_min p_O2, chi_max p_O2) from kifmm_model_constants."""
+    a, b, _ = model_constants(760.0, p_o2)
+    return a, b
 
 
 def scale_c(p, p_q=30.0, xi_omega_alpha=0.06):
-    """C = xi (omega/alpha) p_q / (p + p_q) of Eq. (Ifun)."""
-    return xi_omega_alpha * p_q / (p + p_q)
+    """C = xi (omega/alpha) p_q / (p + p_q) of Eq. (Ifun), from kifmm_model_constants."""
+    return model_constants(p, 1.0, p_q, xi_omega_alpha)[2]
 
 
 class KifmmError(RuntimeError):
@@ -57,11 +64,13 @@ class _Info(ctypes.Structure):
                 ("p2p_pairs", ctypes.c_int64), ("m2l_tensor", ctypes.c_int64), ("device_error", ctypes.c_int64),
                 ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double),
                 ("upward_mma_flops", ctypes.c_double), ("near_tensor", ctypes.c_int64),
-                ("lattice_far", ctypes.c_int64)]
+                ("lattice_far", ctypes.c_int64), ("m2m_tensor_levels", ctypes.c_int64),
+                ("l2l_tensor_levels", ctypes.c_int64), ("upward_tensor_levels", ctypes.c_int64)]
 
 
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
-           "kifmm_destroy", "kifmm_last_error", "kifmm_get_info", "kifmm_get_tree", "kifmm_get_list",
+           "kifmm_destroy", "kifmm_last_error", "kifmm_check", "kifmm_model_constants", "kifmm_get_info",
+           "kifmm_get_tree", "kifmm_get_list",
            "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
@@ -90,6 +99,9 @@ def load():
     L.kifmm_eval_host.argtypes = [vp, vp, vp, i32, dbl]
     L.kifmm_eval_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp), i32, i32,
                                    ctypes.POINTER(dbl), i32, i32]
+    L.kifmm_check.argtypes = [vp]
+    L.kifmm_model_constants.argtypes = [dbl, dbl, dbl, dbl, ctypes.POINTER(dbl), ctypes.POINTER(dbl),
+                                        ctypes.POINTER(dbl)]
     L.kifmm_destroy.argtypes = [vp]
     L.kifmm_destroy.restype = None
     L.kifmm_last_error.restype = ctypes.c_char_p
@@ -101,7 +113,8 @@ def load():
     L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
     L.kifmm_direct_noalloc.argtypes = [vp, i64, dbl, vp, vp, dbl, dbl, dbl, i32, vp]
     L.kifmm_autotune.argtypes = [vp, i64, vp, dbl, vp, i32, i32, dbl, dbl, ctypes.POINTER(_Opts), i32, vp, vp]
-    for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_get_info",
+    for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_check",
+                 "kifmm_model_constants", "kifmm_get_info",
                  "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times",
                  "kifmm_direct_noalloc", "kifmm_autotune"):
         getattr(L, name).restype = ctypes.c_int
@@ -190,6 +203,11 @@ class Plan:
                                       dt, float(C)))
         return S
 
+    def check(self):
+        """Synchronises the plan's stream and raises KifmmError (ERR_TIMEOUT) if a bounded
+        device wait of its work gave up since the last check (kifmm_check)."""
+        _check(load().kifmm_check(self._h_ptr))
+
     def info(self):
         inf = _Info()
         _check(load().kifmm_get_info(self._h_ptr, ctypes.byref(inf)))
@@ -200,7 +218,8 @@ class Plan:
                     m2l_tensor=bool(inf.m2l_tensor), device_error=int(inf.device_error),
                     m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops),
                     upward_mma_flops=float(inf.upward_mma_flops), near_tensor=bool(inf.near_tensor),
-                    lattice_far=bool(inf.lattice_far))
+                    lattice_far=bool(inf.lattice_far), m2m_tensor_levels=int(inf.m2m_tensor_levels),
+                    l2l_tensor_levels=int(inf.l2l_tensor_levels), upward_tensor_levels=int(inf.upward_tensor_levels))
 
     def tree(self):
         inf = self.info()
@@ -285,12 +304,29 @@ NOALLOC_MAX_POINTS = 65536
 def direct_noalloc(points, h, I, a, b, C=1.0, S=None, self_mode="cell_exact", stream=None):
     """Direct FP64 sum for cells of one edge h through kifmm_direct_noalloc, which uses a
     fixed device work space instead of allocating (for callers that cannot allocate, e.g.
-    inside a stream capture). points, I (and S) are CUDA float64 tensors; n <= 65536."""
+    code whose device memory belongs to another allocator). points (n, 3), I and S (n,) are
+    contiguous CUDA float64 tensors on one device; n <= 65536. Nothing is copied: a tensor
+    of the wrong dtype, shape, device or layout raises before the call."""
     import torch
-    pts = points.contiguous()
+
+    def ok(x, shape):
+        return (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+                and tuple(x.shape) == shape)
+
+    if not (isinstance(points, torch.Tensor) and points.dim() == 2):
+        raise TypeError("points must be an (n, 3) CUDA float64 tensor")
+    n = int(points.shape[0])
+    if not ok(points, (n, 3)):
+        raise TypeError("points must be a contiguous (n, 3) CUDA float64 tensor")
+    if not ok(I, (n,)):
+        raise TypeError("I must be a contiguous CUDA float64 tensor of n = %d entries" % n)
     if S is None:
         S = torch.empty_like(I)
-    _check(load().kifmm_direct_noalloc(ctypes.c_void_p(pts.data_ptr()), int(pts.shape[0]), float(h),
+    if not ok(S, (n,)):
+        raise TypeError("S must be a contiguous CUDA float64 tensor of n = %d entries" % n)
+    if not (points.device == I.device == S.device):
+        raise ValueError("points, I and S must be on one device")
+    _check(load().kifmm_direct_noalloc(ctypes.c_void_p(points.data_ptr()), n, float(h),
                                        ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(S.data_ptr()), float(a),
                                        float(b), float(C), SELF_MODE[self_mode], _stream_ptr(stream)))
     return S

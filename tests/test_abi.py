@@ -132,15 +132,28 @@ def test_batch_rejects_bad_arguments(lib):
     assert re.search(r"#define KIFMM_MAX_LANES (\d+)", hdr).group(1) == str(kifmm.KIFMM_MAX_LANES)
 
 
-def test_physics_constants():
-    # Eq. (gfun) and Eq. (Ifun) with the parameters the paper prints (Sec. 2.1, Sec. 4.1)
+def test_physics_constants(lib):
+    # Eq. (gfun) and Eq. (Ifun) with the parameters the paper prints (Sec. 2.1, Sec. 4.1),
+    # computed by kifmm_model_constants behind the C-ABI
     from golden import read as G
     c = G.paper_constants()
-    assert (kifmm.CHI_MIN, kifmm.CHI_MAX) == (c["chi_min"], c["chi_max"])
     a, b = kifmm.absorption(c["p_O2"])
+    assert a == pytest.approx(c["chi_min"] * c["p_O2"], rel=1e-15) and b == c["chi_max"] * c["p_O2"]
     assert a == pytest.approx(5.25, rel=1e-15) and b == 300.0
     C = c["xi"] * c["omega_over_alpha"] * c["p_q"] / (c["p"] + c["p_q"])
     assert kifmm.scale_c(c["p"]) == pytest.approx(C, rel=1e-15)
+    a2, b2, C2 = kifmm.model_constants(c["p"], c["p_O2"], c["p_q"], c["xi"] * c["omega_over_alpha"])
+    assert (a2, b2) == (a, b) and C2 == pytest.approx(C, rel=1e-15)
+    d = ctypes.c_double()
+    for bad in [(0.0, 150.0, 30.0, 0.06), (760.0, -1.0, 30.0, 0.06), (760.0, 150.0, float("nan"), 0.06),
+                (760.0, 150.0, 30.0, float("inf"))]:
+        assert lib.kifmm_model_constants(*bad, ctypes.byref(d), None, None) == ERR_ARG
+        assert "kifmm_model_constants" in lib.kifmm_last_error().decode()
+
+
+def test_check_rejects_null(lib):
+    assert lib.kifmm_check(None) == ERR_ARG
+    assert lib.kifmm_last_error().decode().startswith("kifmm_check")
 
 
 def test_sno_rejects_bad_sizes_on_the_host(lib):

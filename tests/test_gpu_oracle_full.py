@@ -1,0 +1,115 @@
+"""The mixed form's fast paths against the oracle KIFMM itself, point by point (marked gpu).
+
+At 64^3 cell centres with leaves of 64 cells every fast path of the mixed form engages:
+the near field as 27 per-offset kernel matrices on the tensor cores, the leaves' upward
+coefficients c = (G1 P) q by exact slices, the lattice L2P, the tcgen05 M2L, and (with
+the test switch KIFMM_TC_MIN_TILES=1, which lets a level of a few tiles take the tensor
+cores) the tensor-core M2M and L2L translations. The CUDA result is compared with the
+oracle's plain FP64 KIFMM of the same tree, surfaces and pseudo-inverse cut-off (Sec. 3,
+Eqs. (s2m)-(l2l), outline steps 1-4), not with the GPU's own FP64 form.
+
+Bars (mixed form): rel-L2 <= 1e-6 (the method's stated gate); the largest pointwise
+difference <= 1e-6 of max |S| (no point is off by more than the gate allows on the peak);
+per point, relative difference <= 1e-4 wherever |S_i| >= 1e-4 max |S| and <= 1e-3 wherever
+|S_i| >= 1e-6 max |S|. Below that the oracle's own FMM values are not a per-point
+reference: far from the source the FMM's approximation error is about 1e-5 of max |S|
+(some of its values there are negative), while the mixed form's deviation at those points
+stays near 1e-11 of max |S| (FP32 rounding of far-field terms of the peak), which the
+absolute bar covers. Measured at 64^3: 1.8e-7, 2.6e-7, 3.8e-5 and 2.7e-4.
+FP64 form: rel-L2 <= 1e-10 and per point 1e-10 of max |S| (the two share the operators'
+definitions but not the SVD).
+
+A batch of uneven fields (one CUDA graph, four lanes) is compared field by field with the
+oracle as well, so that the batch path is checked against the method and not only against
+its own per-field evaluation.
+"""
+import numpy as np
+import pytest
+
+from oracle import kernel as K
+from oracle import kifmm as KF
+from paper_2006_03515_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(x):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), dtype=torch.float64, device="cuda")
+
+
+def _relerr(x, y):
+    return float(np.linalg.norm(x - y) / np.linalg.norm(y))
+
+
+def _pointwise(got, ref, floor=1e-4):
+    """(rel-L2, max |diff| / max |ref|, largest per-point relative difference over the points
+    with |ref_i| >= floor * max |ref|)."""
+    d = np.abs(got - ref)
+    m = np.abs(ref).max()
+    sel = np.abs(ref) >= floor * m
+    return _relerr(got, ref), float(d.max() / m), float((d[sel] / np.abs(ref[sel])).max())
+
+
+@pytest.fixture(scope="module")
+def case64():
+    pts, h, I = W.config_uniform(64)
+    a, b = K.absorption_coefficients(152.0)
+    C = K.source_scale(760.0)
+    ref = KF.kifmm(pts, h, I, 64, 6, a, b, C)
+    return pts, h, I, a, b, C, ref
+
+
+@pytest.mark.parametrize("all_tensor", [False, True])
+def test_mixed_lattice_paths_against_oracle_64(kf, monkeypatch, case64, all_tensor):
+    pts, h, I, a, b, C, ref = case64
+    if all_tensor:   # every level through the tensor-core translations and exact slices
+        monkeypatch.setenv("KIFMM_TC_MIN_TILES", "1")
+        monkeypatch.setenv("KIFMM_OZ_MIN", "0")
+    p = kf.Plan(_dev(pts), float(h[0]), 64, 6, a, b, precision="mixed")
+    inf = p.info()
+    assert inf["m2l_tensor"] and inf["near_tensor"] and inf["lattice_far"]
+    assert inf["l2l_tensor_levels"] >= 1
+    if all_tensor:
+        assert inf["m2m_tensor_levels"] >= 1 and inf["upward_tensor_levels"] >= 2
+    got = p.eval(_dev(I), C=C).cpu().numpy()
+    p.check()
+    e2, emax, eloc = _pointwise(got, ref)
+    assert e2 <= 1e-6, e2
+    assert emax <= 1e-6, emax
+    assert eloc <= 1e-4, eloc
+    assert _pointwise(got, ref, 1e-6)[2] <= 1e-3
+
+
+def test_fp64_against_oracle_64(kf, case64):
+    pts, h, I, a, b, C, ref = case64
+    p = kf.Plan(_dev(pts), float(h[0]), 64, 6, a, b, precision="fp64")
+    got = p.eval(_dev(I), C=C).cpu().numpy()
+    e2, emax, eloc = _pointwise(got, ref, 1e-6)
+    assert e2 <= 1e-10 and emax <= 1e-10 and eloc <= 1e-8, (e2, emax, eloc)
+
+
+def test_batched_fields_against_oracle(kf):
+    import torch
+    st = torch.cuda.Stream()
+    fields = [W.two_channel_field(k, n_min=20, n_max=36) for k in range(4)]
+    with torch.cuda.stream(st):
+        plans, Is, Cs, refs = [], [], [], []
+        for pts, h, I, p in fields:
+            a, b = K.absorption_coefficients(0.2 * p)
+            C = K.source_scale(p)
+            plans.append(kf.Plan(_dev(pts), float(h[0]), 32, 6, a, b, precision="mixed", stream=st))
+            Is.append(_dev(I))
+            Cs.append(C)
+            refs.append(KF.kifmm(pts, h, I, 32, 6, a, b, C))
+        Ss = [torch.empty_like(x) for x in Is]
+        for _ in range(2):   # capture, then replay
+            for s in Ss:
+                s.fill_(float("nan"))
+            kf.eval_batch(plans, Is, Ss, C=Cs, capture=True, lanes=4)
+            st.synchronize()
+            for pl in plans:
+                pl.check()
+            for s, r in zip(Ss, refs):
+                e2, emax, eloc = _pointwise(s.cpu().numpy(), r)
+                assert e2 <= 1e-6 and emax <= 1e-6 and eloc <= 1e-4, (e2, emax, eloc)
