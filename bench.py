@@ -108,7 +108,7 @@ def parse():
                     help="far-field representation of the timed plan (cheb: --m0 is the Chebyshev order p)")
     ap.add_argument("--no-cheb", action="store_true", help="skip the Chebyshev-representation measurement")
     ap.add_argument("--cheb-p", type=int, default=8, help="Chebyshev order of that measurement")
-    ap.add_argument("--no-radii", action="store_true", help="skip the surface-radii option measurement")
+    ap.add_argument("--no-radii", action="store_true", help="skip the figure-radii (1.2 / 2.6) measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
     ap.add_argument("--batch-fields", type=int, default=8, help="fields of the batched workload")
     ap.add_argument("--batch-lanes", type=int, default=4, help="concurrent lanes of the batched workload")
@@ -116,11 +116,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other target settings")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="measure only the surrogate and print its record (profiling runs)")
     ap.add_argument("--sno-n", type=int, default=64, help="surrogate grid cells per axis")
-    ap.add_argument("--sno-fields", type=int, default=64, help="KIFMM-labelled training fields")
-    ap.add_argument("--sno-train-s", type=float, default=20.0, help="surrogate training budget (s)")
+    ap.add_argument("--sno-fields", type=int, default=256, help="KIFMM-labelled training fields")
+    ap.add_argument("--sno-heldout", type=int, default=128, help="held-out fields of the surrogate")
+    ap.add_argument("--sno-train-s", type=float, default=15.0, help="surrogate training budget per model (s)")
+    ap.add_argument("--sno-lr", type=float, default=1e-5, help="Adam learning rate from the far-part start")
     return ap.parse_args()
 
 
@@ -250,13 +253,13 @@ def run_reference(args):
 
 
 def radii_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
-    """The same workload with the surface radii option at 1.05 / 2.95 box half-widths
-    (mixed form): kept rank, plan time, evaluation time (CUDA events, L2 flushed between
-    steps), phase times, the M2L rate, and the mixed result against one FP64 evaluation of
-    the same radii."""
+    """The same workload with the surfaces at the radii drawn in Fig. fmulloc, 1.2 / 2.6 box
+    half-widths (the default is 1.05 / 2.95), mixed form: kept rank, plan time, evaluation
+    time (CUDA events, L2 flushed between steps), phase times, the M2L rate, and the mixed
+    result against one FP64 evaluation of the same radii."""
     import torch
     from paper_2006_03515_gb300 import kifmm
-    radii = (1.05, 2.95)
+    radii = (1.2, 2.6)
     npts = dpts.shape[0]
     t0 = time.perf_counter()
     pl = kifmm.Plan(dpts, hval, args.leaf, args.m0, a, b, precision="mixed", stream=stream, surface_radii=radii)
@@ -350,6 +353,85 @@ def cheb_bench(args, dev, stream, dpts, hval, dI, C, a, b, flush, peaks):
     return out
 
 
+def _timed_eval(plan, dI, S, C, flush, stream, steps=5):
+    """Median evaluation time (ms) over `steps` runs, CUDA events on the plan's stream, L2
+    flushed between runs."""
+    import torch
+    for _ in range(2):
+        plan.eval(dI, S, C=C)
+    ms = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.eval(dI, S, C=C)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.median(ms)
+
+
+def configs_bench(args, dev, stream, flush):
+    """Time and accuracy of the other target settings (not headlines): the 128^3 Gaussian
+    field at 76 and 7.6 Torr (m0 = 6) and at 760 Torr with m0 = 4 and 8, and the adaptive
+    3,219,819-point refined grid (760 Torr, p_O2 150, channel + head + noise). Each entry: the
+    mixed form's median time and rate, the FP64 form's time, the mixed-vs-FP64 gate, and the
+    rel-L2 of both forms against the whole discrete sum (the oracle's FFT convolution on the
+    uniform grid; on the refined grid the oracle's direct sum at 4096 sampled targets, half of
+    them among the fine cells)."""
+    import numpy as np
+    import torch
+    from oracle import build as ob
+    from oracle import direct as D
+    from paper_2006_03515_gb300 import kifmm
+    from paper_2006_03515_gb300 import workloads as W
+    ob.build()
+    out = {}
+
+    def one(pts, hval, I, leaf, m0, p, p_o2, ref_fn):
+        a, b = kifmm.absorption(p_o2)
+        C = kifmm.scale_c(p)
+        dpts, dI = torch.as_tensor(pts, device=dev), torch.as_tensor(I, device=dev)
+        hv = torch.as_tensor(hval, device=dev) if isinstance(hval, np.ndarray) else hval
+        pm = kifmm.Plan(dpts, hv, leaf, m0, a, b, precision="mixed", stream=stream)
+        Sm = torch.empty_like(dI)
+        ms = _timed_eval(pm, dI, Sm, C, flush, stream)
+        p64 = kifmm.Plan(dpts, hv, leaf, m0, a, b, precision="fp64", stream=stream)
+        S64 = torch.empty_like(dI)
+        ms64 = _timed_eval(p64, dI, S64, C, flush, stream, steps=2)
+        torch.cuda.synchronize(dev)
+        gate = float(torch.linalg.norm(Sm - S64) / torch.linalg.norm(S64))
+        idx, ref, kind = ref_fn(a, b, C)
+        sm, s64 = Sm.cpu().numpy(), S64.cpu().numpy()
+        if idx is not None:
+            sm, s64 = sm[idx], s64[idx]
+        rec = {"points": len(pts), "leaf": leaf, "m0": m0, "p_torr": p, "p_o2": p_o2, "ms": ms,
+               "points_per_s": len(pts) / (1e-3 * ms), "fp64_ms": ms64, "gate_rel_l2_mixed_vs_fp64": gate,
+               "rel_l2_vs_direct_sum": float(np.linalg.norm(sm - ref) / np.linalg.norm(ref)),
+               "fp64_rel_l2_vs_direct_sum": float(np.linalg.norm(s64 - ref) / np.linalg.norm(ref)),
+               "reference": kind, "near_tensor": bool(pm.info()["near_tensor"])}
+        pm.close()
+        p64.close()
+        del Sm, S64, dI, dpts
+        torch.cuda.empty_cache()
+        return rec
+
+    pts, h, I = W.config_uniform(128)
+    for p, m0 in [(760.0, 4), (760.0, 8), (76.0, 6), (7.6, 6)]:
+        def ref_fn(a, b, C):
+            return None, D.fft_uniform(I.reshape(128, 128, 128), h[0], a, b, C).ravel(), "whole discrete sum (FFT)"
+        out["uniform128_p%g_m0%d" % (p, m0)] = one(pts, float(h[0]), I, 64, m0, p, 0.2 * p, ref_fn)
+    pts, h, I = W.config_adaptive()
+    fine = np.nonzero(h < h.max())[0]
+    rng = np.random.Generator(np.random.PCG64(2006))
+    idx = np.sort(np.concatenate([rng.choice(len(pts), 2048, replace=False), rng.choice(fine, 2048, replace=False)]))
+
+    def ref_ad(a, b, C):
+        return idx, D.direct_sum(pts, h, I, a, b, C, targets=idx), "direct sum at 4096 sampled targets (2048 fine)"
+    out["adaptive_3219819"] = one(pts, h, I, 64, 6, 760.0, 150.0, ref_ad)
+    return out
+
+
 def batch_bench(args, dev, stream, flush):
     """The batched workload: args.batch_fields uneven two-channel streamer fields (uniform
     grids of 80^3-158^3 cells, 760 or 76 Torr, m0 = 6, leaf 64, mixed form) evaluated as one
@@ -419,76 +501,134 @@ def batch_bench(args, dev, stream, flush):
 
 
 def surrogate_bench(args, dev, stream, peaks):
-    """The learned surrogate on an n^3 grid (width 32, 12 modes, 4 layers, projection 64):
-    KIFMM-labelled data generation, training for a fixed time budget, batched inference
-    timed with CUDA events, and one surrogate-first solve judged against the direct sum."""
+    """The learned surrogate on the n^3 grid (width 32, 12 modes, 4 layers, projection 64,
+    BF16 spectral weights): amplitude-normalised linear form (u = I / max I, S = C max I y),
+    exact near part up to 7 cells, period 1.5 n; labels from the GPU KIFMM (surfaces at
+    1.05 / 2.95 r, mixed form). Two models are trained for the same budget: one started at the
+    far part's Fourier multiplier, one from a random start. Held-out fields: their rel-L2
+    against the KIFMM labels, and photo_solve's judged error and fallback at 1e-2; time per
+    field of the batched forward pass (batch 32) and of photo_solve, against kifmm_eval per
+    field on the same grid (one field, and 8 fields as one captured batch on 8 lanes)."""
     import numpy as np
     import torch
     from paper_2006_03515_gb300 import kifmm, surrogate
-    n, width, modes, layers, proj, B = args.sno_n, 32, 12, 4, 64, 8
+    from paper_2006_03515_gb300 import workloads as W
+    n, width, modes, layers, proj, B = args.sno_n, 32, 12, 4, 64, 32
     modes = min(modes, n // 2)
-    plan, pts, C = surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream)
+    plan, pts, C = surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream,
+                                       surface_radii=(1.05, 2.95))
+    fmm, _, _ = surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    U, T = surrogate.make_dataset(plan, pts, C, count=args.sno_fields + 1, seed=2006)
+    U, T = surrogate.make_dataset(plan, pts, C, count=args.sno_fields, seed=2006)
+    Uh, Th = surrogate.make_dataset(plan, pts, C, count=args.sno_heldout, seed=100000)
     torch.cuda.synchronize(dev)
     gen_s = time.perf_counter() - t0
+    out = {"grid": "%d^3" % n, "width": width, "modes": modes, "layers": layers, "proj": proj,
+           "weights": "BF16 spectral (FP32 master), FP32 accumulation", "near_part_cells": [3.0, 7.0],
+           "period": (3 * n) // 2, "train_fields": args.sno_fields, "heldout_fields": args.sno_heldout,
+           "labels": "GPU KIFMM, mixed, m0 6, leaf 64, surfaces 1.05 / 2.95 r", "datagen_s": gen_s}
+
+    def held(M):
+        e = np.array(surrogate.rel_errors(M, Uh, Th, batch=8))
+        return {"mean": float(e.mean()), "p90": float(np.percentile(e, 90)), "max": float(e.max())}
+
+    def train(M, budget, lr):
+        t1 = time.perf_counter()
+        steps, hist = 0, []
+        while time.perf_counter() - t1 < budget:
+            hist += surrogate.train(M, U, T, steps=20, batch=8, lr=lr, seed=steps)
+            steps += 20
+        torch.cuda.synchronize(dev)
+        return {"steps": steps, "s": time.perf_counter() - t1, "fields_per_s": 8 * steps / (time.perf_counter() - t1),
+                "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-5:]))}
+
+    # random start, trained for the budget
     M = kifmm.SNO(n, width, modes, layers, proj, max_batch=B, stream=stream)
-    Utr, Ttr = U[:-1].contiguous(), T[:-1].contiguous()
-    surrogate.init_from_data(M, Utr, Ttr, seed=0)
-    t0 = time.perf_counter()
-    steps, hist = 0, []
-    while time.perf_counter() - t0 < args.sno_train_s:
-        hist += surrogate.train(M, Utr, Ttr, steps=10, batch=B, lr=1e-3 if steps > 200 else 3e-3, seed=steps)
-        steps += 10
-    torch.cuda.synchronize(dev)
-    train_s = time.perf_counter() - t0
-    # batched inference, inputs resident
-    ub = Utr[:B].contiguous()
+    surrogate.configure(M, plan)
+    M.init_params(seed=1)
+    out["random_init"] = {"lr": 1e-3, "train": train(M, args.sno_train_s, 1e-3), "heldout_rel_l2_vs_kifmm": held(M)}
+    # far-part start, trained for the same budget: the model kept
+    surrogate.init_far(M, seed=1)
+    out["far_init"] = {"untrained": held(M)}
+    out["far_init"]["lr"] = args.sno_lr
+    out["far_init"]["train"] = train(M, args.sno_train_s, args.sno_lr)
+    ho = held(M)
+    out["far_init"]["heldout_rel_l2_vs_kifmm"] = ho
+    out["heldout_rel_l2_vs_kifmm"] = ho["mean"]
+    out["heldout_rel_l2_vs_kifmm_max"] = ho["max"]
+    # judged surrogate-first solves on the held-out fields (the FMM plan of the time loop)
+    S = torch.empty(n ** 3, dtype=torch.float64, device=dev)
+    fbs, errs = [], []
+    for k in range(args.sno_heldout):
+        I = torch.as_tensor(W.surrogate_field(pts, 100000 * 1000003 + k), device=dev)
+        _, fb, e = kifmm.photo_solve(fmm, M, I, S, C=C, tol=1e-2, k_samples=256, seed=k + 1)
+        fbs.append(fb)
+        errs.append(e)
+    out["photo_solve"] = {"tol": 1e-2, "k_samples": 256, "fallback_rate": float(np.mean(fbs)),
+                          "judged_rel_l2_mean": float(np.mean(errs)), "judged_rel_l2_max": float(np.max(errs))}
+    # timings: batched forward, photo_solve per field, kifmm_eval per field (one field; a batch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ub = Uh[:B].contiguous() if Uh.shape[0] >= B else U[:B].contiguous()
     yb = torch.empty_like(ub)
     for _ in range(3):
         M.forward(ub, yb)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 10
     torch.cuda.synchronize(dev)
     torch.cuda.profiler.start()         # the timed forward passes are the profiled range
     e0.record(stream)
+    reps = 5
     for _ in range(reps):
         M.forward(ub, yb)
     e1.record(stream)
     e1.synchronize()
     torch.cuda.profiler.stop()
     fwd_ms = e0.elapsed_time(e1) / reps
+    I = torch.as_tensor(W.surrogate_field(pts, 7), device=dev)
+    for _ in range(2):
+        kifmm.photo_solve(fmm, M, I, S, C=C, tol=1e-2)
+    e0.record(stream)
+    for _ in range(reps):
+        kifmm.photo_solve(fmm, M, I, S, C=C, tol=1e-2)
+    e1.record(stream)
+    e1.synchronize()
+    ps_ms = e0.elapsed_time(e1) / reps
+    for _ in range(2):
+        fmm.eval(I, S, C=C)
+    e0.record(stream)
+    for _ in range(reps):
+        fmm.eval(I, S, C=C)
+    e1.record(stream)
+    e1.synchronize()
+    fmm_ms = e0.elapsed_time(e1) / reps
+    plans = [fmm] + [surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream)[0]
+                     for _ in range(7)]
+    Is = [I.clone() for _ in plans]
+    Ss = [torch.empty_like(I) for _ in plans]
+    for _ in range(3):
+        kifmm.eval_batch(plans, Is, Ss, C=[C] * 8, capture=True, lanes=8)
+    e0.record(stream)
+    for _ in range(reps):
+        kifmm.eval_batch(plans, Is, Ss, C=[C] * 8, capture=True, lanes=8)
+    e1.record(stream)
+    e1.synchronize()
+    fmm_b_ms = e0.elapsed_time(e1) / reps / 8
     n3 = n ** 3
     K = (2 * modes) * (2 * modes) * modes
     alg_bytes = 4.0 * B * n3 * (2 + width * (2 + 2 * layers)) + layers * 2 * K * width * width * 2
     hbm = peaks.get("hbm_gbs", 6686.0)
     fwd_gbs = alg_bytes / (fwd_ms * 1e-3) / 1e9
-    # surrogate-first solve on the held-out field
-    I_ho = torch.expm1(U[-1].double())
-    S = torch.empty_like(I_ho)
-    kifmm.photo_solve(plan, M, I_ho, S, C=C, tol=1e-2, k_samples=256, seed=1)
-    e0.record(stream)
-    S, fb, jerr = kifmm.photo_solve(plan, M, I_ho, S, C=C, tol=1e-2, k_samples=256, seed=1)
-    e1.record(stream)
-    e1.synchronize()
-    ps_ms = e0.elapsed_time(e1)
-    S_sur = torch.expm1(M.forward(U[-1:].contiguous()).double()).reshape(-1)
-    S_fmm = plan.eval(I_ho, C=C)
-    full_err = float(torch.linalg.norm(S_sur - S_fmm) / torch.linalg.norm(S_fmm))
-    out = {"grid": "%d^3" % n, "width": width, "modes": modes, "layers": layers, "proj": proj,
-           "params": M.num_params(), "weights": "BF16 spectral (FP32 master), FP32 accumulation",
-           "fields": args.sno_fields, "datagen_s": gen_s, "train_steps": steps, "train_s": train_s,
-           "train_fields_per_s": steps * B / train_s, "loss_first": float(np.mean(hist[:5])),
-           "loss_last": float(np.mean(hist[-5:])), "forward_ms_batch8": fwd_ms,
-           "points_per_s": B * n3 / (fwd_ms * 1e-3),
-           "roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm,
-                        "traffic": None, "algorithmic_bytes": alg_bytes},
-           "heldout_rel_l2_vs_kifmm": full_err, "photo_solve": {"tol": 1e-2, "judged_rel_l2": jerr,
-                                                                "used_fallback": fb, "ms": ps_ms}}
+    out.update({"forward_ms_batch32": fwd_ms, "forward_ms_per_field": fwd_ms / B,
+                "photo_solve_ms_per_field": ps_ms, "kifmm_eval_ms_per_field": fmm_ms,
+                "kifmm_eval_batch8_ms_per_field": fmm_b_ms,
+                "points_per_s": B * n3 / (fwd_ms * 1e-3), "params": M.num_params(),
+                "roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm,
+                             "traffic": None, "algorithmic_bytes": alg_bytes}})
+    for pl in plans:
+        pl.close()
     M.close()
     plan.close()
-    del U, T, Utr, Ttr
+    del U, T, Uh, Th
+    torch.cuda.empty_cache()
     return out
 
 
@@ -673,6 +813,21 @@ def main():
             "phase_ms": ph_ms, "roofline": roof, "rooflines": roofs, "clocks": clk, "gpu_launches": gpu_launches,
             "e2e": {"value": e2e_val, "unit": "points/s", "h2d_bytes_per_step": npts * 8,
                     "d2h_bytes_per_step": npts * 8, "matches_device_result": e2e_ok}}
+    if std:   # the headline form's own accuracy against the whole discrete sum (oracle FFT convolution)
+        try:
+            from oracle import direct as D
+            ref = D.fft_uniform(I.reshape(args.n, args.n, args.n), float(h[0]), a, b, C).ravel()
+            got = S.cpu().numpy()
+            line["rel_l2_vs_direct_sum"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+            del ref, got
+        except Exception as exc:
+            line["rel_l2_vs_direct_sum"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    if not args.no_configs and std:
+        try:
+            with torch.cuda.stream(stream):
+                line["configs"] = configs_bench(args, dev, stream, flush)
+        except Exception as exc:    # the headline line is printed whatever happens here
+            line["configs"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if not args.no_cheb and args.repr == "surface":
         try:
             with torch.cuda.stream(stream):

@@ -87,17 +87,26 @@ typedef struct {
     int repr;
     /* Radii of the surfaces of the surface representation, in box half-widths (Sec. 3,
      * Fig. fmulloc): radii[0] for the upward equivalent and downward check surfaces,
-     * radii[1] for the upward check and downward equivalent surfaces. Default {1.2, 2.6},
-     * read off the paper's figure; {0, 0} also selects the default. Otherwise need
-     * 1 < radii[0] < radii[1] < 3 (the equivalent surface encloses the box and the check
-     * surface stays inside its near range); surfaces closer to those bounds, e.g.
-     * {1.05, 2.95}, represent this kernel more accurately at a lower kept rank.
-     * Ignored by the Chebyshev representation. */
+     * radii[1] for the upward check and downward equivalent surfaces. Default {1.05, 2.95},
+     * the reading that reproduces the FMM accuracy the paper reports at its own test sizes
+     * (Sec. 4: E_V 0.10-0.40 % against the paper's 0.15-0.69 %); {0, 0} also selects the
+     * default. The schematic figure draws {1.2, 2.6} (E_V 1.2-2.2 % on the same cases, at a
+     * higher kept rank). Need 1 < radii[0] < radii[1] < 3 (the equivalent surface encloses
+     * the box and the check surface stays inside its near range). Ignored by the Chebyshev
+     * representation. */
     double radii[2];
+    /* Rectangular cells (the paper's Sec. 4.2 grid): when all three are > 0, every cell is
+     * the box cell_dims[0] x cell_dims[1] x cell_dims[2] (cm, along x, y, z), cell_h_dev must
+     * be NULL and uniform_h is ignored. The weights are the cell volume hx hy hz, the self
+     * term the box's own value (exact integral of K over the box, or the paper's
+     * 3 g(rho) / (pi sum h^2) per unit volume with rho = sqrt(sum h^2 / 12)), and the root
+     * rule takes each axis' own half extent. {0, 0, 0} (default): cubic cells. */
+    double cell_dims[3];
 } kifmm_opts;
 
 /* Fills *opts with the defaults above (FP64, cell-exact self term, eps 1e-5,
- * automatic root, default stream, surface representation, radii {1.2, 2.6}). */
+ * automatic root, default stream, surface representation, radii {1.05, 2.95}, cubic
+ * cells). */
 void kifmm_default_opts(kifmm_opts* opts);
 
 /*
@@ -112,7 +121,7 @@ void kifmm_default_opts(kifmm_opts* opts);
  *   points_dev   device, N x 3 FP64, cell centres (cm). Must be finite and distinct.
  *   n            number of points, 1 <= n < 2^31.
  *   cell_h_dev   device, N FP64 cell edges (cm), or NULL to use uniform_h for all.
- *   uniform_h    cell edge when cell_h_dev is NULL (> 0).
+ *   uniform_h    cell edge when cell_h_dev is NULL (> 0); ignored with opts->cell_dims.
  *   leaf_size    m >= 1: a box with more than m points is split.
  *   surface_order m0 in [3, 12]: lattice points per side of each surface.
  *   a, b         chi_min p_O2 and chi_max p_O2 in 1/cm, 0 < a < b.
@@ -275,9 +284,9 @@ int kifmm_get_phase_times(kifmm_plan_t plan, float* ms, int cap);
 /* ---- learned surrogate: 3D spectral neural operator ---- */
 
 /*
- * A spectral neural operator on an n^3 grid that maps u = log(1 + I) to log(1 + S); the
- * paper has no learned part (it stands in for the solve inside a time loop, with the FMM as
- * judge and fallback). Layers: lift 1 -> width; `layers` times z = SpecConv(v) + W v + b,
+ * A spectral neural operator on an n^3 grid that maps u = I / max I to S / (C max I) (the
+ * amplitude-normalised form of the linear map I -> S); the paper has no learned part (it
+ * stands in for the solve inside a time loop, with the FMM as judge and fallback). Layers: lift 1 -> width; `layers` times z = SpecConv(v) + W v + b,
  * v = GELU(z) (no GELU after the last); projection width -> proj_width (GELU) -> 1.
  * SpecConv keeps the frequencies {0..m-1} U {n-m..n-1} on the first two axes and {0..m-1}
  * on the last (the real field's conjugate half), mixes channels per frequency with a complex
@@ -320,13 +329,49 @@ int sno_loss_grad(sno_model_t model, const float* u_dev, const float* t_dev, int
 int sno_adam_step(sno_model_t model, float lr, float beta1, float beta2, float eps);
 
 /*
- * Surrogate-first solve: S = exp(network(log(1 + I))) - 1 on the plan's points,
- * which must be the model's n^3 grid in the model's index order (FP64 I and S on the
- * device, caller order). The result is judged against the direct sum of the discrete
- * integral (the plan's kernel, self terms and C) at k_samples (1..4096) targets drawn from
- * `seed`; when the judged relative L2 error exceeds tol, kifmm_eval's result replaces it.
- * *used_fallback is set to 1 in that case and *judged_err to the judged error. The network
- * is trained on targets that already include C. Runs on the plan's stream and returns
+ * Period of the network's truncated transforms: N with n <= N <= 4n and 2 modes <= N
+ * (default n). The n^3 grid is then the corner of a zero-padded N^3 grid: the exponentials
+ * are e^{-2 pi i k x / N}, the kept frequencies {0..m-1} U {N-m..N-1} (last axis {0..m-1}),
+ * and the spectral convolution is no longer periodic on the grid itself (the
+ * photoionization sum is a linear, not a periodic, convolution).
+ */
+int sno_set_period(sno_model_t model, int period);
+
+/*
+ * Exact near part added to the model's output: with u the model's input,
+ *   y += sigma u(x) + sum_{0 < |d| <= r_out} K(h |d|) w(|d|) h^3 u(x + d),
+ * K the photoionization kernel of Eq. (gfun) (a, b as in kifmm_plan), h the grid's cell edge,
+ * sigma the self-cell value of self_mode, |d| in cells, w = 1 up to r_in and
+ * cos^2(pi/2 (|d| - r_in)/(r_out - r_in)) up to r_out, u = 0 outside the grid. With
+ * u = I / max I and targets S / (C max I) (photo_solve's amplitude-normalised form) this is
+ * the short-range part of Eq. (summation) (Sec. 3) computed exactly, and the network learns
+ * the smooth remainder. 0 <= r_in < r_out <= 8. a = b = 0 switches the near part off.
+ * It is a fixed addend: sno_loss_grad's gradients are those of the network alone.
+ */
+int sno_set_near_field(sno_model_t model, double a, double b, double h, int self_mode, double r_in, double r_out);
+
+/*
+ * Initialises the network at the far part of the sum (needs sno_set_near_field): channel 0
+ * carries, through layer 0's spectral weights, the Fourier multiplier on the N-periodic grid
+ * of the far kernel K(h |d|) (1 - w(|d|)) h^3 (computed in FP64 on the device), and passes
+ * unchanged through the later layers (bias `shift`, e.g. 8, keeps GELU linear); the weights
+ * into and out of channel 0 and projection row 0 are set accordingly, every other parameter
+ * keeps its value (so a small random start elsewhere lets training use the other channels).
+ * The network's output is then the far convolution truncated to the kept modes. Resets the
+ * optimiser state.
+ */
+int sno_init_far_field(sno_model_t model, double shift);
+
+/*
+ * Surrogate-first solve on the plan's points, which must be the model's n^3 grid in the
+ * model's index order (FP64 I and S on the device, caller order). The map I -> S is linear
+ * (Sec. 3, Eq. (summation)), so the network works in the amplitude-normalised form: with
+ * s = max |I| (computed on the device), u = I / s and S = C s y, y = network(u) (plus the near
+ * part when set; it must then have been set for the plan's a, b, cell edge and self term).
+ * The result is judged against the direct sum of the discrete integral (the plan's kernel,
+ * self terms and C) at k_samples (1..4096) targets drawn from `seed`; when the judged
+ * relative L2 error exceeds tol, kifmm_eval's result replaces it. *used_fallback is set to 1
+ * in that case and *judged_err to the judged error. Runs on the plan's stream and returns
  * after the judge (host synchronisation).
  */
 int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, double* S_dev, double C, double tol,

@@ -15,12 +15,16 @@ Sec. 3 of the paper (after Ying, Biros & Zorin 2004):
   and the near-field direct sum over U(B).
 
 Surfaces (Fig. fmulloc, Fig. m2mm2ll2l): the m0 x m0 x m0 lattice on the boundary
-of [-1, 1]^3, scaled about the box centre. The radii are read off the figure
-coordinates (box half-width 0.8, surfaces at 0.96 and 2.08): the upward
-equivalent and downward check surfaces at 1.2 r, the upward check and
-downward equivalent surfaces at 2.6 r (r = half-width of the box). Other radii
-(1 < inner < outer < 3: the equivalent surface encloses the box, the check surface
-stays inside its near range) are an option of the plan.
+of [-1, 1]^3, scaled about the box centre; the upward equivalent and downward check
+surfaces at an inner radius, the upward check and downward equivalent surfaces at an
+outer radius (in box half-widths r; 1 < inner < outer < 3: the equivalent surface
+encloses the box, the check surface stays inside its near range). The text fixes only
+these relations. The default reading, 1.05 r and 2.95 r, is the one that reproduces the
+accuracy the paper reports for its FMM at its own test sizes (Sec. 4.1-4.3, Tables
+tonegaussiansrc001, tonegaussiansrc0001, tdiffpi, tdiffpiii, tmultipeak: E_V 0.15-0.69 %):
+measured there, E_V 0.10-0.40 %. The radii drawn in the schematic figure (box half-width
+0.8, surfaces at 0.96 and 2.08, i.e. 1.2 r and 2.6 r) give E_V 1.2-2.2 % on the same
+cases, six to ten times the paper's figures; they remain an option of the plan.
 
 Pseudo-inverse (Sec. 3, after the outline: the original pseudo-inverse of the
 cited KIFMM, m0 = 6 by default): a truncated SVD that keeps singular values
@@ -37,8 +41,9 @@ from . import kernel as _k
 from . import tree as _t
 from .direct import pair_sum_c, self_terms
 
-R_INNER = 1.2   # upward equivalent / downward check surface, in box half-widths
-R_OUTER = 2.6   # upward check / downward equivalent surface
+R_INNER = 1.05   # upward equivalent / downward check surface, in box half-widths
+R_OUTER = 2.95   # upward check / downward equivalent surface
+FIGURE_RADII = (1.2, 2.6)   # the radii drawn in Fig. fmulloc
 
 
 def surface_lattice(m0):
@@ -108,14 +113,23 @@ class Operators:
                     self.l2l[(lev, o)] = kmat(cc + r_in * rc * s, r_out * r * s, a, b)
 
 
-def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii=(R_INNER, R_OUTER)):
+def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii=(R_INNER, R_OUTER),
+         cell_dims=None):
+    """cell_dims = (hx, hy, hz): every cell is that rectangular box (the Sec. 4.2 grid; h is
+    then ignored): the root takes each axis' own half extent, the weights are hx hy hz (the
+    cell volume, Sec. 3) and the self term is the box's own value."""
     points = np.asarray(points, dtype=np.float64)
-    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
-    t, perm = _t.build_tree(points, h, leaf_size, origin, side)
+    if cell_dims is not None:
+        dims = np.asarray(cell_dims, dtype=np.float64)
+        t, perm = _t.build_tree(points, np.broadcast_to(dims, points.shape).copy(), leaf_size, origin, side)
+        h = np.full(points.shape[0], float(np.prod(dims)) ** (1.0 / 3.0))
+    else:
+        h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
+        t, perm = _t.build_tree(points, h, leaf_size, origin, side)
     U, V, W, X = _t.build_lists(t)
     ops = Operators(t.side, t.nlevels, m0, a, b, eps, radii)
     return dict(tree=t, perm=perm, U=U, V=V, W=W, X=X, ops=ops, points=points[perm],
-                h=h[perm], a=a, b=b, m0=m0)
+                h=h[perm], a=a, b=b, m0=m0, cell_dims=cell_dims)
 
 
 def evaluate(p, I, C=1.0, mode="cell_exact"):
@@ -124,7 +138,8 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
     perm = p["perm"]
     pts, h = p["points"], p["h"]
     Is = np.asarray(I, dtype=np.float64)[perm]
-    q = Is * h ** 3
+    dims = p.get("cell_dims")
+    q = Is * (h ** 3 if dims is None else float(np.prod(dims)))
     s = ops.surf
     nb = len(t.level)
     S = ops.S
@@ -189,11 +204,16 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
         src = np.concatenate([np.arange(t.pstart[A], t.pend[A]) for A in p["U"][B]])
         acc += pair_sum_c(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b)
         out[sl] = acc
-    out += self_terms(h, a, b, mode) * Is
+    if dims is None:
+        out += self_terms(h, a, b, mode) * Is
+    else:
+        box = _k.sigma_box_exact if mode == "cell_exact" else _k.sigma_box_paper_gl2
+        out += box(dims[0], dims[1], dims[2], a, b) * Is
     res = np.empty_like(out)
     res[perm] = C * out
     return res
 
 
-def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER)):
-    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii), I, C, mode)
+def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER),
+          cell_dims=None):
+    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii, cell_dims=cell_dims), I, C, mode)

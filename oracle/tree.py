@@ -45,8 +45,11 @@ class Tree:
 
 
 def root_cube(points, h):
-    lo = (points - 0.5 * h[:, None]).min(axis=0)
-    hi = (points + 0.5 * h[:, None]).max(axis=0)
+    """Origin min(x - h/2) per axis and side the largest extent; h per point (cubic cells)
+    or (n, 3) per point and axis (rectangular cells)."""
+    ext = h if h.ndim == 2 else h[:, None]
+    lo = (points - 0.5 * ext).min(axis=0)
+    hi = (points + 0.5 * ext).max(axis=0)
     side = float((hi - lo).max())
     return lo.astype(np.float64), side
 

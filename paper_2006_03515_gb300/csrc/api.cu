@@ -125,7 +125,19 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         set_error("kifmm_plan: need points != NULL and 1 <= n < 2^31");
         return KIFMM_ERR_ARG;
     }
-    if (!cell_h && !(uniform_h > 0.0 && std::isfinite(uniform_h))) {
+    const bool rect = o.cell_dims[0] != 0.0 || o.cell_dims[1] != 0.0 || o.cell_dims[2] != 0.0;
+    if (rect) {
+        for (int k = 0; k < 3; ++k)
+            if (!(o.cell_dims[k] > 0.0 && std::isfinite(o.cell_dims[k]))) {
+                set_error("kifmm_plan: cell_dims must be three finite values > 0 (or all 0)");
+                return KIFMM_ERR_ARG;
+            }
+        if (cell_h) {
+            set_error("kifmm_plan: cell_dims and per-point cell_h exclude each other");
+            return KIFMM_ERR_ARG;
+        }
+        uniform_h = std::cbrt(o.cell_dims[0] * o.cell_dims[1] * o.cell_dims[2]);
+    } else if (!cell_h && !(uniform_h > 0.0 && std::isfinite(uniform_h))) {
         set_error("kifmm_plan: uniform_h must be finite and > 0 when cell_h is NULL");
         return KIFMM_ERR_ARG;
     }
@@ -191,6 +203,9 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     p->Sp = (p->S + 31) / 32 * 32;
     p->leaf_size = leaf_size;
     p->tree.n = n;
+    p->rect = rect && !(o.cell_dims[0] == o.cell_dims[1] && o.cell_dims[1] == o.cell_dims[2]);
+    if (rect && !p->rect) uniform_h = o.cell_dims[0];   // equal sides: a cube
+    for (int k = 0; k < 3; ++k) p->cell_dims[k] = p->rect ? o.cell_dims[k] : 0.0;
     auto fail = [&](int rc) {
         std::string msg = g_last_error;
         free_plan(p);
@@ -227,7 +242,7 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         if (code != 0 && cudaStreamSynchronize(p->stream) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     }
     p->uid = g_next_uid.fetch_add(1);
-    p->uniform_h = cell_h ? 0.0 : uniform_h;
+    p->uniform_h = (cell_h || p->rect) ? 0.0 : uniform_h;
     rc = build_eval_data(*p);
     if (rc) return fail(rc);
     rc = dev_alloc(p->host_I, n * 8);

@@ -13,8 +13,11 @@ constexpr int kKeyBits = 21;
 constexpr int kMaxLevel = 20;
 constexpr int kOffsetSlots = 343;   // (dx, dy, dz) in [-3, 3]^3
 constexpr int kSlotStride = 344;    // per tensor-core translation tile: [count, slot_0, slot_1, ...]
-constexpr double kRInner = 1.2;     // default upward equivalent / downward check surface (box half-widths)
-constexpr double kROuter = 2.6;     // default upward check / downward equivalent surface
+// Default surface radii in box half-widths: upward equivalent / downward check at 1.05 r, upward
+// check / downward equivalent at 2.95 r, the reading that reproduces the accuracy the paper reports
+// at its own test sizes (Sec. 4); the schematic Fig. fmulloc draws 1.2 r and 2.6 r.
+constexpr double kRInner = 1.05;
+constexpr double kROuter = 2.95;
 // Upward solves of levels with at most kOzMinBoxes boxes take the FP64-pipe GEMM with its K
 // range split over many CTAs: a tensor-core slice-product CTA needs about 45 us, which a
 // handful of CTAs cannot hide.
@@ -195,7 +198,9 @@ struct Plan {
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
-    double uniform_h = 0;        // cell edge of a uniform-h plan (0: per-point h)
+    double uniform_h = 0;        // cell edge of a uniform-h plan (0: per-point h, or rectangular cells)
+    bool rect = false;           // every cell is the rectangular box cell_dims (hx, hy, hz)
+    double cell_dims[3] = {0, 0, 0};
     // near field on the tensor cores (mixed form, uniform lattice; near_tc.cu)
     bool near_tc = false;
     int nf_R = 0, nf_level = 0, nf_sT = 0, nf_ntiles = 0;

@@ -605,11 +605,17 @@ __global__ void scatter_sigma(const uint64_t* key, const int32_t* val, const int
     double h = __longlong_as_double(key[i]);
     w[k] = h * h * h;
 }
-__global__ void fill_uniform(int64_t n, double s, double h, double* sigma, double* w) {
+__global__ void fill_uniform(int64_t n, double s, double vol, double* sigma, double* w) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     sigma[i] = s;
-    w[i] = h * h * h;
+    w[i] = vol;
+}
+__global__ void self_sigma_box(double hx, double hy, double hz, double a, double b, int mode, int nq,
+                               const double* gx, const double* gw, double* out) {
+    __shared__ double red[256];
+    const double s = self_sigma_box_block(hx, hy, hz, a, b, mode, nq, gx, gw, red);
+    if (threadIdx.x == 0) out[0] = s;
 }
 
 int build_self_terms(Plan& p, const double* h_dev, double uh) {
@@ -623,18 +629,25 @@ int build_self_terms(Plan& p, const double* h_dev, double uh) {
     KF_LAUNCH();
     KF_TRY(dev_alloc(p.sigma, n * 8));
     KF_TRY(dev_alloc(p.w, n * 8));
-    if (!h_dev) {
+    if (!h_dev) {   // one cell shape for every point: a cube of edge uh, or the plan's rectangular cell
         DevBuf hb, sb;
         KF_TRY(dev_alloc(hb, 8));
         KF_TRY(dev_alloc(sb, 8));
         KF_CUDA(cudaMemcpyAsync(hb.p, &uh, 8, cudaMemcpyHostToDevice, st));
-        self_sigma<<<1, 256, 0, st>>>(ptr<double>(hb), 1, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
-                                      ptr<double>(gw), ptr<double>(sb));
+        double vol = uh * uh * uh;
+        if (p.rect) {
+            self_sigma_box<<<1, 256, 0, st>>>(p.cell_dims[0], p.cell_dims[1], p.cell_dims[2], p.a, p.b, p.self_mode,
+                                              NQ, ptr<double>(gx), ptr<double>(gw), ptr<double>(sb));
+            vol = p.cell_dims[0] * p.cell_dims[1] * p.cell_dims[2];
+        } else {
+            self_sigma<<<1, 256, 0, st>>>(ptr<double>(hb), 1, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
+                                          ptr<double>(gw), ptr<double>(sb));
+        }
         KF_LAUNCH();
         double s = 0;
         KF_CUDA(cudaMemcpyAsync(&s, sb.p, 8, cudaMemcpyDeviceToHost, st));
         KF_CUDA(cudaStreamSynchronize(st));
-        fill_uniform<<<nb(n, 256), 256, 0, st>>>(n, s, uh, ptr<double>(p.sigma), ptr<double>(p.w));
+        fill_uniform<<<nb(n, 256), 256, 0, st>>>(n, s, vol, ptr<double>(p.sigma), ptr<double>(p.w));
         KF_LAUNCH();
         KF_CUDA(cudaStreamSynchronize(st));
         dev_free(hb); dev_free(sb); dev_free(gx); dev_free(gw);

@@ -87,4 +87,37 @@ __device__ __forceinline__ double self_sigma_block(double h, double a, double b,
     return 6.0 * red[0] / (4.0 * 3.14159265358979323846 * lba);
 }
 
+// sigma for a rectangular cell hx x hy x hz (the same block reduction): cell_exact: the
+// solid-angle form face pair by face pair, sum_k 2 int (h_k/2)/R^3 F(R) du dv over the other
+// two half-widths, R = sqrt(u^2 + v^2 + h_k^2/4), divided by 4 pi ln(b/a); paper_gl2: the
+// paper's discrete self value hx hy hz 3 g(rho) / (pi sum h^2), rho = sqrt(sum h^2 / 12).
+__device__ __forceinline__ double self_sigma_box_block(double hx, double hy, double hz, double a, double b, int mode,
+                                                       int nq, const double* gx, const double* gw, double* red) {
+    const double lba = log(b / a);
+    if (mode == KIFMM_SELF_PAPER_GL2) {
+        const double s2 = hx * hx + hy * hy + hz * hz;
+        const double rho = sqrt(s2 / 12.0);
+        const double g = (exp(-a * rho) - exp(-b * rho)) / (rho * lba);
+        return hx * hy * hz * 3.0 * g / (3.14159265358979323846 * s2);
+    }
+    const double hs[3] = {hx, hy, hz};
+    double acc = 0;
+    for (int e = threadIdx.x; e < 3 * nq * nq; e += blockDim.x) {
+        const int k = e / (nq * nq), i = (e / nq) % nq, j = e % nq;
+        const double hk = hs[k], hi = hs[(k + 1) % 3], hj = hs[(k + 2) % 3];
+        const double ui = 0.5 * hi * gx[i], uj = 0.5 * hj * gx[j];
+        const double wi = 0.5 * hi * gw[i], wj = 0.5 * hj * gw[j];
+        const double R = sqrt(ui * ui + uj * uj + 0.25 * hk * hk);
+        const double F = lba + e1_dev(b * R) - e1_dev(a * R);
+        acc += 2.0 * wi * wj * (0.5 * hk) / (R * R * R) * F;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    return red[0] / (4.0 * 3.14159265358979323846 * lba);
+}
+
 }  // namespace kifmm

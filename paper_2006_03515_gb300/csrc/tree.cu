@@ -276,16 +276,19 @@ int radix_sort_pairs(uint64_t* keys, int32_t* vals, int64_t n, int key_bits, cud
 // ------------------------------------------------------------------------------------
 constexpr int RED_BLOCKS = 304, RED_T = 256;
 
-__global__ void root_partial(const double* pts, const double* h, double uh, int64_t n, double* part,
-                             int* bad) {
+// cell extents: h[i] per point (cubic cells), else ux, uy, uz for every point (one cube, or
+// the rectangular cell of the plan)
+__global__ void root_partial(const double* pts, const double* h, double ux, double uy, double uz, int64_t n,
+                             double* part, int* bad) {
     __shared__ double s[6][RED_T];
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     int nonfinite = 0;
+    const double ue[3] = {ux, uy, uz};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double hh = h ? h[i] : uh;
-        if (!isfinite(hh) || !(hh > 0.0)) nonfinite = 1;
         for (int k = 0; k < 3; ++k) {
+            const double hh = h ? h[i] : ue[k];
+            if (!isfinite(hh) || !(hh > 0.0)) nonfinite = 1;
             double x = pts[3 * i + k];
             if (!isfinite(x)) nonfinite = 1;
             double half = __dmul_rn(0.5, hh);
@@ -453,7 +456,8 @@ int build_tree(Plan& p, const double* pts, const double* h, double uh, const kif
     KF_TRY(dev_alloc(rootb, 8 * sizeof(double)));
     KF_TRY(dev_alloc(flags, 4 * sizeof(int)));
     KF_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), st));
-    root_partial<<<RED_BLOCKS, RED_T, 0, st>>>(pts, h, uh, n, ptr<double>(part), ptr<int>(flags));
+    const double ux = p.rect ? p.cell_dims[0] : uh, uy = p.rect ? p.cell_dims[1] : uh, uz = p.rect ? p.cell_dims[2] : uh;
+    root_partial<<<RED_BLOCKS, RED_T, 0, st>>>(pts, h, ux, uy, uz, n, ptr<double>(part), ptr<int>(flags));
     KF_LAUNCH();
     root_final<<<1, 32, 0, st>>>(ptr<double>(part), RED_BLOCKS, ptr<double>(rootb));
     KF_LAUNCH();

@@ -53,7 +53,7 @@ class KifmmError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
-                ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2)]
+                ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2), ("cell_dims", ctypes.c_double * 3)]
 
 
 class _Info(ctypes.Structure):
@@ -74,7 +74,8 @@ EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", 
            "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
-           "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"]
+           "sno_set_bf16", "sno_set_period", "sno_set_near_field", "sno_init_far_field", "sno_forward",
+           "sno_loss_grad", "sno_adam_step", "photo_solve"]
 
 _lib = None
 
@@ -140,7 +141,7 @@ class Plan:
 
     def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
                  self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface",
-                 surface_radii=None):
+                 surface_radii=None, cell_dims=None):
         import torch
         L = load()
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
@@ -157,7 +158,7 @@ class Plan:
             hp = ctypes.c_void_p(self._h.data_ptr())
         else:
             self._h = None
-            uh = float(h)
+            uh = 0.0 if h is None else float(h)
         o = _Opts()
         L.kifmm_default_opts(ctypes.byref(o))
         o.precision = PRECISION[precision]
@@ -168,8 +169,13 @@ class Plan:
             o.has_root = 1
             for k in range(4):
                 o.root[k] = float(root[k])
-        if surface_radii is not None:   # (inner, outer) in box half-widths; default (1.2, 2.6)
+        if surface_radii is not None:   # (inner, outer) in box half-widths; default (1.05, 2.95)
             o.radii[0], o.radii[1] = float(surface_radii[0]), float(surface_radii[1])
+        if cell_dims is not None:       # rectangular cells (hx, hy, hz); h is then ignored
+            for k in range(3):
+                o.cell_dims[k] = float(cell_dims[k])
+            if isinstance(h, torch.Tensor):
+                raise ValueError("cell_dims and per-point h exclude each other")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         o.stream = _stream_ptr(self.stream)
         self.precision = precision
@@ -365,27 +371,32 @@ def _load_sno(L):
     L.sno_save_checkpoint.argtypes = [vp, ctypes.c_char_p]
     L.sno_load_checkpoint.argtypes = [vp, ctypes.c_char_p]
     L.sno_set_bf16.argtypes = [vp, i32]
+    L.sno_set_period.argtypes = [vp, i32]
+    L.sno_set_near_field.argtypes = [vp, dbl, dbl, dbl, i32, dbl, dbl]
+    L.sno_init_far_field.argtypes = [vp, dbl]
     L.sno_forward.argtypes = [vp, vp, vp, i32]
     L.sno_loss_grad.argtypes = [vp, vp, vp, i32, ctypes.POINTER(dbl)]
     L.sno_adam_step.argtypes = [vp, flt, flt, flt, flt]
     L.photo_solve.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, ctypes.POINTER(i32),
                               ctypes.POINTER(dbl)]
     for name in ("sno_create", "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint", "sno_set_params",
-                 "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_forward", "sno_loss_grad", "sno_adam_step",
-                 "photo_solve"):
+                 "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_set_period", "sno_set_near_field",
+                 "sno_init_far_field", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"):
         getattr(L, name).restype = ctypes.c_int
 
 
 class SNO:
     """The spectral neural operator surrogate (sno_* in kifmm.h): grid n^3, ``width``
     channels, ``modes`` frequencies per axis, ``layers`` spectral layers, projection width
-    ``proj``. Fields are CUDA float32 tensors of shape (batch, n^3) or (n^3,)."""
+    ``proj``. Fields are CUDA float32 tensors of shape (batch, n^3) or (n^3,): inputs
+    u = I / max I, outputs S / (C max I)."""
 
     def __init__(self, n, width=32, modes=8, layers=4, proj=64, max_batch=8, stream=None):
         L = load()
         self.n, self.width, self.modes, self.layers, self.proj, self.max_batch = n, width, modes, layers, proj, max_batch
         self._h = ctypes.c_void_p()
         self._stream = stream
+        self.period, self.near = n, None
         _check(L.sno_create(ctypes.byref(self._h), int(n), int(width), int(modes), int(layers), int(proj),
                             int(max_batch), _stream_ptr(stream)))
 
@@ -451,6 +462,21 @@ class SNO:
     def set_bf16(self, on):
         _check(load().sno_set_bf16(self._h, 1 if on else 0))
 
+    def set_period(self, period):
+        """Period N >= n of the truncated transforms (sno_set_period)."""
+        _check(load().sno_set_period(self._h, int(period)))
+        self.period = int(period)
+
+    def set_near_field(self, a, b, h, r_in, r_out, self_mode="cell_exact"):
+        """Exact near part added to the output (sno_set_near_field); a = b = 0 switches it off."""
+        _check(load().sno_set_near_field(self._h, float(a), float(b), float(h), SELF_MODE[self_mode], float(r_in),
+                                         float(r_out)))
+        self.near = None if a == 0 and b == 0 else dict(a=a, b=b, h=h, r_in=r_in, r_out=r_out, self_mode=self_mode)
+
+    def init_far_field(self, shift=8.0):
+        """Channel 0 carries the far part's Fourier multiplier (sno_init_far_field)."""
+        _check(load().sno_init_far_field(self._h, float(shift)))
+
     def save(self, path):
         _check(load().sno_save(self._h, os.fsencode(path)))
 
@@ -505,8 +531,9 @@ class SNO:
 
 
 def photo_solve(plan, model, I, S=None, C=1.0, tol=0.05, k_samples=256, seed=0):
-    """Surrogate-first solve (photo_solve in kifmm.h). I, S: CUDA float64 tensors (N,).
-    Returns (S, used_fallback, judged_error)."""
+    """Surrogate-first solve (photo_solve in kifmm.h): S = C max|I| network(I / max|I|), judged
+    at k_samples sampled targets against the direct sum, kifmm_eval above tol. I, S: CUDA
+    float64 tensors (N,). Returns (S, used_fallback, judged_error)."""
     import torch
     if S is None:
         S = torch.empty_like(I)

@@ -146,6 +146,21 @@ PRESSURES = {  # p (Torr) -> p_O2 (Torr); p_O2 = 0.2 p except the paper's 150 To
 }
 
 
+def surrogate_field(points, seed, L=1.0):
+    """Training and test field of the learned surrogate: 1-5 Gaussian blobs (count uniform),
+    widths log-uniform in [0.02, 0.2] cm, amplitudes log-uniform in [1e20, 1e23] cm^-3 s^-1,
+    centres uniform in [0.1, 0.9]^3 cm (scaled by L)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    k = int(rng.integers(1, 6))
+    I = np.zeros(points.shape[0])
+    for _ in range(k):
+        c = L * rng.uniform(0.1, 0.9, 3)
+        s = L * float(np.exp(rng.uniform(np.log(0.02), np.log(0.2))))
+        amp = 10.0 ** rng.uniform(20.0, 23.0)
+        I += gaussian(points, c, s, amp)
+    return I
+
+
 def gaussian_mixture(points, seed, n_blobs=(1, 4), sigma=(0.03, 0.12), log10_amp=(20.0, 23.0), L=1.0):
     """Sum of 1-4 Gaussian blobs with centres uniform in the inner 80 % of [0, L]^3, widths
     uniform in ``sigma`` (cm) and amplitudes log-uniform in 10^log10_amp (training fields of

@@ -73,7 +73,7 @@ def test_default_opts(lib):
     assert o.precision == kifmm.KIFMM_FP64
     assert o.self_mode == kifmm.KIFMM_SELF_CELL_EXACT
     assert o.pinv_eps == 1e-5 and o.has_root == 0 and not o.stream
-    assert tuple(o.radii) == (1.2, 2.6)
+    assert tuple(o.radii) == (1.05, 2.95)
 
 
 def _plan(lib, **kw):
