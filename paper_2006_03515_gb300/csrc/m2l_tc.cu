@@ -14,29 +14,19 @@
 // multiplies the gathered source rows c[A] (A operand, 128 x 64) by the chunk's rows of
 // T[slot] (B operand, NT x 64), both K-major in the 128-byte swizzled layout.
 //
-// Row scaling: the sources of one target row are brought to a common scale, the row's
-// largest source: e_row = min over the row's sources of e_A, and the source rows, stored as
-// c[A] 2^{e_A}, are multiplied by 2^{-(e_A - e_row)} (exact in FP16 unless the product falls
-// below FP16's normal range, i.e. for sources 2^14 and more below the row's largest, whose
-// contributions lose bits far below the row's FP32 accuracy). Every slot of a row then adds
-// into one tensor-memory accumulator, and the epilogue drains it once per span of SPAN slots
-// (the tensor core's own truncating accumulation spans at most SPAN slots) and scales the
-// row by 2^{-(e_row + e_T)} once at the end.
-//
 // Roles (warp specialization, 11 warps):
-//  * all threads, at the tile's start: e_row of the tile's 128 rows (shared memory).
 //  * warps 8-9, producers: per iteration each thread gathers two source rows with
 //    16-byte cp.async copies (hi and lo, zero-filled where the box has no source at this
 //    offset); thread 0 of warp 8 also moves the pre-swizzled B chunk with two 1-D bulk
-//    copies (completion on the stage's "full" mbarrier). One iteration later, when its own
-//    copies have landed, a thread rescales its rows in shared memory (FP16 x2 multiplies by
-//    powers of two), fences them for the tensor core and arrives on the stage's "full".
-//  * warp 10, lane 0: waits for a full stage, issues its k-steps x 3 MMAs into the span's
+//    copies. Completion arrives on the stage's "full" mbarrier.
+//  * warp 10, lane 0: waits for a full stage, issues its k-steps x 3 MMAs into the slot's
 //    tensor-memory accumulator and commits the stage's "empty" mbarrier; after the last
-//    chunk of a span it commits the accumulator's "ready" mbarrier.
-//  * warps 0-7, epilogue: two accumulators take the spans in turn; the epilogue adds a
-//    finished one into FP32 registers (round-to-nearest) and releases it; (R <= 256) within
-//    a k-chunk the small cross terms are accumulated before the hi x hi terms.
+//    chunk of a slot it commits the accumulator's "ready" mbarrier.
+//  * warps 0-7, epilogue: a ring of up to four accumulators takes the slots in turn; the
+//    epilogue scales a finished one by the slot's 2^{-(e_A + e_T)} into FP32 registers
+//    (round-to-nearest) and releases it. The tensor core's own (truncating) accumulation
+//    thus spans one slot, not the V list, and (R <= 256) within a k-chunk the small cross
+//    terms are accumulated before the hi x hi terms.
 // Every wait is bounded; a timeout sets an abort flag that ends the other roles' waits,
 // records an error code, and the tensor memory is freed before the CTA exits.
 #include <cuda_fp16.h>
@@ -55,8 +45,6 @@ constexpr int TC_HI_EXP = 14;             // scaled operands keep their largest 
 constexpr int TC_EPI = 256;               // epilogue threads (warps 0-7)
 constexpr int TC_PROD = 64;               // producer threads (warps 8-9), two source rows each
 constexpr int TC_THREADS = TC_EPI + TC_PROD + 32;
-constexpr int TC_SPAN = 8;                // slots per drained accumulator
-constexpr int TC_EZERO = 1 << 20;         // exponent of an all-zero source row (never the row's largest)
 
 // ------------------------------------------------------------------------------------
 // plan and per-evaluation operand preparation
@@ -98,15 +86,14 @@ __global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* 
     float m = 0.f;
     for (int k = lane; k < R; k += 32) m = fmaxf(m, fabsf((float)row[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    int e = TC_EZERO;               // all zero: no scale of its own
+    int e = 0;
     if (m > 0.f) {
         int ex;
         frexpf(m, &ex);             // m = f 2^ex, f in [0.5, 1)
         e = TC_HI_EXP + 1 - ex;     // m 2^e in [2^13, 2^14)
     }
-    const int es = e == TC_EZERO ? 0 : e;
     for (int k = lane; k < R; k += 32) {
-        const float x = ldexpf((float)row[k], es);
+        const float x = ldexpf((float)row[k], e);
         const __half h = __float2half_rn(x);
         chi[b * R + k] = h;
         clo[b * R + k] = __float2half_rn(x - __half2float(h));
@@ -131,17 +118,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int n0 = blockIdx.y * NT;
     constexpr int A_BYTES = TC_M * 128, B_BYTES = NT * 128;
     constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-    // two span accumulators of ACC columns each: the MMAs of a span wait for the drain of the
-    // span before last
+    // a ring of NACC slot accumulators of ACC columns each in the 512 TMEM columns, so that the
+    // MMAs of a slot wait for the drain of the slot NACC back, not the one before last
     constexpr int ACC = (NT + 31) / 32 * 32;
-    constexpr int NACC = 2;
+    constexpr int NACC = 512 / ACC >= 4 ? 4 : 512 / ACC;
     constexpr uint32_t NCOLS = NACC * ACC <= 32 ? 32 : (NACC * ACC <= 64 ? 64 : (NACC * ACC <= 128 ? 128 : (NACC * ACC <= 256 ? 256 : 512)));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ uint64_t full[NS], empty[NS], ready[NACC], freed[NACC];
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
-    __shared__ int sl[344];             // [count, slot_0, ...] of this tile
-    __shared__ int erow[2][TC_M];       // per row: its largest source's exponent (two partial minima)
+    __shared__ int sl[344];   // [count, slot_0, ...] of this tile
     unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 tile = tiles[blockIdx.x];   // level, first box (index into all_boxes), box count
@@ -150,25 +136,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int sT = tabs.sT[tile.x];
     const int32_t* __restrict__ boxes = all_boxes + tile.y;
     const int nbox = tile.z;
+    const int t0 = 0;
     for (int e = tid; e < 344; e += TC_THREADS) sl[e] = slots[(int64_t)blockIdx.x * 344 + e];
     __syncthreads();
     const int ns = sl[0];
     const int total = ns * NK;
-    const int nspan = (ns + TC_SPAN - 1) / TC_SPAN;
-    // row exponents: e_row = min over the row's sources of e_A (threads 0-255: row, half of the slots)
-    if (tid < 2 * TC_M) {
-        const int row = tid & (TC_M - 1), part = tid >> 7;
-        const int box = row < nbox ? boxes[row] : -1;
-        int e = TC_EZERO;
-        if (box >= 0)
-            for (int si = part; si < ns; si += 2) {
-                const int a = vtab[(int64_t)box * vstride + sl[1 + si]];
-                if (a >= 0) e = min(e, cexp[a]);
-            }
-        erow[part][row] = e;
-    }
-    __syncthreads();
-    if (tid < TC_M) erow[0][tid] = min(erow[0][tid], erow[1][tid]);
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
@@ -195,58 +167,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     if (warp >= 8 && warp < 10) {
         // ---------------- producers ----------------
         const int p = tid - TC_EPI;          // 0..63: rows p and p + 64 of the tile
-        int box2[2], er2[2];
-        for (int h = 0; h < 2; ++h) {
-            box2[h] = (p + 64 * h < nbox) ? boxes[p + 64 * h] : -1;
-            er2[h] = erow[0][p + 64 * h];
-        }
+        int box2[2];
+        for (int h = 0; h < 2; ++h) box2[h] = (t0 + p + 64 * h < nbox) ? boxes[t0 + p + 64 * h] : -1;
         // source box of each row for the current slot; the next slot's are fetched one slot
         // ahead so that the index load is off the critical path
         auto lookup = [&](int si, int h) -> int {
             return (si < ns && box2[h] >= 0) ? vtab[(int64_t)box2[h] * vstride + sl[1 + si]] : -1;
         };
-        // the row's rescale exponent for a source: its distance below the row's largest source
-        auto shift_of = [&](int a, int h) -> int { return a >= 0 ? cexp[a] - er2[h] : 0; };
         int acur[2] = {lookup(0, 0), lookup(0, 1)};
         int anext[2] = {lookup(1, 0), lookup(1, 1)};
-        int kcur[2] = {shift_of(acur[0], 0), shift_of(acur[1], 1)};
-        // the previous iteration's stage, waiting for its own copies before its rescale
-        int prev_s = -1, prev_kv = 0;
-        int prev_k[2] = {0, 0};
-        // rows p, p + 64 of stage s times 2^{-k}: FP16 x2 multiplies by powers of two (two
-        // factors below 2^-14; sources more than 2^28 below the row's largest are dropped)
-        auto rescale = [&](int s, int kv, const int* ks) {
-            unsigned char* st = base + s * STAGE;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int k = ks[h];
-                if (k <= 0) continue;
-                const __half2 f1 = __float2half2_rn(ldexpf(1.0f, -min(k, 14)));
-                const __half2 f2 = __float2half2_rn(ldexpf(1.0f, -max(0, min(k - 14, 14))));
-                const bool drop = k > 28;
-                const int row = p + 64 * h;
-#pragma unroll
-                for (int j = 0; j < TC_KH / 8; ++j) {
-                    if (8 * j >= kv) break;
-                    const uint32_t o = sw128_off_h(row, 8 * j);
-#pragma unroll
-                    for (int part = 0; part < 2; ++part) {
-                        uint4* q = reinterpret_cast<uint4*>(st + part * A_BYTES + o);
-                        uint4 v = *q;
-                        __half2* hv = reinterpret_cast<__half2*>(&v);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const __half2 x = __hmul2(__hmul2(hv[u], f1), f2);
-                            hv[u] = drop ? __float2half2_rn(0.f) : x;
-                        }
-                        *q = v;
-                    }
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
-            mbar_arrive(smem_u32(&full[s]));
-        };
-        bool aborted = false;
         for (int it = 0; it < total; ++it) {
             const int s = it % NS;
             if (it % NK == 0 && it > 0) {
@@ -255,13 +184,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 acur[1] = anext[1];
                 anext[0] = lookup(si + 1, 0);
                 anext[1] = lookup(si + 1, 1);
-                kcur[0] = shift_of(acur[0], 0);
-                kcur[1] = shift_of(acur[1], 1);
             }
-            if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NS - 1) & 1), &abort_flag)) {
-                aborted = true;
-                break;
-            }
+            if (it >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / NS - 1) & 1), &abort_flag)) break;
             const int slot = sl[1 + it / NK];
             const int kc = it % NK;
             const int k0 = kc * TC_KH;
@@ -301,71 +225,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     }
                 }
             }
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            if (prev_s >= 0) {   // the previous stage's copies have landed: rescale, then it is full
-                asm volatile("cp.async.wait_group 1;" ::: "memory");
-                rescale(prev_s, prev_kv, prev_k);
-            }
-            prev_s = s;
-            prev_kv = kvalid;
-            prev_k[0] = kcur[0];
-            prev_k[1] = kcur[1];
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
-        if (!aborted && prev_s >= 0) rescale(prev_s, prev_kv, prev_k);
     } else if (warp == 10) {
         // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = f16_idesc(TC_M, NT);
             uint32_t fphase[NS] = {};
-            bool ok = true;
-            for (int g = 0; g < nspan && ok && !abort_flag; ++g) {
-                const int j = g % NACC;
-                if (g >= NACC && !mbar_wait(smem_u32(&freed[j]), (uint32_t)(((g - NACC) / NACC) & 1), &abort_flag))
+            for (int si = 0; si < ns && !abort_flag; ++si) {
+                const int j = si % NACC;
+                if (si >= NACC && !mbar_wait(smem_u32(&freed[j]), (uint32_t)(((si - NACC) / NACC) & 1), &abort_flag))
                     break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t dacc = tmem + (uint32_t)(j * ACC);
-                const int s0 = g * TC_SPAN, s1 = min(ns, s0 + TC_SPAN);
-                for (int si = s0; si < s1 && ok; ++si) {
-                    for (int kc = 0; kc < NK; ++kc) {
-                        const int it = si * NK + kc, s = it % NS;
-                        if (!mbar_wait(smem_u32(&full[s]), fphase[s], &abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        fphase[s] ^= 1u;
-                        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                        const unsigned char* st = base + s * STAGE;
-                        const uint32_t ah = smem_u32(st), al = ah + A_BYTES, bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
-                        const int ksteps = min(TC_KH, R - kc * TC_KH) / 16;
-                        const bool first = si == s0 && kc == 0;   // the span's first MMA overwrites
-                        if (NB == 1) {
-                            // the small cross terms of the chunk first, then its hi x hi terms: the
-                            // accumulator truncates each addition, so most additions then land on a
-                            // smaller partial sum (16 FP16 = 32 bytes along K inside the swizzle row)
-                            for (int k = 0; k < ksteps; ++k) {
-                                const uint32_t ko = 32u * k;
-                                const uint32_t acc = (first && k == 0) ? 0u : 1u;
-                                mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, acc);
-                                mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
-                            }
-                            for (int k = 0; k < ksteps; ++k) {
-                                const uint32_t ko = 32u * k;
-                                mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, 1u);
-                            }
-                        } else {
-                            // row blocks of 256 (R > 256): the interleaved order (consecutive MMAs on
-                            // the same A tile)
-                            for (int k = 0; k < ksteps; ++k) {
-                                const uint32_t ko = 32u * k;
-                                const uint32_t acc = (first && k == 0) ? 0u : 1u;
-                                mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
-                                mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
-                                mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
-                            }
-                        }
-                        mma_commit(smem_u32(&empty[s]));
+                bool ok = true;
+                for (int kc = 0; kc < NK; ++kc) {
+                    const int it = si * NK + kc, s = it % NS;
+                    if (!mbar_wait(smem_u32(&full[s]), fphase[s], &abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    fphase[s] ^= 1u;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const unsigned char* st = base + s * STAGE;
+                    const uint32_t ah = smem_u32(st), al = ah + A_BYTES, bh = ah + 2 * A_BYTES, bl = bh + B_BYTES;
+                    const int ksteps = min(TC_KH, R - kc * TC_KH) / 16;
+                    if (NB == 1) {
+                        // the small cross terms of the chunk first, then its hi x hi terms: the
+                        // accumulator truncates each addition, so most additions then land on a
+                        // small partial sum (16 FP16 = 32 bytes along K inside the swizzle row)
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, acc);
+                            mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
+                    } else {
+                        // row blocks of 256 (R > 256): the interleaved order, which measured 8 %
+                        // faster there (consecutive MMAs on the same A tile)
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t ko = 32u * k;
+                            const uint32_t acc = (kc > 0 || k > 0) ? 1u : 0u;
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bh + ko), idesc, acc);
+                            mma_f16(dacc, sw128_desc(ah + ko), sw128_desc(bl + ko), idesc, 1u);
+                            mma_f16(dacc, sw128_desc(al + ko), sw128_desc(bh + ko), idesc, 1u);
+                        }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
                 }
                 if (!ok) break;
                 mma_commit(smem_u32(&ready[j]));
@@ -380,9 +291,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         float acc[NT / 2];
 #pragma unroll
         for (int k = 0; k < NT / 2; ++k) acc[k] = 0.f;
-        for (int g = 0; g < nspan; ++g) {
-            const int j = g % NACC;
-            const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((g / NACC) & 1), &abort_flag);
+        // this row's box and the scale 2^{-(e_A + e_T)} of its source at each slot (one slot ahead)
+        const int brow = t0 + 32 * q + lane;
+        const int bbox = brow < nbox ? boxes[brow] : -1;
+        auto slot_scale = [&](int si) -> float {
+            if (si >= ns || bbox < 0) return 0.f;
+            const int a = vtab[(int64_t)bbox * vstride + sl[1 + si]];
+            return a >= 0 ? pow2i(-(cexp[a] + sT)) : 0.f;
+        };
+        float fnext = slot_scale(0);
+        for (int si = 0; si < ns; ++si) {
+            const int j = si % NACC;
+            const float f = fnext;
+            fnext = slot_scale(si + 1);
+            const bool ok = mbar_wait(smem_u32(&ready[j]), (uint32_t)((si / NACC) & 1), &abort_flag);
             if (__any_sync(0xffffffffu, !ok)) break;   // warp-uniform exit (tcgen05.ld is .sync.aligned)
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
@@ -398,19 +320,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     : "r"(ta));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int k = 0; k < 16; ++k) acc[cc + k] += __uint_as_float(v[k]);
+                for (int k = 0; k < 16; ++k) acc[cc + k] = fmaf(__uint_as_float(v[k]), f, acc[cc + k]);
             }
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&freed[j]));
         }
-        const int bi = 32 * q + lane;
+        const int bi = t0 + 32 * q + lane;
         if (!abort_flag && bi < nbox) {
-            const int er = erow[0][bi];
-            const float f = er >= TC_EZERO ? 0.f : pow2i(-(er + sT));   // undo 2^{e_row + e_T}
             float4* o = reinterpret_cast<float4*>(d + (int64_t)boxes[bi] * R + n0 + col0);
 #pragma unroll
             for (int k = 0; k < NT / 8; ++k) {
-                float4 v = make_float4(acc[4 * k] * f, acc[4 * k + 1] * f, acc[4 * k + 2] * f, acc[4 * k + 3] * f);
+                float4 v = make_float4(acc[4 * k], acc[4 * k + 1], acc[4 * k + 2], acc[4 * k + 3]);
                 if (accum) {   // add to the row already there (L2L onto the M2L result)
                     const float4 u = o[k];
                     v = make_float4(u.x + v.x, u.y + v.y, u.z + v.z, u.w + v.w);

@@ -57,16 +57,21 @@ def case64():
     a, b = K.absorption_coefficients(152.0)
     C = K.source_scale(760.0)
     ref = KF.kifmm(pts, h, I, 64, 6, a, b, C)
-    return pts, h, I, a, b, C, ref
+    # the radii drawn in Fig. fmulloc keep a rank above S = 152 rounded to R = 160, where the
+    # M2M translations also take the tensor cores (they need S <= R)
+    ref_fig = KF.kifmm(pts, h, I, 64, 6, a, b, C, radii=KF.FIGURE_RADII)
+    return pts, h, I, a, b, C, ref, ref_fig
 
 
 @pytest.mark.parametrize("all_tensor", [False, True])
 def test_mixed_lattice_paths_against_oracle_64(kf, monkeypatch, case64, all_tensor):
-    pts, h, I, a, b, C, ref = case64
+    pts, h, I, a, b, C, ref, ref_fig = case64
+    radii = None
     if all_tensor:   # every level through the tensor-core translations and exact slices
         monkeypatch.setenv("KIFMM_TC_MIN_TILES", "1")
         monkeypatch.setenv("KIFMM_OZ_MIN", "0")
-    p = kf.Plan(_dev(pts), float(h[0]), 64, 6, a, b, precision="mixed")
+        radii, ref = KF.FIGURE_RADII, ref_fig
+    p = kf.Plan(_dev(pts), float(h[0]), 64, 6, a, b, precision="mixed", surface_radii=radii)
     inf = p.info()
     assert inf["m2l_tensor"] and inf["near_tensor"] and inf["lattice_far"]
     assert inf["l2l_tensor_levels"] >= 1
@@ -82,7 +87,7 @@ def test_mixed_lattice_paths_against_oracle_64(kf, monkeypatch, case64, all_tens
 
 
 def test_fp64_against_oracle_64(kf, case64):
-    pts, h, I, a, b, C, ref = case64
+    pts, h, I, a, b, C, ref, _ = case64
     p = kf.Plan(_dev(pts), float(h[0]), 64, 6, a, b, precision="fp64")
     got = p.eval(_dev(I), C=C).cpu().numpy()
     e2, emax, eloc = _pointwise(got, ref, 1e-6)

@@ -170,8 +170,12 @@ def test_mixed_matches_fp64(kf, m0, po2):
 @pytest.mark.parametrize("adaptive", [False, True])
 def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
     """The mixed form's upward pseudo-inverse on the tensor cores (exact integer slices, FP64
-    combination) against the same plan's FP64-pipe GEMM: FP64 agreement of the upward
-    coefficients c of every box."""
+    combination) against the same plan's FP64-pipe GEMM: agreement of the upward coefficients
+    c of every box to FP64 accuracy. Each input row is cut to 54-bit fixed point relative to
+    its largest element, so both products err by about 2^-53 sum_k |G1_rk chk_k|, which
+    exceeds |c_r| by the cancellation in G1 chk (up to ~1e6 here with the default surfaces):
+    the bar is 1e-9 of the box's largest coefficient, three orders below the FP32 arithmetic
+    of the rest of the mixed form."""
     if adaptive:
         pts, h = _adaptive_small()
         I = W.streamer_source(pts, axis_xy=(0.5, 0.5), z_range=(0.2, 0.7), radius=0.05, head=(0.5, 0.5, 0.7),
@@ -200,7 +204,7 @@ def test_upward_tensor_slices_match_fp64(kf, monkeypatch, adaptive):
     s_64, c_64 = run("fp64")
     scale = np.abs(c_64).max(axis=1, keepdims=True)
     scale[scale == 0] = 1.0
-    assert np.max(np.abs(c_tc - c_64) / scale) <= 1e-12
+    assert np.max(np.abs(c_tc - c_64) / scale) <= 1e-9
     assert _relerr(s_tc, s_64) <= 1e-9
 
 
