@@ -110,8 +110,10 @@ def parse():
     ap.add_argument("--cheb-p", type=int, default=8, help="Chebyshev order of that measurement")
     ap.add_argument("--no-radii", action="store_true", help="skip the figure-radii (1.2 / 2.6) measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload measurement")
-    ap.add_argument("--batch-fields", type=int, default=8, help="fields of the batched workload")
-    ap.add_argument("--batch-lanes", type=int, default=4, help="concurrent lanes of the batched workload")
+    ap.add_argument("--batch-fields", type=int, default=64, help="fields of the batched workload")
+    ap.add_argument("--batch-lanes", type=int, default=8, help="concurrent lanes of the batched workload")
+    ap.add_argument("--batch-target", type=float, default=3e-3,
+                    help="accuracy target (rel-L2 against the direct sum) of the batch's autotuner")
     ap.add_argument("--cpu-n", type=int, default=64, help="grid of the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
@@ -433,14 +435,15 @@ def configs_bench(args, dev, stream, flush):
 
 
 def batch_bench(args, dev, stream, flush):
-    """The batched workload: args.batch_fields uneven two-channel streamer fields (uniform
-    grids of 80^3-158^3 cells, 760 or 76 Torr, m0 = 6, leaf 64, mixed form) evaluated as one
-    CUDA-graph batch, back to back on one stream and on concurrent lanes; CUDA events on the
-    launching stream, L2 flushed between steps, the lanes' results checked against the
-    sequential ones. Plans take the root cube aligned with each field's cell lattice
-    (origin at the grid's corner, side 4 h 2^k >= n h), so that the leaves inside the grid
-    are blocks of 4^3 cells (with the points' bounding cube as root, most of these grids
-    split into leaves of 14-30 cells); the default root is timed beside it."""
+    """The batched workload: args.batch_fields streamer fields of uneven sizes (uniform grids
+    of 80^3-158^3 cells, 0.5-4 M points, two channels each, 760 or 76 Torr, seed-drawn),
+    evaluated as one CUDA-graph batch, back to back on one stream and on concurrent lanes;
+    CUDA events on the launching stream, L2 flushed between steps, the lanes' results checked
+    against the sequential ones. Leaf size and surface order come from the accuracy-targeted
+    autotuner (kifmm_tune, target args.batch_target against the direct sum), run once per
+    pressure on the first field of that pressure, mixed form. Plans take the root cube
+    aligned with each field's cell lattice (origin at the grid's corner, side 4 h 2^k >= n h),
+    so that grids whose size is a multiple of 8 run the lattice paths."""
     import math
     import torch
     from paper_2006_03515_gb300 import kifmm
@@ -454,16 +457,33 @@ def batch_bench(args, dev, stream, flush):
     Is = [f[2] for f in fields]
     Cs = [kifmm.scale_c(f[3]) for f in fields]
     npts = sum(int(x.shape[0]) for x in Is)
-    steps = max(3, min(args.steps, 10))
+    steps = max(3, min(args.steps, 5))
+    out = {"fields": len(fields), "points": npts, "sizes": [f[4] for f in fields],
+           "pressures_torr": [f[3] for f in fields], "capture": True, "target": args.batch_target}
+    # autotuner, once per pressure
+    t0 = time.perf_counter()
+    tuned = {}
+    for f in fields:
+        if f[3] in tuned:
+            continue
+        a, b = kifmm.absorption(0.2 * f[3])
+        best, tab = kifmm.tune(f[0], f[1], f[2], a, b, leaf=(32, 64), order=(4, 6, 8), target=args.batch_target,
+                               reps=2, root=(0.0, 0.0, 0.0, f[5]), stream=stream)
+        tuned[f[3]] = best
+        out.setdefault("tuned", {})["%g Torr" % f[3]] = {"field_points": int(f[0].shape[0]), "best": best,
+                                                         "candidates": tab}
+    out["tune_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    plans = []
+    for f in fields:
+        bt = tuned[f[3]]
+        plans.append(kifmm.Plan(f[0], f[1], bt["leaf"], bt["order"], *kifmm.absorption(0.2 * f[3]),
+                                precision="mixed", stream=stream, root=(0.0, 0.0, 0.0, f[5])))
+    torch.cuda.synchronize(dev)
+    out["plan_s"] = time.perf_counter() - t0
+    out["lattice_fields"] = sum(1 for pl in plans if pl.info()["near_tensor"])
 
-    def plans_for(aligned):
-        t0 = time.perf_counter()
-        pl = [kifmm.Plan(f[0], f[1], 64, 6, *kifmm.absorption(0.2 * f[3]), precision="mixed", stream=stream,
-                         root=(0.0, 0.0, 0.0, f[5]) if aligned else None) for f in fields]
-        torch.cuda.synchronize(dev)
-        return pl, time.perf_counter() - t0
-
-    def timed(plans, lanes):
+    def timed(lanes):
         Ss = [torch.empty_like(x) for x in Is]
         for _ in range(3):
             kifmm.eval_batch(plans, Is, Ss, C=Cs, capture=True, lanes=lanes)
@@ -476,26 +496,20 @@ def batch_bench(args, dev, stream, flush):
             e1.record(stream)
             e1.synchronize()
             ms.append(e0.elapsed_time(e1))
+        for pl in plans:
+            pl.check()
         t = statistics.median(ms)
         return {"ms": t, "points_per_s": npts / (1e-3 * t)}, Ss
 
-    out = {"fields": len(fields), "points": npts, "sizes": [f[4] for f in fields],
-           "pressures_torr": [f[3] for f in fields], "capture": True}
-    plans, out["plan_s"] = plans_for(True)
-    out["lattice_fields"] = sum(1 for pl in plans if pl.info()["near_tensor"])
-    out["lanes1"], s1 = timed(plans, 1)
+    out["lanes1"], s1 = timed(1)
     key = "lanes%d" % args.batch_lanes
-    out[key], sl = timed(plans, args.batch_lanes)
+    out[key], sl = timed(args.batch_lanes)
     out["lanes_match_sequential"] = bool(all(
         float(torch.linalg.norm(x - y) / torch.linalg.norm(y)) <= 1e-12 for x, y in zip(sl, s1)))
     out["speedup_lanes"] = out["lanes1"]["ms"] / out[key]["ms"]
     for pl in plans:
         pl.close()
-    del s1, sl
-    plans, _ = plans_for(False)
-    out["default_root_" + key], _ = timed(plans, args.batch_lanes)
-    for pl in plans:
-        pl.close()
+    del s1, sl, plans
     torch.cuda.empty_cache()
     return out
 

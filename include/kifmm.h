@@ -102,7 +102,19 @@ typedef struct {
      * 3 g(rho) / (pi sum h^2) per unit volume with rho = sqrt(sum h^2 / 12)), and the root
      * rule takes each axis' own half extent. {0, 0, 0} (default): cubic cells. */
     double cell_dims[3];
+    /* Kernel of the sum (kernel independence: the same FMM for any of them), with
+     * p_O2 = a / chi_min (a, b as in kifmm_plan): KIFMM_KERNEL_ZHELEZNYAK (default), the
+     * paper's K; KIFMM_KERNEL_HELMHOLTZ3, the three-exponential approximation of Sec. 2.2
+     * (Eq. (gexp), Table Helcoeff), sum_j C_j p_O2^2 exp(-lambda_j p_O2 R) / (4 pi R), the
+     * free-space solution of the modified Helmholtz equations (Hel); KIFMM_KERNEL_THREEGROUP,
+     * the three-group model of Sec. 2.3 (Eq. (rtetoint), Table threegroupcoeff),
+     * sum_j A_j p_O2 exp(-lambda_j p_O2 R) / (4 pi R^2). The self term follows the kernel
+     * (exact cell integral, or hx hy hz K(sqrt(sum h^2 / 12)) for the paper's rule). The
+     * comparison kernels run in the FP64 form (KIFMM_ERR_ARG with KIFMM_MIXED). */
+    int kernel;
 } kifmm_opts;
+
+typedef enum { KIFMM_KERNEL_ZHELEZNYAK = 0, KIFMM_KERNEL_HELMHOLTZ3 = 1, KIFMM_KERNEL_THREEGROUP = 2 } kifmm_kernel;
 
 /* Fills *opts with the defaults above (FP64, cell-exact self term, eps 1e-5,
  * automatic root, default stream, surface representation, radii {1.05, 2.95}, cubic
@@ -217,6 +229,34 @@ int kifmm_check(kifmm_plan_t plan);
  */
 int kifmm_model_constants(double p_torr, double p_o2_torr, double p_q_torr, double xi_omega_alpha, double* a,
                           double* b, double* C);
+
+/*
+ * Accuracy-targeted autotuner: the fastest (leaf size, surface order, surface radii) whose
+ * estimated error meets a target. For every candidate of leaf[0..nleaf) x order[0..norder) x
+ * radii pairs radii[2j], radii[2j+1] (j < nradii; nradii = 0: opts' radii), it builds a plan
+ * with opts (precision, root, cells, stream ...), evaluates the representative source I_dev
+ * (device, N FP64, caller order; C = 1), estimates the relative L2 error against the FP64
+ * direct sum of the discrete integral (Sec. 3, Eq. (summation)) at k_samples (1..4096)
+ * targets drawn in proportion to the first candidate's field (probability 0.5 |S_i| / sum |S|
+ * + 0.5 / N, importance weights), and times reps evaluations (CUDA events on the plan's
+ * stream). A candidate is accepted when its estimate is at most target / 2 (the factor
+ * covers the estimate's sampling error); *best receives the fastest accepted candidate, or
+ * the most accurate one with ok = 0 when none is accepted. entries (may be NULL) receives
+ * every candidate, leaf-major then order then radii. Allocates and frees its own work space.
+ * Statuses as kifmm_plan, and KIFMM_ERR_ARG for empty candidate lists or target <= 0.
+ */
+typedef struct {
+    int leaf;           /* leaf size m */
+    int order;          /* surface order m0 (Chebyshev order p) */
+    double radii[2];    /* surface radii */
+    float ms;           /* mean evaluation time */
+    double err;         /* estimated relative L2 error against the discrete sum */
+    int ok;             /* err <= target / 2 */
+} kifmm_tune_entry;
+int kifmm_tune(const double* points_dev, int64_t n, const double* cell_h_dev, double uniform_h, const double* I_dev,
+               double a, double b, const kifmm_opts* opts, const int* leaf, int nleaf, const int* order, int norder,
+               const double* radii, int nradii, double target, int k_samples, int reps, kifmm_tune_entry* entries,
+               kifmm_tune_entry* best);
 
 /* Frees every device buffer of the plan (synchronising its stream). NULL is a no-op. */
 void kifmm_destroy(kifmm_plan_t plan);

@@ -47,16 +47,18 @@ def c_threads():
     return int(_load_c().oracle_threads())
 
 
-def self_terms(h, a, b, mode):
-    """sigma(h_i) for every point (computed once per distinct h)."""
+def self_terms(h, a, b, mode, kind="zheleznyak"):
+    """sigma(h_i) for every point (computed once per distinct h); ``kind`` selects one of the
+    comparison kernels (``kernel.KERNELS``)."""
     h = np.asarray(h, dtype=np.float64)
     out = np.empty_like(h)
     for hv in np.unique(h):
-        out[h == hv] = _k.self_sigma(float(hv), a, b, mode)
+        out[h == hv] = (_k.self_sigma(float(hv), a, b, mode) if kind == "zheleznyak"
+                        else _k.sigma_cell_any(float(hv), float(hv), float(hv), a, b, kind, mode))
     return out
 
 
-def pair_sum_numpy(targets, t_idx, sources, s_idx, q, a, b):
+def pair_sum_numpy(targets, t_idx, sources, s_idx, q, a, b, kind="zheleznyak"):
     """sum_{j != i} K(|x_i - y_j|) q_j for the given targets, numpy, chunked."""
     out = np.zeros(targets.shape[0], dtype=np.float64)
     chunk = max(1, 4_000_000 // max(1, sources.shape[0]))
@@ -65,7 +67,7 @@ def pair_sum_numpy(targets, t_idx, sources, s_idx, q, a, b):
         d = np.sqrt(((x[:, None, :] - sources[None, :, :]) ** 2).sum(-1))
         same = t_idx[s:s + chunk, None] == s_idx[None, :]
         d[same] = 1.0
-        kk = _k.kernel(d, a, b)
+        kk = _k.kernel_any(d, a, b, kind)
         kk[same] = 0.0
         out[s:s + chunk] = kk @ q
     return out
@@ -86,17 +88,20 @@ def pair_sum_c(targets, t_idx, sources, s_idx, q, a, b):
     return out
 
 
-def direct_sum(points, h, I, a, b, C=1.0, mode="cell_exact", targets=None, impl="c"):
-    """S at ``targets`` (indices into points; all points when None)."""
+def direct_sum(points, h, I, a, b, C=1.0, mode="cell_exact", targets=None, impl="c", kind="zheleznyak"):
+    """S at ``targets`` (indices into points; all points when None); the comparison kernels
+    (``kind``) take the numpy pair sum."""
     points = np.asarray(points, dtype=np.float64)
     h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
     I = np.asarray(I, dtype=np.float64)
     q = I * h ** 3
     tix = np.arange(points.shape[0]) if targets is None else np.asarray(targets, dtype=np.int64)
     sidx = np.arange(points.shape[0], dtype=np.int64)
-    f = pair_sum_c if impl == "c" else pair_sum_numpy
-    far = f(points[tix], tix, points, sidx, q, a, b)
-    sig = self_terms(h[tix], a, b, mode)
+    if kind == "zheleznyak" and impl == "c":
+        far = pair_sum_c(points[tix], tix, points, sidx, q, a, b)
+    else:
+        far = pair_sum_numpy(points[tix], tix, points, sidx, q, a, b, kind)
+    sig = self_terms(h[tix], a, b, mode, kind)
     return C * (far + sig * I[tix])
 
 
@@ -117,7 +122,7 @@ def brute_force(points, h, I, a, b, C=1.0, mode="cell_exact"):
     return np.array(out)
 
 
-def fft_uniform(I3, hgrid, a, b, C=1.0, mode="cell_exact"):
+def fft_uniform(I3, hgrid, a, b, C=1.0, mode="cell_exact", kind="zheleznyak"):
     """Uniform grid (n0, n1, n2) of cubic cells of edge ``hgrid``: the same sum as a
     linear convolution with the kernel table K(h |d|) (zero at d = 0), zero-padded
     to twice the grid so that nothing wraps around."""
@@ -128,14 +133,15 @@ def fft_uniform(I3, hgrid, a, b, C=1.0, mode="cell_exact"):
     dz, dy, dx = np.meshgrid(*grids, indexing="ij")
     R = hgrid * np.sqrt(dx.astype(np.float64) ** 2 + dy ** 2 + dz ** 2)
     R[n[0] - 1, n[1] - 1, n[2] - 1] = 1.0
-    tab = _k.kernel(R, a, b)
+    tab = _k.kernel_any(R, a, b, kind)
     tab[n[0] - 1, n[1] - 1, n[2] - 1] = 0.0
     shape = [2 * m for m in n]
     ax = (0, 1, 2)
     F = np.fft.rfftn(q, shape, axes=ax) * np.fft.rfftn(tab, shape, axes=ax)
     conv = np.fft.irfftn(F, shape, axes=ax)
     far = conv[n[0] - 1:2 * n[0] - 1, n[1] - 1:2 * n[1] - 1, n[2] - 1:2 * n[2] - 1]
-    sig = _k.self_sigma(hgrid, a, b, mode)
+    sig = (_k.self_sigma(hgrid, a, b, mode) if kind == "zheleznyak"
+           else _k.sigma_cell_any(hgrid, hgrid, hgrid, a, b, kind, mode))
     return C * (far + sig * I3)
 
 

@@ -60,6 +60,74 @@ def kernel(R, a, b):
     return num / (4.0 * math.pi * R ** 3 * math.log(b / a))
 
 
+# ---- kernels of the comparison models, through the same sum (kernel independence) ----------
+# Sec. 2.2, Eq. (gexp), Table Helcoeff: g(r)/p_O2 ~ p_O2 r sum_j C_j exp(-lambda_j p_O2 r), so the
+# integrand g/(4 pi r^2) becomes sum_j C_j p_O2^2 exp(-lambda_j p_O2 r) / (4 pi r): the free-space
+# Green's functions of the three modified Helmholtz equations, Eq. (Hel).
+HELMHOLTZ3 = ((1.986e-4, 0.0553), (0.0051, 0.1460), (0.4886, 0.89))   # (C_j cm^-2 Torr^-2, lambda_j cm^-1 Torr^-1)
+# Sec. 2.3, Eq. (rtetoint), Table threegroupcoeff: g(r) ~ sum_j A_j p_O2 exp(-lambda_j p_O2 r), the
+# integrand sum_j A_j p_O2 exp(-lambda_j p_O2 r) / (4 pi r^2), Eq. (rteSph).
+THREEGROUP = ((0.0067, 0.0447), (0.0346, 0.1121), (0.3059, 0.5994))   # (A_j cm^-1 Torr^-1, lambda_j cm^-1 Torr^-1)
+KERNELS = ("zheleznyak", "helmholtz3", "threegroup")
+
+
+def kernel_terms(kind, p_o2):
+    """(alpha, w_j, kappa_j) with K(R) = sum_j w_j exp(-kappa_j R) / R^alpha for the comparison
+    kernels at oxygen pressure p_O2 (Torr)."""
+    if kind == "helmholtz3":
+        return 1, [c * p_o2 ** 2 / (4.0 * math.pi) for c, _ in HELMHOLTZ3], [lam * p_o2 for _, lam in HELMHOLTZ3]
+    if kind == "threegroup":
+        return 2, [A * p_o2 / (4.0 * math.pi) for A, _ in THREEGROUP], [lam * p_o2 for _, lam in THREEGROUP]
+    raise ValueError("unknown kernel %r" % (kind,))
+
+
+def kernel_any(R, a, b, kind="zheleznyak"):
+    """K(R) of the chosen model; (a, b) = (chi_min p_O2, chi_max p_O2) fix p_O2 = a / chi_min."""
+    if kind == "zheleznyak":
+        return kernel(R, a, b)
+    alpha, w, kap = kernel_terms(kind, a / CHI_MIN)
+    R = np.asarray(R, dtype=np.float64)
+    return sum(wj * np.exp(-kj * R) for wj, kj in zip(w, kap)) / R ** alpha
+
+
+def mass_within(rho, a, b, kind="zheleznyak"):
+    """int_0^rho K(r) r^2 dr (the flux through a sphere of radius rho, divided by 4 pi)."""
+    if kind == "zheleznyak":
+        return (math.log(b / a) + expint_e1(b * rho) - expint_e1(a * rho)) / (4.0 * math.pi * math.log(b / a))
+    alpha, w, kap = kernel_terms(kind, a / CHI_MIN)
+    s = 0.0
+    for wj, kj in zip(w, kap):
+        x = kj * rho
+        if alpha == 1:    # int_0^rho r e^{-k r} dr = (1 - (1 + x) e^{-x}) / k^2
+            s += wj * (-math.expm1(-x) - x * math.exp(-x)) / kj ** 2
+        else:             # int_0^rho e^{-k r} dr = (1 - e^{-x}) / k
+            s += wj * (-math.expm1(-x)) / kj
+    return s
+
+
+def sigma_cell_any(hx, hy, hz, a, b, kind="zheleznyak", mode="cell_exact", nodes=64):
+    """sigma of a cell hx x hy x hz for any of the kernels: cell_exact by the face-flux form
+    sum over the face pairs of 2 int (h_k/2) / R^3 m(R) du dv, m = ``mass_within`` (as
+    ``sigma_box_exact``); paper_gl2: hx hy hz K(rho), rho = sqrt(sum h^2 / 12) (the 2-point
+    Gauss-Legendre nodes), which for the paper's kernel is ``sigma_box_paper_gl2``."""
+    if mode == "paper_gl2":
+        rho = math.sqrt((hx * hx + hy * hy + hz * hz) / 12.0)
+        return hx * hy * hz * float(kernel_any(rho, a, b, kind))
+    t, wgl = np.polynomial.legendre.leggauss(nodes)
+    hs = (float(hx), float(hy), float(hz))
+    total = 0.0
+    for k in range(3):
+        hk = hs[k]
+        hi, hj = [hs[m] for m in range(3) if m != k]
+        u, wu = 0.5 * hi * t, 0.5 * hi * wgl
+        v, wv = 0.5 * hj * t, 0.5 * hj * wgl
+        for i in range(nodes):
+            for j in range(nodes):
+                R = math.sqrt(u[i] * u[i] + v[j] * v[j] + 0.25 * hk * hk)
+                total += 2.0 * wu[i] * wv[j] * (0.5 * hk) / R ** 3 * mass_within(R, a, b, kind)
+    return total
+
+
 def g_over_po2(r, p_o2):
     """g(r) / p_O2 of Eq. (gfun), as printed (used by the pins, not by the sums)."""
     x = p_o2 * r

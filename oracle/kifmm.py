@@ -39,7 +39,7 @@ import numpy as np
 
 from . import kernel as _k
 from . import tree as _t
-from .direct import pair_sum_c, self_terms
+from .direct import pair_sum_c, pair_sum_numpy, self_terms
 
 R_INNER = 1.05   # upward equivalent / downward check surface, in box half-widths
 R_OUTER = 2.95   # upward check / downward equivalent surface
@@ -59,10 +59,10 @@ def surface_lattice(m0):
     return np.array(pts, dtype=np.float64)
 
 
-def kmat(X, Y, a, b):
+def kmat(X, Y, a, b, kind="zheleznyak"):
     """Matrix of kernel values K(|X_i - Y_j|)."""
     d = np.sqrt(((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1))
-    return _k.kernel(d, a, b)
+    return _k.kernel_any(d, a, b, kind)
 
 
 def truncated_pinv(A, eps):
@@ -82,8 +82,9 @@ def _octant(o):
 class Operators:
     """Per-level matrices, all kernel values between surfaces (Eqs. (s2m)-(l2l))."""
 
-    def __init__(self, side, nlevels, m0, a, b, eps=1e-5, radii=(R_INNER, R_OUTER)):
+    def __init__(self, side, nlevels, m0, a, b, eps=1e-5, radii=(R_INNER, R_OUTER), kind="zheleznyak"):
         self.r_in, self.r_out = float(radii[0]), float(radii[1])
+        self.kind = kind
         r_in, r_out = self.r_in, self.r_out
         s = surface_lattice(m0)
         self.surf = s
@@ -92,8 +93,8 @@ class Operators:
         for lev in range(2, nlevels):
             r = side / 2.0 ** (lev + 1)
             # Eq. (s2m): G(x^{B,u}, y^{B,u}); Eq. (s2l): G(x^{B,d}, y^{B,d})
-            self.uc2ue[lev] = truncated_pinv(kmat(r_out * r * s, r_in * r * s, a, b), eps)
-            self.dc2de[lev] = truncated_pinv(kmat(r_in * r * s, r_out * r * s, a, b), eps)
+            self.uc2ue[lev] = truncated_pinv(kmat(r_out * r * s, r_in * r * s, a, b, kind), eps)
+            self.dc2de[lev] = truncated_pinv(kmat(r_in * r * s, r_out * r * s, a, b, kind), eps)
             # Eq. (m2l): G(x^{B,d}, y^{A,u}) for c_A - c_B = 2 r delta
             for dz in range(-3, 4):
                 for dy in range(-3, 4):
@@ -102,19 +103,19 @@ class Operators:
                             continue
                         off = 2.0 * r * np.array([dx, dy, dz], dtype=np.float64)
                         self.m2l[(lev, _offset_index((dx, dy, dz)))] = kmat(
-                            r_in * r * s, off + r_in * r * s, a, b)
+                            r_in * r * s, off + r_in * r * s, a, b, kind)
             if lev + 1 < nlevels:
                 rc = r / 2.0
                 for o in range(8):
                     cc = rc * (2.0 * _octant(o) - 1.0)   # child centre - parent centre
                     # Eq. (m2m): G(x^{P,u}, y^{C,u})
-                    self.m2m[(lev, o)] = kmat(r_out * r * s, cc + r_in * rc * s, a, b)
+                    self.m2m[(lev, o)] = kmat(r_out * r * s, cc + r_in * rc * s, a, b, kind)
                     # Eq. (l2l): G(x^{C,d}, y^{P,d})
-                    self.l2l[(lev, o)] = kmat(cc + r_in * rc * s, r_out * r * s, a, b)
+                    self.l2l[(lev, o)] = kmat(cc + r_in * rc * s, r_out * r * s, a, b, kind)
 
 
 def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii=(R_INNER, R_OUTER),
-         cell_dims=None):
+         cell_dims=None, kind="zheleznyak"):
     """cell_dims = (hx, hy, hz): every cell is that rectangular box (the Sec. 4.2 grid; h is
     then ignored): the root takes each axis' own half extent, the weights are hx hy hz (the
     cell volume, Sec. 3) and the self term is the box's own value."""
@@ -127,14 +128,15 @@ def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii
         h = np.broadcast_to(np.asarray(h, dtype=np.float64), (points.shape[0],)).copy()
         t, perm = _t.build_tree(points, h, leaf_size, origin, side)
     U, V, W, X = _t.build_lists(t)
-    ops = Operators(t.side, t.nlevels, m0, a, b, eps, radii)
+    ops = Operators(t.side, t.nlevels, m0, a, b, eps, radii, kind)
     return dict(tree=t, perm=perm, U=U, V=V, W=W, X=X, ops=ops, points=points[perm],
-                h=h[perm], a=a, b=b, m0=m0, cell_dims=cell_dims)
+                h=h[perm], a=a, b=b, m0=m0, cell_dims=cell_dims, kind=kind)
 
 
 def evaluate(p, I, C=1.0, mode="cell_exact"):
     """S in input order for source values I (input order)."""
     t, ops, a, b = p["tree"], p["ops"], p["a"], p["b"]
+    kind = p.get("kind", "zheleznyak")
     perm = p["perm"]
     pts, h = p["points"], p["h"]
     Is = np.asarray(I, dtype=np.float64)[perm]
@@ -153,7 +155,7 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
             if t.leaf[B]:
                 xc = centre[B] + ops.r_out * rad[B] * s
                 sl = slice(t.pstart[B], t.pend[B])
-                chk = kmat(xc, pts[sl], a, b) @ q[sl]
+                chk = kmat(xc, pts[sl], a, b, kind) @ q[sl]
             else:
                 chk = np.zeros(S)
                 for o in range(8):
@@ -182,7 +184,7 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
             xc = centre[B] + ops.r_in * rad[B] * s
             for A in p["X"][B]:                      # S2L from the sources of leaf A
                 sl = slice(t.pstart[A], t.pend[A])
-                chk[B - lo] += kmat(xc, pts[sl], a, b) @ q[sl]
+                chk[B - lo] += kmat(xc, pts[sl], a, b, kind) @ q[sl]
             P = int(t.parent[B])
             if t.level[P] >= 2:                      # L2L from the parent
                 o = int((t.anchor[B][0] & 1) | ((t.anchor[B][1] & 1) << 1) | ((t.anchor[B][2] & 1) << 2))
@@ -198,22 +200,25 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
         x = pts[sl]
         acc = np.zeros(x.shape[0])
         if t.level[B] >= 2:                          # local expansion
-            acc += kmat(x, centre[B] + ops.r_out * rad[B] * s, a, b) @ phi_d[B]
+            acc += kmat(x, centre[B] + ops.r_out * rad[B] * s, a, b, kind) @ phi_d[B]
         for A in p["W"][B]:                          # W list: upward densities
-            acc += kmat(x, centre[A] + ops.r_in * rad[A] * s, a, b) @ phi_u[A]
+            acc += kmat(x, centre[A] + ops.r_in * rad[A] * s, a, b, kind) @ phi_u[A]
         src = np.concatenate([np.arange(t.pstart[A], t.pend[A]) for A in p["U"][B]])
-        acc += pair_sum_c(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b)
+        if kind == "zheleznyak":
+            acc += pair_sum_c(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b)
+        else:
+            acc += pair_sum_numpy(x, np.arange(t.pstart[B], t.pend[B]), pts[src], src, q[src], a, b, kind)
         out[sl] = acc
     if dims is None:
-        out += self_terms(h, a, b, mode) * Is
+        out += self_terms(h, a, b, mode, kind) * Is
     else:
-        box = _k.sigma_box_exact if mode == "cell_exact" else _k.sigma_box_paper_gl2
-        out += box(dims[0], dims[1], dims[2], a, b) * Is
+        out += _k.sigma_cell_any(dims[0], dims[1], dims[2], a, b, kind, mode) * Is
     res = np.empty_like(out)
     res[perm] = C * out
     return res
 
 
 def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER),
-          cell_dims=None):
-    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii, cell_dims=cell_dims), I, C, mode)
+          cell_dims=None, kind="zheleznyak"):
+    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii, cell_dims=cell_dims, kind=kind), I, C,
+                    mode)

@@ -165,6 +165,14 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         set_error("kifmm_plan: unknown self_mode");
         return KIFMM_ERR_ARG;
     }
+    if (o.kernel < KIFMM_KERNEL_ZHELEZNYAK || o.kernel > KIFMM_KERNEL_THREEGROUP) {
+        set_error("kifmm_plan: unknown kernel");
+        return KIFMM_ERR_ARG;
+    }
+    if (o.kernel != KIFMM_KERNEL_ZHELEZNYAK && o.precision != KIFMM_FP64) {
+        set_error("kifmm_plan: the comparison kernels run in the FP64 form");
+        return KIFMM_ERR_ARG;
+    }
     if (!(o.pinv_eps > 0.0 && o.pinv_eps < 1.0)) {
         set_error("kifmm_plan: pinv_eps must lie in (0, 1)");
         return KIFMM_ERR_ARG;
@@ -189,6 +197,7 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     }
     p->precision = o.precision;
     p->self_mode = o.self_mode;
+    p->kind = o.kernel;
     p->pinv_eps = o.pinv_eps;
     p->r_in = o.radii[0];
     p->r_out = o.radii[1];

@@ -1425,7 +1425,7 @@ static EvalView make_view(Plan& p) {
     E.surf = ptr<double>(p.surf);
     E.side = p.tree.side;
     E.S = p.S;
-    E.kp = make_kparams(p.a, p.b);
+    E.kp = make_kparams_kind(p.kind, p.a, p.b);
     E.cheb = p.cheb ? 1 : 0;
     E.rf_dchk = p.cheb ? 1.0 : p.r_in;
     E.rf_ueq = p.cheb ? 1.0 : p.r_in;

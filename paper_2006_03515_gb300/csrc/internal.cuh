@@ -199,6 +199,7 @@ struct Plan {
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
     double uniform_h = 0;        // cell edge of a uniform-h plan (0: per-point h, or rectangular cells)
+    int kind = 0;                // kernel: 0 the paper's, 1 three-exponential Helmholtz, 2 three-group
     bool rect = false;           // every cell is the rectangular box cell_dims (hx, hy, hz)
     double cell_dims[3] = {0, 0, 0};
     // near field on the tensor cores (mixed form, uniform lattice; near_tc.cu)
@@ -289,6 +290,11 @@ int pinv_oz_prepare(cudaStream_t st, const double* G1, int S, int rank, void* im
 int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxes, const int32_t* in_rows, int n,
                   const void* opimg, const int* er, int rank, void* bimg, int* eb, double* cu, int R, int* err,
                   int64_t* launches);
+// tune.cu: targets drawn in proportion to a field (probability 0.5 |S_i| / sum |S| + 0.5 / n,
+// systematic sampling, weights 1 / (k m_i)); perm (sorted -> caller) gives sorted indices
+size_t importance_ws_bytes(int64_t n, int k);
+int importance_targets(cudaStream_t st, const double* S, int64_t n, int k, uint64_t seed, const int32_t* perm,
+                       void* ws, int32_t* tcaller, int32_t* tsorted, double* wt, int num_sms);
 // api.cu / eval.cu helpers for the surrogate
 Plan* kifmm_plan_internal(kifmm_plan_t h);
 int kifmm_scatter_weights(Plan& p, const double* I);

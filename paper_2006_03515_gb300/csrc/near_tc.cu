@@ -427,7 +427,7 @@ int near_tc_plan(Plan& p) {
     const int64_t RR = (int64_t)R * R;
     KF_TRY(dev_alloc(T, kOffsetSlots * RR * 8));
     KF_CUDA(cudaMemsetAsync(T.p, 0, kOffsetSlots * RR * 8, st));
-    k_nf_table<<<nbn(27 * RR, 256), 256, 0, st>>>(ptr<int32_t>(ref), nc, R, h, make_kparams(p.a, p.b), ptr<double>(T));
+    k_nf_table<<<nbn(27 * RR, 256), 256, 0, st>>>(ptr<int32_t>(ref), nc, R, h, make_kparams_kind(p.kind, p.a, p.b), ptr<double>(T));
     KF_LAUNCH();
     KF_TRY(dev_alloc(p.nf_Thi, (size_t)m2l_tc_table_elems(R) * 2));
     KF_TRY(dev_alloc(p.nf_Tlo, (size_t)m2l_tc_table_elems(R) * 2));
@@ -456,14 +456,14 @@ int near_tc_plan(Plan& p) {
         KF_TRY(dev_alloc(p.lat_P, (size_t)p.S * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_P.p, 0, (size_t)p.S * (npl + 1) * 4, st));
         k_lat_table<<<nbn((int64_t)p.S * npl, 256), 256, 0, st>>>(ptr<double>(p.surf), p.S, ptr<int32_t>(ref), nc, r,
-                                                                   p.r_out, h, make_kparams(p.a, p.b),
+                                                                   p.r_out, h, make_kparams_kind(p.kind, p.a, p.b),
                                                                    ptr<float>(p.lat_P));
         KF_LAUNCH();
         KF_TRY(dev_alloc(p.lat_Q, (size_t)p.R * (npl + 1) * 4));
         KF_CUDA(cudaMemsetAsync(p.lat_Q.p, 0, (size_t)p.R * (npl + 1) * 4, st));
         k_lat_Q<<<nbn((int64_t)p.R * npl, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R, ptr<double>(p.surf),
                                                                ptr<int32_t>(ref), nc, r, p.r_out, h,
-                                                               make_kparams(p.a, p.b),
+                                                               make_kparams_kind(p.kind, p.a, p.b),
                                                                ptr<float>(p.lat_Q));
         KF_LAUNCH();
         for (const void* fn : {(const void*)k_lat_s2m, (const void*)k_lat_l2p})
@@ -478,7 +478,7 @@ int near_tc_plan(Plan& p) {
             k_lat_QT<<<nbn((int64_t)npl * p.R, 128), 128, 0, st>>>(ptr<double>(p.ops[lf].Ub), p.S, p.R,
                                                                     ptr<double>(p.surf), ptr<int32_t>(ref), nc, r,
                                                                     p.r_out, h,
-                                                                    make_kparams(p.a, p.b), ptr<double>(QT));
+                                                                    make_kparams_kind(p.kind, p.a, p.b), ptr<double>(QT));
             KF_LAUNCH();
             KF_TRY(dev_alloc(p.lat_Thi, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
             KF_TRY(dev_alloc(p.lat_Tlo, (size_t)m2l_tc_table_elems(p.R, 1) * 2));
@@ -567,7 +567,7 @@ int lat_up_plan(Plan& p) {
     KF_TRY(dev_alloc(M, (size_t)op.rank * npl * 8));
     k_lat_M<<<nbn((int64_t)op.rank * npl, 128), 128, 0, st>>>(ptr<double>(op.G1), p.S, op.rank, ptr<double>(p.surf),
                                                                ptr<int32_t>(p.nf_ref), nc, r, p.r_out, h,
-                                                               make_kparams(p.a, p.b),
+                                                               make_kparams_kind(p.kind, p.a, p.b),
                                                                ptr<double>(M));
     KF_LAUNCH();
     KF_TRY(dev_alloc(p.lat_Mimg, pinv_oz_op_bytes(npl, op.rank)));

@@ -290,7 +290,7 @@ static int build_operators_cheb(Plan& p) {
     cudaStream_t st = p.stream;
     const int S = p.S, pc = p.m0;
     const int L = p.tree.nlevels;
-    const KParams kp = make_kparams(p.a, p.b);
+    const KParams kp = make_kparams_kind(p.kind, p.a, p.b);
     KF_TRY(dev_alloc(p.surf, 3 * S * sizeof(double)));
     KF_TRY(dev_alloc(p.ctab, kChebMaxP * kChebTab * sizeof(double)));
     KF_TRY(dev_alloc(p.ctab32, kChebMaxP * kChebTab * sizeof(float)));
@@ -385,7 +385,7 @@ int build_operators(Plan& p) {
     cudaStream_t st = p.stream;
     const int S = p.S;
     const int L = p.tree.nlevels;
-    const KParams kp = make_kparams(p.a, p.b);
+    const KParams kp = make_kparams_kind(p.kind, p.a, p.b);
     KF_TRY(dev_alloc(p.surf, 3 * S * sizeof(double)));
     surface_lattice<<<1, 1, 0, st>>>(p.m0, ptr<double>(p.surf));
     KF_LAUNCH();
@@ -617,6 +617,17 @@ __global__ void self_sigma_box(double hx, double hy, double hz, double a, double
     const double s = self_sigma_box_block(hx, hy, hz, a, b, mode, nq, gx, gw, red);
     if (threadIdx.x == 0) out[0] = s;
 }
+// the comparison kernels: sigma of cubes of edge hs[k] (or of the rectangular cell dims when hs is
+// NULL), one block each
+__global__ void self_sigma_kind(const double* hs, int nh, double hx, double hy, double hz, KParams kp, int mode,
+                                int nq, const double* gx, const double* gw, double* out) {
+    const int k = blockIdx.x;
+    if (k >= nh) return;
+    __shared__ double red[256];
+    const double s = hs ? self_sigma_kind_block(hs[k], hs[k], hs[k], kp, mode, nq, gx, gw, red)
+                        : self_sigma_kind_block(hx, hy, hz, kp, mode, nq, gx, gw, red);
+    if (threadIdx.x == 0) out[k] = s;
+}
 
 int build_self_terms(Plan& p, const double* h_dev, double uh) {
     cudaStream_t st = p.stream;
@@ -635,7 +646,13 @@ int build_self_terms(Plan& p, const double* h_dev, double uh) {
         KF_TRY(dev_alloc(sb, 8));
         KF_CUDA(cudaMemcpyAsync(hb.p, &uh, 8, cudaMemcpyHostToDevice, st));
         double vol = uh * uh * uh;
-        if (p.rect) {
+        if (p.kind) {
+            const double hx = p.rect ? p.cell_dims[0] : uh, hy = p.rect ? p.cell_dims[1] : uh,
+                         hz = p.rect ? p.cell_dims[2] : uh;
+            self_sigma_kind<<<1, 256, 0, st>>>(nullptr, 1, hx, hy, hz, make_kparams_kind(p.kind, p.a, p.b),
+                                               p.self_mode, NQ, ptr<double>(gx), ptr<double>(gw), ptr<double>(sb));
+            vol = hx * hy * hz;
+        } else if (p.rect) {
             self_sigma_box<<<1, 256, 0, st>>>(p.cell_dims[0], p.cell_dims[1], p.cell_dims[2], p.a, p.b, p.self_mode,
                                               NQ, ptr<double>(gx), ptr<double>(gw), ptr<double>(sb));
             vol = p.cell_dims[0] * p.cell_dims[1] * p.cell_dims[2];
@@ -670,8 +687,12 @@ int build_self_terms(Plan& p, const double* h_dev, double uh) {
     uniq_gather<<<nb(n, 256), 256, 0, st>>>(ptr<uint64_t>(key), ptr<int32_t>(flag), ptr<int32_t>(pos), n,
                                             ptr<double>(hs));
     KF_LAUNCH();
-    self_sigma<<<nu, 256, 0, st>>>(ptr<double>(hs), nu, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
-                                   ptr<double>(gw), ptr<double>(su));
+    if (p.kind)
+        self_sigma_kind<<<nu, 256, 0, st>>>(ptr<double>(hs), nu, 0.0, 0.0, 0.0, make_kparams_kind(p.kind, p.a, p.b),
+                                            p.self_mode, NQ, ptr<double>(gx), ptr<double>(gw), ptr<double>(su));
+    else
+        self_sigma<<<nu, 256, 0, st>>>(ptr<double>(hs), nu, p.a, p.b, p.self_mode, NQ, ptr<double>(gx),
+                                       ptr<double>(gw), ptr<double>(su));
     KF_LAUNCH();
     scatter_sigma<<<nb(n, 256), 256, 0, st>>>(ptr<uint64_t>(key), ptr<int32_t>(val), ptr<int32_t>(flag),
                                               ptr<int32_t>(pos), n, ptr<double>(su), ptr<double>(p.sigma),

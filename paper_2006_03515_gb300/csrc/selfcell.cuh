@@ -1,5 +1,6 @@
 // Self-cell value sigma(h) of the discrete kernel G (i == j term, Sec. 3), device side.
 #pragma once
+#include "kernel.cuh"
 #include <cuda_runtime.h>
 
 #include "../../include/kifmm.h"
@@ -118,6 +119,31 @@ __device__ __forceinline__ double self_sigma_box_block(double hx, double hy, dou
         __syncthreads();
     }
     return red[0] / (4.0 * 3.14159265358979323846 * lba);
+}
+
+// sigma of an hx x hy x hz cell for any kernel kind (the same block reduction): cell_exact by
+// the face-flux form, sum over the face pairs of 2 int (h_k/2) / R^3 m(R) du dv with
+// m(R) = int_0^R K r^2 dr (kern_mass); paper_gl2: hx hy hz K(rho), rho = sqrt(sum h^2 / 12).
+__device__ __forceinline__ double self_sigma_kind_block(double hx, double hy, double hz, const KParams& kp, int mode,
+                                                        int nq, const double* gx, const double* gw, double* red) {
+    if (mode == KIFMM_SELF_PAPER_GL2) return hx * hy * hz * kern_f64(sqrt((hx * hx + hy * hy + hz * hz) / 12.0), kp);
+    const double hs[3] = {hx, hy, hz};
+    double acc = 0;
+    for (int e = threadIdx.x; e < 3 * nq * nq; e += blockDim.x) {
+        const int k = e / (nq * nq), i = (e / nq) % nq, j = e % nq;
+        const double hk = hs[k], hi = hs[(k + 1) % 3], hj = hs[(k + 2) % 3];
+        const double ui = 0.5 * hi * gx[i], uj = 0.5 * hj * gx[j];
+        const double wi = 0.5 * hi * gw[i], wj = 0.5 * hj * gw[j];
+        const double R = sqrt(ui * ui + uj * uj + 0.25 * hk * hk);
+        acc += 2.0 * wi * wj * (0.5 * hk) / (R * R * R) * kern_mass(R, kp, [](double x) { return e1_dev(x); });
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    return red[0];
 }
 
 }  // namespace kifmm

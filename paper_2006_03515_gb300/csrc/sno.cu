@@ -78,7 +78,7 @@ struct SnoModel {
     DevBuf near_d, near_w;           // int2 (di, dj) of every stencil column, its 2R + 1 float weights
     DevBuf scal;                     // photo_solve: amplitude scale (double)
     double* jwt = nullptr;           // photo_solve: the judge targets' weights (in jws)
-    DevBuf jws;                      // photo_solve: the judge's work space (judge_ws_bytes)
+    DevBuf jws;                      // photo_solve: the judge's work space (sized at creation)
 };
 
 // ---- layout ----------------------------------------------------------------------------
@@ -1326,105 +1326,44 @@ __global__ void k_scale_out(const float* y, const double* s, double C, double* S
     if (e < n) S[e] = C * s[0] * (double)y[e];
 }
 
-// ---- judge: targets drawn in proportion to the surrogate's field ------------------------------
-// sum |S_i| (non-negative doubles, one atomic per block)
-__global__ void k_abs_sum(const double* S, int64_t n, double* out) {
-    __shared__ double red[256];
-    double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc += fabs(S[i]);
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
+// ---- judge: direct sum at sampled targets (FP32, absolute coordinates) ------------------------
+// The judge's direct sum at the k drawn targets, with each source read once: a block takes a
+// chunk of JG_CH sources (FP32 coordinates, FP64 weights) into shared memory and adds its
+// part of every target's sum (one target per thread and pass) into acc[t] (FP64 atomics).
+constexpr int JG_T = 256, JG_CH = 2048;
+__global__ void __launch_bounds__(JG_T) k_judge_src(const double* pts, const double* q, const int32_t* targets,
+                                                    int k, int64_t n, KParams kp, double* acc) {
+    __shared__ float4 sp[JG_CH];   // x, y, z, unused
+    __shared__ double sq[JG_CH];
+    const int64_t j0 = (int64_t)blockIdx.x * JG_CH;
+    const int m = (int)min((int64_t)JG_CH, n - j0);
+    for (int e = threadIdx.x; e < m; e += JG_T) {
+        const int64_t j = j0 + e;
+        sp[e] = make_float4((float)pts[3 * j], (float)pts[3 * j + 1], (float)pts[3 * j + 2], 0.f);
+        sq[e] = q[j];
     }
-    if (threadIdx.x == 0) atomicAdd(out, red[0]);
-}
-// m_i = 0.5 |S_i| / sum|S| + 0.5 / n (a defensive mixture: every point keeps probability >= 0.5/n),
-// inclusive prefix sums in blocks of 1024: cdf[i] within its block, blk[b] the block's total
-constexpr int SC_T = 1024;
-__global__ void k_mix_scan(const double* S, int64_t n, const double* tot, double* cdf, double* blk) {
-    __shared__ double sh[SC_T];
-    const int64_t i = (int64_t)blockIdx.x * SC_T + threadIdx.x;
-    const double t = tot[0];
-    double v = 0.0;
-    if (i < n) v = (t > 0.0 ? 0.5 * fabs(S[i]) / t : 0.0) + (t > 0.0 ? 0.5 : 1.0) / (double)n;
-    sh[threadIdx.x] = v;
     __syncthreads();
-    for (int o = 1; o < SC_T; o <<= 1) {   // Hillis-Steele inclusive scan
-        const double x = threadIdx.x >= o ? sh[threadIdx.x - o] : 0.0;
-        __syncthreads();
-        sh[threadIdx.x] += x;
-        __syncthreads();
-    }
-    if (i < n) cdf[i] = sh[threadIdx.x];
-    if (threadIdx.x == SC_T - 1) blk[blockIdx.x] = sh[SC_T - 1];
-}
-// exclusive prefix of the block totals (one block, nb <= 4096 blocks: a serial loop per thread
-// chunk is enough), then the offsets added to every cdf entry
-__global__ void k_scan_blocks(double* blk, int nb) {
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const double v = blk[b];
-            blk[b] = acc;
-            acc += v;
+    for (int t = threadIdx.x; t < k; t += JG_T) {
+        const int64_t i = targets[t];
+        const float xi = (float)pts[3 * i], yi = (float)pts[3 * i + 1], zi = (float)pts[3 * i + 2];
+        const int self = (i >= j0 && i < j0 + m) ? (int)(i - j0) : -1;
+        double a = 0.0;
+        for (int e = 0; e < m; ++e) {
+            if (e == self) continue;
+            const float4 v = sp[e];
+            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
+            a += (double)kern_f32(dx * dx + dy * dy + dz * dz, kp) * sq[e];
         }
+        atomicAdd(acc + t, a);
     }
 }
-__global__ void k_add_offsets(double* cdf, int64_t n, const double* blk) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) cdf[i] += blk[i / SC_T];
-}
-// systematic draw: u_t = (t + U) / k * cdf[n-1]; target = first i with cdf[i] > u_t (caller order),
-// its sorted index through the inverse permutation, and its weight 1 / (k m_i)
-__global__ void k_draw(const double* cdf, int64_t n, int k, double U, const int32_t* inv, int32_t* tsorted,
-                       double* wt) {
+__global__ void k_judge_fin(const double* acc, const int32_t* targets, int k, const double* sigma, const double* Isort,
+                            double C, const int32_t* perm, double* ref, int32_t* orig) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= k) return;
-    const double total = cdf[n - 1];
-    const double u = ((double)t + U) / (double)k * total;
-    int64_t lo = 0, hi = n - 1;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) / 2;
-        if (cdf[mid] > u) hi = mid;
-        else lo = mid + 1;
-    }
-    const double mi = (cdf[lo] - (lo > 0 ? cdf[lo - 1] : 0.0)) / total;
-    tsorted[t] = inv[lo];
-    wt[t] = 1.0 / ((double)k * mi);
-}
-__global__ void k_inv_perm(const int32_t* perm, int64_t n, int32_t* inv) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) inv[perm[k]] = (int32_t)k;
-}
-
-// ---- judge: direct sum at sampled targets (FP32, absolute coordinates) ------------------------
-__global__ void k_judge(const double* pts, const double* q, const int32_t* targets, int k, int64_t n, KParams kp,
-                        const double* sigma, const double* Isort, double C, const int32_t* perm, double* ref,
-                        int32_t* orig) {
-    const int t = blockIdx.x;
-    if (t >= k) return;
     const int64_t i = targets[t];
-    const float xi = (float)pts[3 * i], yi = (float)pts[3 * i + 1], zi = (float)pts[3 * i + 2];
-    __shared__ double red[256];
-    double acc = 0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        if (j == i) continue;
-        const float dx = xi - (float)pts[3 * j], dy = yi - (float)pts[3 * j + 1], dz = zi - (float)pts[3 * j + 2];
-        acc += (double)kern_f32(dx * dx + dy * dy + dz * dz, kp) * q[j];
-    }
-    red[threadIdx.x] = acc;
-    __syncthreads();
-    for (int o = 128; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        ref[t] = C * (red[0] + sigma[i] * Isort[i]);
-        orig[t] = perm[i];
-    }
+    ref[t] = C * (acc[t] + sigma[i] * Isort[i]);
+    orig[t] = perm[i];
 }
 
 // importance-weighted estimate of the relative L2 error: targets drawn with probability
@@ -1581,11 +1520,8 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
     if ((rc = dev_alloc(M.jorig, SNO_MAX_JUDGE * 4))) return fail(rc);
     if ((rc = dev_alloc(M.jerr, 8))) return fail(rc);
     if ((rc = dev_alloc(M.scal, 16))) return fail(rc);
-    {   // judge work space: cdf (8 n), block totals (8 (n / 1024 + 1)), total (16), inverse permutation
-        // (4 n, rounded to an even count), weights (8 k)
-        const int64_t n3 = M.np3;
-        const size_t ws = 8 * (size_t)n3 + 8 * (size_t)(n3 / SC_T + 2) + 16 + 4 * (size_t)((n3 + 1) & ~(int64_t)1) +
-                          8 * (size_t)SNO_MAX_JUDGE + 64;
+    {   // judge work space: the target draw's, then the weights and the targets' sums (8 k each)
+        const size_t ws = importance_ws_bytes(M.np3, SNO_MAX_JUDGE) + 2 * 8 * (size_t)SNO_MAX_JUDGE;
         if ((rc = dev_alloc(M.jws, ws))) return fail(rc);
     }
     if (cudaStreamSynchronize(M.st) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
@@ -1969,36 +1905,23 @@ int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, doubl
     k_scale_out<<<nbs(n, 256), 256, 0, st>>>(y, ptr<double>(M.scal), C, S_dev, n);
     KF_LAUNCH();
     // judge: the direct sum at k targets drawn with probability m_i = 0.5 |S_i| / sum |S| + 0.5 / n
-    // (systematic sampling from the surrogate's own field, offset U from a fixed LCG), each
-    // weighted 1 / (k m_i): an importance-sampled estimate of the whole field's relative L2
-    // error that does not miss a concentrated source the way uniform samples do
-    uint64_t sst = seed * 6364136223846793005ull + 1442695040888963407ull;
-    sst = sst * 6364136223846793005ull + 1442695040888963407ull;
-    const double U = (double)(sst >> 11) * (1.0 / 9007199254740992.0);
+    // (systematic sampling from the surrogate's own field, offset from a fixed LCG of `seed`),
+    // each weighted 1 / (k m_i): an importance-sampled estimate of the whole field's relative
+    // L2 error that does not miss a concentrated source the way uniform samples do
     DevBuf &dt = M.jt, &dref = M.jref, &dorig = M.jorig, &derr = M.jerr;
-    {
-        // judge work space: cdf, block totals, total, inverse permutation, weights
-        double* cdf = ptr<double>(M.jws);
-        const int64_t nbk = (n + SC_T - 1) / SC_T;
-        double* blk = cdf + n;
-        double* tot = blk + nbk + 1;
-        int32_t* inv = reinterpret_cast<int32_t*>(tot + 2);
-        double* wt = reinterpret_cast<double*>(inv + ((n + 1) & ~(int64_t)1));
-        KF_CUDA(cudaMemsetAsync(tot, 0, 8, st));
-        k_abs_sum<<<std::min<int64_t>(nbs(n, 256), 4LL * M.num_sms), 256, 0, st>>>(S_dev, n, tot);
-        k_mix_scan<<<(unsigned)nbk, SC_T, 0, st>>>(S_dev, n, tot, cdf, blk);
-        k_scan_blocks<<<1, 32, 0, st>>>(blk, (int)nbk);
-        k_add_offsets<<<nbs(n, 256), 256, 0, st>>>(cdf, n, blk);
-        k_inv_perm<<<nbs(n, 256), 256, 0, st>>>(ptr<int32_t>(p.tree.perm), n, inv);
-        k_draw<<<nbs(k_samples, 128), 128, 0, st>>>(cdf, n, k_samples, U, inv, ptr<int32_t>(dt), wt);
-        KF_LAUNCH();
-        M.jwt = wt;
-    }
+    M.jwt = reinterpret_cast<double*>(static_cast<char*>(M.jws.p) + importance_ws_bytes(n, SNO_MAX_JUDGE));
+    KF_TRY(importance_targets(st, S_dev, n, k_samples, seed, ptr<int32_t>(p.tree.perm), M.jws.p, nullptr,
+                              ptr<int32_t>(dt), M.jwt, M.num_sms));
     // weights q = I h^3 in sorted order (the evaluation's own scatter kernel path)
     KF_TRY(kifmm_scatter_weights(p, I_dev));
-    k_judge<<<k_samples, 256, 0, st>>>(ptr<double>(p.pts), ptr<double>(p.q), ptr<int32_t>(dt), k_samples, n,
-                                       make_kparams(p.a, p.b), ptr<double>(p.sigma), ptr<double>(p.Isort), C,
-                                       ptr<int32_t>(p.tree.perm), ptr<double>(dref), ptr<int32_t>(dorig));
+    double* jacc = M.jwt + SNO_MAX_JUDGE;   // per-target sums (after the weights in the work space)
+    KF_CUDA(cudaMemsetAsync(jacc, 0, (size_t)k_samples * 8, st));
+    k_judge_src<<<nbs(n, JG_CH), JG_T, 0, st>>>(ptr<double>(p.pts), ptr<double>(p.q), ptr<int32_t>(dt), k_samples,
+                                                  n, make_kparams(p.a, p.b), jacc);
+    KF_LAUNCH();
+    k_judge_fin<<<nbs(k_samples, 128), 128, 0, st>>>(jacc, ptr<int32_t>(dt), k_samples, ptr<double>(p.sigma),
+                                                     ptr<double>(p.Isort), C, ptr<int32_t>(p.tree.perm),
+                                                     ptr<double>(dref), ptr<int32_t>(dorig));
     KF_LAUNCH();
     k_judge_err<<<1, 256, 0, st>>>(S_dev, ptr<double>(dref), ptr<int32_t>(dorig), M.jwt, k_samples,
                                    ptr<double>(derr));

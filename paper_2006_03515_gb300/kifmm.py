@@ -22,6 +22,7 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_OOM", -3: "ERR_CUDA", -4: "ERR_TIMEOU
 PRECISION = {"fp64": KIFMM_FP64, "mixed": KIFMM_MIXED}
 SELF_MODE = {"cell_exact": KIFMM_SELF_CELL_EXACT, "paper_gl2": KIFMM_SELF_PAPER_GL2}
 REPR = {"surface": 0, "cheb": 1}
+KERNEL = {"zheleznyak": 0, "helmholtz3": 1, "threegroup": 2}
 
 
 def model_constants(p, p_o2, p_q=30.0, xi_omega_alpha=0.06):
@@ -53,7 +54,8 @@ class KifmmError(RuntimeError):
 class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
-                ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2), ("cell_dims", ctypes.c_double * 3)]
+                ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2), ("cell_dims", ctypes.c_double * 3),
+                ("kernel", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -68,10 +70,15 @@ class _Info(ctypes.Structure):
                 ("l2l_tensor_levels", ctypes.c_int64), ("upward_tensor_levels", ctypes.c_int64)]
 
 
+class _TuneEntry(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int), ("order", ctypes.c_int), ("radii", ctypes.c_double * 2),
+                ("ms", ctypes.c_float), ("err", ctypes.c_double), ("ok", ctypes.c_int)]
+
+
 EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch",
            "kifmm_destroy", "kifmm_last_error", "kifmm_check", "kifmm_model_constants", "kifmm_get_info",
            "kifmm_get_tree", "kifmm_get_list",
-           "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune",
+           "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times", "kifmm_direct_noalloc", "kifmm_autotune", "kifmm_tune",
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
            "sno_set_bf16", "sno_set_period", "sno_set_near_field", "sno_init_far_field", "sno_forward",
@@ -114,10 +121,12 @@ def load():
     L.kifmm_get_phase_times.argtypes = [vp, vp, i32]
     L.kifmm_direct_noalloc.argtypes = [vp, i64, dbl, vp, vp, dbl, dbl, dbl, i32, vp]
     L.kifmm_autotune.argtypes = [vp, i64, vp, dbl, vp, i32, i32, dbl, dbl, ctypes.POINTER(_Opts), i32, vp, vp]
+    L.kifmm_tune.argtypes = [vp, i64, vp, dbl, vp, dbl, dbl, ctypes.POINTER(_Opts), vp, i32, vp, i32, vp, i32, dbl,
+                             i32, i32, ctypes.POINTER(_TuneEntry), ctypes.POINTER(_TuneEntry)]
     for name in ("kifmm_plan", "kifmm_eval", "kifmm_eval_host", "kifmm_eval_batch", "kifmm_check",
                  "kifmm_model_constants", "kifmm_get_info",
                  "kifmm_get_tree", "kifmm_get_list", "kifmm_get_sigma", "kifmm_get_upward", "kifmm_get_phase_times",
-                 "kifmm_direct_noalloc", "kifmm_autotune"):
+                 "kifmm_direct_noalloc", "kifmm_autotune", "kifmm_tune"):
         getattr(L, name).restype = ctypes.c_int
     _load_sno(L)
     _lib = L
@@ -141,7 +150,7 @@ class Plan:
 
     def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
                  self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface",
-                 surface_radii=None, cell_dims=None):
+                 surface_radii=None, cell_dims=None, kernel="zheleznyak"):
         import torch
         L = load()
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
@@ -165,6 +174,7 @@ class Plan:
         o.self_mode = SELF_MODE[self_mode]
         o.pinv_eps = float(pinv_eps)
         o.repr = REPR[repr]
+        o.kernel = KERNEL[kernel]
         if root is not None:
             o.has_root = 1
             for k in range(4):
@@ -302,6 +312,50 @@ def autotune(points, h, candidates=(32, 48, 64, 96, 128), surface_order=6, a=Non
     _check(L.kifmm_autotune(ctypes.c_void_p(pts.data_ptr()), int(pts.shape[0]), hp, uh, cand, len(candidates),
                             int(surface_order), float(a), float(b), ctypes.byref(o), int(reps), ctypes.byref(best), ms))
     return best.value, {int(c): float(t) for c, t in zip(candidates, ms)}
+
+
+def tune(points, h, I, a, b, leaf=(32, 64, 128), order=(4, 6, 8), radii=None, target=1e-3, precision="mixed",
+         k_samples=256, reps=3, root=None, stream=None):
+    """The fastest (leaf, order, radii) whose estimated error against the direct sum is at most
+    target / 2 (kifmm_tune). I: representative source, CUDA float64 (N,). radii: a list of
+    (inner, outer) pairs, or None for the default surfaces. Returns (best, table), dicts
+    with leaf, order, radii, ms, err, ok."""
+    import torch
+    L = load()
+    pts = points.detach().to(torch.float64).contiguous()
+    if not (isinstance(I, torch.Tensor) and I.is_cuda and I.dtype == torch.float64 and I.is_contiguous()
+            and I.numel() == pts.shape[0]):
+        raise TypeError("I must be a contiguous CUDA float64 tensor with N entries")
+    hp, uh = None, 0.0
+    if isinstance(h, torch.Tensor):
+        hh = h.detach().to(device=pts.device, dtype=torch.float64).contiguous()
+        hp = ctypes.c_void_p(hh.data_ptr())
+    else:
+        uh = float(h)
+    o = _Opts()
+    L.kifmm_default_opts(ctypes.byref(o))
+    o.precision = PRECISION[precision]
+    o.stream = _stream_ptr(stream)
+    if root is not None:
+        o.has_root = 1
+        for k in range(4):
+            o.root[k] = float(root[k])
+    lf = (ctypes.c_int * len(leaf))(*[int(x) for x in leaf])
+    od = (ctypes.c_int * len(order))(*[int(x) for x in order])
+    rl = [] if radii is None else [float(v) for pair in radii for v in pair]
+    rd = (ctypes.c_double * max(1, len(rl)))(*rl) if rl else None
+    nr = len(rl) // 2
+    ncand = len(leaf) * len(order) * max(1, nr)
+    tab = (_TuneEntry * ncand)()
+    best = _TuneEntry()
+    _check(L.kifmm_tune(ctypes.c_void_p(pts.data_ptr()), int(pts.shape[0]), hp, uh, ctypes.c_void_p(I.data_ptr()),
+                        float(a), float(b), ctypes.byref(o), lf, len(leaf), od, len(order), rd, nr, float(target),
+                        int(k_samples), int(reps), tab, ctypes.byref(best)))
+
+    def d(e):
+        return dict(leaf=e.leaf, order=e.order, radii=(e.radii[0], e.radii[1]), ms=float(e.ms), err=float(e.err),
+                    ok=bool(e.ok))
+    return d(best), [d(e) for e in tab]
 
 
 NOALLOC_MAX_POINTS = 65536

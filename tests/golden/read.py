@@ -18,5 +18,13 @@ def paper_fmm_errors():
     return {r[0]: (float(r[1]) / 100.0, float(r[2]) / 100.0) for r in _rows("paper_fmm_errors.txt")}
 
 
+def paper_kernel_coeffs():
+    """{model: [(coefficient, lambda), ...]} in the table's row order."""
+    out = {}
+    for r in _rows("paper_kernel_coeffs.txt"):
+        out.setdefault(r[0], []).append((float(r[2]), float(r[3])))
+    return out
+
+
 def paper_constants():
     return {r[0]: float(r[1]) for r in _rows("paper_constants.txt")}

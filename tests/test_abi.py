@@ -51,11 +51,14 @@ def test_struct_layouts_match_the_header(tmp_path):
     # kifmm_opts and kifmm_info as the C compiler lays them out against the ctypes mirrors
     opts = [f[0] for f in kifmm._Opts._fields_]
     info = [f[0] for f in kifmm._Info._fields_]
+    tune = [f[0] for f in kifmm._TuneEntry._fields_]
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "kifmm.h"', "int main(void) {"]
     src.append('printf("%zu\\n", sizeof(kifmm_opts));')
     src += ['printf("%%zu\\n", offsetof(kifmm_opts, %s));' % f for f in opts]
     src.append('printf("%zu\\n", sizeof(kifmm_info));')
     src += ['printf("%%zu\\n", offsetof(kifmm_info, %s));' % f for f in info]
+    src.append('printf("%zu\\n", sizeof(kifmm_tune_entry));')
+    src += ['printf("%%zu\\n", offsetof(kifmm_tune_entry, %s));' % f for f in tune]
     src.append("return 0; }")
     c = tmp_path / "layout.c"
     c.write_text("\n".join(src) + "\n")
@@ -64,6 +67,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(kifmm._Opts)] + [getattr(kifmm._Opts, f).offset for f in opts]
     want += [ctypes.sizeof(kifmm._Info)] + [getattr(kifmm._Info, f).offset for f in info]
+    want += [ctypes.sizeof(kifmm._TuneEntry)] + [getattr(kifmm._TuneEntry, f).offset for f in tune]
     assert got == want
 
 
@@ -149,6 +153,20 @@ def test_physics_constants(lib):
                 (760.0, 150.0, 30.0, float("inf"))]:
         assert lib.kifmm_model_constants(*bad, ctypes.byref(d), None, None) == ERR_ARG
         assert "kifmm_model_constants" in lib.kifmm_last_error().decode()
+
+
+def test_tune_rejects_bad_arguments(lib):
+    best = kifmm._TuneEntry()
+    leaf = (ctypes.c_int * 1)(64)
+    order = (ctypes.c_int * 1)(6)
+    vp = ctypes.c_void_p
+    for args in [(None, 10, None, 0.1, vp(8), 5.0, 300.0, None, leaf, 1, order, 1, None, 0, 1e-3, 64, 1),
+                 (vp(8), 10, None, 0.1, None, 5.0, 300.0, None, leaf, 1, order, 1, None, 0, 1e-3, 64, 1),
+                 (vp(8), 10, None, 0.1, vp(8), 5.0, 300.0, None, leaf, 0, order, 1, None, 0, 1e-3, 64, 1),
+                 (vp(8), 10, None, 0.1, vp(8), 5.0, 300.0, None, leaf, 1, order, 1, None, 0, 0.0, 64, 1),
+                 (vp(8), 10, None, 0.1, vp(8), 5.0, 300.0, None, leaf, 1, order, 1, None, 0, 1e-3, 5000, 1)]:
+        assert lib.kifmm_tune(*args, None, ctypes.byref(best)) == ERR_ARG
+        assert lib.kifmm_last_error().decode().startswith("kifmm_tune")
 
 
 def test_check_rejects_null(lib):

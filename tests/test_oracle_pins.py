@@ -498,3 +498,81 @@ def test_cheb_fmm_converges_to_the_direct_sum():
     err = [np.linalg.norm(cheb.fmm(pts, h, I, 8, p, a, b) - ref) / np.linalg.norm(ref) for p in (4, 6)]
     assert err[1] < 0.1 * err[0]
     assert err[1] <= 1e-5
+
+
+# ---- comparison kernels through the same sum (Sec. 2.2, 2.3) --------------------------------
+def test_comparison_kernel_coefficients_are_the_papers():
+    c = G.paper_kernel_coeffs()
+    assert tuple(c["helmholtz3"]) == K.HELMHOLTZ3 and tuple(c["threegroup"]) == K.THREEGROUP
+
+
+@pytest.mark.parametrize("kind", ["helmholtz3", "threegroup"])
+@pytest.mark.parametrize("p_o2", [150.0, 10.0])
+def test_comparison_kernel_mass_by_radial_quadrature(kind, p_o2):
+    # m(rho) = int_0^rho K r^2 dr against adaptive quadrature of the kernel itself, and the
+    # whole-space mass 4 pi m(inf) against the closed form sum 4 pi w_j / kappa_j^(3 - alpha)
+    a, b = K.absorption_coefficients(p_o2)
+    for rho in (0.01, 0.3, 2.0):
+        ref, _ = integrate.quad(lambda r: float(K.kernel_any(r, a, b, kind)) * r * r, 0.0, rho, limit=200,
+                                epsabs=0.0, epsrel=1e-13)
+        assert K.mass_within(rho, a, b, kind) == pytest.approx(ref, rel=1e-10)
+    alpha, w, kap = K.kernel_terms(kind, p_o2)
+    total = sum(4.0 * math.pi * wj / kj ** (3 - alpha) for wj, kj in zip(w, kap))
+    assert 4.0 * math.pi * K.mass_within(1e4 / p_o2, a, b, kind) == pytest.approx(total, rel=1e-12)
+
+
+def _sigma_any_duffy(hs, a, b, kind, n=64):
+    x, w = np.polynomial.legendre.leggauss(n)
+    t, wt = 0.5 * (x + 1), 0.5 * w
+    tot = 0.0
+    for k in range(3):
+        hk = hs[k]
+        hi, hj = [hs[m] for m in range(3) if m != k]
+        U, V = np.meshgrid(0.5 * hi * x, 0.5 * hj * x, indexing="ij")
+        WU = np.outer(0.5 * hi * w, 0.5 * hj * w)
+        Rf = np.sqrt(U * U + V * V + 0.25 * hk * hk)
+        for tk, wk in zip(t, wt):
+            tot += 2.0 * wk * np.sum(WU * K.kernel_any(tk * Rf, a, b, kind) * tk * tk * (0.5 * hk))
+    return tot
+
+
+@pytest.mark.parametrize("kind", ["zheleznyak", "helmholtz3", "threegroup"])
+@pytest.mark.parametrize("hs", [(1.0 / 64,) * 3, (0.001, 0.002, 0.004)])
+def test_comparison_kernel_self_integral_independent(kind, hs):
+    # the face-flux form against the volume route on the kernel itself; the paper's kernel
+    # reproduces sigma_box_exact
+    a, b = K.absorption_coefficients(150.0)
+    got = K.sigma_cell_any(*hs, a, b, kind)
+    assert got == pytest.approx(_sigma_any_duffy(hs, a, b, kind), rel=1e-9)
+    if kind == "zheleznyak":
+        assert got == pytest.approx(K.sigma_box_exact(*hs, a, b), rel=1e-13)
+
+
+@pytest.mark.parametrize("kind,bound", [("helmholtz3", 0.6), ("threegroup", 0.35)])
+def test_comparison_kernels_fit_the_papers_kernel(kind, bound):
+    # Sec. 2.2 / 2.3: fitted to g(r) over 1 < p_O2 r < 150 Torr cm (Helmholtz) and
+    # 0.1 < p_O2 r < 150 (three groups); relative deviation of the kernels there (up to 57 %
+    # and 30 %: the fits are coarse, which is why the paper measures E_V of 12-83 % for the
+    # models built on them); at p_O2 r = 1 the three-exponential sum is within 0.1 %
+    a, b = K.absorption_coefficients(150.0)
+    r = np.geomspace(1.0, 150.0, 400) / 150.0
+    dev = np.abs(K.kernel_any(r, a, b, kind) / K.kernel(r, a, b) - 1.0)
+    assert dev.max() < bound, dev.max()
+    # and the deviation is what makes these models differ from the paper's sum: not small
+    assert dev.max() > 0.02
+    if kind == "helmholtz3":
+        r1 = 1.0 / 150.0
+        assert float(K.kernel_any(r1, a, b, kind) / K.kernel(r1, a, b)) == pytest.approx(1.0, abs=1e-3)
+
+
+@pytest.mark.parametrize("kind", ["helmholtz3", "threegroup"])
+def test_kifmm_comparison_kernels(kind):
+    # the same FMM with the comparison kernels: one leaf is the direct sum; the FFT sum of the
+    # uniform grid is the direct sum; leaves of 8 points follow it to the method's magnitude
+    pts, h, I = W.config_uniform(10)
+    a, b = K.absorption_coefficients(150.0)
+    ref = D.direct_sum(pts, h, I, a, b, kind=kind)
+    np.testing.assert_allclose(D.fft_uniform(I.reshape(10, 10, 10), h[0], a, b, kind=kind).ravel(), ref, rtol=1e-11)
+    np.testing.assert_allclose(KF.kifmm(pts, h, I, len(pts), 6, a, b, kind=kind), ref, rtol=1e-12)
+    got = KF.kifmm(pts, h, I, 8, 6, a, b, kind=kind)
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
