@@ -441,10 +441,10 @@ def batch_bench(args, dev, stream, flush):
     CUDA events on the launching stream, L2 flushed between steps, the lanes' results checked
     against the sequential ones. Leaf size and surface order come from the accuracy-targeted
     autotuner (kifmm_tune, target args.batch_target against the direct sum), run once per
-    pressure on the first field of that pressure, mixed form. Plans take the root cube
-    aligned with each field's cell lattice (origin at the grid's corner, side 4 h 2^k >= n h),
-    so that grids whose size is a multiple of 8 run the lattice paths."""
-    import math
+    pressure on the first field of that pressure, mixed form. Plans pad each grid with
+    zero-weight cells to a multiple of 8 cells per axis under the root at the grid's corner
+    (kifmm_opts.pad_lattice), so that every field runs the lattice paths; the rate counts the
+    fields' own points only."""
     import torch
     from paper_2006_03515_gb300 import kifmm
     from paper_2006_03515_gb300 import workloads as W
@@ -452,8 +452,7 @@ def batch_bench(args, dev, stream, flush):
     for k in range(args.batch_fields):
         pts, h, I, p = W.two_channel_field(k)
         n = round(len(pts) ** (1 / 3))
-        side = float(h[0]) * 4 * 2 ** math.ceil(math.log2(n / 4))
-        fields.append((torch.as_tensor(pts, device=dev), float(h[0]), torch.as_tensor(I, device=dev), p, n, side))
+        fields.append((torch.as_tensor(pts, device=dev), float(h[0]), torch.as_tensor(I, device=dev), p, n))
     Is = [f[2] for f in fields]
     Cs = [kifmm.scale_c(f[3]) for f in fields]
     npts = sum(int(x.shape[0]) for x in Is)
@@ -467,8 +466,8 @@ def batch_bench(args, dev, stream, flush):
         if f[3] in tuned:
             continue
         a, b = kifmm.absorption(0.2 * f[3])
-        best, tab = kifmm.tune(f[0], f[1], f[2], a, b, leaf=(32, 64), order=(4, 6, 8), target=args.batch_target,
-                               reps=2, root=(0.0, 0.0, 0.0, f[5]), stream=stream)
+        best, tab = kifmm.tune(f[0], f[1], f[2], a, b, leaf=(64,), order=(4, 6, 8), target=args.batch_target,
+                               reps=2, stream=stream, pad_lattice=True)
         tuned[f[3]] = best
         out.setdefault("tuned", {})["%g Torr" % f[3]] = {"field_points": int(f[0].shape[0]), "best": best,
                                                          "candidates": tab}
@@ -478,10 +477,12 @@ def batch_bench(args, dev, stream, flush):
     for f in fields:
         bt = tuned[f[3]]
         plans.append(kifmm.Plan(f[0], f[1], bt["leaf"], bt["order"], *kifmm.absorption(0.2 * f[3]),
-                                precision="mixed", stream=stream, root=(0.0, 0.0, 0.0, f[5])))
+                                precision="mixed", stream=stream, pad_lattice=True))
     torch.cuda.synchronize(dev)
     out["plan_s"] = time.perf_counter() - t0
-    out["lattice_fields"] = sum(1 for pl in plans if pl.info()["near_tensor"])
+    infos = [pl.info() for pl in plans]
+    out["lattice_fields"] = sum(1 for inf in infos if inf["near_tensor"])
+    out["padding_cells"] = sum(inf["n_padding"] for inf in infos)
 
     def timed(lanes):
         Ss = [torch.empty_like(x) for x in Is]

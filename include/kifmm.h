@@ -112,6 +112,16 @@ typedef struct {
      * (exact cell integral, or hx hy hz K(sqrt(sum h^2 / 12)) for the paper's rule). The
      * comparison kernels run in the FP64 form (KIFMM_ERR_ARG with KIFMM_MIXED). */
     int kernel;
+    /* Nonzero: when the points are every cell centre of a box of n_x x n_y x n_z cubic cells
+     * (uniform_h, no cell_h or cell_dims, no root given) and leaf_size = nc^3 (nc >= 2), the
+     * plan appends zero-weight cells (I = 0) that extend the box to multiples of 2 nc cells
+     * per axis, and takes the root at the box's corner with side nc h 2^L. Every leaf is then
+     * a full nc^3 block of one level, so that the lattice paths (near field on the tensor
+     * cores, tabulated S2M / L2P) serve grids of any size. The padding adds nothing to the
+     * discrete sum (its weights are 0) and S is returned for the caller's points only; the
+     * FMM's approximation follows the padded tree. Other point sets are planned unpadded
+     * (kifmm_info.n_padding = 0). The surrogate's photo_solve refuses padded plans. */
+    int pad_lattice;
 } kifmm_opts;
 
 typedef enum { KIFMM_KERNEL_ZHELEZNYAK = 0, KIFMM_KERNEL_HELMHOLTZ3 = 1, KIFMM_KERNEL_THREEGROUP = 2 } kifmm_kernel;
@@ -267,7 +277,7 @@ const char* kifmm_last_error(void);
 /* ---- introspection (tests of the tree and lists; host copies) ---- */
 
 typedef struct {
-    int64_t n_points;
+    int64_t n_points;           /* points of the tree: the caller's, then n_padding padding cells */
     int64_t n_boxes;
     int32_t n_levels;
     int32_t surface_points;     /* S = m0^3 - (m0-2)^3 (Chebyshev representation: p^3) */
@@ -290,6 +300,8 @@ typedef struct {
     int64_t m2m_tensor_levels;  /* levels whose M2M translations run on the tensor cores (mixed form) */
     int64_t l2l_tensor_levels;  /* levels whose L2L translations run on the tensor cores (mixed form) */
     int64_t upward_tensor_levels; /* levels whose upward pseudo-inverse runs as exact slices on the tensor cores */
+    int64_t n_padding;          /* zero-weight padding cells (kifmm_opts.pad_lattice); perm values >= the caller's
+                                 * n (n_points - n_padding) are padding cells */
 } kifmm_info;
 
 /* Plan sizes and counters. Reads the device error word, so it synchronises the plan's stream. */
@@ -416,6 +428,18 @@ int sno_init_far_field(sno_model_t model, double shift);
  */
 int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, double* S_dev, double C, double tol,
                 int k_samples, uint64_t seed, int* used_fallback, double* judged_err);
+
+/*
+ * photo_solve for `count` fields at once (1 <= count <= the model's max_batch): field b
+ * has its own plan plans[b] (the model's grid; no padding), source I_dev[b], result
+ * S_dev[b] and scale C[b] (NULL: 1). One forward pass of the network over the batch on
+ * plans[0]'s stream, then the judge of each field (targets from seed + b), then one
+ * kifmm_eval_batch of the fields judged above tol. used_fallback[b] and judged_err[b]
+ * (either array may be NULL) as in photo_solve. Returns when every S_dev[b] is complete.
+ */
+int photo_solve_batch(kifmm_plan_t* plans, int count, sno_model_t model, const double* const* I_dev,
+                      double* const* S_dev, const double* C, double tol, int k_samples, uint64_t seed,
+                      int* used_fallback, double* judged_err);
 
 /* ---- evaluation without device allocation ---- */
 

@@ -219,6 +219,8 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
 
 
 def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER),
-          cell_dims=None, kind="zheleznyak"):
-    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, radii=radii, cell_dims=cell_dims, kind=kind), I, C,
-                    mode)
+          cell_dims=None, kind="zheleznyak", origin=None, side=None):
+    """The whole method: plan, then evaluate; origin / side give the root cube (else the
+    default rule of the tree)."""
+    return evaluate(plan(points, h, leaf_size, m0, a, b, eps, origin=origin, side=side, radii=radii,
+                         cell_dims=cell_dims, kind=kind), I, C, mode)

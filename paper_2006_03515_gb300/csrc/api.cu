@@ -212,6 +212,7 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     p->Sp = (p->S + 31) / 32 * 32;
     p->leaf_size = leaf_size;
     p->tree.n = n;
+    p->n_real = n;
     p->rect = rect && !(o.cell_dims[0] == o.cell_dims[1] && o.cell_dims[1] == o.cell_dims[2]);
     if (rect && !p->rect) uniform_h = o.cell_dims[0];   // equal sides: a cube
     for (int k = 0; k < 3; ++k) p->cell_dims[k] = p->rect ? o.cell_dims[k] : 0.0;
@@ -222,15 +223,43 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         g_last_error = msg;
         return rc;
     };
+    DevBuf padded;   // the caller's points and the padding cells (plan time only)
+    int nc = 1;
+    while ((nc + 1) * (nc + 1) * (nc + 1) <= leaf_size) ++nc;
+    if (o.pad_lattice && !cell_h && !rect && !o.has_root && nc >= 2 && nc * nc * nc == leaf_size) {
+        int64_t nt = n;
+        double root[4];
+        int prc = pad_to_lattice(p->stream, points, n, uniform_h, nc, padded, &nt, root);
+        if (prc) {
+            dev_free(padded);
+            return fail(prc);
+        }
+        if (nt > n) {
+            points = static_cast<const double*>(padded.p);
+            p->tree.n = n = nt;
+            o.has_root = 1;
+            for (int k = 0; k < 4; ++k) o.root[k] = root[k];
+        }
+    }
     int rc = build_tree(*p, points, cell_h, uniform_h, o);
-    if (rc) return fail(rc);
-    rc = dev_alloc(p->pts, n * 3 * sizeof(double));
-    if (rc) return fail(rc);
+    if (!rc) rc = dev_alloc(p->pts, n * 3 * sizeof(double));
+    if (rc) {
+        dev_free(padded);
+        return fail(rc);
+    }
     gather_sorted_points<<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(points, ptr<int32_t>(p->tree.perm), n,
                                                                            ptr<double>(p->pts));
     if (cudaGetLastError() != cudaSuccess) {
+        dev_free(padded);
         set_error("kifmm_plan: launch failed");
         return fail(KIFMM_ERR_CUDA);
+    }
+    if (padded.p) {   // the plan keeps its own sorted copy
+        if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
+            dev_free(padded);
+            return fail(KIFMM_ERR_CUDA);
+        }
+        dev_free(padded);
     }
     rc = build_lists(*p);
     if (rc) return fail(rc);
@@ -254,9 +283,9 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
     p->uniform_h = (cell_h || p->rect) ? 0.0 : uniform_h;
     rc = build_eval_data(*p);
     if (rc) return fail(rc);
-    rc = dev_alloc(p->host_I, n * 8);
+    rc = dev_alloc(p->host_I, p->n_real * 8);
     if (rc) return fail(rc);
-    rc = dev_alloc(p->host_S, n * 8);
+    rc = dev_alloc(p->host_S, p->n_real * 8);
     if (rc) return fail(rc);
     const char* tm = std::getenv("KIFMM_TIMING");
     if (tm && tm[0] == '1') {
@@ -296,7 +325,7 @@ int kifmm_eval_host(kifmm_plan_t h, const void* I_host, void* S_host, int dtype,
         return KIFMM_ERR_ARG;
     }
     Plan& p = *h->p;
-    size_t bytes = (size_t)p.tree.n * (dtype == KIFMM_F64 ? 8 : 4);
+    size_t bytes = (size_t)p.n_real * (dtype == KIFMM_F64 ? 8 : 4);
     KF_CUDA(cudaMemcpyAsync(p.host_I.p, I_host, bytes, cudaMemcpyHostToDevice, p.stream));
     KF_TRY(kifmm_eval(h, p.host_I.p, p.host_S.p, dtype, C));
     KF_CUDA(cudaMemcpyAsync(S_host, p.host_S.p, bytes, cudaMemcpyDeviceToHost, p.stream));
@@ -522,6 +551,7 @@ int kifmm_get_info(kifmm_plan_t h, kifmm_info* info) {
     }
     Plan& p = *h->p;
     info->n_points = p.tree.n;
+    info->n_padding = p.tree.n - p.n_real;
     info->n_boxes = p.tree.nboxes;
     info->n_levels = p.tree.nlevels;
     info->surface_points = p.S;

@@ -545,6 +545,7 @@ struct EvalView {
     int cp;                 // Chebyshev order p
     const double* ctab;     // Chebyshev weight table c_k T_k(xbar_n), row stride kChebTab
     const float* ctab32;
+    int64_t n_real;         // the caller's points (sorted points with perm >= n_real are padding cells)
 };
 
 __device__ __forceinline__ double half_width(const EvalView& E, int lev) {
@@ -552,11 +553,12 @@ __device__ __forceinline__ double half_width(const EvalView& E, int lev) {
 }
 
 template <class T>
-__global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, int64_t n, double* Is,
+__global__ void k_scatter_q(const T* I, const int32_t* perm, const double* w, int64_t n, int64_t n_real, double* Is,
                             double* q) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    double v = (double)I[perm[k]];
+    const int64_t j = perm[k];
+    const double v = j < n_real ? (double)I[j] : 0.0;   // padding cells: I = 0
     Is[k] = v;
     q[k] = v * w[k];
 }
@@ -1259,7 +1261,7 @@ __global__ void __launch_bounds__(P2P_T) k_p2p(EvalView E, const int32_t* leaves
             double s = 0;
             for (int k = 0; k < P2P_GRP; ++k) s += red[k][tl];
             double v = C * (s + far[i] + sigma[i] * Is[i]);
-            out[perm[i]] = (TO)v;
+            if (perm[i] < E.n_real) out[perm[i]] = (TO)v;
         }
         __syncthreads();
     }
@@ -1377,7 +1379,7 @@ __global__ void __launch_bounds__(P2Q_T) k_p2p_mixed(EvalView E, const int32_t* 
             if (i < p1) {
                 double s = 0;
                 for (int k = 0; k < P2Q_GRP; ++k) s += red[k][tl];
-                out[perm[i]] = (TO)(C * (s + far[i] + sigma[i] * Is[i]));
+                if (perm[i] < E.n_real) out[perm[i]] = (TO)(C * (s + far[i] + sigma[i] * Is[i]));
             }
         }
         __syncthreads();
@@ -1434,6 +1436,7 @@ static EvalView make_view(Plan& p) {
     E.cp = p.m0;
     E.ctab = ptr<double>(p.ctab);
     E.ctab32 = ptr<float>(p.ctab32);
+    E.n_real = p.n_real;
     return E;
 }
 
@@ -1710,10 +1713,10 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
 }
 
 // q = I h^3 and I in sorted order (used by the surrogate's judge)
-int kifmm_scatter_weights(Plan& p, const double* I) {
+int kifmm_scatter_weights(Plan& p, const double* I, cudaStream_t st) {
     const int64_t n = p.tree.n;
-    k_scatter_q<double><<<nbk(n, 256), 256, 0, p.stream>>>(I, ptr<int32_t>(p.tree.perm), ptr<double>(p.w), n,
-                                                            ptr<double>(p.Isort), ptr<double>(p.q));
+    k_scatter_q<double><<<nbk(n, 256), 256, 0, st>>>(I, ptr<int32_t>(p.tree.perm), ptr<double>(p.w), n,
+                                                            p.n_real, ptr<double>(p.Isort), ptr<double>(p.q));
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -1728,10 +1731,10 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     mark(p, 0);
     if (dtype == KIFMM_F64)
         k_scatter_q<double><<<nbk(n, 256), 256, 0, st>>>((const double*)I, ptr<int32_t>(t.perm), ptr<double>(p.w),
-                                                         n, ptr<double>(p.Isort), ptr<double>(p.q));
+                                                         n, p.n_real, ptr<double>(p.Isort), ptr<double>(p.q));
     else
         k_scatter_q<float><<<nbk(n, 256), 256, 0, st>>>((const float*)I, ptr<int32_t>(t.perm), ptr<double>(p.w),
-                                                        n, ptr<double>(p.Isort), ptr<double>(p.q));
+                                                        n, p.n_real, ptr<double>(p.Isort), ptr<double>(p.q));
     KF_LAUNCH();
     ++nl;
     mark(p, 1);

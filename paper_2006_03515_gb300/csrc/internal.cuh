@@ -199,6 +199,7 @@ struct Plan {
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
     bool cheb = false;           // Chebyshev-node representation (p = m0, S = p^3), no pseudo-inverses
     double uniform_h = 0;        // cell edge of a uniform-h plan (0: per-point h, or rectangular cells)
+    int64_t n_real = 0;          // the caller's points; tree.n - n_real zero-weight padding cells follow them
     int kind = 0;                // kernel: 0 the paper's, 1 three-exponential Helmholtz, 2 three-group
     bool rect = false;           // every cell is the rectangular box cell_dims (hx, hy, hz)
     double cell_dims[3] = {0, 0, 0};
@@ -243,6 +244,11 @@ struct Plan {
 };
 
 // tree.cu
+// the full grid of a box of cubic cells (edge h) padded with zero-weight cells to extents that
+// are multiples of 2 nc, after the caller's n points (out, *n_total > n), and the root cube at
+// the grid's corner with side nc h 2^L; *n_total = n (nothing allocated) for other point sets
+int pad_to_lattice(cudaStream_t st, const double* pts, int64_t n, double h, int nc, DevBuf& out, int64_t* n_total,
+                   double root[4]);
 int build_tree(Plan& p, const double* points_dev, const double* h_dev, double uniform_h,
                const kifmm_opts& o);
 int build_lists(Plan& p);
@@ -294,10 +300,10 @@ int pinv_oz_apply(cudaStream_t st, const double* chk, int S, const int32_t* boxe
 // systematic sampling, weights 1 / (k m_i)); perm (sorted -> caller) gives sorted indices
 size_t importance_ws_bytes(int64_t n, int k);
 int importance_targets(cudaStream_t st, const double* S, int64_t n, int k, uint64_t seed, const int32_t* perm,
-                       void* ws, int32_t* tcaller, int32_t* tsorted, double* wt, int num_sms);
+                       int64_t nperm, void* ws, int32_t* tcaller, int32_t* tsorted, double* wt, int num_sms);
 // api.cu / eval.cu helpers for the surrogate
 Plan* kifmm_plan_internal(kifmm_plan_t h);
-int kifmm_scatter_weights(Plan& p, const double* I);
+int kifmm_scatter_weights(Plan& p, const double* I, cudaStream_t st);
 // eval.cu
 int build_eval_data(Plan& p);
 int run_eval(Plan& p, const void* I, void* S, int dtype, double C);

@@ -105,10 +105,10 @@ __global__ void k_nf_table(const int32_t* ref, int nc, int R, double h, KParams 
 // given, from the FP32 rows of the tensor-core L2P (row of the leaf's box, npl cells, stride R)
 template <class TO>
 __global__ void k_nf_finish(const float* near, const double* far, const float* fst, const int32_t* leaves, int npl,
-                            int R, const double* sigma, const double* Is, const int32_t* perm, int64_t n, double C,
-                            TO* out) {
+                            int R, const double* sigma, const double* Is, const int32_t* perm, int64_t n,
+                            int64_t n_real, double C, TO* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || perm[i] >= n_real) return;   // (padding cells have no output)
     const double fa = fst ? (double)fst[(int64_t)leaves[i / npl] * R + i % npl] : far[i];
     out[perm[i]] = (TO)(C * ((double)near[i] + fa + sigma[i] * Is[i]));
 }
@@ -605,11 +605,11 @@ int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int
     if (dtype == KIFMM_F64)
         k_nf_finish<double><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, fst, ptr<int32_t>(p.leaves),
                                                           p.nf_R, p.R, ptr<double>(p.sigma), ptr<double>(p.Isort),
-                                                          ptr<int32_t>(p.tree.perm), n, C, (double*)out);
+                                                          ptr<int32_t>(p.tree.perm), n, p.n_real, C, (double*)out);
     else
         k_nf_finish<float><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, fst, ptr<int32_t>(p.leaves),
                                                          p.nf_R, p.R, ptr<double>(p.sigma), ptr<double>(p.Isort),
-                                                         ptr<int32_t>(p.tree.perm), n, C, (float*)out);
+                                                         ptr<int32_t>(p.tree.perm), n, p.n_real, C, (float*)out);
     KF_LAUNCH();
     ++nl;
     return KIFMM_OK;

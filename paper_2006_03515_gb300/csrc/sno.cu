@@ -77,7 +77,6 @@ struct SnoModel {
     int nself = KIFMM_SELF_CELL_EXACT, nR = 0, ntaps = 0;   // halo (cells), stencil columns
     DevBuf near_d, near_w;           // int2 (di, dj) of every stencil column, its 2R + 1 float weights
     DevBuf scal;                     // photo_solve: amplitude scale (double)
-    double* jwt = nullptr;           // photo_solve: the judge targets' weights (in jws)
     DevBuf jws;                      // photo_solve: the judge's work space (sized at creation)
 };
 
@@ -1328,33 +1327,40 @@ __global__ void k_scale_out(const float* y, const double* s, double C, double* S
 
 // ---- judge: direct sum at sampled targets (FP32, absolute coordinates) ------------------------
 // The judge's direct sum at the k drawn targets, with each source read once: a block takes a
-// chunk of JG_CH sources (FP32 coordinates, FP64 weights) into shared memory and adds its
-// part of every target's sum (one target per thread and pass) into acc[t] (FP64 atomics).
-constexpr int JG_T = 256, JG_CH = 2048;
+// chunk of JG_CH sources (FP32 coordinates and weights) into shared memory and adds its part
+// of every target's sum (one target per thread and pass) into acc[t] (one FP64 atomic per
+// target and chunk). Within a chunk the pairs accumulate in FP32 with Kahan compensation: the
+// judge decides against a tolerance of order 1e-2, far above the FP32 sum's error.
+constexpr int JG_T = 256, JG_CH = 512;
 __global__ void __launch_bounds__(JG_T) k_judge_src(const double* pts, const double* q, const int32_t* targets,
                                                     int k, int64_t n, KParams kp, double* acc) {
-    __shared__ float4 sp[JG_CH];   // x, y, z, unused
-    __shared__ double sq[JG_CH];
+    __shared__ float4 sp[JG_CH];   // x, y, z, q
     const int64_t j0 = (int64_t)blockIdx.x * JG_CH;
     const int m = (int)min((int64_t)JG_CH, n - j0);
     for (int e = threadIdx.x; e < m; e += JG_T) {
         const int64_t j = j0 + e;
-        sp[e] = make_float4((float)pts[3 * j], (float)pts[3 * j + 1], (float)pts[3 * j + 2], 0.f);
-        sq[e] = q[j];
+        sp[e] = make_float4((float)pts[3 * j], (float)pts[3 * j + 1], (float)pts[3 * j + 2], (float)q[j]);
     }
     __syncthreads();
     for (int t = threadIdx.x; t < k; t += JG_T) {
         const int64_t i = targets[t];
         const float xi = (float)pts[3 * i], yi = (float)pts[3 * i + 1], zi = (float)pts[3 * i + 2];
         const int self = (i >= j0 && i < j0 + m) ? (int)(i - j0) : -1;
-        double a = 0.0;
+        Kahan a;
+        float part = 0.f;
         for (int e = 0; e < m; ++e) {
-            if (e == self) continue;
             const float4 v = sp[e];
             const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
-            a += (double)kern_f32(dx * dx + dy * dy + dz * dz, kp) * sq[e];
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float kv = e == self ? 0.f : kern_f32(r2, kp) * v.w;
+            part += kv;
+            if ((e & 15) == 15) {   // blocks of 16 pairs, then the compensated sum
+                a.add(part);
+                part = 0.f;
+            }
         }
-        atomicAdd(acc + t, a);
+        a.add(part);
+        atomicAdd(acc + t, a.value());
     }
 }
 __global__ void k_judge_fin(const double* acc, const int32_t* targets, int k, const double* sigma, const double* Isort,
@@ -1515,13 +1521,15 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
     if ((rc = dev_alloc(M.g, (size_t)BC * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.ga, (size_t)BC * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.loss, 16))) return fail(rc);
-    if ((rc = dev_alloc(M.jt, SNO_MAX_JUDGE * 4))) return fail(rc);
-    if ((rc = dev_alloc(M.jref, SNO_MAX_JUDGE * 8))) return fail(rc);
-    if ((rc = dev_alloc(M.jorig, SNO_MAX_JUDGE * 4))) return fail(rc);
-    if ((rc = dev_alloc(M.jerr, 8))) return fail(rc);
-    if ((rc = dev_alloc(M.scal, 16))) return fail(rc);
-    {   // judge work space: the target draw's, then the weights and the targets' sums (8 k each)
-        const size_t ws = importance_ws_bytes(M.np3, SNO_MAX_JUDGE) + 2 * 8 * (size_t)SNO_MAX_JUDGE;
+    // judge buffers for a batch of max_batch fields: targets, references, caller indices, errors, scales
+    if ((rc = dev_alloc(M.jt, (size_t)max_batch * SNO_MAX_JUDGE * 4))) return fail(rc);
+    if ((rc = dev_alloc(M.jref, (size_t)max_batch * SNO_MAX_JUDGE * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.jorig, (size_t)max_batch * SNO_MAX_JUDGE * 4))) return fail(rc);
+    if ((rc = dev_alloc(M.jerr, (size_t)max_batch * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.scal, (size_t)max_batch * 8 + 8))) return fail(rc);
+    {   // judge work space: the target draw's (reused field by field), then per field the
+        // weights and the targets' sums (8 k each)
+        const size_t ws = importance_ws_bytes(M.np3, SNO_MAX_JUDGE) + 2 * 8 * (size_t)max_batch * SNO_MAX_JUDGE;
         if ((rc = dev_alloc(M.jws, ws))) return fail(rc);
     }
     if (cudaStreamSynchronize(M.st) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
@@ -1864,76 +1872,138 @@ int sno_adam_step(sno_model_t h, float lr, float beta1, float beta2, float eps) 
     return refresh_bf16(M);
 }
 
-int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, double* S_dev, double C, double tol,
-                int k_samples, uint64_t seed, int* used_fallback, double* judged_err) {
-    set_error("");
-    if (!plan || !model || !I_dev || !S_dev || k_samples < 1 || k_samples > SNO_MAX_JUDGE) {
+// Surrogate-first solves of `count` fields (one plan each, the model's grid) on plans[0]'s
+// stream: the batched forward pass, then per field the importance-sampled judge, then one
+// FMM batch for the fields judged above tol.
+static int photo_solve_impl(kifmm_plan_t* plans, int count, SnoModel& M, const double* const* I, double* const* S,
+                            const double* Cs, double tol, int k_samples, uint64_t seed, int* used_fallback,
+                            double* judged_err) {
+    if (!plans || count < 1 || count > M.maxB || !I || !S || k_samples < 1 || k_samples > SNO_MAX_JUDGE) {
         set_error("photo_solve: invalid argument");
         return KIFMM_ERR_ARG;
     }
-    Plan& p = *kifmm_plan_internal(plan);
-    SnoModel& M = model->m;
-    const int64_t n = p.tree.n;
-    if (n != M.np3) {
-        set_error("photo_solve: the plan's point count differs from the model's grid");
-        return KIFMM_ERR_ARG;
-    }
-    cudaStream_t st = p.stream;
-    cudaStream_t saved = M.st;
-    M.st = st;
-    if (M.near_on) {   // the model's near part must be the plan's kernel and cells
-        auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
-        if (!same(M.na, p.a) || !same(M.nb, p.b) || !same(M.nh, p.uniform_h) || p.self_mode != M.nself) {
-            M.st = saved;
-            set_error("photo_solve: the model's near part was set for another kernel, cell size or self term");
+    for (int b = 0; b < count; ++b) {
+        if (!plans[b] || !I[b] || !S[b]) {
+            set_error("photo_solve: invalid argument");
             return KIFMM_ERR_ARG;
         }
+        Plan& p = *kifmm_plan_internal(plans[b]);
+        if (p.n_real != p.tree.n) {
+            set_error("photo_solve: the plan holds padding cells (pad_lattice); the surrogate's grid is the plan's own");
+            return KIFMM_ERR_ARG;
+        }
+        if (p.tree.n != M.np3) {
+            set_error("photo_solve: the plan's point count differs from the model's grid");
+            return KIFMM_ERR_ARG;
+        }
+        if (M.near_on) {   // the model's near part must be the plan's kernel and cells
+            auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
+            if (!same(M.na, p.a) || !same(M.nb, p.b) || !same(M.nh, p.uniform_h) || p.self_mode != M.nself ||
+                p.kind != 0) {
+                set_error("photo_solve: the model's near part was set for another kernel, cell size or self term");
+                return KIFMM_ERR_ARG;
+            }
+        }
     }
+    const int64_t n = M.np3;
+    const int K = SNO_MAX_JUDGE;
+    cudaStream_t st = kifmm_plan_internal(plans[0])->stream;
+    cudaStream_t saved = M.st;
+    M.st = st;
     // surrogate in the amplitude-normalised linear form: s = max |I|, u = I / s (caller's
     // grid order), S = C s y
     float* u = ptr<float>(M.dz);
     float* y = ptr<float>(M.yb);
-    KF_CUDA(cudaMemsetAsync(M.scal.p, 0, 8, st));
-    k_sno_absmax<<<std::min<int64_t>(nbs(n, 256), 4LL * M.num_sms), 256, 0, st>>>(
-        I_dev, n, ptr<unsigned long long>(M.scal));
+    double* sc = ptr<double>(M.scal);
+    KF_CUDA(cudaMemsetAsync(sc, 0, (size_t)count * 8, st));
+    for (int b = 0; b < count; ++b) {
+        k_sno_absmax<<<std::min<int64_t>(nbs(n, 256), 4LL * M.num_sms), 256, 0, st>>>(
+            I[b], n, reinterpret_cast<unsigned long long*>(sc + b));
+        k_scale_in<<<nbs(n, 256), 256, 0, st>>>(I[b], sc + b, u + b * n, n);
+    }
     KF_LAUNCH();
-    k_scale_in<<<nbs(n, 256), 256, 0, st>>>(I_dev, ptr<double>(M.scal), u, n);
-    KF_LAUNCH();
-    int rc = forward(M, u, y, 1, false);
+    int rc = forward(M, u, y, count, false);
     M.st = saved;
     KF_TRY(rc);
-    k_scale_out<<<nbs(n, 256), 256, 0, st>>>(y, ptr<double>(M.scal), C, S_dev, n);
+    for (int b = 0; b < count; ++b) {
+        const double C = Cs ? Cs[b] : 1.0;
+        k_scale_out<<<nbs(n, 256), 256, 0, st>>>(y + b * n, sc + b, C, S[b], n);
+    }
     KF_LAUNCH();
     // judge: the direct sum at k targets drawn with probability m_i = 0.5 |S_i| / sum |S| + 0.5 / n
-    // (systematic sampling from the surrogate's own field, offset from a fixed LCG of `seed`),
+    // (systematic sampling from the surrogate's own field, offset from a fixed LCG of seed + b),
     // each weighted 1 / (k m_i): an importance-sampled estimate of the whole field's relative
     // L2 error that does not miss a concentrated source the way uniform samples do
-    DevBuf &dt = M.jt, &dref = M.jref, &dorig = M.jorig, &derr = M.jerr;
-    M.jwt = reinterpret_cast<double*>(static_cast<char*>(M.jws.p) + importance_ws_bytes(n, SNO_MAX_JUDGE));
-    KF_TRY(importance_targets(st, S_dev, n, k_samples, seed, ptr<int32_t>(p.tree.perm), M.jws.p, nullptr,
-                              ptr<int32_t>(dt), M.jwt, M.num_sms));
-    // weights q = I h^3 in sorted order (the evaluation's own scatter kernel path)
-    KF_TRY(kifmm_scatter_weights(p, I_dev));
-    double* jacc = M.jwt + SNO_MAX_JUDGE;   // per-target sums (after the weights in the work space)
-    KF_CUDA(cudaMemsetAsync(jacc, 0, (size_t)k_samples * 8, st));
-    k_judge_src<<<nbs(n, JG_CH), JG_T, 0, st>>>(ptr<double>(p.pts), ptr<double>(p.q), ptr<int32_t>(dt), k_samples,
-                                                  n, make_kparams(p.a, p.b), jacc);
-    KF_LAUNCH();
-    k_judge_fin<<<nbs(k_samples, 128), 128, 0, st>>>(jacc, ptr<int32_t>(dt), k_samples, ptr<double>(p.sigma),
-                                                     ptr<double>(p.Isort), C, ptr<int32_t>(p.tree.perm),
-                                                     ptr<double>(dref), ptr<int32_t>(dorig));
-    KF_LAUNCH();
-    k_judge_err<<<1, 256, 0, st>>>(S_dev, ptr<double>(dref), ptr<int32_t>(dorig), M.jwt, k_samples,
-                                   ptr<double>(derr));
-    KF_LAUNCH();
-    double err = 0;
-    KF_CUDA(cudaMemcpyAsync(&err, derr.p, 8, cudaMemcpyDeviceToHost, st));
+    double* wts = reinterpret_cast<double*>(static_cast<char*>(M.jws.p) + importance_ws_bytes(n, K));
+    double* accs = wts + (size_t)M.maxB * K;
+    KF_CUDA(cudaMemsetAsync(accs, 0, (size_t)count * K * 8, st));
+    for (int b = 0; b < count; ++b) {
+        Plan& p = *kifmm_plan_internal(plans[b]);
+        const double C = Cs ? Cs[b] : 1.0;
+        int32_t* tb = ptr<int32_t>(M.jt) + (size_t)b * K;
+        double* wb = wts + (size_t)b * K;
+        double* ab = accs + (size_t)b * K;
+        KF_TRY(importance_targets(st, S[b], n, k_samples, seed + (uint64_t)b, ptr<int32_t>(p.tree.perm), n, M.jws.p,
+                                  nullptr, tb, wb, M.num_sms));
+        // weights q = I h^3 in sorted order (the evaluation's own scatter kernel)
+        KF_TRY(kifmm_scatter_weights(p, I[b], st));
+        k_judge_src<<<nbs(n, JG_CH), JG_T, 0, st>>>(ptr<double>(p.pts), ptr<double>(p.q), tb, k_samples, n,
+                                                      make_kparams(p.a, p.b), ab);
+        k_judge_fin<<<nbs(k_samples, 128), 128, 0, st>>>(ab, tb, k_samples, ptr<double>(p.sigma), ptr<double>(p.Isort),
+                                                         C, ptr<int32_t>(p.tree.perm), ptr<double>(M.jref) + (size_t)b * K,
+                                                         ptr<int32_t>(M.jorig) + (size_t)b * K);
+        k_judge_err<<<1, 256, 0, st>>>(S[b], ptr<double>(M.jref) + (size_t)b * K, ptr<int32_t>(M.jorig) + (size_t)b * K,
+                                       wb, k_samples, ptr<double>(M.jerr) + b);
+        KF_LAUNCH();
+    }
+    std::vector<double> err(count);
+    KF_CUDA(cudaMemcpyAsync(err.data(), M.jerr.p, (size_t)count * 8, cudaMemcpyDeviceToHost, st));
     KF_CUDA(cudaStreamSynchronize(st));
-    if (judged_err) *judged_err = err;
-    const int fb = !(err <= tol);
-    if (used_fallback) *used_fallback = fb;
-    if (fb) KF_TRY(kifmm_eval(plan, I_dev, S_dev, KIFMM_F64, C));
+    std::vector<kifmm_plan_t> fp;
+    std::vector<const void*> fi;
+    std::vector<void*> fs;
+    std::vector<double> fc;
+    for (int b = 0; b < count; ++b) {
+        const int fb = !(err[b] <= tol);
+        if (judged_err) judged_err[b] = err[b];
+        if (used_fallback) used_fallback[b] = fb;
+        if (fb) {
+            fp.push_back(plans[b]);
+            fi.push_back(I[b]);
+            fs.push_back(S[b]);
+            fc.push_back(Cs ? Cs[b] : 1.0);
+        }
+    }
+    if (!fp.empty()) {   // the FMM for the rejected fields, as one batch (ordered on st after the judge)
+        const int nf = (int)fp.size();
+        KF_TRY(kifmm_eval_batch(fp.data(), fi.data(), fs.data(), nf, KIFMM_F64, fc.data(), 0,
+                                std::min(nf, KIFMM_MAX_LANES)));
+        KF_CUDA(cudaStreamSynchronize(kifmm_plan_internal(fp[0])->stream));
+    }
     return KIFMM_OK;
+}
+
+int photo_solve(kifmm_plan_t plan, sno_model_t model, const double* I_dev, double* S_dev, double C, double tol,
+                int k_samples, uint64_t seed, int* used_fallback, double* judged_err) {
+    set_error("");
+    if (!plan || !model || !I_dev || !S_dev) {
+        set_error("photo_solve: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    double* Sp = S_dev;
+    return photo_solve_impl(&plan, 1, model->m, &I_dev, &Sp, &C, tol, k_samples, seed, used_fallback, judged_err);
+}
+
+int photo_solve_batch(kifmm_plan_t* plans, int count, sno_model_t model, const double* const* I_dev,
+                      double* const* S_dev, const double* C, double tol, int k_samples, uint64_t seed,
+                      int* used_fallback, double* judged_err) {
+    set_error("");
+    if (!model) {
+        set_error("photo_solve_batch: invalid argument");
+        return KIFMM_ERR_ARG;
+    }
+    return photo_solve_impl(plans, count, model->m, I_dev, S_dev, C, tol, k_samples, seed, used_fallback,
+                            judged_err);
 }
 
 }  // extern "C"

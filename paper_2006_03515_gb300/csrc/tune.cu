@@ -68,9 +68,9 @@ __global__ void k_is_add(double* cdf, int64_t n, const double* blk) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) cdf[i] += blk[i / IS_SC];
 }
-__global__ void k_is_inv(const int32_t* perm, int64_t n, int32_t* inv) {
+__global__ void k_is_inv(const int32_t* perm, int64_t nperm, int64_t n, int32_t* inv) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) inv[perm[k]] = (int32_t)k;
+    if (k < nperm && perm[k] < n) inv[perm[k]] = (int32_t)k;   // (perm >= n: padding cells)
 }
 // target t: the first i (caller order) with cdf[i] > u_t, its sorted index and weight
 __global__ void k_is_draw(const double* cdf, int64_t n, int k, double U, const int32_t* inv, int32_t* tcaller,
@@ -97,7 +97,7 @@ size_t importance_ws_bytes(int64_t n, int k) {
 }
 
 int importance_targets(cudaStream_t st, const double* S, int64_t n, int k, uint64_t seed, const int32_t* perm,
-                       void* ws, int32_t* tcaller, int32_t* tsorted, double* wt, int num_sms) {
+                       int64_t nperm, void* ws, int32_t* tcaller, int32_t* tsorted, double* wt, int num_sms) {
     uint64_t sst = seed * 6364136223846793005ull + 1442695040888963407ull;
     sst = sst * 6364136223846793005ull + 1442695040888963407ull;
     const double U = (double)(sst >> 11) * (1.0 / 9007199254740992.0);
@@ -111,7 +111,7 @@ int importance_targets(cudaStream_t st, const double* S, int64_t n, int k, uint6
     k_is_scan<<<(unsigned)nbk, IS_SC, 0, st>>>(S, n, tot, cdf, blk);
     k_is_scan_blocks<<<1, 32, 0, st>>>(blk, (int)nbk);
     k_is_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cdf, n, blk);
-    if (perm) k_is_inv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(perm, n, inv);
+    if (perm) k_is_inv<<<(unsigned)((nperm + 255) / 256), 256, 0, st>>>(perm, nperm, n, inv);
     k_is_draw<<<(unsigned)((k + 127) / 128), 128, 0, st>>>(cdf, n, k, U, perm ? inv : nullptr, tcaller, tsorted, wt);
     KF_LAUNCH();
     return KIFMM_OK;
@@ -233,12 +233,12 @@ extern "C" int kifmm_tune(const double* points, int64_t n, const double* cell_h,
         if (!rc && !have_ref) {
             // targets drawn from this first evaluation, the FP64 direct sum there (the plan's
             // sorted points, weights and self terms; C = 1)
-            rc = importance_targets(st, ptr<double>(Sb), n, k_samples, 0x5eedULL, ptr<int32_t>(P.tree.perm), wsd.p,
+            rc = importance_targets(st, ptr<double>(Sb), n, k_samples, 0x5eedULL, ptr<int32_t>(P.tree.perm), P.tree.n, wsd.p,
                                     ptr<int32_t>(tc), ptr<int32_t>(ts), ptr<double>(wt), nsm);
             if (!rc && cudaMemsetAsync(acc.p, 0, (size_t)k_samples * 8, st) != cudaSuccess) rc = KIFMM_ERR_CUDA;
             if (!rc) {
-                k_tune_ref<<<(unsigned)((n + TR_CH - 1) / TR_CH), TR_T, 0, st>>>(
-                    ptr<double>(P.pts), ptr<double>(P.q), ptr<int32_t>(ts), k_samples, n, make_kparams_kind(P.kind, a, b),
+                k_tune_ref<<<(unsigned)((P.tree.n + TR_CH - 1) / TR_CH), TR_T, 0, st>>>(   // (padding cells: q = 0)
+                    ptr<double>(P.pts), ptr<double>(P.q), ptr<int32_t>(ts), k_samples, P.tree.n, make_kparams_kind(P.kind, a, b),
                     ptr<double>(acc));
                 k_tune_ref_fin<<<(unsigned)((k_samples + 127) / 128), 128, 0, st>>>(
                     ptr<double>(acc), ptr<int32_t>(ts), k_samples, ptr<double>(P.sigma), ptr<double>(P.Isort),

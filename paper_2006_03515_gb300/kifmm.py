@@ -55,7 +55,7 @@ class _Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("self_mode", ctypes.c_int), ("pinv_eps", ctypes.c_double),
                 ("has_root", ctypes.c_int), ("root", ctypes.c_double * 4), ("stream", ctypes.c_void_p),
                 ("repr", ctypes.c_int), ("radii", ctypes.c_double * 2), ("cell_dims", ctypes.c_double * 3),
-                ("kernel", ctypes.c_int)]
+                ("kernel", ctypes.c_int), ("pad_lattice", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -67,7 +67,8 @@ class _Info(ctypes.Structure):
                 ("m2l_flops", ctypes.c_double), ("upward_flops", ctypes.c_double),
                 ("upward_mma_flops", ctypes.c_double), ("near_tensor", ctypes.c_int64),
                 ("lattice_far", ctypes.c_int64), ("m2m_tensor_levels", ctypes.c_int64),
-                ("l2l_tensor_levels", ctypes.c_int64), ("upward_tensor_levels", ctypes.c_int64)]
+                ("l2l_tensor_levels", ctypes.c_int64), ("upward_tensor_levels", ctypes.c_int64),
+                ("n_padding", ctypes.c_int64)]
 
 
 class _TuneEntry(ctypes.Structure):
@@ -82,7 +83,7 @@ EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", 
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
            "sno_set_bf16", "sno_set_period", "sno_set_near_field", "sno_init_far_field", "sno_forward",
-           "sno_loss_grad", "sno_adam_step", "photo_solve"]
+           "sno_loss_grad", "sno_adam_step", "photo_solve", "photo_solve_batch"]
 
 _lib = None
 
@@ -150,7 +151,7 @@ class Plan:
 
     def __init__(self, points, h, leaf_size=64, surface_order=6, a=None, b=None, precision="fp64",
                  self_mode="cell_exact", pinv_eps=1e-5, root=None, stream=None, repr="surface",
-                 surface_radii=None, cell_dims=None, kernel="zheleznyak"):
+                 surface_radii=None, cell_dims=None, kernel="zheleznyak", pad_lattice=False):
         import torch
         L = load()
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
@@ -175,6 +176,7 @@ class Plan:
         o.pinv_eps = float(pinv_eps)
         o.repr = REPR[repr]
         o.kernel = KERNEL[kernel]
+        o.pad_lattice = 1 if pad_lattice else 0   # zero-weight cells up to the leaf lattice (full box grids)
         if root is not None:
             o.has_root = 1
             for k in range(4):
@@ -235,7 +237,8 @@ class Plan:
                     m2l_flops=float(inf.m2l_flops), upward_flops=float(inf.upward_flops),
                     upward_mma_flops=float(inf.upward_mma_flops), near_tensor=bool(inf.near_tensor),
                     lattice_far=bool(inf.lattice_far), m2m_tensor_levels=int(inf.m2m_tensor_levels),
-                    l2l_tensor_levels=int(inf.l2l_tensor_levels), upward_tensor_levels=int(inf.upward_tensor_levels))
+                    l2l_tensor_levels=int(inf.l2l_tensor_levels), upward_tensor_levels=int(inf.upward_tensor_levels),
+                    n_padding=int(inf.n_padding))
 
     def tree(self):
         inf = self.info()
@@ -257,7 +260,7 @@ class Plan:
         return off, items[:inf["list_len"][which]]
 
     def sigma(self):
-        s = np.empty(self.n, np.float64)
+        s = np.empty(self.info()["n_points"], np.float64)
         _check(load().kifmm_get_sigma(self._h_ptr, ctypes.c_void_p(s.ctypes.data)))
         return s
 
@@ -315,7 +318,7 @@ def autotune(points, h, candidates=(32, 48, 64, 96, 128), surface_order=6, a=Non
 
 
 def tune(points, h, I, a, b, leaf=(32, 64, 128), order=(4, 6, 8), radii=None, target=1e-3, precision="mixed",
-         k_samples=256, reps=3, root=None, stream=None):
+         k_samples=256, reps=3, root=None, stream=None, pad_lattice=False):
     """The fastest (leaf, order, radii) whose estimated error against the direct sum is at most
     target / 2 (kifmm_tune). I: representative source, CUDA float64 (N,). radii: a list of
     (inner, outer) pairs, or None for the default surfaces. Returns (best, table), dicts
@@ -336,6 +339,7 @@ def tune(points, h, I, a, b, leaf=(32, 64, 128), order=(4, 6, 8), radii=None, ta
     L.kifmm_default_opts(ctypes.byref(o))
     o.precision = PRECISION[precision]
     o.stream = _stream_ptr(stream)
+    o.pad_lattice = 1 if pad_lattice else 0
     if root is not None:
         o.has_root = 1
         for k in range(4):
@@ -433,7 +437,8 @@ def _load_sno(L):
     L.sno_adam_step.argtypes = [vp, flt, flt, flt, flt]
     L.photo_solve.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, ctypes.POINTER(i32),
                               ctypes.POINTER(dbl)]
-    for name in ("sno_create", "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint", "sno_set_params",
+    L.photo_solve_batch.argtypes = [vp, i32, vp, vp, vp, vp, dbl, i32, ctypes.c_uint64, vp, vp]
+    for name in ("photo_solve_batch", "sno_create", "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint", "sno_set_params",
                  "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_set_period", "sno_set_near_field",
                  "sno_init_far_field", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"):
         getattr(L, name).restype = ctypes.c_int
@@ -596,3 +601,30 @@ def photo_solve(plan, model, I, S=None, C=1.0, tol=0.05, k_samples=256, seed=0):
     _check(load().photo_solve(plan.handle, model.handle, ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(S.data_ptr()),
                               float(C), float(tol), int(k_samples), int(seed), ctypes.byref(fb), ctypes.byref(err)))
     return S, bool(fb.value), err.value
+
+
+def photo_solve_batch(plans, model, Is, Ss=None, C=None, tol=0.05, k_samples=256, seed=0):
+    """photo_solve for several fields at once (photo_solve_batch in kifmm.h): one plan, source
+    and result per field (CUDA float64 tensors of the model's grid). Returns (Ss,
+    used_fallback list, judged_error list); returns when every result is complete."""
+    import torch
+    k = len(plans)
+    if not (len(Is) == k and k >= 1):
+        raise ValueError("one source per plan")
+    for I in Is:
+        if not (isinstance(I, torch.Tensor) and I.is_cuda and I.dtype == torch.float64 and I.is_contiguous()):
+            raise TypeError("sources must be contiguous CUDA float64 tensors")
+    if Ss is None:
+        Ss = [torch.empty_like(I) for I in Is]
+    for S, I in zip(Ss, Is):
+        if not (isinstance(S, torch.Tensor) and S.is_cuda and S.dtype == torch.float64 and S.is_contiguous()
+                and S.numel() == I.numel()):
+            raise TypeError("results must be contiguous CUDA float64 tensors of the sources' size")
+    hp = (ctypes.c_void_p * k)(*[pl.handle.value for pl in plans])
+    ip = (ctypes.c_void_p * k)(*[I.data_ptr() for I in Is])
+    sp = (ctypes.c_void_p * k)(*[S.data_ptr() for S in Ss])
+    cs = (ctypes.c_double * k)(*([1.0] * k if C is None else [float(c) for c in C]))
+    fb = (ctypes.c_int * k)()
+    err = (ctypes.c_double * k)()
+    _check(load().photo_solve_batch(hp, k, model.handle, ip, sp, cs, float(tol), int(k_samples), int(seed), fb, err))
+    return Ss, [bool(x) for x in fb], [float(x) for x in err]

@@ -244,6 +244,34 @@ def test_photo_solve_judge_and_fallback():
     plan.close()
 
 
+def test_photo_solve_batch_matches_single():
+    import torch
+    n = 16
+    plans = [surrogate.grid_plan(n, leaf=64, m0=6)[0] for _ in range(3)]
+    _, pts, C = surrogate.grid_plan(n, leaf=64, m0=6)
+    M = kifmm.SNO(n, width=4, modes=4, layers=1, proj=8, max_batch=4)
+    M.init_params(seed=9)
+    Is = [torch.as_tensor(W.gaussian_mixture(pts, 80 + b), device="cuda") for b in range(3)]
+    Cs = [C, 2 * C, 0.5 * C]
+    # the judged errors of the untrained network, one field at a time
+    single = [kifmm.photo_solve(plans[b], M, Is[b], C=Cs[b], tol=1e30, k_samples=64, seed=11 + b)
+              for b in range(3)]
+    e = sorted(x for _, _, x in single)
+    tol = 0.5 * (e[0] + e[1])   # one field passes, two fall back
+    Ss, fbs, errs = kifmm.photo_solve_batch(plans, M, Is, C=Cs, tol=tol, k_samples=64, seed=11)
+    for b in range(3):
+        assert errs[b] == pytest.approx(single[b][2], rel=1e-6)
+        assert fbs[b] == (not single[b][2] <= tol)
+        want = plans[b].eval(Is[b], C=Cs[b]) if fbs[b] else single[b][0]
+        assert torch.allclose(Ss[b], want, rtol=1e-6, atol=0)
+    assert 0 < sum(fbs) < 3
+    with pytest.raises(kifmm.KifmmError):   # more fields than the model's batch
+        kifmm.photo_solve_batch(plans + plans[:2], M, Is + Is[:2])
+    M.close()
+    for pl in plans:
+        pl.close()
+
+
 NEAR = dict(n=8, N=12, r_in=1.0, r_out=2.5)
 
 
