@@ -523,7 +523,8 @@ def surrogate_bench(args, dev, stream, peaks):
     far part's Fourier multiplier, one from a random start. Held-out fields: their rel-L2
     against the KIFMM labels, and photo_solve's judged error and fallback at 1e-2; time per
     field of the batched forward pass (batch 32) and of photo_solve, against kifmm_eval per
-    field on the same grid (one field, and 8 fields as one captured batch on 8 lanes)."""
+    field on the same grid (one field, and 8 fields as one captured batch on 8 lanes), and of
+    photo_solve_batch over 32 held-out fields (one forward pass, 32 judges)."""
     import numpy as np
     import torch
     from paper_2006_03515_gb300 import kifmm, surrogate
@@ -607,6 +608,22 @@ def surrogate_bench(args, dev, stream, peaks):
     e1.record(stream)
     e1.synchronize()
     ps_ms = e0.elapsed_time(e1) / reps
+    # batched surrogate-first solves: B held-out fields on B plans of the grid (judge at 256 targets)
+    bplans = [fmm] + [surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream)[0]
+                      for _ in range(B - 1)]
+    bIs = [torch.as_tensor(W.surrogate_field(pts, 100000 * 1000003 + k), device=dev) for k in range(B)]
+    bSs = [torch.empty_like(x) for x in bIs]
+    for _ in range(2):
+        kifmm.photo_solve_batch(bplans, M, bIs, bSs, C=[C] * B, tol=1e-2, k_samples=256, seed=1)
+    e0.record(stream)
+    for _ in range(reps):
+        _, bfb, berr = kifmm.photo_solve_batch(bplans, M, bIs, bSs, C=[C] * B, tol=1e-2, k_samples=256, seed=1)
+    e1.record(stream)
+    e1.synchronize()
+    psb_ms = e0.elapsed_time(e1) / reps / B
+    for pl in bplans[1:]:
+        pl.close()
+    del bIs, bSs
     for _ in range(2):
         fmm.eval(I, S, C=C)
     e0.record(stream)
@@ -634,6 +651,8 @@ def surrogate_bench(args, dev, stream, peaks):
     fwd_gbs = alg_bytes / (fwd_ms * 1e-3) / 1e9
     out.update({"forward_ms_batch32": fwd_ms, "forward_ms_per_field": fwd_ms / B,
                 "photo_solve_ms_per_field": ps_ms, "kifmm_eval_ms_per_field": fmm_ms,
+                "photo_solve_batch32_ms_per_field": psb_ms,
+                "photo_solve_batch32_fallbacks": int(sum(bfb)), "photo_solve_batch32_judged_max": float(max(berr)),
                 "kifmm_eval_batch8_ms_per_field": fmm_b_ms,
                 "points_per_s": B * n3 / (fwd_ms * 1e-3), "params": M.num_params(),
                 "roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm, "unit": "GB/s", "frac": fwd_gbs / hbm,

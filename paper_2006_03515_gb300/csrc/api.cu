@@ -237,6 +237,8 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         if (nt > n) {
             points = static_cast<const double*>(padded.p);
             p->tree.n = n = nt;
+        }
+        if (root[3] > 0.0) {   // a box grid: the root on its leaf lattice (padded or not)
             o.has_root = 1;
             for (int k = 0; k < 4; ++k) o.root[k] = root[k];
         }

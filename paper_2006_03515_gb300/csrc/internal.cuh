@@ -245,8 +245,9 @@ struct Plan {
 
 // tree.cu
 // the full grid of a box of cubic cells (edge h) padded with zero-weight cells to extents that
-// are multiples of 2 nc, after the caller's n points (out, *n_total > n), and the root cube at
-// the grid's corner with side nc h 2^L; *n_total = n (nothing allocated) for other point sets
+// are multiples of 2 nc, after the caller's n points (out, *n_total > n; nothing allocated when
+// the extents already are), and the root cube at the grid's corner with side nc h 2^L in
+// root[0..3]; other point sets: *n_total = n, root[3] = 0
 int pad_to_lattice(cudaStream_t st, const double* pts, int64_t n, double h, int nc, DevBuf& out, int64_t* n_total,
                    double root[4]);
 int build_tree(Plan& p, const double* points_dev, const double* h_dev, double uniform_h,

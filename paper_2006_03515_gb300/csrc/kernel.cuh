@@ -111,9 +111,9 @@ __device__ __forceinline__ float one_minus_exp_neg(float x, float x_l2e) {
     return 1.0f - ex2_approx(-x_l2e);
 }
 
-// FP32 kernel from the squared distance r2 > 0 (box-local coordinates).
+// FP32 kernel from the squared distance r2 > 0 (box-local coordinates); the paper's kernel
+// only (the comparison kernels run in the FP64 form).
 __device__ __forceinline__ float kern_f32(float r2, const KParams& k) {
-    if (k.kind) return (float)kern_f64(sqrt((double)r2), k);   // comparison kernels: FP64 evaluation
     const float rinv = rsqrt_approx(r2);
     const float R = r2 * rinv;
     const float ea = ex2_approx(-k.a_l2e * R);

@@ -65,9 +65,11 @@ struct SnoModel {
     // spectra (float2): cz [B][C][n][n][m], cy / gx [B][C][n][2m][m], gy [B][C][n][n][m],
     // V per layer [L][B][C][K], g / ga [B][C][K]
     DevBuf cz, cy, gx, gy, Vst, g, ga;
+    DevBuf m0ab;                     // inference, layer 0: A = R Wl and Bc = (R bl) O, [2][C][K] complex
     DevBuf jt, jref, jorig, jerr;    // photo_solve judge: targets, reference values, caller indices, error
     int mix_mb = 1;                  // modes per block of the mixing kernels
     size_t zr_smem_f = 0, zr_smem_b = 0, zr_smem_p = 0, mix_smem = 0, mixg_smem = 0, zf_smem = 0;
+    size_t zi_smem = 0, zi_smem_y = 0;   // k_zrow_inf (0: the shape does not suit it)
     int num_sms = 1;
     int64_t steps = 0;
     int period = 0;                  // N of the transforms (>= n)
@@ -209,6 +211,171 @@ __global__ void __launch_bounds__(256) k_plane(const float2* __restrict__ in, fl
                 if (u < nj) out[((p0 + pl) * Lout + j0 + u) * (int64_t)inner + i0 + w] = make_float2(re[h][u], im[h][u]);
         }
     }
+}
+
+// 8-byte asynchronous global-to-shared copies (the plane and z-row kernels' prefetch)
+__device__ __forceinline__ void sno_cp8(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void sno_cp16(void* dst, const void* src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void sno_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void sno_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Plane DFT, persistent and double-buffered: the same contraction as k_plane over tiles of
+// PB planes (or one plane and a chunk of ICH columns); each block walks its tiles with the
+// next tile's inputs copied asynchronously into the second buffer while it computes the
+// current one, so the global loads overlap the arithmetic. T stays in shared memory.
+__global__ void __launch_bounds__(256) k_plane2(const float2* __restrict__ in, float2* __restrict__ out,
+                                                const float2* __restrict__ T, int64_t P, int Lin, int Lout,
+                                                int inner, int PB, int ICH, int nch, int64_t ntiles) {
+    extern __shared__ float2 psh[];   // T [Lout][Lin], then two buffers [Lin][PB * ICH]
+    float2* Ts = psh;
+    const int cmax = PB * min(ICH, inner);
+    float2* const buf0 = psh + Lout * Lin;   // buffer k at buf0 + k Lin cmax
+    for (int e = threadIdx.x; e < Lout * Lin; e += blockDim.x) Ts[e] = T[e];
+    auto shape = [&](int64_t t, int64_t& p0, int& np, int& i0, int& W) {
+        const int64_t pb = t / nch;
+        p0 = pb * PB;
+        np = (int)min((int64_t)PB, P - p0);
+        i0 = (int)(t % nch) * ICH;
+        W = min(ICH, inner - i0);
+    };
+    auto issue = [&](int64_t t, float2* dst) {   // a thread per column, down the Lin rows
+        int64_t p0;
+        int np, i0, W;
+        shape(t, p0, np, i0, W);
+        const int ncol = np * W;
+        for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+            const int pl = col / W, w = col - pl * W;
+            const float2* src = in + (p0 + pl) * Lin * (int64_t)inner + i0 + w;
+            for (int q = 0; q < Lin; ++q) sno_cp8(dst + q * ncol + col, src + (int64_t)q * inner);
+        }
+    };
+    int64_t t = blockIdx.x;
+    if (t < ntiles) issue(t, buf0);
+    sno_commit();
+    for (int it = 0; t < ntiles; t += gridDim.x, ++it) {
+        const int64_t tn = t + gridDim.x;
+        if (tn < ntiles) issue(tn, buf0 + (size_t)((it + 1) & 1) * Lin * cmax);
+        sno_commit();
+        sno_wait_prev();
+        __syncthreads();
+        const float2* X = buf0 + (size_t)(it & 1) * Lin * cmax;
+        int64_t p0;
+        int np, i0, W;
+        shape(t, p0, np, i0, W);
+        const int ncol = np * W;
+        // each thread: 8 consecutive outputs j0..j0+7 of two columns (col, col + ncol/2)
+        const int njb = (Lout + 7) / 8, nch2 = (ncol + 1) / 2;
+        for (int e = threadIdx.x; e < njb * nch2; e += blockDim.x) {
+            const int jb = e / nch2, c0 = e % nch2;
+            const int c1 = c0 + nch2 < ncol ? c0 + nch2 : c0;
+            const int j0 = 8 * jb;
+            const int nj = min(8, Lout - j0);
+            const float2* t0 = Ts + j0 * Lin;
+            float re[2][8], im[2][8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) re[0][u] = im[0][u] = re[1][u] = im[1][u] = 0.f;
+            for (int q = 0; q < Lin; ++q) {
+                const float2 x0 = X[q * ncol + c0], x1 = X[q * ncol + c1];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float2 a = t0[min(u, nj - 1) * Lin + q];
+                    re[0][u] = fmaf(a.x, x0.x, fmaf(-a.y, x0.y, re[0][u]));
+                    im[0][u] = fmaf(a.x, x0.y, fmaf(a.y, x0.x, im[0][u]));
+                    re[1][u] = fmaf(a.x, x1.x, fmaf(-a.y, x1.y, re[1][u]));
+                    im[1][u] = fmaf(a.x, x1.y, fmaf(a.y, x1.x, im[1][u]));
+                }
+            }
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                if (hh == 1 && c1 == c0) break;
+                const int col = hh ? c1 : c0;
+                const int pl = col / W, w = col % W;
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (u < nj) out[((p0 + pl) * Lout + j0 + u) * (int64_t)inner + i0 + w] = make_float2(re[hh][u], im[hh][u]);
+            }
+        }
+        __syncthreads();   // the buffer is refilled two tiles later
+    }
+}
+
+// ---- inference, layer 0: the lift v0 = Wl u + bl has rank one in the channels, so its
+// spectrum is V0[c][k] = Wl[c] U[k] + bl[c] O[k] (U the truncated transform of u, O that of
+// the field of ones, separable: O = Sx[kx] Sy[ky] Sz[kz] with S the sums of the tables' rows)
+// and the layer's mix G[o][k] = sum_c R[k][o][c] V0[c][k] = A[o][k] U[k] + Bc[o][k].
+// cu[b][x][y][kz] = sum_z Tzf[kz][z] u[b][x][y][z]; a block stages LU rows and the table
+constexpr int LU = 16;
+__global__ void __launch_bounds__(256) k_lift_u(const float* __restrict__ u, const float2* __restrict__ Tzf,
+                                                float2* __restrict__ cu, int64_t rows, int n, int m) {
+    extern __shared__ __align__(16) float lsh[];
+    float* us = lsh;                                            // [LU][n]
+    float2* tf = reinterpret_cast<float2*>(lsh + LU * n);       // [m][n]
+    for (int e = threadIdx.x; e < m * n; e += blockDim.x) tf[e] = Tzf[e];
+    const int64_t r0 = (int64_t)blockIdx.x * LU;
+    const int nr = (int)min((int64_t)LU, rows - r0);
+    for (int e = threadIdx.x; e < nr * n; e += blockDim.x) us[e] = u[r0 * n + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nr * m; e += blockDim.x) {
+        const int kz = e % m, rq = e / m;
+        float re = 0.f, im = 0.f;
+        for (int zz = 0; zz < n; ++zz) {
+            const float x = us[rq * n + zz];
+            const float2 t = tf[kz * n + zz];
+            re = fmaf(t.x, x, re);
+            im = fmaf(t.y, x, im);
+        }
+        cu[(r0 + rq) * m + kz] = make_float2(re, im);
+    }
+}
+// A[o][k] = sum_c R[k][o][c] Wl[c], Bc[o][k] = (sum_c R[k][o][c] bl[c]) O[k]
+template <class TR>
+__global__ void k_mix0_prep(const TR* __restrict__ Rr, const TR* __restrict__ Ri, const float* __restrict__ Wl,
+                            const float* __restrict__ bl, const float2* __restrict__ tyf,
+                            const float2* __restrict__ tzf, int C, int64_t K, int n, int m, float2* __restrict__ A,
+                            float2* __restrict__ Bc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)C * K) return;
+    const int64_t k = e % K;
+    const int o = (int)(e / K);
+    const int M2 = 2 * m;
+    const int kz = (int)(k % m), ky = (int)((k / m) % M2), kx = (int)(k / ((int64_t)M2 * m));
+    auto rowsum = [&](const float2* T, int j) {
+        float sr = 0.f, si = 0.f;
+        for (int q = 0; q < n; ++q) {
+            sr += T[j * n + q].x;
+            si += T[j * n + q].y;
+        }
+        return make_float2(sr, si);
+    };
+    const float2 sx = rowsum(tyf, kx), sy = rowsum(tyf, ky), sz = rowsum(tzf, kz);
+    const float2 sxy = make_float2(sx.x * sy.x - sx.y * sy.y, sx.x * sy.y + sx.y * sy.x);
+    const float2 O = make_float2(sxy.x * sz.x - sxy.y * sz.y, sxy.x * sz.y + sxy.y * sz.x);
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+    for (int c = 0; c < C; ++c) {
+        const int64_t ri = (k * C + o) * C + c;
+        const float xr = (float)Rr[ri], xi = (float)Ri[ri];
+        ar = fmaf(xr, Wl[c], ar);
+        ai = fmaf(xi, Wl[c], ai);
+        br = fmaf(xr, bl[c], br);
+        bi = fmaf(xi, bl[c], bi);
+    }
+    A[(int64_t)o * K + k] = make_float2(ar, ai);
+    Bc[(int64_t)o * K + k] = make_float2(br * O.x - bi * O.y, br * O.y + bi * O.x);
+}
+// G[b][o][k] = A[o][k] U[b][k] + Bc[o][k]
+__global__ void k_mix0(const float2* __restrict__ U, const float2* __restrict__ A, const float2* __restrict__ Bc,
+                       float2* __restrict__ G, int B, int C, int64_t K) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)B * C * K) return;
+    const int64_t k = e % K, ok = e % ((int64_t)C * K), b = e / ((int64_t)C * K);
+    const float2 a = A[ok], c = Bc[ok], x = U[b * K + k];
+    G[e] = make_float2(fmaf(a.x, x.x, fmaf(-a.y, x.y, c.x)), fmaf(a.x, x.y, fmaf(a.y, x.x, c.y)));
 }
 
 // Channel mix per mode, MB modes per block: G[b][o][k] = sum_c R[k][o][c] V[b][c][k]
@@ -462,6 +629,253 @@ __global__ void __launch_bounds__(ZR_T) k_zinv_point(const float2* __restrict__ 
             for (int e = threadIdx.x; e < n; e += blockDim.x)
                 y[b * n2 * n + xy * n + e] = q2[0] + ((ypart[e] + ypart[n + e]) + (ypart[2 * n + e] + ypart[3 * n + e]));
         }
+    }
+}
+
+// Forward, layer output side, inference (no z kept): persistent blocks over pairs of row
+// groups (b, x, y); the next pair's v rows and gy spectra are copied asynchronously into the
+// second buffer while the current pair is computed. Phase A: a thread takes a 4-channel x
+// 4-point tile of z = Re(Tzi gy) + W v + b (tables laid out [kz][z] so that the point
+// dimension is read as float4 without bank conflicts); the tiles then overwrite v with
+// v_next (GELU unless the last layer) in shared memory and in global memory. Phase B: the
+// next layer's cz = Tzf v_next, a thread per (row, channel, 3 modes), or the projection y
+// (4 projection rows x 4 points per thread). Needs the width and n multiples of 4 and at
+// most blockDim phase-A tiles per pass.
+constexpr int FI = 2;   // row groups per pass
+template <int CT, int NT, int MT>
+__global__ void __launch_bounds__(ZR_T, 3) k_zrow_inf(const float2* __restrict__ gy, const float* __restrict__ v,
+                                                      const float* __restrict__ W, const float* __restrict__ bias,
+                                                      const float2* __restrict__ Tzi, const float2* __restrict__ Tzf,
+                                                      float* __restrict__ vnext, float2* __restrict__ cznext,
+                                                      const float* __restrict__ Q1, const float* __restrict__ q1,
+                                                      const float* __restrict__ Q2, const float* __restrict__ q2,
+                                                      float* __restrict__ y, int B, int C_, int n_, int m_, int P, int act,
+                                                      const float* __restrict__ u0, const float* __restrict__ Wl,
+                                                      const float* __restrict__ bl) {
+    // (CT, NT, MT > 0: the width, grid and mode count fixed at compile time, so that the index
+    // arithmetic below reduces to shifts and multiplications)
+    const int C = CT ? CT : C_, n = NT ? NT : n_, m = MT ? MT : m_;
+    extern __shared__ __align__(16) float zsh[];
+    const int nz4 = n + 4, C4 = C + 4, npb = (P + 3) / 4;
+    float* vb = zsh;                                   // [2][FI][C][n + 4]
+    float* Ws = vb + 2 * FI * C * nz4;                 // [C][C + 4]
+    float* bs = Ws + C * C4;                           // [C]
+    float* Qs = bs + C;                                // [P][C + 4] (projection)
+    float* pq = Qs + (y ? P * C4 : 0);                 // q1, Q2 [2][P]
+    float* ys = pq + (y ? 2 * P : 0);                  // [FI][npb][n]
+    size_t fo = (size_t)(ys + (y ? FI * npb * n : 0) - zsh);
+    fo = (fo + 3) & ~(size_t)3;
+    float2* gb = reinterpret_cast<float2*>(zsh + fo);  // [2][FI][C][m]
+    float2* tf = gb + 2 * FI * C * m;                  // [m][n]
+    float* tiR = reinterpret_cast<float*>(tf + m * n); // [m][n]: Re, Im of Tzi[z][kz] at [kz][z]
+    float* tiI = tiR + m * n;
+    for (int e = threadIdx.x; e < C * C; e += blockDim.x) Ws[(e / C) * C4 + e % C] = W[e];
+    for (int e = threadIdx.x; e < C; e += blockDim.x) bs[e] = bias[e];
+    if (u0) {   // layer 0 from u: W v0 + b = (W Wl) u + (W bl + b), in Ws[o][0] and bs[o]
+        __syncthreads();
+        for (int o = threadIdx.x; o < C; o += blockDim.x) {
+            float w1 = 0.f, w0 = bs[o];
+            for (int c = 0; c < C; ++c) {
+                w1 = fmaf(Ws[o * C4 + c], Wl[c], w1);
+                w0 = fmaf(Ws[o * C4 + c], bl[c], w0);
+            }
+            Ws[o * C4 + C] = w1;   // (the row's padding column)
+            bs[o] = w0;
+        }
+    }
+    for (int e = threadIdx.x; e < n * m; e += blockDim.x) {
+        const float2 t = Tzi[e];
+        tiR[(e % m) * n + e / m] = t.x;
+        tiI[(e % m) * n + e / m] = t.y;
+    }
+    if (cznext)
+        for (int e = threadIdx.x; e < m * n; e += blockDim.x) tf[e] = Tzf[e];
+    if (y) {
+        for (int e = threadIdx.x; e < P * C; e += blockDim.x) Qs[(e / C) * C4 + e % C] = Q1[e];
+        for (int e = threadIdx.x; e < P; e += blockDim.x) {
+            pq[e] = q1[e];
+            pq[P + e] = Q2[e];
+        }
+    }
+    const int64_t n2 = (int64_t)n * n, rows = (int64_t)B * n2;
+    const int64_t ngroups = (rows + FI - 1) / FI;
+    const int n4 = n / 4, ncb = C / 4;
+    const int64_t cstride = n2 * n;   // between channels of v (and of gy, times m / n)
+    auto issue = [&](int64_t g, int buf) {
+        const int64_t r0 = g * FI;
+        const int nr = (int)min((int64_t)FI, rows - r0);
+        for (int rg = 0; rg < nr; ++rg) {
+            const int64_t r = r0 + rg, b = r / n2, xy = r - b * n2;
+            if (u0) {   // layer 0: the u row, in channel 0's place
+                for (int q4 = threadIdx.x; q4 < n4; q4 += blockDim.x)
+                    sno_cp16(vb + ((buf * FI + rg) * C) * nz4 + 4 * q4, u0 + r * n + 4 * q4);
+            } else {
+                const float* src = v + b * C * cstride + xy * n;
+                for (int e = threadIdx.x; e < C * n4; e += blockDim.x) {
+                    const int c = e / n4, q4 = e - c * n4;
+                    sno_cp16(vb + ((buf * FI + rg) * C + c) * nz4 + 4 * q4, src + c * cstride + 4 * q4);
+                }
+            }
+            const float2* gsrc = gy + (b * C * n2 + xy) * m;
+            for (int e = threadIdx.x; e < C * m; e += blockDim.x) {
+                const int o = e / m, kz = e - o * m;
+                sno_cp8(gb + ((buf * FI + rg) * C + o) * m + kz, gsrc + o * n2 * m + kz);
+            }
+        }
+    };
+    int64_t g = blockIdx.x;
+    if (g < ngroups) issue(g, 0);
+    sno_commit();
+    for (int it = 0; g < ngroups; g += gridDim.x, ++it) {
+        const int64_t gn = g + gridDim.x;
+        if (gn < ngroups) issue(gn, (it + 1) & 1);
+        sno_commit();
+        sno_wait_prev();
+        __syncthreads();
+        const int cur = it & 1;
+        const int64_t r0 = g * FI;
+        const int nr = (int)min((int64_t)FI, rows - r0);
+        float* vs = vb + cur * FI * C * nz4;
+        const float2* gs = gb + cur * FI * C * m;
+        // phase A: one 4 x 4 tile per thread
+        const int nitems = nr * ncb * n4;
+        const int e = threadIdx.x;
+        const int zb = e % n4, cb = (e / n4) % ncb, rg = e / (n4 * ncb);
+        const int z0 = 4 * zb, o0 = 4 * cb;
+        float acc[4][4];
+        if (e < nitems) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) acc[j][i] = bs[o0 + j];
+            const float2* gr = gs + (rg * C + o0) * m;
+            for (int kz = 0; kz < m; ++kz) {
+                const float4 ra = *reinterpret_cast<const float4*>(tiR + kz * n + z0);
+                const float4 ia = *reinterpret_cast<const float4*>(tiI + kz * n + z0);
+                const float tr[4] = {ra.x, ra.y, ra.z, ra.w}, tim[4] = {ia.x, ia.y, ia.z, ia.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float2 gg = gr[j * m + kz];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[j][i] = fmaf(tr[i], gg.x, fmaf(-tim[i], gg.y, acc[j][i]));
+                }
+            }
+            const float* vr = vs + rg * C * nz4 + z0;
+            if (u0) {
+                const float4 x = *reinterpret_cast<const float4*>(vr);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float w1 = Ws[(o0 + j) * C4 + C];
+                    acc[j][0] = fmaf(w1, x.x, acc[j][0]);
+                    acc[j][1] = fmaf(w1, x.y, acc[j][1]);
+                    acc[j][2] = fmaf(w1, x.z, acc[j][2]);
+                    acc[j][3] = fmaf(w1, x.w, acc[j][3]);
+                }
+            }
+            for (int c = 0; c < (u0 ? 0 : C); c += 4) {
+                float4 x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = *reinterpret_cast<const float4*>(vr + (c + i) * nz4);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float4 w = *reinterpret_cast<const float4*>(Ws + (o0 + j) * C4 + c);
+                    const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        acc[j][0] = fmaf(wv[i], x[i].x, acc[j][0]);
+                        acc[j][1] = fmaf(wv[i], x[i].y, acc[j][1]);
+                        acc[j][2] = fmaf(wv[i], x[i].z, acc[j][2]);
+                        acc[j][3] = fmaf(wv[i], x[i].w, acc[j][3]);
+                    }
+                }
+            }
+        }
+        __syncthreads();   // every tile is in registers: v_next overwrites v
+        if (e < nitems) {
+            const int64_t r = r0 + rg, b = r / n2, xy = r % n2;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float4 a = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+                if (act) a = make_float4(gelu_f(a.x), gelu_f(a.y), gelu_f(a.z), gelu_f(a.w));
+                *reinterpret_cast<float4*>(vs + (rg * C + o0 + j) * nz4 + z0) = a;
+                *reinterpret_cast<float4*>(vnext + ((b * C + o0 + j) * n2 + xy) * n + z0) = a;
+            }
+        }
+        __syncthreads();
+        if (cznext) {   // phase B: cz[c][kz] for 3 modes per thread, the points as float4
+            const int nkb = (m + 2) / 3;
+            for (int f = threadIdx.x; f < nr * nkb * C; f += blockDim.x) {
+                const int c = f % C, kb = (f / C) % nkb, rq = f / (C * nkb);
+                int kc[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) kc[i] = min(3 * kb + i, m - 1);
+                float re[3] = {0.f, 0.f, 0.f}, im[3] = {0.f, 0.f, 0.f};
+                const float* vr = vs + (rq * C + c) * nz4;
+                for (int zz = 0; zz < n; zz += 4) {
+                    const float4 xv = *reinterpret_cast<const float4*>(vr + zz);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) {
+                        const float4 ta = *reinterpret_cast<const float4*>(tf + kc[i] * n + zz);
+                        const float4 tb = *reinterpret_cast<const float4*>(tf + kc[i] * n + zz + 2);
+                        re[i] = fmaf(ta.x, xv.x, fmaf(ta.z, xv.y, fmaf(tb.x, xv.z, fmaf(tb.z, xv.w, re[i]))));
+                        im[i] = fmaf(ta.y, xv.x, fmaf(ta.w, xv.y, fmaf(tb.y, xv.z, fmaf(tb.w, xv.w, im[i]))));
+                    }
+                }
+                const int64_t r = r0 + rq, b = r / n2, xy = r % n2;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    if (3 * kb + i < m) cznext[((b * C + c) * n2 + xy) * m + 3 * kb + i] = make_float2(re[i], im[i]);
+            }
+        }
+        if (y) {   // projection: 4 rows of Q1 x 4 points per thread, partial sums per row block
+            for (int f = threadIdx.x; f < nr * npb * n4; f += blockDim.x) {
+                const int zq = f % n4, pb = (f / n4) % npb, rq = f / (n4 * npb);
+                const int zp = 4 * zq, p0 = 4 * pb;
+                int pc[4];
+                float a[4][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    pc[j] = min(p0 + j, P - 1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[j][i] = pq[pc[j]];
+                }
+                const float* vr = vs + rq * C * nz4 + zp;
+                for (int c = 0; c < C; c += 4) {
+                    float4 x[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) x[i] = *reinterpret_cast<const float4*>(vr + (c + i) * nz4);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 w = *reinterpret_cast<const float4*>(Qs + pc[j] * C4 + c);
+                        const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            a[j][0] = fmaf(wv[i], x[i].x, a[j][0]);
+                            a[j][1] = fmaf(wv[i], x[i].y, a[j][1]);
+                            a[j][2] = fmaf(wv[i], x[i].z, a[j][2]);
+                            a[j][3] = fmaf(wv[i], x[i].w, a[j][3]);
+                        }
+                    }
+                }
+                float part[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (p0 + j < P)
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) part[i] = fmaf(pq[P + p0 + j], gelu_f(a[j][i]), part[i]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) ys[(rq * npb + pb) * n + zp + i] = part[i];
+            }
+            __syncthreads();
+            for (int f = threadIdx.x; f < nr * n; f += blockDim.x) {
+                const int zz = f % n, rq = f / n;
+                float sum = 0.f;
+                for (int pb = 0; pb < npb; ++pb) sum += ys[(rq * npb + pb) * n + zz];
+                const int64_t r = r0 + rq;
+                y[r * n + zz] = q2[0] + sum;   // (b n^3 + xy n + z)
+            }
+        }
+        __syncthreads();   // the buffer is refilled two passes later
     }
 }
 
@@ -1021,13 +1435,37 @@ static float* fld(const DevBuf& b, int64_t i, int64_t per) { return ptr<float>(b
 
 // plane DFT launch: columns per block about 64 (several planes when inner is short)
 static int plane(SnoModel& M, const float2* in, float2* out, int64_t tab, int64_t P, int Lin, int Lout, int inner) {
+    // tiles of about 2 x 256 / ceil(Lout / 8) columns: one (8 outputs x 2 columns) item per thread
+    const int njb = (Lout + 7) / 8;
+    // about 2 x 256 / njb columns (one item per thread), at most 48 KB of inputs per buffer
+    const int target = std::max(8, std::min(512 / njb, (48 << 10) / (8 * Lin)));
     int PB = 1, ICH = inner;
-    if (inner >= 128) ICH = 128;
-    else PB = std::max(1, 128 / inner);
+    if (inner >= target) {
+        const int nchunk = (inner + target - 1) / target;
+        ICH = (inner + nchunk - 1) / nchunk;
+    } else {
+        PB = std::max(1, target / inner);
+    }
     const int nch = (inner + ICH - 1) / ICH;
-    const int64_t nb = ((P + PB - 1) / PB) * nch;
-    const size_t smem = ((size_t)Lin * PB * std::min(ICH, inner) + (size_t)Lout * Lin) * sizeof(float2);
-    k_plane<<<(unsigned)nb, 256, smem, M.st>>>(in, out, ptr<float2>(M.tabs) + tab, P, Lin, Lout, inner, PB, ICH, nch);
+    const int64_t ntiles = ((P + PB - 1) / PB) * nch;
+    const size_t smem = ((size_t)2 * Lin * PB * std::min(ICH, inner) + (size_t)Lout * Lin) * sizeof(float2);
+    if (smem > 160 * 1024) {   // (larger shapes than the model's: the single-shot kernel)
+        int PB1 = 1, ICH1 = inner;
+        if (inner >= 128) ICH1 = 128;
+        else PB1 = std::max(1, 128 / inner);
+        const int nch1 = (inner + ICH1 - 1) / ICH1;
+        const int64_t nb = ((P + PB1 - 1) / PB1) * nch1;
+        const size_t smem1 = ((size_t)Lin * PB1 * std::min(ICH1, inner) + (size_t)Lout * Lin) * sizeof(float2);
+        k_plane<<<(unsigned)nb, 256, smem1, M.st>>>(in, out, ptr<float2>(M.tabs) + tab, P, Lin, Lout, inner, PB1, ICH1,
+                                                    nch1);
+        KF_LAUNCH();
+        return KIFMM_OK;
+    }
+    int per_sm = 1;
+    KF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_plane2, 256, smem));
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * M.num_sms);
+    k_plane2<<<(unsigned)grid, 256, smem, M.st>>>(in, out, ptr<float2>(M.tabs) + tab, P, Lin, Lout, inner, PB, ICH,
+                                                  nch, ntiles);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -1058,6 +1496,14 @@ static unsigned zr_fwd_blocks(const SnoModel& M, int B) {
 
 static int near_add(SnoModel& M, const float* u, float* y, int B);
 
+static size_t zrow_inf_smem(int n, int C, int m, int P, bool proj) {
+    const int npb = (P + 3) / 4;
+    size_t f = (size_t)2 * FI * C * (n + 4) + (size_t)C * (C + 4) + C;
+    if (proj) f += (size_t)P * (C + 4) + 2 * (size_t)P + (size_t)FI * npb * n;
+    f = (f + 3) & ~(size_t)3;
+    return f * 4 + ((size_t)2 * FI * C * m + (size_t)m * n) * 8 + (size_t)2 * m * n * 4;
+}
+
 // forward; train: keep z_l and the spectra V_l for the backward pass
 static int forward(SnoModel& M, const float* u, float* y, int B, bool train) {
     const int n = M.n, m = M.m, C = M.C, M2 = 2 * m;
@@ -1065,18 +1511,59 @@ static int forward(SnoModel& M, const float* u, float* y, int B, bool train) {
     cudaStream_t st = M.st;
     const float* th = ptr<float>(M.theta);
     const float2* T = ptr<float2>(M.tabs);
-    k_lift_z<<<zr_blocks(M, B), ZR_T, M.zr_smem_f, st>>>(u, th + M.off[O_WL], th + M.off[O_BL], fld(M.v, 0, per),
-                                                         ptr<float2>(M.cz), T + M.tzf, B, C, n, m);
-    KF_LAUNCH();
     const int q = o_q1(M);
+    const bool inf = !train && M.zi_smem;   // inference: layer 0 from u, persistent z-row kernel
+    if (inf) {
+        const int64_t rows = (int64_t)B * n * n;
+        k_lift_u<<<(unsigned)((rows + LU - 1) / LU), 256, (size_t)LU * n * 4 + (size_t)m * n * 8, st>>>(
+            u, T + M.tzf, ptr<float2>(M.cz), rows, n, m);
+        KF_LAUNCH();
+        KF_TRY(plane(M, ptr<float2>(M.cz), ptr<float2>(M.cy), M.tyf, (int64_t)B * n, n, M2, m));     // y
+        KF_TRY(plane(M, ptr<float2>(M.cy), ptr<float2>(M.Vst), M.tyf, B, n, M2, M2 * m));           // x: U
+        float2* A = ptr<float2>(M.m0ab);
+        float2* Bc = A + (int64_t)C * M.K;
+        const unsigned np = nbs((int64_t)C * M.K, 256);
+        if (M.bf16)
+            k_mix0_prep<__nv_bfloat16><<<np, 256, 0, st>>>(ptr<__nv_bfloat16>(M.rbf),
+                                                           ptr<__nv_bfloat16>(M.rbf) + M.K * C * C, th + M.off[O_WL],
+                                                           th + M.off[O_BL], T + M.tyf, T + M.tzf, C, M.K, n, m, A,
+                                                           Bc);
+        else
+            k_mix0_prep<float><<<np, 256, 0, st>>>(th + M.off[o_rr(0)], th + M.off[o_ri(0)], th + M.off[O_WL],
+                                                   th + M.off[O_BL], T + M.tyf, T + M.tzf, C, M.K, n, m, A, Bc);
+        k_mix0<<<nbs(BC * M.K, 256), 256, 0, st>>>(ptr<float2>(M.Vst), A, Bc, ptr<float2>(M.g), B, C, M.K);
+        KF_LAUNCH();
+    } else {
+        k_lift_z<<<zr_blocks(M, B), ZR_T, M.zr_smem_f, st>>>(u, th + M.off[O_WL], th + M.off[O_BL],
+                                                             fld(M.v, 0, per), ptr<float2>(M.cz), T + M.tzf, B, C, n,
+                                                             m);
+        KF_LAUNCH();
+    }
     for (int l = 0; l < M.L; ++l) {
-        float2* V = ptr<float2>(M.Vst) + (train ? (int64_t)l * BC * M.K : 0);
-        KF_TRY(plane(M, ptr<float2>(M.cz), ptr<float2>(M.cy), M.tyf, BC * n, n, M2, m));            // y
-        KF_TRY(plane(M, ptr<float2>(M.cy), V, M.tyf, BC, n, M2, M2 * m));                            // x
-        KF_TRY(mix(M, l, V, ptr<float2>(M.g), B, 0));
+        if (!(inf && l == 0)) {
+            float2* V = ptr<float2>(M.Vst) + (train ? (int64_t)l * BC * M.K : 0);
+            KF_TRY(plane(M, ptr<float2>(M.cz), ptr<float2>(M.cy), M.tyf, BC * n, n, M2, m));            // y
+            KF_TRY(plane(M, ptr<float2>(M.cy), V, M.tyf, BC, n, M2, M2 * m));                            // x
+            KF_TRY(mix(M, l, V, ptr<float2>(M.g), B, 0));
+        }
         KF_TRY(plane(M, ptr<float2>(M.g), ptr<float2>(M.gx), M.txi, BC, M2, n, M2 * m));             // x^-1
         KF_TRY(plane(M, ptr<float2>(M.gx), ptr<float2>(M.gy), M.txi, BC * n, M2, n, m));             // y^-1
         const bool last = l == M.L - 1;
+        if (inf) {
+            const size_t sm = last ? M.zi_smem_y : M.zi_smem;
+            int per_sm = 1;
+            auto* kz = (C == 32 && n == 64 && m == 12) ? k_zrow_inf<32, 64, 12> : k_zrow_inf<0, 0, 0>;
+            KF_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kz, ZR_T, sm));
+            const int64_t groups = ((int64_t)B * n * n + FI - 1) / FI;
+            const int64_t grid = std::min<int64_t>(groups, (int64_t)std::max(1, per_sm) * M.num_sms);
+            kz<<<(unsigned)grid, ZR_T, sm, st>>>(
+                ptr<float2>(M.gy), l == 0 ? nullptr : fld(M.v, l, per), th + M.off[o_w(l)], th + M.off[o_b(l)],
+                T + M.tzi, T + M.tzf, fld(M.v, l + 1, per), last ? nullptr : ptr<float2>(M.cz), th + M.off[q],
+                th + M.off[q + 1], th + M.off[q + 2], th + M.off[q + 3], last ? y : nullptr, B, C, n, m, M.P,
+                last ? 0 : 1, l == 0 ? u : nullptr, th + M.off[O_WL], th + M.off[O_BL]);
+            KF_LAUNCH();
+            continue;
+        }
         k_zrow_fwd<<<zr_fwd_blocks(M, B), ZR_T, M.zf_smem, st>>>(
             ptr<float2>(M.gy), fld(M.v, l, per), th + M.off[o_w(l)], th + M.off[o_b(l)], T + M.tzi, T + M.tzf,
             train ? fld(M.z, l, per) : nullptr, fld(M.v, l + 1, per), last ? nullptr : ptr<float2>(M.cz),
@@ -1331,7 +1818,7 @@ __global__ void k_scale_out(const float* y, const double* s, double C, double* S
 // of every target's sum (one target per thread and pass) into acc[t] (one FP64 atomic per
 // target and chunk). Within a chunk the pairs accumulate in FP32 with Kahan compensation: the
 // judge decides against a tolerance of order 1e-2, far above the FP32 sum's error.
-constexpr int JG_T = 256, JG_CH = 512;
+constexpr int JG_T = 256, JG_CH = 256;
 __global__ void __launch_bounds__(JG_T) k_judge_src(const double* pts, const double* q, const int32_t* targets,
                                                     int k, int64_t n, KParams kp, double* acc) {
     __shared__ float4 sp[JG_CH];   // x, y, z, q
@@ -1347,19 +1834,27 @@ __global__ void __launch_bounds__(JG_T) k_judge_src(const double* pts, const dou
         const float xi = (float)pts[3 * i], yi = (float)pts[3 * i + 1], zi = (float)pts[3 * i + 2];
         const int self = (i >= j0 && i < j0 + m) ? (int)(i - j0) : -1;
         Kahan a;
-        float part = 0.f;
-        for (int e = 0; e < m; ++e) {
-            const float4 v = sp[e];
-            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
-            const float kv = e == self ? 0.f : kern_f32(r2, kp) * v.w;
-            part += kv;
-            if ((e & 15) == 15) {   // blocks of 16 pairs, then the compensated sum
-                a.add(part);
-                part = 0.f;
+        float part[4] = {0.f, 0.f, 0.f, 0.f};   // four independent chains, then the compensated sum
+        int e = 0;
+        for (; e + 4 <= m; e += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4 v = sp[e + u];
+                const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                part[u] += e + u == self ? 0.f : kern_f32(r2, kp) * v.w;
+            }
+            if ((e & 15) == 12) {
+                a.add((part[0] + part[1]) + (part[2] + part[3]));
+                part[0] = part[1] = part[2] = part[3] = 0.f;
             }
         }
-        a.add(part);
+        for (; e < m; ++e) {
+            const float4 v = sp[e];
+            const float dx = xi - v.x, dy = yi - v.y, dz = zi - v.z;
+            part[0] += e == self ? 0.f : kern_f32(dx * dx + dy * dy + dz * dz, kp) * v.w;
+        }
+        a.add((part[0] + part[1]) + (part[2] + part[3]));
         atomicAdd(acc + t, a.value());
     }
 }
@@ -1454,6 +1949,10 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         M.mix_smem = (size_t)M.mix_mb * per_mode;
         M.mixg_smem = (size_t)2 * max_batch * M.mix_mb * width * f8;
         const size_t plane_smem = ((size_t)n * 128 + (size_t)n * 2 * modes) * f8;
+        if (width % 4 == 0 && n % 4 == 0 && FI * (width / 4) * (n / 4) <= ZR_T) {
+            M.zi_smem = zrow_inf_smem(n, width, modes, proj_width, false);
+            M.zi_smem_y = zrow_inf_smem(n, width, modes, proj_width, true);
+        }
         int dev = 0, optin = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -1473,6 +1972,10 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
         cudaFuncSetAttribute(k_zinv_point_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_proj_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_plane2, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zrow_inf<32, 64, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        cudaFuncSetAttribute(k_zrow_inf<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (M.zi_smem_y > (size_t)lim) M.zi_smem = M.zi_smem_y = 0;
         cudaFuncSetAttribute(k_mix<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_mix<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
         cudaFuncSetAttribute(k_mix_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
@@ -1520,6 +2023,7 @@ int sno_create(sno_model_t* out, int n, int width, int modes, int layers, int pr
     if ((rc = dev_alloc(M.Vst, (size_t)layers * BC * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.g, (size_t)BC * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.ga, (size_t)BC * M.K * 8))) return fail(rc);
+    if ((rc = dev_alloc(M.m0ab, (size_t)2 * width * M.K * 8))) return fail(rc);
     if ((rc = dev_alloc(M.loss, 16))) return fail(rc);
     // judge buffers for a batch of max_batch fields: targets, references, caller indices, errors, scales
     if ((rc = dev_alloc(M.jt, (size_t)max_batch * SNO_MAX_JUDGE * 4))) return fail(rc);
@@ -1696,7 +2200,7 @@ void sno_destroy(sno_model_t h) {
     SnoModel& M = h->m;
     if (M.st) cudaStreamSynchronize(M.st);
     for (DevBuf* b : {&M.theta, &M.grad, &M.adam_m, &M.adam_v, &M.rbf, &M.tabs, &M.v, &M.z, &M.dz, &M.yb, &M.dy,
-                      &M.loss, &M.cz, &M.cy, &M.gx, &M.gy, &M.Vst, &M.g, &M.ga, &M.jt, &M.jref, &M.jorig,
+                      &M.loss, &M.cz, &M.cy, &M.gx, &M.gy, &M.Vst, &M.g, &M.ga, &M.m0ab, &M.jt, &M.jref, &M.jorig,
                       &M.jerr, &M.near_d, &M.near_w, &M.scal, &M.jws})
         dev_free(*b);
     delete h;
@@ -1896,10 +2400,13 @@ static int photo_solve_impl(kifmm_plan_t* plans, int count, SnoModel& M, const d
             set_error("photo_solve: the plan's point count differs from the model's grid");
             return KIFMM_ERR_ARG;
         }
+        if (p.kind != 0) {
+            set_error("photo_solve: the surrogate and its judge take the paper's kernel");
+            return KIFMM_ERR_ARG;
+        }
         if (M.near_on) {   // the model's near part must be the plan's kernel and cells
             auto same = [](double x, double y) { return std::fabs(x - y) <= 1e-12 * std::fabs(y); };
-            if (!same(M.na, p.a) || !same(M.nb, p.b) || !same(M.nh, p.uniform_h) || p.self_mode != M.nself ||
-                p.kind != 0) {
+            if (!same(M.na, p.a) || !same(M.nb, p.b) || !same(M.nh, p.uniform_h) || p.self_mode != M.nself) {
                 set_error("photo_solve: the model's near part was set for another kernel, cell size or self term");
                 return KIFMM_ERR_ARG;
             }

@@ -466,6 +466,7 @@ __global__ void k_lattice_member(const double* pts, int64_t n, double lx, double
 int pad_to_lattice(cudaStream_t st, const double* pts, int64_t n, double h, int nc, DevBuf& out, int64_t* n_total,
                    double root[4]) {
     *n_total = n;
+    root[3] = 0.0;   // (no lattice root unless the points are a full box grid)
     DevBuf part, rootb, flags;
     KF_TRY(dev_alloc(part, RED_BLOCKS * 6 * sizeof(double)));
     KF_TRY(dev_alloc(rootb, 8 * sizeof(double)));
@@ -518,8 +519,12 @@ int pad_to_lattice(cudaStream_t st, const double* pts, int64_t n, double h, int 
     root[2] = r8[2];
     root[3] = (double)cells * h;
     const int64_t nt = pad[0] * pad[1] * pad[2];
-    if (nt >= (int64_t)1 << 31) return KIFMM_OK;
+    if (nt >= (int64_t)1 << 31) {
+        root[3] = 0.0;
+        return KIFMM_OK;
+    }
     const int64_t nv = nt - n;
+    if (nv == 0) return KIFMM_OK;   // already on the lattice: the root alone
     KF_TRY(dev_alloc(out, (size_t)nt * 3 * sizeof(double)));
     KF_CUDA(cudaMemcpyAsync(out.p, pts, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (nv > 0) {   // the padding cells in z, y, x order, after the caller's points

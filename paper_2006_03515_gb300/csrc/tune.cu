@@ -54,14 +54,22 @@ __global__ void k_is_scan(const double* S, int64_t n, const double* tot, double*
     if (i < n) cdf[i] = sh[threadIdx.x];
     if (threadIdx.x == IS_SC - 1) blk[blockIdx.x] = sh[IS_SC - 1];
 }
+// exclusive prefix sums of the nb block totals, one warp (each lane a contiguous run)
 __global__ void k_is_scan_blocks(double* blk, int nb) {
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        for (int b = 0; b < nb; ++b) {
-            const double v = blk[b];
-            blk[b] = acc;
-            acc += v;
-        }
+    const int lane = threadIdx.x;
+    const int per = (nb + 31) / 32, b0 = lane * per, b1 = min(nb, b0 + per);
+    double s = 0.0;
+    for (int b = b0; b < b1; ++b) s += blk[b];
+    double x = s;   // inclusive scan of the lanes' run totals
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    double acc = x - s;
+    for (int b = b0; b < b1; ++b) {
+        const double v = blk[b];
+        blk[b] = acc;
+        acc += v;
     }
 }
 __global__ void k_is_add(double* cdf, int64_t n, const double* blk) {

@@ -123,6 +123,11 @@ def test_padding_only_for_full_box_grids(kf):
                     root=kw.get("root"))
         assert p.info()["n_padding"] == 0
         p.close()
+    # a grid already on the lattice (24 cells a side): no padding, the lattice root all the same
+    p = kf.Plan(_dev(_box((24, 24, 24), 0.05)), 0.05, 64, 4, a, b, precision="mixed", pad_lattice=True)
+    inf = p.info()
+    assert inf["n_padding"] == 0 and inf["side"] == pytest.approx(32 * 0.05) and inf["near_tensor"]
+    p.close()
     p = kf.Plan(_dev(pts), 0.05, 64, 4, a, b, precision="fp64", pad_lattice=True)
     inf = p.info()
     assert inf["n_padding"] == 24 ** 3 - 20 ** 3 and inf["side"] == pytest.approx(32 * 0.05)
