@@ -103,12 +103,13 @@ __global__ void parent_tab(const int32_t* parent, const int32_t* anchor, const i
 }
 
 // Mc [8][S][R] -> [8][R][R] (rows >= S zero), the square tables of the tensor-core kernel
-__global__ void pad_mc(const double* Mc, int S, int R, double* out) {
+// Mc [8][S][R] into square tables [8][Mt][Mt] (zero rows i >= S and columns j >= R)
+__global__ void pad_mc(const double* Mc, int S, int R, int Mt, double* out) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 8LL * R * R) return;
-    const int64_t o = e / ((int64_t)R * R);
-    const int i = (int)((e / R) % R), j = (int)(e % R);
-    out[e] = i < S ? Mc[(o * S + i) * R + j] : 0.0;
+    if (e >= 8LL * Mt * Mt) return;
+    const int64_t o = e / ((int64_t)Mt * Mt);
+    const int i = (int)((e / Mt) % Mt), j = (int)(e % Mt);
+    out[e] = (i < S && j < R) ? Mc[(o * S + i) * R + j] : 0.0;
 }
 
 // out[box][j] = (double) in[box][j], j < ncol, for the listed boxes (in rows of R floats)
@@ -426,15 +427,22 @@ int build_eval_data(Plan& p) {
             }
         }
         // M2M translations likewise: per parent tile the 8 child octants as slots (the tree's child
-        // table is the source table), Mc padded to square tables, the result staged in FP32 and
-        // copied into the parents' check rows (KIFMM_M2M=simt keeps the SIMT apply). Surface form
-        // with S <= R only (the check rows must fit the square tables); the Chebyshev translations
-        // (K = p^3 = 512 at p = 8) would take 96 truncating accumulations per slot, a bias that
-        // compounds level by level up the tree.
+        // table is the source table), Mc padded to square tables of Mt = max(S, R) rounded to 32,
+        // the result staged in FP32 and copied into the parents' check rows (KIFMM_M2M=simt keeps
+        // the SIMT apply). By default only when S <= R: with more check points than coefficients
+        // (S > R) the children's c pass through FP16 hi / lo rows padded to Mt, whose 22 bits
+        // relative to each row's largest value cost 1.5e-7 of the mixed form's error at 7.6 Torr
+        // (1.03e-6 against 8.9e-7 with the FP32 apply), beyond the 1e-6 gate; KIFMM_M2M=tc takes
+        // the tensor cores there too. Surface form only: the Chebyshev translations (K = p^3 = 512
+        // at p = 8) would take 96 truncating accumulations per slot, a bias that compounds level by
+        // level up the tree.
         const char* m2m = std::getenv("KIFMM_M2M");
-        p.m2m_tc = !(m2m && std::string(m2m) == "simt") && t.nlevels > 3 && !p.cheb && S <= p.R;   // square tables
+        p.m2m_R = (std::max(S, p.R) + 31) / 32 * 32;
+        const bool m2m_force = m2m && std::string(m2m) == "tc";
+        p.m2m_tc = !(m2m && std::string(m2m) == "simt") && t.nlevels > 3 && !p.cheb && m2l_tc_supported(p.m2m_R) &&
+                   (S <= p.R || m2m_force);
         if (p.m2m_tc) {
-            const int R = p.R;
+            const int R = p.m2m_R;
             std::vector<int4> mt;
             DevBuf pad;
             KF_TRY(dev_alloc(pad, (size_t)8 * R * R * 8));
@@ -445,7 +453,7 @@ int build_eval_data(Plan& p) {
                 p.m2m_count[l] = (np + 127) / 128;
                 for (int k = 0; k < p.m2m_count[l]; ++k) mt.push_back(make_int4(l, 128 * k, std::min(128, np - 128 * k), 0));
                 if (np == 0) continue;
-                pad_mc<<<nbk(8LL * R * R, 256), 256, 0, st>>>(ptr<double>(op.Mc), S, R, ptr<double>(pad));
+                pad_mc<<<nbk(8LL * R * R, 256), 256, 0, st>>>(ptr<double>(op.Mc), S, p.R, R, ptr<double>(pad));
                 KF_LAUNCH();
                 KF_TRY(dev_alloc(op.Mhi, (size_t)m2l_tc_table_elems(R, 8) * 2));
                 KF_TRY(dev_alloc(op.Mlo, (size_t)m2l_tc_table_elems(R, 8) * 2));
@@ -460,6 +468,10 @@ int build_eval_data(Plan& p) {
             KF_TRY(dev_alloc(p.m2m_tiles, std::max<size_t>(mt.size(), 1) * sizeof(int4)));
             KF_TRY(dev_alloc(p.m2m_slots, ms.size() * 4));
             KF_TRY(dev_alloc(p.stage32, (size_t)nb * R * 4));
+            if (R > p.R) {
+                KF_TRY(dev_alloc(p.m2m_hi, (size_t)nb * R * 2));
+                KF_TRY(dev_alloc(p.m2m_lo, (size_t)nb * R * 2));
+            }
             if (!mt.empty())
                 KF_CUDA(cudaMemcpyAsync(p.m2m_tiles.p, mt.data(), mt.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
             KF_CUDA(cudaMemcpyAsync(p.m2m_slots.p, ms.data(), ms.size() * 4, cudaMemcpyHostToDevice, st));
@@ -641,6 +653,7 @@ __global__ void __launch_bounds__(P2M_T) k_p2m(EvalView E, const int32_t* boxes,
 // base + c. Tile TM = 16*RM rows x TN = 16*CN boxes, k-chunks of 16; each thread RM x CN.
 // Arithmetic in T; the input is read as TI and the output stored as TO.
 constexpr int AP_TK = 16;
+constexpr int AP_NT = 8;   // terms whose source indices a block stages in shared memory
 // With zoff != NULL the launch is a batch over blockIdx.z: batch z uses Op + z * zstride and
 // the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch). With
 // zoff == NULL and gridDim.z > 1 the work items (term, k-chunk), taken term-major, are split
@@ -670,8 +683,17 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
     }
     __shared__ T As[AP_TK][TM + 1];
     __shared__ T Bs[AP_TK][TN + 1];
+    __shared__ int32_t sidx[AP_NT][TN];   // the block's source boxes per term (nterm <= AP_NT)
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int row0 = blockIdx.y * TM, col0 = blockIdx.x * TN;
+    const bool staged = src && nterm <= AP_NT;
+    if (staged) {   // one dependent global load per gathered value instead of two
+        for (int e = tid; e < nterm * TN; e += 256) {
+            const int t = e / TN, col = col0 + e % TN;
+            sidx[t][e % TN] = col < count ? src[(int64_t)t * count + col] : -1;
+        }
+        __syncthreads();
+    }
     T acc[RM][CN] = {};
     T ra[RM], rb[CN];
     auto load = [&](int it) {
@@ -689,7 +711,8 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
             const int col = col0 + e / AP_TK, k = k0 + e % AP_TK;
             T v = T(0);
             if (col < count && k < Ki) {
-                const int64_t b = src ? (int64_t)src[(int64_t)t * count + col] : base + col;
+                const int64_t b = staged ? (int64_t)sidx[t][col - col0]
+                                  : src ? (int64_t)src[(int64_t)t * count + col] : base + col;
                 if (b >= 0) v = (T)in[b * ldi + k];
             }
             rb[j] = v;
@@ -1564,19 +1587,22 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             // tensor cores: the children's c split FP16 x 3 (the M2L operand buffers, rewritten
             // before M2L), 8 octant slots per parent tile, staged in FP32, copied to the check rows
             const int64_t lo = t.level_start[l + 1], cnt = t.level_start[l + 2] - lo;
-            KF_TRY(m2l_tc_split(st, cu + lo * R, cnt, R, static_cast<char*>(p.chi.p) + lo * R * 2,
-                                static_cast<char*>(p.clo.p) + lo * R * 2, ptr<int>(p.cexp) + lo));
+            const int Mt = p.m2m_R;
+            void* hi = Mt > R ? p.m2m_hi.p : p.chi.p;
+            void* lo16 = Mt > R ? p.m2m_lo.p : p.clo.p;
+            KF_TRY(m2l_tc_split_pad(st, cu + lo * R, cnt, R, Mt, static_cast<char*>(hi) + lo * Mt * 2,
+                                    static_cast<char*>(lo16) + lo * Mt * 2, ptr<int>(p.cexp) + lo));
             ++nl;
             M2LTables tabs{};
             tabs.hi[l] = p.ops[l].Mhi.p;
             tabs.lo[l] = p.ops[l].Mlo.p;
             tabs.sT[l] = p.ops[l].m2m_sT;
-            RUN(launch_tc_translate(st, tabs, R, ptr<int4>(p.m2m_tiles) + p.m2m_first[l], p.m2m_count[l],
+            RUN(launch_tc_translate(st, tabs, Mt, ptr<int4>(p.m2m_tiles) + p.m2m_first[l], p.m2m_count[l],
                                     ptr<int32_t>(LL.parents), ptr<int32_t>(t.child), 8,
-                                    ptr<int32_t>(p.m2m_slots) + (int64_t)p.m2m_first[l] * kSlotStride, p.chi.p,
-                                    p.clo.p, ptr<int>(p.cexp), ptr<float>(p.stage32), 0, ptr<int>(p.err)));
+                                    ptr<int32_t>(p.m2m_slots) + (int64_t)p.m2m_first[l] * kSlotStride, hi, lo16,
+                                    ptr<int>(p.cexp), ptr<float>(p.stage32), 0, ptr<int>(p.err)));
             rows_f2d<<<nbk((int64_t)LL.n_par * S, 256), 256, 0, st>>>(ptr<int32_t>(LL.parents), LL.n_par,
-                                                                     ptr<float>(p.stage32), R,
+                                                                     ptr<float>(p.stage32), Mt,
                                                                      p.cheb ? cu : ptr<double>(p.chk),
                                                                      p.cheb ? R : S, S);
             KF_LAUNCH();
@@ -1584,7 +1610,9 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         } else if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
-            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms + tiles - 1) / tiles));
+            // split the terms so that the launch is one whole wave (4 blocks of 256 per SM at 64
+            // registers): a partial second wave costs a wave of latency
+            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms) / tiles));
             // (Chebyshev: the parents' node weights W^P = sum_o M_o W^{C_o}, straight into c)
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,

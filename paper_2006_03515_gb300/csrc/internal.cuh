@@ -193,7 +193,9 @@ struct Plan {
     DevBuf ptab, l2l_slots;      // i32[nb][8] parent at the box's octant slot; per-tile L2L slot lists
     int tc_first[kMaxLevel + 1] = {0}, tc_count[kMaxLevel + 1] = {0};   // M2L tiles of each level
     bool m2m_tc = false;         // M2M translations through the same kernel (mixed form)
-    DevBuf m2m_tiles, m2m_slots, stage32;   // parent tiles per level, their 8 slots, FP32 staging [nb][R]
+    DevBuf m2m_tiles, m2m_slots, stage32;   // parent tiles per level, their 8 slots, FP32 staging [nb][m2m_R]
+    int m2m_R = 0;                          // square table size of the M2M translations: max(S, R) rounded to 32
+    DevBuf m2m_hi, m2m_lo;                  // children's c split FP16 x 2 in rows of m2m_R (when m2m_R > R)
     int m2m_first[kMaxLevel + 1] = {0}, m2m_count[kMaxLevel + 1] = {0};
     int num_sms = 1;             // multiprocessors of the plan's device (grid sizing)
     bool p2p_series = true;      // some near pair is closer than 0.5 / (b - a) (mixed P2P)
@@ -266,6 +268,8 @@ int64_t m2l_tc_table_elems(int R, int nslots = kOffsetSlots);   // FP16 elements
 int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo, int* sT_out,
                    int nslots = kOffsetSlots);
 int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp);
+// the same with output rows of ldo >= R halves (columns R..ldo-1 zero)
+int m2l_tc_split_pad(cudaStream_t st, const double* c, int64_t nb, int R, int ldo, void* chi, void* clo, int* cexp);
 int m2l_tc_split_f32(cudaStream_t st, const float* c, int64_t nb, int R, void* chi, void* clo, int* cexp);
 struct M2LTables {                 // per-level FP16 hi/lo M2L tables for the tensor-core kernel
     const void* hi[kMaxLevel + 1];

@@ -78,7 +78,7 @@ __global__ void k_swizzle_T(const double* T, int R, int NK, int nslots, int sT, 
 // upward coefficients (FP64, rows of R) -> their FP32 values scaled by 2^{e_b} per box (largest
 // magnitude near 2^14), split into FP16 hi/lo; one warp per box
 template <class TIN>
-__global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp) {
+__global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp, int ldo) {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
@@ -92,11 +92,11 @@ __global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* 
         frexpf(m, &ex);             // m = f 2^ex, f in [0.5, 1)
         e = TC_HI_EXP + 1 - ex;     // m 2^e in [2^13, 2^14)
     }
-    for (int k = lane; k < R; k += 32) {
-        const float x = ldexpf((float)row[k], e);
+    for (int k = lane; k < ldo; k += 32) {   // (output rows of ldo, zero beyond R)
+        const float x = k < R ? ldexpf((float)row[k], e) : 0.f;
         const __half h = __float2half_rn(x);
-        chi[b * R + k] = h;
-        clo[b * R + k] = __float2half_rn(x - __half2float(h));
+        chi[b * ldo + k] = h;
+        clo[b * ldo + k] = __float2half_rn(x - __half2float(h));
     }
     if (lane == 0) cexp[b] = e;
 }
@@ -402,7 +402,15 @@ int m2l_tc_prepare(cudaStream_t st, const double* T, int R, void* Thi, void* Tlo
 int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi, void* clo, int* cexp) {
     if (nb <= 0) return KIFMM_OK;
     k_split_c<double><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
-                                                                         reinterpret_cast<__half*>(clo), cexp);
+                                                                         reinterpret_cast<__half*>(clo), cexp, R);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+int m2l_tc_split_pad(cudaStream_t st, const double* c, int64_t nb, int R, int ldo, void* chi, void* clo, int* cexp) {
+    if (nb <= 0) return KIFMM_OK;
+    k_split_c<double><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
+                                                                         reinterpret_cast<__half*>(clo), cexp, ldo);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -410,7 +418,7 @@ int m2l_tc_split(cudaStream_t st, const double* c, int64_t nb, int R, void* chi,
 int m2l_tc_split_f32(cudaStream_t st, const float* c, int64_t nb, int R, void* chi, void* clo, int* cexp) {
     if (nb <= 0) return KIFMM_OK;
     k_split_c<float><<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(c, nb, R, reinterpret_cast<__half*>(chi),
-                                                                        reinterpret_cast<__half*>(clo), cexp);
+                                                                        reinterpret_cast<__half*>(clo), cexp, R);
     KF_LAUNCH();
     return KIFMM_OK;
 }

@@ -12,15 +12,18 @@
 // in FP64:  c[b][r] = 2^{e_b + e_r} sum_L 2^{-6L} P_L[b][r].
 // The result equals the FP64 product to the rounding of an FP64 GEMM.
 //
-// One CTA takes 128 boxes (MMA M) and 48 operator rows (MMA N): it keeps all 9 operator
-// slices of its rows in shared memory (loaded once), streams the 9 box slices chunk by chunk
-// (K-chunks of 64 FP16, 128-byte swizzled images written by the slicing kernel), and for
-// box slice i issues the MMAs against operator slices j = 1..10-i into the accumulator of
-// level i + j (9 accumulators of 48 columns in tensor memory). Roles: warp 8 lane 0 moves the
-// images with bulk copies, warp 9 lane 0 issues the MMAs, warps 0-7 drain the accumulators.
+// One CTA takes 48 operator rows (MMA N) and, persistently, the box tiles of 128 boxes (MMA M)
+// bt, bt + gridDim.x, ... (one wave of CTAs): it keeps all 9 operator slices of its rows in
+// shared memory (loaded once), streams the 9 box slices of each tile chunk by chunk (K-chunks
+// of 64 FP16, 128-byte swizzled images written by the slicing kernel) through a ring of
+// stages, and for box slice i issues the MMAs against operator slices j = 1..10-i into the
+// accumulator of level i + j (9 accumulators of 48 columns in tensor memory). Roles: warp 8
+// lane 0 moves the images with bulk copies, warp 9 lane 0 issues the MMAs, warps 0-7 drain
+// the accumulators and hand them back (a "drained" barrier) before the next tile's MMAs.
 // Every wait is bounded; a timeout raises the abort flag and an error code.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
@@ -34,13 +37,14 @@ constexpr int OZ_W = 6;          // bits per slice
 constexpr int OZ_N = 48;         // operator rows per CTA (MMA N)
 constexpr int OZ_M = 128;        // boxes per CTA (MMA M)
 constexpr int OZ_KC = 64;        // FP16 per K-chunk (one 128-byte swizzle row)
-constexpr int OZ_NS = 3;         // box-slice stages
+constexpr int OZ_NS = 3;         // box-slice stages (K of one chunk: 8, the operator image leaving room)
+__host__ __device__ constexpr int oz_stages(int nk) { return nk == 1 ? 8 : OZ_NS; }
 constexpr int OZ_THREADS = 320;  // warps 0-7 epilogue, 8 producer, 9 MMA
 
 __host__ __device__ inline int oz_kp(int S) { return (S + 31) / 32 * 32; }   // K padded to a multiple of 32
 __host__ __device__ inline int oz_nk(int S) { return (oz_kp(S) + OZ_KC - 1) / OZ_KC; }
 static inline size_t oz_b_bytes(int S) { return (size_t)OZ_S * oz_nk(S) * OZ_N * 128; }   // per row tile
-static inline size_t oz_smem(int S) { return 1024 + oz_b_bytes(S) + (size_t)OZ_NS * OZ_M * 128; }
+static inline size_t oz_smem(int S) { return 1024 + oz_b_bytes(S) + (size_t)oz_stages(oz_nk(S)) * OZ_M * 128; }
 
 int pinv_oz_supported(int S) { return oz_smem(S) <= 227 * 1024 ? 1 : 0; }
 
@@ -152,7 +156,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     constexpr uint32_t OPB = OZ_S * NK * OPCH;          // all operator slices of the row tile
     constexpr uint32_t NCOLS = 512;                     // 9 accumulators x 48 columns
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    __shared__ uint64_t full[OZ_NS], empty[OZ_NS], opfull, done;
+    constexpr int NS = oz_stages(NK);
+    __shared__ uint64_t full[NS], empty[NS], opfull, done, drained;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ int ers[OZ_N];
@@ -172,12 +177,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
     }
     if (tid == 0) {
         abort_flag = 0;
-        for (int s = 0; s < OZ_NS; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
         }
         mbar_init(smem_u32(&opfull), 1);
         mbar_init(smem_u32(&done), 1);
+        mbar_init(smem_u32(&drained), 8);   // one arrival per epilogue warp and box tile
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -187,22 +193,30 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 
     if (warp == 8) {
         // ---------------- producer ----------------
+        // persistent: the operator slices once, then the box slices of the CTA's box tiles
+        // bt, bt + gridDim.x, ... through the stage ring (g counts stages over the tiles)
         if (lane == 0) {
             const uint32_t ob = smem_u32(&opfull);
             mbar_expect(ob, OPB);
             const unsigned char* src = reinterpret_cast<const unsigned char*>(opimg) + (int64_t)rt * OPB;
             for (int c = 0; c < OZ_S * NK; ++c) bulk_g2s(smem_u32(ops + c * OPCH), src + (int64_t)c * OPCH, OPCH, ob);
             const int64_t slice_stride = (int64_t)nbt * NK * CHUNK;
-            for (int it = 0; it < total; ++it) {
-                const int s = it % OZ_NS;
-                if (it >= OZ_NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((it / OZ_NS - 1) & 1), &abort_flag))
-                    break;
-                const int i = it / NK, kc = it % NK;
-                const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect(fb, CHUNK);
-                const unsigned char* a = reinterpret_cast<const unsigned char*>(bimg) + i * slice_stride +
-                                         ((int64_t)bt * NK + kc) * CHUNK;
-                bulk_g2s(smem_u32(stg + s * CHUNK), a, CHUNK, fb);
+            int g = 0;
+            bool ok = true;
+            for (int btile = bt; ok && btile < nbt; btile += gridDim.x) {
+                for (int it = 0; it < total; ++it, ++g) {
+                    const int s = g % NS;
+                    if (g >= NS && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((g / NS - 1) & 1), &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const int i = it / NK, kc = it % NK;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect(fb, CHUNK);
+                    const unsigned char* a = reinterpret_cast<const unsigned char*>(bimg) + i * slice_stride +
+                                             ((int64_t)btile * NK + kc) * CHUNK;
+                    bulk_g2s(smem_u32(stg + s * CHUNK), a, CHUNK, fb);
+                }
             }
         }
         __syncwarp();
@@ -211,37 +225,50 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
         if (lane == 0) {
             const uint32_t idesc = f16_idesc(OZ_M, OZ_N);
             bool ok = mbar_wait(smem_u32(&opfull), 0, &abort_flag);
-            uint32_t fphase[OZ_NS] = {};
-            for (int it = 0; ok && it < total; ++it) {
-                const int s = it % OZ_NS;
-                if (!mbar_wait(smem_u32(&full[s]), fphase[s], &abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                fphase[s] ^= 1u;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const int i = it / NK, kc = it % NK;
-                const int ksteps = min(OZ_KC, KP - kc * OZ_KC) / 16;
-                const uint32_t a0 = smem_u32(stg + s * CHUNK);
-                for (int j = 0; i + j < OZ_S; ++j) {   // levels i + j = 0 .. 8 (slices 1-based: 2 .. 10)
-                    const uint32_t dacc = tmem + (uint32_t)((i + j) * OZ_N);
-                    const uint32_t b0 = smem_u32(ops + (j * NK + kc) * OPCH);
-                    for (int k = 0; k < ksteps; ++k) {
-                        const uint32_t acc = (i > 0 || kc > 0 || k > 0) ? 1u : 0u;
-                        mma_f16(dacc, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc, acc);
+            uint32_t fphase[NS] = {};
+            int g = 0, tl = 0;
+            for (int btile = bt; ok && btile < nbt; btile += gridDim.x, ++tl) {
+                // the accumulators are reused: wait until the epilogue has read the last tile's
+                if (tl > 0) {
+                    if (!mbar_wait(smem_u32(&drained), (uint32_t)((tl - 1) & 1), &abort_flag)) {
+                        ok = false;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 }
-                mma_commit(smem_u32(&empty[s]));
+                for (int it = 0; it < total; ++it, ++g) {
+                    const int s = g % NS;
+                    if (!mbar_wait(smem_u32(&full[s]), fphase[s], &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    fphase[s] ^= 1u;
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const int i = it / NK, kc = it % NK;
+                    const int ksteps = min(OZ_KC, KP - kc * OZ_KC) / 16;
+                    const uint32_t a0 = smem_u32(stg + s * CHUNK);
+                    for (int j = 0; i + j < OZ_S; ++j) {   // levels i + j = 0 .. 8 (slices 1-based: 2 .. 10)
+                        const uint32_t dacc = tmem + (uint32_t)((i + j) * OZ_N);
+                        const uint32_t b0 = smem_u32(ops + (j * NK + kc) * OPCH);
+                        for (int k = 0; k < ksteps; ++k) {
+                            const uint32_t acc = (i > 0 || kc > 0 || k > 0) ? 1u : 0u;
+                            mma_f16(dacc, sw128_desc(a0 + 32u * k), sw128_desc(b0 + 32u * k), idesc, acc);
+                        }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                }
+                if (ok) mma_commit(smem_u32(&done));
             }
-            if (ok) mma_commit(smem_u32(&done));
         }
         __syncwarp();
     } else {
         // ---------------- epilogue: warps 0-7 ----------------
         const int q = warp & 3, half = warp >> 2;   // rows 32q..32q+31, columns 24 half .. +23
         const uint32_t t_row = (uint32_t)(32 * q) << 16;
-        const bool ok = mbar_wait(smem_u32(&done), 0, &abort_flag);
-        if (!__any_sync(0xffffffffu, !ok)) {
+        int tl = 0;
+        for (int btile = bt; btile < nbt; btile += gridDim.x, ++tl) {
+            const bool ok = mbar_wait(smem_u32(&done), (uint32_t)(tl & 1), &abort_flag);
+            if (__any_sync(0xffffffffu, !ok)) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             // level sums are exact integers below 2^22 in FP32: read them as integers (magic-number
             // add) and combine exactly in 64-bit integers, levels 2..6 (hi) and 7..10 (lo)
@@ -271,7 +298,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
                     else lo[c] += P << (OZ_W * (8 - L));
                 }
             }
-            const int p = bt * OZ_M + 32 * q + lane;
+            // every level is in registers: hand the accumulators back to the MMA warp
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&drained));
+            const int p = btile * OZ_M + 32 * q + lane;
             if (p < n) {
                 const int e_b = eb[p];
                 double* o = cu + (int64_t)boxes[p] * R + r0 + 24 * half;
@@ -320,7 +351,15 @@ static int launch_oz(cudaStream_t st, const void* bimg, const void* opimg, const
         KF_CUDA(cudaFuncSetAttribute(k_pinv_oz<NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         configured = true;
     }
-    dim3 g(nbt, (rank + OZ_N - 1) / OZ_N);
+    static int num_sms = 0;
+    if (!num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+        num_sms = std::max(num_sms, 1);
+    }
+    const int nrt = (rank + OZ_N - 1) / OZ_N;   // one wave: about one CTA per SM over the row tiles
+    dim3 g(std::min(nbt, std::max(1, num_sms / nrt)), nrt);
     k_pinv_oz<NK><<<g, OZ_THREADS, smem, st>>>(reinterpret_cast<const __half*>(bimg),
                                                  reinterpret_cast<const __half*>(opimg), eb, er, boxes, n, nbt, rank, S,
                                                  cu, R, err);
