@@ -441,6 +441,61 @@ int photo_solve_batch(kifmm_plan_t* plans, int count, sno_model_t model, const d
                       double* const* S_dev, const double* C, double tol, int k_samples, uint64_t seed,
                       int* used_fallback, double* judged_err);
 
+/* ---- streamer time loop (Sec. 5, Eq. (eM)) ---- */
+
+/*
+ * The discharge model that the photoionization sum feeds (Sec. 5, Eq. (eM)):
+ *   dn_e/dt - div(mu_e E n_e) - div(D_e grad n_e) = S_i + S_ph,
+ *   dn_p/dt + div(mu_p E n_p) = S_i + S_ph,   -Laplace(phi) = (e / eps0)(n_p - n_e),  E = -grad(phi),
+ *   S_i = mu_e n_e alpha(|E|) |E|, alpha = 5.7 p exp(-260 p / |E|) cm^-1,
+ *   S_ph = kifmm_eval of S_i with scale C (Eqs. (integral), (Ifun)),
+ * on nx x ny x nz cubic cells of edge h (cm) of the box [0, nx h] x [0, ny h] x [0, nz h],
+ * fields [z][y][x] (x fastest, cell (i, j, k) centred at ((i + 1/2) h, (j + 1/2) h, (k + 1/2) h)).
+ * phi = 0 on the face z = 0 and phi0 on the face z = nz h, homogeneous Neumann conditions for
+ * phi on the side faces and for the densities on every face. Drift fluxes from MUSCL face
+ * values with the Koren limiter, diffusion by central differences, Heun's second-order
+ * explicit scheme (S_ph twice per step), the Poisson equation by multigrid V-cycles to a
+ * relative residual of mg_tol. FP64 throughout; every array argument is a device pointer
+ * of nx ny nz doubles owned by the caller.
+ */
+typedef struct streamer_s* streamer_t;
+typedef struct {
+    double p;          /* gas pressure, Torr */
+    double phi0;       /* potential of the top electrode, V (Sec. 5: 52 kV) */
+    double mu_e, mu_p; /* mobilities, cm^2 / (V s) (Sec. 5: 2.9e5 / p and 2.6e3 / p) */
+    double D_e;        /* electron diffusion coefficient, cm^2 / s (Sec. 5: 1800) */
+    double C;          /* scale of S_ph: xi (omega / alpha) p_q / (p + p_q) (Eq. (Ifun)) */
+    double mg_tol;     /* relative residual of the Poisson solve (Sec. 5: 1e-8) */
+    int mg_max_cycles; /* V-cycles before KIFMM_ERR_TIMEOUT */
+} streamer_params;
+
+/* The paper's parameters of Sec. 5 at pressure p (phi0 52 kV, xi omega / alpha = 0.06,
+ * p_q = 30 Torr, mg_tol 1e-8, 100 cycles). */
+void streamer_default_params(streamer_params* prm, double p_torr);
+
+/* plan: a kifmm plan over the nx ny nz cell centres in the fields' order (the FMM of S_ph,
+ * built once and reused at every evaluation), or NULL for a run without photoionization.
+ * stream: the cudaStream_t of every launch. The densities start at 0.
+ * KIFMM_ERR_ARG on invalid sizes or parameters, or a plan of another point count. */
+int streamer_create(streamer_t* out, int nx, int ny, int nz, double h, const streamer_params* prm,
+                    kifmm_plan_t plan, void* stream);
+/* Copies the densities n_e, n_p in. */
+int streamer_set(streamer_t s, const double* ne_dev, const double* np_dev);
+/* Copies out n_e, n_p, and phi and S_ph of the last right-hand-side evaluation (any NULL). */
+int streamer_get(streamer_t s, double* ne_dev, double* np_dev, double* phi_dev, double* sph_dev);
+/* The right-hand side L(n_e, n_p) of the current densities: (dn_e/dt, dn_p/dt). */
+int streamer_rhs(streamer_t s, double* dne_dev, double* dnp_dev);
+/* nsteps steps of Heun's method with step dt (s). KIFMM_ERR_TIMEOUT when a Poisson solve does
+ * not reach mg_tol within mg_max_cycles. */
+int streamer_step(streamer_t s, double dt, int nsteps);
+/* The potential for the charge term rho_dev (the right-hand side of -Laplace(phi) = rho, V /
+ * cm^2) with the boundary conditions above, into phi_dev; synchronises; *rel_residual and
+ * *cycles (either may be NULL) report the solve. */
+int streamer_poisson(streamer_t s, const double* rho_dev, double* phi_dev, double* rel_residual, int* cycles);
+/* Multigrid levels and the last solve's cycles and relative residual. */
+int streamer_info(streamer_t s, int* mg_levels, int* last_cycles, double* last_residual);
+void streamer_destroy(streamer_t s);
+
 /* ---- evaluation without device allocation ---- */
 
 /* Largest point count kifmm_direct_noalloc accepts (its fixed work space: 8 bytes per point). */

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libkifmm.so")
 SOURCES = ["api.cu", "tree.cu", "operators.cu", "eval.cu", "m2l_tc.cu", "noalloc.cu", "sno.cu", "pinv_oz.cu", "near_tc.cu",
-           "tune.cu"]
+           "tune.cu", "streamer.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -61,7 +61,7 @@ static void free_plan(Plan* p) {
     for (DevBuf* b : {&p->surf, &p->ctab, &p->ctab32, &p->cheb_A, &p->pts, &p->loc32, &p->w, &p->sigma, &p->leaf_of, &p->leaves, &p->p2m_boxes,
                       &p->q, &p->Isort, &p->chk, &p->chkx, &p->cu, &p->cu32, &p->chi, &p->clo, &p->cexp, &p->ozBox, &p->ozEb, &p->dd, &p->phid, &p->phiu,
                       &p->far, &p->wleaves, &p->host_I, &p->host_S, &p->err,
-                      &p->tc_tiles, &p->tc_boxes, &p->tc_slots, &p->ptab, &p->l2l_slots, &p->m2m_tiles, &p->m2m_slots, &p->stage32, &p->m2m_hi, &p->m2m_lo, &p->nf_utab, &p->nf_Thi, &p->nf_Tlo, &p->nf_tiles,
+                      &p->tc_tiles, &p->tc_boxes, &p->tc_slots, &p->ptab, &p->l2l_slots, &p->m2m_tiles, &p->m2m_slots, &p->stage32, &p->m2m_hi, &p->m2m_lo, &p->apply_part, &p->nf_utab, &p->nf_Thi, &p->nf_Tlo, &p->nf_tiles,
                       &p->nf_slots, &p->nf_boxes, &p->nf_qhi, &p->nf_qlo, &p->nf_qexp, &p->nf_near, &p->lat_P, &p->lat_Q, &p->lat_Thi, &p->lat_Tlo, &p->lat_iota, &p->lat_slots, &p->lat_fst, &p->lat_Mimg, &p->lat_Mer, &p->nf_ref})
         dev_free(*b);
     for (auto& L : p->lv) {

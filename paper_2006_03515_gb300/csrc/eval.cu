@@ -187,6 +187,9 @@ int build_eval_data(Plan& p) {
     cudaStream_t st = p.stream;
     const int64_t n = t.n, nb = t.nboxes;
     const int S = p.S;
+    // work space of the split SIMT applies: a split launch is at most 4 blocks per SM of at most
+    // 64 x 64 FP64 partial sums each
+    if (t.nlevels > 2) KF_TRY(dev_alloc(p.apply_part, (size_t)4 * p.num_sms * 64 * 64 * sizeof(double)));
     KF_TRY(dev_alloc(p.leaf_of, n * 4));
     mark_leaf_points<<<nbk(nb, 256), 256, 0, st>>>(ptr<int32_t>(t.leaf), ptr<int32_t>(t.pstart),
                                                     ptr<int32_t>(t.pend), nb, ptr<int32_t>(p.leaf_of));
@@ -657,14 +660,16 @@ constexpr int AP_NT = 8;   // terms whose source indices a block stages in share
 // With zoff != NULL the launch is a batch over blockIdx.z: batch z uses Op + z * zstride and
 // the columns [zoff[z], zoff[z+1]) of src/dst (count is then the largest batch). With
 // zoff == NULL and gridDim.z > 1 the work items (term, k-chunk), taken term-major, are split
-// into gridDim.z contiguous ranges and the partial sums are added atomically into out
-// (which the caller zeroes). The next item's operands are loaded into registers while the
-// current one is multiplied.
+// into gridDim.z contiguous ranges: each range's partial sums go to part[z][col][row]
+// (col < gridDim.x TN, row < gridDim.y TM) and k_apply_finish adds them in z order, so the
+// result does not depend on the order in which blocks finish (without part they are added
+// atomically into out, which the caller zeroes). The next item's operands are loaded into
+// registers while the current one is multiplied.
 template <class T, class TI, class TO, int RM, int CN>
 __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t op_stride, int ldop, int nterm,
                                                int Mo, int Ki, const int32_t* src, const int32_t* dst, int64_t base,
                                                int count, const TI* __restrict__ in, int ldi, TO* out, int ldo,
-                                               int accumulate, const int32_t* zoff, int64_t zstride) {
+                                               int accumulate, const int32_t* zoff, int64_t zstride, TO* part) {
     constexpr int TM = 16 * RM, TN = 16 * CN;
     const int nkc = (Ki + AP_TK - 1) / AP_TK;
     int it0 = 0, it1 = nterm * nkc;
@@ -756,10 +761,25 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
             if (col >= count) continue;
             int64_t b = dst ? dst[col] : base + col;
             TO* o = out + b * ldo + row;
-            if (split) atomicAdd(o, (TO)acc[i][j]);
+            if (split && part) part[((int64_t)blockIdx.z * gridDim.x * TN + col) * (gridDim.y * TM) + row] = (TO)acc[i][j];
+            else if (split) atomicAdd(o, (TO)acc[i][j]);
             else *o = accumulate ? *o + (TO)acc[i][j] : (TO)acc[i][j];
         }
     }
+}
+// out[dst(col)][row] (+)= sum over z (in order) of part[z][col][row]
+template <class TO>
+__global__ void k_apply_finish(const TO* __restrict__ part, int nz, int64_t ncp, int nrp, int count, int Mo,
+                               const int32_t* dst, int64_t base, TO* out, int ldo, int accumulate) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)count * Mo) return;
+    const int64_t col = e / Mo;
+    const int row = (int)(e - col * Mo);
+    TO sum = 0;
+    for (int z = 0; z < nz; ++z) sum += part[((int64_t)z * ncp + col) * nrp + row];
+    const int64_t b = dst ? dst[col] : base + col;
+    TO* o = out + b * ldo + row;
+    *o = accumulate ? *o + sum : sum;
 }
 // tile shapes: FP64 48 x 32 (3 x 2 per thread; ranks near 141 pad to 144), FP32 64 x 64
 template <class T> struct ApplyShape;
@@ -1517,13 +1537,26 @@ template <> const float* sel<float>(const DevBuf&, const DevBuf& d32) { return p
 template <class T, class TI = T, class TO = T>
 static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, const int32_t* src, const int32_t* dst,
                         int64_t base, int count, const TI* in, int ldi, TO* out, int ldo, int acc, int nterm = 1,
-                        int64_t op_stride = 0, const int32_t* zoff = nullptr, int nz = 1, int64_t zstride = 0) {
+                        int64_t op_stride = 0, const int32_t* zoff = nullptr, int nz = 1, int64_t zstride = 0,
+                        DevBuf* part = nullptr, int64_t* nl = nullptr) {
     if (count <= 0) return KIFMM_OK;
     constexpr int RM = ApplyShape<T>::RM, CN = ApplyShape<T>::CN;
     dim3 g(nbk(count, 16 * CN), nbk(Mo, 16 * RM), nz);
+    const int64_t ncp = (int64_t)g.x * 16 * CN, nrp = (int64_t)g.y * 16 * RM;
+    TO* pp = nullptr;
+    // the split's partial sums, added in order by k_apply_finish (the work space is sized at plan
+    // time for a split of at most one wave; nothing is allocated here, so evaluations can be
+    // captured in a graph)
+    if (nz > 1 && !zoff && part && part->bytes >= (size_t)nz * ncp * nrp * sizeof(TO)) pp = static_cast<TO*>(part->p);
     k_apply<T, TI, TO, RM, CN><<<g, 256, 0, st>>>(Op, op_stride, ldop, nterm, Mo, Ki, src, dst, base, count, in, ldi,
-                                                  out, ldo, acc, zoff, zstride);
+                                                  out, ldo, acc, zoff, zstride, pp);
     KF_LAUNCH();
+    if (pp) {
+        k_apply_finish<TO><<<nbk((int64_t)count * Mo, 256), 256, 0, st>>>(pp, nz, ncp, (int)nrp, count, Mo, dst, base,
+                                                                         out, ldo, acc);
+        KF_LAUNCH();
+        if (nl) ++*nl;
+    }
     return KIFMM_OK;
 }
 
@@ -1617,7 +1650,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
                                                  cu, R, p.cheb ? cu : ptr<double>(p.chk), p.cheb ? R : S, 0, 8,
-                                                 (int64_t)S * R, nullptr, nz)));
+                                                 (int64_t)S * R, nullptr, nz, 0, &p.apply_part, &nl)));
         }
         if (p.cheb) continue;   // no pseudo-inverse
         if (p.lat_up && l == p.nf_level) {   // lattice leaves: c = (G1 P) q, FP64-exact on the tensor cores
@@ -1634,7 +1667,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             const int nz = std::max(1, std::min((S + AP_TK - 1) / AP_TK, (2 * p.num_sms + tiles - 1) / tiles));
             RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.upb),
                                      ptr<int32_t>(LL.upb), 0, LL.n_up, ptr<double>(p.chk), S, cu, R, 0, 1, 0, nullptr,
-                                     nz));
+                                     nz, 0, &p.apply_part, &nl));
         }
     }
     mark(p, 3);

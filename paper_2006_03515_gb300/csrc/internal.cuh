@@ -194,6 +194,7 @@ struct Plan {
     int tc_first[kMaxLevel + 1] = {0}, tc_count[kMaxLevel + 1] = {0};   // M2L tiles of each level
     bool m2m_tc = false;         // M2M translations through the same kernel (mixed form)
     DevBuf m2m_tiles, m2m_slots, stage32;   // parent tiles per level, their 8 slots, FP32 staging [nb][m2m_R]
+    DevBuf apply_part;                      // partial sums of the SIMT applies split over their terms
     int m2m_R = 0;                          // square table size of the M2M translations: max(S, R) rounded to 32
     DevBuf m2m_hi, m2m_lo;                  // children's c split FP16 x 2 in rows of m2m_R (when m2m_R > R)
     int m2m_first[kMaxLevel + 1] = {0}, m2m_count[kMaxLevel + 1] = {0};

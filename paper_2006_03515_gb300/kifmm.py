@@ -71,6 +71,12 @@ class _Info(ctypes.Structure):
                 ("n_padding", ctypes.c_int64)]
 
 
+class _StreamerParams(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double), ("phi0", ctypes.c_double), ("mu_e", ctypes.c_double),
+                ("mu_p", ctypes.c_double), ("D_e", ctypes.c_double), ("C", ctypes.c_double),
+                ("mg_tol", ctypes.c_double), ("mg_max_cycles", ctypes.c_int)]
+
+
 class _TuneEntry(ctypes.Structure):
     _fields_ = [("leaf", ctypes.c_int), ("order", ctypes.c_int), ("radii", ctypes.c_double * 2),
                 ("ms", ctypes.c_float), ("err", ctypes.c_double), ("ok", ctypes.c_int)]
@@ -83,7 +89,9 @@ EXPORTS = ["kifmm_default_opts", "kifmm_plan", "kifmm_eval", "kifmm_eval_host", 
            "sno_create", "sno_destroy", "sno_num_params", "sno_set_params", "sno_get_params", "sno_get_grads",
            "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint",
            "sno_set_bf16", "sno_set_period", "sno_set_near_field", "sno_init_far_field", "sno_forward",
-           "sno_loss_grad", "sno_adam_step", "photo_solve", "photo_solve_batch"]
+           "sno_loss_grad", "sno_adam_step", "photo_solve", "photo_solve_batch",
+           "streamer_default_params", "streamer_create", "streamer_set", "streamer_get", "streamer_rhs",
+           "streamer_step", "streamer_poisson", "streamer_info", "streamer_destroy"]
 
 _lib = None
 
@@ -438,6 +446,20 @@ def _load_sno(L):
     L.photo_solve.argtypes = [vp, vp, vp, vp, dbl, dbl, i32, ctypes.c_uint64, ctypes.POINTER(i32),
                               ctypes.POINTER(dbl)]
     L.photo_solve_batch.argtypes = [vp, i32, vp, vp, vp, vp, dbl, i32, ctypes.c_uint64, vp, vp]
+    L.streamer_default_params.argtypes = [ctypes.POINTER(_StreamerParams), dbl]
+    L.streamer_default_params.restype = None
+    L.streamer_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, dbl, ctypes.POINTER(_StreamerParams), vp, vp]
+    L.streamer_set.argtypes = [vp, vp, vp]
+    L.streamer_get.argtypes = [vp, vp, vp, vp, vp]
+    L.streamer_rhs.argtypes = [vp, vp, vp]
+    L.streamer_step.argtypes = [vp, dbl, i32]
+    L.streamer_poisson.argtypes = [vp, vp, vp, ctypes.POINTER(dbl), ctypes.POINTER(i32)]
+    L.streamer_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(dbl)]
+    L.streamer_destroy.argtypes = [vp]
+    L.streamer_destroy.restype = None
+    for name in ("streamer_create", "streamer_set", "streamer_get", "streamer_rhs", "streamer_step",
+                 "streamer_poisson", "streamer_info"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("photo_solve_batch", "sno_create", "sno_save", "sno_load", "sno_save_checkpoint", "sno_load_checkpoint", "sno_set_params",
                  "sno_get_params", "sno_get_grads", "sno_set_bf16", "sno_set_period", "sno_set_near_field",
                  "sno_init_far_field", "sno_forward", "sno_loss_grad", "sno_adam_step", "photo_solve"):
@@ -628,3 +650,80 @@ def photo_solve_batch(plans, model, Is, Ss=None, C=None, tol=0.05, k_samples=256
     err = (ctypes.c_double * k)()
     _check(load().photo_solve_batch(hp, k, model.handle, ip, sp, cs, float(tol), int(k_samples), int(seed), fb, err))
     return Ss, [bool(x) for x in fb], [float(x) for x in err]
+
+
+class Streamer:
+    """The streamer time loop of Sec. 5, Eq. (eM) (streamer_* in kifmm.h): fields [z][y][x] on
+    nx x ny x nz cubic cells of edge h (cm), CUDA float64 tensors of nx ny nz entries. plan: a
+    Plan over the cell centres in that order (the FMM of S_ph) or None; params: overrides of
+    the paper's values (p, phi0, mu_e, mu_p, D_e, C, mg_tol, mg_max_cycles)."""
+
+    def __init__(self, nx, ny, nz, h, p=760.0, plan=None, stream=None, **params):
+        import torch
+        L = load()
+        prm = _StreamerParams()
+        L.streamer_default_params(ctypes.byref(prm), float(p))
+        for k, v in params.items():
+            if not hasattr(prm, k):
+                raise KeyError(k)
+            setattr(prm, k, v)
+        self.shape = (int(nz), int(ny), int(nx))
+        self.n = int(nx) * int(ny) * int(nz)
+        self.plan = plan   # (kept alive with the streamer)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(L.streamer_create(ctypes.byref(self._h), int(nx), int(ny), int(nz), float(h), ctypes.byref(prm),
+                                 plan.handle if plan is not None else None, _stream_ptr(self.stream)))
+
+    def _t(self, x):
+        import torch
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()
+                and x.numel() == self.n):
+            raise TypeError("fields must be contiguous CUDA float64 tensors of nx ny nz entries")
+        return ctypes.c_void_p(x.data_ptr())
+
+    def _new(self):
+        import torch
+        return torch.empty(self.shape, dtype=torch.float64, device="cuda")
+
+    def set(self, ne, np_):
+        _check(load().streamer_set(self._h, self._t(ne), self._t(np_)))
+
+    def get(self):
+        """(n_e, n_p, phi, S_ph) of the current state / last right-hand side."""
+        out = [self._new() for _ in range(4)]
+        _check(load().streamer_get(self._h, *[self._t(x) for x in out]))
+        self.stream.synchronize()
+        return tuple(out)
+
+    def rhs(self):
+        dne, dnp = self._new(), self._new()
+        _check(load().streamer_rhs(self._h, self._t(dne), self._t(dnp)))
+        self.stream.synchronize()
+        return dne, dnp
+
+    def step(self, dt, nsteps=1):
+        _check(load().streamer_step(self._h, float(dt), int(nsteps)))
+
+    def poisson(self, rho):
+        phi = self._new()
+        res, cyc = ctypes.c_double(), ctypes.c_int()
+        _check(load().streamer_poisson(self._h, self._t(rho), self._t(phi), ctypes.byref(res), ctypes.byref(cyc)))
+        return phi, res.value, cyc.value
+
+    def info(self):
+        lv, cyc, res = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(load().streamer_info(self._h, ctypes.byref(lv), ctypes.byref(cyc), ctypes.byref(res)))
+        return dict(mg_levels=lv.value, last_cycles=cyc.value, last_residual=res.value)
+
+    def close(self):
+        if self._h:
+            self.stream.synchronize()
+            load().streamer_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

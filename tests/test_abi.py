@@ -52,6 +52,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     opts = [f[0] for f in kifmm._Opts._fields_]
     info = [f[0] for f in kifmm._Info._fields_]
     tune = [f[0] for f in kifmm._TuneEntry._fields_]
+    strm = [f[0] for f in kifmm._StreamerParams._fields_]
     src = ['#include <stdio.h>', '#include <stddef.h>', '#include "kifmm.h"', "int main(void) {"]
     src.append('printf("%zu\\n", sizeof(kifmm_opts));')
     src += ['printf("%%zu\\n", offsetof(kifmm_opts, %s));' % f for f in opts]
@@ -59,6 +60,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     src += ['printf("%%zu\\n", offsetof(kifmm_info, %s));' % f for f in info]
     src.append('printf("%zu\\n", sizeof(kifmm_tune_entry));')
     src += ['printf("%%zu\\n", offsetof(kifmm_tune_entry, %s));' % f for f in tune]
+    src.append('printf("%zu\\n", sizeof(streamer_params));')
+    src += ['printf("%%zu\\n", offsetof(streamer_params, %s));' % f for f in strm]
     src.append("return 0; }")
     c = tmp_path / "layout.c"
     c.write_text("\n".join(src) + "\n")
@@ -68,6 +71,7 @@ def test_struct_layouts_match_the_header(tmp_path):
     want = [ctypes.sizeof(kifmm._Opts)] + [getattr(kifmm._Opts, f).offset for f in opts]
     want += [ctypes.sizeof(kifmm._Info)] + [getattr(kifmm._Info, f).offset for f in info]
     want += [ctypes.sizeof(kifmm._TuneEntry)] + [getattr(kifmm._TuneEntry, f).offset for f in tune]
+    want += [ctypes.sizeof(kifmm._StreamerParams)] + [getattr(kifmm._StreamerParams, f).offset for f in strm]
     assert got == want
 
 
