@@ -118,6 +118,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 gate and FP64 timing")
     ap.add_argument("--no-surrogate", action="store_true", help="skip the surrogate measurement")
+    ap.add_argument("--no-streamer", action="store_true", help="skip the streamer time-loop measurement")
+    ap.add_argument("--sd-n", type=int, default=128, help="streamer grid: n x n x 2n cells of the 0.5 x 0.5 x 1 cm gap")
+    ap.add_argument("--sd-steps", type=int, default=10, help="timed streamer steps")
     ap.add_argument("--no-configs", action="store_true", help="skip the other target settings")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="measure only the surrogate and print its record (profiling runs)")
@@ -516,6 +519,89 @@ def batch_bench(args, dev, stream, flush):
     return out
 
 
+def streamer_bench(args, dev, stream):
+    """The streamer time loop of Sec. 5 (Eq. (eM)): the double-headed streamer initial condition
+    (two Gaussians of 1e14 cm^-3, width 0.03 cm, at (0.22, 0.25, 0.41) and (0.28, 0.25, 0.59)
+    cm) in the 0.5 x 0.5 x 1 cm gap at 52 kV, 760 Torr, p_O2 150 Torr, on n x n x 2n cubic
+    cells, time step 2.5e-3 ns (the paper's), Heun's method with S_ph from the mixed-form FMM
+    on a plan of the grid built once (twice per step), the Poisson equation by multigrid to a
+    relative residual of 1e-8. Timed: steps after two warm-up steps (CUDA events); the FMM's
+    share from the same number of stand-alone evaluations; and the local evaluation (S_ph over
+    the central sub-box of half the gap's width and 0.6 of its height, sources above 1e-4 of
+    the largest)."""
+    import numpy as np
+    import torch
+    from paper_2006_03515_gb300 import kifmm
+    n = args.sd_n
+    nx, ny, nz, h = n, n, 2 * n, 0.5 / n
+    g = [(np.arange(m) + 0.5) * h for m in (nx, ny, nz)]
+    zz, yy, xx = np.meshgrid(g[2], g[1], g[0], indexing="ij")
+    pts = np.stack([xx.ravel(), yy.ravel(), zz.ravel()], axis=1)
+    c = pts.reshape(nz, ny, nx, 3)
+
+    def gauss(x0):
+        return np.exp(-((c - np.asarray(x0)) ** 2).sum(-1) / 0.03 ** 2)
+    n0 = torch.as_tensor(1e14 * (gauss((0.22, 0.25, 0.41)) + gauss((0.28, 0.25, 0.59))), device=dev)
+    a, b = kifmm.absorption(150.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"grid": [nx, ny, nz], "cells": nx * ny * nz, "h_cm": h, "dt_ns": 2.5e-3, "steps": args.sd_steps,
+           "photo": "mixed KIFMM, m0 6, leaf 64, lattice-padded plan, twice per step"}
+
+    def run(plan, region=None, threshold=0.0, Si_eval=None):
+        kw = {} if region is None else {"region": region}
+        sd = kifmm.Streamer(nx, ny, nz, h, plan=plan, stream=stream, threshold=threshold, **kw)
+        sd.set(n0, n0)
+        sd.step(2.5e-12, 2)
+        stream.synchronize()
+        e0.record(stream)
+        sd.step(2.5e-12, args.sd_steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.sd_steps
+        if plan is not None and region is None:   # one more step: the profiled range (ncu --profile-from-start off)
+            torch.cuda.profiler.start()
+            sd.step(2.5e-12, 1)
+            stream.synchronize()
+            torch.cuda.profiler.stop()
+        inf = sd.info()
+        ne, npi, _, _ = sd.get()
+        ok = bool(torch.isfinite(ne).all() and torch.isfinite(npi).all())
+        sd.close()
+        return {"ms_per_step": ms, "cells_per_s": nx * ny * nz / (ms * 1e-3), "mg_levels": inf["mg_levels"],
+                "mg_cycles_last": inf["last_cycles"], "mg_residual_last": inf["last_residual"], "finite": ok}
+
+    t0 = time.perf_counter()
+    plan = kifmm.Plan(torch.as_tensor(pts, device=dev), h, 64, 6, a, b, precision="mixed", stream=stream,
+                      pad_lattice=True)
+    stream.synchronize()
+    out["plan_s"] = time.perf_counter() - t0
+    out["full"] = run(plan)
+    # the FMM's share: two evaluations per step, timed alone on the same plan
+    Si = torch.rand(nx * ny * nz, dtype=torch.float64, device=dev)
+    S = torch.empty_like(Si)
+    for _ in range(2):
+        plan.eval(Si, S)
+    e0.record(stream)
+    for _ in range(2 * args.sd_steps):
+        plan.eval(Si, S)
+    e1.record(stream)
+    e1.synchronize()
+    out["fmm_ms_per_step"] = e0.elapsed_time(e1) / args.sd_steps
+    out["fmm_share"] = out["fmm_ms_per_step"] / out["full"]["ms_per_step"]
+    plan.close()
+    # local evaluation over the central sub-box
+    reg = (nx // 4, 3 * nx // 4, ny // 4, 3 * ny // 4, int(0.2 * nz), int(0.8 * nz))
+    rp = pts.reshape(nz, ny, nx, 3)[reg[4]:reg[5], reg[2]:reg[3], reg[0]:reg[1]].reshape(-1, 3)
+    lplan = kifmm.Plan(torch.as_tensor(rp, device=dev), h, 64, 6, a, b, precision="mixed", stream=stream,
+                       pad_lattice=True)
+    out["local"] = run(lplan, region=reg, threshold=1e-4)
+    out["local"]["region"] = list(reg)
+    lplan.close()
+    out["none"] = run(None)   # without photoionization: the transport and Poisson alone
+    torch.cuda.empty_cache()
+    return out
+
+
 def surrogate_bench(args, dev, stream, peaks):
     """The learned surrogate on the n^3 grid (width 32, 12 modes, 4 layers, projection 64,
     BF16 spectral weights): amplitude-normalised linear form (u = I / max I, S = C max I y),
@@ -887,6 +973,12 @@ def main():
                 line["surrogate"] = surrogate_bench(args, dev, stream, peaks)
         except Exception as exc:    # the headline line is printed whatever happens here
             line["surrogate"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
+    if not args.no_streamer:
+        try:
+            with torch.cuda.stream(stream):
+                line["streamer"] = streamer_bench(args, dev, stream)
+        except Exception as exc:    # the headline line is printed whatever happens here
+            line["streamer"] = {"error": "%s: %s" % (type(exc).__name__, exc)}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         from oracle import build as ob
         ob.build()

@@ -455,8 +455,9 @@ int photo_solve_batch(kifmm_plan_t* plans, int count, sno_model_t model, const d
  * phi on the side faces and for the densities on every face. Drift fluxes from MUSCL face
  * values with the Koren limiter, diffusion by central differences, Heun's second-order
  * explicit scheme (S_ph twice per step), the Poisson equation by multigrid V-cycles to a
- * relative residual of mg_tol. FP64 throughout; every array argument is a device pointer
- * of nx ny nz doubles owned by the caller.
+ * relative residual of mg_tol (FP64 residual and potential, FP32 error equations). FP64
+ * densities and fields; every array argument is a device pointer of nx ny nz doubles owned
+ * by the caller.
  */
 typedef struct streamer_s* streamer_t;
 typedef struct {
@@ -467,14 +468,22 @@ typedef struct {
     double C;          /* scale of S_ph: xi (omega / alpha) p_q / (p + p_q) (Eq. (Ifun)) */
     double mg_tol;     /* relative residual of the Poisson solve (Sec. 5: 1e-8) */
     int mg_max_cycles; /* V-cycles before KIFMM_ERR_TIMEOUT */
+    /* Local, thresholded photoionization (the saving the paper suggests at the end of Sec. 5.1):
+     * region = {x0, x1, y0, y1, z0, z1} cell ranges [x0, x1) ... of the sub-box where S_ph is
+     * evaluated, from the sources inside it (the plan is then over the sub-box's cell centres,
+     * x fastest); all zero: the whole grid. Sources with S_i < threshold max S_i are left out
+     * (threshold 0: none). S_ph is 0 outside the region. */
+    int region[6];
+    double threshold;
 } streamer_params;
 
 /* The paper's parameters of Sec. 5 at pressure p (phi0 52 kV, xi omega / alpha = 0.06,
  * p_q = 30 Torr, mg_tol 1e-8, 100 cycles). */
 void streamer_default_params(streamer_params* prm, double p_torr);
 
-/* plan: a kifmm plan over the nx ny nz cell centres in the fields' order (the FMM of S_ph,
- * built once and reused at every evaluation), or NULL for a run without photoionization.
+/* plan: a kifmm plan over the nx ny nz cell centres in the fields' order (or over the region's
+ * cells in that order when a region is set; the FMM of S_ph, built once and reused at every
+ * evaluation), or NULL for a run without photoionization.
  * stream: the cudaStream_t of every launch. The densities start at 0.
  * KIFMM_ERR_ARG on invalid sizes or parameters, or a plan of another point count. */
 int streamer_create(streamer_t* out, int nx, int ny, int nz, double h, const streamer_params* prm,

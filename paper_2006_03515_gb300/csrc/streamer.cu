@@ -16,7 +16,9 @@
 // differences, Heun's two-stage explicit scheme in time. The Poisson equation is solved by
 // geometric multigrid V-cycles (red-black Gauss-Seidel, full-weighting restriction of the
 // residual, trilinear prolongation of the correction) until the relative residual is below
-// the tolerance (1e-8 in Sec. 5). Everything is FP64.
+// the tolerance (1e-8 in Sec. 5), as iterative refinement: the potential and its residual in
+// FP64, each V-cycle on the error equation in FP32 (this GPU's FP64 pipe is scarce; the FP64
+// residual keeps the result at FP64 accuracy). The densities, fields and fluxes are FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,9 +37,18 @@ inline unsigned nbs(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 struct Grid {
     int nx, ny, nz;
-    double h;
+    double h, ih, ih2;   // edge, 1 / h, 1 / h^2
     __host__ __device__ int64_t n() const { return (int64_t)nx * ny * nz; }
 };
+inline Grid make_grid(int nx, int ny, int nz, double h) { return Grid{nx, ny, nz, h, 1.0 / h, 1.0 / (h * h)}; }
+// cell (i, j, k) of index c < 2^31 (32-bit arithmetic)
+__device__ __forceinline__ void cell_ijk(const Grid& g, int c, int& i, int& j, int& k) {
+    const int xy = g.nx * g.ny;
+    k = c / xy;
+    const int r = c - k * xy;
+    j = r / g.nx;
+    i = r - j * g.nx;
+}
 
 // ---- multigrid -------------------------------------------------------------------------
 // diagonal of the discrete -Laplace(u) h^2 at cell (i, j, k): one per interior neighbour,
@@ -49,10 +60,17 @@ __device__ __forceinline__ double mg_diag(const Grid& g, int i, int j, int k) {
     d += k < g.nz - 1 ? 1.0 : 2.0;
     return d;
 }
-__device__ __forceinline__ double mg_nbsum(const Grid& g, const double* u, int i, int j, int k) {
+// 1 / diagonal: the diagonal is an integer from 2 to 8 (a table instead of a division)
+__device__ __forceinline__ double mg_rdiag(const Grid& g, int i, int j, int k) {
+    const int d = (i > 0) + (i < g.nx - 1) + (j > 0) + (j < g.ny - 1) + (k > 0 ? 1 : 2) + (k < g.nz - 1 ? 1 : 2);
+    constexpr double inv[9] = {0.0, 1.0, 0.5, 1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0, 1.0 / 7.0, 0.125};
+    return inv[d];
+}
+template <class T>
+__device__ __forceinline__ T mg_nbsum(const Grid& g, const T* u, int i, int j, int k) {
     const int64_t sx = 1, sy = g.nx, sz = (int64_t)g.nx * g.ny;
     const int64_t c = (int64_t)k * sz + (int64_t)j * sy + i;
-    double s = 0.0;
+    T s = 0;
     if (i > 0) s += u[c - sx];
     if (i < g.nx - 1) s += u[c + sx];
     if (j > 0) s += u[c - sy];
@@ -63,85 +81,103 @@ __device__ __forceinline__ double mg_nbsum(const Grid& g, const double* u, int i
 }
 
 // red-black Gauss-Seidel sweep of one colour: u = (b h^2 + sum of neighbours) / diag
-__global__ void k_mg_smooth(Grid g, double* u, const double* b, int color) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <class T>
+__global__ void k_mg_smooth(Grid g, T* u, const T* b, int color) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     // the cells of one colour: two per pair along x
     const int hx = (g.nx + 1) / 2;
-    if (e >= (int64_t)hx * g.ny * g.nz) return;
-    const int k = (int)(e / ((int64_t)hx * g.ny)), j = (int)((e / hx) % g.ny);
-    const int i = 2 * (int)(e % hx) + ((j + k + color) & 1);
+    if (e >= hx * g.ny * g.nz) return;
+    const int k = e / (hx * g.ny), r = e - k * (hx * g.ny), j = r / hx;
+    const int i = 2 * (r - j * hx) + ((j + k + color) & 1);
     if (i >= g.nx) return;
     const int64_t c = ((int64_t)k * g.ny + j) * g.nx + i;
-    u[c] = (b[c] * g.h * g.h + mg_nbsum(g, u, i, j, k)) / mg_diag(g, i, j, k);
+    u[c] = (b[c] * (T)(g.h * g.h) + mg_nbsum(g, u, i, j, k)) * (T)mg_rdiag(g, i, j, k);
 }
 
-// r = b - A u, with A = -Laplace (including the z boundary faces' Dirichlet terms)
-__global__ void k_mg_residual(Grid g, const double* u, const double* b, double* r) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// r = b - A u, with A = -Laplace (including the z boundary faces' Dirichlet terms); r32 (when
+// given) receives r rounded to FP32, the right-hand side of the FP32 error equation
+template <class T>
+__global__ void k_mg_residual(Grid g, const T* u, const T* b, T* r, float* r32) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.n()) return;
-    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
-    r[c] = b[c] - (mg_diag(g, i, j, k) * u[c] - mg_nbsum(g, u, i, j, k)) / (g.h * g.h);
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
+    const T v = b[c] - ((T)mg_diag(g, i, j, k) * u[c] - mg_nbsum(g, u, i, j, k)) * (T)g.ih2;
+    r[c] = v;
+    if (r32) r32[c] = (float)v;
+}
+
+// u += e (the FP32 correction into the FP64 potential)
+__global__ void k_mg_correct(int64_t n, const float* e, double* u) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < n) u[c] += (double)e[c];
 }
 
 // coarse right-hand side: the average of the 8 fine residuals of each coarse cell
-__global__ void k_mg_restrict(Grid f, Grid cg, const double* r, double* bc) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+template <class T>
+__global__ void k_mg_restrict(Grid f, Grid cg, const T* r, T* bc) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= cg.n()) return;
-    const int I = (int)(c % cg.nx), J = (int)((c / cg.nx) % cg.ny), K = (int)(c / ((int64_t)cg.nx * cg.ny));
-    double s = 0.0;
+    int I, J, K;
+    cell_ijk(cg, c, I, J, K);
+    T s = 0;
     for (int dk = 0; dk < 2; ++dk)
         for (int dj = 0; dj < 2; ++dj)
             for (int di = 0; di < 2; ++di)
                 s += r[((int64_t)(2 * K + dk) * f.ny + (2 * J + dj)) * f.nx + (2 * I + di)];
-    bc[c] = 0.125 * s;
+    bc[c] = (T)0.125 * s;
 }
 
 // coarse value at integer coarse index (I, J, K) with the ghost rules of the correction:
 // mirrored across the side faces (Neumann), negated across the z faces (zero at the face)
-__device__ __forceinline__ double mg_coarse_at(const Grid& cg, const double* e, int I, int J, int K) {
-    double sgn = 1.0;
+template <class T>
+__device__ __forceinline__ T mg_coarse_at(const Grid& cg, const T* e, int I, int J, int K) {
+    T sgn = 1;
     if (I < 0) I = 0;
     if (I >= cg.nx) I = cg.nx - 1;
     if (J < 0) J = 0;
     if (J >= cg.ny) J = cg.ny - 1;
     if (K < 0) {
         K = 0;
-        sgn = -1.0;
+        sgn = -1;
     }
     if (K >= cg.nz) {
         K = cg.nz - 1;
-        sgn = -1.0;
+        sgn = -1;
     }
     return sgn * e[((int64_t)K * cg.ny + J) * cg.nx + I];
 }
 
 // u_fine += trilinear interpolation of the coarse correction (cell-centred: weights 3/4 and
 // 1/4 per axis towards the nearer coarse neighbour)
-__global__ void k_mg_prolong(Grid f, Grid cg, const double* e, double* u) {
+template <class T>
+__global__ void k_mg_prolong(Grid f, Grid cg, const T* e, T* u) {
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= f.n()) return;
     const int i = (int)(c % f.nx), j = (int)((c / f.nx) % f.ny), k = (int)(c / ((int64_t)f.nx * f.ny));
     const int I = i >> 1, J = j >> 1, K = k >> 1;
     const int oi = (i & 1) ? 1 : -1, oj = (j & 1) ? 1 : -1, ok = (k & 1) ? 1 : -1;
-    double s = 0.0;
+    T s = 0;
     for (int a = 0; a < 2; ++a)
         for (int b2 = 0; b2 < 2; ++b2)
             for (int d = 0; d < 2; ++d) {
-                const double w = (a ? 0.25 : 0.75) * (b2 ? 0.25 : 0.75) * (d ? 0.25 : 0.75);
+                const T w = (T)((a ? 0.25 : 0.75) * (b2 ? 0.25 : 0.75) * (d ? 0.25 : 0.75));
                 s += w * mg_coarse_at(cg, e, I + a * oi, J + b2 * oj, K + d * ok);
             }
     u[c] += s;
 }
 
 // the coarsest level: many red-black sweeps in one block
-__global__ void k_mg_coarse_solve(Grid g, double* u, const double* b, int sweeps) {
+template <class T>
+__global__ void k_mg_coarse_solve(Grid g, T* u, const T* b, int sweeps) {
     const int64_t n = g.n();
     for (int s = 0; s < sweeps; ++s)
         for (int color = 0; color < 2; ++color) {
-            for (int64_t c = threadIdx.x; c < n; c += blockDim.x) {
-                const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+            for (int c = threadIdx.x; c < n; c += blockDim.x) {
+                int i, j, k;
+                cell_ijk(g, c, i, j, k);
                 if (((i + j + k) & 1) != color) continue;
-                u[c] = (b[c] * g.h * g.h + mg_nbsum(g, u, i, j, k)) / mg_diag(g, i, j, k);
+                u[c] = (b[c] * (T)(g.h * g.h) + mg_nbsum(g, u, i, j, k)) * (T)mg_rdiag(g, i, j, k);
             }
             __syncthreads();
         }
@@ -165,50 +201,58 @@ __global__ void k_sumsq(const double* x, int64_t n, double* out) {
 // ---- fields and transport -------------------------------------------------------------
 // b = (e / eps0)(n_p - n_e), plus the top face's Dirichlet term 2 phi0 / h^2
 __global__ void k_sd_charge(Grid g, const double* ne, const double* np, double phi0, double* b) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.n()) return;
-    const int k = (int)(c / ((int64_t)g.nx * g.ny));
-    b[c] = kEoverEps0 * (np[c] - ne[c]) + (k == g.nz - 1 ? 2.0 * phi0 / (g.h * g.h) : 0.0);
+    const int k = c / (g.nx * g.ny);
+    b[c] = kEoverEps0 * (np[c] - ne[c]) + (k == g.nz - 1 ? 2.0 * phi0 * g.ih2 : 0.0);
 }
 
 // E on the face between cells c - s and c along an axis of m cells (f = 0..m: face index)
-__device__ __forceinline__ double face_E(const double* phi, int64_t c_lo, int64_t stride, int f, int m, double h,
+__device__ __forceinline__ double face_E(const double* phi, int64_t c_lo, int64_t stride, int f, int m, double ih,
                                          bool zaxis, double phi0) {
-    if (f > 0 && f < m) return -(phi[c_lo + stride] - phi[c_lo]) / h;
-    if (!zaxis) return 0.0;                                   // side faces: Neumann
-    if (f == 0) return -(phi[c_lo + stride] - 0.0) / (0.5 * h);   // bottom electrode, phi = 0
-    return -(phi0 - phi[c_lo]) / (0.5 * h);                   // top electrode, phi = phi0
+    if (f > 0 && f < m) return -(phi[c_lo + stride] - phi[c_lo]) * ih;
+    if (!zaxis) return 0.0;                                         // side faces: Neumann
+    if (f == 0) return -(phi[c_lo + stride] - 0.0) * (2.0 * ih);   // bottom electrode, phi = 0
+    return -(phi0 - phi[c_lo]) * (2.0 * ih);                        // top electrode, phi = phi0
 }
 
 // |E| at the cell centres (averages of each component's two faces) and S_i = mu_e n_e alpha |E|
 __global__ void k_sd_source(Grid g, const double* phi, double phi0, const double* ne, double mu_e, double p,
                             double* Emag, double* Si) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.n()) return;
-    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
     const int64_t sy = g.nx, sz = (int64_t)g.nx * g.ny;
-    const double ex = 0.5 * (face_E(phi, c - 1, 1, i, g.nx, g.h, false, phi0) +
-                             face_E(phi, c, 1, i + 1, g.nx, g.h, false, phi0));
-    const double ey = 0.5 * (face_E(phi, c - sy, sy, j, g.ny, g.h, false, phi0) +
-                             face_E(phi, c, sy, j + 1, g.ny, g.h, false, phi0));
-    const double ez = 0.5 * (face_E(phi, c - sz, sz, k, g.nz, g.h, true, phi0) +
-                             face_E(phi, c, sz, k + 1, g.nz, g.h, true, phi0));
+    const double ex = 0.5 * (face_E(phi, c - 1, 1, i, g.nx, g.ih, false, phi0) +
+                             face_E(phi, c, 1, i + 1, g.nx, g.ih, false, phi0));
+    const double ey = 0.5 * (face_E(phi, c - sy, sy, j, g.ny, g.ih, false, phi0) +
+                             face_E(phi, c, sy, j + 1, g.ny, g.ih, false, phi0));
+    const double ez = 0.5 * (face_E(phi, c - sz, sz, k, g.nz, g.ih, true, phi0) +
+                             face_E(phi, c, sz, k + 1, g.nz, g.ih, true, phi0));
     const double E = sqrt(ex * ex + ey * ey + ez * ez);
     const double a = E > 0.0 ? 5.7 * p * exp(-260.0 * p / E) : 0.0;
     Emag[c] = E;
     Si[c] = mu_e * ne[c] * a * E;
 }
 
-__device__ __forceinline__ double koren(double r) { return fmax(0.0, fmin(fmin(2.0 * r, (1.0 + 2.0 * r) / 3.0), 2.0)); }
-__device__ __forceinline__ double ratio(double num, double den) { return den != 0.0 ? num / den : 0.0; }
+// Koren's limiter times the slope, phi(num / den) den with phi(r) = max(0, min(2r, (1 + 2r) / 3, 2)),
+// without the division: for den > 0 it is max(0, min(2 num, (den + 2 num) / 3, 2 den)), for
+// den < 0 the mirror image with min and max exchanged, and 0 for den = 0 (r taken as 0)
+__device__ __forceinline__ double koren_slope(double num, double den) {
+    const double a = 2.0 * num, b = (den + 2.0 * num) * (1.0 / 3.0), c = 2.0 * den;
+    if (den > 0.0) return fmax(0.0, fmin(fmin(a, b), c));
+    if (den < 0.0) return fmin(0.0, fmax(fmax(a, b), c));
+    return 0.0;
+}
 
 // upwind MUSCL face value (Koren limiter) at face f of a line of m cells starting at c0 with
 // the given stride; cells beyond the ends repeat the boundary cell (zero gradient)
 __device__ __forceinline__ double muscl(const double* n, int64_t c0, int64_t stride, int f, int m, double v) {
     auto at = [&](int q) { return n[c0 + (int64_t)min(max(q, 0), m - 1) * stride]; };
     const double um = at(f - 2), u0 = at(f - 1), u1 = at(f), u2 = at(f + 1);
-    if (v >= 0.0) return u0 + 0.5 * koren(ratio(u0 - um, u1 - u0)) * (u1 - u0);
-    return u1 + 0.5 * koren(ratio(u1 - u2, u0 - u1)) * (u0 - u1);
+    if (v >= 0.0) return u0 + 0.5 * koren_slope(u0 - um, u1 - u0);
+    return u1 + 0.5 * koren_slope(u1 - u2, u0 - u1);
 }
 
 // fluxes through the faces of one axis: electrons F_e = -mu_e E n_e^face - D_e dn_e/dx (zero
@@ -217,20 +261,22 @@ __global__ void k_sd_flux(Grid g, int axis, const double* phi, double phi0, cons
                           double mu_e, double mu_p, double D_e, double* Fe, double* Fp) {
     const int m = axis == 0 ? g.nx : axis == 1 ? g.ny : g.nz;
     const int64_t stride = axis == 0 ? 1 : axis == 1 ? (int64_t)g.nx : (int64_t)g.nx * g.ny;
-    const int64_t lines = g.n() / m;
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int lines = (int)(g.n() / m);
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= lines * (m + 1)) return;
-    const int64_t line = e / (m + 1);
-    const int f = (int)(e % (m + 1));
+    const int line = e / (m + 1);
+    const int f = e - line * (m + 1);
     // first cell of the line: the other two indices
-    int64_t c0;
+    int c0;
     if (axis == 0) c0 = line * g.nx;
-    else if (axis == 1) c0 = (line / g.nx) * ((int64_t)g.nx * g.ny) + line % g.nx;
-    else c0 = line;
-    const double E = face_E(phi, c0 + (int64_t)(f - 1) * stride, stride, f, m, g.h, axis == 2, phi0);
+    else if (axis == 1) {
+        const int k = line / g.nx;
+        c0 = k * (g.nx * g.ny) + (line - k * g.nx);
+    } else c0 = line;
+    const double E = face_E(phi, c0 + (int64_t)(f - 1) * stride, stride, f, m, g.ih, axis == 2, phi0);
     const double ve = -mu_e * E, vp = mu_p * E;
     double fe = ve * muscl(ne, c0, stride, f, m, ve);
-    if (f > 0 && f < m) fe += -D_e * (ne[c0 + (int64_t)f * stride] - ne[c0 + (int64_t)(f - 1) * stride]) / g.h;
+    if (f > 0 && f < m) fe += -D_e * (ne[c0 + (int64_t)f * stride] - ne[c0 + (int64_t)(f - 1) * stride]) * g.ih;
     Fe[e] = fe;
     Fp[e] = vp * muscl(np, c0, stride, f, m, vp);
 }
@@ -239,14 +285,43 @@ __global__ void k_sd_flux(Grid g, int axis, const double* phi, double phi0, cons
 __global__ void k_sd_div(Grid g, const double* Fex, const double* Fey, const double* Fez, const double* Fpx,
                          const double* Fpy, const double* Fpz, const double* Si, const double* Sph, double* dne,
                          double* dnp) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= g.n()) return;
-    const int i = (int)(c % g.nx), j = (int)((c / g.nx) % g.ny), k = (int)(c / ((int64_t)g.nx * g.ny));
+    int i, j, k;
+    cell_ijk(g, c, i, j, k);
     const int64_t lx = (int64_t)k * g.ny + j, ly = (int64_t)k * g.nx + i, lz = (int64_t)j * g.nx + i;
     const int64_t fx = lx * (g.nx + 1) + i, fy = ly * (g.ny + 1) + j, fz = lz * (g.nz + 1) + k;
-    const double src = Si[c] + (Sph ? Sph[c] : 0.0);
-    dne[c] = -((Fex[fx + 1] - Fex[fx]) + (Fey[fy + 1] - Fey[fy]) + (Fez[fz + 1] - Fez[fz])) / g.h + src;
-    dnp[c] = -((Fpx[fx + 1] - Fpx[fx]) + (Fpy[fy + 1] - Fpy[fy]) + (Fpz[fz + 1] - Fpz[fz])) / g.h + src;
+    const double src = Si[c] + (Sph ? Sph[c] : 0.0), rh = g.ih;
+    dne[c] = -((Fex[fx + 1] - Fex[fx]) + (Fey[fy + 1] - Fey[fy]) + (Fez[fz + 1] - Fez[fz])) * rh + src;
+    dnp[c] = -((Fpx[fx + 1] - Fpx[fx]) + (Fpy[fy + 1] - Fpy[fy]) + (Fpz[fz + 1] - Fpz[fz])) * rh + src;
+}
+
+// the region's sources in its own order (x fastest), those below thr * max S_i dropped (the
+// maximum read from the device: the bits of a non-negative double order like integers)
+__global__ void k_sd_gather(Grid g, const int* reg, const double* Si, const unsigned long long* maxbits, double thr,
+                            double* out) {
+    const int rx = reg[1] - reg[0], ry = reg[3] - reg[2], rz = reg[5] - reg[4];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rx * ry * rz) return;
+    const int i = reg[0] + (int)(e % rx), j = reg[2] + (int)((e / rx) % ry), k = reg[4] + (int)(e / ((int64_t)rx * ry));
+    const double v = Si[((int64_t)k * g.ny + j) * g.nx + i];
+    const double cut = maxbits ? thr * __longlong_as_double((long long)*maxbits) : 0.0;
+    out[e] = v >= cut ? v : 0.0;
+}
+// S_ph of the region back into the grid (the rest was zeroed)
+__global__ void k_sd_scatter(Grid g, const int* reg, const double* in, double* Sph) {
+    const int rx = reg[1] - reg[0], ry = reg[3] - reg[2], rz = reg[5] - reg[4];
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)rx * ry * rz) return;
+    const int i = reg[0] + (int)(e % rx), j = reg[2] + (int)((e / rx) % ry), k = reg[4] + (int)(e / ((int64_t)rx * ry));
+    Sph[((int64_t)k * g.ny + j) * g.nx + i] = in[e];
+}
+__global__ void k_sd_absmax(const double* x, int64_t n, unsigned long long* out) {
+    double m = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[e]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
 }
 
 // b[e] += v for the n cells of the top layer (its Dirichlet term)
@@ -273,8 +348,12 @@ struct Streamer {
     cudaStream_t st = nullptr;
     int num_sms = 1;
     DevBuf ne, np, ne0, np0, dne, dnp, phi, Emag, Si, Sph, F[6], red;
+    DevBuf reg, rsrc, rout, rmax;   // local evaluation: region bounds, its sources and S_ph, max S_i
+    int64_t nreg = 0;               // cells of the region (0: the whole grid, no gather)
     std::vector<Grid> lv;           // multigrid levels, lv[0] = the grid
-    std::vector<DevBuf> u, b, r;    // per level: unknown, right-hand side, residual
+    std::vector<DevBuf> u, b, r;    // level 0: phi, right-hand side, residual (FP64); then the
+                                    // FP32 error equation per level: unknown, right-hand side, residual
+    DevBuf e0, rhs0, t0;            // level 0 of the FP32 error equation
     int last_cycles = 0;
     double last_res = 0.0;
 };
@@ -294,26 +373,32 @@ int mg_norm(Streamer& S, const double* x, int64_t n, double* out) {
     return KIFMM_OK;
 }
 
+// one FP32 V-cycle on the error equation A e = rhs of level l (l = 0: e0 / rhs0 / t0, else
+// u[l] / b[l] / r[l]), from e = 0 below level 0 (the caller zeroes e0)
 int vcycle(Streamer& S, int l) {
     const Grid& g = S.lv[l];
     const int64_t n = g.n();
+    float* e = l == 0 ? ptr<float>(S.e0) : ptr<float>(S.u[l]);
+    const float* rhs = l == 0 ? ptr<float>(S.rhs0) : ptr<float>(S.b[l]);
+    float* res = l == 0 ? ptr<float>(S.t0) : ptr<float>(S.r[l]);
     const unsigned half = nbs((int64_t)((g.nx + 1) / 2) * g.ny * g.nz, 256);
-    if (l + 1 == (int)S.lv.size()) {   // coarsest: enough sweeps to converge on a few hundred cells
-        k_mg_coarse_solve<<<1, 1024, 0, S.st>>>(g, ptr<double>(S.u[l]), ptr<double>(S.b[l]), 40 * (g.nx + g.ny + g.nz));
+    if (l + 1 == (int)S.lv.size()) {   // coarsest: sweeps in one block
+        // (the V-cycle needs the coarse error reduced by about its own factor, not solved exactly)
+        k_mg_coarse_solve<float><<<1, 1024, 0, S.st>>>(g, e, rhs, 8 * (g.nx + g.ny + g.nz));
         KF_LAUNCH();
         return KIFMM_OK;
     }
     for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color) k_mg_smooth<<<half, 256, 0, S.st>>>(g, ptr<double>(S.u[l]), ptr<double>(S.b[l]), color);
-    k_mg_residual<<<nbs(n, 256), 256, 0, S.st>>>(g, ptr<double>(S.u[l]), ptr<double>(S.b[l]), ptr<double>(S.r[l]));
+        for (int color = 0; color < 2; ++color) k_mg_smooth<float><<<half, 256, 0, S.st>>>(g, e, rhs, color);
+    k_mg_residual<float><<<nbs(n, 256), 256, 0, S.st>>>(g, e, rhs, res, nullptr);
     const Grid& cg = S.lv[l + 1];
-    k_mg_restrict<<<nbs(cg.n(), 256), 256, 0, S.st>>>(g, cg, ptr<double>(S.r[l]), ptr<double>(S.b[l + 1]));
-    KF_CUDA(cudaMemsetAsync(S.u[l + 1].p, 0, cg.n() * 8, S.st));
+    k_mg_restrict<float><<<nbs(cg.n(), 256), 256, 0, S.st>>>(g, cg, res, ptr<float>(S.b[l + 1]));
+    KF_CUDA(cudaMemsetAsync(S.u[l + 1].p, 0, cg.n() * 4, S.st));
     KF_LAUNCH();
     KF_TRY(vcycle(S, l + 1));
-    k_mg_prolong<<<nbs(n, 256), 256, 0, S.st>>>(g, cg, ptr<double>(S.u[l + 1]), ptr<double>(S.u[l]));
+    k_mg_prolong<float><<<nbs(n, 256), 256, 0, S.st>>>(g, cg, ptr<float>(S.u[l + 1]), e);
     for (int s = 0; s < 2; ++s)
-        for (int color = 0; color < 2; ++color) k_mg_smooth<<<half, 256, 0, S.st>>>(g, ptr<double>(S.u[l]), ptr<double>(S.b[l]), color);
+        for (int color = 0; color < 2; ++color) k_mg_smooth<float><<<half, 256, 0, S.st>>>(g, e, rhs, color);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -324,12 +409,16 @@ int poisson(Streamer& S) {
     double bn = 0.0, rn = 0.0;
     KF_TRY(mg_norm(S, ptr<double>(S.b[0]), g.n(), &bn));
     int c = 0;
-    for (;;) {
-        k_mg_residual<<<nbs(g.n(), 256), 256, 0, S.st>>>(g, ptr<double>(S.u[0]), ptr<double>(S.b[0]), ptr<double>(S.r[0]));
+    for (;;) {   // iterative refinement: the residual in FP64, the correction by an FP32 V-cycle
+        k_mg_residual<double><<<nbs(g.n(), 256), 256, 0, S.st>>>(g, ptr<double>(S.u[0]), ptr<double>(S.b[0]),
+                                                                   ptr<double>(S.r[0]), ptr<float>(S.rhs0));
         KF_LAUNCH();
         KF_TRY(mg_norm(S, ptr<double>(S.r[0]), g.n(), &rn));
         if (!(bn > 0.0) || rn <= S.prm.mg_tol * bn || c >= S.prm.mg_max_cycles) break;
+        KF_CUDA(cudaMemsetAsync(S.e0.p, 0, g.n() * 4, S.st));
         KF_TRY(vcycle(S, 0));
+        k_mg_correct<<<nbs(g.n(), 256), 256, 0, S.st>>>(g.n(), ptr<float>(S.e0), ptr<double>(S.u[0]));
+        KF_LAUNCH();
         ++c;
     }
     S.last_cycles = c;
@@ -355,7 +444,26 @@ int rhs(Streamer& S, const double* ne, const double* np, double* dne, double* dn
     KF_LAUNCH();
     const double* sph = nullptr;
     if (S.plan) {   // the photoionization sum of S_i (Eq. (integral) with C = prm.C)
-        KF_TRY(kifmm_eval(S.plan, S.Si.p, S.Sph.p, KIFMM_F64, S.prm.C));
+        const bool thr = S.prm.threshold > 0.0;
+        if (thr) {
+            KF_CUDA(cudaMemsetAsync(S.rmax.p, 0, 8, st));
+            k_sd_absmax<<<(unsigned)std::min<int64_t>(nbs(n, 256), 4LL * S.num_sms), 256, 0, st>>>(
+                ptr<double>(S.Si), n, ptr<unsigned long long>(S.rmax));
+            KF_LAUNCH();
+        }
+        if (S.nreg > 0 || thr) {   // local and / or thresholded: gather, evaluate, scatter
+            const int64_t nr = S.nreg > 0 ? S.nreg : n;
+            k_sd_gather<<<nbs(nr, 256), 256, 0, st>>>(g, ptr<int>(S.reg), ptr<double>(S.Si),
+                                                       thr ? ptr<unsigned long long>(S.rmax) : nullptr,
+                                                       S.prm.threshold, ptr<double>(S.rsrc));
+            KF_LAUNCH();
+            KF_TRY(kifmm_eval(S.plan, S.rsrc.p, S.rout.p, KIFMM_F64, S.prm.C));
+            KF_CUDA(cudaMemsetAsync(S.Sph.p, 0, n * 8, st));
+            k_sd_scatter<<<nbs(nr, 256), 256, 0, st>>>(g, ptr<int>(S.reg), ptr<double>(S.rout), ptr<double>(S.Sph));
+            KF_LAUNCH();
+        } else {
+            KF_TRY(kifmm_eval(S.plan, S.Si.p, S.Sph.p, KIFMM_F64, S.prm.C));
+        }
         sph = ptr<double>(S.Sph);
     }
     const int m[3] = {g.nx, g.ny, g.nz};
@@ -372,11 +480,13 @@ int rhs(Streamer& S, const double* ne, const double* np, double* dne, double* dn
 }
 
 void release(Streamer& S) {
-    for (DevBuf* d : {&S.ne, &S.np, &S.ne0, &S.np0, &S.dne, &S.dnp, &S.phi, &S.Emag, &S.Si, &S.Sph, &S.red})
+    for (DevBuf* d : {&S.ne, &S.np, &S.ne0, &S.np0, &S.dne, &S.dnp, &S.phi, &S.Emag, &S.Si, &S.Sph, &S.red, &S.reg,
+                      &S.rsrc, &S.rout, &S.rmax})
         dev_free(*d);
     for (DevBuf& d : S.F) dev_free(d);
     for (auto* v : {&S.u, &S.b, &S.r})
         for (DevBuf& d : *v) dev_free(d);
+    for (DevBuf* d : {&S.e0, &S.rhs0, &S.t0}) dev_free(*d);
 }
 
 }  // namespace
@@ -412,14 +522,26 @@ int streamer_create(streamer_t* out, int nx, int ny, int nz, double h, const str
         return KIFMM_ERR_ARG;
     }
     *out = nullptr;
-    if (plan && kifmm_plan_internal(plan)->n_real != (int64_t)nx * ny * nz) {
-        set_error("streamer_create: the plan's point count differs from the grid's cells");
+    const int* rg = prm->region;
+    const bool has_reg = rg[0] || rg[1] || rg[2] || rg[3] || rg[4] || rg[5];
+    if (has_reg && !(rg[0] >= 0 && rg[0] < rg[1] && rg[1] <= nx && rg[2] >= 0 && rg[2] < rg[3] && rg[3] <= ny &&
+                     rg[4] >= 0 && rg[4] < rg[5] && rg[5] <= nz)) {
+        set_error("streamer_create: region must be cell ranges inside the grid");
+        return KIFMM_ERR_ARG;
+    }
+    if (!(prm->threshold >= 0.0 && prm->threshold < 1.0)) {
+        set_error("streamer_create: threshold must lie in [0, 1)");
+        return KIFMM_ERR_ARG;
+    }
+    const int64_t ncell = has_reg ? (int64_t)(rg[1] - rg[0]) * (rg[3] - rg[2]) * (rg[5] - rg[4]) : (int64_t)nx * ny * nz;
+    if (plan && kifmm_plan_internal(plan)->n_real != ncell) {
+        set_error("streamer_create: the plan's point count differs from the grid's (or the region's) cells");
         return KIFMM_ERR_ARG;
     }
     auto* h_ = new (std::nothrow) streamer_s();
     if (!h_) return KIFMM_ERR_OOM;
     Streamer& S = h_->s;
-    S.g = Grid{nx, ny, nz, h};
+    S.g = make_grid(nx, ny, nz, h);
     S.prm = *prm;
     S.plan = plan;
     S.st = (cudaStream_t)stream;
@@ -427,12 +549,12 @@ int streamer_create(streamer_t* out, int nx, int ny, int nz, double h, const str
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&S.num_sms, cudaDevAttrMultiProcessorCount, dev);
     S.num_sms = std::max(S.num_sms, 1);
-    // multigrid levels: halve while every extent is even and at least 8, then the coarsest
+    // multigrid levels: halve while every extent is even and at least 4, then the coarsest
     S.lv.push_back(S.g);
-    while (S.lv.back().nx % 2 == 0 && S.lv.back().ny % 2 == 0 && S.lv.back().nz % 2 == 0 && S.lv.back().nx >= 8 &&
-           S.lv.back().ny >= 8 && S.lv.back().nz >= 8) {
+    while (S.lv.back().nx % 2 == 0 && S.lv.back().ny % 2 == 0 && S.lv.back().nz % 2 == 0 && S.lv.back().nx >= 4 &&
+           S.lv.back().ny >= 4 && S.lv.back().nz >= 4) {
         const Grid& f = S.lv.back();
-        S.lv.push_back(Grid{f.nx / 2, f.ny / 2, f.nz / 2, 2.0 * f.h});
+        S.lv.push_back(make_grid(f.nx / 2, f.ny / 2, f.nz / 2, 2.0 * f.h));
     }
     auto fail = [&](int rc) {
         release(S);
@@ -454,14 +576,27 @@ int streamer_create(streamer_t* out, int nx, int ny, int nz, double h, const str
     const int64_t faces[3] = {n / nx * (nx + 1), n / ny * (ny + 1), n / nz * (nz + 1)};
     for (int a = 0; a < 6 && !rc; ++a) rc = dev_alloc(S.F[a], faces[a % 3] * 8);
     if (!rc) rc = dev_alloc(S.red, (size_t)2 * S.num_sms * 8 + 64);
+    {   // local / thresholded evaluation: the region's bounds (the whole grid without one)
+        const int whole[6] = {0, nx, 0, ny, 0, nz};
+        const int* r6 = has_reg ? rg : whole;
+        S.nreg = has_reg ? ncell : 0;
+        if (!rc) rc = dev_alloc(S.reg, 6 * sizeof(int));
+        if (!rc && cudaMemcpy(S.reg.p, r6, 6 * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) rc = KIFMM_ERR_CUDA;
+        if (!rc) rc = dev_alloc(S.rsrc, ncell * 8);
+        if (!rc) rc = dev_alloc(S.rout, ncell * 8);
+        if (!rc) rc = dev_alloc(S.rmax, 8);
+    }
     S.u.resize(S.lv.size());
     S.b.resize(S.lv.size());
     S.r.resize(S.lv.size());
-    for (size_t l = 0; l < S.lv.size() && !rc; ++l) {
-        rc = dev_alloc(S.u[l], S.lv[l].n() * 8);
-        if (!rc) rc = dev_alloc(S.b[l], S.lv[l].n() * 8);
-        if (!rc) rc = dev_alloc(S.r[l], S.lv[l].n() * 8);
+    for (size_t l = 0; l < S.lv.size() && !rc; ++l) {   // level 0 FP64, the error equation's levels FP32
+        const size_t w = l == 0 ? 8 : 4;
+        rc = dev_alloc(S.u[l], S.lv[l].n() * w);
+        if (!rc) rc = dev_alloc(S.b[l], S.lv[l].n() * w);
+        if (!rc) rc = dev_alloc(S.r[l], S.lv[l].n() * w);
     }
+    for (DevBuf* d : {&S.e0, &S.rhs0, &S.t0})
+        if (!rc) rc = dev_alloc(*d, n * 4);
     if (rc) return fail(rc);
     for (DevBuf* d : {&S.ne, &S.np, &S.phi, &S.Sph, &S.u[0]})
         if (cudaMemsetAsync(d->p, 0, n * 8, S.st) != cudaSuccess) return fail(KIFMM_ERR_CUDA);

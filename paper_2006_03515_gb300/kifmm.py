@@ -74,7 +74,8 @@ class _Info(ctypes.Structure):
 class _StreamerParams(ctypes.Structure):
     _fields_ = [("p", ctypes.c_double), ("phi0", ctypes.c_double), ("mu_e", ctypes.c_double),
                 ("mu_p", ctypes.c_double), ("D_e", ctypes.c_double), ("C", ctypes.c_double),
-                ("mg_tol", ctypes.c_double), ("mg_max_cycles", ctypes.c_int)]
+                ("mg_tol", ctypes.c_double), ("mg_max_cycles", ctypes.c_int), ("region", ctypes.c_int * 6),
+                ("threshold", ctypes.c_double)]
 
 
 class _TuneEntry(ctypes.Structure):
@@ -655,8 +656,9 @@ def photo_solve_batch(plans, model, Is, Ss=None, C=None, tol=0.05, k_samples=256
 class Streamer:
     """The streamer time loop of Sec. 5, Eq. (eM) (streamer_* in kifmm.h): fields [z][y][x] on
     nx x ny x nz cubic cells of edge h (cm), CUDA float64 tensors of nx ny nz entries. plan: a
-    Plan over the cell centres in that order (the FMM of S_ph) or None; params: overrides of
-    the paper's values (p, phi0, mu_e, mu_p, D_e, C, mg_tol, mg_max_cycles)."""
+    Plan over the cell centres in that order (the FMM of S_ph; over the region's cells when
+    region = (x0, x1, y0, y1, z0, z1) is given) or None; params: overrides of the paper's
+    values (p, phi0, mu_e, mu_p, D_e, C, mg_tol, mg_max_cycles, threshold)."""
 
     def __init__(self, nx, ny, nz, h, p=760.0, plan=None, stream=None, **params):
         import torch
@@ -664,6 +666,10 @@ class Streamer:
         prm = _StreamerParams()
         L.streamer_default_params(ctypes.byref(prm), float(p))
         for k, v in params.items():
+            if k == "region":
+                for q in range(6):
+                    prm.region[q] = int(v[q])
+                continue
             if not hasattr(prm, k):
                 raise KeyError(k)
             setattr(prm, k, v)

@@ -134,6 +134,39 @@ def test_without_photoionization_and_argument_checks(kf):
     pl.close()
 
 
+def test_local_and_thresholded_photoionization(kf):
+    # S_ph over a sub-box from the sources inside it above 1e-3 of the largest (Sec. 5.1's
+    # remark): the plan over the region's cells; zero outside; the oracle KIFMM of the same
+    # thresholded region sources
+    ne, npi = _state(5)
+    reg = (2, 14, 3, 13, 4, 20)
+    sub = (slice(reg[4], reg[5]), slice(reg[2], reg[3]), slice(reg[0], reg[1]))
+    rp = _centres(NX, NY, NZ, H).reshape(NZ, NY, NX, 3)[sub].reshape(-1, 3)
+    a, b = K.absorption_coefficients(150.0)
+    C = SD.params()["C"]
+    op = KF.plan(rp, np.full(len(rp), H), 64, 4, a, b)
+    pl = kf.Plan(_dev(rp), H, 64, 4, a, b, precision="fp64")
+    s = kf.Streamer(NX, NY, NZ, H, plan=pl, mg_tol=1e-12, region=reg, threshold=1e-3)
+
+    def sph(Si):
+        loc = Si[sub].ravel().copy()
+        loc[loc < 1e-3 * Si.max()] = 0.0
+        out = np.zeros_like(Si)
+        out[sub] = KF.evaluate(op, loc, C).reshape(out[sub].shape)
+        return out
+    s.set(_dev(ne), _dev(npi))
+    dne, _ = s.rhs()
+    _, _, _, Sph = s.get()
+    want_e, _, aux = SD.rhs(ne, npi, H, SD.params(), sph)
+    got = Sph.cpu().numpy()
+    assert _rel(got, aux["Sph"]) <= 1e-8 and np.all(got[:reg[4]] == 0.0)
+    assert _rel(dne.cpu().numpy(), want_e) <= 1e-8
+    s.close()
+    pl.close()
+    with pytest.raises(kf.KifmmError):   # a region outside the grid
+        kf.Streamer(NX, NY, NZ, H, region=(0, NX + 1, 0, NY, 0, NZ))
+
+
 def test_double_headed_streamers_advance(kf):
     # Sec. 5's two Gaussian seeds in a 0.5 x 0.5 x 1 cm gap at 52 kV, 32 x 32 x 64 cells, the
     # mixed-form FMM for S_ph (a lattice plan, padded), 20 steps of 2.5e-3 ns
