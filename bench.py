@@ -122,9 +122,12 @@ def parse():
     ap.add_argument("--sd-n", type=int, default=128, help="streamer grid: n x n x 2n cells of the 0.5 x 0.5 x 1 cm gap")
     ap.add_argument("--sd-steps", type=int, default=10, help="timed streamer steps")
     ap.add_argument("--no-configs", action="store_true", help="skip the other target settings")
+    ap.add_argument("--streamer-only", action="store_true",
+                    help="measure only the streamer time loop (one JSON object; for its launch list)")
     ap.add_argument("--surrogate-only", action="store_true",
                     help="measure only the surrogate and print its record (profiling runs)")
     ap.add_argument("--sno-n", type=int, default=64, help="surrogate grid cells per axis")
+    ap.add_argument("--sno-batch", type=int, default=32, help="surrogate inference batch (fields per forward pass)")
     ap.add_argument("--sno-fields", type=int, default=256, help="KIFMM-labelled training fields")
     ap.add_argument("--sno-heldout", type=int, default=128, help="held-out fields of the surrogate")
     ap.add_argument("--sno-train-s", type=float, default=15.0, help="surrogate training budget per model (s)")
@@ -616,7 +619,7 @@ def surrogate_bench(args, dev, stream, peaks):
     import torch
     from paper_2006_03515_gb300 import kifmm, surrogate
     from paper_2006_03515_gb300 import workloads as W
-    n, width, modes, layers, proj, B = args.sno_n, 32, 12, 4, 64, 32
+    n, width, modes, layers, proj, B = args.sno_n, 32, 12, 4, 64, args.sno_batch
     modes = min(modes, n // 2)
     plan, pts, C = surrogate.grid_plan(n, leaf=64, m0=6, p_torr=760.0, p_o2=150.0, stream=stream,
                                        surface_radii=(1.05, 2.95))
@@ -757,6 +760,16 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.streamer_only:
+        import torch
+        from paper_2006_03515_gb300 import build as pb
+        pb.build()
+        dev = torch.device("cuda", 0)
+        stream = torch.cuda.Stream(device=dev)
+        with torch.cuda.stream(stream):
+            rec = streamer_bench(args, dev, stream)
+        print(json.dumps({"streamer": rec}), flush=True)
+        return 0
     if args.surrogate_only:
         import torch
         from paper_2006_03515_gb300 import build as pb
