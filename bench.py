@@ -44,19 +44,19 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 296.56e6 + 16.29e6, "per_point_scaled": False,
+    "M2L": {"bytes": 165.945e6 + 13.516e6, "per_point_scaled": False,
             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                    "02e9ac452138dfe01856ae207ea80db09e4f48af65ad8afb9b3937696c6e36ad"},
+                    "b8ad63f18f5197f235580d11661f1bafca743abe240f207bc031e4042d8595d5"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
     "P2P": {"bytes": 14.20e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
             "src": {"paper_2006_03515_gb300/csrc/eval.cu":
                     "27add4c5c6f89bc5081df57c5cc3f95224a7882530864fae517b59636790b1c6"},
             "profile": "profiles/k_p2p_mixed_uniform64.md"},
-    "NEAR": {"bytes": 3.96e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
+    "NEAR": {"bytes": 3.958e6, "per_point_scaled": True, "n_profiled": 64 ** 3,
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
-                     "02e9ac452138dfe01856ae207ea80db09e4f48af65ad8afb9b3937696c6e36ad",
+                     "b8ad63f18f5197f235580d11661f1bafca743abe240f207bc031e4042d8595d5",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "631c78d191c65df6df2bce139946743a8c7c9a6d4d7e61b272428b0d93ea169b"},
+                     "815ca76ae373545c9e2856c6d7bb61e192f730d0c71330b6bcd5ba5082fbc84e"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
@@ -635,18 +635,20 @@ def surrogate_bench(args, dev, stream, peaks):
            "period": (3 * n) // 2, "train_fields": args.sno_fields, "heldout_fields": args.sno_heldout,
            "labels": "GPU KIFMM, mixed, m0 6, leaf 64, surfaces 1.05 / 2.95 r", "datagen_s": gen_s}
 
+    tb = min(8, B)   # training and held-out batches (within the model's batch)
+
     def held(M):
-        e = np.array(surrogate.rel_errors(M, Uh, Th, batch=8))
+        e = np.array(surrogate.rel_errors(M, Uh, Th, batch=tb))
         return {"mean": float(e.mean()), "p90": float(np.percentile(e, 90)), "max": float(e.max())}
 
     def train(M, budget, lr):
         t1 = time.perf_counter()
         steps, hist = 0, []
         while time.perf_counter() - t1 < budget:
-            hist += surrogate.train(M, U, T, steps=20, batch=8, lr=lr, seed=steps)
+            hist += surrogate.train(M, U, T, steps=20, batch=tb, lr=lr, seed=steps)
             steps += 20
         torch.cuda.synchronize(dev)
-        return {"steps": steps, "s": time.perf_counter() - t1, "fields_per_s": 8 * steps / (time.perf_counter() - t1),
+        return {"steps": steps, "s": time.perf_counter() - t1, "fields_per_s": tb * steps / (time.perf_counter() - t1),
                 "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-5:]))}
 
     # random start, trained for the budget

@@ -767,10 +767,11 @@ __global__ void __launch_bounds__(256) k_apply(const T* __restrict__ Op, int64_t
         }
     }
 }
-// out[dst(col)][row] (+)= sum over z (in order) of part[z][col][row]
+// out[dst(col)][row] (+)= sum over z of part[z][col][row], z in order, a thread per output
+// (consecutive threads read consecutive rows of each partial)
 template <class TO>
 __global__ void k_apply_finish(const TO* __restrict__ part, int nz, int64_t ncp, int nrp, int count, int Mo,
-                               const int32_t* dst, int64_t base, TO* out, int ldo, int accumulate) {
+                                 const int32_t* dst, int64_t base, TO* out, int ldo, int accumulate) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (int64_t)count * Mo) return;
     const int64_t col = e / Mo;
@@ -1645,7 +1646,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
             // split the terms so that the launch is one whole wave (4 blocks of 256 per SM at 64
             // registers): a partial second wave costs a wave of latency
-            const int nz = std::max(1, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms) / tiles));
+            const int nz = std::max(1, std::min(16, std::min(8 * (int)nbk(p.ops[l + 1].rank, AP_TK), (4 * p.num_sms) / tiles)));
             // (Chebyshev: the parents' node weights W^P = sum_o M_o W^{C_o}, straight into c)
             RUN((launch_apply<T, double, double>(st, sel<T>(p.ops[l].Mc, p.ops[l].Mc32), R, S, p.ops[l + 1].rank,
                                                  ptr<int32_t>(LL.par_kids), ptr<int32_t>(LL.parents), 0, LL.n_par,
@@ -1664,7 +1665,7 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
         } else if (LL.n_up > 0) {   // c = Sigma^+ U^T chk; the K range split over z on small levels (cu is zeroed)
             constexpr int RMd = ApplyShape<double>::RM, CNd = ApplyShape<double>::CN;
             const int tiles = (int)(nbk(LL.n_up, 16 * CNd) * nbk(p.ops[l].rank, 16 * RMd));
-            const int nz = std::max(1, std::min((S + AP_TK - 1) / AP_TK, (2 * p.num_sms + tiles - 1) / tiles));
+            const int nz = std::max(1, std::min(16, std::min((S + AP_TK - 1) / AP_TK, (2 * p.num_sms + tiles - 1) / tiles)));
             RUN(launch_apply<double>(st, ptr<double>(p.ops[l].G1), S, p.ops[l].rank, S, ptr<int32_t>(LL.upb),
                                      ptr<int32_t>(LL.upb), 0, LL.n_up, ptr<double>(p.chk), S, cu, R, 0, 1, 0, nullptr,
                                      nz, 0, &p.apply_part, &nl));

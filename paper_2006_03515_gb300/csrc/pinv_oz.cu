@@ -37,8 +37,8 @@ constexpr int OZ_W = 6;          // bits per slice
 constexpr int OZ_N = 48;         // operator rows per CTA (MMA N)
 constexpr int OZ_M = 128;        // boxes per CTA (MMA M)
 constexpr int OZ_KC = 64;        // FP16 per K-chunk (one 128-byte swizzle row)
-constexpr int OZ_NS = 3;         // box-slice stages (K of one chunk: 8, the operator image leaving room)
-__host__ __device__ constexpr int oz_stages(int nk) { return nk == 1 ? 8 : OZ_NS; }
+constexpr int OZ_NS = 3;         // box-slice stages (eight for K of one chunk measured no faster)
+__host__ __device__ constexpr int oz_stages(int nk) { return OZ_NS + 0 * nk; }
 constexpr int OZ_THREADS = 320;  // warps 0-7 epilogue, 8 producer, 9 MMA
 
 __host__ __device__ inline int oz_kp(int S) { return (S + 31) / 32 * 32; }   // K padded to a multiple of 32
@@ -135,6 +135,38 @@ __global__ void k_oz_slice_boxes(const double* chk, int S, const int32_t* boxes,
 __device__ __forceinline__ double pow2d(int k) {
     if (k >= -1022 && k <= 1023) return __longlong_as_double((long long)(k + 1023) << 52);
     return ldexp(1.0, k);
+}
+
+// (hi 2^24 + lo) 2^e as the nearest double (ties to even), hi and lo the exact level sums, in
+// integer arithmetic: the 128-bit integer is rounded to 53 significant bits and the exponent
+// and sign assembled into the bits (this GPU's FP64 pipe is scarce); results outside the
+// normal range take the FP64 expression, which rounds the same sum once as well
+__device__ __forceinline__ double oz_combine(long long hi, long long lo, int e) {
+    const __int128 m = ((__int128)hi << 24) + (__int128)lo;
+    if (m == 0) return 0.0;
+    const bool neg = m < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-m) : (unsigned __int128)m;
+    const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
+    const int nbits = ah ? 128 - __clzll((long long)ah) : 64 - __clzll((long long)al);
+    int shift = nbits - 53;
+    unsigned long long q;
+    if (shift > 0) {
+        q = (unsigned long long)(a >> shift);
+        const unsigned __int128 rem = a & (((unsigned __int128)1 << shift) - 1);
+        const unsigned __int128 half = (unsigned __int128)1 << (shift - 1);
+        if (rem > half || (rem == half && (q & 1ull))) ++q;
+        if (q == (1ull << 53)) {   // the rounding carried into a new bit
+            q >>= 1;
+            ++shift;
+        }
+    } else {
+        q = (unsigned long long)a << (-shift);
+    }
+    const int biased = shift + 52 + e + 1023;   // value = q 2^(shift + e), q in [2^52, 2^53)
+    if (biased <= 0 || biased >= 2047) return fma((double)hi, pow2d(e + 24), (double)lo * pow2d(e));
+    const unsigned long long bits =
+        ((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) | (q & ((1ull << 52) - 1));
+    return __longlong_as_double((long long)bits);
 }
 
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
@@ -309,9 +341,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
                 for (int c = 0; c < 24; ++c) {
                     if (r0 + 24 * half + c >= rank) break;
-                    // c = 2^{e_b + e_r} (hi 2^-36 + lo 2^-60)
+                    // c = 2^{e_b + e_r} (hi 2^-36 + lo 2^-60) = (hi 2^24 + lo) 2^{E - 60}
                     const int E = e_b + ers[24 * half + c];
-                    o[c] = fma((double)hi[c], pow2d(E - 36), (double)lo[c] * pow2d(E - 60));
+                    o[c] = oz_combine(hi[c], lo[c], E - 60);
                 }
             }
         }
