@@ -137,38 +137,6 @@ __device__ __forceinline__ double pow2d(int k) {
     return ldexp(1.0, k);
 }
 
-// (hi 2^24 + lo) 2^e as the nearest double (ties to even), hi and lo the exact level sums, in
-// integer arithmetic: the 128-bit integer is rounded to 53 significant bits and the exponent
-// and sign assembled into the bits (this GPU's FP64 pipe is scarce); results outside the
-// normal range take the FP64 expression, which rounds the same sum once as well
-__device__ __forceinline__ double oz_combine(long long hi, long long lo, int e) {
-    const __int128 m = ((__int128)hi << 24) + (__int128)lo;
-    if (m == 0) return 0.0;
-    const bool neg = m < 0;
-    const unsigned __int128 a = neg ? (unsigned __int128)(-m) : (unsigned __int128)m;
-    const unsigned long long ah = (unsigned long long)(a >> 64), al = (unsigned long long)a;
-    const int nbits = ah ? 128 - __clzll((long long)ah) : 64 - __clzll((long long)al);
-    int shift = nbits - 53;
-    unsigned long long q;
-    if (shift > 0) {
-        q = (unsigned long long)(a >> shift);
-        const unsigned __int128 rem = a & (((unsigned __int128)1 << shift) - 1);
-        const unsigned __int128 half = (unsigned __int128)1 << (shift - 1);
-        if (rem > half || (rem == half && (q & 1ull))) ++q;
-        if (q == (1ull << 53)) {   // the rounding carried into a new bit
-            q >>= 1;
-            ++shift;
-        }
-    } else {
-        q = (unsigned long long)a << (-shift);
-    }
-    const int biased = shift + 52 + e + 1023;   // value = q 2^(shift + e), q in [2^52, 2^53)
-    if (biased <= 0 || biased >= 2047) return fma((double)hi, pow2d(e + 24), (double)lo * pow2d(e));
-    const unsigned long long bits =
-        ((unsigned long long)neg << 63) | ((unsigned long long)biased << 52) | (q & ((1ull << 52) - 1));
-    return __longlong_as_double((long long)bits);
-}
-
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
                  "l"(src), "r"(bytes), "r"(mbar)
@@ -341,9 +309,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1)
 #pragma unroll
                 for (int c = 0; c < 24; ++c) {
                     if (r0 + 24 * half + c >= rank) break;
-                    // c = 2^{e_b + e_r} (hi 2^-36 + lo 2^-60) = (hi 2^24 + lo) 2^{E - 60}
+                    // c = 2^{e_b + e_r} (hi 2^-36 + lo 2^-60)
                     const int E = e_b + ers[24 * half + c];
-                    o[c] = oz_combine(hi[c], lo[c], E - 60);
+                    o[c] = fma((double)hi[c], pow2d(E - 36), (double)lo[c] * pow2d(E - 60));
                 }
             }
         }
