@@ -468,82 +468,84 @@ int pad_to_lattice(cudaStream_t st, const double* pts, int64_t n, double h, int 
     *n_total = n;
     root[3] = 0.0;   // (no lattice root unless the points are a full box grid)
     DevBuf part, rootb, flags;
-    KF_TRY(dev_alloc(part, RED_BLOCKS * 6 * sizeof(double)));
-    KF_TRY(dev_alloc(rootb, 8 * sizeof(double)));
-    KF_TRY(dev_alloc(flags, 4 * sizeof(int)));
     auto release = [&]() {
         for (DevBuf* d : {&part, &rootb, &flags}) dev_free(*d);
     };
-    KF_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), st));
-    root_partial<<<RED_BLOCKS, RED_T, 0, st>>>(pts, nullptr, h, h, h, n, ptr<double>(part), ptr<int>(flags));
-    KF_LAUNCH();
-    root_final<<<1, 32, 0, st>>>(ptr<double>(part), RED_BLOCKS, ptr<double>(rootb));
-    KF_LAUNCH();
-    double r8[8];
-    int hflags[4];
-    KF_CUDA(cudaMemcpyAsync(r8, rootb.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
-    KF_CUDA(cudaMemcpyAsync(hflags, flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    KF_CUDA(cudaStreamSynchronize(st));
-    if (hflags[0]) {   // non-finite input: the tree build reports it
-        release();
-        return KIFMM_OK;
-    }
-    int64_t ext[3], pad[3];
-    double prod = 1.0;
-    for (int k = 0; k < 3; ++k) {
-        const double e = (r8[4 + k] - r8[k]) / h;
-        ext[k] = (int64_t)std::llround(e);
-        if (!(std::fabs(e - (double)ext[k]) <= 1e-6 * std::max(1.0, e)) || ext[k] < 1) {
-            release();
+    // the body returns through the error macros; the work buffers are released on every path
+    auto body = [&]() -> int {
+        KF_TRY(dev_alloc(part, RED_BLOCKS * 6 * sizeof(double)));
+        KF_TRY(dev_alloc(rootb, 8 * sizeof(double)));
+        KF_TRY(dev_alloc(flags, 4 * sizeof(int)));
+        KF_CUDA(cudaMemsetAsync(flags.p, 0, 4 * sizeof(int), st));
+        root_partial<<<RED_BLOCKS, RED_T, 0, st>>>(pts, nullptr, h, h, h, n, ptr<double>(part), ptr<int>(flags));
+        KF_LAUNCH();
+        root_final<<<1, 32, 0, st>>>(ptr<double>(part), RED_BLOCKS, ptr<double>(rootb));
+        KF_LAUNCH();
+        double r8[8];
+        int hflags[4];
+        KF_CUDA(cudaMemcpyAsync(r8, rootb.p, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaMemcpyAsync(hflags, flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        if (hflags[0]) {   // non-finite input: the tree build reports it
             return KIFMM_OK;
         }
-        prod *= (double)ext[k];
-        pad[k] = (ext[k] + 2 * nc - 1) / (2 * nc) * (2 * nc);
-    }
-    if (prod != (double)n) {   // not every cell of the box: no padding
-        release();
+        int64_t ext[3], pad[3];
+        double prod = 1.0;
+        for (int k = 0; k < 3; ++k) {
+            const double e = (r8[4 + k] - r8[k]) / h;
+            ext[k] = (int64_t)std::llround(e);
+            if (!(std::fabs(e - (double)ext[k]) <= 1e-6 * std::max(1.0, e)) || ext[k] < 1) {
+                return KIFMM_OK;
+            }
+            prod *= (double)ext[k];
+            pad[k] = (ext[k] + 2 * nc - 1) / (2 * nc) * (2 * nc);
+        }
+        if (prod != (double)n) {   // not every cell of the box: no padding
+            return KIFMM_OK;
+        }
+        k_lattice_member<<<nblk(n, 256), 256, 0, st>>>(pts, n, r8[0], r8[1], r8[2], h, ext[0], ext[1], ext[2],
+                                                        ptr<int>(flags) + 1);
+        KF_LAUNCH();
+        KF_CUDA(cudaMemcpyAsync(hflags, flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        KF_CUDA(cudaStreamSynchronize(st));
+        if (hflags[1]) return KIFMM_OK;
+        // the root: origin at the grid's corner, side nc h 2^L >= every padded extent
+        int64_t cells = nc;
+        while (cells < std::max(pad[0], std::max(pad[1], pad[2]))) cells *= 2;
+        root[0] = r8[0];
+        root[1] = r8[1];
+        root[2] = r8[2];
+        root[3] = (double)cells * h;
+        const int64_t nt = pad[0] * pad[1] * pad[2];
+        if (nt >= (int64_t)1 << 31) {
+            root[3] = 0.0;
+            return KIFMM_OK;
+        }
+        const int64_t nv = nt - n;
+        if (nv == 0) return KIFMM_OK;   // already on the lattice: the root alone
+        KF_TRY(dev_alloc(out, (size_t)nt * 3 * sizeof(double)));
+        KF_CUDA(cudaMemcpyAsync(out.p, pts, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        if (nv > 0) {   // the padding cells in z, y, x order, after the caller's points
+            std::vector<double> v;
+            v.reserve((size_t)nv * 3);
+            for (int64_t z = 0; z < pad[2]; ++z)
+                for (int64_t y = 0; y < pad[1]; ++y)
+                    for (int64_t x = 0; x < pad[0]; ++x) {
+                        if (x < ext[0] && y < ext[1] && z < ext[2]) continue;
+                        v.push_back(r8[0] + ((double)x + 0.5) * h);
+                        v.push_back(r8[1] + ((double)y + 0.5) * h);
+                        v.push_back(r8[2] + ((double)z + 0.5) * h);
+                    }
+            KF_CUDA(cudaMemcpyAsync(static_cast<double*>(out.p) + 3 * n, v.data(), v.size() * sizeof(double),
+                                    cudaMemcpyHostToDevice, st));
+            KF_CUDA(cudaStreamSynchronize(st));   // v is released on return
+        }
+        *n_total = nt;
         return KIFMM_OK;
-    }
-    k_lattice_member<<<nblk(n, 256), 256, 0, st>>>(pts, n, r8[0], r8[1], r8[2], h, ext[0], ext[1], ext[2],
-                                                    ptr<int>(flags) + 1);
-    KF_LAUNCH();
-    KF_CUDA(cudaMemcpyAsync(hflags, flags.p, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-    KF_CUDA(cudaStreamSynchronize(st));
+    };
+    const int rc = body();
     release();
-    if (hflags[1]) return KIFMM_OK;
-    // the root: origin at the grid's corner, side nc h 2^L >= every padded extent
-    int64_t cells = nc;
-    while (cells < std::max(pad[0], std::max(pad[1], pad[2]))) cells *= 2;
-    root[0] = r8[0];
-    root[1] = r8[1];
-    root[2] = r8[2];
-    root[3] = (double)cells * h;
-    const int64_t nt = pad[0] * pad[1] * pad[2];
-    if (nt >= (int64_t)1 << 31) {
-        root[3] = 0.0;
-        return KIFMM_OK;
-    }
-    const int64_t nv = nt - n;
-    if (nv == 0) return KIFMM_OK;   // already on the lattice: the root alone
-    KF_TRY(dev_alloc(out, (size_t)nt * 3 * sizeof(double)));
-    KF_CUDA(cudaMemcpyAsync(out.p, pts, (size_t)n * 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (nv > 0) {   // the padding cells in z, y, x order, after the caller's points
-        std::vector<double> v;
-        v.reserve((size_t)nv * 3);
-        for (int64_t z = 0; z < pad[2]; ++z)
-            for (int64_t y = 0; y < pad[1]; ++y)
-                for (int64_t x = 0; x < pad[0]; ++x) {
-                    if (x < ext[0] && y < ext[1] && z < ext[2]) continue;
-                    v.push_back(r8[0] + ((double)x + 0.5) * h);
-                    v.push_back(r8[1] + ((double)y + 0.5) * h);
-                    v.push_back(r8[2] + ((double)z + 0.5) * h);
-                }
-        KF_CUDA(cudaMemcpyAsync(static_cast<double*>(out.p) + 3 * n, v.data(), v.size() * sizeof(double),
-                                cudaMemcpyHostToDevice, st));
-        KF_CUDA(cudaStreamSynchronize(st));   // v is released on return
-    }
-    *n_total = nt;
-    return KIFMM_OK;
+    return rc;
 }
 
 int build_tree(Plan& p, const double* pts, const double* h, double uh, const kifmm_opts& o) {
