@@ -330,7 +330,10 @@ int kifmm_get_upward(kifmm_plan_t plan, double* c, int* stride);
 
 /* Per-phase device times (ms) of the last kifmm_eval when KIFMM_TIMING=1 in
  * the environment at plan time: [scatter, P2M, M2M, M2L, S2L+L2L+DC2DE,
- * L2P+M2P, P2P]. Returns the number of phases written (<= cap). */
+ * L2P+M2P, P2P] and, where the tensor-core lattice near field ran its sums on
+ * the plan's own second stream beside the far field, an eighth entry: the
+ * span of those sums (P2P then holds the join and the output combination).
+ * Returns the number of phases written (<= cap). */
 int kifmm_get_phase_times(kifmm_plan_t plan, float* ms, int cap);
 
 /* ---- learned surrogate: 3D spectral neural operator ---- */

@@ -79,6 +79,11 @@ static void free_plan(Plan* p) {
     if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
     for (auto s : p->lanes) cudaStreamDestroy(s);
     for (auto e : p->lane_ev) cudaEventDestroy(e);
+    if (p->near_st) cudaStreamDestroy(p->near_st);
+    for (auto e : p->near_ev)
+        if (e) cudaEventDestroy(e);
+    for (auto e : p->near_tev)
+        if (e) cudaEventDestroy(e);
     delete p;
 }
 
@@ -294,6 +299,9 @@ int kifmm_plan(kifmm_plan_t* out, const double* points, int64_t n, const double*
         p->timing = true;
         for (auto& e : p->ev)
             if (cudaEventCreate(&e) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
+        if (p->near_st)
+            for (auto& e : p->near_tev)
+                if (cudaEventCreate(&e) != cudaSuccess) return fail(KIFMM_ERR_CUDA);
     }
     if (cudaStreamSynchronize(p->stream) != cudaSuccess) {
         set_error(std::string("kifmm_plan: ") + cudaGetErrorString(cudaGetLastError()));
@@ -317,6 +325,10 @@ int kifmm_eval(kifmm_plan_t h, const void* I, void* S, int dtype, double C) {
         cudaEventSynchronize(p.ev[7]);
         for (int k = 0; k < 7; ++k) cudaEventElapsedTime(&p.phase_ms[k], p.ev[k], p.ev[k + 1]);
         p.n_phases = 7;
+        if (p.near_forked && p.near_tev[1]) {   // the near sums on their own stream, beside the far field
+            cudaEventElapsedTime(&p.phase_ms[7], p.near_tev[0], p.near_tev[1]);
+            p.n_phases = 8;
+        }
     }
     return KIFMM_OK;
 }

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include <cooperative_groups.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.cuh"
@@ -782,6 +783,146 @@ __global__ void k_apply_finish(const TO* __restrict__ part, int nz, int64_t ncp,
     TO* o = out + b * ldo + row;
     *o = accumulate ? *o + sum : sum;
 }
+
+// M2M of the mixed surface form (Eq. (m2m)): chk[parents[p]][s] = sum over the octants o and
+// k < K of Mc_o[s][k] c[kids[o][p]][k] (FP32 arithmetic on FP64 coefficients), for S <= 160
+// check points and child ranks K <= 128. A cluster of 8 blocks takes TN parents, block o of
+// it the octant-o term for every check row (a thread holds 4 rows rq + 40 i x 4 parents
+// pq + TN/4 j). The block copies all its K / 32 operator chunks into shared memory at once
+// (asynchronous 16-byte copies) and loads and rounds the children's chunks into registers
+// beside them, so it waits for memory once; both operands are stored along k. Each block
+// then leaves its term in its shared memory and, after a cluster barrier, sums one eighth of
+// the outputs over the 8 blocks' terms in octant order through distributed shared memory:
+// the result does not depend on scheduling. Mc is [8][S][R] with R a multiple of 32, so each
+// chunk's operator rows lie inside it; columns past the child rank multiply zeros.
+constexpr int MM_TK = 32, MM_TM = 160, MM_NS = 4, MM_LD = MM_TK + 4, MM_LDP = MM_TM + 1;
+template <int TN>
+constexpr size_t m2m_f32_smem() { return MM_NS * (size_t)(MM_TM + TN) * MM_LD * sizeof(float); }
+
+template <int TN>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
+    k_m2m_f32(const float* __restrict__ Mc, int S, int R, int K, const int32_t* __restrict__ kids,
+              const int32_t* __restrict__ parents, int count, const double* __restrict__ c, int ldc,
+              double* __restrict__ out, int ldo) {
+    constexpr int NT = 10 * TN, PG = TN / 4, NA = MM_TM * (MM_TK / 4) / NT, NB = (TN * MM_TK + NT - 1) / NT;
+    static_assert(MM_TM * (MM_TK / 4) % NT == 0, "whole operator copies per thread");
+    static_assert(TN * MM_LDP <= MM_NS * MM_TM * MM_LD, "the term fits the operator stages");
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) float mm_sm[];
+    float* As = mm_sm;                          // [MM_NS][MM_TM][MM_LD]; afterwards the term [TN][MM_LDP]
+    float* Bs = mm_sm + MM_NS * MM_TM * MM_LD;  // [MM_NS][TN][MM_LD]
+    const int tid = threadIdx.x, o = (int)cl.block_rank(), p0 = (blockIdx.x / 8) * TN;
+    const int rq = tid / PG, pq = tid % PG;
+    const int nit = (K + MM_TK - 1) / MM_TK;   // 1..MM_NS
+    for (int e = tid; e < MM_NS * MM_TM * MM_LD; e += NT)   // rows past S stay zero
+        As[e] = 0.f;
+    __syncthreads();
+    // every chunk's copies and loads are issued at once: one memory latency a block
+    const float* A = Mc + (int64_t)o * S * R;
+#pragma unroll
+    for (int it = 0; it < MM_NS; ++it) {   // row e / 8, quad e % 8: a row's 128 bytes per 8 lanes
+        if (it < nit) {
+#pragma unroll
+            for (int i = 0; i < NA; ++i) {
+                const int e = tid + NT * i, row = e >> 3, q = e & 7;
+                if (row < S) {
+                    const uint32_t d = (uint32_t)__cvta_generic_to_shared(As + (it * MM_TM + row) * MM_LD + 4 * q);
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
+                                 "l"(A + (int64_t)row * R + it * MM_TK + 4 * q)
+                                 : "memory");
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    float rb[MM_NS][NB];   // parent e / 32, k e % 32: a child's row per warp
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int e = tid + NT * i, pp = e >> 5;
+        const int ch = (pp < TN && p0 + pp < count) ? kids[(int64_t)o * count + p0 + pp] : -1;
+        const double* src = c + (int64_t)max(ch, 0) * ldc + (e & 31);
+#pragma unroll
+        for (int it = 0; it < MM_NS; ++it) {
+            const int k = it * MM_TK + (e & 31);
+            rb[it][i] = (ch >= 0 && k < K) ? (float)src[it * MM_TK] : 0.f;
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < MM_NS; ++it)
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int e = tid + NT * i, pp = e >> 5, k = e & 31;
+            if (pp < TN) Bs[(it * TN + pp) * MM_LD + k] = rb[it][i];
+        }
+    float acc[4][4] = {};
+#pragma unroll
+    for (int it = 0; it < MM_NS; ++it) {
+        if (it >= nit) break;
+        // chunk it's copies are done once at most MM_NS - 1 - it later groups are pending
+        if (it == 0) asm volatile("cp.async.wait_group 3;" ::: "memory");
+        else if (it == 1) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else if (it == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        const float* Ab = As + (it * MM_TM + rq) * MM_LD;
+        const float* Bb = Bs + (it * TN + pq) * MM_LD;
+#pragma unroll
+        for (int kk = 0; kk < MM_TK; kk += 4) {
+            float4 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(Ab + 40 * i * MM_LD + kk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const float4*>(Bb + PG * j * MM_LD + kk);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float v = acc[i][j];
+                    v = fmaf(a[i].x, b[j].x, v);
+                    v = fmaf(a[i].y, b[j].y, v);
+                    v = fmaf(a[i].z, b[j].z, v);
+                    acc[i][j] = fmaf(a[i].w, b[j].w, v);
+                }
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // every thread is done with the stages before the term overwrites them
+    float* P = As;   // this octant's term, [parent][row]
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) P[(pq + PG * j) * MM_LDP + rq + 40 * i] = acc[i][j];
+    cl.sync();
+    const float* Pr[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) Pr[r] = cl.map_shared_rank(P, r);
+    const int np = min(TN, count - p0);
+    for (int e = o * NT + tid; e < np * S; e += 8 * NT) {   // parent e / S, row e % S
+        const int pp = e / S, row = e - pp * S;
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v += Pr[r][pp * MM_LDP + row];
+        out[(int64_t)parents[p0 + pp] * ldo + row] = (double)v;
+    }
+    cl.sync();   // no block leaves while another reads its term
+}
+
+template <int TN>
+static int launch_m2m_f32(cudaStream_t st, const float* Mc, int S, int R, int K, const int32_t* kids,
+                          const int32_t* parents, int count, const double* c, int ldc, double* out, int ldo) {
+    static bool configured = false;   // one attribute per instantiation (its size never changes)
+    if (!configured) {
+        KF_CUDA(cudaFuncSetAttribute(k_m2m_f32<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)m2m_f32_smem<TN>()));
+        configured = true;
+    }
+    k_m2m_f32<TN><<<8u * nbk(count, TN), 10 * TN, m2m_f32_smem<TN>(), st>>>(Mc, S, R, K, kids, parents, count, c,
+                                                                           ldc, out, ldo);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
 // tile shapes: FP64 48 x 32 (3 x 2 per thread; ranks near 141 pad to 144), FP32 64 x 64
 template <class T> struct ApplyShape;
 template <> struct ApplyShape<double> { static constexpr int RM = 3, CN = 2; };
@@ -1641,6 +1782,13 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                                                      p.cheb ? R : S, S);
             KF_LAUNCH();
             ++nl;
+        } else if (LL.n_par > 0 && mixed && S <= MM_TM && p.ops[l + 1].rank <= MM_NS * MM_TK) {
+            // chk[P] = sum_o Mc_{l,o} c[C_o], FP32
+            // (32 parents a cluster where that gives every SM two blocks, else 16)
+            auto* fn = 8 * nbk(LL.n_par, 32) >= 2u * p.num_sms ? launch_m2m_f32<32> : launch_m2m_f32<16>;
+            KF_TRY(fn(st, ptr<float>(p.ops[l].Mc32), S, R, p.ops[l + 1].rank, ptr<int32_t>(LL.par_kids),
+                      ptr<int32_t>(LL.parents), LL.n_par, cu, R, ptr<double>(p.chk), S));
+            ++nl;
         } else if (LL.n_par > 0) {   // chk[P] = sum_o Mc_{l,o} c[C_o]; the 8 octant terms split over z on small levels
             constexpr int RMt = ApplyShape<T>::RM, CNt = ApplyShape<T>::CN;
             const int tiles = (int)(nbk(LL.n_par, 16 * CNt) * nbk(S, 16 * RMt));
@@ -1799,14 +1947,39 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
                                                         n, p.n_real, ptr<double>(p.Isort), ptr<double>(p.q));
     KF_LAUNCH();
     ++nl;
+    // fork: the near sums (tensor-core lattice near field) read only q, so they run on their
+    // own stream beside the far field and are joined before the output combination
+    const bool fork = mixed && p.near_tc && p.near_st;
+    p.near_forked = fork;
+    if (fork) {
+        KF_CUDA(cudaEventRecord(p.near_ev[0], st));
+        KF_CUDA(cudaStreamWaitEvent(p.near_st, p.near_ev[0], 0));
+        if (p.timing && p.near_tev[0]) KF_CUDA(cudaEventRecord(p.near_tev[0], p.near_st));
+        int rc = near_tc_contract(p, p.near_st, nl);
+        if (p.timing && p.near_tev[1]) cudaEventRecord(p.near_tev[1], p.near_st);
+        // the join is recorded whatever happened, so that a capture never holds an open fork
+        cudaError_t e = cudaEventRecord(p.near_ev[1], p.near_st);
+        if (rc == KIFMM_OK && e != cudaSuccess) {
+            set_error(std::string("near-field fork: ") + cudaGetErrorString(e));
+            rc = KIFMM_ERR_CUDA;
+        }
+        if (rc != KIFMM_OK) {
+            cudaStreamWaitEvent(st, p.near_ev[1], 0);
+            return rc;
+        }
+    }
     mark(p, 1);
+    int far_rc = KIFMM_OK;
     if (t.nlevels > 2) {
-        if (mixed) KF_TRY(run_far<float>(p, E, nl));
-        else KF_TRY(run_far<double>(p, E, nl));
+        far_rc = mixed ? run_far<float>(p, E, nl) : run_far<double>(p, E, nl);
     } else {
         mark(p, 2);
         mark(p, 3);
         mark(p, 4);
+    }
+    if (far_rc != KIFMM_OK) {
+        if (fork) cudaStreamWaitEvent(st, p.near_ev[1], 0);
+        return far_rc;
     }
     mark(p, 5);
     // ---- targets: local expansion and W list, then the near field, self term and output
@@ -1843,7 +2016,9 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     }
     mark(p, 6);
     if (mixed && p.near_tc) {   // uniform lattice: near field as per-offset contractions on the tensor cores
-        KF_TRY(near_tc_eval(p, ptr<double>(p.far), C, S_out, dtype, nl));
+        if (fork) KF_CUDA(cudaStreamWaitEvent(st, p.near_ev[1], 0));   // join
+        else KF_TRY(near_tc_contract(p, st, nl));
+        KF_TRY(near_tc_finish(p, ptr<double>(p.far), C, S_out, dtype, nl));
     } else {
         size_t smem = (size_t)(mixed ? P2Q_CHUNK : P2P_CHUNK) * 16;
         const int32_t* uo = ptr<int32_t>(p.lists[0].off);

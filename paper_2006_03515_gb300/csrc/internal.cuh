@@ -244,6 +244,12 @@ struct Plan {
     // concurrent batch lanes owned by this plan: streams, and events [0] fork, [1 + j] join
     std::vector<cudaStream_t> lanes;
     std::vector<cudaEvent_t> lane_ev;
+    // the near-field contraction's own stream (tensor-core lattice near field): it needs only
+    // the sorted weights, so it runs beside the far field; events [0] fork, [1] join
+    cudaStream_t near_st = nullptr;
+    cudaEvent_t near_ev[2] = {nullptr, nullptr};
+    cudaEvent_t near_tev[2] = {nullptr, nullptr};   // its start and end (phase timing)
+    bool near_forked = false;    // the last evaluation ran the near sums on near_st
 };
 
 // tree.cu
@@ -287,7 +293,8 @@ int launch_tc_translate(cudaStream_t st, const M2LTables& tabs, int R, const int
                         const void* clo, const int* cexp, float* d, int accum, int* err);
 // near_tc.cu: near field on a uniform lattice
 int near_tc_plan(Plan& p);
-int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
+int near_tc_contract(Plan& p, cudaStream_t st, int64_t& nl);   // the near sums into nf_near on st
+int near_tc_finish(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl);
 int lat_s2m(Plan& p);   // chk of every leaf (lat_far plans)
 int lat_l2p(Plan& p);   // far of every point from the leaves' d (lat_far plans)
 int lat_up_plan(Plan& p);   // M = G1 P for the leaves' FP64-exact upward solve (after the slice set-up)

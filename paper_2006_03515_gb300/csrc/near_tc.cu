@@ -529,6 +529,13 @@ int near_tc_plan(Plan& p) {
     p.nf_level = lf;
     p.nf_ntiles = ntiles;
     p.near_tc = true;
+    // the near sums need only the sorted weights: their own stream lets them fill the SMs the
+    // small upward levels leave idle (KIFMM_NEAR_STREAM=same keeps them on the plan's stream)
+    const char* ns = std::getenv("KIFMM_NEAR_STREAM");
+    if (!(ns && std::string(ns) == "same") && !p.near_st) {
+        KF_CUDA(cudaStreamCreateWithFlags(&p.near_st, cudaStreamNonBlocking));
+        for (auto& e : p.near_ev) KF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     return KIFMM_OK;
 }
 
@@ -588,9 +595,9 @@ int lat_up_apply(Plan& p, double* cu, int64_t& nl) {
     return KIFMM_OK;
 }
 
-int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl) {
-    cudaStream_t st = p.stream;
-    const int64_t n = p.tree.n;
+// the per-offset contractions of the near field into nf_near, on stream st (they read only the
+// sorted weights q)
+int near_tc_contract(Plan& p, cudaStream_t st, int64_t& nl) {
     KF_TRY(m2l_tc_split(st, ptr<double>(p.q), p.nleaves, p.nf_R, p.nf_qhi.p, p.nf_qlo.p, ptr<int>(p.nf_qexp)));
     ++nl;
     M2LTables tabs{};
@@ -601,6 +608,13 @@ int near_tc_eval(Plan& p, const double* far, double C, void* out, int dtype, int
                          ptr<int32_t>(p.nf_utab), ptr<int32_t>(p.nf_slots), p.nf_qhi.p, p.nf_qlo.p, ptr<int>(p.nf_qexp),
                          ptr<float>(p.nf_near), ptr<int>(p.err)));
     ++nl;
+    return KIFMM_OK;
+}
+
+// out = far + near + self term, on the plan's stream once nf_near is complete there
+int near_tc_finish(Plan& p, const double* far, double C, void* out, int dtype, int64_t& nl) {
+    cudaStream_t st = p.stream;
+    const int64_t n = p.tree.n;
     const float* fst = p.lat_l2p_tc && p.tree.nlevels > 2 ? ptr<float>(p.lat_fst) : nullptr;
     if (dtype == KIFMM_F64)
         k_nf_finish<double><<<nbn(n, 256), 256, 0, st>>>(ptr<float>(p.nf_near), far, fst, ptr<int32_t>(p.leaves),
