@@ -795,7 +795,8 @@ __global__ void k_apply_finish(const TO* __restrict__ part, int nz, int64_t ncp,
 // the outputs over the 8 blocks' terms in octant order through distributed shared memory:
 // the result does not depend on scheduling. Mc is [8][S][R] with R a multiple of 32, so each
 // chunk's operator rows lie inside it; columns past the child rank multiply zeros.
-constexpr int MM_TK = 32, MM_TM = 160, MM_NS = 4, MM_LD = MM_TK + 4, MM_LDP = MM_TM + 1;
+// (the term's row stride MM_LDP = 4 mod 32: a warp's 8 parents x 4 rows hit 32 banks)
+constexpr int MM_TK = 32, MM_TM = 160, MM_NS = 4, MM_LD = MM_TK + 4, MM_LDP = MM_TM + 4;
 template <int TN>
 constexpr size_t m2m_f32_smem() { return MM_NS * (size_t)(MM_TM + TN) * MM_LD * sizeof(float); }
 
@@ -815,9 +816,7 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
     const int tid = threadIdx.x, o = (int)cl.block_rank(), p0 = (blockIdx.x / 8) * TN;
     const int rq = tid / PG, pq = tid % PG;
     const int nit = (K + MM_TK - 1) / MM_TK;   // 1..MM_NS
-    for (int e = tid; e < MM_NS * MM_TM * MM_LD; e += NT)   // rows past S stay zero
-        As[e] = 0.f;
-    __syncthreads();
+    // (operator rows past S are never copied: they only feed accumulators that are not summed)
     // every chunk's copies and loads are issued at once: one memory latency a block
     const float* A = Mc + (int64_t)o * S * R;
 #pragma unroll
@@ -1704,6 +1703,29 @@ static int launch_apply(cudaStream_t st, const T* Op, int ldop, int Mo, int Ki, 
 
 // Far field: upward pass (FP64 in both forms), M2L, downward pass and the leaves'
 // downward equivalent densities, in type T (FP64 form: double; mixed form: float).
+// the near sums on the plan's second stream, after the work ordered before near_ev[0] on the
+// plan's stream; near_ev[1] is recorded whatever happened, so that a join never waits on an
+// unrecorded event and a capture never holds an open fork
+static int near_fork_launch(Plan& p, int64_t& nl) {
+    cudaError_t e = cudaStreamWaitEvent(p.near_st, p.near_ev[0], 0);
+    int rc = KIFMM_OK;
+    if (e != cudaSuccess) {
+        set_error(std::string("near-field fork: ") + cudaGetErrorString(e));
+        return KIFMM_ERR_CUDA;
+    }
+    p.near_forked = true;
+    p.near_pending = false;
+    if (p.timing && p.near_tev[0]) cudaEventRecord(p.near_tev[0], p.near_st);
+    rc = near_tc_contract(p, p.near_st, nl);
+    if (p.timing && p.near_tev[1]) cudaEventRecord(p.near_tev[1], p.near_st);
+    e = cudaEventRecord(p.near_ev[1], p.near_st);
+    if (rc == KIFMM_OK && e != cudaSuccess) {
+        set_error(std::string("near-field fork: ") + cudaGetErrorString(e));
+        rc = KIFMM_ERR_CUDA;
+    }
+    return rc;
+}
+
 template <class T>
 static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
     Tree& t = p.tree;
@@ -1845,10 +1867,12 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
             tabs.lo[l] = p.ops[l].Tlo.p;
             tabs.sT[l] = p.ops[l].tc_sT;
         }
+        if (p.near_pending) KF_CUDA(cudaEventRecord(p.near_ev[0], st));   // (the near sums need q alone)
         KF_TRY(launch_m2l_tc(st, tabs, R, ptr<int4>(p.tc_tiles), p.tc_ntiles, ptr<int32_t>(p.tc_boxes),
                              ptr<int32_t>(p.vtab), ptr<int32_t>(p.tc_slots), p.chi.p, p.clo.p, ptr<int>(p.cexp),
                              reinterpret_cast<float*>(dd), ptr<int>(p.err)));
         ++nl;
+        if (p.near_pending) KF_TRY(near_fork_launch(p, nl));
     } else {
         for (int l = 2; l < L; ++l) {
             auto& LL = p.lv[l];
@@ -1947,24 +1971,19 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
                                                         n, p.n_real, ptr<double>(p.Isort), ptr<double>(p.q));
     KF_LAUNCH();
     ++nl;
-    // fork: the near sums (tensor-core lattice near field) read only q, so they run on their
-    // own stream beside the far field and are joined before the output combination
+    // the near sums (tensor-core lattice near field) read only q: they run on their own stream
+    // beside the far field and are joined before the output combination. They are forked where
+    // the M2L starts (the far field's run_far issues them after its M2L launch), so that the
+    // earlier-issued M2L takes the SMs first and the near sums fill its last wave and the
+    // downward pass; without a far field, right here.
     const bool fork = mixed && p.near_tc && p.near_st;
-    p.near_forked = fork;
-    if (fork) {
+    p.near_forked = false;
+    p.near_pending = fork && t.nlevels > 2 && !p.near_fork_early;
+    if (fork && !p.near_pending) {
         KF_CUDA(cudaEventRecord(p.near_ev[0], st));
-        KF_CUDA(cudaStreamWaitEvent(p.near_st, p.near_ev[0], 0));
-        if (p.timing && p.near_tev[0]) KF_CUDA(cudaEventRecord(p.near_tev[0], p.near_st));
-        int rc = near_tc_contract(p, p.near_st, nl);
-        if (p.timing && p.near_tev[1]) cudaEventRecord(p.near_tev[1], p.near_st);
-        // the join is recorded whatever happened, so that a capture never holds an open fork
-        cudaError_t e = cudaEventRecord(p.near_ev[1], p.near_st);
-        if (rc == KIFMM_OK && e != cudaSuccess) {
-            set_error(std::string("near-field fork: ") + cudaGetErrorString(e));
-            rc = KIFMM_ERR_CUDA;
-        }
+        const int rc = near_fork_launch(p, nl);
         if (rc != KIFMM_OK) {
-            cudaStreamWaitEvent(st, p.near_ev[1], 0);
+            if (p.near_forked) cudaStreamWaitEvent(st, p.near_ev[1], 0);
             return rc;
         }
     }
@@ -1977,8 +1996,13 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
         mark(p, 3);
         mark(p, 4);
     }
+    if (far_rc == KIFMM_OK && p.near_pending) {   // (the SIMT M2L path: after the far field)
+        KF_CUDA(cudaEventRecord(p.near_ev[0], st));
+        far_rc = near_fork_launch(p, nl);
+    }
+    p.near_pending = false;
     if (far_rc != KIFMM_OK) {
-        if (fork) cudaStreamWaitEvent(st, p.near_ev[1], 0);
+        if (p.near_forked) cudaStreamWaitEvent(st, p.near_ev[1], 0);   // (a capture needs its fork joined)
         return far_rc;
     }
     mark(p, 5);
@@ -2016,7 +2040,7 @@ int run_eval(Plan& p, const void* I, void* S_out, int dtype, double C) {
     }
     mark(p, 6);
     if (mixed && p.near_tc) {   // uniform lattice: near field as per-offset contractions on the tensor cores
-        if (fork) KF_CUDA(cudaStreamWaitEvent(st, p.near_ev[1], 0));   // join
+        if (p.near_forked) KF_CUDA(cudaStreamWaitEvent(st, p.near_ev[1], 0));   // join
         else KF_TRY(near_tc_contract(p, st, nl));
         KF_TRY(near_tc_finish(p, ptr<double>(p.far), C, S_out, dtype, nl));
     } else {

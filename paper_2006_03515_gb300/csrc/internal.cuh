@@ -250,6 +250,8 @@ struct Plan {
     cudaEvent_t near_ev[2] = {nullptr, nullptr};
     cudaEvent_t near_tev[2] = {nullptr, nullptr};   // its start and end (phase timing)
     bool near_forked = false;    // the last evaluation ran the near sums on near_st
+    bool near_pending = false;   // (during an evaluation) the far field is to fork them at its M2L
+    bool near_fork_early = false;   // fork them after the weights' scatter instead (KIFMM_NEAR_STREAM=early)
 };
 
 // tree.cu

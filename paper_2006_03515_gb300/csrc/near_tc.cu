@@ -529,9 +529,11 @@ int near_tc_plan(Plan& p) {
     p.nf_level = lf;
     p.nf_ntiles = ntiles;
     p.near_tc = true;
-    // the near sums need only the sorted weights: their own stream lets them fill the SMs the
-    // small upward levels leave idle (KIFMM_NEAR_STREAM=same keeps them on the plan's stream)
+    // the near sums need only the sorted weights: their own stream lets them fill the SMs that
+    // the M2L's last wave and the downward pass leave idle (KIFMM_NEAR_STREAM=same keeps them
+    // on the plan's stream, =early forks them right after the scatter of the weights)
     const char* ns = std::getenv("KIFMM_NEAR_STREAM");
+    p.near_fork_early = ns && std::string(ns) == "early";
     if (!(ns && std::string(ns) == "same") && !p.near_st) {
         KF_CUDA(cudaStreamCreateWithFlags(&p.near_st, cudaStreamNonBlocking));
         for (auto& e : p.near_ev) KF_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
