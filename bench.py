@@ -44,7 +44,7 @@ METRIC = "S_ph points/s at rel-L2<=1e-6 (FP64 vs mixed KIFMM)"
 # the far-field structure of the 128^3 workload (same M2L launch); the 64^3 capture has its per-leaf
 # shape, and the pair kernel's traffic is compulsory and scales with the point count (x 8 for 128^3).
 PROFILED_TRAFFIC = {
-    "M2L": {"bytes": 165.945e6 + 13.516e6, "per_point_scaled": False,
+    "M2L": {"bytes": 165.548e6 + 12.911e6, "per_point_scaled": False,
             "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
                     "b8ad63f18f5197f235580d11661f1bafca743abe240f207bc031e4042d8595d5"},
             "profile": "profiles/k_m2l_tc_uniform96.md"},
@@ -56,7 +56,7 @@ PROFILED_TRAFFIC = {
              "src": {"paper_2006_03515_gb300/csrc/m2l_tc.cu":
                      "b8ad63f18f5197f235580d11661f1bafca743abe240f207bc031e4042d8595d5",
                      "paper_2006_03515_gb300/csrc/near_tc.cu":
-                     "815ca76ae373545c9e2856c6d7bb61e192f730d0c71330b6bcd5ba5082fbc84e"},
+                     "46fa6d5f4f4f0e56deeea2645bf8112cb643b02e5a7550efca2993006487a7eb"},
              "profile": "profiles/k_m2l_tc_near_uniform64.md"},
 }
 
@@ -881,11 +881,32 @@ def main():
         e2e_val = whole_job_rate(npts, ws, max_over_ranks(sum(e2e_ms) / len(e2e_ms), ws))
         e2e_ok = bool(np.allclose(hSn, S.cpu().numpy(), rtol=1e-12, atol=0))   # split partial sums add atomically
 
+        # the lattice near field alone: its sums overlap the far field on their own stream in
+        # the timed plan, so its roofline is timed on a plan that keeps them on the plan's stream
+        near_alone_ms = None
+        if info.get("near_tensor"):
+            os.environ["KIFMM_NEAR_STREAM"] = "same"
+            try:
+                pn = kifmm.Plan(dpts, float(h[0]), args.leaf, args.m0, a, b, precision=args.precision,
+                                stream=stream, repr=args.repr)
+            finally:
+                del os.environ["KIFMM_NEAR_STREAM"]
+            for _ in range(2):
+                pn.eval(dI, S, C=C)
+            acc = []
+            for k in range(5):
+                flush.fill_(float(k))
+                pn.eval(dI, S, C=C)
+                torch.cuda.synchronize(dev)
+                acc.append(pn.phase_times()[6])
+            near_alone_ms = sum(acc) / len(acc)
+            pn.close()
+
     # (an eighth entry: the near sums' span on their own stream, overlapping the far field;
     # P2P is then the join and the output combination)
     phases = ["scatter", "S2M", "M2M+UC2UE", "M2L", "S2L+L2L+DC2DE", "L2P+M2P", "P2P", "near sums (own stream)"]
     ph_ms = {k: v / args.steps for k, v in zip(phases, phase_sum)}
-    near_ms = ph_ms["P2P"] + ph_ms.get("near sums (own stream)", 0.0)
+    near_ms = near_alone_ms if near_alone_ms else ph_ms["P2P"] + ph_ms.get("near sums (own stream)", 0.0)
     dom = max((k for k in ph_ms if k != "near sums (own stream)"), key=ph_ms.get)
     peaks = measured_peaks()
     sm_clk = 2070.0
@@ -924,12 +945,13 @@ def main():
     }
     if info.get("near_tensor"):   # uniform lattice: near field as 27 per-offset matrices on the tensor cores
         nf_ach = 2.0 * info["p2p_pairs"] / (near_ms * 1e-3) / 1e12
-        roofs["P2P"] = {"kernel": "k_m2l_tc on the 27 near-offset kernel matrices (R = 64 cells per leaf; the time "
-                                  "is the span of the weight split and the contraction on their own stream, which "
-                                  "overlaps the far field, plus the output combination)",
+        roofs["P2P"] = {"kernel": "k_m2l_tc on the 27 near-offset kernel matrices (R = 64 cells per leaf; timed "
+                                  "on a plan that runs the weight split, the contraction and the output "
+                                  "combination on its own stream, not overlapping the far field)",
                         "bound": "tensor", "achieved": nf_ach, "peak": f16_peak / 3.0, "unit": "TFLOP/s",
                         "frac": nf_ach / (f16_peak / 3.0), "traffic": profiled_traffic("NEAR", npts, std),
                         "pairs_per_s": info["p2p_pairs"] / (near_ms * 1e-3),
+                        "ms": near_ms,
                         "peak_source": "of measured: bf16_tflops (dense FP16 = BF16 rate) / 3 MMAs per product; "
                                        "achieved = 2 flop per near pair over the whole near-field phase"}
     if not info["m2l_tensor"]:   # SIMT M2L (FP64 form, or a coefficient count the tensor path does not take)

@@ -76,29 +76,15 @@ __global__ void k_swizzle_T(const double* T, int R, int NK, int nslots, int sT, 
 }
 
 // upward coefficients (FP64, rows of R) -> their FP32 values scaled by 2^{e_b} per box (largest
-// magnitude near 2^14), split into FP16 hi/lo; one warp per box. Rows of at most 32 SPLIT_V
-// values are rounded to FP32 once and held in registers (the FP64 pipe that rounds them is
-// narrow); longer rows are read twice.
-constexpr int SPLIT_V = 8;
+// magnitude near 2^14), split into FP16 hi/lo; one warp per box
 template <class TIN>
 __global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* clo, int* cexp, int ldo) {
     const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (b >= nb) return;
     const TIN* row = c + b * R;
-    const bool held = R <= 32 * SPLIT_V;
-    float v[SPLIT_V];
     float m = 0.f;
-    if (held) {
-#pragma unroll
-        for (int i = 0; i < SPLIT_V; ++i) {
-            const int k = lane + 32 * i;
-            v[i] = k < R ? (float)row[k] : 0.f;
-            m = fmaxf(m, fabsf(v[i]));
-        }
-    } else {
-        for (int k = lane; k < R; k += 32) m = fmaxf(m, fabsf((float)row[k]));
-    }
+    for (int k = lane; k < R; k += 32) m = fmaxf(m, fabsf((float)row[k]));
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     int e = 0;
     if (m > 0.f) {
@@ -106,19 +92,11 @@ __global__ void k_split_c(const TIN* c, int64_t nb, int R, __half* chi, __half* 
         frexpf(m, &ex);             // m = f 2^ex, f in [0.5, 1)
         e = TC_HI_EXP + 1 - ex;     // m 2^e in [2^13, 2^14)
     }
-    auto put = [&](int k, float x) {
+    for (int k = lane; k < ldo; k += 32) {   // (output rows of ldo, zero beyond R)
+        const float x = k < R ? ldexpf((float)row[k], e) : 0.f;
         const __half h = __float2half_rn(x);
         chi[b * ldo + k] = h;
         clo[b * ldo + k] = __float2half_rn(x - __half2float(h));
-    };
-    if (held) {
-#pragma unroll
-        for (int i = 0; i < SPLIT_V; ++i)   // (v is 0 beyond R)
-            if (lane + 32 * i < ldo) put(lane + 32 * i, ldexpf(v[i], e));
-        for (int k = lane + 32 * SPLIT_V; k < ldo; k += 32) put(k, 0.f);
-    } else {
-        for (int k = lane; k < ldo; k += 32)   // (output rows of ldo, zero beyond R)
-            put(k, k < R ? ldexpf((float)row[k], e) : 0.f);
     }
     if (lane == 0) cexp[b] = e;
 }
