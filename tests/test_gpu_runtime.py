@@ -107,3 +107,43 @@ def test_direct_noalloc_checks_its_tensors(kf):
     S = kf.direct_noalloc(dp, h, I, a, b)
     torch.cuda.synchronize()
     assert bool(torch.isfinite(S).all())
+
+
+def test_near_sums_stream_changes_no_bit(kf, monkeypatch):
+    # the lattice near sums run on the plan's second stream (forked at the M2L by default,
+    # after the scatter with KIFMM_NEAR_STREAM=early) or on its own stream (=same): the same
+    # kernels on the same data, so every result is bit-identical, alone, from host buffers
+    # and in a captured batch on two lanes; the forked plans report the near sums' span as an
+    # eighth phase time
+    import torch
+    pts, h, I = W.config_uniform(32)
+    a, b = K.absorption_coefficients(152.0)
+    st = torch.cuda.Stream()
+    monkeypatch.setenv("KIFMM_TIMING", "1")
+    with torch.cuda.stream(st):
+        dp, dI = _dev(pts), _dev(I)
+        plans = {}
+        for mode in ("default", "early", "same"):
+            if mode == "default":
+                monkeypatch.delenv("KIFMM_NEAR_STREAM", raising=False)
+            else:
+                monkeypatch.setenv("KIFMM_NEAR_STREAM", mode)
+            plans[mode] = kf.Plan(dp, float(h[0]), 64, 6, a, b, precision="mixed", stream=st)
+        monkeypatch.delenv("KIFMM_NEAR_STREAM", raising=False)
+        assert all(p.info()["near_tensor"] for p in plans.values())
+        out = {m: p.eval(dI) for m, p in plans.items()}
+        st.synchronize()
+        ref = out["same"].cpu().numpy()
+        for m in ("default", "early"):
+            assert np.array_equal(out[m].cpu().numpy(), ref), m
+            assert len(plans[m].phase_times()) == 8
+        assert len(plans["same"].phase_times()) == 7
+        assert np.array_equal(plans["default"].eval_host(I), ref)
+        Ss = [torch.empty_like(dI) for _ in range(3)]
+        for _ in range(2):   # recorded, then replayed
+            kf.eval_batch([plans["default"], plans["early"], plans["same"]], [dI] * 3, Ss, capture=True, lanes=2)
+            st.synchronize()
+            for s in Ss:
+                assert np.array_equal(s.cpu().numpy(), ref)
+        for p in plans.values():
+            p.close()
