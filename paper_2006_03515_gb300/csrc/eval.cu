@@ -433,7 +433,7 @@ int build_eval_data(Plan& p) {
         // M2M translations likewise: per parent tile the 8 child octants as slots (the tree's child
         // table is the source table), Mc padded to square tables of Mt = max(S, R) rounded to 32,
         // the result staged in FP32 and copied into the parents' check rows (KIFMM_M2M=simt keeps
-        // the SIMT apply). By default only when S <= R: with more check points than coefficients
+        // the FP32 M2M kernels). By default only when S <= R: with more check points than coefficients
         // (S > R) the children's c pass through FP16 hi / lo rows padded to Mt, whose 22 bits
         // relative to each row's largest value cost 1.5e-7 of the mixed form's error at 7.6 Torr
         // (1.03e-6 against 8.9e-7 with the FP32 apply), beyond the 1e-6 gate; KIFMM_M2M=tc takes
