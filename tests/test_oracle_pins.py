@@ -1,8 +1,10 @@
 """The oracle pinned to things other than itself: the constants the paper prints
 (tests/golden), library special functions, closed forms (Frullani's integral, the
 uniformly emitting ball), an independent quadrature of the self-cell integral, brute
-force on tiny inputs, the uniform-grid FFT convolution, symmetries, and the list
-definitions by exhaustive enumeration."""
+force on tiny inputs, the uniform-grid FFT convolution, symmetries, the list
+definitions by exhaustive enumeration, and each translation operator (S2M, M2M, M2L, L2L)
+against the direct sum whose far or local field it represents, with mirrored-index negative
+controls."""
 import math
 
 import numpy as np
@@ -576,3 +578,94 @@ def test_kifmm_comparison_kernels(kind):
     np.testing.assert_allclose(KF.kifmm(pts, h, I, len(pts), 6, a, b, kind=kind), ref, rtol=1e-12)
     got = KF.kifmm(pts, h, I, 8, 6, a, b, kind=kind)
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-3
+
+
+# ---- each translation operator against the direct sum it stands for -------------------------
+# One box's sources, their representation carried through a single operator of the oracle
+# (Eqs. (s2m), (m2m), (m2l), (l2l), (s2l)), and the potential that representation gives at
+# points where it is valid, against the direct sum of the same sources (7.6 Torr, m0 = 6, the
+# default surfaces). The negative controls take the operator of the mirrored octant or offset:
+# an index or sign mistake in the operator tables shows as an O(1) error, far above the bar.
+
+def _ops_case(seed=0):
+    a, b = K.absorption_coefficients(1.52)
+    ops = KF.Operators(1.0, 5, 6, a, b)
+    return a, b, ops, np.random.default_rng(seed)
+
+
+def _maxrel(x, y):
+    return float(np.abs(x - y).max() / np.abs(y).max())
+
+
+def _shell(rng, n, rmin, rmax):
+    d = rng.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1)[:, None]
+    return d * rng.uniform(rmin, rmax, n)[:, None]
+
+
+def _upward(ops, lev, centre, src, q, a, b):
+    """phi^{B,u} of sources in the box of level lev at centre (Eq. (s2m))."""
+    r = 1.0 / 2 ** (lev + 1)
+    chk = KF.kmat(centre + ops.r_out * r * ops.surf, src, a, b) @ q
+    return ops.uc2ue[lev] @ chk
+
+
+@pytest.mark.parametrize("lev", [2, 3])
+def test_s2m_and_m2m_reproduce_the_far_field(lev):
+    a, b, ops, rng = _ops_case(lev)
+    r = 1.0 / 2 ** (lev + 1)
+    s = ops.surf
+    q = rng.uniform(0.5, 1.5, 40)
+    tg = _shell(rng, 200, 4 * r, 6 * r)   # beyond the upward check surface (2.95 r)
+    src = rng.uniform(-r, r, (40, 3))
+    phi = _upward(ops, lev, np.zeros(3), src, q, a, b)
+    direct = KF.kmat(tg, src, a, b) @ q
+    assert _maxrel(KF.kmat(tg, ops.r_in * r * s, a, b) @ phi, direct) < 5e-3
+    for o in range(8):   # a child's density translated to its parent (Eq. (m2m))
+        cc = 0.5 * r * (2.0 * KF._octant(o) - 1.0)
+        srcc = cc + rng.uniform(-r / 2, r / 2, (40, 3))
+        phic = _upward(ops, lev + 1, cc, srcc, q, a, b)
+        direct = KF.kmat(tg, srcc, a, b) @ q
+        got = [KF.kmat(tg, ops.r_in * r * s, a, b) @ (ops.uc2ue[lev] @ (ops.m2m[(lev, oo)] @ phic))
+               for oo in (o, 7 - o)]
+        assert _maxrel(got[0], direct) < 5e-3
+        assert _maxrel(got[1], direct) > 0.3
+
+
+@pytest.mark.parametrize("lev", [2, 3])
+@pytest.mark.parametrize("delta", [(3, 1, -2), (2, 0, 0), (-3, -3, 3), (0, -2, 1)])
+def test_m2l_gives_the_local_field(lev, delta):
+    a, b, ops, rng = _ops_case(7 * lev + sum(delta))
+    r = 1.0 / 2 ** (lev + 1)
+    s = ops.surf
+    q = rng.uniform(0.5, 1.5, 40)
+    off = 2.0 * r * np.array(delta, dtype=np.float64)   # centre of A - centre of B
+    srcA = off + rng.uniform(-r, r, (40, 3))
+    phiA = _upward(ops, lev, off, srcA, q, a, b)
+    x = rng.uniform(-r, r, (100, 3))                     # points of B
+    direct = KF.kmat(x, srcA, a, b) @ q
+    got = []
+    for d in (delta, tuple(-v for v in delta)):
+        phiB = ops.dc2de[lev] @ (ops.m2l[(lev, KF._offset_index(d))] @ phiA)   # Eqs. (m2l), (s2l)
+        got.append(KF.kmat(x, ops.r_out * r * s, a, b) @ phiB)
+    assert _maxrel(got[0], direct) < 2e-2
+    assert _maxrel(got[1], direct) > 0.3
+
+
+@pytest.mark.parametrize("lev", [2, 3])
+def test_l2l_gives_the_childs_local_field(lev):
+    a, b, ops, rng = _ops_case(11 + lev)
+    r = 1.0 / 2 ** (lev + 1)
+    s = ops.surf
+    q = rng.uniform(0.5, 1.5, 40)
+    off = 2.0 * r * np.array((3.0, 0.0, 0.0))
+    srcF = off + rng.uniform(-r, r, (40, 3))           # far from the parent
+    phiP = ops.dc2de[lev] @ (KF.kmat(ops.r_in * r * s, srcF, a, b) @ q)
+    for o in range(8):
+        cc = 0.5 * r * (2.0 * KF._octant(o) - 1.0)
+        x = cc + rng.uniform(-r / 2, r / 2, (100, 3))
+        direct = KF.kmat(x, srcF, a, b) @ q
+        got = [KF.kmat(x, cc + ops.r_out * 0.5 * r * s, a, b) @ (ops.dc2de[lev + 1] @ (ops.l2l[(lev, oo)] @ phiP))
+               for oo in (o, 7 - o)]
+        assert _maxrel(got[0], direct) < 5e-3
+        assert _maxrel(got[1], direct) > 0.3
