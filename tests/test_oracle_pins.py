@@ -301,6 +301,25 @@ def test_kifmm_with_one_leaf_is_the_direct_sum():
     np.testing.assert_allclose(got, ref, rtol=1e-13)
 
 
+def test_kifmm_adaptive_tree_with_w_and_x_lists():
+    # a clustered cloud (half the points in a small sub-cube) makes an adaptive tree whose W
+    # and X lists are not empty; the oracle KIFMM against the brute-force sum, and with the
+    # W or the X list emptied in the plan (a dropped term) the error grows past ten times the bar
+    pts, h, _ = W.random_cloud(2000, 1)
+    pts[:1000] = 0.31 + 0.07 * pts[:1000]
+    I = np.random.default_rng(1).uniform(0.5, 1.5, len(pts))
+    a, b = K.absorption_coefficients(15.2)
+    ref = D.direct_sum(pts, h, I, a, b)
+    p = KF.plan(pts, h, 16, 6, a, b)
+    assert sum(len(x) for x in p["W"]) > 0 and sum(len(x) for x in p["X"]) > 0
+
+    def rel(plan):
+        return np.linalg.norm(KF.evaluate(plan, I) - ref) / np.linalg.norm(ref)
+    assert rel(p) < 2e-3
+    assert rel(dict(p, W=[[] for _ in p["W"]])) > 2e-2
+    assert rel(dict(p, X=[[] for _ in p["X"]])) > 2e-2
+
+
 @pytest.mark.parametrize("m0,tol", [(4, 3e-3), (6, 5e-4), (8, 2e-4)])
 def test_kifmm_accuracy_32cube(m0, tol):
     # 32^3 cells on a 1 cm cube, centred Gaussian, p = 760 Torr, p_O2 = 150 Torr, leaf 64
