@@ -784,67 +784,59 @@ __global__ void k_apply_finish(const TO* __restrict__ part, int nz, int64_t ncp,
     *o = accumulate ? *o + sum : sum;
 }
 
-// M2M of the mixed surface form (Eq. (m2m)): chk[parents[p]][s] = sum over the octants o and
-// k < K of Mc_o[s][k] c[kids[o][p]][k] (FP32 arithmetic on FP64 coefficients), for S <= 160
-// check points and child ranks K <= 128. A cluster of 8 blocks takes TN parents, block o of
-// it the octant-o term for every check row (a thread holds 4 rows rq + 40 i x 4 parents
-// pq + TN/4 j). The block copies all its K / 32 operator chunks into shared memory at once
-// (asynchronous 16-byte copies) and loads and rounds the children's chunks into registers
-// beside them, so it waits for memory once; both operands are stored along k. Each block
-// then leaves its term in its shared memory and, after a cluster barrier, sums one eighth of
-// the outputs over the 8 blocks' terms in octant order through distributed shared memory:
-// the result does not depend on scheduling. Mc is [8][S][R] with R a multiple of 32, so each
-// chunk's operator rows lie inside it; columns past the child rank multiply zeros.
-// (the term's row stride MM_LDP = 4 mod 32: a warp's 8 parents x 4 rows hit 32 banks)
+// FP32 translations of the mixed surface form on the SIMT pipes, for at most 160 output rows
+// and input ranks K <= 128: a block takes one operator (one octant) and TN coefficient rows,
+// and a thread holds 4 output rows rq + 40 i x 4 coefficient rows pq + TN/4 j. The block
+// copies all its K / 32 operator chunks into shared memory at once (asynchronous 16-byte
+// copies) and loads (and rounds) the coefficient chunks into registers beside them, so it
+// waits for memory once; both operands are stored along k (float4 reads, conflict-free).
+// Operators are [8][rows][ld] with ld a multiple of 32, so each chunk's operator rows lie
+// inside them; columns past K multiply zeros.
 constexpr int MM_TK = 32, MM_TM = 160, MM_NS = 4, MM_LD = MM_TK + 4, MM_LDP = MM_TM + 4;
 template <int TN>
 constexpr size_t m2m_f32_smem() { return MM_NS * (size_t)(MM_TM + TN) * MM_LD * sizeof(float); }
-
 template <int TN>
-__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
-    k_m2m_f32(const float* __restrict__ Mc, int S, int R, int K, const int32_t* __restrict__ kids,
-              const int32_t* __restrict__ parents, int count, const double* __restrict__ c, int ldc,
-              double* __restrict__ out, int ldo) {
-    constexpr int NT = 10 * TN, PG = TN / 4, NA = MM_TM * (MM_TK / 4) / NT, NB = (TN * MM_TK + NT - 1) / NT;
+struct MMShape {
+    static constexpr int NT = 10 * TN, PG = TN / 4, NA = MM_TM * (MM_TK / 4) / NT, NB = (TN * MM_TK + NT - 1) / NT;
     static_assert(MM_TM * (MM_TK / 4) % NT == 0, "whole operator copies per thread");
-    static_assert(TN * MM_LDP <= MM_NS * MM_TM * MM_LD, "the term fits the operator stages");
-    namespace cg = cooperative_groups;
-    cg::cluster_group cl = cg::this_cluster();
-    extern __shared__ __align__(16) float mm_sm[];
-    float* As = mm_sm;                          // [MM_NS][MM_TM][MM_LD]; afterwards the term [TN][MM_LDP]
-    float* Bs = mm_sm + MM_NS * MM_TM * MM_LD;  // [MM_NS][TN][MM_LD]
-    const int tid = threadIdx.x, o = (int)cl.block_rank(), p0 = (blockIdx.x / 8) * TN;
-    const int rq = tid / PG, pq = tid % PG;
+};
+
+// acc[i][j] = sum_{k < K} A[rq + 40 i][k] B[pq + TN/4 j][k] for the operator A (rows < Mrows,
+// row stride lda) and the coefficient rows B; bsrc[i] is the row of element e = tid + NT i
+// (coefficient row e / 32), already offset by its k = e % 32, or null for a zero row. Returns
+// with every copy complete and the block synchronised, so the stages may be reused.
+template <int TN, class TI>
+__device__ __forceinline__ void mm_term(const float* __restrict__ A, int Mrows, int lda, int K,
+                                        const TI* const* bsrc, float* As, float* Bs, float (&acc)[4][4]) {
+    using Sh = MMShape<TN>;
+    constexpr int NT = Sh::NT, PG = Sh::PG, NA = Sh::NA, NB = Sh::NB;
+    const int tid = threadIdx.x, rq = tid / PG, pq = tid % PG;
     const int nit = (K + MM_TK - 1) / MM_TK;   // 1..MM_NS
-    // (operator rows past S are never copied: they only feed accumulators that are not summed)
-    // every chunk's copies and loads are issued at once: one memory latency a block
-    const float* A = Mc + (int64_t)o * S * R;
+    // (operator rows past Mrows are never copied: they only feed accumulators that are not used)
 #pragma unroll
     for (int it = 0; it < MM_NS; ++it) {   // row e / 8, quad e % 8: a row's 128 bytes per 8 lanes
         if (it < nit) {
 #pragma unroll
             for (int i = 0; i < NA; ++i) {
                 const int e = tid + NT * i, row = e >> 3, q = e & 7;
-                if (row < S) {
+                if (row < Mrows) {
                     const uint32_t d = (uint32_t)__cvta_generic_to_shared(As + (it * MM_TM + row) * MM_LD + 4 * q);
                     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d),
-                                 "l"(A + (int64_t)row * R + it * MM_TK + 4 * q)
+                                 "l"(A + (int64_t)row * lda + it * MM_TK + 4 * q)
                                  : "memory");
                 }
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    float rb[MM_NS][NB];   // parent e / 32, k e % 32: a child's row per warp
+    float rb[MM_NS][NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
-        const int e = tid + NT * i, pp = e >> 5;
-        const int ch = (pp < TN && p0 + pp < count) ? kids[(int64_t)o * count + p0 + pp] : -1;
-        const double* src = c + (int64_t)max(ch, 0) * ldc + (e & 31);
+        const TI* src = bsrc[i];
 #pragma unroll
         for (int it = 0; it < MM_NS; ++it) {
-            const int k = it * MM_TK + (e & 31);
-            rb[it][i] = (ch >= 0 && k < K) ? (float)src[it * MM_TK] : 0.f;
+            const int k = it * MM_TK + ((tid + NT * i) & 31);
+            rb[it][i] = (src && k < K) ? (float)src[it * MM_TK] : 0.f;
         }
     }
 #pragma unroll
@@ -854,7 +846,6 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
             const int e = tid + NT * i, pp = e >> 5, k = e & 31;
             if (pp < TN) Bs[(it * TN + pp) * MM_LD + k] = rb[it][i];
         }
-    float acc[4][4] = {};
 #pragma unroll
     for (int it = 0; it < MM_NS; ++it) {
         if (it >= nit) break;
@@ -886,7 +877,40 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
         }
     }
     asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();   // every thread is done with the stages before the term overwrites them
+    __syncthreads();   // every thread is done with the stages
+}
+
+// M2M (Eq. (m2m)): chk[parents[p]][s] = sum over the octants o and k < K of
+// Mc_o[s][k] c[kids[o][p]][k] (FP32 arithmetic on FP64 coefficients), S <= 160 check points.
+// A cluster of 8 blocks takes TN parents, block o of it the octant-o term for every check row
+// (mm_term). Each block then leaves its term in its shared memory and, after a cluster
+// barrier, sums one eighth of the outputs over the 8 blocks' terms in octant order through
+// distributed shared memory: the result does not depend on scheduling.
+// (the term's row stride MM_LDP = 4 mod 32: a warp's 8 parents x 4 rows hit 32 banks)
+template <int TN>
+__global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
+    k_m2m_f32(const float* __restrict__ Mc, int S, int R, int K, const int32_t* __restrict__ kids,
+              const int32_t* __restrict__ parents, int count, const double* __restrict__ c, int ldc,
+              double* __restrict__ out, int ldo) {
+    using Sh = MMShape<TN>;
+    constexpr int NT = Sh::NT, PG = Sh::PG, NB = Sh::NB;
+    static_assert(TN * MM_LDP <= MM_NS * MM_TM * MM_LD, "the term fits the operator stages");
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ __align__(16) float mm_sm[];
+    float* As = mm_sm;                          // [MM_NS][MM_TM][MM_LD]; afterwards the term [TN][MM_LDP]
+    float* Bs = mm_sm + MM_NS * MM_TM * MM_LD;  // [MM_NS][TN][MM_LD]
+    const int tid = threadIdx.x, o = (int)cl.block_rank(), p0 = (blockIdx.x / 8) * TN;
+    const int rq = tid / PG, pq = tid % PG;
+    const double* bsrc[NB];   // parent e / 32, k e % 32: a child's row per warp
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int e = tid + NT * i, pp = e >> 5;
+        const int ch = (pp < TN && p0 + pp < count) ? kids[(int64_t)o * count + p0 + pp] : -1;
+        bsrc[i] = ch >= 0 ? c + (int64_t)ch * ldc + (e & 31) : nullptr;
+    }
+    float acc[4][4] = {};
+    mm_term<TN, double>(Mc + (int64_t)o * S * R, S, R, K, bsrc, As, Bs, acc);
     float* P = As;   // this octant's term, [parent][row]
 #pragma unroll
     for (int j = 0; j < 4; ++j)
@@ -907,17 +931,68 @@ __global__ void __cluster_dims__(8, 1, 1) __launch_bounds__(10 * TN, 2)
     cl.sync();   // no block leaves while another reads its term
 }
 
+// L2L (Eq. (l2l)) in coefficients, added onto the children's M2L result: for the octant o =
+// blockIdx.y, d[dst[zoff[o] + p]][r] += sum_{k < K} Lo_o[r][k] d[src[zoff[o] + p]][k] for
+// r < Mo (the child level's rank) and the TN entries p of tile blockIdx.x (mm_term). Each
+// output has one term, so no reduction is needed.
+template <int TN>
+__global__ void __launch_bounds__(10 * TN, 2)
+    k_l2l_f32(const float* __restrict__ Lo, int R, int Mo, int K, const int32_t* __restrict__ src,
+              const int32_t* __restrict__ dst, const int32_t* __restrict__ zoff, const float* in, float* out) {
+    using Sh = MMShape<TN>;
+    constexpr int NT = Sh::NT, PG = Sh::PG, NB = Sh::NB;
+    extern __shared__ __align__(16) float mm_sm[];
+    float* As = mm_sm;
+    float* Bs = mm_sm + MM_NS * MM_TM * MM_LD;
+    const int o = blockIdx.y, base = zoff[o], count = zoff[o + 1] - base, p0 = blockIdx.x * TN;
+    if (p0 >= count) return;   // (the whole block: no barrier is pending)
+    const int tid = threadIdx.x, rq = tid / PG, pq = tid % PG;
+    const float* bsrc[NB];   // entry e / 32, k e % 32: a parent's row per warp
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int e = tid + NT * i, pp = e >> 5;
+        bsrc[i] = (pp < TN && p0 + pp < count) ? in + (int64_t)src[base + p0 + pp] * R + (e & 31) : nullptr;
+    }
+    float acc[4][4] = {};
+    mm_term<TN, float>(Lo + (int64_t)o * R * R, Mo, R, K, bsrc, As, Bs, acc);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int p = p0 + pq + PG * j;
+        if (p >= count) continue;
+        float* orow = out + (int64_t)dst[base + p] * R;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (rq + 40 * i < Mo) orow[rq + 40 * i] += acc[i][j];
+    }
+}
+
+template <class F>
+static int mm_configure(F* fn, size_t smem, bool& configured) {
+    if (!configured) {   // one attribute per instantiation (its size never changes)
+        KF_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured = true;
+    }
+    return KIFMM_OK;
+}
+
 template <int TN>
 static int launch_m2m_f32(cudaStream_t st, const float* Mc, int S, int R, int K, const int32_t* kids,
                           const int32_t* parents, int count, const double* c, int ldc, double* out, int ldo) {
-    static bool configured = false;   // one attribute per instantiation (its size never changes)
-    if (!configured) {
-        KF_CUDA(cudaFuncSetAttribute(k_m2m_f32<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)m2m_f32_smem<TN>()));
-        configured = true;
-    }
+    static bool configured = false;
+    KF_TRY(mm_configure(k_m2m_f32<TN>, m2m_f32_smem<TN>(), configured));
     k_m2m_f32<TN><<<8u * nbk(count, TN), 10 * TN, m2m_f32_smem<TN>(), st>>>(Mc, S, R, K, kids, parents, count, c,
                                                                            ldc, out, ldo);
+    KF_LAUNCH();
+    return KIFMM_OK;
+}
+
+template <int TN>
+static int launch_l2l_f32(cudaStream_t st, const float* Lo, int R, int Mo, int K, const int32_t* src,
+                          const int32_t* dst, const int32_t* zoff, int max_count, const float* in, float* out) {
+    static bool configured = false;
+    KF_TRY(mm_configure(k_l2l_f32<TN>, m2m_f32_smem<TN>(), configured));
+    k_l2l_f32<TN><<<dim3(nbk(max_count, TN), 8), 10 * TN, m2m_f32_smem<TN>(), st>>>(Lo, R, Mo, K, src, dst, zoff,
+                                                                                   in, out);
     KF_LAUNCH();
     return KIFMM_OK;
 }
@@ -1925,6 +2000,14 @@ static int run_far(Plan& p, const EvalView& E, int64_t& nl) {
                                         ptr<int32_t>(p.tc_boxes), ptr<int32_t>(p.ptab), 8,
                                         ptr<int32_t>(p.l2l_slots) + (int64_t)p.tc_first[l] * kSlotStride, p.chi.p,
                                         p.clo.p, ptr<int>(p.cexp), reinterpret_cast<float*>(dd), 1, ptr<int>(p.err)));
+            } else if (LP.l2l_max > 0 && sizeof(T) == 4 && op.rank <= MM_TM && pop.rank <= MM_NS * MM_TK) {
+                // FP32, one block per (octant, tile of parents), every chunk loaded at once (32
+                // parents a tile where that gives every SM two blocks, else 16)
+                auto* fn = 8 * nbk(LP.l2l_max, 32) >= 2u * p.num_sms ? launch_l2l_f32<32> : launch_l2l_f32<16>;
+                KF_TRY(fn(st, ptr<float>(pop.Lo32), R, op.rank, pop.rank, ptr<int32_t>(LP.l2l_src),
+                          ptr<int32_t>(LP.l2l_dst), ptr<int32_t>(LP.l2l_off), (int)LP.l2l_max,
+                          reinterpret_cast<const float*>(dd), reinterpret_cast<float*>(dd)));
+                ++nl;
             } else if (LP.l2l_max > 0)   // one launch, batched over the 8 child octants
                 RUN(launch_apply<T>(st, sel<T>(pop.Lo, pop.Lo32), R, op.rank, pop.rank, ptr<int32_t>(LP.l2l_src),
                                     ptr<int32_t>(LP.l2l_dst), 0, LP.l2l_max, dd, R, dd, R, 1, 1, 0,
