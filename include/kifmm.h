@@ -163,6 +163,9 @@ int kifmm_plan(kifmm_plan_t* out, const double* points_dev, int64_t n,
  *   S_dev  device, N outputs (same dtype), fully overwritten (never accumulated).
  *   C      scale factor (1.0 gives the raw sum).
  * Asynchronous on the plan's stream; allocates nothing; no host synchronisation.
+ * Mixed plans with the lattice near field run its sums on a second stream owned by the
+ * plan, forked from and joined back into the plan's stream by events within the call, so
+ * the whole evaluation stays ordered on the plan's stream (and inside a capture of it).
  * Statuses: KIFMM_ERR_ARG (NULL, bad dtype), KIFMM_ERR_CUDA (launch failure). A bounded
  * device wait that gives up is reported by kifmm_check (below), not by this call.
  */
