@@ -115,10 +115,11 @@ class Operators:
 
 
 def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii=(R_INNER, R_OUTER),
-         cell_dims=None, kind="zheleznyak"):
+         cell_dims=None, kind="zheleznyak", m2l="dense"):
     """cell_dims = (hx, hy, hz): every cell is that rectangular box (the Sec. 4.2 grid; h is
     then ignored): the root takes each axis' own half extent, the weights are hx hy hz (the
-    cell volume, Sec. 3) and the self term is the box's own value."""
+    cell volume, Sec. 3) and the self term is the box's own value. m2l = "fft" takes the V-list
+    translations by FFT (`fft_m2l`) instead of one dense matrix per offset."""
     points = np.asarray(points, dtype=np.float64)
     if cell_dims is not None:
         dims = np.asarray(cell_dims, dtype=np.float64)
@@ -130,7 +131,7 @@ def plan(points, h, leaf_size, m0, a, b, eps=1e-5, origin=None, side=None, radii
     U, V, W, X = _t.build_lists(t)
     ops = Operators(t.side, t.nlevels, m0, a, b, eps, radii, kind)
     return dict(tree=t, perm=perm, U=U, V=V, W=W, X=X, ops=ops, points=points[perm],
-                h=h[perm], a=a, b=b, m0=m0, cell_dims=cell_dims, kind=kind)
+                h=h[perm], a=a, b=b, m0=m0, cell_dims=cell_dims, kind=kind, m2l=m2l)
 
 
 def evaluate(p, I, C=1.0, mode="cell_exact"):
@@ -176,10 +177,15 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
             for A in p["V"][B]:
                 d = t.anchor[A] - t.anchor[B]
                 groups.setdefault(_offset_index(d), []).append((B - lo, A))
-        for key, pairs in groups.items():
-            tb = np.array([x[0] for x in pairs])
-            sa = np.array([x[1] for x in pairs])
-            np.add.at(chk, tb, phi_u[sa] @ ops.m2l[(lev, key)].T)
+        if p.get("m2l", "dense") == "fft":   # the same sums by FFT (the remark after Eq. (m2l))
+            from . import fft_m2l as _fm
+            chk += _fm.m2l_level_fft(ops, lev, t.side / 2.0 ** (lev + 1), range(lo, hi), p["V"], t.anchor,
+                                     phi_u, a, b)
+        else:
+            for key, pairs in groups.items():
+                tb = np.array([x[0] for x in pairs])
+                sa = np.array([x[1] for x in pairs])
+                np.add.at(chk, tb, phi_u[sa] @ ops.m2l[(lev, key)].T)
         for B in range(lo, hi):
             xc = centre[B] + ops.r_in * rad[B] * s
             for A in p["X"][B]:                      # S2L from the sources of leaf A
@@ -219,8 +225,8 @@ def evaluate(p, I, C=1.0, mode="cell_exact"):
 
 
 def kifmm(points, h, I, leaf_size, m0, a, b, C=1.0, mode="cell_exact", eps=1e-5, radii=(R_INNER, R_OUTER),
-          cell_dims=None, kind="zheleznyak", origin=None, side=None):
+          cell_dims=None, kind="zheleznyak", origin=None, side=None, m2l="dense"):
     """The whole method: plan, then evaluate; origin / side give the root cube (else the
     default rule of the tree)."""
     return evaluate(plan(points, h, leaf_size, m0, a, b, eps, origin=origin, side=side, radii=radii,
-                         cell_dims=cell_dims, kind=kind), I, C, mode)
+                         cell_dims=cell_dims, kind=kind, m2l=m2l), I, C, mode)

@@ -709,3 +709,43 @@ def test_l2l_gives_the_childs_local_field(lev):
                for oo in (o, 7 - o)]
         assert _maxrel(got[0], direct) < 5e-3
         assert _maxrel(got[1], direct) > 0.3
+
+
+# ---- the M2L by FFT (the remark after Eq. (m2l)) ----------------------------------------------
+@pytest.mark.parametrize("m0", [4, 6, 8])
+def test_fft_m2l_is_the_dense_translation(m0):
+    # the frequency-space sum over five sources against the dense operators of the same offsets
+    # and against the kernel summed over the explicit surface points
+    from oracle import fft_m2l as F
+    a, b = K.absorption_coefficients(15.2)
+    ops = KF.Operators(1.0, 4, m0, a, b)
+    lev, r = 2, 1.0 / 8
+    rng = np.random.default_rng(m0)
+    s = KF.surface_lattice(m0)
+    srcs, dense, brute = [], np.zeros(ops.S), np.zeros(ops.S)
+    for d in [(3, 1, -2), (2, 0, 0), (-3, -3, 3), (0, -2, 1), (-2, 3, 0)]:
+        phi = rng.standard_normal(ops.S)
+        srcs.append((d, phi))
+        dense += ops.m2l[(lev, KF._offset_index(d))] @ phi
+        x = ops.r_in * r * s
+        y = 2.0 * r * np.asarray(d, dtype=np.float64) + ops.r_in * r * s
+        brute += K.kernel(np.sqrt(((x[:, None, :] - y[None, :, :]) ** 2).sum(-1)), a, b) @ phi
+    got = F.m2l_fft(ops, lev, srcs, r, a, b)
+    assert np.abs(got - dense).max() <= 1e-12 * np.abs(dense).max()
+    assert np.abs(got - brute).max() <= 1e-12 * np.abs(brute).max()
+
+
+def test_kifmm_with_fft_m2l_equals_dense():
+    # the whole oracle FMM with the V-list translations by FFT: the same result as the dense
+    # per-offset matrices, on a uniform grid and on the clustered cloud's adaptive tree
+    a, b = K.absorption_coefficients(15.2)
+    pts, h, I = W.config_uniform(16)
+    d = KF.kifmm(pts, h, I, 8, 6, a, b)
+    f = KF.kifmm(pts, h, I, 8, 6, a, b, m2l="fft")
+    assert np.linalg.norm(f - d) <= 1e-12 * np.linalg.norm(d)
+    pts, h, _ = W.random_cloud(2000, 1)
+    pts[:1000] = 0.31 + 0.07 * pts[:1000]
+    I = np.random.default_rng(1).uniform(0.5, 1.5, len(pts))
+    d = KF.kifmm(pts, h, I, 16, 6, a, b)
+    f = KF.kifmm(pts, h, I, 16, 6, a, b, m2l="fft")
+    assert np.linalg.norm(f - d) <= 1e-12 * np.linalg.norm(d)
