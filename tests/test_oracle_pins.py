@@ -733,6 +733,10 @@ def test_fft_m2l_is_the_dense_translation(m0):
     got = F.m2l_fft(ops, lev, srcs, r, a, b)
     assert np.abs(got - dense).max() <= 1e-12 * np.abs(dense).max()
     assert np.abs(got - brute).max() <= 1e-12 * np.abs(brute).max()
+    # the per-pair work of the cost comparison: N^2 (N/2 + 1) complex products, N = 2 m0
+    n = 2 * m0
+    assert F.flops_per_pair(m0, 128) == {"fft": 8.0 * n * n * (n // 2 + 1), "dense_rank": 32768.0}
+    assert m0 != 6 or F.flops_per_pair(6, 128)["fft"] == 8064.0
 
 
 def test_kifmm_with_fft_m2l_equals_dense():
